@@ -1,0 +1,13 @@
+"""FP64 CPU oracle for the separated fast-spectral Boltzmann collision operator.
+
+TEST INFRASTRUCTURE ONLY.  Tests, the smoke check and the benchmark's CPU
+baseline leg are the only code allowed to import it.  It shares no code with
+the CUDA library (`paper_2112_02695_gb300`), which must never import it.
+
+Modules:
+  quadrature  Gauss-Legendre by Newton, circle rule, octahedral sphere rules
+              derived from their moment equations.
+  collision   the separated algorithm step by step (plain separable DFTs),
+              the brute-force direct sum, projection and moments.
+"""
+from . import quadrature, collision  # noqa: F401
