@@ -1,0 +1,381 @@
+"""Benchmark: batched fast-spectral collision evaluations on GB300.
+
+Workload (default): 3D velocity grid 32^3 on [-8,8]^3, hard spheres gamma = 1,
+R = 8, N_rho = 32 Gauss-Legendre radial nodes x M = 38 sphere directions; a
+rank-16 Hermite-Maxwellian basis (seed 2112) gives the 256 ordered pairs
+Q(V_j, V_l) of one low-rank step plus the 16^3 projection <V_k, Q(V_j, V_l)>.
+One step = spectra of the 16 basis functions + all 256 evaluations + the
+projection, inputs already resident in HBM; metric = collision evaluations/s.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--config c2|c3|c1]
+
+Prints one JSON line on rank 0.  --impl reference times the FP64 CPU oracle
+on a bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+CONFIGS = {
+    # name: (N, d, L, R, gamma, N_rho, M, kind, size)
+    "c2": (32, 3, 8.0, 8.0, 1.0, 32, 38, "pairs", 16),
+    "c3": (32, 3, 8.0, 8.0, 1.0, 32, 38, "cells", 512),
+    "c1": (32, 2, 8.0, 8.0, 0.0, 16, 16, "bkw", 1),
+}
+WORKLOAD_NAMES = {
+    "c2": "lowrank pair batch: 3D 32^3 on [-8,8]^3, gamma=1, R=8, N_rho=32 x M=38, rank 16 -> 256 pairs Q(V_j,V_l) + r^3 projection",
+    "c3": "full-tensor-grid batch: 512 normal-shock cells (Mach 3, d=3), 3D 32^3, gamma=1, R=8, N_rho=32 x M=38",
+    "c1": "single homogeneous Q(f,f): 2D 32^2 on [-8,8]^2, Maxwell molecules, R=8, N_rho=16 x M=16, BKW t0=0.5",
+}
+METRIC = "collision evals/s at 32^3 (batch 256) & % roofline; fast form vs plain FP32"
+L2_FLUSH_BYTES = 512 << 20
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "shift_kernel_traffic.json")
+
+
+# ----------------------------------------------------------------------------- inputs
+
+def make_inputs(cfg_name):
+    from paper_2112_02695_gb300 import workloads as W
+    N, d, L, R, gamma, n_rho, M, kind, size = CONFIGS[cfg_name]
+    if kind == "pairs":
+        fields = W.hermite_maxwellian_basis(N, d, L, size, seed=2112)
+        pairs = [(j, l) for j in range(size) for l in range(size)]
+    elif kind == "cells":
+        fields, _ = W.shock_cells(N, d, L, n_cells=size)
+        pairs = [(x, x) for x in range(size)]
+    else:
+        fields = W.bkw(N, d, L, 0.5)[None]
+        pairs = [(0, 0)]
+    return np.asarray(fields, dtype=np.float32), pairs
+
+
+def flops_per_transform(n):
+    """Nominal real transform of n points: 2.5 n log2 n."""
+    return 2.5 * n * math.log2(n)
+
+
+def algorithmic_flops(cfg_name, n_inputs, pairs):
+    """Algorithmic FP32 work of one step, by step of the method."""
+    N, d, L, R, gamma, n_rho, M, kind, size = CONFIGS[cfg_name]
+    n = N ** d
+    U = len({(min(a, b), max(a, b)) for a, b in pairs})
+    ft = flops_per_transform(n)
+    out = {
+        "spectrum": n_inputs * (ft + 3 * n),
+        "prep": 2 * n_inputs * (ft + 3 * n),
+        "shift": n_rho * M * n_inputs * (ft + 3 * n),
+        "contract": n_rho * M * (2 * U * n + n_inputs * n),
+        "radial": n_rho * U * (ft + 2 * n),
+        "output": U * ft + len(pairs) * 2 * n,
+        "project": (2 * n_inputs ** 3 * n) if kind == "pairs" else 0,
+    }
+    return out
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.proc = None
+        self.lines = []
+        self.device_index = device_index
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device_index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- oracle timing
+
+def oracle_sample(cfg_name, r=4):
+    """A bounded sample of the workload for the FP64 CPU oracle: the first r
+    basis functions (r^2 of the 256 pairs) for the pair batch, 4 cells for the
+    cell batch, the single evaluation for c1."""
+    fields, pairs = make_inputs(cfg_name)
+    N, d, L, R, gamma, n_rho, M, kind, size = CONFIGS[cfg_name]
+    if kind == "pairs":
+        return fields[:r], [(j, l) for j in range(r) for l in range(r)], f"rank-{r} subset: {r * r} of the 256 pairs"
+    if kind == "cells":
+        idx = [0, 200, 256, 511]
+        return fields[idx], [(i, i) for i in range(4)], "4 of the 512 cells"
+    return fields, pairs, "the single evaluation"
+
+
+def time_oracle(cfg_name, r=4):
+    from oracle import collision as C
+    N, d, L, R, gamma, n_rho, M, kind, size = CONFIGS[cfg_name]
+    fields, pairs, desc = oracle_sample(cfg_name, r)
+    prob = C.Problem(N=N, d=d, L=L, R=R, gamma=gamma, n_rho=n_rho, M=M)
+    t0 = time.perf_counter()
+    C.collide_fields(prob, fields.astype(np.float64), pairs)
+    dt = time.perf_counter() - t0
+    return len(pairs) / dt, dt, desc
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count()
+
+
+# ----------------------------------------------------------------------------- main
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="c2", choices=sorted(CONFIGS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    N, d, L, R, gamma, n_rho, M, kind, size = CONFIGS[args.config]
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        ev = []
+        for i in range(args.warmup + args.steps):
+            rate, dt, desc = time_oracle(args.config, r=3)
+            if i >= args.warmup:
+                ev.append(dt)
+        _, pairs_s, desc = oracle_sample(args.config, r=3)
+        value = len(pairs_s) * len(ev) / sum(ev)
+        cores = host_cores()
+        print(json.dumps({
+            "impl": "reference", "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(ev) / len(ev),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD_NAMES[args.config], "sample": desc},
+            "cpu_baseline": {"value": value, "unit": "evals/s", "cores": cores, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }))
+        return
+
+    import torch
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    from paper_2112_02695_gb300 import boltz as B
+
+    fields, pairs = make_inputs(args.config)
+    n_in = fields.shape[0]
+    pj = [p[0] for p in pairs]
+    pl = [p[1] for p in pairs]
+    g = B.boltz_grid_init(N, d, L, R, gamma, n_rho, M)
+    dev = torch.device("cuda", local_rank)
+    f_dev = torch.tensor(fields, device=dev)
+    spec = torch.empty((n_in,) + g.half_shape, dtype=torch.complex64, device=dev)
+    Q = torch.empty((len(pairs),) + g.shape, dtype=torch.float32, device=dev)
+    T = torch.empty((n_in, n_in, n_in), dtype=torch.float32, device=dev) if kind == "pairs" else None
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        B.boltz_spectrum(g, f_dev, out=spec)
+        B.boltz_collide_batched(g, spec, pj, pl, out=Q)
+        if kind == "pairs":
+            B.boltz_project(g, f_dev, Q, out=T)
+
+    def timed(fn, steps):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for e0, e1 in evs:
+            flush.zero_()                      # L2 flush between timed steps (outside the events)
+            e0.record()
+            fn()
+            e1.record()
+        torch.cuda.synchronize()
+        return [e0.elapsed_time(e1) for e0, e1 in evs]
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    B.boltz_profile_read(g, reset=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clk:
+        wall0 = time.perf_counter()
+        times = timed(step, args.steps)
+        wall = time.perf_counter() - wall0
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    counts = B.boltz_profile_read(g, reset=True)
+    gpu_launches = sum(c for c, _ in counts.values())
+    total_ms = sum(times)
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    evals = len(pairs) * args.steps * world
+    value = evals / (total_ms / 1e3)
+    ms_per_step = total_ms / args.steps
+
+    # kernel-level timing: the same steps again with per-launch events on the launching stream
+    B.boltz_profile_enable(g, True)
+    timed(step, args.steps)
+    prof = B.boltz_profile_read(g, reset=True)
+    B.boltz_profile_enable(g, False)
+
+    # end to end through the public C API from pinned host buffers
+    e2e = None
+    if kind == "pairs":
+        Vh = torch.tensor(fields).pin_memory()
+        Qh = torch.empty((len(pairs),) + g.shape, dtype=torch.float32).pin_memory()
+        Th = torch.empty((n_in, n_in, n_in), dtype=torch.float32).pin_memory()
+        for _ in range(2):
+            B.boltz_lowrank_step_host(g, Vh, Qh, Th)
+        te = []
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            B.boltz_lowrank_step_host(g, Vh, Qh, Th)
+            te.append(time.perf_counter() - t0)
+        e2e = {"value": len(pairs) * len(te) / sum(te), "unit": "evals/s",
+               "h2d_bytes_per_step": int(Vh.numel() * 4),
+               "d2h_bytes_per_step": int(Qh.numel() * 4 + Th.numel() * 4)}
+
+    # plain per-evaluation FP32 form on the same batch
+    plain = None
+    if not args.no_plain:
+        Qp = torch.empty_like(Q)
+
+        def step_plain():
+            B.boltz_spectrum(g, f_dev, out=spec)
+            B.boltz_collide_batched(g, spec, pj, pl, form=B.BOLTZ_FORM_PLAIN, out=Qp)
+            if kind == "pairs":
+                B.boltz_project(g, f_dev, Qp, out=T)
+        step_plain()
+        torch.cuda.synchronize()
+        tp = timed(step_plain, max(2, min(5, args.steps // 4)))
+        plain = {"value": len(pairs) * len(tp) / (sum(tp) / 1e3), "unit": "evals/s",
+                 "ms_per_step": sum(tp) / len(tp)}
+        plain["batched_speedup"] = value / world / plain["value"]
+        B.boltz_profile_read(g, reset=True)
+
+    # roofline of the dominant kernel (the shifted-field inverse transforms)
+    props = torch.cuda.get_device_properties(dev)
+    clocks = clk.summary()
+    max_mhz = clocks.get("sm_max_mhz") or 2070.0
+    alu_peak = props.multi_processor_count * 128 * 2 * max_mhz * 1e6 / 1e12    # TFLOP/s FP32
+    fl = algorithmic_flops(args.config, n_in, pairs)
+    launches_s, ms_s = prof["shift"]
+    shift_launches_per_step = launches_s / args.steps
+    avg_launch_ms = ms_s / max(launches_s, 1)
+    flops_per_launch = fl["shift"] / shift_launches_per_step
+    achieved = flops_per_launch / (avg_launch_ms * 1e-3) / 1e12
+    traffic = None
+    try:
+        with open(TRAFFIC_FILE) as fh:
+            tr = json.load(fh)
+        ksrc = open(os.path.join(ROOT, "paper_2112_02695_gb300", "csrc", "kernels.cuh"), "rb").read()
+        fsrc = open(os.path.join(ROOT, "paper_2112_02695_gb300", "csrc", "fft.cuh"), "rb").read()
+        if (tr.get("source_sha256") == hashlib.sha256(ksrc + fsrc).hexdigest()
+                and tr.get("config") == args.config):
+            traffic = tr["bytes_per_launch"]
+    except (OSError, ValueError, KeyError):
+        traffic = None
+    total_ms_prof = sum(ms for _, ms in prof.values())
+    shares = {k: round(ms / total_ms_prof, 4) for k, (_, ms) in prof.items() if ms > 0}
+    step_flops = sum(fl.values())
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, dt, desc = time_oracle(args.config)
+        cpu = {"value": rate, "unit": "evals/s", "cores": host_cores(), "kind": "oracle",
+               "sample": f"{desc}; {dt:.1f} s of FP64 numpy/BLAS on the host"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAMES[args.config], "evals_per_step": len(pairs),
+                       "l2": "flushed between timed steps (512 MB write outside the timed events)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                         "frac": achieved / alu_peak, "traffic": traffic,
+                         "kernel": "k_synth (phase-weighted inverse 3D transforms of the shifted fields)",
+                         "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz",
+                         "step_alu_frac": (step_flops / (ms_per_step * 1e-3) / 1e12) / alu_peak},
+            "kernel_shares": shares,
+            "gpu_launches": gpu_launches,
+            "clocks": clocks,
+            "e2e": e2e,
+            "plain_fp32": plain,
+            "cpu_baseline": cpu,
+            "wall_s_timed_region": wall,
+        }
+        print(json.dumps(line))
+    g.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

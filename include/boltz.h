@@ -1,0 +1,235 @@
+/*
+ * boltz.h -- C ABI of the GB300 (sm_103a) fast-spectral Boltzmann collision library.
+ *
+ * The library evaluates the bilinear collision operator of the paper's Sec. 1
+ * (eq. "eqn:collision_operator", post-collision velocities eq.
+ * "eqn:collision velocity") as a discrete-velocity method (Sec. 2.1): values of
+ * h1, h2 on a uniform grid of [-L, L]^d in, values of Q(h1, h2) on the same
+ * grid out.  The collision kernel is the truncated VHS kernel
+ * B = b |q|^gamma for |q| <= R, q = v - v_*.  The integral is evaluated by the
+ * separated fast-spectral quadrature: Gauss-Legendre radial nodes rho_q on
+ * [0, R] times a centrally symmetric direction rule sigma_p on S^{d-1}; for
+ * every node both functions are phase-shifted in Fourier space, transformed
+ * back, multiplied and summed over directions, then one forward transform per
+ * radial node applies the exact omega-average
+ * F_3(s) = 4 pi sin(s)/s, F_2(s) = 2 pi J0(s), s = pi rho_q |k| / (2L).
+ * Batches follow Sec. 2 and Sec. 2.4: the r^2 basis pairs Q(V_m, V_n) of the
+ * K-, S- and L-steps and the projection <V_j, Q(V_m, V_n)>_v, or one
+ * evaluation per spatial cell for the full tensor grid.
+ *
+ * Conventions (all fixed by this header):
+ *   grid        v_j = -L + j * dv, dv = 2L/N, j = 0..N-1 along every axis; a
+ *               physical field is float32 [N]^d, C order, axis 0 slowest.
+ *   spectra     fhat_k = N^-d sum_j f(v_j) exp(-i pi k.v_j / L), k_a in
+ *               [-N/2, N/2).  Stored as the real-to-complex half spectrum:
+ *               complex64 (float2 re, im) [N]^(d-1) x [N/2 + 1], last axis
+ *               holding k = 0..N/2, other axes in DFT index order
+ *               (index i <-> k = i for i < N/2, i - N otherwise).
+ *               Entries with any k_a = -N/2 (index N/2) are the Nyquist modes;
+ *               they are IGNORED on input (treated as zero), and
+ *               boltz_spectrum writes them as zero.
+ *   kernel      b defaults to 1/|S^{d-1}| (1/(2 pi) in 2D, 1/(4 pi) in 3D).
+ *   loss        Q-(g,f)(v) = f_N(v) * sum_l G-(l) ghat_l exp(i pi l.v / L),
+ *               G-(l) = b |S^{d-1}| sum_q w_q rho_q^(gamma+d-1) F_d(pi rho_q |l| / L).
+ *   pairs       evaluation e computes Q(g, f) with g = input pair_j[e] and
+ *               f = input pair_l[e]; the gain part is symmetric in (g, f),
+ *               the loss part is not.
+ *
+ * Memory: every data pointer marked "device" is caller-owned device memory
+ * (for example a torch tensor's data_ptr) that must stay valid until the work
+ * queued on `stream` has completed; the library reads and writes it
+ * asynchronously on that stream.  Pointers marked "host" are read or written
+ * synchronously during the call.  The library owns only the grid handle, its
+ * tables and its workspace, allocated on the device that is current when the
+ * grid is created; all later calls must be made with that device current.
+ *
+ * Errors: every entry point returns a boltz_status and never throws.  Argument
+ * checks are synchronous and leave device memory untouched.  BOLTZ_ECUDA
+ * reports a failed CUDA call (launch or allocation); a context error is
+ * sticky in CUDA, so the grid should then be destroyed.
+ *
+ * Threading: a grid handle is not thread safe; distinct handles are
+ * independent.  Calls on one handle must not overlap on different streams
+ * (they share the handle's workspace).
+ */
+#ifndef BOLTZ_H
+#define BOLTZ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BOLTZ_ABI_VERSION 1
+
+typedef struct boltz_grid_s* boltz_grid;
+
+typedef enum {
+    BOLTZ_OK = 0,
+    BOLTZ_EINVAL = 1,        /* bad argument (size, pointer, index)            */
+    BOLTZ_ENOMEM = 2,        /* host or device allocation failed               */
+    BOLTZ_ECUDA = 3,         /* a CUDA runtime call failed                     */
+    BOLTZ_ETIMEOUT = 4,      /* a bounded device wait gave up                  */
+    BOLTZ_EUNSUPPORTED = 5,  /* valid request this build does not implement    */
+    BOLTZ_ENONFINITE = 6     /* non-finite value detected                      */
+} boltz_status;
+
+/* Evaluation forms of boltz_collide_batched. */
+typedef enum {
+    /* Batched form: every distinct input's shifted fields are computed once
+     * per node and shared by all pairs that use it (the f-side field of
+     * direction p is the g-side field of the antipodal direction), and the
+     * symmetric gain is computed once per unordered pair.  FP32 arithmetic. */
+    BOLTZ_FORM_BATCHED = 0,
+    /* Plain per-evaluation form: two inverse transforms per (rho, sigma) node
+     * and evaluation, nothing shared between evaluations.  FP32.  Same result
+     * up to FP32 rounding; kept as the comparison baseline. */
+    BOLTZ_FORM_PLAIN = 1
+} boltz_form;
+
+typedef struct {
+    double b;              /* kernel constant; <= 0 selects 1/|S^{d-1}|              */
+    size_t workspace_max;  /* cap on device workspace in bytes; 0 = library default */
+} boltz_options;
+
+/* Library ABI version (BOLTZ_ABI_VERSION of the build). */
+int boltz_abi_version(void);
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char* boltz_status_string(boltz_status s);
+
+/*
+ * Create a grid: N points per axis on [-L, L]^d_v, truncation radius R,
+ * kernel exponent gamma, N_rho Gauss-Legendre radial nodes on [0, R] and M
+ * directions (paper Sec. 2.1: uniform grid, fast spectral collision solver).
+ *   N      in {8, 16, 32} for d_v = 3; in {8, 16, 32, 64} for d_v = 2
+ *   d_v    2 or 3
+ *   M      d_v = 2: even, 2..256 (uniform circle rule theta_p = 2 pi p / M);
+ *          d_v = 3: one of 6, 14, 26, 38, 50, 86 (octahedral rules of design
+ *          degree 3, 5, 7, 9, 11, 15, derived at init from their moment
+ *          equations)
+ *   N_rho  1..128;  L > 0;  R > 0;  gamma > -d_v
+ *   opt    may be NULL (defaults)
+ * Allocates the handle and its device tables on the current device.
+ * Errors: BOLTZ_EINVAL (out may be NULL or a value is out of range; *out is
+ * left untouched), BOLTZ_EUNSUPPORTED (valid but not built, e.g. N = 64 in
+ * 3D), BOLTZ_ENOMEM, BOLTZ_ECUDA.
+ */
+boltz_status boltz_grid_init(boltz_grid* out, int N, int d_v, double L, double R, double gamma,
+                             int N_rho, int M, const boltz_options* opt);
+
+/* Free the handle, its tables and its workspace (synchronises the device first).
+ * NULL is accepted and ignored. */
+boltz_status boltz_grid_destroy(boltz_grid g);
+
+/*
+ * Input spectra of real fields (paper Sec. 2.1: values on the grid are the
+ * method's input): spectra_out[i] = half spectrum of f[i] in the convention
+ * above, Nyquist entries zero.
+ *   f            device float32 [n_inputs][N^d]
+ *   spectra_out  device complex64 [n_inputs][N^(d-1) * (N/2+1)]
+ * n_inputs = 0 is a no-op.  Errors: BOLTZ_EINVAL (NULL grid/pointer with
+ * n_inputs > 0, n_inputs < 0), BOLTZ_ECUDA.
+ */
+boltz_status boltz_spectrum(boltz_grid g, const float* f, int n_inputs, void* spectra_out,
+                            void* stream);
+
+/*
+ * Batched collision evaluations (paper Sec. 2.1 interface, batched over the
+ * basis pairs of Sec. 2.4's K-, S- and L-steps or over spatial cells):
+ *   Q_out[e] = Q(g = input pair_j[e], f = input pair_l[e]) on the grid.
+ *   spectra  device complex64 [n_inputs][N^(d-1) * (N/2+1)] (see boltz_spectrum)
+ *   pair_j, pair_l  HOST int32 [n_pairs], each in [0, n_inputs)
+ *   Q_out    device float32 [n_pairs][N^d]
+ *   form     a boltz_form value
+ * Work is queued on `stream` (a cudaStream_t, NULL = legacy default stream);
+ * the call returns once it is queued.  n_pairs = 0 is a no-op.
+ * Device workspace is allocated on first use and grown when a larger batch
+ * needs it (cudaMalloc; the grid keeps it until destroyed).
+ * Errors: BOLTZ_EINVAL (NULL pointers, n_inputs <= 0 with n_pairs > 0, an
+ * index out of range, unknown form), BOLTZ_ENOMEM, BOLTZ_ECUDA.
+ */
+boltz_status boltz_collide_batched(boltz_grid g, const void* spectra, int n_inputs,
+                                   const int32_t* pair_j, const int32_t* pair_l, int n_pairs,
+                                   float* Q_out, int form, void* stream);
+
+/*
+ * Projection tensor of the K- and S-steps (paper Sec. 2, eq. "eqn:K-step
+ * detailed"; Sec. 2.4 evaluates <.,.>_v with the midpoint rule):
+ *   T_out[k][j][l] = dv^d sum_v V_k(v) Q_{j*r + l}(v),  k, j, l in [0, r).
+ *   V      device float32 [r][N^d]      (physical values of the basis)
+ *   Q      device float32 [r*r][N^d]    (pair p = j*r + l, as produced by
+ *                                        boltz_collide_batched over all r^2 pairs)
+ *   T_out  device float32 [r][r][r]
+ * r in 1..64.  Errors: BOLTZ_EINVAL, BOLTZ_ECUDA.
+ */
+boltz_status boltz_project(boltz_grid g, const float* V, int r, const float* Q, float* T_out,
+                           void* stream);
+
+/*
+ * End-to-end low-rank collision step from host memory: copies the physical
+ * basis V (HOST float32 [r][N^d]) to the device, computes its spectra, all r^2
+ * pairs Q(V_j, V_l) (batched form) and the projection T, and copies Q (HOST
+ * float32 [r*r][N^d], may be NULL to skip the copy) and T (HOST float32
+ * [r][r][r]) back.  Synchronises `stream` before returning.  Device staging
+ * buffers come from the grid's workspace.  Host buffers that are page-locked
+ * (cudaHostAlloc / pinned torch tensors) give full copy bandwidth.
+ * Errors: BOLTZ_EINVAL, BOLTZ_ENOMEM, BOLTZ_ECUDA.
+ */
+boltz_status boltz_lowrank_step_host(boltz_grid g, const float* V_host, int r, float* Q_host,
+                                     float* T_host, void* stream);
+
+/*
+ * Quadrature the library uses, computed on the host without a GPU (for
+ * checking against an independent implementation):
+ *   rho, w_rho      HOST double [N_rho]   Gauss-Legendre on [0, R]
+ *   sigma, w_sigma  HOST double [M][d_v], [M]   direction rule
+ * Errors: BOLTZ_EINVAL (unsupported d_v / M / N_rho, NULL pointer).
+ */
+boltz_status boltz_host_quadrature(int d_v, int N_rho, int M, double R, double* rho,
+                                   double* w_rho, double* sigma, double* w_sigma);
+
+/*
+ * Size of the device workspace a batched call would use for this batch, in
+ * bytes, without allocating (host-only planning).  Same argument rules as
+ * boltz_collide_batched; `bytes` is HOST size_t.
+ */
+boltz_status boltz_workspace_size(boltz_grid g, int n_inputs, const int32_t* pair_j,
+                                  const int32_t* pair_l, int n_pairs, int form, size_t* bytes);
+
+/* Kernel classes reported by boltz_profile_read. */
+typedef enum {
+    BOLTZ_KCLASS_SPECTRUM = 0,  /* input spectra (forward real transforms)                  */
+    BOLTZ_KCLASS_PREP = 1,      /* f_N and Lambda_g of a chunk's inputs                       */
+    BOLTZ_KCLASS_SHIFT = 2,     /* phase-weighted inverse transforms: the shifted fields      */
+    BOLTZ_KCLASS_CONTRACT = 3,  /* sigma-contraction of shifted-field products                */
+    BOLTZ_KCLASS_RADIAL = 4,    /* forward transform x radial multiplier, accumulated over q  */
+    BOLTZ_KCLASS_OUTPUT = 5,    /* gain synthesis minus loss, written per ordered pair        */
+    BOLTZ_KCLASS_PROJECT = 6,   /* projection tensor (two kernels)                            */
+    BOLTZ_KCLASS_COUNT = 7
+} boltz_kernel_class;
+
+/*
+ * Launch accounting and kernel timing (tracing aid; not part of the paper).
+ * Every kernel launch is counted per class.  While profiling is enabled, each
+ * launch is bracketed by a CUDA event pair recorded on its own stream, so the
+ * durations are device times of the kernels themselves (the event records
+ * add a few microseconds per launch to a step).
+ */
+boltz_status boltz_profile_enable(boltz_grid g, int enable);
+
+/*
+ * launches: HOST long long [BOLTZ_KCLASS_COUNT] launches since the last reset;
+ * ms:       HOST double [BOLTZ_KCLASS_COUNT] summed event durations in
+ *           milliseconds of the profiled launches (waits for them to finish).
+ * reset != 0 clears both afterwards.  Errors: BOLTZ_EINVAL, BOLTZ_ECUDA.
+ */
+boltz_status boltz_profile_read(boltz_grid g, int reset, long long* launches, double* ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BOLTZ_H */

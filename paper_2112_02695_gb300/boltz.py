@@ -1,0 +1,254 @@
+"""Thin ctypes binding of libboltz.so (include/boltz.h), same names as the C ABI.
+
+Argument marshalling only: tensors are passed as raw device pointers on the
+caller's current CUDA stream; every computation runs in the library's
+kernels.  There is no fallback: if the shared library cannot be loaded the
+import of this module raises, and every status other than BOLTZ_OK raises
+BoltzError.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+BOLTZ_OK = 0
+BOLTZ_EINVAL = 1
+BOLTZ_ENOMEM = 2
+BOLTZ_ECUDA = 3
+BOLTZ_ETIMEOUT = 4
+BOLTZ_EUNSUPPORTED = 5
+BOLTZ_ENONFINITE = 6
+
+BOLTZ_FORM_BATCHED = 0
+BOLTZ_FORM_PLAIN = 1
+
+EXPORTED = (
+    "boltz_abi_version", "boltz_status_string", "boltz_grid_init", "boltz_grid_destroy",
+    "boltz_spectrum", "boltz_collide_batched", "boltz_project", "boltz_lowrank_step_host",
+    "boltz_host_quadrature", "boltz_workspace_size", "boltz_profile_enable", "boltz_profile_read",
+)
+
+KERNEL_CLASSES = ("spectrum", "prep", "shift", "contract", "radial", "output", "project")
+
+
+class BoltzError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)} (status {status})")
+
+
+class _Options(ctypes.Structure):
+    _fields_ = [("b", ctypes.c_double), ("workspace_max", ctypes.c_size_t)]
+
+
+def _load() -> ctypes.CDLL:
+    path = os.environ.get("BOLTZ_LIB") or _build.LIB
+    if not os.path.exists(path):
+        raise ImportError(f"libboltz.so not built ({path}); run python -m paper_2112_02695_gb300.build")
+    lib = ctypes.CDLL(path)
+    vp, i32p, f64p = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)
+    sig = {
+        "boltz_abi_version": ([], ctypes.c_int),
+        "boltz_status_string": ([ctypes.c_int], ctypes.c_char_p),
+        "boltz_grid_init": ([ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                             ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_Options)], ctypes.c_int),
+        "boltz_grid_destroy": ([vp], ctypes.c_int),
+        "boltz_spectrum": ([vp, vp, ctypes.c_int, vp, vp], ctypes.c_int),
+        "boltz_collide_batched": ([vp, vp, ctypes.c_int, i32p, i32p, ctypes.c_int, vp, ctypes.c_int, vp],
+                                  ctypes.c_int),
+        "boltz_project": ([vp, vp, ctypes.c_int, vp, vp, vp], ctypes.c_int),
+        "boltz_lowrank_step_host": ([vp, vp, ctypes.c_int, vp, vp, vp], ctypes.c_int),
+        "boltz_host_quadrature": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, f64p, f64p, f64p,
+                                   f64p], ctypes.c_int),
+        "boltz_workspace_size": ([vp, ctypes.c_int, i32p, i32p, ctypes.c_int, ctypes.c_int,
+                                  ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+        "boltz_profile_enable": ([vp, ctypes.c_int], ctypes.c_int),
+        "boltz_profile_read": ([vp, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
+                                ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    return lib
+
+
+_lib = _load()
+LIB_PATH = _lib._name
+
+
+def status_string(status: int) -> str:
+    return _lib.boltz_status_string(int(status)).decode()
+
+
+def _check(status: int, what: str):
+    if status != BOLTZ_OK:
+        raise BoltzError(status, what)
+
+
+def boltz_abi_version() -> int:
+    return _lib.boltz_abi_version()
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev_ptr(t, dtype_name: str, what: str):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{what} must be a CUDA tensor")
+    if str(t.dtype) != f"torch.{dtype_name}":
+        raise TypeError(f"{what} must be {dtype_name}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Grid:
+    """Owning wrapper of a boltz_grid handle."""
+
+    def __init__(self, handle, N, d_v, L, R, gamma, N_rho, M, b):
+        self.handle = handle
+        self.N, self.d_v, self.L, self.R, self.gamma, self.N_rho, self.M, self.b = N, d_v, L, R, gamma, N_rho, M, b
+        self.n = N ** d_v
+        self.half = N ** (d_v - 1) * (N // 2 + 1)
+
+    @property
+    def shape(self):
+        return (self.N,) * self.d_v
+
+    @property
+    def half_shape(self):
+        return (self.N,) * (self.d_v - 1) + (self.N // 2 + 1,)
+
+    def close(self):
+        if self.handle:
+            _lib.boltz_grid_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def boltz_grid_init(N: int, d_v: int, L: float, R: float, gamma: float, N_rho: int, M: int,
+                    b: float | None = None, workspace_max: int = 0) -> Grid:
+    h = ctypes.c_void_p()
+    opt = _Options(b if b is not None else 0.0, workspace_max)
+    _check(_lib.boltz_grid_init(ctypes.byref(h), N, d_v, L, R, gamma, N_rho, M, ctypes.byref(opt)),
+           "boltz_grid_init")
+    area = 2 * np.pi if d_v == 2 else 4 * np.pi
+    return Grid(h, N, d_v, L, R, gamma, N_rho, M, b if b is not None else 1.0 / area)
+
+
+def boltz_grid_destroy(grid: Grid):
+    grid.close()
+
+
+def boltz_spectrum(grid: Grid, f, out=None, stream=None):
+    """Half spectra (complex64 [n_inputs, *half_shape]) of real fields f [n_inputs, *shape]."""
+    import torch
+    n_in = f.shape[0]
+    if out is None:
+        out = torch.empty((n_in,) + grid.half_shape, dtype=torch.complex64, device=f.device)
+    _check(_lib.boltz_spectrum(grid.handle, _dev_ptr(f, "float32", "f"), n_in,
+                               _dev_ptr(out, "complex64", "out"), _stream_ptr(stream)), "boltz_spectrum")
+    return out
+
+
+def _pairs(pair_j, pair_l):
+    pj = np.ascontiguousarray(np.asarray(pair_j, dtype=np.int32))
+    pl = np.ascontiguousarray(np.asarray(pair_l, dtype=np.int32))
+    if pj.shape != pl.shape or pj.ndim != 1:
+        raise ValueError("pair_j and pair_l must be 1-D of equal length")
+    return pj, pl
+
+
+def boltz_collide_batched(grid: Grid, spectra, pair_j, pair_l, form: int = BOLTZ_FORM_BATCHED, out=None,
+                          stream=None):
+    """Q(g = input pair_j[e], f = input pair_l[e]) for every e: float32 [n_pairs, *shape]."""
+    import torch
+    pj, pl = _pairs(pair_j, pair_l)
+    if out is None:
+        out = torch.empty((len(pj),) + grid.shape, dtype=torch.float32, device=spectra.device)
+    i32p = ctypes.POINTER(ctypes.c_int32)
+    _check(_lib.boltz_collide_batched(grid.handle, _dev_ptr(spectra, "complex64", "spectra"), spectra.shape[0],
+                                      pj.ctypes.data_as(i32p), pl.ctypes.data_as(i32p), len(pj),
+                                      _dev_ptr(out, "float32", "out"), int(form), _stream_ptr(stream)),
+           "boltz_collide_batched")
+    return out
+
+
+def boltz_project(grid: Grid, V, Q, out=None, stream=None):
+    """T[k, j, l] = dv^d sum_v V_k Q_{j*r+l}: float32 [r, r, r]."""
+    import torch
+    r = V.shape[0]
+    if Q.shape[0] != r * r:
+        raise ValueError("Q must hold r*r fields")
+    if out is None:
+        out = torch.empty((r, r, r), dtype=torch.float32, device=V.device)
+    _check(_lib.boltz_project(grid.handle, _dev_ptr(V, "float32", "V"), r, _dev_ptr(Q, "float32", "Q"),
+                              _dev_ptr(out, "float32", "out"), _stream_ptr(stream)), "boltz_project")
+    return out
+
+
+def boltz_lowrank_step_host(grid: Grid, V_host, Q_host=None, T_host=None, stream=None):
+    """Host-memory end-to-end step: V (host float32 [r, *shape]) -> Q (host, optional), T (host)."""
+    import torch
+    r = V_host.shape[0]
+    if T_host is None:
+        T_host = torch.empty((r, r, r), dtype=torch.float32)
+    for name, t in (("V_host", V_host), ("Q_host", Q_host), ("T_host", T_host)):
+        if t is not None and (t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous()):
+            raise TypeError(f"{name} must be a contiguous float32 CPU tensor")
+    qp = ctypes.c_void_p(Q_host.data_ptr()) if Q_host is not None else None
+    _check(_lib.boltz_lowrank_step_host(grid.handle, ctypes.c_void_p(V_host.data_ptr()), r, qp,
+                                        ctypes.c_void_p(T_host.data_ptr()), _stream_ptr(stream)),
+           "boltz_lowrank_step_host")
+    return Q_host, T_host
+
+
+def boltz_host_quadrature(d_v: int, N_rho: int, M: int, R: float):
+    """(rho, w_rho, sigma [M, d_v], w_sigma) as the library computes them (no GPU needed)."""
+    rho = np.zeros(N_rho)
+    wr = np.zeros(N_rho)
+    sig = np.zeros(M * d_v)
+    ws = np.zeros(M)
+    f64p = ctypes.POINTER(ctypes.c_double)
+    _check(_lib.boltz_host_quadrature(d_v, N_rho, M, R, rho.ctypes.data_as(f64p), wr.ctypes.data_as(f64p),
+                                      sig.ctypes.data_as(f64p), ws.ctypes.data_as(f64p)), "boltz_host_quadrature")
+    return rho, wr, sig.reshape(M, d_v), ws
+
+
+def boltz_workspace_size(grid: Grid, n_inputs: int, pair_j, pair_l, form: int = BOLTZ_FORM_BATCHED) -> int:
+    pj, pl = _pairs(pair_j, pair_l)
+    out = ctypes.c_size_t()
+    i32p = ctypes.POINTER(ctypes.c_int32)
+    _check(_lib.boltz_workspace_size(grid.handle, n_inputs, pj.ctypes.data_as(i32p), pl.ctypes.data_as(i32p),
+                                     len(pj), int(form), ctypes.byref(out)), "boltz_workspace_size")
+    return out.value
+
+
+def boltz_profile_enable(grid: Grid, enable: bool = True):
+    _check(_lib.boltz_profile_enable(grid.handle, int(bool(enable))), "boltz_profile_enable")
+
+
+def boltz_profile_read(grid: Grid, reset: bool = True):
+    """{class: (launches, total_ms)} since the last reset (see KERNEL_CLASSES)."""
+    n = len(KERNEL_CLASSES)
+    la = (ctypes.c_longlong * n)()
+    ms = (ctypes.c_double * n)()
+    _check(_lib.boltz_profile_read(grid.handle, int(bool(reset)), la, ms), "boltz_profile_read")
+    return {name: (int(la[i]), float(ms[i])) for i, name in enumerate(KERNEL_CLASSES)}

@@ -1,0 +1,874 @@
+// C ABI of the GB300 fast-spectral collision library (see include/boltz.h).
+//
+// Host side: grid creation (quadrature, FP64 tables rounded once to FP32),
+// batch planning (chunks of inputs, gain slots, contraction tiles, radial
+// node blocks), workspace management and kernel launches.  Every step of the
+// collision evaluation runs in the kernels of kernels.cuh.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <set>
+#include <utility>
+#include <vector>
+
+#include "boltz.h"
+#include "kernels.cuh"
+#include "quadrature.hpp"
+
+using namespace boltz_dev;
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr size_t kDefaultWorkspace = size_t(8) << 30;    // hard cap
+constexpr size_t kFieldBudget = size_t(96) << 20;        // shifted fields per radial block
+
+#define BZ_CUDA(call)                                  \
+    do {                                               \
+        cudaError_t e_ = (call);                       \
+        if (e_ != cudaSuccess) return BOLTZ_ECUDA;     \
+    } while (0)
+
+// ------------------------------------------------------------------ plan
+
+struct ChunkPlan {
+    std::vector<int> inputs;                      // chunk-local -> global input
+    std::vector<Tile> tiles[3];                   // TRI16/TRI8, FULL16/FULL8, LIST16
+    int tile_T = 16;                              // block width of TRI/FULL tiles
+    std::vector<int> out_start;                   // [U+1]
+    std::vector<int4> outs;                       // (e, jloc, lloc, 0)
+    int U = 0;
+    // offsets of this chunk's descriptors inside the device plan buffer (bytes)
+    size_t off_inputs = 0, off_tiles[3] = {0, 0, 0}, off_start = 0, off_outs = 0;
+};
+
+struct Plan {
+    std::vector<ChunkPlan> chunks;
+    int nq = 1;
+    int max_nc = 0, max_U = 0;
+    size_t plan_bytes = 0;
+    // workspace layout (byte offsets)
+    size_t off_plan = 0, off_A = 0, off_P = 0, off_qhat = 0, off_fN = 0, off_lam = 0, total = 0;
+};
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace
+
+struct boltz_grid_s {
+    int N = 0, D = 0, n_rho = 0, M = 0, device = 0;
+    double L = 0, R = 0, gamma = 0, b = 0;
+    int n = 0, half = 0, smax = 0;
+    std::vector<double> rho, w_rho;
+    boltz::DirectionRule dir;
+    // device tables
+    float2* d_phase = nullptr;   // [(n_rho*M + 1)][D][N]
+    float* d_ctab = nullptr;     // [n_rho][smax+1]
+    float* d_gm = nullptr;       // [smax+1]
+    float* d_w = nullptr;        // [M]
+    int* d_anti = nullptr;       // [M]
+    // workspace
+    char* d_ws = nullptr;
+    size_t ws_cap = 0, ws_max = kDefaultWorkspace;
+    // last plan (reused when the same pair list comes back)
+    std::vector<int32_t> last_j, last_l;
+    int last_form = -1, last_n_inputs = -1;
+    Plan last_plan;
+    bool plan_uploaded = false;
+    // profiling: launches per kernel class (always counted) and, when enabled,
+    // an event pair around every launch on the launching stream
+    bool prof_on = false;
+    long long launches[BOLTZ_KCLASS_COUNT] = {};
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_events;
+    std::vector<cudaEvent_t> event_pool;
+};
+
+namespace {
+
+bool supported_shape(int N, int D) {
+    if (D == 3) return N == 8 || N == 16 || N == 32;
+    if (D == 2) return N == 8 || N == 16 || N == 32 || N == 64;
+    return false;
+}
+
+
+// ---------------------------------------------------------------- planning
+
+// Build the chunk/tile/slot structure of a batch.  BATCHED: unordered gain
+// slots shared by (j,l) and (l,j), inputs shared by every pair in a chunk.
+// PLAIN: every evaluation gets its own two inputs and its own slot.
+boltz_status build_plan(const boltz_grid_s* g, int n_inputs, const int32_t* pj, const int32_t* pl, int n_pairs,
+                        int form, Plan& plan) {
+    plan = Plan();
+    const size_t field_bytes = size_t(g->n) * 4;
+    // inputs per chunk so that one radial node's shifted fields fit the budget
+    int nc_cap = (int)std::max<size_t>(2, kFieldBudget / (field_bytes * g->M));
+    nc_cap = std::min(nc_cap, 64);
+    if (form == BOLTZ_FORM_PLAIN) {
+        const int E = std::max(1, nc_cap / 2);
+        for (int e0 = 0; e0 < n_pairs; e0 += E) {
+            ChunkPlan c;
+            const int ne = std::min(E, n_pairs - e0);
+            for (int e = 0; e < ne; ++e) {
+                c.inputs.push_back(pj[e0 + e]);
+                c.inputs.push_back(pl[e0 + e]);
+            }
+            for (int t0 = 0; t0 < ne; t0 += 16) {
+                Tile t;
+                std::memset(&t, 0, sizeof(t));
+                t.slot0 = t0;
+                t.count = std::min(16, ne - t0);
+                for (int i = 0; i < 16; ++i) {
+                    const int e = t0 + std::min(i, t.count - 1);
+                    t.ja[i] = 2 * e;
+                    t.lb[i] = 2 * e + 1;
+                }
+                c.tiles[TILE_LIST].push_back(t);
+            }
+            c.U = ne;
+            c.out_start.resize(ne + 1);
+            for (int e = 0; e < ne; ++e) {
+                c.out_start[e] = e;
+                c.outs.push_back(make_int4(e0 + e, 2 * e, 2 * e + 1, 0));
+            }
+            c.out_start[ne] = ne;
+            plan.chunks.push_back(std::move(c));
+        }
+    } else {
+        // unordered slots in first-appearance order, with their ordered outputs
+        std::map<std::pair<int, int>, int> slot_of;
+        std::vector<std::pair<int, int>> slots;
+        std::vector<std::vector<std::pair<int, int>>> slot_outs;   // (e, which-first)
+        for (int e = 0; e < n_pairs; ++e) {
+            const int a = std::min(pj[e], pl[e]), b = std::max(pj[e], pl[e]);
+            auto it = slot_of.find({a, b});
+            int s;
+            if (it == slot_of.end()) {
+                s = (int)slots.size();
+                slot_of[{a, b}] = s;
+                slots.push_back({a, b});
+                slot_outs.emplace_back();
+            } else {
+                s = it->second;
+            }
+            slot_outs[s].push_back({e, 0});
+        }
+        // greedy chunking by input set
+        std::vector<std::vector<int>> chunk_slots;
+        std::vector<std::set<int>> chunk_inputs;
+        for (int s = 0; s < (int)slots.size(); ++s) {
+            const int a = slots[s].first, b = slots[s].second;
+            bool placed = false;
+            if (!chunk_slots.empty()) {
+                std::set<int>& cur = chunk_inputs.back();
+                int grow = (cur.count(a) ? 0 : 1) + (a != b && !cur.count(b) ? 1 : 0);
+                if ((int)cur.size() + grow <= nc_cap) {
+                    cur.insert(a);
+                    cur.insert(b);
+                    chunk_slots.back().push_back(s);
+                    placed = true;
+                }
+            }
+            if (!placed) {
+                chunk_slots.push_back({s});
+                chunk_inputs.push_back({a, b});
+            }
+        }
+        for (size_t ci = 0; ci < chunk_slots.size(); ++ci) {
+            ChunkPlan c;
+            c.inputs.assign(chunk_inputs[ci].begin(), chunk_inputs[ci].end());
+            std::map<int, int> loc;
+            for (int i = 0; i < (int)c.inputs.size(); ++i) loc[c.inputs[i]] = i;
+            const int nc = (int)c.inputs.size();
+            // local pair set
+            std::map<std::pair<int, int>, int> local;   // (ja <= lb) -> global slot id
+            for (int s : chunk_slots[ci]) local[{loc[slots[s].first], loc[slots[s].second]}] = s;
+            const int T = nc >= 16 ? 16 : 8;
+            c.tile_T = T;
+            std::vector<std::pair<int, int>> order;     // local slot order
+            std::set<std::pair<int, int>> covered;
+            auto new_tile = [&](int kind, int j0, int l0, int tj, int tl_) {
+                Tile t;
+                std::memset(&t, 0, sizeof(t));
+                t.slot0 = (int)order.size();
+                t.j0 = j0;
+                t.l0 = l0;
+                for (int x = 0; x < tj; ++x)
+                    for (int y = (kind == TILE_TRI ? x : 0); y < tl_; ++y) {
+                        order.push_back({j0 + x, l0 + y});
+                        covered.insert({j0 + x, l0 + y});
+                    }
+                t.count = (int)order.size() - t.slot0;
+                c.tiles[kind].push_back(t);
+            };
+            if (nc >= 8) {
+                const int nb = nc / T;                  // full-width blocks only
+                for (int J = 0; J < nb; ++J) {
+                    for (int Lb = J; Lb < nb; ++Lb) {
+                        bool full = true;
+                        for (int x = 0; x < T && full; ++x)
+                            for (int y = (J == Lb ? x : 0); y < T && full; ++y)
+                                full = local.count({J * T + x, Lb * T + y}) > 0;
+                        if (!full) continue;
+                        if (J == Lb) {
+                            new_tile(TILE_TRI, J * T, J * T, T, T);
+                        } else {
+                            // off-diagonal block as 8-row strips (8 x T accumulators per thread)
+                            for (int x0 = 0; x0 < T; x0 += 8) new_tile(TILE_FULL, J * T + x0, Lb * T, 8, T);
+                        }
+                    }
+                }
+            }
+            std::vector<std::pair<int, int>> rest;
+            for (auto& kv : local)
+                if (!covered.count(kv.first)) rest.push_back(kv.first);
+            for (size_t t0 = 0; t0 < rest.size(); t0 += 16) {
+                Tile t;
+                std::memset(&t, 0, sizeof(t));
+                t.slot0 = (int)order.size();
+                t.count = (int)std::min<size_t>(16, rest.size() - t0);
+                for (int i = 0; i < 16; ++i) {
+                    const auto& pr = rest[t0 + std::min(i, t.count - 1)];
+                    t.ja[i] = pr.first;
+                    t.lb[i] = pr.second;
+                }
+                for (int i = 0; i < t.count; ++i) order.push_back(rest[t0 + i]);
+                c.tiles[TILE_LIST].push_back(t);
+            }
+            c.U = (int)order.size();
+            c.out_start.resize(c.U + 1);
+            for (int u = 0; u < c.U; ++u) {
+                c.out_start[u] = (int)c.outs.size();
+                const int s = local[order[u]];
+                for (auto& eo : slot_outs[s]) {
+                    const int e = eo.first;
+                    c.outs.push_back(make_int4(e, loc[pj[e]], loc[pl[e]], 0));
+                }
+            }
+            c.out_start[c.U] = (int)c.outs.size();
+            plan.chunks.push_back(std::move(c));
+        }
+    }
+    // sizes
+    for (auto& c : plan.chunks) {
+        plan.max_nc = std::max(plan.max_nc, (int)c.inputs.size());
+        plan.max_U = std::max(plan.max_U, c.U);
+    }
+    const size_t per_node = size_t(g->M) * plan.max_nc * field_bytes + size_t(plan.max_U) * field_bytes;
+    plan.nq = (int)std::max<size_t>(1, std::min<size_t>(g->n_rho, kFieldBudget / std::max<size_t>(per_node, 1)));
+    // device plan descriptors
+    size_t off = 0;
+    for (auto& c : plan.chunks) {
+        c.off_inputs = off;
+        off = align_up(off + c.inputs.size() * sizeof(int), 256);
+        for (int k = 0; k < 3; ++k) {
+            c.off_tiles[k] = off;
+            off = align_up(off + c.tiles[k].size() * sizeof(Tile), 256);
+        }
+        c.off_start = off;
+        off = align_up(off + c.out_start.size() * sizeof(int), 256);
+        c.off_outs = off;
+        off = align_up(off + c.outs.size() * sizeof(int4), 256);
+    }
+    plan.plan_bytes = off;
+    size_t w = align_up(off, 256);
+    plan.off_plan = 0;
+    plan.off_A = w;
+    w = align_up(w + size_t(plan.nq) * g->M * plan.max_nc * field_bytes, 256);
+    plan.off_P = w;
+    w = align_up(w + size_t(plan.nq) * plan.max_U * field_bytes, 256);
+    plan.off_qhat = w;
+    w = align_up(w + size_t(plan.max_U) * g->half * 8, 256);
+    plan.off_fN = w;
+    w = align_up(w + size_t(plan.max_nc) * field_bytes, 256);
+    plan.off_lam = w;
+    w = align_up(w + size_t(plan.max_nc) * field_bytes, 256);
+    plan.total = w;
+    return BOLTZ_OK;
+}
+
+boltz_status ensure_workspace(boltz_grid_s* g, size_t bytes, cudaStream_t stream) {
+    if (bytes <= g->ws_cap) return BOLTZ_OK;
+    if (bytes > g->ws_max) return BOLTZ_ENOMEM;
+    if (g->d_ws) {
+        BZ_CUDA(cudaStreamSynchronize(stream));
+        BZ_CUDA(cudaFree(g->d_ws));
+        g->d_ws = nullptr;
+        g->ws_cap = 0;
+    }
+    const size_t cap = align_up(bytes + bytes / 8, size_t(1) << 20);
+    cudaError_t e = cudaMalloc(&g->d_ws, cap);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        g->d_ws = nullptr;
+        return BOLTZ_ENOMEM;
+    }
+    g->ws_cap = cap;
+    g->plan_uploaded = false;
+    return BOLTZ_OK;
+}
+
+boltz_status upload_plan(boltz_grid_s* g, const Plan& plan, cudaStream_t stream) {
+    std::vector<char> host(plan.plan_bytes, 0);
+    for (const auto& c : plan.chunks) {
+        std::memcpy(host.data() + c.off_inputs, c.inputs.data(), c.inputs.size() * sizeof(int));
+        for (int k = 0; k < 3; ++k)
+            if (!c.tiles[k].empty())
+                std::memcpy(host.data() + c.off_tiles[k], c.tiles[k].data(), c.tiles[k].size() * sizeof(Tile));
+        std::memcpy(host.data() + c.off_start, c.out_start.data(), c.out_start.size() * sizeof(int));
+        if (!c.outs.empty()) std::memcpy(host.data() + c.off_outs, c.outs.data(), c.outs.size() * sizeof(int4));
+    }
+    if (plan.plan_bytes) {
+        BZ_CUDA(cudaMemcpyAsync(g->d_ws + plan.off_plan, host.data(), plan.plan_bytes, cudaMemcpyHostToDevice, stream));
+        BZ_CUDA(cudaStreamSynchronize(stream));   // host staging buffer goes out of scope
+    }
+    return BOLTZ_OK;
+}
+
+// ---------------------------------------------------------------- profiling
+
+cudaEvent_t take_event(boltz_grid_s* g) {
+    if (!g->event_pool.empty()) {
+        cudaEvent_t e = g->event_pool.back();
+        g->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+// Brackets one kernel launch: counts it and, when profiling is on, records an
+// event pair around it on the launching stream.
+struct ProfScope {
+    boltz_grid_s* g;
+    int cls;
+    cudaStream_t st;
+    cudaEvent_t e0 = nullptr;
+    ProfScope(boltz_grid_s* g_, int cls_, cudaStream_t st_) : g(g_), cls(cls_), st(st_) {
+        ++g->launches[cls];
+        if (g->prof_on && (e0 = take_event(g))) cudaEventRecord(e0, st);
+    }
+    ~ProfScope() {
+        if (!e0) return;
+        cudaEvent_t e1 = take_event(g);
+        if (!e1) return;
+        cudaEventRecord(e1, st);
+        g->prof_events.push_back({cls, {e0, e1}});
+    }
+};
+
+// ---------------------------------------------------------------- launches
+
+template <typename K>
+cudaError_t set_smem(K kernel, size_t bytes) {
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <int N, int D>
+struct Launch {
+    using G = Geo<N, D>;
+    static constexpr int FPC = (D == 3) ? (N == 32 ? 1 : (N == 16 ? 4 : 8))
+                                        : (N == 64 ? 4 : (N == 32 ? 16 : (N == 16 ? 32 : 64)));
+    static constexpr int BLOCK = G::TPF * FPC;
+    static constexpr size_t SMEM = size_t(G::SMEM_F) * FPC * sizeof(float2);
+
+    static cudaError_t prepare() {
+        cudaError_t e;
+        if ((e = set_smem(k_synth<N, D, FPC, SYN_SHIFT>, SMEM)) != cudaSuccess) return e;
+        if ((e = set_smem(k_synth<N, D, FPC, SYN_PREP>, SMEM)) != cudaSuccess) return e;
+        if ((e = set_smem(k_analysis<N, D, FPC, ANA_SPECTRUM>, SMEM)) != cudaSuccess) return e;
+        if ((e = set_smem(k_analysis<N, D, FPC, ANA_ACCUM>, SMEM)) != cudaSuccess) return e;
+        return set_smem(k_output<N, D, FPC>, SMEM);
+    }
+    static void synth(const SynParams& p, int mode, cudaStream_t st) {
+        const int grid = (p.n_fields + FPC - 1) / FPC;
+        if (mode == SYN_SHIFT)
+            k_synth<N, D, FPC, SYN_SHIFT><<<grid, BLOCK, SMEM, st>>>(p);
+        else
+            k_synth<N, D, FPC, SYN_PREP><<<grid, BLOCK, SMEM, st>>>(p);
+    }
+    static void analysis(const AnaParams& p, int mode, cudaStream_t st) {
+        const int grid = (p.n_fields + FPC - 1) / FPC;
+        if (mode == ANA_SPECTRUM)
+            k_analysis<N, D, FPC, ANA_SPECTRUM><<<grid, BLOCK, SMEM, st>>>(p);
+        else
+            k_analysis<N, D, FPC, ANA_ACCUM><<<grid, BLOCK, SMEM, st>>>(p);
+    }
+    static void output(const OutParams& p, cudaStream_t st) {
+        const int grid = (p.U + FPC - 1) / FPC;
+        k_output<N, D, FPC><<<grid, BLOCK, SMEM, st>>>(p);
+    }
+};
+
+struct Dispatch {
+    cudaError_t (*prepare)();
+    void (*synth)(const SynParams&, int, cudaStream_t);
+    void (*analysis)(const AnaParams&, int, cudaStream_t);
+    void (*output)(const OutParams&, cudaStream_t);
+};
+
+template <int N, int D>
+Dispatch make_dispatch() {
+    return {&Launch<N, D>::prepare, &Launch<N, D>::synth, &Launch<N, D>::analysis, &Launch<N, D>::output};
+}
+
+const Dispatch* dispatch_for(int N, int D) {
+    static const Dispatch d3_8 = make_dispatch<8, 3>(), d3_16 = make_dispatch<16, 3>(),
+                          d3_32 = make_dispatch<32, 3>(), d2_8 = make_dispatch<8, 2>(),
+                          d2_16 = make_dispatch<16, 2>(), d2_32 = make_dispatch<32, 2>(),
+                          d2_64 = make_dispatch<64, 2>();
+    if (D == 3) return N == 8 ? &d3_8 : N == 16 ? &d3_16 : N == 32 ? &d3_32 : nullptr;
+    return N == 8 ? &d2_8 : N == 16 ? &d2_16 : N == 32 ? &d2_32 : N == 64 ? &d2_64 : nullptr;
+}
+
+void launch_contract(int kind, int T, const ConParams& cp, int n_tiles, int nq, cudaStream_t st) {
+    dim3 grid((cp.n + 255) / 256, n_tiles, nq);
+    if (kind == TILE_TRI) {
+        if (T == 16) k_contract<TILE_TRI, 16, 16><<<grid, 256, 0, st>>>(cp);
+        else k_contract<TILE_TRI, 8, 8><<<grid, 256, 0, st>>>(cp);
+    } else if (kind == TILE_FULL) {
+        if (T == 16) k_contract<TILE_FULL, 8, 16><<<grid, 256, 0, st>>>(cp);
+        else k_contract<TILE_FULL, 8, 8><<<grid, 256, 0, st>>>(cp);
+    } else {
+        k_contract<TILE_LIST, 16, 16><<<grid, 256, 0, st>>>(cp);
+    }
+}
+
+boltz_status check_pairs(int n_inputs, const int32_t* pj, const int32_t* pl, int n_pairs) {
+    if (n_pairs < 0) return BOLTZ_EINVAL;
+    if (n_pairs == 0) return BOLTZ_OK;
+    if (!pj || !pl || n_inputs <= 0) return BOLTZ_EINVAL;
+    for (int e = 0; e < n_pairs; ++e)
+        if (pj[e] < 0 || pj[e] >= n_inputs || pl[e] < 0 || pl[e] >= n_inputs) return BOLTZ_EINVAL;
+    return BOLTZ_OK;
+}
+
+boltz_status run_batched(boltz_grid_s* g, const float2* spectra, int n_inputs, const int32_t* pj, const int32_t* pl,
+                         int n_pairs, float* Q_out, int form, cudaStream_t st) {
+    const bool same = g->plan_uploaded && form == g->last_form && n_inputs == g->last_n_inputs &&
+                      (int)g->last_j.size() == n_pairs &&
+                      std::equal(pj, pj + n_pairs, g->last_j.begin()) &&
+                      std::equal(pl, pl + n_pairs, g->last_l.begin());
+    if (!same) {
+        Plan plan;
+        boltz_status s = build_plan(g, n_inputs, pj, pl, n_pairs, form, plan);
+        if (s != BOLTZ_OK) return s;
+        if ((s = ensure_workspace(g, plan.total, st)) != BOLTZ_OK) return s;
+        if ((s = upload_plan(g, plan, st)) != BOLTZ_OK) return s;
+        g->last_plan = std::move(plan);
+        g->last_j.assign(pj, pj + n_pairs);
+        g->last_l.assign(pl, pl + n_pairs);
+        g->last_form = form;
+        g->last_n_inputs = n_inputs;
+        g->plan_uploaded = true;
+    }
+    const Plan& plan = g->last_plan;
+    const Dispatch* dp = dispatch_for(g->N, g->D);
+    char* ws = g->d_ws;
+    float* A = reinterpret_cast<float*>(ws + plan.off_A);
+    float* Pbuf = reinterpret_cast<float*>(ws + plan.off_P);
+    float2* qhat = reinterpret_cast<float2*>(ws + plan.off_qhat);
+    float* fN = reinterpret_cast<float*>(ws + plan.off_fN);
+    float* lam = reinterpret_cast<float*>(ws + plan.off_lam);
+    for (const auto& c : plan.chunks) {
+        const int nc = (int)c.inputs.size();
+        const int* d_inputs = reinterpret_cast<const int*>(ws + plan.off_plan + c.off_inputs);
+        // f_N and Lambda_g of the chunk's inputs (fN and lam are contiguous: [2][nc_max][n])
+        SynParams sp{};
+        sp.spectra = spectra;
+        sp.inputs = d_inputs;
+        sp.phase = g->d_phase;
+        sp.gm = g->d_gm;
+        sp.n_c = nc;
+        sp.M = g->M;
+        sp.id_node = g->n_rho * g->M;
+        // PREP writes field f at out + f*n: f < nc -> f_N, f >= nc -> Lambda
+        sp.out = fN;
+        sp.n_fields = 2 * nc;
+        {
+            ProfScope ps(g, BOLTZ_KCLASS_PREP, st);
+            dp->synth(sp, SYN_PREP, st);
+        }
+        const float* lam_c = fN + size_t(nc) * g->n;
+        BZ_CUDA(cudaMemsetAsync(qhat, 0, size_t(c.U) * g->half * sizeof(float2), st));
+        for (int q0 = 0; q0 < g->n_rho; q0 += plan.nq) {
+            const int nq = std::min(plan.nq, g->n_rho - q0);
+            SynParams ss = sp;
+            ss.out = A;
+            ss.q0 = q0;
+            ss.n_fields = nq * g->M * nc;
+            {
+                ProfScope ps(g, BOLTZ_KCLASS_SHIFT, st);
+                dp->synth(ss, SYN_SHIFT, st);
+            }
+            ConParams cp{};
+            cp.A = A;
+            cp.P = Pbuf;
+            cp.w = g->d_w;
+            cp.anti = g->d_anti;
+            cp.M = g->M;
+            cp.n_c = nc;
+            cp.U = c.U;
+            cp.n = g->n;
+            for (int k = 0; k < 3; ++k) {
+                if (c.tiles[k].empty()) continue;
+                cp.tiles = reinterpret_cast<const Tile*>(ws + plan.off_plan + c.off_tiles[k]);
+                ProfScope ps(g, BOLTZ_KCLASS_CONTRACT, st);
+                launch_contract(k, k == TILE_LIST ? 16 : c.tile_T, cp, (int)c.tiles[k].size(), nq, st);
+            }
+            AnaParams ap{};
+            ap.in = Pbuf;
+            ap.out = qhat;
+            ap.ctab = g->d_ctab;
+            ap.n_fields = c.U;
+            ap.nq = nq;
+            ap.q0 = q0;
+            ap.U = c.U;
+            ProfScope ps(g, BOLTZ_KCLASS_RADIAL, st);
+            dp->analysis(ap, ANA_ACCUM, st);
+        }
+        OutParams op{};
+        op.qhat = qhat;
+        op.fN = fN;
+        op.lam = lam_c;
+        op.out_start = reinterpret_cast<const int*>(ws + plan.off_plan + c.off_start);
+        op.outs = reinterpret_cast<const int4*>(ws + plan.off_plan + c.off_outs);
+        op.Q = Q_out;
+        op.U = c.U;
+        ProfScope ps(g, BOLTZ_KCLASS_OUTPUT, st);
+        dp->output(op, st);
+    }
+    (void)lam;
+    BZ_CUDA(cudaGetLastError());
+    return BOLTZ_OK;
+}
+
+boltz_status run_project(boltz_grid_s* g, const float* V, int r, const float* Q, float* T, float* partial,
+                         cudaStream_t st) {
+    constexpr int PB = 8, RT = 16;
+    const int r2 = r * r;
+    const int bx = (r2 + PB - 1) / PB, bz = (r + RT - 1) / RT;
+    int slices = std::max(1, std::min(64, (2 * 152) / std::max(1, bx * bz)));
+    slices = std::min(slices, std::max(1, g->n / 256));
+    {
+        ProfScope ps(g, BOLTZ_KCLASS_PROJECT, st);
+        k_project<PB, RT><<<dim3(bx, slices, bz), 256, 0, st>>>(V, Q, partial, r, g->n, slices);
+    }
+    const int count = r * r2;
+    const float scale = (float)std::pow(2.0 * g->L / g->N, g->D);
+    ProfScope ps(g, BOLTZ_KCLASS_PROJECT, st);
+    k_project_reduce<<<(count + 255) / 256, 256, 0, st>>>(partial, T, count, slices, scale);
+    BZ_CUDA(cudaGetLastError());
+    return BOLTZ_OK;
+}
+
+size_t project_partial_bytes(int r) { return size_t(64) * r * r * r * sizeof(float); }
+
+// The twiddle table lives in constant memory, once per device.
+boltz_status ensure_twiddles(int device) {
+    static std::mutex mu;
+    static std::set<int> done;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done.count(device)) return BOLTZ_OK;
+    float2 tw[128];
+    for (int t = 0; t < 128; ++t)
+        tw[t] = make_float2((float)std::cos(-2.0 * kPi * t / 128), (float)std::sin(-2.0 * kPi * t / 128));
+    if (cudaMemcpyToSymbol(c_twiddle, tw, sizeof(tw)) != cudaSuccess) return BOLTZ_ECUDA;
+    done.insert(device);
+    return BOLTZ_OK;
+}
+
+}  // namespace
+
+// ==================================================================== C ABI
+
+extern "C" {
+
+int boltz_abi_version(void) { return BOLTZ_ABI_VERSION; }
+
+const char* boltz_status_string(boltz_status s) {
+    switch (s) {
+        case BOLTZ_OK: return "ok";
+        case BOLTZ_EINVAL: return "invalid argument";
+        case BOLTZ_ENOMEM: return "out of memory";
+        case BOLTZ_ECUDA: return "CUDA error";
+        case BOLTZ_ETIMEOUT: return "device wait timed out";
+        case BOLTZ_EUNSUPPORTED: return "unsupported configuration";
+        case BOLTZ_ENONFINITE: return "non-finite value";
+    }
+    return "unknown status";
+}
+
+boltz_status boltz_host_quadrature(int d_v, int N_rho, int M, double R, double* rho, double* w_rho, double* sigma,
+                                   double* w_sigma) {
+    if ((d_v != 2 && d_v != 3) || N_rho < 1 || N_rho > 128 || !(R > 0) || !rho || !w_rho || !sigma || !w_sigma)
+        return BOLTZ_EINVAL;
+    std::vector<double> x, w;
+    if (!boltz::gauss_legendre(N_rho, x, w)) return BOLTZ_EINVAL;
+    boltz::DirectionRule dr;
+    if (!boltz::direction_rule(d_v, M, dr)) return BOLTZ_EINVAL;
+    for (int q = 0; q < N_rho; ++q) {
+        rho[q] = 0.5 * R * (x[q] + 1.0);
+        w_rho[q] = 0.5 * R * w[q];
+    }
+    for (int p = 0; p < M; ++p) {
+        w_sigma[p] = dr.w[p];
+        for (int a = 0; a < d_v; ++a) sigma[p * d_v + a] = dr.sigma[p * d_v + a];
+    }
+    return BOLTZ_OK;
+}
+
+boltz_status boltz_grid_init(boltz_grid* out, int N, int d_v, double L, double R, double gamma, int N_rho, int M,
+                             const boltz_options* opt) {
+    if (!out) return BOLTZ_EINVAL;
+    if ((d_v != 2 && d_v != 3) || N < 4 || N % 2 || N > 256 || !(L > 0) || !(R > 0) || !(gamma > -d_v) ||
+        !std::isfinite(L) || !std::isfinite(R) || !std::isfinite(gamma) || N_rho < 1 || N_rho > 128)
+        return BOLTZ_EINVAL;
+    if (d_v == 2 && (M < 2 || M % 2 || M > 256)) return BOLTZ_EINVAL;
+    if (d_v == 3 && !(M == 6 || M == 14 || M == 26 || M == 38 || M == 50 || M == 86)) return BOLTZ_EINVAL;
+    if (!supported_shape(N, d_v)) return BOLTZ_EUNSUPPORTED;
+
+    boltz_grid_s* g = new (std::nothrow) boltz_grid_s();
+    if (!g) return BOLTZ_ENOMEM;
+    g->N = N;
+    g->D = d_v;
+    g->L = L;
+    g->R = R;
+    g->gamma = gamma;
+    g->n_rho = N_rho;
+    g->M = M;
+    const double area = d_v == 2 ? 2.0 * kPi : 4.0 * kPi;
+    g->b = (opt && opt->b > 0) ? opt->b : 1.0 / area;
+    if (opt && opt->workspace_max) g->ws_max = opt->workspace_max;
+    g->n = d_v == 3 ? N * N * N : N * N;
+    g->half = d_v == 3 ? N * N * (N / 2 + 1) : N * (N / 2 + 1);
+    g->smax = d_v * (N / 2) * (N / 2);
+    std::vector<double> x, w;
+    boltz::gauss_legendre(N_rho, x, w);
+    g->rho.resize(N_rho);
+    g->w_rho.resize(N_rho);
+    for (int q = 0; q < N_rho; ++q) {
+        g->rho[q] = 0.5 * R * (x[q] + 1.0);
+        g->w_rho[q] = 0.5 * R * w[q];
+    }
+    if (!boltz::direction_rule(d_v, M, g->dir)) {
+        delete g;
+        return BOLTZ_EINVAL;
+    }
+    // ---- tables in FP64, rounded once to FP32
+    const int H = N / 2;
+    const int nodes = N_rho * M + 1;
+    std::vector<float2> phase(size_t(nodes) * d_v * N);
+    for (int node = 0; node < nodes; ++node) {
+        for (int a = 0; a < d_v; ++a) {
+            const double s = node < N_rho * M ? 0.5 * g->rho[node / M] * g->dir.sigma[(node % M) * d_v + a] : 0.0;
+            for (int i = 0; i < N; ++i) {
+                const int k = i < H ? i : i - N;
+                float2 v = make_float2(0.f, 0.f);
+                if (i != H) {
+                    const double ang = -kPi * k * s / L;
+                    const double sg = (i & 1) ? -1.0 : 1.0;
+                    v = make_float2((float)(sg * std::cos(ang)), (float)(sg * std::sin(ang)));
+                }
+                phase[(size_t(node) * d_v + a) * N + i] = v;
+            }
+        }
+    }
+    const double kp = gamma + d_v - 1;
+    std::vector<float> ctab(size_t(N_rho) * (g->smax + 1)), gm(g->smax + 1);
+    for (int sq = 0; sq <= g->smax; ++sq) {
+        const double km = std::sqrt((double)sq);
+        double acc = 0;
+        for (int q = 0; q < N_rho; ++q) {
+            const double base = g->w_rho[q] * std::pow(g->rho[q], kp);
+            ctab[size_t(q) * (g->smax + 1) + sq] =
+                (float)(g->b * base * boltz::omega_average(d_v, kPi * g->rho[q] * km / (2.0 * L)) / g->n);
+            acc += base * boltz::omega_average(d_v, kPi * g->rho[q] * km / L);
+        }
+        gm[sq] = (float)(g->b * area * acc);
+    }
+    std::vector<float> wdir(M);
+    for (int p = 0; p < M; ++p) wdir[p] = (float)g->dir.w[p];
+
+    auto fail = [&](boltz_status s) {
+        boltz_grid_destroy(g);
+        return s;
+    };
+    if (cudaGetDevice(&g->device) != cudaSuccess) {
+        (void)cudaGetLastError();
+        delete g;
+        return BOLTZ_ECUDA;
+    }
+    if (ensure_twiddles(g->device) != BOLTZ_OK) return fail(BOLTZ_ECUDA);
+    if (cudaMalloc(&g->d_phase, phase.size() * sizeof(float2)) != cudaSuccess ||
+        cudaMalloc(&g->d_ctab, ctab.size() * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&g->d_gm, gm.size() * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&g->d_w, M * sizeof(float)) != cudaSuccess || cudaMalloc(&g->d_anti, M * sizeof(int)) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return fail(BOLTZ_ENOMEM);
+    }
+    if (cudaMemcpy(g->d_phase, phase.data(), phase.size() * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(g->d_ctab, ctab.data(), ctab.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(g->d_gm, gm.data(), gm.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(g->d_w, wdir.data(), M * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(g->d_anti, g->dir.antipode.data(), M * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(BOLTZ_ECUDA);
+    if (dispatch_for(N, d_v)->prepare() != cudaSuccess) return fail(BOLTZ_ECUDA);
+    *out = g;
+    return BOLTZ_OK;
+}
+
+boltz_status boltz_grid_destroy(boltz_grid g) {
+    if (!g) return BOLTZ_OK;
+    if (g->d_phase || g->d_ws) cudaDeviceSynchronize();
+    for (auto& pe : g->prof_events) {
+        cudaEventDestroy(pe.second.first);
+        cudaEventDestroy(pe.second.second);
+    }
+    for (auto e : g->event_pool) cudaEventDestroy(e);
+    cudaFree(g->d_phase);
+    cudaFree(g->d_ctab);
+    cudaFree(g->d_gm);
+    cudaFree(g->d_w);
+    cudaFree(g->d_anti);
+    cudaFree(g->d_ws);
+    delete g;
+    return BOLTZ_OK;
+}
+
+boltz_status boltz_spectrum(boltz_grid g, const float* f, int n_inputs, void* spectra_out, void* stream) {
+    if (!g || n_inputs < 0) return BOLTZ_EINVAL;
+    if (n_inputs == 0) return BOLTZ_OK;
+    if (!f || !spectra_out) return BOLTZ_EINVAL;
+    AnaParams ap{};
+    ap.in = f;
+    ap.out = reinterpret_cast<float2*>(spectra_out);
+    ap.ctab = g->d_ctab;
+    ap.n_fields = n_inputs;
+    ap.nq = 1;
+    ap.inv_n = 1.0f / (float)g->n;
+    {
+        ProfScope ps(g, BOLTZ_KCLASS_SPECTRUM, reinterpret_cast<cudaStream_t>(stream));
+        dispatch_for(g->N, g->D)->analysis(ap, ANA_SPECTRUM, reinterpret_cast<cudaStream_t>(stream));
+    }
+    BZ_CUDA(cudaGetLastError());
+    return BOLTZ_OK;
+}
+
+boltz_status boltz_workspace_size(boltz_grid g, int n_inputs, const int32_t* pair_j, const int32_t* pair_l,
+                                  int n_pairs, int form, size_t* bytes) {
+    if (!g || !bytes || (form != BOLTZ_FORM_BATCHED && form != BOLTZ_FORM_PLAIN)) return BOLTZ_EINVAL;
+    boltz_status s = check_pairs(n_inputs, pair_j, pair_l, n_pairs);
+    if (s != BOLTZ_OK) return s;
+    if (n_pairs == 0) {
+        *bytes = 0;
+        return BOLTZ_OK;
+    }
+    Plan plan;
+    if ((s = build_plan(g, n_inputs, pair_j, pair_l, n_pairs, form, plan)) != BOLTZ_OK) return s;
+    *bytes = plan.total;
+    return BOLTZ_OK;
+}
+
+boltz_status boltz_collide_batched(boltz_grid g, const void* spectra, int n_inputs, const int32_t* pair_j,
+                                   const int32_t* pair_l, int n_pairs, float* Q_out, int form, void* stream) {
+    if (!g || (form != BOLTZ_FORM_BATCHED && form != BOLTZ_FORM_PLAIN)) return BOLTZ_EINVAL;
+    boltz_status s = check_pairs(n_inputs, pair_j, pair_l, n_pairs);
+    if (s != BOLTZ_OK) return s;
+    if (n_pairs == 0) return BOLTZ_OK;
+    if (!spectra || !Q_out) return BOLTZ_EINVAL;
+    return run_batched(g, reinterpret_cast<const float2*>(spectra), n_inputs, pair_j, pair_l, n_pairs, Q_out, form,
+                       reinterpret_cast<cudaStream_t>(stream));
+}
+
+boltz_status boltz_project(boltz_grid g, const float* V, int r, const float* Q, float* T_out, void* stream) {
+    if (!g || !V || !Q || !T_out || r < 1 || r > 64) return BOLTZ_EINVAL;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    // the partial sums go right after the cached plan descriptors (the field
+    // buffers behind them are free once earlier work on the stream is done)
+    const size_t off = g->plan_uploaded ? align_up(g->last_plan.plan_bytes, 256) : 0;
+    boltz_status s = ensure_workspace(g, off + project_partial_bytes(r), st);
+    if (s != BOLTZ_OK) return s;
+    const size_t off2 = g->plan_uploaded ? align_up(g->last_plan.plan_bytes, 256) : 0;
+    return run_project(g, V, r, Q, T_out, reinterpret_cast<float*>(g->d_ws + off2), st);
+}
+
+boltz_status boltz_lowrank_step_host(boltz_grid g, const float* V_host, int r, float* Q_host, float* T_host,
+                                     void* stream) {
+    if (!g || !V_host || !T_host || r < 1 || r > 64) return BOLTZ_EINVAL;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int r2 = r * r;
+    std::vector<int32_t> pj(r2), pl(r2);
+    for (int j = 0; j < r; ++j)
+        for (int l = 0; l < r; ++l) {
+            pj[j * r + l] = j;
+            pl[j * r + l] = l;
+        }
+    Plan plan;
+    boltz_status s = build_plan(g, r, pj.data(), pl.data(), r2, BOLTZ_FORM_BATCHED, plan);
+    if (s != BOLTZ_OK) return s;
+    // staging after the batched workspace: V, spectra, Q, T, partial sums
+    const size_t nb = size_t(g->n) * 4;
+    size_t off_V = align_up(plan.total, 256);
+    size_t off_S = align_up(off_V + size_t(r) * nb, 256);
+    size_t off_Q = align_up(off_S + size_t(r) * g->half * 8, 256);
+    size_t off_T = align_up(off_Q + size_t(r2) * nb, 256);
+    size_t off_part = align_up(off_T + size_t(r) * r2 * 4, 256);
+    size_t total = align_up(off_part + project_partial_bytes(r), 256);
+    if ((s = ensure_workspace(g, total, st)) != BOLTZ_OK) return s;
+    float* dV = reinterpret_cast<float*>(g->d_ws + off_V);
+    float2* dS = reinterpret_cast<float2*>(g->d_ws + off_S);
+    float* dQ = reinterpret_cast<float*>(g->d_ws + off_Q);
+    float* dT = reinterpret_cast<float*>(g->d_ws + off_T);
+    float* dP = reinterpret_cast<float*>(g->d_ws + off_part);
+    BZ_CUDA(cudaMemcpyAsync(dV, V_host, size_t(r) * nb, cudaMemcpyHostToDevice, st));
+    if ((s = boltz_spectrum(g, dV, r, dS, stream)) != BOLTZ_OK) return s;
+    if ((s = run_batched(g, dS, r, pj.data(), pl.data(), r2, dQ, BOLTZ_FORM_BATCHED, st)) != BOLTZ_OK) return s;
+    if ((s = run_project(g, dV, r, dQ, dT, dP, st)) != BOLTZ_OK) return s;
+    if (Q_host) BZ_CUDA(cudaMemcpyAsync(Q_host, dQ, size_t(r2) * nb, cudaMemcpyDeviceToHost, st));
+    BZ_CUDA(cudaMemcpyAsync(T_host, dT, size_t(r) * r2 * 4, cudaMemcpyDeviceToHost, st));
+    BZ_CUDA(cudaStreamSynchronize(st));
+    return BOLTZ_OK;
+}
+
+boltz_status boltz_profile_enable(boltz_grid g, int enable) {
+    if (!g) return BOLTZ_EINVAL;
+    g->prof_on = enable != 0;
+    return BOLTZ_OK;
+}
+
+boltz_status boltz_profile_read(boltz_grid g, int reset, long long* launches, double* ms) {
+    if (!g || !launches || !ms) return BOLTZ_EINVAL;
+    for (int c = 0; c < BOLTZ_KCLASS_COUNT; ++c) {
+        launches[c] = g->launches[c];
+        ms[c] = 0.0;
+    }
+    for (auto& pe : g->prof_events) {
+        float t = 0.f;
+        if (cudaEventSynchronize(pe.second.second) != cudaSuccess ||
+            cudaEventElapsedTime(&t, pe.second.first, pe.second.second) != cudaSuccess)
+            return BOLTZ_ECUDA;
+        ms[pe.first] += t;
+    }
+    if (reset) {
+        for (auto& pe : g->prof_events) {
+            g->event_pool.push_back(pe.second.first);
+            g->event_pool.push_back(pe.second.second);
+        }
+        g->prof_events.clear();
+        for (int c = 0; c < BOLTZ_KCLASS_COUNT; ++c) g->launches[c] = 0;
+    }
+    return BOLTZ_OK;
+}
+
+}  // extern "C"

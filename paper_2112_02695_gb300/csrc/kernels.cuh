@@ -1,0 +1,509 @@
+// sm_103a kernels of the separated fast-spectral collision operator (FP32).
+//
+// Field layout (all kernels): a physical field is float [N]^D, C order, axis
+// 0 slowest; a spectrum is the real-to-complex half spectrum float2
+// [N]^(D-1) x [N/2+1] (last axis k = 0..N/2, other axes in DFT index order).
+// A CTA holds FPC fields at once, TPF threads per field; every 1-D transform
+// along an axis is done by one thread in registers (fft_reg), the transposes
+// between axes go through shared memory whose rows are padded to N/2+1
+// complex entries so that both row- and column-wise accesses are free of bank
+// conflicts.  The real-to-complex and complex-to-real steps along the last
+// axis pack two real lines into one complex line.
+//
+// Sign and scale conventions: with v_j = -L + j dv the synthesis
+// sum_k F_k exp(i pi k.v_j / L) equals sum_k F_k (-1)^k exp(2 pi i k.j / N),
+// so the (-1)^k factor is folded into the phase tables (synthesis) or applied
+// from the index parity (analysis, output); the 1/N^D of the analysis is
+// folded into the radial table.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fft.cuh"
+
+namespace boltz_dev {
+
+template <int N, int D>
+struct Geo {
+    static constexpr int H = N / 2;
+    static constexpr int NH = H + 1;                             // half-axis length
+    static constexpr int RS = H + 1;                             // smem row stride (float2)
+    static constexpr int n = (D == 3) ? N * N * N : N * N;       // real points
+    static constexpr int half = (D == 3) ? N * N * NH : N * NH;  // half-spectrum entries
+    static constexpr int TPF = (D == 3) ? N * H : H;             // threads per field
+    static constexpr int SMEM_F = (D == 3) ? N * N * RS : N * RS;
+    static constexpr int COLS = (D == 3) ? N * NH : NH;          // columns incl. the half-axis Nyquist
+    static constexpr int SMAX = D * H * H;                       // largest |k|^2
+};
+
+__device__ __forceinline__ int wrapk(int i, int N) { return i < N / 2 ? i : i - N; }
+
+// ------------------------------------------------------------------ synthesis
+// Spectra -> real fields.  SHIFT: the shifted fields A_{q,p,j}(v) =
+// g_j,N(v - rho_q sigma_p / 2) for every (node in the q-block, direction,
+// chunk input); PREP: f_N (identity node) and Lambda_g (identity node times
+// the loss multiplier G-(|l|^2)) for every chunk input.
+enum { SYN_SHIFT = 0, SYN_PREP = 1 };
+
+struct SynParams {
+    const float2* spectra;  // [n_inputs][half]
+    const int* inputs;      // chunk-local -> global input index [n_c]
+    const float2* phase;    // [nodes][D][N]: (-1)^k exp(-i pi k s_a / L), zero at the Nyquist index
+    const float* gm;        // [SMAX+1] loss multiplier
+    float* out;             // SHIFT: [nq][M][n_c][n]; PREP: [2][n_c][n]
+    int n_c, M, q0, id_node, n_fields;
+};
+
+template <int N, int D, int FPC, int MODE>
+__global__ void __launch_bounds__(Geo<N, D>::TPF * FPC) k_synth(SynParams P) {
+    using G = Geo<N, D>;
+    constexpr int H = G::H, RS = G::RS;
+    extern __shared__ float2 smem[];
+    const int grp = threadIdx.x / G::TPF, lt = threadIdx.x % G::TPF;
+    const int f = blockIdx.x * FPC + grp;
+    const bool active = f < P.n_fields;
+    float2* s = smem + grp * G::SMEM_F;
+
+    int input = 0, node = P.id_node;
+    bool use_gm = false;
+    if (active) {
+        const int jj = f % P.n_c;
+        input = P.inputs[jj];
+        if (MODE == SYN_SHIFT) {
+            const int t = f / P.n_c, p = t % P.M, qq = t / P.M;
+            node = (P.q0 + qq) * P.M + p;
+        } else {
+            use_gm = f >= P.n_c;
+        }
+    }
+    const float2* __restrict__ src = P.spectra + (size_t)input * G::half;
+    const float2* __restrict__ ph = P.phase + (size_t)node * D * N;
+    float* __restrict__ dst = P.out + (size_t)f * G::n;
+    float2 x[N];
+
+    if (D == 3) {
+        // axis 0: columns (k1, k2), k2 < N/2 (the input's half-axis Nyquist is zero)
+        if (active) {
+            const int k1 = lt / H, k2 = lt % H;
+            const float2 w12 = cmul(__ldg(&ph[N + k1]), __ldg(&ph[2 * N + k2]));
+#pragma unroll
+            for (int k0 = 0; k0 < N; ++k0) {
+                float2 v = cmul(__ldg(&src[(k0 * N + k1) * G::NH + k2]), cmul(w12, __ldg(&ph[k0])));
+                if (MODE == SYN_PREP && use_gm) {
+                    const int a = wrapk(k0, N), b = wrapk(k1, N);
+                    v = cscale(v, __ldg(&P.gm[a * a + b * b + k2 * k2]));
+                }
+                x[k0] = v;
+            }
+            fft_reg<N, true>(x);
+#pragma unroll
+            for (int i0 = 0; i0 < N; ++i0) s[(i0 * N + k1) * RS + k2] = x[i0];
+        }
+        __syncthreads();
+        // axis 1
+        if (active) {
+            const int i0 = lt / H, k2 = lt % H;
+#pragma unroll
+            for (int k1 = 0; k1 < N; ++k1) x[k1] = s[(i0 * N + k1) * RS + k2];
+            fft_reg<N, true>(x);
+#pragma unroll
+            for (int i1 = 0; i1 < N; ++i1) s[(i0 * N + i1) * RS + k2] = x[i1];
+        }
+        __syncthreads();
+        // axis 2: complex-to-real of rows (i0, i1) and (i0, i1 + N/2) together
+        if (active) {
+            const int i0 = lt / H, i1 = lt % H;
+            const float2* r1 = s + (i0 * N + i1) * RS;
+            const float2* r2 = s + (i0 * N + i1 + H) * RS;
+            x[0] = make_float2(r1[0].x, r2[0].x);
+            x[H] = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int k = 1; k < H; ++k) {
+                const float2 a = r1[k], b = r2[k];
+                x[k] = make_float2(a.x - b.y, a.y + b.x);
+                x[N - k] = make_float2(a.x + b.y, b.x - a.y);
+            }
+            fft_reg<N, true>(x);
+            float4* o1 = reinterpret_cast<float4*>(dst + (i0 * N + i1) * N);
+            float4* o2 = reinterpret_cast<float4*>(dst + (i0 * N + i1 + H) * N);
+#pragma unroll
+            for (int c = 0; c < N / 4; ++c) {
+                o1[c] = make_float4(x[4 * c].x, x[4 * c + 1].x, x[4 * c + 2].x, x[4 * c + 3].x);
+                o2[c] = make_float4(x[4 * c].y, x[4 * c + 1].y, x[4 * c + 2].y, x[4 * c + 3].y);
+            }
+        }
+    } else {
+        // axis 0: columns k1 < N/2
+        if (active) {
+            const int k1 = lt;
+            const float2 w1 = __ldg(&ph[N + k1]);
+#pragma unroll
+            for (int k0 = 0; k0 < N; ++k0) {
+                float2 v = cmul(__ldg(&src[k0 * G::NH + k1]), cmul(w1, __ldg(&ph[k0])));
+                if (MODE == SYN_PREP && use_gm) {
+                    const int a = wrapk(k0, N);
+                    v = cscale(v, __ldg(&P.gm[a * a + k1 * k1]));
+                }
+                x[k0] = v;
+            }
+            fft_reg<N, true>(x);
+#pragma unroll
+            for (int i0 = 0; i0 < N; ++i0) s[i0 * RS + k1] = x[i0];
+        }
+        __syncthreads();
+        // axis 1: complex-to-real of rows i0 and i0 + N/2
+        if (active) {
+            const int i0 = lt;
+            const float2* r1 = s + i0 * RS;
+            const float2* r2 = s + (i0 + H) * RS;
+            x[0] = make_float2(r1[0].x, r2[0].x);
+            x[H] = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int k = 1; k < H; ++k) {
+                const float2 a = r1[k], b = r2[k];
+                x[k] = make_float2(a.x - b.y, a.y + b.x);
+                x[N - k] = make_float2(a.x + b.y, b.x - a.y);
+            }
+            fft_reg<N, true>(x);
+            float4* o1 = reinterpret_cast<float4*>(dst + i0 * N);
+            float4* o2 = reinterpret_cast<float4*>(dst + (i0 + H) * N);
+#pragma unroll
+            for (int c = 0; c < N / 4; ++c) {
+                o1[c] = make_float4(x[4 * c].x, x[4 * c + 1].x, x[4 * c + 2].x, x[4 * c + 3].x);
+                o2[c] = make_float4(x[4 * c].y, x[4 * c + 1].y, x[4 * c + 2].y, x[4 * c + 3].y);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ analysis
+// Real fields -> half spectra.  SPECTRUM: the input spectra (x (-1)^k / n,
+// Nyquist entries written as zero).  ACCUM: for every gain slot u and node q
+// of the q-block, Qhat+_u += c_q(|k|^2) (-1)^k DFT[P_{q,u}]  (c_q includes 1/n).
+enum { ANA_SPECTRUM = 0, ANA_ACCUM = 1 };
+
+struct AnaParams {
+    const float* in;     // SPECTRUM: [n_fields][n]; ACCUM: [nq][U][n]
+    float2* out;         // [n_fields][half]
+    const float* ctab;   // [N_rho][SMAX+1]
+    int n_fields, nq, q0, U;
+    float inv_n;
+};
+
+template <int N, int D, int FPC, int MODE>
+__global__ void __launch_bounds__(Geo<N, D>::TPF * FPC) k_analysis(AnaParams P) {
+    using G = Geo<N, D>;
+    constexpr int H = G::H, RS = G::RS, NH = G::NH;
+    extern __shared__ float2 smem[];
+    const int grp = threadIdx.x / G::TPF, lt = threadIdx.x % G::TPF;
+    const int f = blockIdx.x * FPC + grp;
+    const bool active = f < P.n_fields;
+    float2* s = smem + grp * G::SMEM_F;
+    float2* __restrict__ dst = P.out + (size_t)f * G::half;
+    float2 x[N];
+    const int n_iter = (MODE == ANA_ACCUM) ? P.nq : 1;
+
+    for (int qq = 0; qq < n_iter; ++qq) {
+        const float* __restrict__ src =
+            (MODE == ANA_ACCUM) ? P.in + ((size_t)qq * P.U + f) * G::n : P.in + (size_t)f * G::n;
+        const float* __restrict__ ct = P.ctab + (size_t)(P.q0 + qq) * (G::SMAX + 1);
+        // last axis: real-to-complex of two rows at once
+        if (active) {
+            const int row = (D == 3) ? (lt / H) * N + (lt % H) : lt;   // (i0, i1) or i0
+            const float4* a4 = reinterpret_cast<const float4*>(src + row * N);
+            const float4* b4 = reinterpret_cast<const float4*>(src + (row + H) * N);
+#pragma unroll
+            for (int c = 0; c < N / 4; ++c) {
+                const float4 a = __ldg(&a4[c]), b = __ldg(&b4[c]);
+                x[4 * c] = make_float2(a.x, b.x);
+                x[4 * c + 1] = make_float2(a.y, b.y);
+                x[4 * c + 2] = make_float2(a.z, b.z);
+                x[4 * c + 3] = make_float2(a.w, b.w);
+            }
+            fft_reg<N, false>(x);
+            float2* r1 = s + row * RS;
+            float2* r2 = s + (row + H) * RS;
+#pragma unroll
+            for (int k = 0; k <= H; ++k) {
+                const float2 z = x[k], zc = x[(N - k) & (N - 1)];
+                // X1 = (Z_k + conj Z_{N-k}) / 2,  X2 = (Z_k - conj Z_{N-k}) / (2i)
+                r1[k] = make_float2(0.5f * (z.x + zc.x), 0.5f * (z.y - zc.y));
+                r2[k] = make_float2(0.5f * (z.y + zc.y), -0.5f * (z.x - zc.x));
+            }
+        }
+        __syncthreads();
+        if (D == 3) {
+            // axis 1
+            if (active) {
+                for (int c = lt; c < G::COLS; c += G::TPF) {
+                    const int i0 = c / NH, k2 = c % NH;
+#pragma unroll
+                    for (int k1 = 0; k1 < N; ++k1) x[k1] = s[(i0 * N + k1) * RS + k2];
+                    fft_reg<N, false>(x);
+#pragma unroll
+                    for (int k1 = 0; k1 < N; ++k1) s[(i0 * N + k1) * RS + k2] = x[k1];
+                }
+            }
+            __syncthreads();
+        }
+        // axis 0, then scale and store
+        if (active) {
+            for (int c = lt; c < G::COLS; c += G::TPF) {
+                const int k1 = (D == 3) ? c / NH : 0, k2 = (D == 3) ? c % NH : c;
+#pragma unroll
+                for (int k0 = 0; k0 < N; ++k0) x[k0] = s[(D == 3 ? (k0 * N + k1) * RS : k0 * RS) + k2];
+                fft_reg<N, false>(x);
+#pragma unroll
+                for (int k0 = 0; k0 < N; ++k0) {
+                    const int idx = (D == 3) ? (k0 * N + k1) * NH + k2 : k0 * NH + k2;
+                    const int par = (k0 + k1 + k2) & 1;
+                    if (MODE == ANA_SPECTRUM) {
+                        const bool nyq = (k0 == H) || (k2 == H) || (D == 3 && k1 == H);
+                        const float sc = nyq ? 0.f : (par ? -P.inv_n : P.inv_n);
+                        dst[idx] = cscale(x[k0], sc);
+                    } else {
+                        const int a = wrapk(k0, N), b = (D == 3) ? wrapk(k1, N) : 0;
+                        const float c0 = __ldg(&ct[a * a + b * b + k2 * k2]);
+                        const float sc = par ? -c0 : c0;
+                        const float2 old = dst[idx];
+                        dst[idx] = make_float2(fmaf(x[k0].x, sc, old.x), fmaf(x[k0].y, sc, old.y));
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ output
+// Gain field of every slot (complex-to-real of Qhat+ with all modes, Nyquist
+// included) minus the loss f_N(l) * Lambda(j), written for every ordered pair
+// (e, j, l) that maps to the slot.
+struct OutParams {
+    const float2* qhat;   // [U][half]
+    const float* fN;      // [n_c][n]
+    const float* lam;     // [n_c][n]
+    const int* out_start; // [U+1]
+    const int4* outs;     // (e, jloc, lloc, 0)
+    float* Q;             // [n_pairs][n]
+    int U;
+};
+
+template <int N, int D, int FPC>
+__global__ void __launch_bounds__(Geo<N, D>::TPF * FPC) k_output(OutParams P) {
+    using G = Geo<N, D>;
+    constexpr int H = G::H, RS = G::RS, NH = G::NH;
+    extern __shared__ float2 smem[];
+    const int grp = threadIdx.x / G::TPF, lt = threadIdx.x % G::TPF;
+    const int u = blockIdx.x * FPC + grp;
+    const bool active = u < P.U;
+    float2* s = smem + grp * G::SMEM_F;
+    const float2* __restrict__ src = P.qhat + (size_t)u * G::half;
+    float2 x[N];
+    // axis 0 (all columns, Nyquist included), sign (-1)^k from the index parity
+    if (active) {
+        for (int c = lt; c < G::COLS; c += G::TPF) {
+            const int k1 = (D == 3) ? c / NH : 0, k2 = (D == 3) ? c % NH : c;
+#pragma unroll
+            for (int k0 = 0; k0 < N; ++k0) {
+                const int idx = (D == 3) ? (k0 * N + k1) * NH + k2 : k0 * NH + k2;
+                const float2 v = src[idx];
+                x[k0] = ((k0 + k1 + k2) & 1) ? make_float2(-v.x, -v.y) : v;
+            }
+            fft_reg<N, true>(x);
+#pragma unroll
+            for (int i0 = 0; i0 < N; ++i0) s[(D == 3 ? (i0 * N + k1) * RS : i0 * RS) + k2] = x[i0];
+        }
+    }
+    __syncthreads();
+    if (D == 3) {
+        if (active) {
+            for (int c = lt; c < G::COLS; c += G::TPF) {
+                const int i0 = c / NH, k2 = c % NH;
+#pragma unroll
+                for (int k1 = 0; k1 < N; ++k1) x[k1] = s[(i0 * N + k1) * RS + k2];
+                fft_reg<N, true>(x);
+#pragma unroll
+                for (int i1 = 0; i1 < N; ++i1) s[(i0 * N + i1) * RS + k2] = x[i1];
+            }
+        }
+        __syncthreads();
+    }
+    if (!active) return;
+    const int row = (D == 3) ? (lt / H) * N + (lt % H) : lt;
+    {
+        const float2* r1 = s + row * RS;
+        const float2* r2 = s + (row + H) * RS;
+        x[0] = make_float2(r1[0].x, r2[0].x);
+        x[H] = make_float2(r1[H].x, r2[H].x);
+#pragma unroll
+        for (int k = 1; k < H; ++k) {
+            const float2 a = r1[k], b = r2[k];
+            x[k] = make_float2(a.x - b.y, a.y + b.x);
+            x[N - k] = make_float2(a.x + b.y, b.x - a.y);
+        }
+        fft_reg<N, true>(x);
+    }
+    for (int o = P.out_start[u]; o < P.out_start[u + 1]; ++o) {
+        const int4 e = P.outs[o];
+        const float4* f1 = reinterpret_cast<const float4*>(P.fN + (size_t)e.z * G::n + row * N);
+        const float4* f2 = reinterpret_cast<const float4*>(P.fN + (size_t)e.z * G::n + (row + H) * N);
+        const float4* l1 = reinterpret_cast<const float4*>(P.lam + (size_t)e.y * G::n + row * N);
+        const float4* l2 = reinterpret_cast<const float4*>(P.lam + (size_t)e.y * G::n + (row + H) * N);
+        float4* q1 = reinterpret_cast<float4*>(P.Q + (size_t)e.x * G::n + row * N);
+        float4* q2 = reinterpret_cast<float4*>(P.Q + (size_t)e.x * G::n + (row + H) * N);
+#pragma unroll
+        for (int c = 0; c < N / 4; ++c) {
+            const float4 a = __ldg(&f1[c]), b = __ldg(&l1[c]), a2 = __ldg(&f2[c]), b2 = __ldg(&l2[c]);
+            q1[c] = make_float4(fmaf(-a.x, b.x, x[4 * c].x), fmaf(-a.y, b.y, x[4 * c + 1].x),
+                                fmaf(-a.z, b.z, x[4 * c + 2].x), fmaf(-a.w, b.w, x[4 * c + 3].x));
+            q2[c] = make_float4(fmaf(-a2.x, b2.x, x[4 * c].y), fmaf(-a2.y, b2.y, x[4 * c + 1].y),
+                                fmaf(-a2.z, b2.z, x[4 * c + 2].y), fmaf(-a2.w, b2.w, x[4 * c + 3].y));
+        }
+    }
+}
+
+// ------------------------------------------------------------------ sigma-contraction
+// P_{q,u}(v) = sum_p w_p A_{q,p,j_u}(v) A_{q,antipode(p),l_u}(v) for the slots of a tile:
+//   TRI  (TJ = TL = T): all (j0+a, j0+b), a <= b   -> slot0 + a*T - a(a-1)/2 + (b-a)
+//   FULL (TJ x TL)    : all (j0+a, l0+b)           -> slot0 + a*TL + b
+//   LIST (T = 16)     : (ja[t], lb[t]) for t < count -> slot0 + t
+// One thread per voxel; the TJ + TL field values of a direction are loaded
+// once and reused by every slot of the tile (a register-blocked outer product).
+enum { TILE_TRI = 0, TILE_FULL = 1, TILE_LIST = 2 };
+
+struct Tile {
+    int ja[16];
+    int lb[16];
+    int slot0;
+    int count;
+    int j0, l0;
+};
+
+struct ConParams {
+    const float* A;       // [nq][M][n_c][n]
+    float* P;             // [nq][U][n]
+    const Tile* tiles;
+    const float* w;       // [M]
+    const int* anti;      // [M]
+    int M, n_c, U, n;
+};
+
+template <int KIND, int TJ, int TL>
+__global__ void __launch_bounds__(256) k_contract(ConParams C) {
+    const int v = blockIdx.x * 256 + threadIdx.x;
+    if (v >= C.n) return;
+    const Tile& tl = C.tiles[blockIdx.y];
+    const size_t n = (size_t)C.n;
+    const float* __restrict__ Aq = C.A + (size_t)blockIdx.z * C.M * C.n_c * n + v;
+    constexpr int NACC = (KIND == TILE_TRI) ? TJ * (TJ + 1) / 2 : (KIND == TILE_FULL ? TJ * TL : TJ);
+    float acc[NACC];
+#pragma unroll
+    for (int i = 0; i < NACC; ++i) acc[i] = 0.f;
+    if (KIND == TILE_LIST) {
+        int ja[TJ], lb[TJ];
+#pragma unroll
+        for (int t = 0; t < TJ; ++t) {
+            ja[t] = tl.ja[t];
+            lb[t] = tl.lb[t];
+        }
+        for (int p = 0; p < C.M; ++p) {
+            const float wp = __ldg(&C.w[p]);
+            const float* __restrict__ Ap = Aq + (size_t)p * C.n_c * n;
+            const float* __restrict__ Ab = Aq + (size_t)__ldg(&C.anti[p]) * C.n_c * n;
+#pragma unroll
+            for (int t = 0; t < TJ; ++t)
+                acc[t] = fmaf(wp * __ldg(&Ap[(size_t)ja[t] * n]), __ldg(&Ab[(size_t)lb[t] * n]), acc[t]);
+        }
+    } else {
+        const int j0 = tl.j0, l0 = (KIND == TILE_TRI) ? tl.j0 : tl.l0;
+        for (int p = 0; p < C.M; ++p) {
+            const float wp = __ldg(&C.w[p]);
+            const float* __restrict__ Ap = Aq + ((size_t)p * C.n_c + j0) * n;
+            const float* __restrict__ Ab = Aq + ((size_t)__ldg(&C.anti[p]) * C.n_c + l0) * n;
+            float a[TJ], b[TL];
+#pragma unroll
+            for (int t = 0; t < TJ; ++t) a[t] = wp * __ldg(&Ap[t * n]);
+#pragma unroll
+            for (int t = 0; t < TL; ++t) b[t] = __ldg(&Ab[t * n]);
+            if (KIND == TILE_TRI) {
+                int i = 0;
+#pragma unroll
+                for (int x = 0; x < TJ; ++x)
+#pragma unroll
+                    for (int y = x; y < TJ; ++y) {
+                        acc[i] = fmaf(a[x], b[y], acc[i]);
+                        ++i;
+                    }
+            } else {
+#pragma unroll
+                for (int x = 0; x < TJ; ++x)
+#pragma unroll
+                    for (int y = 0; y < TL; ++y) acc[x * TL + y] = fmaf(a[x], b[y], acc[x * TL + y]);
+            }
+        }
+    }
+    float* __restrict__ Pq = C.P + (size_t)blockIdx.z * C.U * n + v;
+    const int cnt = (KIND == TILE_LIST) ? tl.count : NACC;
+#pragma unroll
+    for (int i = 0; i < NACC; ++i)
+        if (i < cnt) Pq[(size_t)(tl.slot0 + i) * n] = acc[i];
+}
+
+// ------------------------------------------------------------------ projection
+// partial[vs][k][pr] = sum_{v in slice vs} V_k(v) Q_pr(v); the reduce kernel sums
+// the slices in a fixed order and applies dv^D (midpoint rule).
+template <int PB, int RT>
+__global__ void __launch_bounds__(256) k_project(const float* __restrict__ V, const float* __restrict__ Q,
+                                                 float* __restrict__ partial, int r, int n, int n_slices) {
+    const int pr0 = blockIdx.x * PB, vs = blockIdx.y, k0 = blockIdx.z * RT;
+    const int r2 = r * r;
+    const int v0 = (int)((long long)n * vs / n_slices), v1 = (int)((long long)n * (vs + 1) / n_slices);
+    float acc[PB][RT];
+#pragma unroll
+    for (int i = 0; i < PB; ++i)
+#pragma unroll
+        for (int j = 0; j < RT; ++j) acc[i][j] = 0.f;
+    for (int v = v0 + threadIdx.x; v < v1; v += 256) {
+        float q[PB], w[RT];
+#pragma unroll
+        for (int i = 0; i < PB; ++i) q[i] = (pr0 + i < r2) ? __ldg(&Q[(size_t)(pr0 + i) * n + v]) : 0.f;
+#pragma unroll
+        for (int j = 0; j < RT; ++j) w[j] = (k0 + j < r) ? __ldg(&V[(size_t)(k0 + j) * n + v]) : 0.f;
+#pragma unroll
+        for (int i = 0; i < PB; ++i)
+#pragma unroll
+            for (int j = 0; j < RT; ++j) acc[i][j] = fmaf(q[i], w[j], acc[i][j]);
+    }
+    __shared__ float red[8][PB * RT];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < PB; ++i)
+#pragma unroll
+        for (int j = 0; j < RT; ++j) {
+            float t = acc[i][j];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            if (lane == 0) red[warp][i * RT + j] = t;
+        }
+    __syncthreads();
+    for (int e = threadIdx.x; e < PB * RT; e += 256) {
+        float t = 0.f;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) t += red[w][e];
+        const int i = e / RT, j = e % RT;
+        if (pr0 + i < r2 && k0 + j < r) partial[((size_t)vs * r + k0 + j) * r2 + pr0 + i] = t;
+    }
+}
+
+__global__ void k_project_reduce(const float* __restrict__ partial, float* __restrict__ T, int count,
+                                 int n_slices, float scale) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    float t = 0.f;
+    for (int s = 0; s < n_slices; ++s) t += partial[(size_t)s * count + i];
+    T[i] = t * scale;
+}
+
+}  // namespace boltz_dev

@@ -1,0 +1,190 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerance (FP32 path): relative L-infinity error <= 1e-5 of the per-result
+scale s = max(max|Q|, max|Q+|, max|Q-|) of the oracle, the same bound for the
+projection tensor normalised by max|T|.  Inputs are seeded and rounded once to
+FP32; both sides receive the same values.
+"""
+import numpy as np
+import pytest
+
+from gpu_helpers import as_fp32, gpu_collide, oracle_collide, rel_err, require_gpu
+from paper_2112_02695_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def B():
+    return require_gpu()
+
+
+@pytest.mark.parametrize("N,d", [(16, 3), (32, 3), (8, 3), (32, 2), (64, 2), (8, 2)])
+def test_spectrum_matches_oracle(B, N, d):
+    import torch
+    from oracle import collision as C
+    f = as_fp32(W.random_fields(N, d, 8.0, 3, seed=100 + N))
+    g = B.boltz_grid_init(N, d, 8.0, 8.0, 1.0, 4, 6 if d == 3 else 8)
+    try:
+        spec = B.boltz_spectrum(g, torch.tensor(f, dtype=torch.float32, device="cuda")).cpu().numpy()
+    finally:
+        g.close()
+    prob = C.Problem(N=N, d=d, L=8.0, R=8.0, gamma=1.0, n_rho=4, M=6 if d == 3 else 8)
+    ref = C.spectrum(prob, f)[..., : N // 2 + 1]
+    assert np.max(np.abs(spec - ref)) / np.max(np.abs(ref)) < 1e-6
+
+
+def test_c1_bkw_2d_single_evaluation(B):
+    """2D, N=32 on [-8,8]^2, Maxwell molecules, R=8, N_rho=16 x M=16, BKW at t=0.5."""
+    cfg = (32, 2, 8.0, 8.0, 0.0, 16, 16)
+    f = as_fp32(W.bkw(32, 2, 8.0, 0.5))[None]
+    Qg = gpu_collide(B, cfg, f, [(0, 0)])
+    _, Qo, s = oracle_collide(cfg, f, [(0, 0)])
+    assert rel_err(Qg, Qo, s).max() < TOL
+
+
+@pytest.mark.parametrize("form", [0, 1])
+def test_small_3d_all_pairs_and_projection(B, form):
+    """3D N=16, rank-4 Hermite-Maxwellian basis, all 16 ordered pairs + T."""
+    cfg = (16, 3, 8.0, 8.0, 1.0, 8, 14)
+    V = as_fp32(W.hermite_maxwellian_basis(16, 3, 8.0, 4, seed=7))
+    pairs = [(j, l) for j in range(4) for l in range(4)]
+    Qg, Tg = gpu_collide(B, cfg, V, pairs, form=form, return_T=True)
+    prob, Qo, s = oracle_collide(cfg, V, pairs)
+    assert rel_err(Qg, Qo, s).max() < TOL
+    from oracle import collision as C
+    To = C.project(prob, V, Qo).reshape(4, 4, 4)
+    assert np.max(np.abs(Tg - To)) / np.max(np.abs(To)) < TOL
+
+
+def test_plain_form_equals_batched_form(B):
+    cfg = (16, 3, 8.0, 8.0, 1.0, 6, 26)
+    V = as_fp32(W.hermite_maxwellian_basis(16, 3, 8.0, 3, seed=8))
+    pairs = [(0, 1), (1, 0), (2, 2), (1, 2)]
+    Qb = gpu_collide(B, cfg, V, pairs, form=0)
+    Qp = gpu_collide(B, cfg, V, pairs, form=1)
+    scale = np.max(np.abs(Qb), axis=(1, 2, 3))
+    assert (np.max(np.abs(Qb - Qp), axis=(1, 2, 3)) / scale).max() < 2e-6
+
+
+def test_tiles_and_ragged_tail(B):
+    """r = 20 inputs: one 16-wide triangular tile, off-diagonal strips and a
+    ragged list tail; all 400 ordered pairs against the oracle."""
+    cfg = (8, 3, 8.0, 8.0, 1.0, 3, 38)
+    V = as_fp32(W.random_fields(8, 3, 8.0, 20, seed=20))
+    pairs = [(j, l) for j in range(20) for l in range(20)]
+    Qg = gpu_collide(B, cfg, V, pairs)
+    _, Qo, s = oracle_collide(cfg, V, pairs)
+    assert rel_err(Qg, Qo, s).max() < TOL
+
+
+def test_tri8_and_full8_tiles(B):
+    """r = 12 inputs use 8-wide tiles plus list tiles."""
+    cfg = (8, 3, 8.0, 8.0, 0.0, 3, 14)
+    V = as_fp32(W.random_fields(8, 3, 8.0, 12, seed=12))
+    pairs = [(j, l) for j in range(12) for l in range(12)]
+    Qg = gpu_collide(B, cfg, V, pairs)
+    _, Qo, s = oracle_collide(cfg, V, pairs)
+    assert rel_err(Qg, Qo, s).max() < TOL
+
+
+def test_many_cells_span_several_chunks(B):
+    """70 cells Q(f_x, f_x) at N=8, M=86: more inputs than one chunk holds."""
+    cfg = (8, 3, 8.0, 8.0, 1.0, 4, 86)
+    F = as_fp32(W.random_fields(8, 3, 8.0, 70, seed=70))
+    pairs = [(x, x) for x in range(70)]
+    Qg = gpu_collide(B, cfg, F, pairs)
+    _, Qo, s = oracle_collide(cfg, F, pairs)
+    assert rel_err(Qg, Qo, s).max() < TOL
+
+
+@pytest.mark.parametrize("N", [8, 16, 64])
+def test_2d_sizes(B, N):
+    cfg = (N, 2, 8.0, 8.0, 1.0, 8, 12)
+    F = as_fp32(W.random_fields(N, 2, 8.0, 3, seed=N))
+    pairs = [(0, 1), (2, 0), (1, 1)]
+    Qg = gpu_collide(B, cfg, F, pairs)
+    _, Qo, s = oracle_collide(cfg, F, pairs)
+    assert rel_err(Qg, Qo, s).max() < TOL
+
+
+def test_duplicate_and_reversed_pairs(B):
+    cfg = (16, 2, 8.0, 8.0, 1.0, 6, 10)
+    F = as_fp32(W.random_fields(16, 2, 8.0, 2, seed=5))
+    pairs = [(0, 1), (1, 0), (0, 1), (0, 0)]
+    Qg = gpu_collide(B, cfg, F, pairs)
+    _, Qo, s = oracle_collide(cfg, F, pairs)
+    assert rel_err(Qg, Qo, s).max() < TOL
+    assert np.array_equal(Qg[0], Qg[2])
+
+
+def test_empty_batch_and_bad_indices(B):
+    import torch
+    g = B.boltz_grid_init(16, 3, 8.0, 8.0, 1.0, 4, 6)
+    try:
+        spec = torch.zeros((2,) + g.half_shape, dtype=torch.complex64, device="cuda")
+        out = B.boltz_collide_batched(g, spec, [], [])
+        assert out.shape[0] == 0
+        for pj, pl in (([0], [2]), ([-1], [0])):
+            with pytest.raises(B.BoltzError) as ei:
+                B.boltz_collide_batched(g, spec, pj, pl)
+            assert ei.value.status == B.BOLTZ_EINVAL
+        with pytest.raises(B.BoltzError):
+            B.boltz_collide_batched(g, spec, [0], [0], form=7)
+    finally:
+        g.close()
+
+
+def test_lowrank_step_host_matches_device_path(B):
+    import torch
+    cfg = (16, 3, 8.0, 8.0, 1.0, 6, 14)
+    V = as_fp32(W.hermite_maxwellian_basis(16, 3, 8.0, 4, seed=3))
+    pairs = [(j, l) for j in range(4) for l in range(4)]
+    Qd, Td = gpu_collide(B, cfg, V, pairs, return_T=True)
+    g = B.boltz_grid_init(*cfg)
+    try:
+        Vh = torch.tensor(V, dtype=torch.float32).pin_memory()
+        Qh = torch.empty((16,) + g.shape, dtype=torch.float32).pin_memory()
+        _, Th = B.boltz_lowrank_step_host(g, Vh, Qh)
+    finally:
+        g.close()
+    assert np.array_equal(Qh.numpy().astype(np.float64), Qd)
+    assert np.max(np.abs(Th.numpy() - Td)) <= 1e-6 * np.max(np.abs(Td))
+
+
+# ---------------------------------------------------------------- full-size workloads
+
+def test_c2_full_size_sampled_pairs(B):
+    """3D N=32^3 on [-8,8]^3, gamma=1, R=8, N_rho=32 x M=38, rank 16 (seed 2112):
+    all 256 pairs and T on the GPU in one batched call; sampled pairs against the
+    oracle, and T against an FP64 projection of the GPU's Q."""
+    cfg = (32, 3, 8.0, 8.0, 1.0, 32, 38)
+    V = as_fp32(W.hermite_maxwellian_basis(32, 3, 8.0, 16, seed=2112))
+    pairs = [(j, l) for j in range(16) for l in range(16)]
+    Qg, Tg = gpu_collide(B, cfg, V, pairs, return_T=True)
+    dv3 = 0.5 ** 3
+    T64 = dv3 * V.reshape(16, -1) @ Qg.reshape(256, -1).T
+    assert np.max(np.abs(Tg.reshape(16, 256) - T64)) / np.max(np.abs(T64)) < 1e-5
+    sample = [(0, 0), (3, 11), (15, 2), (7, 7)]
+    for j, l in sample:
+        _, Qo, s = oracle_collide(cfg, V[[j, l]], [(0, 1)] if j != l else [(0, 0)])
+        assert rel_err(Qg[j * 16 + l][None], Qo, s).max() < TOL, (j, l)
+
+
+def test_c3_full_size_shock_cells_bimodal(B):
+    """512 normal-shock cells f_x = (1-w) M_L + w M_R (Mach 3, d=3) in one call.
+    By bilinearity every cell equals a^2 Q_LL + a(1-a)(Q_LR + Q_RL) + (1-a)^2 Q_RR
+    with a = 1-w; the four pair results come from the oracle."""
+    cfg = (32, 3, 8.0, 8.0, 1.0, 32, 38)
+    F, w = W.shock_cells(32, 3, 8.0, n_cells=512)
+    F = as_fp32(F)
+    Qg = gpu_collide(B, cfg, F, [(x, x) for x in range(512)])
+    fL, fR = W.shock_states_fields(32, 3, 8.0)
+    _, Qo, _ = oracle_collide(cfg, np.stack([fL, fR]), [(0, 0), (0, 1), (1, 0), (1, 1)])
+    a = (1.0 - w)[:, None, None, None]
+    pred = a * a * Qo[0] + a * (1 - a) * (Qo[1] + Qo[2]) + (1 - a) ** 2 * Qo[3]
+    scale = np.max(np.abs(Qo))      # gain/loss scale of the two end states
+    err = np.max(np.abs(Qg - pred), axis=(1, 2, 3)) / scale
+    # the cell inputs are FP32 roundings of the exact mixture: allow that input rounding
+    assert err.max() < TOL
