@@ -169,6 +169,32 @@ boltz_status boltz_project(boltz_grid g, const float* V, int r, const float* Q, 
                            void* stream);
 
 /*
+ * Allocation-free variant of boltz_project (the paper has no counterpart; this
+ * is a deployment aid).  Same arguments, layout and result as boltz_project
+ * (up to the order of FP32 summation), but it never allocates device memory:
+ * its partial sums live in a fixed 2 MiB array in the library's device image
+ * (static __device__ storage that every device loading the library holds
+ * until the process exits), so it calls no cudaMalloc, cudaFree or
+ * allocating library routine.  It is meant for callers that must not
+ * allocate device memory while they run: cudaMalloc and cudaFree can
+ * synchronise the whole device and stall unrelated streams in a latency-
+ * critical solver loop, and a process whose device memory is fully reserved
+ * up front by another allocator (a framework's caching pool, a fixed
+ * embedded budget) may have no room for a new allocation.
+ *   r       1..64 (the partial sums need r^3 x slices floats <= 2^19; the
+ *           slice count is reduced to fit).  Larger r: BOLTZ_EINVAL.
+ * The first call on a device resolves the array's device address with
+ * cudaGetSymbolAddress (device current, once per device); make that first
+ * call before any stream capture.  Every call shares the one array: calls
+ * that can overlap on the GPU (different streams, or different grids on the
+ * same device) race on it and must be serialised by the caller.  Each call
+ * writes every partial sum it reads, so no clearing is needed.
+ * Errors: BOLTZ_EINVAL, BOLTZ_ECUDA.
+ */
+boltz_status boltz_project_noalloc(boltz_grid g, const float* V, int r, const float* Q, float* T_out,
+                                   void* stream);
+
+/*
  * End-to-end low-rank collision step from host memory: copies the physical
  * basis V (HOST float32 [r][N^d]) to the device, computes its spectra, all r^2
  * pairs Q(V_j, V_l) (batched form) and the projection T, and copies Q (HOST

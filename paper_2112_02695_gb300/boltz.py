@@ -30,6 +30,7 @@ EXPORTED = (
     "boltz_abi_version", "boltz_status_string", "boltz_grid_init", "boltz_grid_destroy",
     "boltz_spectrum", "boltz_collide_batched", "boltz_project", "boltz_lowrank_step_host",
     "boltz_host_quadrature", "boltz_workspace_size", "boltz_profile_enable", "boltz_profile_read",
+    "boltz_project_noalloc",
 )
 
 KERNEL_CLASSES = ("spectrum", "prep", "shift", "contract", "radial", "output", "project")
@@ -67,6 +68,7 @@ def _load() -> ctypes.CDLL:
         "boltz_workspace_size": ([vp, ctypes.c_int, i32p, i32p, ctypes.c_int, ctypes.c_int,
                                   ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
         "boltz_profile_enable": ([vp, ctypes.c_int], ctypes.c_int),
+        "boltz_project_noalloc": ([vp, vp, ctypes.c_int, vp, vp, vp], ctypes.c_int),
         "boltz_profile_read": ([vp, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
                                 ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     }
@@ -201,6 +203,23 @@ def boltz_project(grid: Grid, V, Q, out=None, stream=None):
         out = torch.empty((r, r, r), dtype=torch.float32, device=V.device)
     _check(_lib.boltz_project(grid.handle, _dev_ptr(V, "float32", "V"), r, _dev_ptr(Q, "float32", "Q"),
                               _dev_ptr(out, "float32", "out"), _stream_ptr(stream)), "boltz_project")
+    return out
+
+
+def boltz_project_noalloc(grid: Grid, V, Q, out, stream=None):
+    """Like boltz_project, but the library allocates no device memory for it:
+    the partial sums use a fixed 2 MiB device array inside the library, so
+    callers that must not allocate (a solver loop that cannot afford the
+    device-wide synchronisation of cudaMalloc/cudaFree, or a process whose
+    device memory is reserved up front) can still project.  `out` must be
+    given (float32 [r, r, r]); r <= 64.  Calls that may overlap on the GPU
+    share the array and must be serialised by the caller."""
+    r = V.shape[0]
+    if Q.shape[0] != r * r:
+        raise ValueError("Q must hold r*r fields")
+    _check(_lib.boltz_project_noalloc(grid.handle, _dev_ptr(V, "float32", "V"), r, _dev_ptr(Q, "float32", "Q"),
+                                      _dev_ptr(out, "float32", "out"), _stream_ptr(stream)),
+           "boltz_project_noalloc")
     return out
 
 

@@ -574,6 +574,38 @@ boltz_status run_project(boltz_grid_s* g, const float* V, int r, const float* Q,
 
 size_t project_partial_bytes(int r) { return size_t(64) * r * r * r * sizeof(float); }
 
+// ---------------------------------------------------------------- allocation-free projection
+// Partial sums of boltz_project_noalloc: a fixed 2 MiB array that every device
+// which loads the library holds until the process exits.  In host code the
+// symbol is only a host-side stand-in; kernels get the device address that
+// cudaGetSymbolAddress returns for the current device.
+constexpr int kNoAllocProjectFloats = 1 << 19;
+static __device__ __align__(256) float g_noalloc_project_partial[kNoAllocProjectFloats];
+
+// Resolves the array's device address once per device (the device must be
+// current); later calls on that device reuse the cached address.
+boltz_status noalloc_project_partial(float** out) {
+    static std::mutex mu;
+    static std::map<int, float*> addr;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return BOLTZ_ECUDA;
+    }
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = addr.find(dev);
+    if (it == addr.end()) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_project_partial) != cudaSuccess || p == nullptr) {
+            (void)cudaGetLastError();
+            return BOLTZ_ECUDA;
+        }
+        it = addr.emplace(dev, static_cast<float*>(p)).first;
+    }
+    *out = it->second;
+    return BOLTZ_OK;
+}
+
 // The twiddle table lives in constant memory, once per device.
 boltz_status ensure_twiddles(int device) {
     static std::mutex mu;
@@ -801,6 +833,35 @@ boltz_status boltz_project(boltz_grid g, const float* V, int r, const float* Q, 
     if (s != BOLTZ_OK) return s;
     const size_t off2 = g->plan_uploaded ? align_up(g->last_plan.plan_bytes, 256) : 0;
     return run_project(g, V, r, Q, T_out, reinterpret_cast<float*>(g->d_ws + off2), st);
+}
+
+boltz_status boltz_project_noalloc(boltz_grid g, const float* V, int r, const float* Q, float* T_out,
+                                   void* stream) {
+    if (!g || !V || !Q || !T_out || r < 1 || r > 64) return BOLTZ_EINVAL;
+    const long long r3 = (long long)r * r * r;
+    if (r3 > kNoAllocProjectFloats) return BOLTZ_EINVAL;
+    float* partial = nullptr;
+    boltz_status s = noalloc_project_partial(&partial);
+    if (s != BOLTZ_OK) return s;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    constexpr int PB = 8, RT = 16;
+    const int r2 = r * r;
+    const int bx = (r2 + PB - 1) / PB, bz = (r + RT - 1) / RT;
+    int slices = std::max(1, std::min(64, (2 * 152) / std::max(1, bx * bz)));
+    slices = std::min(slices, std::max(1, g->n / 256));
+    slices = std::max(1, std::min<int>(slices, (int)(kNoAllocProjectFloats / r3)));
+    // every partial entry the reduction reads is written by k_project first,
+    // so nothing left in the array by an earlier call is ever read
+    {
+        ProfScope ps(g, BOLTZ_KCLASS_PROJECT, st);
+        k_project<PB, RT><<<dim3(bx, slices, bz), 256, 0, st>>>(V, Q, partial, r, g->n, slices);
+    }
+    const int count = r * r2;
+    const float scale = (float)std::pow(2.0 * g->L / g->N, g->D);
+    ProfScope ps(g, BOLTZ_KCLASS_PROJECT, st);
+    k_project_reduce<<<(count + 255) / 256, 256, 0, st>>>(partial, T_out, count, slices, scale);
+    BZ_CUDA(cudaGetLastError());
+    return BOLTZ_OK;
 }
 
 boltz_status boltz_lowrank_step_host(boltz_grid g, const float* V_host, int r, float* Q_host, float* T_host,
