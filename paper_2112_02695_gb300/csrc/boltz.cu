@@ -71,8 +71,8 @@ struct boltz_grid_s {
     float2* d_phase = nullptr;   // [(n_rho*M + 1)][D][N]
     float* d_ctab = nullptr;     // [n_rho][smax+1]
     float* d_gm = nullptr;       // [smax+1]
-    float* d_w = nullptr;        // [M]
-    int* d_anti = nullptr;       // [M]
+    float* d_w = nullptr;        // [M/2] weight of each antipodal direction pair
+    int2* d_dpair = nullptr;     // [M/2] (p, antipode(p)), p < antipode(p)
     // workspace
     char* d_ws = nullptr;
     size_t ws_cap = 0, ws_max = kDefaultWorkspace;
@@ -381,6 +381,10 @@ struct Launch {
                                         : (N == 64 ? 4 : (N == 32 ? 16 : (N == 16 ? 32 : 64)));
     static constexpr int BLOCK = G::TPF * FPC;
     static constexpr size_t SMEM = size_t(G::SMEM_F) * FPC * sizeof(float2);
+    // 3D N = 32: shifted fields and forward transforms on CTA pairs (half the planes each)
+    static constexpr bool PAIR = (D == 3 && N == 32);
+    static constexpr int PBLOCK = (N / 2) * (N / 2);
+    static constexpr size_t PSMEM = PairGeo<N>::SMEM;
 
     static cudaError_t prepare() {
         cudaError_t e;
@@ -388,9 +392,22 @@ struct Launch {
         if ((e = set_smem(k_synth<N, D, FPC, SYN_PREP>, SMEM)) != cudaSuccess) return e;
         if ((e = set_smem(k_analysis<N, D, FPC, ANA_SPECTRUM>, SMEM)) != cudaSuccess) return e;
         if ((e = set_smem(k_analysis<N, D, FPC, ANA_ACCUM>, SMEM)) != cudaSuccess) return e;
+        if constexpr (PAIR) {
+            if ((e = set_smem(k_synth_cl<N, SYN_SHIFT>, PSMEM)) != cudaSuccess) return e;
+            if ((e = set_smem(k_synth_cl<N, SYN_PREP>, PSMEM)) != cudaSuccess) return e;
+            if ((e = set_smem(k_analysis_cl<N, ANA_SPECTRUM>, PSMEM)) != cudaSuccess) return e;
+            if ((e = set_smem(k_analysis_cl<N, ANA_ACCUM>, PSMEM)) != cudaSuccess) return e;
+        }
         return set_smem(k_output<N, D, FPC>, SMEM);
     }
     static void synth(const SynParams& p, int mode, cudaStream_t st) {
+        if constexpr (PAIR) {
+            if (mode == SYN_SHIFT)
+                k_synth_cl<N, SYN_SHIFT><<<2 * p.n_fields, PBLOCK, PSMEM, st>>>(p);
+            else
+                k_synth_cl<N, SYN_PREP><<<2 * p.n_fields, PBLOCK, PSMEM, st>>>(p);
+            return;
+        }
         const int grid = (p.n_fields + FPC - 1) / FPC;
         if (mode == SYN_SHIFT)
             k_synth<N, D, FPC, SYN_SHIFT><<<grid, BLOCK, SMEM, st>>>(p);
@@ -398,6 +415,13 @@ struct Launch {
             k_synth<N, D, FPC, SYN_PREP><<<grid, BLOCK, SMEM, st>>>(p);
     }
     static void analysis(const AnaParams& p, int mode, cudaStream_t st) {
+        if constexpr (PAIR) {
+            if (mode == ANA_SPECTRUM)
+                k_analysis_cl<N, ANA_SPECTRUM><<<2 * p.n_fields, PBLOCK, PSMEM, st>>>(p);
+            else
+                k_analysis_cl<N, ANA_ACCUM><<<2 * p.n_fields, PBLOCK, PSMEM, st>>>(p);
+            return;
+        }
         const int grid = (p.n_fields + FPC - 1) / FPC;
         if (mode == ANA_SPECTRUM)
             k_analysis<N, D, FPC, ANA_SPECTRUM><<<grid, BLOCK, SMEM, st>>>(p);
@@ -515,7 +539,8 @@ boltz_status run_batched(boltz_grid_s* g, const float2* spectra, int n_inputs, c
             cp.A = A;
             cp.P = Pbuf;
             cp.w = g->d_w;
-            cp.anti = g->d_anti;
+            cp.dpair = g->d_dpair;
+            cp.n_dpair = g->M / 2;
             cp.M = g->M;
             cp.n_c = nc;
             cp.U = c.U;
@@ -729,8 +754,21 @@ boltz_status boltz_grid_init(boltz_grid* out, int N, int d_v, double L, double R
         }
         gm[sq] = (float)(g->b * area * acc);
     }
-    std::vector<float> wdir(M);
-    for (int p = 0; p < M; ++p) wdir[p] = (float)g->dir.w[p];
+    // antipodal direction pairs (p, p'), p < p'; the rules are centrally symmetric with w_p = w_p'
+    std::vector<float> wdir;
+    std::vector<int2> dpair;
+    for (int p = 0; p < M; ++p) {
+        const int pb = g->dir.antipode[p];
+        if (pb == p || std::fabs(g->dir.w[p] - g->dir.w[pb]) > 1e-12 * g->dir.w[p]) {
+            delete g;
+            return BOLTZ_EINVAL;
+        }
+        if (p < pb) {
+            dpair.push_back(make_int2(p, pb));
+            wdir.push_back((float)g->dir.w[p]);
+        }
+    }
+    const int n_dp = (int)dpair.size();
 
     auto fail = [&](boltz_status s) {
         boltz_grid_destroy(g);
@@ -745,15 +783,16 @@ boltz_status boltz_grid_init(boltz_grid* out, int N, int d_v, double L, double R
     if (cudaMalloc(&g->d_phase, phase.size() * sizeof(float2)) != cudaSuccess ||
         cudaMalloc(&g->d_ctab, ctab.size() * sizeof(float)) != cudaSuccess ||
         cudaMalloc(&g->d_gm, gm.size() * sizeof(float)) != cudaSuccess ||
-        cudaMalloc(&g->d_w, M * sizeof(float)) != cudaSuccess || cudaMalloc(&g->d_anti, M * sizeof(int)) != cudaSuccess) {
+        cudaMalloc(&g->d_w, n_dp * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&g->d_dpair, n_dp * sizeof(int2)) != cudaSuccess) {
         (void)cudaGetLastError();
         return fail(BOLTZ_ENOMEM);
     }
     if (cudaMemcpy(g->d_phase, phase.data(), phase.size() * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(g->d_ctab, ctab.data(), ctab.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(g->d_gm, gm.data(), gm.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(g->d_w, wdir.data(), M * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(g->d_anti, g->dir.antipode.data(), M * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+        cudaMemcpy(g->d_w, wdir.data(), n_dp * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(g->d_dpair, dpair.data(), n_dp * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess)
         return fail(BOLTZ_ECUDA);
     if (dispatch_for(N, d_v)->prepare() != cudaSuccess) return fail(BOLTZ_ECUDA);
     *out = g;
@@ -772,7 +811,7 @@ boltz_status boltz_grid_destroy(boltz_grid g) {
     cudaFree(g->d_ctab);
     cudaFree(g->d_gm);
     cudaFree(g->d_w);
-    cudaFree(g->d_anti);
+    cudaFree(g->d_dpair);
     cudaFree(g->d_ws);
     delete g;
     return BOLTZ_OK;

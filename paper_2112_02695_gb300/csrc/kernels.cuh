@@ -17,6 +17,7 @@
 // folded into the radial table.
 #pragma once
 
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -276,6 +277,230 @@ __global__ void __launch_bounds__(Geo<N, D>::TPF * FPC) k_analysis(AnaParams P) 
     }
 }
 
+// ------------------------------------------------------------------ 3D field kernels on a CTA pair
+// Same transforms as k_synth / k_analysis for d = 3, with one field spread
+// over a cluster of two CTAs: CTA r holds the planes i0 in [rH, rH + H)
+// (H = N/2) in shared memory, so each CTA needs half the memory and three
+// CTAs fit on an SM.  The transform along axis 0 is the only one that crosses
+// planes; it reads or writes the peer's planes through distributed shared
+// memory, between cluster barriers.  A CTA's half of a real field is one
+// contiguous block of global memory; it is moved through a staging copy in
+// shared memory (rows padded to N+2 floats) so that every warp reads or
+// writes 256 contiguous bytes, and the node's three phase rows are staged
+// once per CTA.  Planes are padded by 8 complex entries so that the two plane
+// groups a warp touches in the axis-1 pass fall on different banks.
+namespace cg = cooperative_groups;
+
+template <int N>
+struct PairGeo {
+    static constexpr int H = N / 2;
+    static constexpr int RS = H + 1;             // complex row stride
+    static constexpr int PS = N * RS + 8;        // complex plane stride
+    static constexpr int RR = N + 2;             // staged real row stride (floats)
+    static constexpr int NT = H * H;             // threads per CTA
+    static constexpr int HALF_N = H * N * N;     // floats of a field held by one CTA
+    static constexpr size_t SMEM = size_t(H) * PS * sizeof(float2) + 3 * N * sizeof(float2);
+    static_assert(size_t(H) * N * RR * sizeof(float) <= size_t(H) * PS * sizeof(float2), "staging fits the planes");
+};
+
+template <int N, int MODE>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__((N / 2) * (N / 2), 3)
+    k_synth_cl(SynParams P) {
+    using G = Geo<N, 3>;
+    using PG = PairGeo<N>;
+    constexpr int H = PG::H, RS = PG::RS, PS = PG::PS, RR = PG::RR, NT = PG::NT;
+    extern __shared__ float2 smem[];             // [H][PS] planes | [3][N] phase rows
+    float2* phs = smem + H * PS;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    float2* peer = cluster.map_shared_rank(smem, rank ^ 1);
+    float2* half0 = rank == 0 ? smem : peer;    // holder of planes [0, H)
+    float2* half1 = rank == 0 ? peer : smem;    // holder of planes [H, N)
+    const int f = blockIdx.x >> 1;
+    const bool active = f < P.n_fields;          // same for both CTAs of the cluster
+    const int lt = threadIdx.x;
+    int input = 0, node = P.id_node;
+    bool use_gm = false;
+    if (active) {
+        const int jj = f % P.n_c;
+        input = P.inputs[jj];
+        if (MODE == SYN_SHIFT) {
+            const int t = f / P.n_c, p = t % P.M, qq = t / P.M;
+            node = (P.q0 + qq) * P.M + p;
+        } else {
+            use_gm = f >= P.n_c;
+        }
+    }
+    const float2* __restrict__ src = P.spectra + (size_t)input * G::half;
+    float* __restrict__ dst = P.out + (size_t)f * G::n + (size_t)rank * PG::HALF_N;
+    for (int i = lt; i < 3 * N; i += NT) phs[i] = __ldg(&P.phase[(size_t)node * 3 * N + i]);
+    __syncthreads();
+    float2 x[N];
+    // axis 0: columns (k1, k2), k1 in this CTA's half, k2 < N/2
+    if (active) {
+        const int k1 = rank * H + lt / H, k2 = lt % H;
+        const float2 w12 = cmul(phs[N + k1], phs[2 * N + k2]);
+#pragma unroll
+        for (int k0 = 0; k0 < N; ++k0) {
+            float2 v = cmul(__ldg(&src[(k0 * N + k1) * G::NH + k2]), cmul(w12, phs[k0]));
+            if (MODE == SYN_PREP && use_gm) {
+                const int a = wrapk(k0, N), b = wrapk(k1, N);
+                v = cscale(v, __ldg(&P.gm[a * a + b * b + k2 * k2]));
+            }
+            x[k0] = v;
+        }
+        fft_reg<N, true>(x);
+#pragma unroll
+        for (int i0 = 0; i0 < H; ++i0) half0[i0 * PS + k1 * RS + k2] = x[i0];
+#pragma unroll
+        for (int i0 = 0; i0 < H; ++i0) half1[i0 * PS + k1 * RS + k2] = x[H + i0];
+    }
+    cluster.sync();
+    // axis 1 on this CTA's planes
+    if (active) {
+        const int i0 = lt / H, k2 = lt % H;
+#pragma unroll
+        for (int k1 = 0; k1 < N; ++k1) x[k1] = smem[i0 * PS + k1 * RS + k2];
+        fft_reg<N, true>(x);
+#pragma unroll
+        for (int i1 = 0; i1 < N; ++i1) smem[i0 * PS + i1 * RS + k2] = x[i1];
+    }
+    __syncthreads();
+    // axis 2: complex-to-real of rows (i0, i1) and (i0, i1 + N/2)
+    const int i0 = lt / H, i1 = lt % H;
+    if (active) {
+        const float2* r1 = smem + i0 * PS + i1 * RS;
+        const float2* r2 = smem + i0 * PS + (i1 + H) * RS;
+        x[0] = make_float2(r1[0].x, r2[0].x);
+        x[H] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k = 1; k < H; ++k) {
+            const float2 a = r1[k], b = r2[k];
+            x[k] = make_float2(a.x - b.y, a.y + b.x);
+            x[N - k] = make_float2(a.x + b.y, b.x - a.y);
+        }
+        fft_reg<N, true>(x);
+    }
+    __syncthreads();                              // every row is read before staging overwrites the planes
+    float* stg = reinterpret_cast<float*>(smem);
+    if (active) {
+        float2* o1 = reinterpret_cast<float2*>(stg + (i0 * N + i1) * RR);
+        float2* o2 = reinterpret_cast<float2*>(stg + (i0 * N + i1 + H) * RR);
+#pragma unroll
+        for (int c = 0; c < N / 2; ++c) {
+            o1[c] = make_float2(x[2 * c].x, x[2 * c + 1].x);
+            o2[c] = make_float2(x[2 * c].y, x[2 * c + 1].y);
+        }
+    }
+    __syncthreads();
+    if (active) {
+        float2* out2 = reinterpret_cast<float2*>(dst);
+#pragma unroll 4
+        for (int L = 2 * lt; L < PG::HALF_N; L += 2 * NT)
+            out2[L >> 1] = *reinterpret_cast<const float2*>(stg + (L / N) * RR + (L % N));
+    }
+}
+
+template <int N, int MODE>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__((N / 2) * (N / 2), 2)
+    k_analysis_cl(AnaParams P) {
+    using G = Geo<N, 3>;
+    using PG = PairGeo<N>;
+    constexpr int H = PG::H, RS = PG::RS, PS = PG::PS, RR = PG::RR, NT = PG::NT, NH = G::NH;
+    constexpr int COLS = H * NH;                  // this CTA's columns along axes 1 and 0
+    extern __shared__ float2 smem[];              // [H][PS] planes (or the staged real rows)
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    float2* peer = cluster.map_shared_rank(smem, rank ^ 1);
+    const float2* half0 = rank == 0 ? smem : peer;
+    const float2* half1 = rank == 0 ? peer : smem;
+    const int f = blockIdx.x >> 1;
+    const bool active = f < P.n_fields;
+    const int lt = threadIdx.x;
+    float2* __restrict__ dst = P.out + (size_t)f * G::half;
+    float* stg = reinterpret_cast<float*>(smem);
+    float2 x[N];
+    const int n_iter = (MODE == ANA_ACCUM) ? P.nq : 1;
+    for (int qq = 0; qq < n_iter; ++qq) {
+        const float* __restrict__ src =
+            ((MODE == ANA_ACCUM) ? P.in + ((size_t)qq * P.U + f) * G::n : P.in + (size_t)f * G::n) +
+            (size_t)rank * PG::HALF_N;
+        const float* __restrict__ ct = P.ctab + (size_t)(P.q0 + qq) * (G::SMAX + 1);
+        // stage this CTA's half of the real field (coalesced), then R2C along the last axis
+        if (active) {
+            const float2* in2 = reinterpret_cast<const float2*>(src);
+#pragma unroll 4
+            for (int L = 2 * lt; L < PG::HALF_N; L += 2 * NT)
+                *reinterpret_cast<float2*>(stg + (L / N) * RR + (L % N)) = __ldg(&in2[L >> 1]);
+        }
+        __syncthreads();
+        const int i0 = lt / H, i1 = lt % H;
+        if (active) {
+            const float2* a2 = reinterpret_cast<const float2*>(stg + (i0 * N + i1) * RR);
+            const float2* b2 = reinterpret_cast<const float2*>(stg + (i0 * N + i1 + H) * RR);
+#pragma unroll
+            for (int c = 0; c < N / 2; ++c) {
+                const float2 a = a2[c], b = b2[c];
+                x[2 * c] = make_float2(a.x, b.x);
+                x[2 * c + 1] = make_float2(a.y, b.y);
+            }
+        }
+        __syncthreads();                          // staged rows consumed before the planes are written
+        if (active) {
+            fft_reg<N, false>(x);
+            float2* r1 = smem + i0 * PS + i1 * RS;
+            float2* r2 = smem + i0 * PS + (i1 + H) * RS;
+#pragma unroll
+            for (int k = 0; k <= H; ++k) {
+                const float2 z = x[k], zc = x[(N - k) & (N - 1)];
+                r1[k] = make_float2(0.5f * (z.x + zc.x), 0.5f * (z.y - zc.y));
+                r2[k] = make_float2(0.5f * (z.y + zc.y), -0.5f * (z.x - zc.x));
+            }
+        }
+        __syncthreads();
+        // axis 1 on this CTA's planes
+        if (active) {
+            for (int c = lt; c < COLS; c += NT) {
+                const int p0 = c / NH, k2 = c % NH;
+#pragma unroll
+                for (int k1 = 0; k1 < N; ++k1) x[k1] = smem[p0 * PS + k1 * RS + k2];
+                fft_reg<N, false>(x);
+#pragma unroll
+                for (int k1 = 0; k1 < N; ++k1) smem[p0 * PS + k1 * RS + k2] = x[k1];
+            }
+        }
+        cluster.sync();
+        // axis 0: columns (k1, k2), k1 in this CTA's half; planes from both CTAs
+        if (active) {
+            for (int c = lt; c < COLS; c += NT) {
+                const int k1 = rank * H + c / NH, k2 = c % NH;
+#pragma unroll
+                for (int p0 = 0; p0 < H; ++p0) x[p0] = half0[p0 * PS + k1 * RS + k2];
+#pragma unroll
+                for (int p0 = 0; p0 < H; ++p0) x[H + p0] = half1[p0 * PS + k1 * RS + k2];
+                fft_reg<N, false>(x);
+#pragma unroll
+                for (int k0 = 0; k0 < N; ++k0) {
+                    const int idx = (k0 * N + k1) * NH + k2;
+                    const int par = (k0 + k1 + k2) & 1;
+                    if (MODE == ANA_SPECTRUM) {
+                        const bool nyq = (k0 == H) || (k1 == H) || (k2 == H);
+                        const float sc = nyq ? 0.f : (par ? -P.inv_n : P.inv_n);
+                        dst[idx] = cscale(x[k0], sc);
+                    } else {
+                        const int a = wrapk(k0, N), b = wrapk(k1, N);
+                        const float c0 = __ldg(&ct[a * a + b * b + k2 * k2]);
+                        const float sc = par ? -c0 : c0;
+                        const float2 old = dst[idx];
+                        dst[idx] = make_float2(fmaf(x[k0].x, sc, old.x), fmaf(x[k0].y, sc, old.y));
+                    }
+                }
+            }
+        }
+        cluster.sync();      // the peer has finished reading these planes
+    }
+}
+
 // ------------------------------------------------------------------ output
 // Gain field of every slot (complex-to-real of Qhat+ with all modes, Nyquist
 // included) minus the loss f_N(l) * Lambda(j), written for every ordered pair
@@ -369,8 +594,10 @@ __global__ void __launch_bounds__(Geo<N, D>::TPF * FPC) k_output(OutParams P) {
 //   TRI  (TJ = TL = T): all (j0+a, j0+b), a <= b   -> slot0 + a*T - a(a-1)/2 + (b-a)
 //   FULL (TJ x TL)    : all (j0+a, l0+b)           -> slot0 + a*TL + b
 //   LIST (T = 16)     : (ja[t], lb[t]) for t < count -> slot0 + t
-// One thread per voxel; the TJ + TL field values of a direction are loaded
-// once and reused by every slot of the tile (a register-blocked outer product).
+// The direction sum runs over antipodal pairs (p, p'): with c = A_p', a = w A_p
+// (w_p = w_p'), the two terms of a pair are a_j c_l + c_j a_l, so every field
+// value loaded serves both directions of the pair.  One thread per voxel; the
+// loads of the next pair are issued before the FMAs of the current one.
 enum { TILE_TRI = 0, TILE_FULL = 1, TILE_LIST = 2 };
 
 struct Tile {
@@ -382,12 +609,12 @@ struct Tile {
 };
 
 struct ConParams {
-    const float* A;       // [nq][M][n_c][n]
-    float* P;             // [nq][U][n]
+    const float* A;        // [nq][M][n_c][n]
+    float* P;              // [nq][U][n]
     const Tile* tiles;
-    const float* w;       // [M]
-    const int* anti;      // [M]
-    int M, n_c, U, n;
+    const float* w;        // [M/2] weight of each antipodal direction pair
+    const int2* dpair;     // [M/2] (p, antipode(p)) with p < antipode(p)
+    int n_dpair, M, n_c, U, n;
 };
 
 template <int KIND, int TJ, int TL>
@@ -396,51 +623,73 @@ __global__ void __launch_bounds__(256) k_contract(ConParams C) {
     if (v >= C.n) return;
     const Tile& tl = C.tiles[blockIdx.y];
     const size_t n = (size_t)C.n;
-    const float* __restrict__ Aq = C.A + (size_t)blockIdx.z * C.M * C.n_c * n + v;
+    const size_t fstride = (size_t)C.n_c * n;    // between directions
+    const float* __restrict__ Aq = C.A + (size_t)blockIdx.z * C.M * fstride + v;
     constexpr int NACC = (KIND == TILE_TRI) ? TJ * (TJ + 1) / 2 : (KIND == TILE_FULL ? TJ * TL : TJ);
+    // rows read per direction: TRI: TJ; FULL: TJ + TL; LIST: 2*TJ
+    constexpr int NR = (KIND == TILE_TRI) ? TJ : (KIND == TILE_FULL ? TJ + TL : 2 * TJ);
     float acc[NACC];
 #pragma unroll
     for (int i = 0; i < NACC; ++i) acc[i] = 0.f;
-    if (KIND == TILE_LIST) {
-        int ja[TJ], lb[TJ];
+    int roff[NR];                                // row offsets (in units of n) within a direction
 #pragma unroll
-        for (int t = 0; t < TJ; ++t) {
-            ja[t] = tl.ja[t];
-            lb[t] = tl.lb[t];
+    for (int t = 0; t < NR; ++t) {
+        if (KIND == TILE_TRI) roff[t] = tl.j0 + t;
+        else if (KIND == TILE_FULL) roff[t] = t < TJ ? tl.j0 + t : tl.l0 + (t - TJ);
+        else roff[t] = t < TJ ? tl.ja[t] : tl.lb[t - TJ];
+    }
+    float xp[NR], xq[NR];                        // A_p and A_p' rows of the current pair
+    {
+        const int2 d = __ldg(&C.dpair[0]);
+        const float* Ap = Aq + (size_t)d.x * fstride;
+        const float* Ab = Aq + (size_t)d.y * fstride;
+#pragma unroll
+        for (int t = 0; t < NR; ++t) {
+            xp[t] = __ldg(&Ap[(size_t)roff[t] * n]);
+            xq[t] = __ldg(&Ab[(size_t)roff[t] * n]);
         }
-        for (int p = 0; p < C.M; ++p) {
-            const float wp = __ldg(&C.w[p]);
-            const float* __restrict__ Ap = Aq + (size_t)p * C.n_c * n;
-            const float* __restrict__ Ab = Aq + (size_t)__ldg(&C.anti[p]) * C.n_c * n;
+    }
+#pragma unroll 1
+    for (int k = 0; k < C.n_dpair; ++k) {
+        const float wk = __ldg(&C.w[k]);
+        float np_[NR], nq_[NR];
+        const bool more = k + 1 < C.n_dpair;
+        if (more) {
+            const int2 d = __ldg(&C.dpair[k + 1]);
+            const float* Ap = Aq + (size_t)d.x * fstride;
+            const float* Ab = Aq + (size_t)d.y * fstride;
 #pragma unroll
-            for (int t = 0; t < TJ; ++t)
-                acc[t] = fmaf(wp * __ldg(&Ap[(size_t)ja[t] * n]), __ldg(&Ab[(size_t)lb[t] * n]), acc[t]);
+            for (int t = 0; t < NR; ++t) {
+                np_[t] = __ldg(&Ap[(size_t)roff[t] * n]);
+                nq_[t] = __ldg(&Ab[(size_t)roff[t] * n]);
+            }
         }
-    } else {
-        const int j0 = tl.j0, l0 = (KIND == TILE_TRI) ? tl.j0 : tl.l0;
-        for (int p = 0; p < C.M; ++p) {
-            const float wp = __ldg(&C.w[p]);
-            const float* __restrict__ Ap = Aq + ((size_t)p * C.n_c + j0) * n;
-            const float* __restrict__ Ab = Aq + ((size_t)__ldg(&C.anti[p]) * C.n_c + l0) * n;
-            float a[TJ], b[TL];
 #pragma unroll
-            for (int t = 0; t < TJ; ++t) a[t] = wp * __ldg(&Ap[t * n]);
+        for (int t = 0; t < NR; ++t) xp[t] *= wk;             // a = w A_p ; c = A_p' (xq)
+        if (KIND == TILE_TRI) {
+            int i = 0;
 #pragma unroll
-            for (int t = 0; t < TL; ++t) b[t] = __ldg(&Ab[t * n]);
-            if (KIND == TILE_TRI) {
-                int i = 0;
+            for (int x = 0; x < TJ; ++x)
 #pragma unroll
-                for (int x = 0; x < TJ; ++x)
+                for (int y = x; y < TJ; ++y) {
+                    acc[i] = fmaf(xp[x], xq[y], fmaf(xq[x], xp[y], acc[i]));
+                    ++i;
+                }
+        } else if (KIND == TILE_FULL) {
 #pragma unroll
-                    for (int y = x; y < TJ; ++y) {
-                        acc[i] = fmaf(a[x], b[y], acc[i]);
-                        ++i;
-                    }
-            } else {
+            for (int x = 0; x < TJ; ++x)
 #pragma unroll
-                for (int x = 0; x < TJ; ++x)
+                for (int y = 0; y < TL; ++y)
+                    acc[x * TL + y] = fmaf(xp[x], xq[TJ + y], fmaf(xq[x], xp[TJ + y], acc[x * TL + y]));
+        } else {
 #pragma unroll
-                    for (int y = 0; y < TL; ++y) acc[x * TL + y] = fmaf(a[x], b[y], acc[x * TL + y]);
+            for (int t = 0; t < TJ; ++t) acc[t] = fmaf(xp[t], xq[TJ + t], fmaf(xq[t], xp[TJ + t], acc[t]));
+        }
+        if (more) {
+#pragma unroll
+            for (int t = 0; t < NR; ++t) {
+                xp[t] = np_[t];
+                xq[t] = nq_[t];
             }
         }
     }
