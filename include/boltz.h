@@ -225,6 +225,25 @@ boltz_status boltz_host_quadrature(int d_v, int N_rho, int M, double R, double* 
 boltz_status boltz_workspace_size(boltz_grid g, int n_inputs, const int32_t* pair_j,
                                   const int32_t* pair_l, int n_pairs, int form, size_t* bytes);
 
+/*
+ * Waits for the work queued on `stream` and reports device-detected errors
+ * since the last check, then clears them: BOLTZ_ETIMEOUT if a bounded device
+ * wait (an asynchronous-copy barrier) gave up, which leaves the affected
+ * results invalid; BOLTZ_ECUDA if a CUDA call failed.  Kernels never trap or
+ * spin without a limit; this call is how their failures surface.
+ */
+boltz_status boltz_sync_status(boltz_grid g, void* stream);
+
+/*
+ * Failure-path self-test (not part of the paper's method).  which = 0 runs a
+ * one-CTA kernel whose asynchronous-copy barrier is never completed; its
+ * bounded wait gives up after about one second, records the timeout and
+ * returns, and this call then returns what boltz_sync_status reports:
+ * BOLTZ_ETIMEOUT when the failure path works.  The device stays usable.
+ * Errors: BOLTZ_EINVAL (NULL grid, unknown `which`), BOLTZ_ECUDA.
+ */
+boltz_status boltz_selftest(boltz_grid g, int which, void* stream);
+
 /* Kernel classes reported by boltz_profile_read. */
 typedef enum {
     BOLTZ_KCLASS_SPECTRUM = 0,  /* input spectra (forward real transforms)                  */

@@ -30,7 +30,7 @@ EXPORTED = (
     "boltz_abi_version", "boltz_status_string", "boltz_grid_init", "boltz_grid_destroy",
     "boltz_spectrum", "boltz_collide_batched", "boltz_project", "boltz_lowrank_step_host",
     "boltz_host_quadrature", "boltz_workspace_size", "boltz_profile_enable", "boltz_profile_read",
-    "boltz_project_noalloc",
+    "boltz_project_noalloc", "boltz_sync_status", "boltz_selftest",
 )
 
 KERNEL_CLASSES = ("spectrum", "prep", "shift", "contract", "radial", "output", "project")
@@ -68,6 +68,8 @@ def _load() -> ctypes.CDLL:
         "boltz_workspace_size": ([vp, ctypes.c_int, i32p, i32p, ctypes.c_int, ctypes.c_int,
                                   ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
         "boltz_profile_enable": ([vp, ctypes.c_int], ctypes.c_int),
+        "boltz_sync_status": ([vp, vp], ctypes.c_int),
+        "boltz_selftest": ([vp, ctypes.c_int, vp], ctypes.c_int),
         "boltz_project_noalloc": ([vp, vp, ctypes.c_int, vp, vp, vp], ctypes.c_int),
         "boltz_profile_read": ([vp, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
                                 ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
@@ -258,6 +260,16 @@ def boltz_workspace_size(grid: Grid, n_inputs: int, pair_j, pair_l, form: int = 
     _check(_lib.boltz_workspace_size(grid.handle, n_inputs, pj.ctypes.data_as(i32p), pl.ctypes.data_as(i32p),
                                      len(pj), int(form), ctypes.byref(out)), "boltz_workspace_size")
     return out.value
+
+
+def boltz_sync_status(grid: Grid, stream=None):
+    """Wait for the stream and raise if a kernel reported a device error (e.g. a timed-out wait)."""
+    _check(_lib.boltz_sync_status(grid.handle, _stream_ptr(stream)), "boltz_sync_status")
+
+
+def boltz_selftest(grid: Grid, which: int = 0, stream=None) -> int:
+    """Run a failure-path self-test; returns the raw status (BOLTZ_ETIMEOUT expected for which=0)."""
+    return _lib.boltz_selftest(grid.handle, int(which), _stream_ptr(stream))
 
 
 def boltz_profile_enable(grid: Grid, enable: bool = True):

@@ -73,6 +73,7 @@ struct boltz_grid_s {
     float* d_gm = nullptr;       // [smax+1]
     float* d_w = nullptr;        // [M/2] weight of each antipodal direction pair
     int2* d_dpair = nullptr;     // [M/2] (p, antipode(p)), p < antipode(p)
+    int* d_err = nullptr;        // device error word (bit kErrTimeout: a bounded wait gave up)
     // workspace
     char* d_ws = nullptr;
     size_t ws_cap = 0, ws_max = kDefaultWorkspace;
@@ -81,6 +82,10 @@ struct boltz_grid_s {
     int last_form = -1, last_n_inputs = -1;
     Plan last_plan;
     bool plan_uploaded = false;
+    // side stream for the radial step and the events of the two-buffer pipeline
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_ready[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr}, ev_join = nullptr,
+                ev_fork = nullptr;
     // profiling: launches per kernel class (always counted) and, when enabled,
     // an event pair around every launch on the launching stream
     bool prof_on = false;
@@ -281,8 +286,8 @@ boltz_status build_plan(const boltz_grid_s* g, int n_inputs, const int32_t* pj, 
     plan.off_plan = 0;
     plan.off_A = w;
     w = align_up(w + size_t(plan.nq) * g->M * plan.max_nc * field_bytes, 256);
-    plan.off_P = w;
-    w = align_up(w + size_t(plan.nq) * plan.max_U * field_bytes, 256);
+    plan.off_P = w;       // two buffers: the radial step of one node block overlaps the next block
+    w = align_up(w + 2 * size_t(plan.nq) * plan.max_U * field_bytes, 256);
     plan.off_qhat = w;
     w = align_up(w + size_t(plan.max_U) * g->half * 8, 256);
     plan.off_fN = w;
@@ -455,17 +460,54 @@ const Dispatch* dispatch_for(int N, int D) {
     return N == 8 ? &d2_8 : N == 16 ? &d2_16 : N == 32 ? &d2_32 : N == 64 ? &d2_64 : nullptr;
 }
 
-void launch_contract(int kind, int T, const ConParams& cp, int n_tiles, int nq, cudaStream_t st) {
-    dim3 grid((cp.n + 255) / 256, n_tiles, nq);
-    if (kind == TILE_TRI) {
-        if (T == 16) k_contract<TILE_TRI, 16, 16><<<grid, 256, 0, st>>>(cp);
-        else k_contract<TILE_TRI, 8, 8><<<grid, 256, 0, st>>>(cp);
-    } else if (kind == TILE_FULL) {
-        if (T == 16) k_contract<TILE_FULL, 8, 16><<<grid, 256, 0, st>>>(cp);
-        else k_contract<TILE_FULL, 8, 8><<<grid, 256, 0, st>>>(cp);
-    } else {
-        k_contract<TILE_LIST, 16, 16><<<grid, 256, 0, st>>>(cp);
+// Pipelined contraction: VC voxels per CTA, ring of STAGES bulk-copy stages
+// sized to stay within 192 KB of shared memory.
+template <int KIND, int TJ, int TL, int VC>
+struct ContractLaunch {
+    static constexpr int ROWS = ContractShape<KIND, TJ, TL>::ROWS;
+    static constexpr int STAGES = (ROWS * VC * 4 * 4 <= (192 << 10)) ? 4 : 3;
+    static constexpr size_t SMEM = size_t(STAGES) * ROWS * VC * sizeof(float);
+    static cudaError_t prepare() { return set_smem(k_contract_pipe<KIND, TJ, TL, VC, STAGES>, SMEM); }
+    static void launch(const ConParams& cp, int n_tiles, int nq, cudaStream_t st) {
+        dim3 grid(cp.n / VC, n_tiles, nq);      // one CTA per voxel chunk of the field layout
+        k_contract_pipe<KIND, TJ, TL, VC, STAGES><<<grid, VC, SMEM, st>>>(cp);
     }
+};
+
+template <int VC>
+cudaError_t prepare_contract_vc() {
+    cudaError_t e;
+    if ((e = ContractLaunch<TILE_TRI, 16, 16, VC>::prepare()) != cudaSuccess) return e;
+    if ((e = ContractLaunch<TILE_TRI, 8, 8, VC>::prepare()) != cudaSuccess) return e;
+    if ((e = ContractLaunch<TILE_FULL, 8, 16, VC>::prepare()) != cudaSuccess) return e;
+    if ((e = ContractLaunch<TILE_FULL, 8, 8, VC>::prepare()) != cudaSuccess) return e;
+    return ContractLaunch<TILE_LIST, 16, 16, VC>::prepare();
+}
+
+cudaError_t prepare_contract() {
+    cudaError_t e;
+    if ((e = prepare_contract_vc<256>()) != cudaSuccess) return e;
+    return prepare_contract_vc<64>();
+}
+
+template <int VC>
+void launch_contract_vc(int kind, int T, const ConParams& cp, int n_tiles, int nq, cudaStream_t st) {
+    if (kind == TILE_TRI) {
+        if (T == 16) ContractLaunch<TILE_TRI, 16, 16, VC>::launch(cp, n_tiles, nq, st);
+        else ContractLaunch<TILE_TRI, 8, 8, VC>::launch(cp, n_tiles, nq, st);
+    } else if (kind == TILE_FULL) {
+        if (T == 16) ContractLaunch<TILE_FULL, 8, 16, VC>::launch(cp, n_tiles, nq, st);
+        else ContractLaunch<TILE_FULL, 8, 8, VC>::launch(cp, n_tiles, nq, st);
+    } else {
+        ContractLaunch<TILE_LIST, 16, 16, VC>::launch(cp, n_tiles, nq, st);
+    }
+}
+
+// n is a power of two >= 64 for every supported grid; VC equals the voxel
+// chunk of the shifted-field layout, min(256, n)
+void launch_contract(int kind, int T, const ConParams& cp, int n_tiles, int nq, cudaStream_t st) {
+    if (cp.n >= 256) launch_contract_vc<256>(kind, T, cp, n_tiles, nq, st);
+    else launch_contract_vc<64>(kind, T, cp, n_tiles, nq, st);
 }
 
 boltz_status check_pairs(int n_inputs, const int32_t* pj, const int32_t* pl, int n_pairs) {
@@ -525,8 +567,17 @@ boltz_status run_batched(boltz_grid_s* g, const float2* spectra, int n_inputs, c
         }
         const float* lam_c = fN + size_t(nc) * g->n;
         BZ_CUDA(cudaMemsetAsync(qhat, 0, size_t(c.U) * g->half * sizeof(float2), st));
-        for (int q0 = 0; q0 < g->n_rho; q0 += plan.nq) {
+        // Node blocks run synth -> contract on the caller's stream and the radial
+        // step on the side stream, with P double-buffered: the radial step of
+        // block i overlaps synth/contract of block i+1.
+        BZ_CUDA(cudaEventRecord(g->ev_fork, st));
+        BZ_CUDA(cudaStreamWaitEvent(g->side, g->ev_fork, 0));
+        const size_t pbuf_floats = size_t(plan.nq) * plan.max_U * g->n;
+        int blk = 0;
+        for (int q0 = 0; q0 < g->n_rho; q0 += plan.nq, ++blk) {
             const int nq = std::min(plan.nq, g->n_rho - q0);
+            const int b = blk & 1;
+            float* Pb = Pbuf + b * pbuf_floats;
             SynParams ss = sp;
             ss.out = A;
             ss.q0 = q0;
@@ -535,11 +586,13 @@ boltz_status run_batched(boltz_grid_s* g, const float2* spectra, int n_inputs, c
                 ProfScope ps(g, BOLTZ_KCLASS_SHIFT, st);
                 dp->synth(ss, SYN_SHIFT, st);
             }
+            if (blk >= 2) BZ_CUDA(cudaStreamWaitEvent(st, g->ev_free[b], 0));
             ConParams cp{};
             cp.A = A;
-            cp.P = Pbuf;
+            cp.P = Pb;
             cp.w = g->d_w;
             cp.dpair = g->d_dpair;
+            cp.err = g->d_err;
             cp.n_dpair = g->M / 2;
             cp.M = g->M;
             cp.n_c = nc;
@@ -551,17 +604,24 @@ boltz_status run_batched(boltz_grid_s* g, const float2* spectra, int n_inputs, c
                 ProfScope ps(g, BOLTZ_KCLASS_CONTRACT, st);
                 launch_contract(k, k == TILE_LIST ? 16 : c.tile_T, cp, (int)c.tiles[k].size(), nq, st);
             }
+            BZ_CUDA(cudaEventRecord(g->ev_ready[b], st));
+            BZ_CUDA(cudaStreamWaitEvent(g->side, g->ev_ready[b], 0));
             AnaParams ap{};
-            ap.in = Pbuf;
+            ap.in = Pb;
             ap.out = qhat;
             ap.ctab = g->d_ctab;
             ap.n_fields = c.U;
             ap.nq = nq;
             ap.q0 = q0;
             ap.U = c.U;
-            ProfScope ps(g, BOLTZ_KCLASS_RADIAL, st);
-            dp->analysis(ap, ANA_ACCUM, st);
+            {
+                ProfScope ps(g, BOLTZ_KCLASS_RADIAL, g->side);
+                dp->analysis(ap, ANA_ACCUM, g->side);
+            }
+            BZ_CUDA(cudaEventRecord(g->ev_free[b], g->side));
         }
+        BZ_CUDA(cudaEventRecord(g->ev_join, g->side));
+        BZ_CUDA(cudaStreamWaitEvent(st, g->ev_join, 0));
         OutParams op{};
         op.qhat = qhat;
         op.fN = fN;
@@ -784,7 +844,8 @@ boltz_status boltz_grid_init(boltz_grid* out, int N, int d_v, double L, double R
         cudaMalloc(&g->d_ctab, ctab.size() * sizeof(float)) != cudaSuccess ||
         cudaMalloc(&g->d_gm, gm.size() * sizeof(float)) != cudaSuccess ||
         cudaMalloc(&g->d_w, n_dp * sizeof(float)) != cudaSuccess ||
-        cudaMalloc(&g->d_dpair, n_dp * sizeof(int2)) != cudaSuccess) {
+        cudaMalloc(&g->d_dpair, n_dp * sizeof(int2)) != cudaSuccess ||
+        cudaMalloc(&g->d_err, sizeof(int)) != cudaSuccess) {
         (void)cudaGetLastError();
         return fail(BOLTZ_ENOMEM);
     }
@@ -792,9 +853,19 @@ boltz_status boltz_grid_init(boltz_grid* out, int N, int d_v, double L, double R
         cudaMemcpy(g->d_ctab, ctab.data(), ctab.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(g->d_gm, gm.data(), gm.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(g->d_w, wdir.data(), n_dp * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(g->d_dpair, dpair.data(), n_dp * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess)
+        cudaMemcpy(g->d_dpair, dpair.data(), n_dp * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(g->d_err, 0, sizeof(int)) != cudaSuccess)
         return fail(BOLTZ_ECUDA);
-    if (dispatch_for(N, d_v)->prepare() != cudaSuccess) return fail(BOLTZ_ECUDA);
+    if (dispatch_for(N, d_v)->prepare() != cudaSuccess || prepare_contract() != cudaSuccess)
+        return fail(BOLTZ_ECUDA);
+    if (cudaStreamCreateWithFlags(&g->side, cudaStreamNonBlocking) != cudaSuccess) return fail(BOLTZ_ECUDA);
+    for (int b = 0; b < 2; ++b)
+        if (cudaEventCreateWithFlags(&g->ev_ready[b], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&g->ev_free[b], cudaEventDisableTiming) != cudaSuccess)
+            return fail(BOLTZ_ECUDA);
+    if (cudaEventCreateWithFlags(&g->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming) != cudaSuccess)
+        return fail(BOLTZ_ECUDA);
     *out = g;
     return BOLTZ_OK;
 }
@@ -807,11 +878,19 @@ boltz_status boltz_grid_destroy(boltz_grid g) {
         cudaEventDestroy(pe.second.second);
     }
     for (auto e : g->event_pool) cudaEventDestroy(e);
+    for (int b = 0; b < 2; ++b) {
+        if (g->ev_ready[b]) cudaEventDestroy(g->ev_ready[b]);
+        if (g->ev_free[b]) cudaEventDestroy(g->ev_free[b]);
+    }
+    if (g->ev_join) cudaEventDestroy(g->ev_join);
+    if (g->ev_fork) cudaEventDestroy(g->ev_fork);
+    if (g->side) cudaStreamDestroy(g->side);
     cudaFree(g->d_phase);
     cudaFree(g->d_ctab);
     cudaFree(g->d_gm);
     cudaFree(g->d_w);
     cudaFree(g->d_dpair);
+    cudaFree(g->d_err);
     cudaFree(g->d_ws);
     delete g;
     return BOLTZ_OK;
@@ -939,6 +1018,26 @@ boltz_status boltz_lowrank_step_host(boltz_grid g, const float* V_host, int r, f
     BZ_CUDA(cudaMemcpyAsync(T_host, dT, size_t(r) * r2 * 4, cudaMemcpyDeviceToHost, st));
     BZ_CUDA(cudaStreamSynchronize(st));
     return BOLTZ_OK;
+}
+
+boltz_status boltz_sync_status(boltz_grid g, void* stream) {
+    if (!g) return BOLTZ_EINVAL;
+    BZ_CUDA(cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)));
+    int err = 0;
+    BZ_CUDA(cudaMemcpy(&err, g->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err) {
+        BZ_CUDA(cudaMemset(g->d_err, 0, sizeof(int)));
+        return (err & kErrTimeout) ? BOLTZ_ETIMEOUT : BOLTZ_ECUDA;
+    }
+    return BOLTZ_OK;
+}
+
+boltz_status boltz_selftest(boltz_grid g, int which, void* stream) {
+    if (!g || which != 0) return BOLTZ_EINVAL;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    k_selftest_wait_timeout<<<1, 32, 0, st>>>(g->d_err);
+    BZ_CUDA(cudaGetLastError());
+    return boltz_sync_status(g, stream);
 }
 
 boltz_status boltz_profile_enable(boltz_grid g, int enable) {

@@ -21,6 +21,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "async.cuh"
 #include "fft.cuh"
 
 namespace boltz_dev {
@@ -36,7 +37,21 @@ struct Geo {
     static constexpr int SMEM_F = (D == 3) ? N * N * RS : N * RS;
     static constexpr int COLS = (D == 3) ? N * NH : NH;          // columns incl. the half-axis Nyquist
     static constexpr int SMAX = D * H * H;                       // largest |k|^2
+    // shifted fields are stored voxel-chunk-major (see shifted_field_row)
+    static constexpr int VCH = n < 256 ? n : 256;                // voxels per chunk
+    static constexpr int NCH = n / VCH;                          // chunks per field
 };
+
+// Layout of the shifted-field buffer: for slot s = qq*M + p (node in the
+// block, direction) and chunk-local input jj, voxel v of the field is stored at
+//   out[((s * NCH + v / VCH) * n_c + jj) * VCH + v % VCH],
+// so the rows of all inputs of one (slot, voxel chunk) are one contiguous
+// block that the contraction fetches with a single bulk copy.
+template <int N, int D>
+__device__ __forceinline__ float* shifted_field_row(float* out, int slot, int jj, int n_c, int v) {
+    using G = Geo<N, D>;
+    return out + (((size_t)slot * G::NCH + v / G::VCH) * n_c + jj) * G::VCH + (v % G::VCH);
+}
 
 __device__ __forceinline__ int wrapk(int i, int N) { return i < N / 2 ? i : i - N; }
 
@@ -80,7 +95,11 @@ __global__ void __launch_bounds__(Geo<N, D>::TPF * FPC) k_synth(SynParams P) {
     }
     const float2* __restrict__ src = P.spectra + (size_t)input * G::half;
     const float2* __restrict__ ph = P.phase + (size_t)node * D * N;
-    float* __restrict__ dst = P.out + (size_t)f * G::n;
+    // start of row r of this field in the output (rows never straddle a voxel chunk)
+    auto row_ptr = [&](int r) -> float* {
+        if (MODE == SYN_SHIFT) return shifted_field_row<N, D>(P.out, f / P.n_c, f % P.n_c, P.n_c, r * N);
+        return P.out + (size_t)f * G::n + (size_t)r * N;
+    };
     float2 x[N];
 
     if (D == 3) {
@@ -126,8 +145,8 @@ __global__ void __launch_bounds__(Geo<N, D>::TPF * FPC) k_synth(SynParams P) {
                 x[N - k] = make_float2(a.x + b.y, b.x - a.y);
             }
             fft_reg<N, true>(x);
-            float4* o1 = reinterpret_cast<float4*>(dst + (i0 * N + i1) * N);
-            float4* o2 = reinterpret_cast<float4*>(dst + (i0 * N + i1 + H) * N);
+            float4* o1 = reinterpret_cast<float4*>(row_ptr(i0 * N + i1));
+            float4* o2 = reinterpret_cast<float4*>(row_ptr(i0 * N + i1 + H));
 #pragma unroll
             for (int c = 0; c < N / 4; ++c) {
                 o1[c] = make_float4(x[4 * c].x, x[4 * c + 1].x, x[4 * c + 2].x, x[4 * c + 3].x);
@@ -167,8 +186,8 @@ __global__ void __launch_bounds__(Geo<N, D>::TPF * FPC) k_synth(SynParams P) {
                 x[N - k] = make_float2(a.x + b.y, b.x - a.y);
             }
             fft_reg<N, true>(x);
-            float4* o1 = reinterpret_cast<float4*>(dst + i0 * N);
-            float4* o2 = reinterpret_cast<float4*>(dst + (i0 + H) * N);
+            float4* o1 = reinterpret_cast<float4*>(row_ptr(i0));
+            float4* o2 = reinterpret_cast<float4*>(row_ptr(i0 + H));
 #pragma unroll
             for (int c = 0; c < N / 4; ++c) {
                 o1[c] = make_float4(x[4 * c].x, x[4 * c + 1].x, x[4 * c + 2].x, x[4 * c + 3].x);
@@ -332,7 +351,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__((N / 2) * (N / 2), 3
         }
     }
     const float2* __restrict__ src = P.spectra + (size_t)input * G::half;
-    float* __restrict__ dst = P.out + (size_t)f * G::n + (size_t)rank * PG::HALF_N;
     for (int i = lt; i < 3 * N; i += NT) phs[i] = __ldg(&P.phase[(size_t)node * 3 * N + i]);
     __syncthreads();
     float2 x[N];
@@ -394,10 +412,28 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__((N / 2) * (N / 2), 3
     }
     __syncthreads();
     if (active) {
-        float2* out2 = reinterpret_cast<float2*>(dst);
-#pragma unroll 4
-        for (int L = 2 * lt; L < PG::HALF_N; L += 2 * NT)
-            out2[L >> 1] = *reinterpret_cast<const float2*>(stg + (L / N) * RR + (L % N));
+        // Thread lt moves floats L = 2 lt + 2 NT it (it = 0, 1, ...): each warp moves 256
+        // contiguous bytes, which never straddle a voxel chunk.  One step of `it` advances
+        // the staged row by 2NT/N and the voxel by 2NT (a whole number of chunks), so both
+        // addresses advance by constants.
+        static_assert((2 * NT) % N == 0 && (2 * NT) % G::VCH == 0, "copy-out strides");
+        constexpr int ITER = PG::HALF_N / (2 * NT);
+        const int L0 = 2 * lt;
+        const float* sp = stg + (L0 / N) * RR + (L0 % N);
+        constexpr int S_STEP = (2 * NT / N) * RR;
+        const int v0 = rank * PG::HALF_N + L0;
+        float* op;
+        size_t o_step;
+        if (MODE == SYN_SHIFT) {
+            op = shifted_field_row<N, 3>(P.out, f / P.n_c, f % P.n_c, P.n_c, v0);
+            o_step = (size_t)(2 * NT / G::VCH) * P.n_c * G::VCH;
+        } else {
+            op = P.out + (size_t)f * G::n + v0;
+            o_step = 2 * NT;
+        }
+#pragma unroll 8
+        for (int it = 0; it < ITER; ++it)
+            *reinterpret_cast<float2*>(op + it * o_step) = *reinterpret_cast<const float2*>(sp + it * S_STEP);
     }
 }
 
@@ -428,10 +464,15 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__((N / 2) * (N / 2), 2
         const float* __restrict__ ct = P.ctab + (size_t)(P.q0 + qq) * (G::SMAX + 1);
         // stage this CTA's half of the real field (coalesced), then R2C along the last axis
         if (active) {
-            const float2* in2 = reinterpret_cast<const float2*>(src);
-#pragma unroll 4
-            for (int L = 2 * lt; L < PG::HALF_N; L += 2 * NT)
-                *reinterpret_cast<float2*>(stg + (L / N) * RR + (L % N)) = __ldg(&in2[L >> 1]);
+            // coalesced: thread lt moves floats 2 lt + 2 NT it; constant strides in both spaces
+            constexpr int ITER = PG::HALF_N / (2 * NT);
+            constexpr int S_STEP = (2 * NT / N) * RR;
+            const int L0 = 2 * lt;
+            const float2* in2 = reinterpret_cast<const float2*>(src + L0);
+            float* sp = stg + (L0 / N) * RR + (L0 % N);
+#pragma unroll 8
+            for (int it = 0; it < ITER; ++it)
+                *reinterpret_cast<float2*>(sp + it * S_STEP) = __ldg(in2 + it * NT);
         }
         __syncthreads();
         const int i0 = lt / H, i1 = lt % H;
@@ -596,8 +637,7 @@ __global__ void __launch_bounds__(Geo<N, D>::TPF * FPC) k_output(OutParams P) {
 //   LIST (T = 16)     : (ja[t], lb[t]) for t < count -> slot0 + t
 // The direction sum runs over antipodal pairs (p, p'): with c = A_p', a = w A_p
 // (w_p = w_p'), the two terms of a pair are a_j c_l + c_j a_l, so every field
-// value loaded serves both directions of the pair.  One thread per voxel; the
-// loads of the next pair are issued before the FMAs of the current one.
+// value loaded serves both directions of the pair.
 enum { TILE_TRI = 0, TILE_FULL = 1, TILE_LIST = 2 };
 
 struct Tile {
@@ -614,58 +654,90 @@ struct ConParams {
     const Tile* tiles;
     const float* w;        // [M/2] weight of each antipodal direction pair
     const int2* dpair;     // [M/2] (p, antipode(p)) with p < antipode(p)
+    int* err;              // device error word
     int n_dpair, M, n_c, U, n;
 };
 
+// A CTA owns VC consecutive voxels (one per thread); for
+// every antipodal pair one warp issues 1-D bulk copies of the 2 x NR field
+// rows (VC floats each) into a ring of shared-memory stages, and all threads
+// read their voxel's column from shared memory.  The copies of STAGES pairs
+// are in flight while the FMAs of the current pair run.
 template <int KIND, int TJ, int TL>
-__global__ void __launch_bounds__(256) k_contract(ConParams C) {
-    const int v = blockIdx.x * 256 + threadIdx.x;
-    if (v >= C.n) return;
+struct ContractShape {
+    static constexpr int NR = (KIND == TILE_TRI) ? TJ : (KIND == TILE_FULL ? TJ + TL : 2 * TJ);
+    static constexpr int ROWS = 2 * NR;                           // A_p rows then A_p' rows
+    static constexpr int NACC = (KIND == TILE_TRI) ? TJ * (TJ + 1) / 2 : (KIND == TILE_FULL ? TJ * TL : TJ);
+};
+
+template <int KIND, int TJ, int TL, int VC, int STAGES>
+__global__ void __launch_bounds__(VC, 1) k_contract_pipe(ConParams C) {
+    using CS = ContractShape<KIND, TJ, TL>;
+    constexpr int NR = CS::NR, ROWS = CS::ROWS, NACC = CS::NACC;
+    constexpr uint32_t STAGE_BYTES = ROWS * VC * sizeof(float);
+    extern __shared__ __align__(128) float sbuf[];                // [STAGES][ROWS][VC]
+    __shared__ uint64_t bars[STAGES];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const Tile& tl = C.tiles[blockIdx.y];
-    const size_t n = (size_t)C.n;
-    const size_t fstride = (size_t)C.n_c * n;    // between directions
-    const float* __restrict__ Aq = C.A + (size_t)blockIdx.z * C.M * fstride + v;
-    constexpr int NACC = (KIND == TILE_TRI) ? TJ * (TJ + 1) / 2 : (KIND == TILE_FULL ? TJ * TL : TJ);
-    // rows read per direction: TRI: TJ; FULL: TJ + TL; LIST: 2*TJ
-    constexpr int NR = (KIND == TILE_TRI) ? TJ : (KIND == TILE_FULL ? TJ + TL : 2 * TJ);
+    const int nch = C.n / VC;                                     // VC is the layout's voxel chunk
+    const size_t blk = (size_t)C.n_c * VC;                        // one (slot, chunk) block
+    // block of (slot = qq*M + p, chunk = blockIdx.x)
+    auto block_of = [&](int p) -> const float* {
+        return C.A + (((size_t)blockIdx.z * C.M + p) * nch + blockIdx.x) * blk;
+    };
+    const int npairs = C.n_dpair;
+    if (t == 0) {
+        for (int s = 0; s < STAGES; ++s) mbar_init(&bars[s], 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    // rows of one direction: TRI j0..j0+TJ; FULL j0..j0+TJ then l0..l0+TL; LIST ja[], lb[]
+    auto issue = [&](int k) {                                     // warp 0 only
+        const int s = k % STAGES;
+        const int2 d = C.dpair[k];
+        float* dstp = sbuf + (size_t)s * ROWS * VC;
+        if (lane == 0) mbar_arrive_expect_tx(&bars[s], STAGE_BYTES);
+        __syncwarp();
+        if (KIND == TILE_LIST) {
+            for (int r = lane; r < ROWS; r += 32) {
+                const int i = r < NR ? r : r - NR;
+                const int row = i < TJ ? tl.ja[i] : tl.lb[i - TJ];
+                bulk_g2s(dstp + (size_t)r * VC, block_of(r < NR ? d.x : d.y) + (size_t)row * VC,
+                         VC * sizeof(float), &bars[s]);
+            }
+        } else if (lane < 2) {
+            const float* b = block_of(lane == 0 ? d.x : d.y);
+            float* o = dstp + (size_t)lane * NR * VC;
+            bulk_g2s(o, b + (size_t)tl.j0 * VC, TJ * VC * sizeof(float), &bars[s]);
+            if (KIND == TILE_FULL) bulk_g2s(o + TJ * VC, b + (size_t)tl.l0 * VC, TL * VC * sizeof(float), &bars[s]);
+        }
+    };
+    if (warp == 0)
+        for (int k = 0; k < STAGES && k < npairs; ++k) issue(k);
     float acc[NACC];
 #pragma unroll
     for (int i = 0; i < NACC; ++i) acc[i] = 0.f;
-    int roff[NR];                                // row offsets (in units of n) within a direction
-#pragma unroll
-    for (int t = 0; t < NR; ++t) {
-        if (KIND == TILE_TRI) roff[t] = tl.j0 + t;
-        else if (KIND == TILE_FULL) roff[t] = t < TJ ? tl.j0 + t : tl.l0 + (t - TJ);
-        else roff[t] = t < TJ ? tl.ja[t] : tl.lb[t - TJ];
-    }
-    float xp[NR], xq[NR];                        // A_p and A_p' rows of the current pair
-    {
-        const int2 d = __ldg(&C.dpair[0]);
-        const float* Ap = Aq + (size_t)d.x * fstride;
-        const float* Ab = Aq + (size_t)d.y * fstride;
-#pragma unroll
-        for (int t = 0; t < NR; ++t) {
-            xp[t] = __ldg(&Ap[(size_t)roff[t] * n]);
-            xq[t] = __ldg(&Ab[(size_t)roff[t] * n]);
-        }
-    }
-#pragma unroll 1
-    for (int k = 0; k < C.n_dpair; ++k) {
-        const float wk = __ldg(&C.w[k]);
-        float np_[NR], nq_[NR];
-        const bool more = k + 1 < C.n_dpair;
-        if (more) {
-            const int2 d = __ldg(&C.dpair[k + 1]);
-            const float* Ap = Aq + (size_t)d.x * fstride;
-            const float* Ab = Aq + (size_t)d.y * fstride;
-#pragma unroll
-            for (int t = 0; t < NR; ++t) {
-                np_[t] = __ldg(&Ap[(size_t)roff[t] * n]);
-                nq_[t] = __ldg(&Ab[(size_t)roff[t] * n]);
+    for (int k = 0; k < npairs; ++k) {
+        const int s = k % STAGES;
+        const bool ok = mbar_wait_bounded(&bars[s], (uint32_t)(k / STAGES) & 1u);
+        if (__syncthreads_or(!ok)) {
+            // a copy did not land: record it, wait (bounded) for the copies still in flight, leave
+            if (t == 0) {
+                atomicOr(C.err, kErrTimeout);
+                for (int k2 = k; k2 < npairs && k2 < k + STAGES; ++k2)
+                    (void)mbar_wait_bounded(&bars[k2 % STAGES], (uint32_t)(k2 / STAGES) & 1u);
             }
+            __syncthreads();
+            return;
         }
+        const float* __restrict__ xs = sbuf + (size_t)s * ROWS * VC + t;
+        const float wk = __ldg(&C.w[k]);
+        float xp[NR], xq[NR];
 #pragma unroll
-        for (int t = 0; t < NR; ++t) xp[t] *= wk;             // a = w A_p ; c = A_p' (xq)
+        for (int i = 0; i < NR; ++i) {
+            xp[i] = wk * xs[i * VC];
+            xq[i] = xs[(NR + i) * VC];
+        }
         if (KIND == TILE_TRI) {
             int i = 0;
 #pragma unroll
@@ -683,21 +755,36 @@ __global__ void __launch_bounds__(256) k_contract(ConParams C) {
                     acc[x * TL + y] = fmaf(xp[x], xq[TJ + y], fmaf(xq[x], xp[TJ + y], acc[x * TL + y]));
         } else {
 #pragma unroll
-            for (int t = 0; t < TJ; ++t) acc[t] = fmaf(xp[t], xq[TJ + t], fmaf(xq[t], xp[TJ + t], acc[t]));
+            for (int i = 0; i < TJ; ++i) acc[i] = fmaf(xp[i], xq[TJ + i], fmaf(xq[i], xp[TJ + i], acc[i]));
         }
-        if (more) {
-#pragma unroll
-            for (int t = 0; t < NR; ++t) {
-                xp[t] = np_[t];
-                xq[t] = nq_[t];
-            }
+        __syncthreads();                                          // stage s fully read
+        if (warp == 0 && k + STAGES < npairs) {
+            fence_proxy_async_smem();
+            issue(k + STAGES);
         }
     }
-    float* __restrict__ Pq = C.P + (size_t)blockIdx.z * C.U * n + v;
+    const size_t n = (size_t)C.n;
+    float* __restrict__ Pq = C.P + (size_t)blockIdx.z * C.U * n + (size_t)blockIdx.x * VC + t;
     const int cnt = (KIND == TILE_LIST) ? tl.count : NACC;
 #pragma unroll
     for (int i = 0; i < NACC; ++i)
         if (i < cnt) Pq[(size_t)(tl.slot0 + i) * n] = acc[i];
+}
+
+// ------------------------------------------------------------------ failure-path self-test
+// One CTA announces an incoming transfer on an mbarrier and never issues it:
+// the bounded wait runs out, the kernel records a timeout in the error word
+// and returns normally, leaving the context usable.
+__global__ void k_selftest_wait_timeout(int* err) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) mbar_arrive_expect_tx(&bar, 16);    // 16 bytes that never arrive
+    const bool ok = mbar_wait_bounded(&bar, 0);
+    if (__syncthreads_or(!ok) && threadIdx.x == 0) atomicOr(err, kErrTimeout);
 }
 
 // ------------------------------------------------------------------ projection

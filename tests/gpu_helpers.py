@@ -30,6 +30,7 @@ def gpu_collide(B, cfg, fields, pairs, form=0, return_T=False):
         pl = [p[1] for p in pairs]
         Q = B.boltz_collide_batched(g, spec, pj, pl, form=form)
         T = B.boltz_project(g, f, Q) if return_T else None
+        B.boltz_sync_status(g)
         torch.cuda.synchronize()
         out = Q.cpu().numpy().astype(np.float64)
         return (out, T.cpu().numpy().astype(np.float64)) if return_T else out

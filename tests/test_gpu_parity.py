@@ -136,6 +136,22 @@ def test_empty_batch_and_bad_indices(B):
         g.close()
 
 
+def test_bounded_wait_reports_timeout_and_context_survives(B):
+    """A barrier nothing completes: the kernel gives up after its wait limit,
+    the host reads BOLTZ_ETIMEOUT, and the next evaluation still succeeds."""
+    g = B.boltz_grid_init(8, 3, 8.0, 8.0, 1.0, 2, 6)
+    try:
+        assert B.boltz_selftest(g, 0) == B.BOLTZ_ETIMEOUT
+        B.boltz_sync_status(g)             # error word was cleared
+    finally:
+        g.close()
+    cfg = (8, 3, 8.0, 8.0, 1.0, 2, 6)
+    F = as_fp32(W.random_fields(8, 3, 8.0, 2, seed=1))
+    Qg = gpu_collide(B, cfg, F, [(0, 1)])
+    _, Qo, s = oracle_collide(cfg, F, [(0, 1)])
+    assert rel_err(Qg, Qo, s).max() < TOL
+
+
 def test_lowrank_step_host_matches_device_path(B):
     import torch
     cfg = (16, 3, 8.0, 8.0, 1.0, 6, 14)
