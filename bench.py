@@ -33,11 +33,13 @@ CONFIGS = {
     "c2": (32, 3, 8.0, 8.0, 1.0, 32, 38, "pairs", 16),
     "c3": (32, 3, 8.0, 8.0, 1.0, 32, 38, "cells", 512),
     "c1": (32, 2, 8.0, 8.0, 0.0, 16, 16, "bkw", 1),
+    "c4": (64, 3, 10.0, 10.0, 1.0, 32, 86, "pairs", 8),
 }
 WORKLOAD_NAMES = {
     "c2": "lowrank pair batch: 3D 32^3 on [-8,8]^3, gamma=1, R=8, N_rho=32 x M=38, rank 16 -> 256 pairs Q(V_j,V_l) + r^3 projection",
     "c3": "full-tensor-grid batch: 512 normal-shock cells (Mach 3, d=3), 3D 32^3, gamma=1, R=8, N_rho=32 x M=38",
     "c1": "single homogeneous Q(f,f): 2D 32^2 on [-8,8]^2, Maxwell molecules, R=8, N_rho=16 x M=16, BKW t0=0.5",
+    "c4": "precision-variant workload, FP32 path: 3D 64^3 on [-10,10]^3, gamma=1, R=10, N_rho=32 x M=86, rank 8 -> 64 pairs + r^3",
 }
 METRIC = "collision evals/s at 32^3 (batch 256) & % roofline; fast form vs plain FP32"
 L2_FLUSH_BYTES = 512 << 20
@@ -51,7 +53,7 @@ def make_inputs(cfg_name):
     from paper_2112_02695_gb300 import workloads as W
     N, d, L, R, gamma, n_rho, M, kind, size = CONFIGS[cfg_name]
     if kind == "pairs":
-        fields = W.hermite_maxwellian_basis(N, d, L, size, seed=2112)
+        fields = W.hermite_maxwellian_basis(N, d, L, size, seed=2113 if cfg_name == "c4" else 2112)
         pairs = [(j, l) for j in range(size) for l in range(size)]
     elif kind == "cells":
         fields, _ = W.shock_cells(N, d, L, n_cells=size)
@@ -149,7 +151,7 @@ def oracle_sample(cfg_name, r=4):
     fields, pairs = make_inputs(cfg_name)
     N, d, L, R, gamma, n_rho, M, kind, size = CONFIGS[cfg_name]
     if kind == "pairs":
-        return fields[:r], [(j, l) for j in range(r) for l in range(r)], f"rank-{r} subset: {r * r} of the 256 pairs"
+        return fields[:r], [(j, l) for j in range(r) for l in range(r)], f"rank-{r} subset: {r * r} of the {size * size} pairs"
     if kind == "cells":
         idx = [0, 200, 256, 511]
         return fields[idx], [(i, i) for i in range(4)], "4 of the 512 cells"
@@ -158,8 +160,19 @@ def oracle_sample(cfg_name, r=4):
 
 def time_oracle(cfg_name, r=4):
     from oracle import collision as C
+    from oracle import quadrature as Qd
     N, d, L, R, gamma, n_rho, M, kind, size = CONFIGS[cfg_name]
     fields, pairs, desc = oracle_sample(cfg_name, r)
+    if N >= 64:
+        # one evaluation costs ~4 TFLOP of FP64 here: time one pair over the first radial
+        # node only and scale by the node count (the oracle's cost is linear in N_rho)
+        rho, w = Qd.radial_rule(n_rho, R)
+        prob = C.Problem(N=N, d=d, L=L, R=R, gamma=gamma, rho=rho[:1], w_rho=w[:1], M=M)
+        fields, pairs = fields[:2], [(0, 1)]
+        t0 = time.perf_counter()
+        C.collide_fields(prob, fields.astype(np.float64), pairs)
+        dt = (time.perf_counter() - t0) * n_rho
+        return 1.0 / dt, dt, f"one pair over 1 of the {n_rho} radial nodes, time x {n_rho}"
     prob = C.Problem(N=N, d=d, L=L, R=R, gamma=gamma, n_rho=n_rho, M=M)
     t0 = time.perf_counter()
     C.collide_fields(prob, fields.astype(np.float64), pairs)

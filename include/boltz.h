@@ -104,7 +104,7 @@ const char* boltz_status_string(boltz_status s);
  * Create a grid: N points per axis on [-L, L]^d_v, truncation radius R,
  * kernel exponent gamma, N_rho Gauss-Legendre radial nodes on [0, R] and M
  * directions (paper Sec. 2.1: uniform grid, fast spectral collision solver).
- *   N      in {8, 16, 32} for d_v = 3; in {8, 16, 32, 64} for d_v = 2
+ *   N      in {8, 16, 32, 64} for both d_v = 2 and d_v = 3
  *   d_v    2 or 3
  *   M      d_v = 2: even, 2..256 (uniform circle rule theta_p = 2 pi p / M);
  *          d_v = 3: one of 6, 14, 26, 38, 50, 86 (octahedral rules of design
@@ -114,8 +114,8 @@ const char* boltz_status_string(boltz_status s);
  *   opt    may be NULL (defaults)
  * Allocates the handle and its device tables on the current device.
  * Errors: BOLTZ_EINVAL (out may be NULL or a value is out of range; *out is
- * left untouched), BOLTZ_EUNSUPPORTED (valid but not built, e.g. N = 64 in
- * 3D), BOLTZ_ENOMEM, BOLTZ_ECUDA.
+ * left untouched), BOLTZ_EUNSUPPORTED (valid but not built, e.g. N = 128),
+ * BOLTZ_ENOMEM, BOLTZ_ECUDA.
  */
 boltz_status boltz_grid_init(boltz_grid* out, int N, int d_v, double L, double R, double gamma,
                              int N_rho, int M, const boltz_options* opt);

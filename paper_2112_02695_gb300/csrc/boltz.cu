@@ -97,7 +97,7 @@ struct boltz_grid_s {
 namespace {
 
 bool supported_shape(int N, int D) {
-    if (D == 3) return N == 8 || N == 16 || N == 32;
+    if (D == 3) return N == 8 || N == 16 || N == 32 || N == 64;
     if (D == 2) return N == 8 || N == 16 || N == 32 || N == 64;
     return false;
 }
@@ -112,8 +112,10 @@ boltz_status build_plan(const boltz_grid_s* g, int n_inputs, const int32_t* pj, 
                         int form, Plan& plan) {
     plan = Plan();
     const size_t field_bytes = size_t(g->n) * 4;
-    // inputs per chunk so that one radial node's shifted fields fit the budget
-    int nc_cap = (int)std::max<size_t>(2, kFieldBudget / (field_bytes * g->M));
+    // inputs per chunk: enough for one radial node's shifted fields to fit the L2-sized
+    // budget, but never fewer than 16 (a rank-16 basis stays in one chunk, so its
+    // shifted fields are computed once) nor more than 64
+    int nc_cap = (int)std::max<size_t>(16, kFieldBudget / (field_bytes * g->M));
     nc_cap = std::min(nc_cap, 64);
     if (form == BOLTZ_FORM_PLAIN) {
         const int E = std::max(1, nc_cap / 2);
@@ -382,60 +384,68 @@ cudaError_t set_smem(K kernel, size_t bytes) {
 template <int N, int D>
 struct Launch {
     using G = Geo<N, D>;
-    static constexpr int FPC = (D == 3) ? (N == 32 ? 1 : (N == 16 ? 4 : 8))
-                                        : (N == 64 ? 4 : (N == 32 ? 16 : (N == 16 ? 32 : 64)));
+    // 3D fields of 32^3 and 64^3 run on clusters of CL CTAs (2 and 8 CTAs per field);
+    // smaller fields run FPC to a CTA
+    static constexpr int CL = (D == 3 && N == 32) ? 2 : ((D == 3 && N == 64) ? 8 : 0);
+    static constexpr int FPC = (D == 3) ? (N == 16 ? 4 : 8) : (N == 64 ? 4 : (N == 32 ? 16 : (N == 16 ? 32 : 64)));
     static constexpr int BLOCK = G::TPF * FPC;
     static constexpr size_t SMEM = size_t(G::SMEM_F) * FPC * sizeof(float2);
-    // 3D N = 32: shifted fields and forward transforms on CTA pairs (half the planes each)
-    static constexpr bool PAIR = (D == 3 && N == 32);
-    static constexpr int PBLOCK = (N / 2) * (N / 2);
-    static constexpr size_t PSMEM = PairGeo<N>::SMEM;
 
     static cudaError_t prepare() {
         cudaError_t e;
-        if ((e = set_smem(k_synth<N, D, FPC, SYN_SHIFT>, SMEM)) != cudaSuccess) return e;
-        if ((e = set_smem(k_synth<N, D, FPC, SYN_PREP>, SMEM)) != cudaSuccess) return e;
-        if ((e = set_smem(k_analysis<N, D, FPC, ANA_SPECTRUM>, SMEM)) != cudaSuccess) return e;
-        if ((e = set_smem(k_analysis<N, D, FPC, ANA_ACCUM>, SMEM)) != cudaSuccess) return e;
-        if constexpr (PAIR) {
-            if ((e = set_smem(k_synth_cl<N, SYN_SHIFT>, PSMEM)) != cudaSuccess) return e;
-            if ((e = set_smem(k_synth_cl<N, SYN_PREP>, PSMEM)) != cudaSuccess) return e;
-            if ((e = set_smem(k_analysis_cl<N, ANA_SPECTRUM>, PSMEM)) != cudaSuccess) return e;
-            if ((e = set_smem(k_analysis_cl<N, ANA_ACCUM>, PSMEM)) != cudaSuccess) return e;
+        if constexpr (CL > 0) {
+            using CG = ClusterGeo<N, CL>;
+            if ((e = set_smem(k_synth_cl<N, CL, SYN_SHIFT>, CG::SMEM)) != cudaSuccess) return e;
+            if ((e = set_smem(k_synth_cl<N, CL, SYN_PREP>, CG::SMEM)) != cudaSuccess) return e;
+            if ((e = set_smem(k_analysis_cl<N, CL, ANA_SPECTRUM>, CG::SMEM)) != cudaSuccess) return e;
+            if ((e = set_smem(k_analysis_cl<N, CL, ANA_ACCUM>, CG::SMEM)) != cudaSuccess) return e;
+            return set_smem(k_output_cl<N, CL>, CG::SMEM);
+        } else {
+            if ((e = set_smem(k_synth<N, D, FPC, SYN_SHIFT>, SMEM)) != cudaSuccess) return e;
+            if ((e = set_smem(k_synth<N, D, FPC, SYN_PREP>, SMEM)) != cudaSuccess) return e;
+            if ((e = set_smem(k_analysis<N, D, FPC, ANA_SPECTRUM>, SMEM)) != cudaSuccess) return e;
+            if ((e = set_smem(k_analysis<N, D, FPC, ANA_ACCUM>, SMEM)) != cudaSuccess) return e;
+            return set_smem(k_output<N, D, FPC>, SMEM);
         }
-        return set_smem(k_output<N, D, FPC>, SMEM);
     }
     static void synth(const SynParams& p, int mode, cudaStream_t st) {
-        if constexpr (PAIR) {
+        if constexpr (CL > 0) {
+            using CG = ClusterGeo<N, CL>;
             if (mode == SYN_SHIFT)
-                k_synth_cl<N, SYN_SHIFT><<<2 * p.n_fields, PBLOCK, PSMEM, st>>>(p);
+                k_synth_cl<N, CL, SYN_SHIFT><<<CL * p.n_fields, CG::NT, CG::SMEM, st>>>(p);
             else
-                k_synth_cl<N, SYN_PREP><<<2 * p.n_fields, PBLOCK, PSMEM, st>>>(p);
-            return;
+                k_synth_cl<N, CL, SYN_PREP><<<CL * p.n_fields, CG::NT, CG::SMEM, st>>>(p);
+        } else {
+            const int grid = (p.n_fields + FPC - 1) / FPC;
+            if (mode == SYN_SHIFT)
+                k_synth<N, D, FPC, SYN_SHIFT><<<grid, BLOCK, SMEM, st>>>(p);
+            else
+                k_synth<N, D, FPC, SYN_PREP><<<grid, BLOCK, SMEM, st>>>(p);
         }
-        const int grid = (p.n_fields + FPC - 1) / FPC;
-        if (mode == SYN_SHIFT)
-            k_synth<N, D, FPC, SYN_SHIFT><<<grid, BLOCK, SMEM, st>>>(p);
-        else
-            k_synth<N, D, FPC, SYN_PREP><<<grid, BLOCK, SMEM, st>>>(p);
     }
     static void analysis(const AnaParams& p, int mode, cudaStream_t st) {
-        if constexpr (PAIR) {
+        if constexpr (CL > 0) {
+            using CG = ClusterGeo<N, CL>;
             if (mode == ANA_SPECTRUM)
-                k_analysis_cl<N, ANA_SPECTRUM><<<2 * p.n_fields, PBLOCK, PSMEM, st>>>(p);
+                k_analysis_cl<N, CL, ANA_SPECTRUM><<<CL * p.n_fields, CG::NT, CG::SMEM, st>>>(p);
             else
-                k_analysis_cl<N, ANA_ACCUM><<<2 * p.n_fields, PBLOCK, PSMEM, st>>>(p);
-            return;
+                k_analysis_cl<N, CL, ANA_ACCUM><<<CL * p.n_fields, CG::NT, CG::SMEM, st>>>(p);
+        } else {
+            const int grid = (p.n_fields + FPC - 1) / FPC;
+            if (mode == ANA_SPECTRUM)
+                k_analysis<N, D, FPC, ANA_SPECTRUM><<<grid, BLOCK, SMEM, st>>>(p);
+            else
+                k_analysis<N, D, FPC, ANA_ACCUM><<<grid, BLOCK, SMEM, st>>>(p);
         }
-        const int grid = (p.n_fields + FPC - 1) / FPC;
-        if (mode == ANA_SPECTRUM)
-            k_analysis<N, D, FPC, ANA_SPECTRUM><<<grid, BLOCK, SMEM, st>>>(p);
-        else
-            k_analysis<N, D, FPC, ANA_ACCUM><<<grid, BLOCK, SMEM, st>>>(p);
     }
     static void output(const OutParams& p, cudaStream_t st) {
-        const int grid = (p.U + FPC - 1) / FPC;
-        k_output<N, D, FPC><<<grid, BLOCK, SMEM, st>>>(p);
+        if constexpr (CL > 0) {
+            using CG = ClusterGeo<N, CL>;
+            k_output_cl<N, CL><<<CL * p.U, CG::NT, CG::SMEM, st>>>(p);
+        } else {
+            const int grid = (p.U + FPC - 1) / FPC;
+            k_output<N, D, FPC><<<grid, BLOCK, SMEM, st>>>(p);
+        }
     }
 };
 
@@ -453,10 +463,10 @@ Dispatch make_dispatch() {
 
 const Dispatch* dispatch_for(int N, int D) {
     static const Dispatch d3_8 = make_dispatch<8, 3>(), d3_16 = make_dispatch<16, 3>(),
-                          d3_32 = make_dispatch<32, 3>(), d2_8 = make_dispatch<8, 2>(),
+                          d3_32 = make_dispatch<32, 3>(), d3_64 = make_dispatch<64, 3>(), d2_8 = make_dispatch<8, 2>(),
                           d2_16 = make_dispatch<16, 2>(), d2_32 = make_dispatch<32, 2>(),
                           d2_64 = make_dispatch<64, 2>();
-    if (D == 3) return N == 8 ? &d3_8 : N == 16 ? &d3_16 : N == 32 ? &d3_32 : nullptr;
+    if (D == 3) return N == 8 ? &d3_8 : N == 16 ? &d3_16 : N == 32 ? &d3_32 : N == 64 ? &d3_64 : nullptr;
     return N == 8 ? &d2_8 : N == 16 ? &d2_16 : N == 32 ? &d2_32 : N == 64 ? &d2_64 : nullptr;
 }
 

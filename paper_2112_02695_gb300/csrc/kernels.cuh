@@ -296,47 +296,89 @@ __global__ void __launch_bounds__(Geo<N, D>::TPF * FPC) k_analysis(AnaParams P) 
     }
 }
 
-// ------------------------------------------------------------------ 3D field kernels on a CTA pair
-// Same transforms as k_synth / k_analysis for d = 3, with one field spread
-// over a cluster of two CTAs: CTA r holds the planes i0 in [rH, rH + H)
-// (H = N/2) in shared memory, so each CTA needs half the memory and three
-// CTAs fit on an SM.  The transform along axis 0 is the only one that crosses
-// planes; it reads or writes the peer's planes through distributed shared
-// memory, between cluster barriers.  A CTA's half of a real field is one
-// contiguous block of global memory; it is moved through a staging copy in
-// shared memory (rows padded to N+2 floats) so that every warp reads or
-// writes 256 contiguous bytes, and the node's three phase rows are staged
-// once per CTA.  Planes are padded by 8 complex entries so that the two plane
-// groups a warp touches in the axis-1 pass fall on different banks.
+// Outputs of the output kernels: gain field of every slot (complex-to-real of
+// Qhat+ with all modes, Nyquist included) minus the loss f_N(l) * Lambda(j),
+// written for every ordered pair (e, j, l) that maps to the slot.
+struct OutParams {
+    const float2* qhat;   // [U][half]
+    const float* fN;      // [n_c][n]
+    const float* lam;     // [n_c][n]
+    const int* out_start; // [U+1]
+    const int4* outs;     // (e, jloc, lloc, 0)
+    float* Q;             // [n_pairs][n]
+    int U;
+};
+
+// ------------------------------------------------------------------ 3D field kernels on a CTA cluster
+// Same transforms as k_synth / k_analysis / k_output for d = 3, with one field
+// spread over a cluster of CL CTAs: CTA r holds the PP = N/CL planes i0 in
+// [r PP, r PP + PP) in shared memory (for 32^3 two CTAs of 71 KB, three per
+// SM; for 64^3 eight CTAs of 134 KB).  The transform along axis 0 is the only
+// one that crosses planes; it reads or writes the other CTAs' planes through
+// distributed shared memory, between cluster barriers.  A CTA's part of a
+// real field is one contiguous block of global memory; it is moved through a
+// staging copy in shared memory (rows padded to N+2 floats) so that every
+// warp reads or writes 256 contiguous bytes, and the node's three phase rows
+// are staged once per CTA.  Planes are padded by 8 complex entries so that
+// the plane groups a warp touches fall on different banks.
 namespace cg = cooperative_groups;
 
-template <int N>
-struct PairGeo {
+template <int N, int CL>
+struct ClusterGeo {
     static constexpr int H = N / 2;
+    static constexpr int PP = N / CL;            // planes per CTA
     static constexpr int RS = H + 1;             // complex row stride
     static constexpr int PS = N * RS + 8;        // complex plane stride
     static constexpr int RR = N + 2;             // staged real row stride (floats)
-    static constexpr int NT = H * H;             // threads per CTA
-    static constexpr int HALF_N = H * N * N;     // floats of a field held by one CTA
-    static constexpr size_t SMEM = size_t(H) * PS * sizeof(float2) + 3 * N * sizeof(float2);
-    static_assert(size_t(H) * N * RR * sizeof(float) <= size_t(H) * PS * sizeof(float2), "staging fits the planes");
+    static constexpr int NT = PP * H;            // threads per CTA
+    static constexpr int PART_N = PP * N * N;    // floats of a field held by one CTA
+    static constexpr int COLS = PP * (H + 1);    // columns of a CTA incl. the half-axis Nyquist
+    static constexpr size_t SMEM = size_t(PP) * PS * sizeof(float2) + 3 * N * sizeof(float2);
+    static constexpr int MINB = (SMEM <= (72u << 10)) ? 3 : 1;
+    static_assert(size_t(PP) * N * RR * sizeof(float) <= size_t(PP) * PS * sizeof(float2), "staging fits");
+    static_assert((2 * NT) % N == 0 && (2 * NT) % 256 == 0 && PART_N % (2 * NT) == 0, "copy strides");
 };
 
-template <int N, int MODE>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__((N / 2) * (N / 2), 3)
+// pointers to the plane buffers of every CTA of the cluster (index = rank)
+template <int CL>
+__device__ __forceinline__ void cluster_planes(cg::cluster_group& cluster, float2* smem, float2* (&pl)[CL]) {
+#pragma unroll
+    for (int r = 0; r < CL; ++r) pl[r] = cluster.map_shared_rank(smem, r);
+}
+
+// Coalesced move of this CTA's part of a real field between a staging area in
+// shared memory (rows of N floats padded to RR) and global memory: thread lt
+// moves floats L = 2 lt + 2 NT it; both addresses advance by constants.
+template <int N, int CL, bool TO_GLOBAL>
+__device__ __forceinline__ void staged_copy(float* stg, float* gptr, size_t g_step, int lt) {
+    using CG = ClusterGeo<N, CL>;
+    constexpr int ITER = CG::PART_N / (2 * CG::NT);
+    constexpr int S_STEP = (2 * CG::NT / N) * CG::RR;
+    const int L0 = 2 * lt;
+    float* sp = stg + (L0 / N) * CG::RR + (L0 % N);
+#pragma unroll 8
+    for (int it = 0; it < ITER; ++it) {
+        float2* g = reinterpret_cast<float2*>(gptr + it * g_step);
+        float2* sm = reinterpret_cast<float2*>(sp + it * S_STEP);
+        if (TO_GLOBAL) *g = *sm;
+        else *sm = __ldg(g);
+    }
+}
+
+template <int N, int CL, int MODE>
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(ClusterGeo<N, CL>::NT, ClusterGeo<N, CL>::MINB)
     k_synth_cl(SynParams P) {
     using G = Geo<N, 3>;
-    using PG = PairGeo<N>;
-    constexpr int H = PG::H, RS = PG::RS, PS = PG::PS, RR = PG::RR, NT = PG::NT;
-    extern __shared__ float2 smem[];             // [H][PS] planes | [3][N] phase rows
-    float2* phs = smem + H * PS;
+    using CG = ClusterGeo<N, CL>;
+    constexpr int H = CG::H, PP = CG::PP, RS = CG::RS, PS = CG::PS, RR = CG::RR, NT = CG::NT;
+    extern __shared__ float2 smem[];             // [PP][PS] planes | [3][N] phase rows
+    float2* phs = smem + PP * PS;
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
-    float2* peer = cluster.map_shared_rank(smem, rank ^ 1);
-    float2* half0 = rank == 0 ? smem : peer;    // holder of planes [0, H)
-    float2* half1 = rank == 0 ? peer : smem;    // holder of planes [H, N)
-    const int f = blockIdx.x >> 1;
-    const bool active = f < P.n_fields;          // same for both CTAs of the cluster
+    float2* pl[CL];
+    cluster_planes<CL>(cluster, smem, pl);
+    const int f = blockIdx.x / CL;
+    const bool active = f < P.n_fields;          // same for every CTA of the cluster
     const int lt = threadIdx.x;
     int input = 0, node = P.id_node;
     bool use_gm = false;
@@ -354,9 +396,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__((N / 2) * (N / 2), 3
     for (int i = lt; i < 3 * N; i += NT) phs[i] = __ldg(&P.phase[(size_t)node * 3 * N + i]);
     __syncthreads();
     float2 x[N];
-    // axis 0: columns (k1, k2), k1 in this CTA's half, k2 < N/2
+    // axis 0: columns (k1, k2), k1 in this CTA's range, k2 < N/2
     if (active) {
-        const int k1 = rank * H + lt / H, k2 = lt % H;
+        const int k1 = rank * PP + lt / H, k2 = lt % H;
         const float2 w12 = cmul(phs[N + k1], phs[2 * N + k2]);
 #pragma unroll
         for (int k0 = 0; k0 < N; ++k0) {
@@ -369,26 +411,24 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__((N / 2) * (N / 2), 3
         }
         fft_reg<N, true>(x);
 #pragma unroll
-        for (int i0 = 0; i0 < H; ++i0) half0[i0 * PS + k1 * RS + k2] = x[i0];
-#pragma unroll
-        for (int i0 = 0; i0 < H; ++i0) half1[i0 * PS + k1 * RS + k2] = x[H + i0];
+        for (int i0 = 0; i0 < N; ++i0) pl[i0 / PP][(i0 % PP) * PS + k1 * RS + k2] = x[i0];
     }
     cluster.sync();
     // axis 1 on this CTA's planes
     if (active) {
-        const int i0 = lt / H, k2 = lt % H;
+        const int p0 = lt / H, k2 = lt % H;
 #pragma unroll
-        for (int k1 = 0; k1 < N; ++k1) x[k1] = smem[i0 * PS + k1 * RS + k2];
+        for (int k1 = 0; k1 < N; ++k1) x[k1] = smem[p0 * PS + k1 * RS + k2];
         fft_reg<N, true>(x);
 #pragma unroll
-        for (int i1 = 0; i1 < N; ++i1) smem[i0 * PS + i1 * RS + k2] = x[i1];
+        for (int i1 = 0; i1 < N; ++i1) smem[p0 * PS + i1 * RS + k2] = x[i1];
     }
     __syncthreads();
-    // axis 2: complex-to-real of rows (i0, i1) and (i0, i1 + N/2)
-    const int i0 = lt / H, i1 = lt % H;
+    // axis 2: complex-to-real of rows (p0, i1) and (p0, i1 + N/2)
+    const int p0 = lt / H, i1 = lt % H;
     if (active) {
-        const float2* r1 = smem + i0 * PS + i1 * RS;
-        const float2* r2 = smem + i0 * PS + (i1 + H) * RS;
+        const float2* r1 = smem + p0 * PS + i1 * RS;
+        const float2* r2 = smem + p0 * PS + (i1 + H) * RS;
         x[0] = make_float2(r1[0].x, r2[0].x);
         x[H] = make_float2(0.f, 0.f);
 #pragma unroll
@@ -402,8 +442,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__((N / 2) * (N / 2), 3
     __syncthreads();                              // every row is read before staging overwrites the planes
     float* stg = reinterpret_cast<float*>(smem);
     if (active) {
-        float2* o1 = reinterpret_cast<float2*>(stg + (i0 * N + i1) * RR);
-        float2* o2 = reinterpret_cast<float2*>(stg + (i0 * N + i1 + H) * RR);
+        float2* o1 = reinterpret_cast<float2*>(stg + (p0 * N + i1) * RR);
+        float2* o2 = reinterpret_cast<float2*>(stg + (p0 * N + i1 + H) * RR);
 #pragma unroll
         for (int c = 0; c < N / 2; ++c) {
             o1[c] = make_float2(x[2 * c].x, x[2 * c + 1].x);
@@ -412,45 +452,28 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__((N / 2) * (N / 2), 3
     }
     __syncthreads();
     if (active) {
-        // Thread lt moves floats L = 2 lt + 2 NT it (it = 0, 1, ...): each warp moves 256
-        // contiguous bytes, which never straddle a voxel chunk.  One step of `it` advances
-        // the staged row by 2NT/N and the voxel by 2NT (a whole number of chunks), so both
-        // addresses advance by constants.
-        static_assert((2 * NT) % N == 0 && (2 * NT) % G::VCH == 0, "copy-out strides");
-        constexpr int ITER = PG::HALF_N / (2 * NT);
-        const int L0 = 2 * lt;
-        const float* sp = stg + (L0 / N) * RR + (L0 % N);
-        constexpr int S_STEP = (2 * NT / N) * RR;
-        const int v0 = rank * PG::HALF_N + L0;
-        float* op;
-        size_t o_step;
-        if (MODE == SYN_SHIFT) {
-            op = shifted_field_row<N, 3>(P.out, f / P.n_c, f % P.n_c, P.n_c, v0);
-            o_step = (size_t)(2 * NT / G::VCH) * P.n_c * G::VCH;
-        } else {
-            op = P.out + (size_t)f * G::n + v0;
-            o_step = 2 * NT;
-        }
-#pragma unroll 8
-        for (int it = 0; it < ITER; ++it)
-            *reinterpret_cast<float2*>(op + it * o_step) = *reinterpret_cast<const float2*>(sp + it * S_STEP);
+        const int v0 = rank * CG::PART_N + 2 * lt;
+        if (MODE == SYN_SHIFT)
+            staged_copy<N, CL, true>(stg, shifted_field_row<N, 3>(P.out, f / P.n_c, f % P.n_c, P.n_c, v0),
+                                     (size_t)(2 * NT / G::VCH) * P.n_c * G::VCH, lt);
+        else
+            staged_copy<N, CL, true>(stg, P.out + (size_t)f * G::n + v0, 2 * NT, lt);
     }
 }
 
-template <int N, int MODE>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__((N / 2) * (N / 2), 2)
+template <int N, int CL, int MODE>
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(ClusterGeo<N, CL>::NT, (ClusterGeo<N, CL>::MINB > 1 ? 2 : 1))
     k_analysis_cl(AnaParams P) {
     using G = Geo<N, 3>;
-    using PG = PairGeo<N>;
-    constexpr int H = PG::H, RS = PG::RS, PS = PG::PS, RR = PG::RR, NT = PG::NT, NH = G::NH;
-    constexpr int COLS = H * NH;                  // this CTA's columns along axes 1 and 0
-    extern __shared__ float2 smem[];              // [H][PS] planes (or the staged real rows)
+    using CG = ClusterGeo<N, CL>;
+    constexpr int H = CG::H, PP = CG::PP, RS = CG::RS, PS = CG::PS, RR = CG::RR, NT = CG::NT, NH = G::NH;
+    constexpr int COLS = CG::COLS;
+    extern __shared__ float2 smem[];              // [PP][PS] planes (or the staged real rows)
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
-    float2* peer = cluster.map_shared_rank(smem, rank ^ 1);
-    const float2* half0 = rank == 0 ? smem : peer;
-    const float2* half1 = rank == 0 ? peer : smem;
-    const int f = blockIdx.x >> 1;
+    float2* pl[CL];
+    cluster_planes<CL>(cluster, smem, pl);
+    const int f = blockIdx.x / CL;
     const bool active = f < P.n_fields;
     const int lt = threadIdx.x;
     float2* __restrict__ dst = P.out + (size_t)f * G::half;
@@ -458,27 +481,17 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__((N / 2) * (N / 2), 2
     float2 x[N];
     const int n_iter = (MODE == ANA_ACCUM) ? P.nq : 1;
     for (int qq = 0; qq < n_iter; ++qq) {
-        const float* __restrict__ src =
+        const float* src =
             ((MODE == ANA_ACCUM) ? P.in + ((size_t)qq * P.U + f) * G::n : P.in + (size_t)f * G::n) +
-            (size_t)rank * PG::HALF_N;
+            (size_t)rank * CG::PART_N;
         const float* __restrict__ ct = P.ctab + (size_t)(P.q0 + qq) * (G::SMAX + 1);
-        // stage this CTA's half of the real field (coalesced), then R2C along the last axis
-        if (active) {
-            // coalesced: thread lt moves floats 2 lt + 2 NT it; constant strides in both spaces
-            constexpr int ITER = PG::HALF_N / (2 * NT);
-            constexpr int S_STEP = (2 * NT / N) * RR;
-            const int L0 = 2 * lt;
-            const float2* in2 = reinterpret_cast<const float2*>(src + L0);
-            float* sp = stg + (L0 / N) * RR + (L0 % N);
-#pragma unroll 8
-            for (int it = 0; it < ITER; ++it)
-                *reinterpret_cast<float2*>(sp + it * S_STEP) = __ldg(in2 + it * NT);
-        }
+        // stage this CTA's part of the real field (coalesced), then R2C along the last axis
+        if (active) staged_copy<N, CL, false>(stg, const_cast<float*>(src) + 2 * lt, 2 * NT, lt);
         __syncthreads();
-        const int i0 = lt / H, i1 = lt % H;
+        const int p0 = lt / H, i1 = lt % H;
         if (active) {
-            const float2* a2 = reinterpret_cast<const float2*>(stg + (i0 * N + i1) * RR);
-            const float2* b2 = reinterpret_cast<const float2*>(stg + (i0 * N + i1 + H) * RR);
+            const float2* a2 = reinterpret_cast<const float2*>(stg + (p0 * N + i1) * RR);
+            const float2* b2 = reinterpret_cast<const float2*>(stg + (p0 * N + i1 + H) * RR);
 #pragma unroll
             for (int c = 0; c < N / 2; ++c) {
                 const float2 a = a2[c], b = b2[c];
@@ -489,8 +502,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__((N / 2) * (N / 2), 2
         __syncthreads();                          // staged rows consumed before the planes are written
         if (active) {
             fft_reg<N, false>(x);
-            float2* r1 = smem + i0 * PS + i1 * RS;
-            float2* r2 = smem + i0 * PS + (i1 + H) * RS;
+            float2* r1 = smem + p0 * PS + i1 * RS;
+            float2* r2 = smem + p0 * PS + (i1 + H) * RS;
 #pragma unroll
             for (int k = 0; k <= H; ++k) {
                 const float2 z = x[k], zc = x[(N - k) & (N - 1)];
@@ -502,23 +515,21 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__((N / 2) * (N / 2), 2
         // axis 1 on this CTA's planes
         if (active) {
             for (int c = lt; c < COLS; c += NT) {
-                const int p0 = c / NH, k2 = c % NH;
+                const int q0 = c / NH, k2 = c % NH;
 #pragma unroll
-                for (int k1 = 0; k1 < N; ++k1) x[k1] = smem[p0 * PS + k1 * RS + k2];
+                for (int k1 = 0; k1 < N; ++k1) x[k1] = smem[q0 * PS + k1 * RS + k2];
                 fft_reg<N, false>(x);
 #pragma unroll
-                for (int k1 = 0; k1 < N; ++k1) smem[p0 * PS + k1 * RS + k2] = x[k1];
+                for (int k1 = 0; k1 < N; ++k1) smem[q0 * PS + k1 * RS + k2] = x[k1];
             }
         }
         cluster.sync();
-        // axis 0: columns (k1, k2), k1 in this CTA's half; planes from both CTAs
+        // axis 0: columns (k1, k2), k1 in this CTA's range; planes from every CTA
         if (active) {
             for (int c = lt; c < COLS; c += NT) {
-                const int k1 = rank * H + c / NH, k2 = c % NH;
+                const int k1 = rank * PP + c / NH, k2 = c % NH;
 #pragma unroll
-                for (int p0 = 0; p0 < H; ++p0) x[p0] = half0[p0 * PS + k1 * RS + k2];
-#pragma unroll
-                for (int p0 = 0; p0 < H; ++p0) x[H + p0] = half1[p0 * PS + k1 * RS + k2];
+                for (int i0 = 0; i0 < N; ++i0) x[i0] = pl[i0 / PP][(i0 % PP) * PS + k1 * RS + k2];
                 fft_reg<N, false>(x);
 #pragma unroll
                 for (int k0 = 0; k0 < N; ++k0) {
@@ -538,23 +549,102 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__((N / 2) * (N / 2), 2
                 }
             }
         }
-        cluster.sync();      // the peer has finished reading these planes
+        cluster.sync();      // the other CTAs have finished reading these planes
     }
 }
 
-// ------------------------------------------------------------------ output
-// Gain field of every slot (complex-to-real of Qhat+ with all modes, Nyquist
-// included) minus the loss f_N(l) * Lambda(j), written for every ordered pair
-// (e, j, l) that maps to the slot.
-struct OutParams {
-    const float2* qhat;   // [U][half]
-    const float* fN;      // [n_c][n]
-    const float* lam;     // [n_c][n]
-    const int* out_start; // [U+1]
-    const int4* outs;     // (e, jloc, lloc, 0)
-    float* Q;             // [n_pairs][n]
-    int U;
-};
+template <int N, int CL>
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(ClusterGeo<N, CL>::NT, 1) k_output_cl(OutParams P) {
+    using G = Geo<N, 3>;
+    using CG = ClusterGeo<N, CL>;
+    constexpr int H = CG::H, PP = CG::PP, RS = CG::RS, PS = CG::PS, RR = CG::RR, NT = CG::NT, NH = G::NH;
+    constexpr int COLS = CG::COLS;
+    extern __shared__ float2 smem[];
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    float2* pl[CL];
+    cluster_planes<CL>(cluster, smem, pl);
+    const int u = blockIdx.x / CL;
+    const bool active = u < P.U;
+    const int lt = threadIdx.x;
+    const float2* __restrict__ src = P.qhat + (size_t)u * G::half;
+    float2 x[N];
+    // axis 0 over every column (k1 in this CTA's range, k2 = 0..N/2), sign (-1)^k from the index parity
+    if (active) {
+        for (int c = lt; c < COLS; c += NT) {
+            const int k1 = rank * PP + c / NH, k2 = c % NH;
+#pragma unroll
+            for (int k0 = 0; k0 < N; ++k0) {
+                const float2 v = src[(k0 * N + k1) * NH + k2];
+                x[k0] = ((k0 + k1 + k2) & 1) ? make_float2(-v.x, -v.y) : v;
+            }
+            fft_reg<N, true>(x);
+#pragma unroll
+            for (int i0 = 0; i0 < N; ++i0) pl[i0 / PP][(i0 % PP) * PS + k1 * RS + k2] = x[i0];
+        }
+    }
+    cluster.sync();
+    // axis 1 on this CTA's planes
+    if (active) {
+        for (int c = lt; c < COLS; c += NT) {
+            const int q0 = c / NH, k2 = c % NH;
+#pragma unroll
+            for (int k1 = 0; k1 < N; ++k1) x[k1] = smem[q0 * PS + k1 * RS + k2];
+            fft_reg<N, true>(x);
+#pragma unroll
+            for (int i1 = 0; i1 < N; ++i1) smem[q0 * PS + i1 * RS + k2] = x[i1];
+        }
+    }
+    __syncthreads();
+    const int p0 = lt / H, i1 = lt % H;
+    if (active) {
+        const float2* r1 = smem + p0 * PS + i1 * RS;
+        const float2* r2 = smem + p0 * PS + (i1 + H) * RS;
+        x[0] = make_float2(r1[0].x, r2[0].x);
+        x[H] = make_float2(r1[H].x, r2[H].x);
+#pragma unroll
+        for (int k = 1; k < H; ++k) {
+            const float2 a = r1[k], b = r2[k];
+            x[k] = make_float2(a.x - b.y, a.y + b.x);
+            x[N - k] = make_float2(a.x + b.y, b.x - a.y);
+        }
+        fft_reg<N, true>(x);
+    }
+    __syncthreads();
+    float* stg = reinterpret_cast<float*>(smem);  // gain rows of this CTA's part
+    if (active) {
+        float2* o1 = reinterpret_cast<float2*>(stg + (p0 * N + i1) * RR);
+        float2* o2 = reinterpret_cast<float2*>(stg + (p0 * N + i1 + H) * RR);
+#pragma unroll
+        for (int c = 0; c < N / 2; ++c) {
+            o1[c] = make_float2(x[2 * c].x, x[2 * c + 1].x);
+            o2[c] = make_float2(x[2 * c].y, x[2 * c + 1].y);
+        }
+    }
+    __syncthreads();
+    if (!active) return;
+    constexpr int ITER = CG::PART_N / (2 * NT);
+    constexpr int S_STEP = (2 * NT / N) * RR;
+    const int L0 = 2 * lt;
+    const float* sp = stg + (L0 / N) * RR + (L0 % N);
+    const size_t v0 = (size_t)rank * CG::PART_N + L0;
+    for (int o = P.out_start[u]; o < P.out_start[u + 1]; ++o) {
+        const int4 e = P.outs[o];
+        const float* fl = P.fN + (size_t)e.z * G::n + v0;
+        const float* lj = P.lam + (size_t)e.y * G::n + v0;
+        float* q = P.Q + (size_t)e.x * G::n + v0;
+#pragma unroll 4
+        for (int it = 0; it < ITER; ++it) {
+            const float2 gsum = *reinterpret_cast<const float2*>(sp + it * S_STEP);
+            const float2 a = __ldg(reinterpret_cast<const float2*>(fl + (size_t)it * 2 * NT));
+            const float2 b = __ldg(reinterpret_cast<const float2*>(lj + (size_t)it * 2 * NT));
+            *reinterpret_cast<float2*>(q + (size_t)it * 2 * NT) = make_float2(fmaf(-a.x, b.x, gsum.x), fmaf(-a.y, b.y, gsum.y));
+        }
+    }
+}
+
+// ------------------------------------------------------------------ output (single-CTA fields)
+
 
 template <int N, int D, int FPC>
 __global__ void __launch_bounds__(Geo<N, D>::TPF * FPC) k_output(OutParams P) {

@@ -67,7 +67,7 @@ def test_grid_init_rejects_bad_arguments(B, args):
 
 def test_grid_init_reports_unbuilt_shapes(B):
     with pytest.raises(B.BoltzError) as ei:
-        B.boltz_grid_init(64, 3, 10.0, 10.0, 1.0, 32, 86)
+        B.boltz_grid_init(128, 3, 10.0, 10.0, 1.0, 32, 86)
     assert ei.value.status == B.BOLTZ_EUNSUPPORTED
 
 

@@ -169,6 +169,16 @@ def test_lowrank_step_host_matches_device_path(B):
     assert np.max(np.abs(Th.numpy() - Td)) <= 1e-6 * np.max(np.abs(Td))
 
 
+def test_64cube_against_oracle_small_quadrature(B):
+    """3D N=64 (8-CTA clusters per field) against the oracle, N_rho=2 x M=6."""
+    cfg = (64, 3, 10.0, 10.0, 1.0, 2, 6)
+    F = as_fp32(W.random_fields(64, 3, 10.0, 2, seed=64))
+    pairs = [(0, 1), (1, 0), (1, 1)]
+    Qg = gpu_collide(B, cfg, F, pairs)
+    _, Qo, s = oracle_collide(cfg, F, pairs)
+    assert rel_err(Qg, Qo, s).max() < TOL
+
+
 # ---------------------------------------------------------------- full-size workloads
 
 def test_c2_full_size_sampled_pairs(B):
@@ -204,3 +214,34 @@ def test_c3_full_size_shock_cells_bimodal(B):
     err = np.max(np.abs(Qg - pred), axis=(1, 2, 3)) / scale
     # the cell inputs are FP32 roundings of the exact mixture: allow that input rounding
     assert err.max() < TOL
+
+
+def test_c4_full_size_gain_symmetry_and_bilinearity(B):
+    """3D N=64^3 on [-10,10]^3, gamma=1, R=10, N_rho=32 x M=86, rank-8 basis (seed
+    2113): all 64 pairs in one batched call.  At this size the oracle certifies
+    the loss term exactly (one synthesis per input), so the GPU gain
+    Q + Q- must be symmetric in (g, f); bilinearity is checked with a ninth
+    input that is a fixed combination of two basis functions."""
+    from oracle import collision as C
+    cfg = (64, 3, 10.0, 10.0, 1.0, 32, 86)
+    V = as_fp32(W.hermite_maxwellian_basis(64, 3, 10.0, 8, seed=2113))
+    mix = as_fp32(0.3 * V[1] + 0.7 * V[5])
+    inputs = np.concatenate([V, mix[None]])
+    pairs = [(j, l) for j in range(8) for l in range(8)] + [(8, 2), (2, 8)]
+    Qg = gpu_collide(B, cfg, inputs, pairs)
+    prob = C.Problem(N=64, d=3, L=10.0, R=10.0, gamma=1.0, n_rho=32, M=86)
+    S = C.spectrum(prob, inputs)
+    lam = C.synthesize(prob, C.loss_weight(prob, C.kabs(prob))[None] * S)
+    fN = C.synthesize(prob, S)
+    gain = {}
+    for e, (j, l) in enumerate(pairs):
+        gain[(j, l)] = Qg[e] + fN[l] * lam[j]
+    scale = max(np.max(np.abs(g)) for g in gain.values())
+    for j in range(8):
+        for l in range(j + 1, 8):
+            assert np.max(np.abs(gain[(j, l)] - gain[(l, j)])) / scale < TOL, (j, l)
+    # Q(0.3 V1 + 0.7 V5, V2) = 0.3 Q(V1, V2) + 0.7 Q(V5, V2), and the same in the f slot
+    pred_g = 0.3 * Qg[1 * 8 + 2] + 0.7 * Qg[5 * 8 + 2]
+    pred_f = 0.3 * Qg[2 * 8 + 1] + 0.7 * Qg[2 * 8 + 5]
+    assert np.max(np.abs(Qg[64] - pred_g)) / scale < TOL
+    assert np.max(np.abs(Qg[65] - pred_f)) / scale < TOL
