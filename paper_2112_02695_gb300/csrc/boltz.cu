@@ -20,6 +20,7 @@
 #include "boltz.h"
 #include "kernels.cuh"
 #include "quadrature.hpp"
+#include "tc_kernels.cuh"
 
 using namespace boltz_dev;
 
@@ -648,19 +649,45 @@ boltz_status run_batched(boltz_grid_s* g, const float2* spectra, int n_inputs, c
     return BOLTZ_OK;
 }
 
+// Projection on the tensor cores (3xTF32 split, FP32-accurate) when the grid
+// has at least 512 voxels; a CUDA-core kernel for the tiny 2D grids.
+template <int NP>
+void launch_project_tc(const float* V, const float* Q, float* partial, int r, int n, int kpc, int* err,
+                       cudaStream_t st) {
+    const dim3 grid(n / kpc, (r * r + 127) / 128);
+    k_project_tc<NP><<<grid, kProjThreads, ProjTcShape<NP>::SMEM, st>>>(V, Q, partial, r, n, kpc, err);
+}
+
+cudaError_t prepare_project_tc() {
+    cudaError_t e;
+    if ((e = set_smem(k_project_tc<16>, ProjTcShape<16>::SMEM)) != cudaSuccess) return e;
+    if ((e = set_smem(k_project_tc<32>, ProjTcShape<32>::SMEM)) != cudaSuccess) return e;
+    if ((e = set_smem(k_project_tc<48>, ProjTcShape<48>::SMEM)) != cudaSuccess) return e;
+    return set_smem(k_project_tc<64>, ProjTcShape<64>::SMEM);
+}
+
 boltz_status run_project(boltz_grid_s* g, const float* V, int r, const float* Q, float* T, float* partial,
                          cudaStream_t st) {
-    constexpr int PB = 8, RT = 16;
     const int r2 = r * r;
-    const int bx = (r2 + PB - 1) / PB, bz = (r + RT - 1) / RT;
-    int slices = std::max(1, std::min(64, (2 * 152) / std::max(1, bx * bz)));
-    slices = std::min(slices, std::max(1, g->n / 256));
-    {
+    const int count = r * r2;
+    const float scale = (float)std::pow(2.0 * g->L / g->N, g->D);
+    int slices;
+    if (g->n >= 512) {
+        const int kpc = std::max(512, g->n / 64);           // n is a power of two: kpc divides it
+        slices = g->n / kpc;
+        ProfScope ps(g, BOLTZ_KCLASS_PROJECT, st);
+        if (r <= 16) launch_project_tc<16>(V, Q, partial, r, g->n, kpc, g->d_err, st);
+        else if (r <= 32) launch_project_tc<32>(V, Q, partial, r, g->n, kpc, g->d_err, st);
+        else if (r <= 48) launch_project_tc<48>(V, Q, partial, r, g->n, kpc, g->d_err, st);
+        else launch_project_tc<64>(V, Q, partial, r, g->n, kpc, g->d_err, st);
+    } else {
+        constexpr int PB = 8, RT = 16;
+        const int bx = (r2 + PB - 1) / PB, bz = (r + RT - 1) / RT;
+        slices = std::max(1, std::min(64, (2 * 152) / std::max(1, bx * bz)));
+        slices = std::min(slices, std::max(1, g->n / 256));
         ProfScope ps(g, BOLTZ_KCLASS_PROJECT, st);
         k_project<PB, RT><<<dim3(bx, slices, bz), 256, 0, st>>>(V, Q, partial, r, g->n, slices);
     }
-    const int count = r * r2;
-    const float scale = (float)std::pow(2.0 * g->L / g->N, g->D);
     ProfScope ps(g, BOLTZ_KCLASS_PROJECT, st);
     k_project_reduce<<<(count + 255) / 256, 256, 0, st>>>(partial, T, count, slices, scale);
     BZ_CUDA(cudaGetLastError());
@@ -866,7 +893,8 @@ boltz_status boltz_grid_init(boltz_grid* out, int N, int d_v, double L, double R
         cudaMemcpy(g->d_dpair, dpair.data(), n_dp * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(g->d_err, 0, sizeof(int)) != cudaSuccess)
         return fail(BOLTZ_ECUDA);
-    if (dispatch_for(N, d_v)->prepare() != cudaSuccess || prepare_contract() != cudaSuccess)
+    if (dispatch_for(N, d_v)->prepare() != cudaSuccess || prepare_contract() != cudaSuccess ||
+        prepare_project_tc() != cudaSuccess)
         return fail(BOLTZ_ECUDA);
     if (cudaStreamCreateWithFlags(&g->side, cudaStreamNonBlocking) != cudaSuccess) return fail(BOLTZ_ECUDA);
     for (int b = 0; b < 2; ++b)
