@@ -104,7 +104,8 @@ const char* boltz_status_string(boltz_status s);
  * Create a grid: N points per axis on [-L, L]^d_v, truncation radius R,
  * kernel exponent gamma, N_rho Gauss-Legendre radial nodes on [0, R] and M
  * directions (paper Sec. 2.1: uniform grid, fast spectral collision solver).
- *   N      in {8, 16, 32, 64} for both d_v = 2 and d_v = 3
+ *   N      in {8, 16, 24, 32, 48, 64} for both d_v = 2 and d_v = 3 (24 and 48 use
+ *          a mixed radix-3 transform)
  *   d_v    2 or 3
  *   M      d_v = 2: even, 2..256 (uniform circle rule theta_p = 2 pi p / M);
  *          d_v = 3: one of 6, 14, 26, 38, 50, 86 (octahedral rules of design
@@ -167,6 +168,17 @@ boltz_status boltz_collide_batched(boltz_grid g, const void* spectra, int n_inpu
  */
 boltz_status boltz_project(boltz_grid g, const float* V, int r, const float* Q, float* T_out,
                            void* stream);
+
+/*
+ * Collision invariants of results, in FP64 (paper Sec. 1: mass, momentum and
+ * energy moments; Q conserves them up to quadrature accuracy):
+ *   out[f][0]      = dv^d sum_v Q_f(v)
+ *   out[f][1 + a]  = dv^d sum_v v_a Q_f(v),  a = 0..d-1
+ *   out[f][d + 1]  = dv^d sum_v |v|^2 Q_f(v)
+ *   Q    device float32 [n_fields][N^d];  out  device float64 [n_fields][d + 2]
+ * Summation order is fixed (run-to-run identical).  Errors: BOLTZ_EINVAL, BOLTZ_ECUDA.
+ */
+boltz_status boltz_moments(boltz_grid g, const float* Q, int n_fields, double* out, void* stream);
 
 /*
  * Allocation-free variant of boltz_project (the paper has no counterpart; this

@@ -30,7 +30,7 @@ EXPORTED = (
     "boltz_abi_version", "boltz_status_string", "boltz_grid_init", "boltz_grid_destroy",
     "boltz_spectrum", "boltz_collide_batched", "boltz_project", "boltz_lowrank_step_host",
     "boltz_host_quadrature", "boltz_workspace_size", "boltz_profile_enable", "boltz_profile_read",
-    "boltz_project_noalloc", "boltz_sync_status", "boltz_selftest",
+    "boltz_project_noalloc", "boltz_sync_status", "boltz_selftest", "boltz_moments",
 )
 
 KERNEL_CLASSES = ("spectrum", "prep", "shift", "contract", "radial", "output", "project")
@@ -69,6 +69,7 @@ def _load() -> ctypes.CDLL:
                                   ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
         "boltz_profile_enable": ([vp, ctypes.c_int], ctypes.c_int),
         "boltz_sync_status": ([vp, vp], ctypes.c_int),
+        "boltz_moments": ([vp, vp, ctypes.c_int, vp, vp], ctypes.c_int),
         "boltz_selftest": ([vp, ctypes.c_int, vp], ctypes.c_int),
         "boltz_project_noalloc": ([vp, vp, ctypes.c_int, vp, vp, vp], ctypes.c_int),
         "boltz_profile_read": ([vp, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
@@ -260,6 +261,17 @@ def boltz_workspace_size(grid: Grid, n_inputs: int, pair_j, pair_l, form: int = 
     _check(_lib.boltz_workspace_size(grid.handle, n_inputs, pj.ctypes.data_as(i32p), pl.ctypes.data_as(i32p),
                                      len(pj), int(form), ctypes.byref(out)), "boltz_workspace_size")
     return out.value
+
+
+def boltz_moments(grid: Grid, Q, out=None, stream=None):
+    """FP64 [n_fields, d+2]: mass, momentum (d components), energy moments of each field."""
+    import torch
+    nf = Q.shape[0]
+    if out is None:
+        out = torch.empty((nf, grid.d_v + 2), dtype=torch.float64, device=Q.device)
+    _check(_lib.boltz_moments(grid.handle, _dev_ptr(Q, "float32", "Q"), nf, _dev_ptr(out, "float64", "out"),
+                              _stream_ptr(stream)), "boltz_moments")
+    return out
 
 
 def boltz_sync_status(grid: Grid, stream=None):

@@ -98,9 +98,14 @@ struct boltz_grid_s {
 namespace {
 
 bool supported_shape(int N, int D) {
-    if (D == 3) return N == 8 || N == 16 || N == 32 || N == 64;
-    if (D == 2) return N == 8 || N == 16 || N == 32 || N == 64;
-    return false;
+    if (D != 2 && D != 3) return false;
+    return N == 8 || N == 16 || N == 24 || N == 32 || N == 48 || N == 64;
+}
+
+// voxels per chunk of the shifted-field layout (must match Geo<N, D>::VCH)
+int voxel_chunk(int N, int D) {
+    const int n = D == 3 ? N * N * N : N * N;
+    return n < 256 ? n : (N % 3 == 0 ? 288 : 256);
 }
 
 
@@ -387,8 +392,9 @@ struct Launch {
     using G = Geo<N, D>;
     // 3D fields of 32^3 and 64^3 run on clusters of CL CTAs (2 and 8 CTAs per field);
     // smaller fields run FPC to a CTA
-    static constexpr int CL = (D == 3 && N == 32) ? 2 : ((D == 3 && N == 64) ? 8 : 0);
-    static constexpr int FPC = (D == 3) ? (N == 16 ? 4 : 8) : (N == 64 ? 4 : (N == 32 ? 16 : (N == 16 ? 32 : 64)));
+    static constexpr int CL = (D == 3 && N == 32) ? 2 : ((D == 3 && N == 64) ? 8 : ((D == 3 && N == 48) ? 4 : 0));
+    static constexpr int FPC = (D == 3) ? (N == 24 ? 1 : (N == 16 ? 4 : 8))
+                                        : (N == 64 ? 4 : ((N == 32 || N == 48) ? 16 : (N == 8 ? 64 : 32)));
     static constexpr int BLOCK = G::TPF * FPC;
     static constexpr size_t SMEM = size_t(G::SMEM_F) * FPC * sizeof(float2);
 
@@ -464,11 +470,16 @@ Dispatch make_dispatch() {
 
 const Dispatch* dispatch_for(int N, int D) {
     static const Dispatch d3_8 = make_dispatch<8, 3>(), d3_16 = make_dispatch<16, 3>(),
+                          d3_24 = make_dispatch<24, 3>(), d3_48 = make_dispatch<48, 3>(),
+                          d2_24 = make_dispatch<24, 2>(), d2_48 = make_dispatch<48, 2>(),
                           d3_32 = make_dispatch<32, 3>(), d3_64 = make_dispatch<64, 3>(), d2_8 = make_dispatch<8, 2>(),
                           d2_16 = make_dispatch<16, 2>(), d2_32 = make_dispatch<32, 2>(),
                           d2_64 = make_dispatch<64, 2>();
-    if (D == 3) return N == 8 ? &d3_8 : N == 16 ? &d3_16 : N == 32 ? &d3_32 : N == 64 ? &d3_64 : nullptr;
-    return N == 8 ? &d2_8 : N == 16 ? &d2_16 : N == 32 ? &d2_32 : N == 64 ? &d2_64 : nullptr;
+    if (D == 3)
+        return N == 8 ? &d3_8 : N == 16 ? &d3_16 : N == 24 ? &d3_24 : N == 32 ? &d3_32 : N == 48 ? &d3_48
+             : N == 64 ? &d3_64 : nullptr;
+    return N == 8 ? &d2_8 : N == 16 ? &d2_16 : N == 24 ? &d2_24 : N == 32 ? &d2_32 : N == 48 ? &d2_48
+         : N == 64 ? &d2_64 : nullptr;
 }
 
 // Pipelined contraction: VC voxels per CTA, ring of STAGES bulk-copy stages
@@ -498,6 +509,7 @@ cudaError_t prepare_contract_vc() {
 cudaError_t prepare_contract() {
     cudaError_t e;
     if ((e = prepare_contract_vc<256>()) != cudaSuccess) return e;
+    if ((e = prepare_contract_vc<288>()) != cudaSuccess) return e;
     return prepare_contract_vc<64>();
 }
 
@@ -514,10 +526,11 @@ void launch_contract_vc(int kind, int T, const ConParams& cp, int n_tiles, int n
     }
 }
 
-// n is a power of two >= 64 for every supported grid; VC equals the voxel
-// chunk of the shifted-field layout, min(256, n)
-void launch_contract(int kind, int T, const ConParams& cp, int n_tiles, int nq, cudaStream_t st) {
-    if (cp.n >= 256) launch_contract_vc<256>(kind, T, cp, n_tiles, nq, st);
+// VC equals the voxel chunk of the shifted-field layout: 64 (the 8^2 grid),
+// 256 (other powers of two) or 288 (N = 24, 48)
+void launch_contract(int vch, int kind, int T, const ConParams& cp, int n_tiles, int nq, cudaStream_t st) {
+    if (vch == 256) launch_contract_vc<256>(kind, T, cp, n_tiles, nq, st);
+    else if (vch == 288) launch_contract_vc<288>(kind, T, cp, n_tiles, nq, st);
     else launch_contract_vc<64>(kind, T, cp, n_tiles, nq, st);
 }
 
@@ -613,7 +626,8 @@ boltz_status run_batched(boltz_grid_s* g, const float2* spectra, int n_inputs, c
                 if (c.tiles[k].empty()) continue;
                 cp.tiles = reinterpret_cast<const Tile*>(ws + plan.off_plan + c.off_tiles[k]);
                 ProfScope ps(g, BOLTZ_KCLASS_CONTRACT, st);
-                launch_contract(k, k == TILE_LIST ? 16 : c.tile_T, cp, (int)c.tiles[k].size(), nq, st);
+                launch_contract(voxel_chunk(g->N, g->D), k, k == TILE_LIST ? 16 : c.tile_T, cp,
+                                (int)c.tiles[k].size(), nq, st);
             }
             BZ_CUDA(cudaEventRecord(g->ev_ready[b], st));
             BZ_CUDA(cudaStreamWaitEvent(g->side, g->ev_ready[b], 0));
@@ -738,6 +752,10 @@ boltz_status ensure_twiddles(int device) {
     for (int t = 0; t < 128; ++t)
         tw[t] = make_float2((float)std::cos(-2.0 * kPi * t / 128), (float)std::sin(-2.0 * kPi * t / 128));
     if (cudaMemcpyToSymbol(c_twiddle, tw, sizeof(tw)) != cudaSuccess) return BOLTZ_ECUDA;
+    float2 tw48[48];
+    for (int t = 0; t < 48; ++t)
+        tw48[t] = make_float2((float)std::cos(-2.0 * kPi * t / 48), (float)std::sin(-2.0 * kPi * t / 48));
+    if (cudaMemcpyToSymbol(c_twiddle48, tw48, sizeof(tw48)) != cudaSuccess) return BOLTZ_ECUDA;
     done.insert(device);
     return BOLTZ_OK;
 }
@@ -1055,6 +1073,18 @@ boltz_status boltz_lowrank_step_host(boltz_grid g, const float* V_host, int r, f
     if (Q_host) BZ_CUDA(cudaMemcpyAsync(Q_host, dQ, size_t(r2) * nb, cudaMemcpyDeviceToHost, st));
     BZ_CUDA(cudaMemcpyAsync(T_host, dT, size_t(r) * r2 * 4, cudaMemcpyDeviceToHost, st));
     BZ_CUDA(cudaStreamSynchronize(st));
+    return BOLTZ_OK;
+}
+
+boltz_status boltz_moments(boltz_grid g, const float* Q, int n_fields, double* out, void* stream) {
+    if (!g || n_fields < 0) return BOLTZ_EINVAL;
+    if (n_fields == 0) return BOLTZ_OK;
+    if (!Q || !out) return BOLTZ_EINVAL;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const double dv = 2.0 * g->L / g->N;
+    if (g->D == 3) k_moments<3><<<n_fields, 256, 0, st>>>(Q, out, g->N, g->L, dv);
+    else k_moments<2><<<n_fields, 256, 0, st>>>(Q, out, g->N, g->L, dv);
+    BZ_CUDA(cudaGetLastError());
     return BOLTZ_OK;
 }
 

@@ -12,6 +12,7 @@
 namespace boltz_dev {
 
 __constant__ float2 c_twiddle[128];
+__constant__ float2 c_twiddle48[48];     // exp(-2 pi i t / 48), for the lengths 3 * 2^k
 
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
@@ -80,9 +81,60 @@ struct Radix2Stage {
 
 // In-place radix-2 decimation-in-time FFT of N (power of two, <= 128) points.
 template <int N, bool INV>
-__device__ __forceinline__ void fft_reg(float2 (&x)[N]) {
+__device__ __forceinline__ void fft_pow2(float2 (&x)[N]) {
     BitRevSwap<N, 0>::run(x);
     Radix2Stage<N, 1, INV>::run(x);
+}
+
+// a * exp(-+ 2 pi i t / 48), t in [0, 48) known at compile time.
+template <bool INV>
+__device__ __forceinline__ float2 twiddle48_mul(float2 a, int t) {
+    if (t == 0) return a;
+    if (t == 24) return make_float2(-a.x, -a.y);
+    if (t == 12) return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+    if (t == 36) return INV ? make_float2(a.y, -a.x) : make_float2(-a.y, a.x);
+    float2 w = c_twiddle48[t];
+    if (INV) w.y = -w.y;
+    return cmul(a, w);
+}
+
+// Mixed radix for N = 3 * 2^k (24, 48): one radix-3 decimation-in-time step
+// over three power-of-two transforms of the subsequences x[3m + r]:
+//   X[k + jM] = sum_r w3^{jr} W_N^{rk} Y_r[k],  M = N/3, w3 = exp(-+ 2 pi i/3).
+template <int N, bool INV>
+__device__ __forceinline__ void fft_radix3(float2 (&x)[N]) {
+    constexpr int M = N / 3;
+    static_assert(48 % N == 0, "radix-3 lengths are divisors of 48");
+    float2 y0[M], y1[M], y2[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+        y0[m] = x[3 * m];
+        y1[m] = x[3 * m + 1];
+        y2[m] = x[3 * m + 2];
+    }
+    fft_pow2<M, INV>(y0);
+    fft_pow2<M, INV>(y1);
+    fft_pow2<M, INV>(y2);
+    constexpr float S3 = 0.86602540378443864676f;          // sqrt(3)/2
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+        const float2 t1 = twiddle48_mul<INV>(y1[k], k * (48 / N));
+        const float2 t2 = twiddle48_mul<INV>(y2[k], 2 * k * (48 / N));
+        const float2 s = cadd(t1, t2), d = csub(t1, t2);
+        const float2 base = make_float2(y0[k].x - 0.5f * s.x, y0[k].y - 0.5f * s.y);
+        // forward: w3 t1 + w3^2 t2 = -s/2 - i (sqrt3/2) d ; inverse flips the sign of the i term
+        const float2 id = INV ? make_float2(-S3 * d.y, S3 * d.x) : make_float2(S3 * d.y, -S3 * d.x);
+        x[k] = cadd(y0[k], s);
+        x[k + M] = cadd(base, id);
+        x[k + 2 * M] = csub(base, id);
+    }
+}
+
+// FFT of a register-resident line of N points: powers of two up to 128, and 24, 48.
+template <int N, bool INV>
+__device__ __forceinline__ void fft_reg(float2 (&x)[N]) {
+    if constexpr (N % 3 == 0) fft_radix3<N, INV>(x);
+    else fft_pow2<N, INV>(x);
 }
 
 }  // namespace boltz_dev

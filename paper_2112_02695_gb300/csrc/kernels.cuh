@@ -38,7 +38,8 @@ struct Geo {
     static constexpr int COLS = (D == 3) ? N * NH : NH;          // columns incl. the half-axis Nyquist
     static constexpr int SMAX = D * H * H;                       // largest |k|^2
     // shifted fields are stored voxel-chunk-major (see shifted_field_row)
-    static constexpr int VCH = n < 256 ? n : 256;                // voxels per chunk
+    // voxels per chunk: 256 for power-of-two sizes, 288 (a whole number of rows) for N = 24, 48
+    static constexpr int VCH = n < 256 ? n : (N % 3 == 0 ? 288 : 256);
     static constexpr int NCH = n / VCH;                          // chunks per field
 };
 
@@ -246,7 +247,7 @@ __global__ void __launch_bounds__(Geo<N, D>::TPF * FPC) k_analysis(AnaParams P) 
             float2* r2 = s + (row + H) * RS;
 #pragma unroll
             for (int k = 0; k <= H; ++k) {
-                const float2 z = x[k], zc = x[(N - k) & (N - 1)];
+                const float2 z = x[k], zc = x[(N - k) % N];
                 // X1 = (Z_k + conj Z_{N-k}) / 2,  X2 = (Z_k - conj Z_{N-k}) / (2i)
                 r1[k] = make_float2(0.5f * (z.x + zc.x), 0.5f * (z.y - zc.y));
                 r2[k] = make_float2(0.5f * (z.y + zc.y), -0.5f * (z.x - zc.x));
@@ -336,7 +337,7 @@ struct ClusterGeo {
     static constexpr size_t SMEM = size_t(PP) * PS * sizeof(float2) + 3 * N * sizeof(float2);
     static constexpr int MINB = (SMEM <= (72u << 10)) ? 3 : 1;
     static_assert(size_t(PP) * N * RR * sizeof(float) <= size_t(PP) * PS * sizeof(float2), "staging fits");
-    static_assert((2 * NT) % N == 0 && (2 * NT) % 256 == 0 && PART_N % (2 * NT) == 0, "copy strides");
+    static_assert((2 * NT) % N == 0 && (2 * NT) % Geo<N, 3>::VCH == 0 && PART_N % (2 * NT) == 0, "copy strides");
 };
 
 // pointers to the plane buffers of every CTA of the cluster (index = rank)
@@ -506,7 +507,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(ClusterGeo<N, CL>::
             float2* r2 = smem + p0 * PS + (i1 + H) * RS;
 #pragma unroll
             for (int k = 0; k <= H; ++k) {
-                const float2 z = x[k], zc = x[(N - k) & (N - 1)];
+                const float2 z = x[k], zc = x[(N - k) % N];
                 r1[k] = make_float2(0.5f * (z.x + zc.x), 0.5f * (z.y - zc.y));
                 r2[k] = make_float2(0.5f * (z.y + zc.y), -0.5f * (z.x - zc.x));
             }
@@ -859,6 +860,49 @@ __global__ void __launch_bounds__(VC, 1) k_contract_pipe(ConParams C) {
 #pragma unroll
     for (int i = 0; i < NACC; ++i)
         if (i < cnt) Pq[(size_t)(tl.slot0 + i) * n] = acc[i];
+}
+
+// ------------------------------------------------------------------ FP64 moment sums
+// out[f][0] = dv^D sum_v Q_f(v), out[f][1+a] = dv^D sum_v v_a Q_f(v),
+// out[f][D+1] = dv^D sum_v |v|^2 Q_f(v)  (paper Sec. 1: mass, momentum,
+// energy), accumulated in FP64 with a fixed-order block reduction.
+template <int D>
+__global__ void __launch_bounds__(256) k_moments(const float* __restrict__ Q, double* __restrict__ out, int N,
+                                                 double L, double dv) {
+    const int f = blockIdx.x;
+    const int n = (D == 3) ? N * N * N : N * N;
+    const float* q = Q + (size_t)f * n;
+    double acc[D + 2];
+#pragma unroll
+    for (int i = 0; i < D + 2; ++i) acc[i] = 0.0;
+    for (int v = threadIdx.x; v < n; v += 256) {
+        const double x = (double)q[v];
+        int rem = v;
+        double r2 = 0.0;
+        double c[D];
+#pragma unroll
+        for (int a = D - 1; a >= 0; --a) {
+            c[a] = -L + (rem % N) * dv;
+            rem /= N;
+            r2 += c[a] * c[a];
+        }
+        acc[0] += x;
+#pragma unroll
+        for (int a = 0; a < D; ++a) acc[1 + a] += c[a] * x;
+        acc[D + 1] += r2 * x;
+    }
+    __shared__ double red[256];
+    const double vol = pow(dv, (double)D);
+    for (int i = 0; i < D + 2; ++i) {
+        red[threadIdx.x] = acc[i];
+        __syncthreads();
+        for (int s = 128; s > 0; s >>= 1) {
+            if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) out[(size_t)f * (D + 2) + i] = vol * red[0];
+        __syncthreads();
+    }
 }
 
 // ------------------------------------------------------------------ failure-path self-test

@@ -152,6 +152,34 @@ def test_bounded_wait_reports_timeout_and_context_survives(B):
     assert rel_err(Qg, Qo, s).max() < TOL
 
 
+def test_fp64_moments_and_conservation(B):
+    """FP64 moment sums on the GPU equal the oracle's moments of the same field,
+    and the GPU's Q(f,f) conserves mass, momentum and energy (R = 5 < 4L/(3+sqrt 2))."""
+    import torch
+    from oracle import collision as C
+    cfg = (32, 2, 8.0, 5.0, 1.0, 16, 32)
+    F = as_fp32(W.random_fields(32, 2, 8.0, 2, seed=6))
+    g = B.boltz_grid_init(*cfg)
+    try:
+        f = torch.tensor(F, dtype=torch.float32, device="cuda")
+        spec = B.boltz_spectrum(g, f)
+        Q = B.boltz_collide_batched(g, spec, [0, 0, 1], [0, 1, 0])
+        mom = B.boltz_moments(g, Q).cpu().numpy()
+        mom_f = B.boltz_moments(g, f).cpu().numpy()
+    finally:
+        g.close()
+    prob = C.Problem(N=32, d=2, L=8.0, R=5.0, gamma=1.0, n_rho=16, M=32)
+    assert np.max(np.abs(mom_f - C.moments(prob, F))) < 1e-12 * np.max(np.abs(mom_f))
+    _, Qo, s = oracle_collide(cfg, F, [(0, 0), (0, 1), (1, 0)])
+    # per-moment scale: dv^d sum |phi| |Q| for phi = 1, v_0, v_1, |v|^2
+    ax = -8.0 + np.arange(32) * 0.5
+    V0, V1 = np.meshgrid(ax, ax, indexing="ij")
+    phis = [np.ones_like(V0), np.abs(V0), np.abs(V1), V0 ** 2 + V1 ** 2]
+    scale = np.array([0.25 * np.sum(ph * np.abs(Qo).max(axis=0)) for ph in phis])
+    assert np.max(np.abs(mom[0]) / scale) < 1e-5                      # Q(f,f): all invariants
+    assert np.max(np.abs(mom[1] + mom[2]) / scale) < 1e-5             # symmetrised pair
+
+
 def test_lowrank_step_host_matches_device_path(B):
     import torch
     cfg = (16, 3, 8.0, 8.0, 1.0, 6, 14)
@@ -174,6 +202,18 @@ def test_64cube_against_oracle_small_quadrature(B):
     cfg = (64, 3, 10.0, 10.0, 1.0, 2, 6)
     F = as_fp32(W.random_fields(64, 3, 10.0, 2, seed=64))
     pairs = [(0, 1), (1, 0), (1, 1)]
+    Qg = gpu_collide(B, cfg, F, pairs)
+    _, Qo, s = oracle_collide(cfg, F, pairs)
+    assert rel_err(Qg, Qo, s).max() < TOL
+
+
+@pytest.mark.parametrize("N,d,r", [(24, 3, 5), (48, 3, 3), (24, 2, 17), (48, 2, 4)])
+def test_radix3_sizes_against_oracle(B, N, d, r):
+    """N = 24, 48 (mixed radix-3 transforms; 48^3 on 4-CTA clusters), r inputs,
+    all ordered pairs; r = 17 in 2D spans a 16-wide tile plus a list tail."""
+    cfg = (N, d, 8.0, 8.0, 0.0, 3, 6 if d == 3 else 12)
+    F = as_fp32(W.random_fields(N, d, 8.0, r, seed=N + r))
+    pairs = [(j, l) for j in range(r) for l in range(r)]
     Qg = gpu_collide(B, cfg, F, pairs)
     _, Qo, s = oracle_collide(cfg, F, pairs)
     assert rel_err(Qg, Qo, s).max() < TOL
