@@ -34,12 +34,17 @@ CONFIGS = {
     "c3": (32, 3, 8.0, 8.0, 1.0, 32, 38, "cells", 512),
     "c1": (32, 2, 8.0, 8.0, 0.0, 16, 16, "bkw", 1),
     "c4": (64, 3, 10.0, 10.0, 1.0, 32, 86, "pairs", 8),
+    "c5": (0, 0, 8.0, 8.0, 0.0, 0, 0, "mixed", 0),
 }
+# mixed batch: (N, d, gamma, M, r); R = L = 8, N_rho = N, bases seeded 2114 + i
+C5_GRIDS = [(24, 3, 0.0, 38, 32), (32, 3, 1.0, 38, 16), (48, 3, 0.0, 86, 8), (64, 3, 1.0, 86, 4),
+            (64, 2, 0.0, 16, 16), (48, 2, 1.0, 16, 8)]
 WORKLOAD_NAMES = {
     "c2": "lowrank pair batch: 3D 32^3 on [-8,8]^3, gamma=1, R=8, N_rho=32 x M=38, rank 16 -> 256 pairs Q(V_j,V_l) + r^3 projection",
     "c3": "full-tensor-grid batch: 512 normal-shock cells (Mach 3, d=3), 3D 32^3, gamma=1, R=8, N_rho=32 x M=38",
     "c1": "single homogeneous Q(f,f): 2D 32^2 on [-8,8]^2, Maxwell molecules, R=8, N_rho=16 x M=16, BKW t0=0.5",
     "c4": "precision-variant workload, FP32 path: 3D 64^3 on [-10,10]^3, gamma=1, R=10, N_rho=32 x M=86, rank 8 -> 64 pairs + r^3",
+    "c5": "uneven mixed batch in one captured CUDA graph: 3D N=24 r=32 M=38 g=0 | 3D N=32 r=16 M=38 g=1 | 3D N=48 r=8 M=86 g=0 | 3D N=64 r=4 M=86 g=1 | 2D N=64 r=16 M=16 g=0 | 2D N=48 r=8 M=16 g=1; N_rho=N, R=L=8; spectra + all r^2 pairs + r^3 per grid",
 }
 METRIC = "collision evals/s at 32^3 (batch 256) & % roofline; fast form vs plain FP32"
 L2_FLUSH_BYTES = 512 << 20
@@ -189,6 +194,56 @@ def host_cores():
 
 # ----------------------------------------------------------------------------- main
 
+def run_mixed(args, world, rank, local_rank):
+    """The mixed batch: all six grids' steps captured in one CUDA graph, replayed per step."""
+    import torch
+    from paper_2112_02695_gb300 import boltz as B
+    from paper_2112_02695_gb300 import workloads as W
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    grids, items = [], []
+    evals = 0
+    for i, (N, d, gamma, M, r) in enumerate(C5_GRIDS):
+        g = B.boltz_grid_init(N, d, 8.0, 8.0, gamma, N, M)
+        grids.append(g)
+        V = torch.tensor(np.asarray(W.hermite_maxwellian_basis(N, d, 8.0, r, seed=2114 + i), dtype=np.float32),
+                         device=dev)
+        pj = [j for j in range(r) for _ in range(r)]
+        pl = [l for _ in range(r) for l in range(r)]
+        items.append(dict(grid=g, fields=V, spectra=torch.empty((r,) + g.half_shape, dtype=torch.complex64, device=dev),
+                          pair_j=pj, pair_l=pl, Q_out=torch.empty((r * r,) + g.shape, device=dev), V=V,
+                          T_out=torch.empty((r, r, r), device=dev)))
+        evals += r * r
+    batch = B.boltz_batch_plan(items)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        B.boltz_batch_run(batch)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(local_rank) as clk:
+        for e0, e1 in evs:
+            flush.zero_()
+            e0.record()
+            B.boltz_batch_run(batch)
+            e1.record()
+        torch.cuda.synchronize()
+    for g in grids:
+        B.boltz_sync_status(g)
+    total_ms = sum(e0.elapsed_time(e1) for e0, e1 in evs)
+    kernels = B.boltz_batch_kernel_count(batch)
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": evals * args.steps / (total_ms / 1e3), "unit": "evals/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAMES["c5"], "evals_per_step": evals, "graph_kernels": kernels,
+                       "l2": "flushed between timed steps (512 MB write outside the timed events)"},
+            "gpu_launches": kernels * args.steps, "clocks": clk.summary()}))
+    batch.close()
+    for g in grids:
+        g.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -225,6 +280,10 @@ def main():
                              "sample": desc},
             "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         }))
+        return
+
+    if kind == "mixed":
+        run_mixed(args, world, rank, local_rank)
         return
 
     import torch

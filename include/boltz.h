@@ -170,6 +170,48 @@ boltz_status boltz_project(boltz_grid g, const float* V, int r, const float* Q, 
                            void* stream);
 
 /*
+ * Mixed batches under one CUDA graph.  A batch is a set of work items, each
+ * on its own grid (grids may differ in N, d_v, quadrature and kernel): an
+ * item optionally computes its input spectra from physical fields, then all
+ * its pairs, then optionally the r^3 projection.  boltz_batch_plan builds
+ * every item's plan, sizes and fills its grid's workspace, and captures all
+ * launches into one CUDA graph with one parallel branch per item (the items
+ * run concurrently); boltz_batch_run replays it with a single graph launch.
+ * Every pointer in the items is baked into the graph: the buffers must stay
+ * valid, and the pair lists unchanged, for as long as the batch is used; the
+ * host pair arrays are read only by boltz_batch_plan.  While a batch exists,
+ * its grids must not be used for other calls with different pair lists
+ * (their workspaces hold the batch's plans).
+ */
+typedef struct boltz_batch_s* boltz_batch;
+
+typedef struct {
+    boltz_grid grid;          /* grid of this item; one item per grid                       */
+    const float* fields;      /* device float32 [n_inputs][N^d] physical inputs, or NULL     */
+    const void* spectra;      /* device complex64 [n_inputs][half]: read, or written from
+                                 `fields` when fields != NULL                                */
+    int n_inputs;
+    const int32_t* pair_j;    /* HOST int32 [n_pairs]                                        */
+    const int32_t* pair_l;    /* HOST int32 [n_pairs]                                        */
+    int n_pairs;
+    float* Q_out;             /* device float32 [n_pairs][N^d]                               */
+    const float* V;           /* device float32 [r][N^d] basis to project on, or NULL        */
+    int r;                    /* projection rank; r*r == n_pairs when V != NULL              */
+    float* T_out;             /* device float32 [r][r][r] when V != NULL                     */
+} boltz_work;
+
+/* Errors: BOLTZ_EINVAL (bad item, two items on one grid, unknown form),
+ * BOLTZ_ENOMEM, BOLTZ_ECUDA (including a failed capture).  `form` applies to
+ * every item. */
+boltz_status boltz_batch_plan(boltz_batch* out, const boltz_work* items, int n_items, int form);
+/* Queues one replay of the batch's graph on `stream`. */
+boltz_status boltz_batch_run(boltz_batch b, void* stream);
+/* Number of kernel launches one replay performs. */
+boltz_status boltz_batch_kernel_count(boltz_batch b, int* n_kernels);
+/* Synchronises the device and frees the graph and its streams.  NULL is ignored. */
+boltz_status boltz_batch_destroy(boltz_batch b);
+
+/*
  * Collision invariants of results, in FP64 (paper Sec. 1: mass, momentum and
  * energy moments; Q conserves them up to quadrature accuracy):
  *   out[f][0]      = dv^d sum_v Q_f(v)

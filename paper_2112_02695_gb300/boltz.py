@@ -31,6 +31,7 @@ EXPORTED = (
     "boltz_spectrum", "boltz_collide_batched", "boltz_project", "boltz_lowrank_step_host",
     "boltz_host_quadrature", "boltz_workspace_size", "boltz_profile_enable", "boltz_profile_read",
     "boltz_project_noalloc", "boltz_sync_status", "boltz_selftest", "boltz_moments",
+    "boltz_batch_plan", "boltz_batch_run", "boltz_batch_kernel_count", "boltz_batch_destroy",
 )
 
 KERNEL_CLASSES = ("spectrum", "prep", "shift", "contract", "radial", "output", "project")
@@ -44,6 +45,14 @@ class BoltzError(RuntimeError):
 
 class _Options(ctypes.Structure):
     _fields_ = [("b", ctypes.c_double), ("workspace_max", ctypes.c_size_t)]
+
+
+class _Work(ctypes.Structure):
+    _fields_ = [("grid", ctypes.c_void_p), ("fields", ctypes.c_void_p), ("spectra", ctypes.c_void_p),
+                ("n_inputs", ctypes.c_int), ("pair_j", ctypes.POINTER(ctypes.c_int32)),
+                ("pair_l", ctypes.POINTER(ctypes.c_int32)), ("n_pairs", ctypes.c_int),
+                ("Q_out", ctypes.c_void_p), ("V", ctypes.c_void_p), ("r", ctypes.c_int),
+                ("T_out", ctypes.c_void_p)]
 
 
 def _load() -> ctypes.CDLL:
@@ -70,6 +79,10 @@ def _load() -> ctypes.CDLL:
         "boltz_profile_enable": ([vp, ctypes.c_int], ctypes.c_int),
         "boltz_sync_status": ([vp, vp], ctypes.c_int),
         "boltz_moments": ([vp, vp, ctypes.c_int, vp, vp], ctypes.c_int),
+        "boltz_batch_plan": ([ctypes.POINTER(vp), ctypes.POINTER(_Work), ctypes.c_int, ctypes.c_int], ctypes.c_int),
+        "boltz_batch_run": ([vp, vp], ctypes.c_int),
+        "boltz_batch_kernel_count": ([vp, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+        "boltz_batch_destroy": ([vp], ctypes.c_int),
         "boltz_selftest": ([vp, ctypes.c_int, vp], ctypes.c_int),
         "boltz_project_noalloc": ([vp, vp, ctypes.c_int, vp, vp, vp], ctypes.c_int),
         "boltz_profile_read": ([vp, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
@@ -295,3 +308,65 @@ def boltz_profile_read(grid: Grid, reset: bool = True):
     ms = (ctypes.c_double * n)()
     _check(_lib.boltz_profile_read(grid.handle, int(bool(reset)), la, ms), "boltz_profile_read")
     return {name: (int(la[i]), float(ms[i])) for i, name in enumerate(KERNEL_CLASSES)}
+
+
+class Batch:
+    """Owning wrapper of a boltz_batch (a captured CUDA graph over several grids).
+    Keeps references to every tensor and pair array the graph uses."""
+
+    def __init__(self, handle, keep):
+        self.handle = handle
+        self._keep = keep
+
+    def close(self):
+        if self.handle:
+            _lib.boltz_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def boltz_batch_plan(items, form: int = BOLTZ_FORM_BATCHED) -> Batch:
+    """items: list of dicts with keys grid, spectra, pair_j, pair_l, Q_out and
+    optionally fields, V, T_out (torch CUDA tensors; V/T_out for the projection)."""
+    n = len(items)
+    arr = (_Work * n)()
+    keep = []
+    i32p = ctypes.POINTER(ctypes.c_int32)
+    for i, it in enumerate(items):
+        pj, pl = _pairs(it["pair_j"], it["pair_l"])
+        keep += [pj, pl, it]
+        w = arr[i]
+        w.grid = it["grid"].handle
+        w.fields = _dev_ptr(it["fields"], "float32", "fields") if it.get("fields") is not None else None
+        w.spectra = _dev_ptr(it["spectra"], "complex64", "spectra")
+        w.n_inputs = it["spectra"].shape[0]
+        w.pair_j = pj.ctypes.data_as(i32p)
+        w.pair_l = pl.ctypes.data_as(i32p)
+        w.n_pairs = len(pj)
+        w.Q_out = _dev_ptr(it["Q_out"], "float32", "Q_out")
+        if it.get("V") is not None:
+            w.V = _dev_ptr(it["V"], "float32", "V")
+            w.r = it["V"].shape[0]
+            w.T_out = _dev_ptr(it["T_out"], "float32", "T_out")
+    h = ctypes.c_void_p()
+    _check(_lib.boltz_batch_plan(ctypes.byref(h), arr, n, int(form)), "boltz_batch_plan")
+    return Batch(h, keep)
+
+
+def boltz_batch_run(batch: Batch, stream=None):
+    _check(_lib.boltz_batch_run(batch.handle, _stream_ptr(stream)), "boltz_batch_run")
+
+
+def boltz_batch_kernel_count(batch: Batch) -> int:
+    k = ctypes.c_int()
+    _check(_lib.boltz_batch_kernel_count(batch.handle, ctypes.byref(k)), "boltz_batch_kernel_count")
+    return k.value
+
+
+def boltz_batch_destroy(batch: Batch):
+    batch.close()

@@ -543,25 +543,41 @@ boltz_status check_pairs(int n_inputs, const int32_t* pj, const int32_t* pl, int
     return BOLTZ_OK;
 }
 
-boltz_status run_batched(boltz_grid_s* g, const float2* spectra, int n_inputs, const int32_t* pj, const int32_t* pl,
-                         int n_pairs, float* Q_out, int form, cudaStream_t st) {
+// Makes the grid's cached plan the one for this batch (building, sizing the
+// workspace to at least `min_ws` bytes and uploading the descriptors when the
+// pair list changed).  Synchronous; never called during stream capture.
+boltz_status prepare_plan(boltz_grid_s* g, int n_inputs, const int32_t* pj, const int32_t* pl, int n_pairs, int form,
+                          size_t min_ws, cudaStream_t st) {
     const bool same = g->plan_uploaded && form == g->last_form && n_inputs == g->last_n_inputs &&
                       (int)g->last_j.size() == n_pairs &&
                       std::equal(pj, pj + n_pairs, g->last_j.begin()) &&
                       std::equal(pl, pl + n_pairs, g->last_l.begin());
-    if (!same) {
-        Plan plan;
-        boltz_status s = build_plan(g, n_inputs, pj, pl, n_pairs, form, plan);
-        if (s != BOLTZ_OK) return s;
-        if ((s = ensure_workspace(g, plan.total, st)) != BOLTZ_OK) return s;
-        if ((s = upload_plan(g, plan, st)) != BOLTZ_OK) return s;
-        g->last_plan = std::move(plan);
-        g->last_j.assign(pj, pj + n_pairs);
-        g->last_l.assign(pl, pl + n_pairs);
-        g->last_form = form;
-        g->last_n_inputs = n_inputs;
+    boltz_status s;
+    if (same) {
+        if (g->ws_cap >= min_ws) return BOLTZ_OK;
+        // a larger workspace loses the uploaded descriptors: upload them again
+        if ((s = ensure_workspace(g, min_ws, st)) != BOLTZ_OK) return s;
+        if ((s = upload_plan(g, g->last_plan, st)) != BOLTZ_OK) return s;
         g->plan_uploaded = true;
+        return BOLTZ_OK;
     }
+    Plan plan;
+    if ((s = build_plan(g, n_inputs, pj, pl, n_pairs, form, plan)) != BOLTZ_OK) return s;
+    if ((s = ensure_workspace(g, std::max(plan.total, min_ws), st)) != BOLTZ_OK) return s;
+    if ((s = upload_plan(g, plan, st)) != BOLTZ_OK) return s;
+    g->last_plan = std::move(plan);
+    g->last_j.assign(pj, pj + n_pairs);
+    g->last_l.assign(pl, pl + n_pairs);
+    g->last_form = form;
+    g->last_n_inputs = n_inputs;
+    g->plan_uploaded = true;
+    return BOLTZ_OK;
+}
+
+boltz_status run_batched(boltz_grid_s* g, const float2* spectra, int n_inputs, const int32_t* pj, const int32_t* pl,
+                         int n_pairs, float* Q_out, int form, cudaStream_t st) {
+    boltz_status s0 = prepare_plan(g, n_inputs, pj, pl, n_pairs, form, 0, st);
+    if (s0 != BOLTZ_OK) return s0;
     const Plan& plan = g->last_plan;
     const Dispatch* dp = dispatch_for(g->N, g->D);
     char* ws = g->d_ws;
@@ -758,6 +774,31 @@ boltz_status ensure_twiddles(int device) {
     if (cudaMemcpyToSymbol(c_twiddle48, tw48, sizeof(tw48)) != cudaSuccess) return BOLTZ_ECUDA;
     done.insert(device);
     return BOLTZ_OK;
+}
+
+}  // namespace
+
+// ==================================================================== batches
+
+struct boltz_batch_s {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t origin = nullptr;
+    std::vector<cudaStream_t> branch;
+    std::vector<cudaEvent_t> events;
+    int n_kernels = 0;
+};
+
+namespace {
+
+void destroy_batch(boltz_batch_s* b) {
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (auto s : b->branch) cudaStreamDestroy(s);
+    for (auto e : b->events) cudaEventDestroy(e);
+    if (b->origin) cudaStreamDestroy(b->origin);
+    delete b;
 }
 
 }  // namespace
@@ -1085,6 +1126,114 @@ boltz_status boltz_moments(boltz_grid g, const float* Q, int n_fields, double* o
     if (g->D == 3) k_moments<3><<<n_fields, 256, 0, st>>>(Q, out, g->N, g->L, dv);
     else k_moments<2><<<n_fields, 256, 0, st>>>(Q, out, g->N, g->L, dv);
     BZ_CUDA(cudaGetLastError());
+    return BOLTZ_OK;
+}
+
+boltz_status boltz_batch_plan(boltz_batch* out, const boltz_work* items, int n_items, int form) {
+    if (!out || !items || n_items <= 0 || (form != BOLTZ_FORM_BATCHED && form != BOLTZ_FORM_PLAIN))
+        return BOLTZ_EINVAL;
+    for (int i = 0; i < n_items; ++i) {
+        const boltz_work& w = items[i];
+        if (!w.grid || !w.spectra || !w.Q_out || w.n_pairs <= 0) return BOLTZ_EINVAL;
+        boltz_status s = check_pairs(w.n_inputs, w.pair_j, w.pair_l, w.n_pairs);
+        if (s != BOLTZ_OK) return s;
+        if (w.V && (!w.T_out || w.r < 1 || w.r > 64 || w.r * w.r != w.n_pairs)) return BOLTZ_EINVAL;
+        for (int k = 0; k < i; ++k)
+            if (items[k].grid == w.grid) return BOLTZ_EINVAL;      // one item per grid
+    }
+    boltz_batch_s* b = new (std::nothrow) boltz_batch_s();
+    if (!b) return BOLTZ_ENOMEM;
+    auto fail = [&](boltz_status st) {
+        destroy_batch(b);
+        return st;
+    };
+    if (cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking) != cudaSuccess) return fail(BOLTZ_ECUDA);
+    // plans and workspaces first: nothing may allocate or synchronise during capture
+    for (int i = 0; i < n_items; ++i) {
+        const boltz_work& w = items[i];
+        const size_t proj = w.V ? align_up(0, 256) + project_partial_bytes(w.r) : 0;
+        boltz_status s = prepare_plan(w.grid, w.n_inputs, w.pair_j, w.pair_l, w.n_pairs, form, 0, b->origin);
+        if (s != BOLTZ_OK) return fail(s);
+        const size_t need = align_up(w.grid->last_plan.plan_bytes, 256) + proj;
+        if (w.grid->ws_cap < need) {
+            if ((s = prepare_plan(w.grid, w.n_inputs, w.pair_j, w.pair_l, w.n_pairs, form, need, b->origin)) !=
+                BOLTZ_OK)
+                return fail(s);
+        }
+        cudaStream_t br;
+        cudaEvent_t ev;
+        if (cudaStreamCreateWithFlags(&br, cudaStreamNonBlocking) != cudaSuccess) return fail(BOLTZ_ECUDA);
+        b->branch.push_back(br);
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return fail(BOLTZ_ECUDA);
+        b->events.push_back(ev);
+    }
+    cudaEvent_t fork;
+    if (cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess) return fail(BOLTZ_ECUDA);
+    b->events.push_back(fork);
+    if (cudaStreamSynchronize(b->origin) != cudaSuccess) return fail(BOLTZ_ECUDA);
+    // capture: one branch per item, forked from and joined to the origin stream
+    if (cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return fail(BOLTZ_ECUDA);
+    boltz_status cs = BOLTZ_OK;
+    if (cudaEventRecord(fork, b->origin) != cudaSuccess) cs = BOLTZ_ECUDA;
+    for (int i = 0; i < n_items && cs == BOLTZ_OK; ++i) {
+        const boltz_work& w = items[i];
+        boltz_grid_s* g = w.grid;
+        const bool prof = g->prof_on;
+        long long saved[BOLTZ_KCLASS_COUNT];
+        std::memcpy(saved, g->launches, sizeof(saved));
+        g->prof_on = false;
+        cudaStream_t br = b->branch[i];
+        if (cudaStreamWaitEvent(br, fork, 0) != cudaSuccess) cs = BOLTZ_ECUDA;
+        if (cs == BOLTZ_OK && w.fields) cs = boltz_spectrum(g, w.fields, w.n_inputs, const_cast<void*>(w.spectra), br);
+        if (cs == BOLTZ_OK)
+            cs = run_batched(g, reinterpret_cast<const float2*>(w.spectra), w.n_inputs, w.pair_j, w.pair_l,
+                             w.n_pairs, w.Q_out, form, br);
+        if (cs == BOLTZ_OK && w.V) {
+            float* partial = reinterpret_cast<float*>(g->d_ws + align_up(g->last_plan.plan_bytes, 256));
+            cs = run_project(g, w.V, w.r, w.Q_out, w.T_out, partial, br);
+        }
+        if (cs == BOLTZ_OK && (cudaEventRecord(b->events[i], br) != cudaSuccess ||
+                               cudaStreamWaitEvent(b->origin, b->events[i], 0) != cudaSuccess))
+            cs = BOLTZ_ECUDA;
+        g->prof_on = prof;
+        std::memcpy(g->launches, saved, sizeof(saved));
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(b->origin, &graph);
+    b->graph = graph;
+    if (cs != BOLTZ_OK || ec != cudaSuccess) {
+        (void)cudaGetLastError();
+        return fail(cs != BOLTZ_OK ? cs : BOLTZ_ECUDA);
+    }
+    if (cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess) return fail(BOLTZ_ECUDA);
+    size_t nn = 0;
+    if (cudaGraphGetNodes(b->graph, nullptr, &nn) != cudaSuccess) return fail(BOLTZ_ECUDA);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (nn && cudaGraphGetNodes(b->graph, nodes.data(), &nn) != cudaSuccess) return fail(BOLTZ_ECUDA);
+    for (auto nd : nodes) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++b->n_kernels;
+    }
+    *out = b;
+    return BOLTZ_OK;
+}
+
+boltz_status boltz_batch_run(boltz_batch b, void* stream) {
+    if (!b || !b->exec) return BOLTZ_EINVAL;
+    BZ_CUDA(cudaGraphLaunch(b->exec, reinterpret_cast<cudaStream_t>(stream)));
+    return BOLTZ_OK;
+}
+
+boltz_status boltz_batch_kernel_count(boltz_batch b, int* n_kernels) {
+    if (!b || !n_kernels) return BOLTZ_EINVAL;
+    *n_kernels = b->n_kernels;
+    return BOLTZ_OK;
+}
+
+boltz_status boltz_batch_destroy(boltz_batch b) {
+    if (!b) return BOLTZ_OK;
+    cudaDeviceSynchronize();
+    destroy_batch(b);
     return BOLTZ_OK;
 }
 
