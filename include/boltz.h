@@ -170,6 +170,24 @@ boltz_status boltz_project(boltz_grid g, const float* V, int r, const float* Q, 
                            void* stream);
 
 /*
+ * Autotuner of the batch schedule.  The tunable is the device memory budget
+ * for the shifted fields of one radial block (48, 96, 192 or 384 MB): it
+ * sets how many inputs share a chunk (so how often shifted fields are
+ * recomputed) and how many radial nodes one launch covers (so how long the
+ * launch chain is and whether the fields stay in the 126 MB L2).  Each
+ * candidate runs the given batch three times on `stream` (the first untimed)
+ * and the fastest is kept in the grid for later calls.  With a cache path,
+ * the choice is read from and written to a JSON file keyed by
+ * (N, d_v, M, N_rho, n_inputs, n_pairs, form, SM count); a cached key skips
+ * the timing.  Q_scratch: device float32 [n_pairs][N^d], overwritten.
+ * chosen_mb (HOST, may be NULL) receives the budget.  Synchronises `stream`.
+ * Errors: BOLTZ_EINVAL, BOLTZ_ENOMEM (no candidate fits), BOLTZ_ECUDA.
+ */
+boltz_status boltz_autotune(boltz_grid g, const void* spectra, int n_inputs, const int32_t* pair_j,
+                            const int32_t* pair_l, int n_pairs, float* Q_scratch, int form, const char* cache_path,
+                            void* stream, int* chosen_mb);
+
+/*
  * Mixed batches under one CUDA graph.  A batch is a set of work items, each
  * on its own grid (grids may differ in N, d_v, quadrature and kernel): an
  * item optionally computes its input spectra from physical fields, then all

@@ -32,6 +32,7 @@ EXPORTED = (
     "boltz_host_quadrature", "boltz_workspace_size", "boltz_profile_enable", "boltz_profile_read",
     "boltz_project_noalloc", "boltz_sync_status", "boltz_selftest", "boltz_moments",
     "boltz_batch_plan", "boltz_batch_run", "boltz_batch_kernel_count", "boltz_batch_destroy",
+    "boltz_autotune",
 )
 
 KERNEL_CLASSES = ("spectrum", "prep", "shift", "contract", "radial", "output", "project")
@@ -81,6 +82,8 @@ def _load() -> ctypes.CDLL:
         "boltz_moments": ([vp, vp, ctypes.c_int, vp, vp], ctypes.c_int),
         "boltz_batch_plan": ([ctypes.POINTER(vp), ctypes.POINTER(_Work), ctypes.c_int, ctypes.c_int], ctypes.c_int),
         "boltz_batch_run": ([vp, vp], ctypes.c_int),
+        "boltz_autotune": ([vp, vp, ctypes.c_int, i32p, i32p, ctypes.c_int, vp, ctypes.c_int, ctypes.c_char_p, vp,
+                            ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
         "boltz_batch_kernel_count": ([vp, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
         "boltz_batch_destroy": ([vp], ctypes.c_int),
         "boltz_selftest": ([vp, ctypes.c_int, vp], ctypes.c_int),
@@ -308,6 +311,24 @@ def boltz_profile_read(grid: Grid, reset: bool = True):
     ms = (ctypes.c_double * n)()
     _check(_lib.boltz_profile_read(grid.handle, int(bool(reset)), la, ms), "boltz_profile_read")
     return {name: (int(la[i]), float(ms[i])) for i, name in enumerate(KERNEL_CLASSES)}
+
+
+def boltz_autotune(grid: Grid, spectra, pair_j, pair_l, Q_scratch=None, form: int = BOLTZ_FORM_BATCHED,
+                   cache_path: str | None = None, stream=None) -> int:
+    """Time the shifted-field budget candidates for this batch, keep the fastest
+    in the grid and return it (MB); with cache_path, reuse/record the choice."""
+    import torch
+    pj, pl = _pairs(pair_j, pair_l)
+    if Q_scratch is None:
+        Q_scratch = torch.empty((len(pj),) + grid.shape, dtype=torch.float32, device=spectra.device)
+    mb = ctypes.c_int()
+    i32p = ctypes.POINTER(ctypes.c_int32)
+    _check(_lib.boltz_autotune(grid.handle, _dev_ptr(spectra, "complex64", "spectra"), spectra.shape[0],
+                               pj.ctypes.data_as(i32p), pl.ctypes.data_as(i32p), len(pj),
+                               _dev_ptr(Q_scratch, "float32", "Q_scratch"), int(form),
+                               cache_path.encode() if cache_path else None, _stream_ptr(stream), ctypes.byref(mb)),
+           "boltz_autotune")
+    return mb.value
 
 
 class Batch:

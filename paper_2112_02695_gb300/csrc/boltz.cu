@@ -14,6 +14,7 @@
 #include <mutex>
 #include <new>
 #include <set>
+#include <string>
 #include <utility>
 #include <vector>
 
@@ -78,6 +79,7 @@ struct boltz_grid_s {
     // workspace
     char* d_ws = nullptr;
     size_t ws_cap = 0, ws_max = kDefaultWorkspace;
+    size_t field_budget = kFieldBudget;   // shifted-field bytes per radial block (autotuned)
     // last plan (reused when the same pair list comes back)
     std::vector<int32_t> last_j, last_l;
     int last_form = -1, last_n_inputs = -1;
@@ -121,7 +123,7 @@ boltz_status build_plan(const boltz_grid_s* g, int n_inputs, const int32_t* pj, 
     // inputs per chunk: enough for one radial node's shifted fields to fit the L2-sized
     // budget, but never fewer than 16 (a rank-16 basis stays in one chunk, so its
     // shifted fields are computed once) nor more than 64
-    int nc_cap = (int)std::max<size_t>(16, kFieldBudget / (field_bytes * g->M));
+    int nc_cap = (int)std::max<size_t>(16, g->field_budget / (field_bytes * g->M));
     nc_cap = std::min(nc_cap, 64);
     if (form == BOLTZ_FORM_PLAIN) {
         const int E = std::max(1, nc_cap / 2);
@@ -274,7 +276,7 @@ boltz_status build_plan(const boltz_grid_s* g, int n_inputs, const int32_t* pj, 
         plan.max_U = std::max(plan.max_U, c.U);
     }
     const size_t per_node = size_t(g->M) * plan.max_nc * field_bytes + size_t(plan.max_U) * field_bytes;
-    plan.nq = (int)std::max<size_t>(1, std::min<size_t>(g->n_rho, kFieldBudget / std::max<size_t>(per_node, 1)));
+    plan.nq = (int)std::max<size_t>(1, std::min<size_t>(g->n_rho, g->field_budget / std::max<size_t>(per_node, 1)));
     // device plan descriptors
     size_t off = 0;
     for (auto& c : plan.chunks) {
@@ -778,6 +780,63 @@ boltz_status ensure_twiddles(int device) {
 
 }  // namespace
 
+// ==================================================================== autotuning
+
+namespace {
+
+// Candidate budgets (MB) for the shifted fields of one radial block: they set
+// how many inputs share a chunk and how many radial nodes a launch covers.
+const int kBudgetCandidatesMB[] = {48, 96, 192, 384};
+
+// Minimal persistent cache: one JSON object {"key": value, ...} of integers.
+std::map<std::string, long> read_cache(const char* path) {
+    std::map<std::string, long> m;
+    FILE* f = path ? std::fopen(path, "r") : nullptr;
+    if (!f) return m;
+    std::string text;
+    char buf[4096];
+    size_t k;
+    while ((k = std::fread(buf, 1, sizeof(buf), f)) > 0) text.append(buf, k);
+    std::fclose(f);
+    size_t pos = 0;
+    while ((pos = text.find('"', pos)) != std::string::npos) {
+        const size_t end = text.find('"', pos + 1);
+        if (end == std::string::npos) break;
+        const std::string key = text.substr(pos + 1, end - pos - 1);
+        const size_t colon = text.find(':', end);
+        if (colon == std::string::npos) break;
+        m[key] = std::strtol(text.c_str() + colon + 1, nullptr, 10);
+        pos = text.find_first_of(",}", colon);
+        if (pos == std::string::npos) break;
+    }
+    return m;
+}
+
+bool write_cache(const char* path, const std::map<std::string, long>& m) {
+    if (!path) return false;
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE* f = std::fopen(tmp.c_str(), "w");
+    if (!f) return false;
+    std::fprintf(f, "{");
+    bool first = true;
+    for (auto& kv : m) {
+        std::fprintf(f, "%s\n  \"%s\": %ld", first ? "" : ",", kv.first.c_str(), kv.second);
+        first = false;
+    }
+    std::fprintf(f, "\n}\n");
+    std::fclose(f);
+    return std::rename(tmp.c_str(), path) == 0;
+}
+
+std::string tune_key(const boltz_grid_s* g, int n_inputs, int n_pairs, int form, int sms) {
+    char k[256];
+    std::snprintf(k, sizeof(k), "N%d_d%d_M%d_nrho%d_in%d_pairs%d_form%d_sm%d", g->N, g->D, g->M, g->n_rho,
+                  n_inputs, n_pairs, form, sms);
+    return k;
+}
+
+}  // namespace
+
 // ==================================================================== batches
 
 struct boltz_batch_s {
@@ -1234,6 +1293,66 @@ boltz_status boltz_batch_destroy(boltz_batch b) {
     if (!b) return BOLTZ_OK;
     cudaDeviceSynchronize();
     destroy_batch(b);
+    return BOLTZ_OK;
+}
+
+boltz_status boltz_autotune(boltz_grid g, const void* spectra, int n_inputs, const int32_t* pair_j,
+                            const int32_t* pair_l, int n_pairs, float* Q_scratch, int form, const char* cache_path,
+                            void* stream, int* chosen_mb) {
+    if (!g || (form != BOLTZ_FORM_BATCHED && form != BOLTZ_FORM_PLAIN)) return BOLTZ_EINVAL;
+    boltz_status s = check_pairs(n_inputs, pair_j, pair_l, n_pairs);
+    if (s != BOLTZ_OK) return s;
+    if (n_pairs == 0 || !spectra || !Q_scratch) return BOLTZ_EINVAL;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device) != cudaSuccess) return BOLTZ_ECUDA;
+    const std::string key = tune_key(g, n_inputs, n_pairs, form, sms);
+    auto cache = read_cache(cache_path);
+    auto it = cache.find(key);
+    long best_mb = -1;
+    if (it != cache.end() && it->second > 0) {
+        best_mb = it->second;
+    } else {
+        cudaEvent_t e0, e1;
+        if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return BOLTZ_ECUDA;
+        float best_ms = 1e30f;
+        for (int mb : kBudgetCandidatesMB) {
+            g->field_budget = size_t(mb) << 20;
+            g->plan_uploaded = false;
+            float ms_sum = 0.f;
+            boltz_status rs = BOLTZ_OK;
+            for (int rep = 0; rep < 3 && rs == BOLTZ_OK; ++rep) {         // rep 0 warms up
+                cudaEventRecord(e0, st);
+                rs = run_batched(g, reinterpret_cast<const float2*>(spectra), n_inputs, pair_j, pair_l, n_pairs,
+                                 Q_scratch, form, st);
+                cudaEventRecord(e1, st);
+                if (cudaEventSynchronize(e1) != cudaSuccess) rs = BOLTZ_ECUDA;
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0) ms_sum += ms;
+            }
+            if (rs == BOLTZ_ENOMEM) continue;                               // candidate too large
+            if (rs != BOLTZ_OK) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return rs;
+            }
+            if (ms_sum < best_ms) {
+                best_ms = ms_sum;
+                best_mb = mb;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (best_mb < 0) return BOLTZ_ENOMEM;
+        if (cache_path) {
+            cache[key] = best_mb;
+            write_cache(cache_path, cache);
+        }
+    }
+    g->field_budget = size_t(best_mb) << 20;
+    g->plan_uploaded = false;
+    if (chosen_mb) *chosen_mb = (int)best_mb;
     return BOLTZ_OK;
 }
 

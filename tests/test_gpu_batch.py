@@ -74,3 +74,29 @@ def test_batch_rejects_two_items_on_one_grid():
         assert ei.value.status == B.BOLTZ_EINVAL
     finally:
         g.close()
+
+
+def test_autotune_picks_a_candidate_and_caches_it(tmp_path):
+    import json
+    import torch
+    B = require_gpu()
+    cfg = (16, 3, 8.0, 8.0, 1.0, 6, 14)
+    V = as_fp32(W.hermite_maxwellian_basis(16, 3, 8.0, 6, seed=9))
+    pairs = [(j, l) for j in range(6) for l in range(6)]
+    g = B.boltz_grid_init(*cfg)
+    try:
+        f = torch.tensor(V, dtype=torch.float32, device="cuda")
+        spec = B.boltz_spectrum(g, f)
+        before = B.boltz_collide_batched(g, spec, [p[0] for p in pairs], [p[1] for p in pairs]).clone()
+        cache = str(tmp_path / "tune.json")
+        mb = B.boltz_autotune(g, spec, [p[0] for p in pairs], [p[1] for p in pairs], cache_path=cache)
+        assert mb in (48, 96, 192, 384)
+        entries = json.load(open(cache))
+        assert list(entries.values()) == [mb]
+        assert B.boltz_autotune(g, spec, [p[0] for p in pairs], [p[1] for p in pairs], cache_path=cache) == mb
+        after = B.boltz_collide_batched(g, spec, [p[0] for p in pairs], [p[1] for p in pairs])
+        torch.cuda.synchronize()
+        scale = before.abs().max().item()
+        assert (after - before).abs().max().item() <= 1e-6 * scale
+    finally:
+        g.close()
