@@ -38,13 +38,13 @@ CONFIGS = {
 }
 # mixed batch: (N, d, gamma, M, r); R = L = 8, N_rho = N, bases seeded 2114 + i
 C5_GRIDS = [(24, 3, 0.0, 38, 32), (32, 3, 1.0, 38, 16), (48, 3, 0.0, 86, 8), (64, 3, 1.0, 86, 4),
-            (64, 2, 0.0, 16, 16), (48, 2, 1.0, 16, 8)]
+            (64, 2, 0.0, 16, 16), (128, 2, 1.0, 16, 8)]
 WORKLOAD_NAMES = {
     "c2": "lowrank pair batch: 3D 32^3 on [-8,8]^3, gamma=1, R=8, N_rho=32 x M=38, rank 16 -> 256 pairs Q(V_j,V_l) + r^3 projection",
     "c3": "full-tensor-grid batch: 512 normal-shock cells (Mach 3, d=3), 3D 32^3, gamma=1, R=8, N_rho=32 x M=38",
     "c1": "single homogeneous Q(f,f): 2D 32^2 on [-8,8]^2, Maxwell molecules, R=8, N_rho=16 x M=16, BKW t0=0.5",
     "c4": "precision-variant workload, FP32 path: 3D 64^3 on [-10,10]^3, gamma=1, R=10, N_rho=32 x M=86, rank 8 -> 64 pairs + r^3",
-    "c5": "uneven mixed batch in one captured CUDA graph: 3D N=24 r=32 M=38 g=0 | 3D N=32 r=16 M=38 g=1 | 3D N=48 r=8 M=86 g=0 | 3D N=64 r=4 M=86 g=1 | 2D N=64 r=16 M=16 g=0 | 2D N=48 r=8 M=16 g=1; N_rho=N, R=L=8; spectra + all r^2 pairs + r^3 per grid",
+    "c5": "uneven mixed batch in one captured CUDA graph: 3D N=24 r=32 M=38 g=0 | 3D N=32 r=16 M=38 g=1 | 3D N=48 r=8 M=86 g=0 | 3D N=64 r=4 M=86 g=1 | 2D N=64 r=16 M=16 g=0 | 2D N=128 r=8 M=16 g=1; N_rho=N, R=L=8; spectra + all r^2 pairs + r^3 per grid",
 }
 METRIC = "collision evals/s at 32^3 (batch 256) & % roofline; fast form vs plain FP32"
 L2_FLUSH_BYTES = 512 << 20

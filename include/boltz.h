@@ -105,7 +105,7 @@ const char* boltz_status_string(boltz_status s);
  * kernel exponent gamma, N_rho Gauss-Legendre radial nodes on [0, R] and M
  * directions (paper Sec. 2.1: uniform grid, fast spectral collision solver).
  *   N      in {8, 16, 24, 32, 48, 64} for both d_v = 2 and d_v = 3 (24 and 48 use
- *          a mixed radix-3 transform)
+ *          a mixed radix-3 transform), and 128 for d_v = 2
  *   d_v    2 or 3
  *   M      d_v = 2: even, 2..256 (uniform circle rule theta_p = 2 pi p / M);
  *          d_v = 3: one of 6, 14, 26, 38, 50, 86 (octahedral rules of design

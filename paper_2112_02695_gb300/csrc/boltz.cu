@@ -22,6 +22,7 @@
 #include "kernels.cuh"
 #include "quadrature.hpp"
 #include "tc_kernels.cuh"
+#include "wide2d.cuh"
 
 using namespace boltz_dev;
 
@@ -101,7 +102,7 @@ namespace {
 
 bool supported_shape(int N, int D) {
     if (D != 2 && D != 3) return false;
-    return N == 8 || N == 16 || N == 24 || N == 32 || N == 48 || N == 64;
+    return N == 8 || N == 16 || N == 24 || N == 32 || N == 48 || N == 64 || (D == 2 && N == 128);
 }
 
 // voxels per chunk of the shifted-field layout (must match Geo<N, D>::VCH)
@@ -400,9 +401,18 @@ struct Launch {
     static constexpr int BLOCK = G::TPF * FPC;
     static constexpr size_t SMEM = size_t(G::SMEM_F) * FPC * sizeof(float2);
 
+    // 2D N = 128: lines split over 4-lane groups
+    static constexpr bool WIDE = (D == 2 && N == 128);
+
     static cudaError_t prepare() {
         cudaError_t e;
-        if constexpr (CL > 0) {
+        if constexpr (WIDE) {
+            if ((e = set_smem(k_synth_w128<SYN_SHIFT>, kWSMEM)) != cudaSuccess) return e;
+            if ((e = set_smem(k_synth_w128<SYN_PREP>, kWSMEM)) != cudaSuccess) return e;
+            if ((e = set_smem(k_analysis_w128<ANA_SPECTRUM>, kWSMEM)) != cudaSuccess) return e;
+            if ((e = set_smem(k_analysis_w128<ANA_ACCUM>, kWSMEM)) != cudaSuccess) return e;
+            return set_smem(k_output_w128, kWSMEM);
+        } else if constexpr (CL > 0) {
             using CG = ClusterGeo<N, CL>;
             if ((e = set_smem(k_synth_cl<N, CL, SYN_SHIFT>, CG::SMEM)) != cudaSuccess) return e;
             if ((e = set_smem(k_synth_cl<N, CL, SYN_PREP>, CG::SMEM)) != cudaSuccess) return e;
@@ -418,7 +428,11 @@ struct Launch {
         }
     }
     static void synth(const SynParams& p, int mode, cudaStream_t st) {
-        if constexpr (CL > 0) {
+        if constexpr (WIDE) {
+            const int grid = (p.n_fields + kWFPC - 1) / kWFPC;
+            if (mode == SYN_SHIFT) k_synth_w128<SYN_SHIFT><<<grid, kWTPF * kWFPC, kWSMEM, st>>>(p);
+            else k_synth_w128<SYN_PREP><<<grid, kWTPF * kWFPC, kWSMEM, st>>>(p);
+        } else if constexpr (CL > 0) {
             using CG = ClusterGeo<N, CL>;
             if (mode == SYN_SHIFT)
                 k_synth_cl<N, CL, SYN_SHIFT><<<CL * p.n_fields, CG::NT, CG::SMEM, st>>>(p);
@@ -433,7 +447,11 @@ struct Launch {
         }
     }
     static void analysis(const AnaParams& p, int mode, cudaStream_t st) {
-        if constexpr (CL > 0) {
+        if constexpr (WIDE) {
+            const int grid = (p.n_fields + kWFPC - 1) / kWFPC;
+            if (mode == ANA_SPECTRUM) k_analysis_w128<ANA_SPECTRUM><<<grid, kWTPF * kWFPC, kWSMEM, st>>>(p);
+            else k_analysis_w128<ANA_ACCUM><<<grid, kWTPF * kWFPC, kWSMEM, st>>>(p);
+        } else if constexpr (CL > 0) {
             using CG = ClusterGeo<N, CL>;
             if (mode == ANA_SPECTRUM)
                 k_analysis_cl<N, CL, ANA_SPECTRUM><<<CL * p.n_fields, CG::NT, CG::SMEM, st>>>(p);
@@ -448,7 +466,9 @@ struct Launch {
         }
     }
     static void output(const OutParams& p, cudaStream_t st) {
-        if constexpr (CL > 0) {
+        if constexpr (WIDE) {
+            k_output_w128<<<(p.U + kWFPC - 1) / kWFPC, kWTPF * kWFPC, kWSMEM, st>>>(p);
+        } else if constexpr (CL > 0) {
             using CG = ClusterGeo<N, CL>;
             k_output_cl<N, CL><<<CL * p.U, CG::NT, CG::SMEM, st>>>(p);
         } else {
@@ -474,6 +494,7 @@ const Dispatch* dispatch_for(int N, int D) {
     static const Dispatch d3_8 = make_dispatch<8, 3>(), d3_16 = make_dispatch<16, 3>(),
                           d3_24 = make_dispatch<24, 3>(), d3_48 = make_dispatch<48, 3>(),
                           d2_24 = make_dispatch<24, 2>(), d2_48 = make_dispatch<48, 2>(),
+                          d2_128 = make_dispatch<128, 2>(),
                           d3_32 = make_dispatch<32, 3>(), d3_64 = make_dispatch<64, 3>(), d2_8 = make_dispatch<8, 2>(),
                           d2_16 = make_dispatch<16, 2>(), d2_32 = make_dispatch<32, 2>(),
                           d2_64 = make_dispatch<64, 2>();
@@ -481,7 +502,7 @@ const Dispatch* dispatch_for(int N, int D) {
         return N == 8 ? &d3_8 : N == 16 ? &d3_16 : N == 24 ? &d3_24 : N == 32 ? &d3_32 : N == 48 ? &d3_48
              : N == 64 ? &d3_64 : nullptr;
     return N == 8 ? &d2_8 : N == 16 ? &d2_16 : N == 24 ? &d2_24 : N == 32 ? &d2_32 : N == 48 ? &d2_48
-         : N == 64 ? &d2_64 : nullptr;
+         : N == 64 ? &d2_64 : N == 128 ? &d2_128 : nullptr;
 }
 
 // Pipelined contraction: VC voxels per CTA, ring of STAGES bulk-copy stages

@@ -207,10 +207,11 @@ def test_64cube_against_oracle_small_quadrature(B):
     assert rel_err(Qg, Qo, s).max() < TOL
 
 
-@pytest.mark.parametrize("N,d,r", [(24, 3, 5), (48, 3, 3), (24, 2, 17), (48, 2, 4)])
+@pytest.mark.parametrize("N,d,r", [(24, 3, 5), (48, 3, 3), (24, 2, 17), (48, 2, 4), (128, 2, 3)])
 def test_radix3_sizes_against_oracle(B, N, d, r):
-    """N = 24, 48 (mixed radix-3 transforms; 48^3 on 4-CTA clusters), r inputs,
-    all ordered pairs; r = 17 in 2D spans a 16-wide tile plus a list tail."""
+    """N = 24, 48 (mixed radix-3 transforms; 48^3 on 4-CTA clusters) and 2D
+    N = 128 (4-lane cooperative line transforms), r inputs, all ordered pairs;
+    r = 17 in 2D spans a 16-wide tile plus a list tail."""
     cfg = (N, d, 8.0, 8.0, 0.0, 3, 6 if d == 3 else 12)
     F = as_fp32(W.random_fields(N, d, 8.0, r, seed=N + r))
     pairs = [(j, l) for j in range(r) for l in range(r)]
