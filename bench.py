@@ -253,6 +253,8 @@ def main():
     ap.add_argument("--config", default="c2", choices=sorted(CONFIGS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--field-budget-mb", type=int, default=0,
+                    help="fix the schedule instead of autotuning it (e.g. for profiling runs)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -298,7 +300,7 @@ def main():
     n_in = fields.shape[0]
     pj = [p[0] for p in pairs]
     pl = [p[1] for p in pairs]
-    g = B.boltz_grid_init(N, d, L, R, gamma, n_rho, M)
+    g = B.boltz_grid_init(N, d, L, R, gamma, n_rho, M, field_budget_mb=args.field_budget_mb)
     dev = torch.device("cuda", local_rank)
     f_dev = torch.tensor(fields, device=dev)
     spec = torch.empty((n_in,) + g.half_shape, dtype=torch.complex64, device=dev)
@@ -308,7 +310,10 @@ def main():
 
     # schedule autotuning (shifted-field budget per radial block), outside the timed region
     B.boltz_spectrum(g, f_dev, out=spec)
-    tuned_mb = B.boltz_autotune(g, spec, pj, pl, Q_scratch=Q, cache_path=os.environ.get("BOLTZ_TUNE_CACHE"))
+    if args.field_budget_mb > 0:
+        tuned_mb = args.field_budget_mb
+    else:
+        tuned_mb = B.boltz_autotune(g, spec, pj, pl, Q_scratch=Q, cache_path=os.environ.get("BOLTZ_TUNE_CACHE"))
 
     def step():
         B.boltz_spectrum(g, f_dev, out=spec)

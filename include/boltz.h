@@ -92,6 +92,8 @@ typedef enum {
 typedef struct {
     double b;              /* kernel constant; <= 0 selects 1/|S^{d-1}|              */
     size_t workspace_max;  /* cap on device workspace in bytes; 0 = library default */
+    int field_budget_mb;   /* shifted-field memory per radial block, MB; 0 = 96 MB
+                              (the schedule boltz_autotune chooses between)        */
 } boltz_options;
 
 /* Library ABI version (BOLTZ_ABI_VERSION of the build). */

@@ -943,6 +943,11 @@ boltz_status boltz_grid_init(boltz_grid* out, int N, int d_v, double L, double R
     const double area = d_v == 2 ? 2.0 * kPi : 4.0 * kPi;
     g->b = (opt && opt->b > 0) ? opt->b : 1.0 / area;
     if (opt && opt->workspace_max) g->ws_max = opt->workspace_max;
+    if (opt && opt->field_budget_mb < 0) {
+        delete g;
+        return BOLTZ_EINVAL;
+    }
+    if (opt && opt->field_budget_mb > 0) g->field_budget = size_t(opt->field_budget_mb) << 20;
     g->n = d_v == 3 ? N * N * N : N * N;
     g->half = d_v == 3 ? N * N * (N / 2 + 1) : N * (N / 2 + 1);
     g->smax = d_v * (N / 2) * (N / 2);
