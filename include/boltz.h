@@ -172,6 +172,35 @@ boltz_status boltz_project(boltz_grid g, const float* V, int r, const float* Q, 
                            void* stream);
 
 /*
+ * FP64 check build of the three calls above (paper Sec. 2.1; the paper fixes
+ * no precision): the same kernels, schedule and quadrature instantiated on
+ * double, with the grid's tables kept unrounded.  It separates the method's
+ * own error (quadrature, truncation, aliasing) from FP32 rounding: against an
+ * FP64 evaluation of the same separated quadrature it agrees to ~1e-13
+ * relative.  Built for the small single-CTA grids only: d_v = 3 with N in
+ * {8, 16} and d_v = 2 with N in {16, 32}; any other grid returns
+ * BOLTZ_EUNSUPPORTED (the grid is left usable).  FP64 throughput on this GPU
+ * is a small fraction of FP32: these calls are for checking, not for speed.
+ *   boltz_spectrum_f64:         f device float64 [n_inputs][N^d];
+ *                               spectra_out device complex128 [n_inputs][half]
+ *   boltz_collide_batched_f64:  spectra device complex128 [n_inputs][half];
+ *                               Q_out device float64 [n_pairs][N^d]; pair
+ *                               arrays, form and stream as boltz_collide_batched
+ *   boltz_project_f64:          V float64 [r][N^d], Q float64 [r*r][N^d],
+ *                               T_out float64 [r][r][r] (device), r in 1..64
+ * The FP64 path shares the grid's workspace and cached plan with the FP32
+ * path (switching precision rebuilds the plan).  Other errors as for the FP32
+ * calls.
+ */
+boltz_status boltz_spectrum_f64(boltz_grid g, const double* f, int n_inputs, void* spectra_out,
+                                void* stream);
+boltz_status boltz_collide_batched_f64(boltz_grid g, const void* spectra, int n_inputs,
+                                       const int32_t* pair_j, const int32_t* pair_l, int n_pairs,
+                                       double* Q_out, int form, void* stream);
+boltz_status boltz_project_f64(boltz_grid g, const double* V, int r, const double* Q,
+                               double* T_out, void* stream);
+
+/*
  * Autotuner of the batch schedule.  The tunable is the device memory budget
  * for the shifted fields of one radial block (48, 96, 192 or 384 MB): it
  * sets how many inputs share a chunk (so how often shifted fields are

@@ -32,7 +32,7 @@ EXPORTED = (
     "boltz_host_quadrature", "boltz_workspace_size", "boltz_profile_enable", "boltz_profile_read",
     "boltz_project_noalloc", "boltz_sync_status", "boltz_selftest", "boltz_moments",
     "boltz_batch_plan", "boltz_batch_run", "boltz_batch_kernel_count", "boltz_batch_destroy",
-    "boltz_autotune",
+    "boltz_autotune", "boltz_spectrum_f64", "boltz_collide_batched_f64", "boltz_project_f64",
 )
 
 KERNEL_CLASSES = ("spectrum", "prep", "shift", "contract", "radial", "output", "project")
@@ -90,6 +90,10 @@ def _load() -> ctypes.CDLL:
         "boltz_project_noalloc": ([vp, vp, ctypes.c_int, vp, vp, vp], ctypes.c_int),
         "boltz_profile_read": ([vp, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
                                 ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+        "boltz_spectrum_f64": ([vp, vp, ctypes.c_int, vp, vp], ctypes.c_int),
+        "boltz_collide_batched_f64": ([vp, vp, ctypes.c_int, i32p, i32p, ctypes.c_int, vp, ctypes.c_int, vp],
+                                      ctypes.c_int),
+        "boltz_project_f64": ([vp, vp, ctypes.c_int, vp, vp, vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -222,6 +226,45 @@ def boltz_project(grid: Grid, V, Q, out=None, stream=None):
         out = torch.empty((r, r, r), dtype=torch.float32, device=V.device)
     _check(_lib.boltz_project(grid.handle, _dev_ptr(V, "float32", "V"), r, _dev_ptr(Q, "float32", "Q"),
                               _dev_ptr(out, "float32", "out"), _stream_ptr(stream)), "boltz_project")
+    return out
+
+
+def boltz_spectrum_f64(grid: Grid, f, out=None, stream=None):
+    """FP64 check build of boltz_spectrum: complex128 half spectra of float64 fields."""
+    import torch
+    n_in = f.shape[0]
+    if out is None:
+        out = torch.empty((n_in,) + grid.half_shape, dtype=torch.complex128, device=f.device)
+    _check(_lib.boltz_spectrum_f64(grid.handle, _dev_ptr(f, "float64", "f"), n_in,
+                                   _dev_ptr(out, "complex128", "out"), _stream_ptr(stream)), "boltz_spectrum_f64")
+    return out
+
+
+def boltz_collide_batched_f64(grid: Grid, spectra, pair_j, pair_l, form: int = BOLTZ_FORM_BATCHED, out=None,
+                              stream=None):
+    """FP64 check build of boltz_collide_batched: float64 [n_pairs, *shape]."""
+    import torch
+    pj, pl = _pairs(pair_j, pair_l)
+    if out is None:
+        out = torch.empty((len(pj),) + grid.shape, dtype=torch.float64, device=spectra.device)
+    i32p = ctypes.POINTER(ctypes.c_int32)
+    _check(_lib.boltz_collide_batched_f64(grid.handle, _dev_ptr(spectra, "complex128", "spectra"),
+                                          spectra.shape[0], pj.ctypes.data_as(i32p), pl.ctypes.data_as(i32p),
+                                          len(pj), _dev_ptr(out, "float64", "out"), int(form),
+                                          _stream_ptr(stream)), "boltz_collide_batched_f64")
+    return out
+
+
+def boltz_project_f64(grid: Grid, V, Q, out=None, stream=None):
+    """FP64 check build of boltz_project: float64 [r, r, r]."""
+    import torch
+    r = V.shape[0]
+    if Q.shape[0] != r * r:
+        raise ValueError("Q must hold r*r fields")
+    if out is None:
+        out = torch.empty((r, r, r), dtype=torch.float64, device=V.device)
+    _check(_lib.boltz_project_f64(grid.handle, _dev_ptr(V, "float64", "V"), r, _dev_ptr(Q, "float64", "Q"),
+                                  _dev_ptr(out, "float64", "out"), _stream_ptr(stream)), "boltz_project_f64")
     return out
 
 

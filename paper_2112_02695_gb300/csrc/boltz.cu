@@ -76,6 +76,11 @@ struct boltz_grid_s {
     float* d_gm = nullptr;       // [smax+1]
     float* d_w = nullptr;        // [M/2] weight of each antipodal direction pair
     int2* d_dpair = nullptr;     // [M/2] (p, antipode(p)), p < antipode(p)
+    // the same tables unrounded, for the FP64 check build (small grids only)
+    double2* d_phase64 = nullptr;
+    double* d_ctab64 = nullptr;
+    double* d_gm64 = nullptr;
+    double* d_w64 = nullptr;
     int* d_err = nullptr;        // device error word (bit kErrTimeout: a bounded wait gave up)
     // workspace
     char* d_ws = nullptr;
@@ -84,6 +89,7 @@ struct boltz_grid_s {
     // last plan (reused when the same pair list comes back)
     std::vector<int32_t> last_j, last_l;
     int last_form = -1, last_n_inputs = -1;
+    size_t last_elem = 0;             // bytes per real of the cached plan (4 or 8)
     Plan last_plan;
     bool plan_uploaded = false;
     // side stream for the radial step and the events of the two-buffer pipeline
@@ -105,6 +111,10 @@ bool supported_shape(int N, int D) {
     return N == 8 || N == 16 || N == 24 || N == 32 || N == 48 || N == 64 || (D == 2 && N == 128);
 }
 
+// Shapes of the FP64 check build: single-CTA fields whose shifted-field
+// voxel chunk is 256 (3D 8^3, 16^3; 2D 16^2, 32^2).
+bool fp64_shape(int N, int D) { return D == 3 ? (N == 8 || N == 16) : (N == 16 || N == 32); }
+
 // voxels per chunk of the shifted-field layout (must match Geo<N, D>::VCH)
 int voxel_chunk(int N, int D) {
     const int n = D == 3 ? N * N * N : N * N;
@@ -117,10 +127,12 @@ int voxel_chunk(int N, int D) {
 // Build the chunk/tile/slot structure of a batch.  BATCHED: unordered gain
 // slots shared by (j,l) and (l,j), inputs shared by every pair in a chunk.
 // PLAIN: every evaluation gets its own two inputs and its own slot.
+// elem: bytes per real (4 for the FP32 path, 8 for the FP64 check build, whose
+// triangle and full tiles are 8 wide to bound the accumulator registers).
 boltz_status build_plan(const boltz_grid_s* g, int n_inputs, const int32_t* pj, const int32_t* pl, int n_pairs,
-                        int form, Plan& plan) {
+                        int form, Plan& plan, size_t elem = 4) {
     plan = Plan();
-    const size_t field_bytes = size_t(g->n) * 4;
+    const size_t field_bytes = size_t(g->n) * elem;
     // inputs per chunk: enough for one radial node's shifted fields to fit the L2-sized
     // budget, but never fewer than 16 (a rank-16 basis stays in one chunk, so its
     // shifted fields are computed once) nor more than 64
@@ -205,7 +217,7 @@ boltz_status build_plan(const boltz_grid_s* g, int n_inputs, const int32_t* pj, 
             // local pair set
             std::map<std::pair<int, int>, int> local;   // (ja <= lb) -> global slot id
             for (int s : chunk_slots[ci]) local[{loc[slots[s].first], loc[slots[s].second]}] = s;
-            const int T = nc >= 16 ? 16 : 8;
+            const int T = (nc >= 16 && elem == 4) ? 16 : 8;
             c.tile_T = T;
             std::vector<std::pair<int, int>> order;     // local slot order
             std::set<std::pair<int, int>> covered;
@@ -300,7 +312,7 @@ boltz_status build_plan(const boltz_grid_s* g, int n_inputs, const int32_t* pj, 
     plan.off_P = w;       // two buffers: the radial step of one node block overlaps the next block
     w = align_up(w + 2 * size_t(plan.nq) * plan.max_U * field_bytes, 256);
     plan.off_qhat = w;
-    w = align_up(w + size_t(plan.max_U) * g->half * 8, 256);
+    w = align_up(w + size_t(plan.max_U) * g->half * 2 * elem, 256);
     plan.off_fN = w;
     w = align_up(w + size_t(plan.max_nc) * field_bytes, 256);
     plan.off_lam = w;
@@ -478,12 +490,14 @@ struct Launch {
     }
 };
 
-struct Dispatch {
+template <typename R>
+struct DispatchT {
     cudaError_t (*prepare)();
-    void (*synth)(const SynParams&, int, cudaStream_t);
-    void (*analysis)(const AnaParams&, int, cudaStream_t);
-    void (*output)(const OutParams&, cudaStream_t);
+    void (*synth)(const SynParamsT<R>&, int, cudaStream_t);
+    void (*analysis)(const AnaParamsT<R>&, int, cudaStream_t);
+    void (*output)(const OutParamsT<R>&, cudaStream_t);
 };
+using Dispatch = DispatchT<float>;
 
 template <int N, int D>
 Dispatch make_dispatch() {
@@ -504,6 +518,55 @@ const Dispatch* dispatch_for(int N, int D) {
     return N == 8 ? &d2_8 : N == 16 ? &d2_16 : N == 24 ? &d2_24 : N == 32 ? &d2_32 : N == 48 ? &d2_48
          : N == 64 ? &d2_64 : N == 128 ? &d2_128 : nullptr;
 }
+
+// FP64 check build: the single-CTA field kernels instantiated on double, with
+// half as many fields per CTA as the FP32 path (twice the shared memory per field).
+template <int N, int D>
+struct Launch64 {
+    using G = Geo<N, D>;
+    static constexpr int FPC = Launch<N, D>::FPC / 2 > 0 ? Launch<N, D>::FPC / 2 : 1;
+    static constexpr int BLOCK = G::TPF * FPC;
+    static constexpr size_t SMEM = size_t(G::SMEM_F) * FPC * sizeof(double2);
+    static_assert(Launch<N, D>::CL == 0 && !Launch<N, D>::WIDE, "single-CTA shapes only");
+    static_assert(SMEM <= (200u << 10), "FP64 field tile fits in shared memory");
+
+    static cudaError_t prepare() {
+        cudaError_t e;
+        if ((e = set_smem(k_synth<N, D, FPC, SYN_SHIFT, double>, SMEM)) != cudaSuccess) return e;
+        if ((e = set_smem(k_synth<N, D, FPC, SYN_PREP, double>, SMEM)) != cudaSuccess) return e;
+        if ((e = set_smem(k_analysis<N, D, FPC, ANA_SPECTRUM, double>, SMEM)) != cudaSuccess) return e;
+        if ((e = set_smem(k_analysis<N, D, FPC, ANA_ACCUM, double>, SMEM)) != cudaSuccess) return e;
+        return set_smem(k_output<N, D, FPC, double>, SMEM);
+    }
+    static void synth(const SynParamsT<double>& p, int mode, cudaStream_t st) {
+        const int grid = (p.n_fields + FPC - 1) / FPC;
+        if (mode == SYN_SHIFT) k_synth<N, D, FPC, SYN_SHIFT, double><<<grid, BLOCK, SMEM, st>>>(p);
+        else k_synth<N, D, FPC, SYN_PREP, double><<<grid, BLOCK, SMEM, st>>>(p);
+    }
+    static void analysis(const AnaParamsT<double>& p, int mode, cudaStream_t st) {
+        const int grid = (p.n_fields + FPC - 1) / FPC;
+        if (mode == ANA_SPECTRUM) k_analysis<N, D, FPC, ANA_SPECTRUM, double><<<grid, BLOCK, SMEM, st>>>(p);
+        else k_analysis<N, D, FPC, ANA_ACCUM, double><<<grid, BLOCK, SMEM, st>>>(p);
+    }
+    static void output(const OutParamsT<double>& p, cudaStream_t st) {
+        k_output<N, D, FPC, double><<<(p.U + FPC - 1) / FPC, BLOCK, SMEM, st>>>(p);
+    }
+};
+
+template <int N, int D>
+DispatchT<double> make_dispatch64() {
+    return {&Launch64<N, D>::prepare, &Launch64<N, D>::synth, &Launch64<N, D>::analysis, &Launch64<N, D>::output};
+}
+
+const DispatchT<double>* dispatch64_for(int N, int D) {
+    static const DispatchT<double> d3_8 = make_dispatch64<8, 3>(), d3_16 = make_dispatch64<16, 3>(),
+                                   d2_16 = make_dispatch64<16, 2>(), d2_32 = make_dispatch64<32, 2>();
+    if (D == 3) return N == 8 ? &d3_8 : N == 16 ? &d3_16 : nullptr;
+    return N == 16 ? &d2_16 : N == 32 ? &d2_32 : nullptr;
+}
+
+const DispatchT<float>* dispatch_of(int N, int D, float) { return dispatch_for(N, D); }
+const DispatchT<double>* dispatch_of(int N, int D, double) { return dispatch64_for(N, D); }
 
 // Pipelined contraction: VC voxels per CTA, ring of STAGES bulk-copy stages
 // sized to stay within 192 KB of shared memory.
@@ -557,6 +620,55 @@ void launch_contract(int vch, int kind, int T, const ConParams& cp, int n_tiles,
     else launch_contract_vc<64>(kind, T, cp, n_tiles, nq, st);
 }
 
+// FP64 contraction (voxel chunk 256, tiles TRI 8, FULL 8x8, LIST 16): as many
+// stages as fit in 200 KB of shared memory, at least one.
+template <int KIND, int TJ, int TL>
+struct ContractLaunch64 {
+    static constexpr int VC = 256;
+    static constexpr int ROWS = ContractShape<KIND, TJ, TL>::ROWS;
+    static constexpr size_t STAGE = size_t(ROWS) * VC * sizeof(double);
+    static constexpr int FIT = (int)((200u << 10) / STAGE);
+    static constexpr int STAGES = FIT < 1 ? 1 : (FIT > 4 ? 4 : FIT);
+    static constexpr size_t SMEM = STAGES * STAGE;
+    static_assert(SMEM <= (227u << 10), "one stage fits in shared memory");
+    static cudaError_t prepare() { return set_smem(k_contract_pipe<KIND, TJ, TL, VC, STAGES, double>, SMEM); }
+    static void launch(const ConParamsT<double>& cp, int n_tiles, int nq, cudaStream_t st) {
+        dim3 grid(cp.n / VC, n_tiles, nq);
+        k_contract_pipe<KIND, TJ, TL, VC, STAGES, double><<<grid, VC, SMEM, st>>>(cp);
+    }
+};
+
+cudaError_t prepare_contract64() {
+    cudaError_t e;
+    if ((e = ContractLaunch64<TILE_TRI, 8, 8>::prepare()) != cudaSuccess) return e;
+    if ((e = ContractLaunch64<TILE_FULL, 8, 8>::prepare()) != cudaSuccess) return e;
+    return ContractLaunch64<TILE_LIST, 16, 16>::prepare();
+}
+
+void launch_contract_of(int vch, int kind, int T, const ConParamsT<float>& cp, int n_tiles, int nq,
+                        cudaStream_t st) {
+    launch_contract(vch, kind, T, cp, n_tiles, nq, st);
+}
+
+void launch_contract_of(int, int kind, int, const ConParamsT<double>& cp, int n_tiles, int nq, cudaStream_t st) {
+    if (kind == TILE_TRI) ContractLaunch64<TILE_TRI, 8, 8>::launch(cp, n_tiles, nq, st);
+    else if (kind == TILE_FULL) ContractLaunch64<TILE_FULL, 8, 8>::launch(cp, n_tiles, nq, st);
+    else ContractLaunch64<TILE_LIST, 16, 16>::launch(cp, n_tiles, nq, st);
+}
+
+// Device tables of one precision.
+template <typename R>
+struct TablesT {
+    const typename Prec<R>::C* phase;
+    const R* ctab;
+    const R* gm;
+    const R* w;
+};
+TablesT<float> tables_of(const boltz_grid_s* g, float) { return {g->d_phase, g->d_ctab, g->d_gm, g->d_w}; }
+TablesT<double> tables_of(const boltz_grid_s* g, double) {
+    return {g->d_phase64, g->d_ctab64, g->d_gm64, g->d_w64};
+}
+
 boltz_status check_pairs(int n_inputs, const int32_t* pj, const int32_t* pl, int n_pairs) {
     if (n_pairs < 0) return BOLTZ_EINVAL;
     if (n_pairs == 0) return BOLTZ_OK;
@@ -570,8 +682,9 @@ boltz_status check_pairs(int n_inputs, const int32_t* pj, const int32_t* pl, int
 // workspace to at least `min_ws` bytes and uploading the descriptors when the
 // pair list changed).  Synchronous; never called during stream capture.
 boltz_status prepare_plan(boltz_grid_s* g, int n_inputs, const int32_t* pj, const int32_t* pl, int n_pairs, int form,
-                          size_t min_ws, cudaStream_t st) {
+                          size_t min_ws, cudaStream_t st, size_t elem = 4) {
     const bool same = g->plan_uploaded && form == g->last_form && n_inputs == g->last_n_inputs &&
+                      elem == g->last_elem &&
                       (int)g->last_j.size() == n_pairs &&
                       std::equal(pj, pj + n_pairs, g->last_j.begin()) &&
                       std::equal(pl, pl + n_pairs, g->last_l.begin());
@@ -585,7 +698,7 @@ boltz_status prepare_plan(boltz_grid_s* g, int n_inputs, const int32_t* pj, cons
         return BOLTZ_OK;
     }
     Plan plan;
-    if ((s = build_plan(g, n_inputs, pj, pl, n_pairs, form, plan)) != BOLTZ_OK) return s;
+    if ((s = build_plan(g, n_inputs, pj, pl, n_pairs, form, plan, elem)) != BOLTZ_OK) return s;
     if ((s = ensure_workspace(g, std::max(plan.total, min_ws), st)) != BOLTZ_OK) return s;
     if ((s = upload_plan(g, plan, st)) != BOLTZ_OK) return s;
     g->last_plan = std::move(plan);
@@ -593,31 +706,37 @@ boltz_status prepare_plan(boltz_grid_s* g, int n_inputs, const int32_t* pj, cons
     g->last_l.assign(pl, pl + n_pairs);
     g->last_form = form;
     g->last_n_inputs = n_inputs;
+    g->last_elem = elem;
     g->plan_uploaded = true;
     return BOLTZ_OK;
 }
 
-boltz_status run_batched(boltz_grid_s* g, const float2* spectra, int n_inputs, const int32_t* pj, const int32_t* pl,
-                         int n_pairs, float* Q_out, int form, cudaStream_t st) {
-    boltz_status s0 = prepare_plan(g, n_inputs, pj, pl, n_pairs, form, 0, st);
+// One batched evaluation in precision R (float: the product path; double:
+// the FP64 check build, same kernels and schedule).
+template <typename R>
+boltz_status run_batched(boltz_grid_s* g, const typename Prec<R>::C* spectra, int n_inputs, const int32_t* pj,
+                         const int32_t* pl, int n_pairs, R* Q_out, int form, cudaStream_t st) {
+    using C = typename Prec<R>::C;
+    boltz_status s0 = prepare_plan(g, n_inputs, pj, pl, n_pairs, form, 0, st, sizeof(R));
     if (s0 != BOLTZ_OK) return s0;
     const Plan& plan = g->last_plan;
-    const Dispatch* dp = dispatch_for(g->N, g->D);
+    const DispatchT<R>* dp = dispatch_of(g->N, g->D, R(0));
+    const TablesT<R> tb = tables_of(g, R(0));
     char* ws = g->d_ws;
-    float* A = reinterpret_cast<float*>(ws + plan.off_A);
-    float* Pbuf = reinterpret_cast<float*>(ws + plan.off_P);
-    float2* qhat = reinterpret_cast<float2*>(ws + plan.off_qhat);
-    float* fN = reinterpret_cast<float*>(ws + plan.off_fN);
-    float* lam = reinterpret_cast<float*>(ws + plan.off_lam);
+    R* A = reinterpret_cast<R*>(ws + plan.off_A);
+    R* Pbuf = reinterpret_cast<R*>(ws + plan.off_P);
+    C* qhat = reinterpret_cast<C*>(ws + plan.off_qhat);
+    R* fN = reinterpret_cast<R*>(ws + plan.off_fN);
+    R* lam = reinterpret_cast<R*>(ws + plan.off_lam);
     for (const auto& c : plan.chunks) {
         const int nc = (int)c.inputs.size();
         const int* d_inputs = reinterpret_cast<const int*>(ws + plan.off_plan + c.off_inputs);
         // f_N and Lambda_g of the chunk's inputs (fN and lam are contiguous: [2][nc_max][n])
-        SynParams sp{};
+        SynParamsT<R> sp{};
         sp.spectra = spectra;
         sp.inputs = d_inputs;
-        sp.phase = g->d_phase;
-        sp.gm = g->d_gm;
+        sp.phase = tb.phase;
+        sp.gm = tb.gm;
         sp.n_c = nc;
         sp.M = g->M;
         sp.id_node = g->n_rho * g->M;
@@ -628,20 +747,20 @@ boltz_status run_batched(boltz_grid_s* g, const float2* spectra, int n_inputs, c
             ProfScope ps(g, BOLTZ_KCLASS_PREP, st);
             dp->synth(sp, SYN_PREP, st);
         }
-        const float* lam_c = fN + size_t(nc) * g->n;
-        BZ_CUDA(cudaMemsetAsync(qhat, 0, size_t(c.U) * g->half * sizeof(float2), st));
+        const R* lam_c = fN + size_t(nc) * g->n;
+        BZ_CUDA(cudaMemsetAsync(qhat, 0, size_t(c.U) * g->half * sizeof(C), st));
         // Node blocks run synth -> contract on the caller's stream and the radial
         // step on the side stream, with P double-buffered: the radial step of
         // block i overlaps synth/contract of block i+1.
         BZ_CUDA(cudaEventRecord(g->ev_fork, st));
         BZ_CUDA(cudaStreamWaitEvent(g->side, g->ev_fork, 0));
-        const size_t pbuf_floats = size_t(plan.nq) * plan.max_U * g->n;
+        const size_t pbuf_elems = size_t(plan.nq) * plan.max_U * g->n;
         int blk = 0;
         for (int q0 = 0; q0 < g->n_rho; q0 += plan.nq, ++blk) {
             const int nq = std::min(plan.nq, g->n_rho - q0);
             const int b = blk & 1;
-            float* Pb = Pbuf + b * pbuf_floats;
-            SynParams ss = sp;
+            R* Pb = Pbuf + b * pbuf_elems;
+            SynParamsT<R> ss = sp;
             ss.out = A;
             ss.q0 = q0;
             ss.n_fields = nq * g->M * nc;
@@ -650,10 +769,10 @@ boltz_status run_batched(boltz_grid_s* g, const float2* spectra, int n_inputs, c
                 dp->synth(ss, SYN_SHIFT, st);
             }
             if (blk >= 2) BZ_CUDA(cudaStreamWaitEvent(st, g->ev_free[b], 0));
-            ConParams cp{};
+            ConParamsT<R> cp{};
             cp.A = A;
             cp.P = Pb;
-            cp.w = g->d_w;
+            cp.w = tb.w;
             cp.dpair = g->d_dpair;
             cp.err = g->d_err;
             cp.n_dpair = g->M / 2;
@@ -665,15 +784,15 @@ boltz_status run_batched(boltz_grid_s* g, const float2* spectra, int n_inputs, c
                 if (c.tiles[k].empty()) continue;
                 cp.tiles = reinterpret_cast<const Tile*>(ws + plan.off_plan + c.off_tiles[k]);
                 ProfScope ps(g, BOLTZ_KCLASS_CONTRACT, st);
-                launch_contract(voxel_chunk(g->N, g->D), k, k == TILE_LIST ? 16 : c.tile_T, cp,
-                                (int)c.tiles[k].size(), nq, st);
+                launch_contract_of(voxel_chunk(g->N, g->D), k, k == TILE_LIST ? 16 : c.tile_T, cp,
+                                   (int)c.tiles[k].size(), nq, st);
             }
             BZ_CUDA(cudaEventRecord(g->ev_ready[b], st));
             BZ_CUDA(cudaStreamWaitEvent(g->side, g->ev_ready[b], 0));
-            AnaParams ap{};
+            AnaParamsT<R> ap{};
             ap.in = Pb;
             ap.out = qhat;
-            ap.ctab = g->d_ctab;
+            ap.ctab = tb.ctab;
             ap.n_fields = c.U;
             ap.nq = nq;
             ap.q0 = q0;
@@ -686,7 +805,7 @@ boltz_status run_batched(boltz_grid_s* g, const float2* spectra, int n_inputs, c
         }
         BZ_CUDA(cudaEventRecord(g->ev_join, g->side));
         BZ_CUDA(cudaStreamWaitEvent(st, g->ev_join, 0));
-        OutParams op{};
+        OutParamsT<R> op{};
         op.qhat = qhat;
         op.fN = fN;
         op.lam = lam_c;
@@ -749,6 +868,30 @@ boltz_status run_project(boltz_grid_s* g, const float* V, int r, const float* Q,
 
 size_t project_partial_bytes(int r) { return size_t(64) * r * r * r * sizeof(float); }
 
+// FP64 projection of the check build: CUDA-core partial sums over voxel
+// slices, reduced in a fixed order (the same kernels as the FP32 fallback for
+// tiny grids, on double).
+boltz_status run_project64(boltz_grid_s* g, const double* V, int r, const double* Q, double* T, double* partial,
+                           cudaStream_t st) {
+    constexpr int PB = 4, RT = 8;
+    const int r2 = r * r;
+    const int count = r * r2;
+    const int bx = (r2 + PB - 1) / PB, bz = (r + RT - 1) / RT;
+    int slices = std::max(1, std::min(32, (2 * 152) / std::max(1, bx * bz)));
+    slices = std::min(slices, std::max(1, g->n / 256));
+    {
+        ProfScope ps(g, BOLTZ_KCLASS_PROJECT, st);
+        k_project<PB, RT, double><<<dim3(bx, slices, bz), 256, 0, st>>>(V, Q, partial, r, g->n, slices);
+    }
+    ProfScope ps(g, BOLTZ_KCLASS_PROJECT, st);
+    k_project_reduce<double><<<(count + 255) / 256, 256, 0, st>>>(partial, T, count, slices,
+                                                                 std::pow(2.0 * g->L / g->N, g->D));
+    BZ_CUDA(cudaGetLastError());
+    return BOLTZ_OK;
+}
+
+size_t project64_partial_bytes(int r) { return size_t(32) * r * r * r * sizeof(double); }
+
 // ---------------------------------------------------------------- allocation-free projection
 // Partial sums of boltz_project_noalloc: a fixed 2 MiB array that every device
 // which loads the library holds until the process exits.  In host code the
@@ -781,7 +924,7 @@ boltz_status noalloc_project_partial(float** out) {
     return BOLTZ_OK;
 }
 
-// The twiddle table lives in constant memory, once per device.
+// The twiddle tables (FP32 and FP64) live in constant memory, once per device.
 boltz_status ensure_twiddles(int device) {
     static std::mutex mu;
     static std::set<int> done;
@@ -795,6 +938,11 @@ boltz_status ensure_twiddles(int device) {
     for (int t = 0; t < 48; ++t)
         tw48[t] = make_float2((float)std::cos(-2.0 * kPi * t / 48), (float)std::sin(-2.0 * kPi * t / 48));
     if (cudaMemcpyToSymbol(c_twiddle48, tw48, sizeof(tw48)) != cudaSuccess) return BOLTZ_ECUDA;
+    double2 twd[128], tw48d[48];
+    for (int t = 0; t < 128; ++t) twd[t] = make_double2(std::cos(-2.0 * kPi * t / 128), std::sin(-2.0 * kPi * t / 128));
+    for (int t = 0; t < 48; ++t) tw48d[t] = make_double2(std::cos(-2.0 * kPi * t / 48), std::sin(-2.0 * kPi * t / 48));
+    if (cudaMemcpyToSymbol(c_twiddle_d, twd, sizeof(twd)) != cudaSuccess) return BOLTZ_ECUDA;
+    if (cudaMemcpyToSymbol(c_twiddle48_d, tw48d, sizeof(tw48d)) != cudaSuccess) return BOLTZ_ECUDA;
     done.insert(device);
     return BOLTZ_OK;
 }
@@ -966,37 +1114,41 @@ boltz_status boltz_grid_init(boltz_grid* out, int N, int d_v, double L, double R
     // ---- tables in FP64, rounded once to FP32
     const int H = N / 2;
     const int nodes = N_rho * M + 1;
-    std::vector<float2> phase(size_t(nodes) * d_v * N);
+    std::vector<double2> phase64(size_t(nodes) * d_v * N);
     for (int node = 0; node < nodes; ++node) {
         for (int a = 0; a < d_v; ++a) {
             const double s = node < N_rho * M ? 0.5 * g->rho[node / M] * g->dir.sigma[(node % M) * d_v + a] : 0.0;
             for (int i = 0; i < N; ++i) {
                 const int k = i < H ? i : i - N;
-                float2 v = make_float2(0.f, 0.f);
+                double2 v = make_double2(0.0, 0.0);
                 if (i != H) {
                     const double ang = -kPi * k * s / L;
                     const double sg = (i & 1) ? -1.0 : 1.0;
-                    v = make_float2((float)(sg * std::cos(ang)), (float)(sg * std::sin(ang)));
+                    v = make_double2(sg * std::cos(ang), sg * std::sin(ang));
                 }
-                phase[(size_t(node) * d_v + a) * N + i] = v;
+                phase64[(size_t(node) * d_v + a) * N + i] = v;
             }
         }
     }
     const double kp = gamma + d_v - 1;
-    std::vector<float> ctab(size_t(N_rho) * (g->smax + 1)), gm(g->smax + 1);
+    std::vector<double> ctab64(size_t(N_rho) * (g->smax + 1)), gm64(g->smax + 1);
     for (int sq = 0; sq <= g->smax; ++sq) {
         const double km = std::sqrt((double)sq);
         double acc = 0;
         for (int q = 0; q < N_rho; ++q) {
             const double base = g->w_rho[q] * std::pow(g->rho[q], kp);
-            ctab[size_t(q) * (g->smax + 1) + sq] =
-                (float)(g->b * base * boltz::omega_average(d_v, kPi * g->rho[q] * km / (2.0 * L)) / g->n);
+            ctab64[size_t(q) * (g->smax + 1) + sq] =
+                g->b * base * boltz::omega_average(d_v, kPi * g->rho[q] * km / (2.0 * L)) / g->n;
             acc += base * boltz::omega_average(d_v, kPi * g->rho[q] * km / L);
         }
-        gm[sq] = (float)(g->b * area * acc);
+        gm64[sq] = g->b * area * acc;
     }
+    std::vector<float2> phase(phase64.size());
+    for (size_t i = 0; i < phase.size(); ++i) phase[i] = make_float2((float)phase64[i].x, (float)phase64[i].y);
+    std::vector<float> ctab(ctab64.begin(), ctab64.end()), gm(gm64.begin(), gm64.end());
     // antipodal direction pairs (p, p'), p < p'; the rules are centrally symmetric with w_p = w_p'
     std::vector<float> wdir;
+    std::vector<double> wdir64;
     std::vector<int2> dpair;
     for (int p = 0; p < M; ++p) {
         const int pb = g->dir.antipode[p];
@@ -1007,6 +1159,7 @@ boltz_status boltz_grid_init(boltz_grid* out, int N, int d_v, double L, double R
         if (p < pb) {
             dpair.push_back(make_int2(p, pb));
             wdir.push_back((float)g->dir.w[p]);
+            wdir64.push_back(g->dir.w[p]);
         }
     }
     const int n_dp = (int)dpair.size();
@@ -1037,6 +1190,24 @@ boltz_status boltz_grid_init(boltz_grid* out, int N, int d_v, double L, double R
         cudaMemcpy(g->d_dpair, dpair.data(), n_dp * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(g->d_err, 0, sizeof(int)) != cudaSuccess)
         return fail(BOLTZ_ECUDA);
+    if (fp64_shape(N, d_v)) {
+        if (cudaMalloc(&g->d_phase64, phase64.size() * sizeof(double2)) != cudaSuccess ||
+            cudaMalloc(&g->d_ctab64, ctab64.size() * sizeof(double)) != cudaSuccess ||
+            cudaMalloc(&g->d_gm64, gm64.size() * sizeof(double)) != cudaSuccess ||
+            cudaMalloc(&g->d_w64, n_dp * sizeof(double)) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return fail(BOLTZ_ENOMEM);
+        }
+        if (cudaMemcpy(g->d_phase64, phase64.data(), phase64.size() * sizeof(double2), cudaMemcpyHostToDevice) !=
+                cudaSuccess ||
+            cudaMemcpy(g->d_ctab64, ctab64.data(), ctab64.size() * sizeof(double), cudaMemcpyHostToDevice) !=
+                cudaSuccess ||
+            cudaMemcpy(g->d_gm64, gm64.data(), gm64.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(g->d_w64, wdir64.data(), n_dp * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+            return fail(BOLTZ_ECUDA);
+        if (dispatch64_for(N, d_v)->prepare() != cudaSuccess || prepare_contract64() != cudaSuccess)
+            return fail(BOLTZ_ECUDA);
+    }
     if (dispatch_for(N, d_v)->prepare() != cudaSuccess || prepare_contract() != cudaSuccess ||
         prepare_project_tc() != cudaSuccess)
         return fail(BOLTZ_ECUDA);
@@ -1073,6 +1244,10 @@ boltz_status boltz_grid_destroy(boltz_grid g) {
     cudaFree(g->d_w);
     cudaFree(g->d_dpair);
     cudaFree(g->d_err);
+    cudaFree(g->d_phase64);
+    cudaFree(g->d_ctab64);
+    cudaFree(g->d_gm64);
+    cudaFree(g->d_w64);
     cudaFree(g->d_ws);
     delete g;
     return BOLTZ_OK;
@@ -1162,6 +1337,50 @@ boltz_status boltz_project_noalloc(boltz_grid g, const float* V, int r, const fl
     k_project_reduce<<<(count + 255) / 256, 256, 0, st>>>(partial, T_out, count, slices, scale);
     BZ_CUDA(cudaGetLastError());
     return BOLTZ_OK;
+}
+
+boltz_status boltz_spectrum_f64(boltz_grid g, const double* f, int n_inputs, void* spectra_out, void* stream) {
+    if (!g || n_inputs < 0) return BOLTZ_EINVAL;
+    if (!fp64_shape(g->N, g->D)) return BOLTZ_EUNSUPPORTED;
+    if (n_inputs == 0) return BOLTZ_OK;
+    if (!f || !spectra_out) return BOLTZ_EINVAL;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    AnaParamsT<double> ap{};
+    ap.in = f;
+    ap.out = reinterpret_cast<double2*>(spectra_out);
+    ap.ctab = g->d_ctab64;
+    ap.n_fields = n_inputs;
+    ap.nq = 1;
+    ap.inv_n = 1.0 / (double)g->n;
+    {
+        ProfScope ps(g, BOLTZ_KCLASS_SPECTRUM, st);
+        dispatch64_for(g->N, g->D)->analysis(ap, ANA_SPECTRUM, st);
+    }
+    BZ_CUDA(cudaGetLastError());
+    return BOLTZ_OK;
+}
+
+boltz_status boltz_collide_batched_f64(boltz_grid g, const void* spectra, int n_inputs, const int32_t* pair_j,
+                                       const int32_t* pair_l, int n_pairs, double* Q_out, int form, void* stream) {
+    if (!g || (form != BOLTZ_FORM_BATCHED && form != BOLTZ_FORM_PLAIN)) return BOLTZ_EINVAL;
+    if (!fp64_shape(g->N, g->D)) return BOLTZ_EUNSUPPORTED;
+    boltz_status s = check_pairs(n_inputs, pair_j, pair_l, n_pairs);
+    if (s != BOLTZ_OK) return s;
+    if (n_pairs == 0) return BOLTZ_OK;
+    if (!spectra || !Q_out) return BOLTZ_EINVAL;
+    return run_batched<double>(g, reinterpret_cast<const double2*>(spectra), n_inputs, pair_j, pair_l, n_pairs, Q_out,
+                               form, reinterpret_cast<cudaStream_t>(stream));
+}
+
+boltz_status boltz_project_f64(boltz_grid g, const double* V, int r, const double* Q, double* T_out, void* stream) {
+    if (!g || !V || !Q || !T_out || r < 1 || r > 64) return BOLTZ_EINVAL;
+    if (!fp64_shape(g->N, g->D)) return BOLTZ_EUNSUPPORTED;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const size_t off = g->plan_uploaded ? align_up(g->last_plan.plan_bytes, 256) : 0;
+    boltz_status s = ensure_workspace(g, off + project64_partial_bytes(r), st);
+    if (s != BOLTZ_OK) return s;
+    const size_t off2 = g->plan_uploaded ? align_up(g->last_plan.plan_bytes, 256) : 0;
+    return run_project64(g, V, r, Q, T_out, reinterpret_cast<double*>(g->d_ws + off2), st);
 }
 
 boltz_status boltz_lowrank_step_host(boltz_grid g, const float* V_host, int r, float* Q_host, float* T_host,

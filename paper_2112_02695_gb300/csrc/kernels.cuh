@@ -1,4 +1,9 @@
-// sm_103a kernels of the separated fast-spectral collision operator (FP32).
+// sm_103a kernels of the separated fast-spectral collision operator.
+//
+// The single-CTA field kernels, the sigma-contraction and the CUDA-core
+// projection are templates on the real type R: float for the product path,
+// double for the FP64 check build of the small grids (same code, same
+// schedule).  The cluster kernels (3D 32^3, 48^3, 64^3) are FP32 only.
 //
 // Field layout (all kernels): a physical field is float [N]^D, C order, axis
 // 0 slowest; a spectrum is the real-to-complex half spectrum float2
@@ -48,8 +53,8 @@ struct Geo {
 //   out[((s * NCH + v / VCH) * n_c + jj) * VCH + v % VCH],
 // so the rows of all inputs of one (slot, voxel chunk) are one contiguous
 // block that the contraction fetches with a single bulk copy.
-template <int N, int D>
-__device__ __forceinline__ float* shifted_field_row(float* out, int slot, int jj, int n_c, int v) {
+template <int N, int D, typename R>
+__device__ __forceinline__ R* shifted_field_row(R* out, int slot, int jj, int n_c, int v) {
     using G = Geo<N, D>;
     return out + (((size_t)slot * G::NCH + v / G::VCH) * n_c + jj) * G::VCH + (v % G::VCH);
 }
@@ -63,24 +68,76 @@ __device__ __forceinline__ int wrapk(int i, int N) { return i < N / 2 ? i : i - 
 // the loss multiplier G-(|l|^2)) for every chunk input.
 enum { SYN_SHIFT = 0, SYN_PREP = 1 };
 
-struct SynParams {
-    const float2* spectra;  // [n_inputs][half]
+template <typename R>
+struct SynParamsT {
+    using C = typename Prec<R>::C;
+    const C* spectra;       // [n_inputs][half]
     const int* inputs;      // chunk-local -> global input index [n_c]
-    const float2* phase;    // [nodes][D][N]: (-1)^k exp(-i pi k s_a / L), zero at the Nyquist index
-    const float* gm;        // [SMAX+1] loss multiplier
-    float* out;             // SHIFT: [nq][M][n_c][n]; PREP: [2][n_c][n]
+    const C* phase;         // [nodes][D][N]: (-1)^k exp(-i pi k s_a / L), zero at the Nyquist index
+    const R* gm;            // [SMAX+1] loss multiplier
+    R* out;                 // SHIFT: [nq][M][n_c][n]; PREP: [2][n_c][n]
     int n_c, M, q0, id_node, n_fields;
 };
+using SynParams = SynParamsT<float>;
 
-template <int N, int D, int FPC, int MODE>
-__global__ void __launch_bounds__(Geo<N, D>::TPF * FPC) k_synth(SynParams P) {
+// Two real rows of N values to and from the two halves of a complex register
+// line (x[c].x <-> row a, x[c].y <-> row b) with 16-byte accesses.
+template <int N>
+__device__ __forceinline__ void store_two_rows(float* a, float* b, const float2 (&x)[N]) {
+    float4* o1 = reinterpret_cast<float4*>(a);
+    float4* o2 = reinterpret_cast<float4*>(b);
+#pragma unroll
+    for (int c = 0; c < N / 4; ++c) {
+        o1[c] = make_float4(x[4 * c].x, x[4 * c + 1].x, x[4 * c + 2].x, x[4 * c + 3].x);
+        o2[c] = make_float4(x[4 * c].y, x[4 * c + 1].y, x[4 * c + 2].y, x[4 * c + 3].y);
+    }
+}
+template <int N>
+__device__ __forceinline__ void store_two_rows(double* a, double* b, const double2 (&x)[N]) {
+    double2* o1 = reinterpret_cast<double2*>(a);
+    double2* o2 = reinterpret_cast<double2*>(b);
+#pragma unroll
+    for (int c = 0; c < N / 2; ++c) {
+        o1[c] = make_double2(x[2 * c].x, x[2 * c + 1].x);
+        o2[c] = make_double2(x[2 * c].y, x[2 * c + 1].y);
+    }
+}
+template <int N>
+__device__ __forceinline__ void load_two_rows(const float* a, const float* b, float2 (&x)[N]) {
+    const float4* a4 = reinterpret_cast<const float4*>(a);
+    const float4* b4 = reinterpret_cast<const float4*>(b);
+#pragma unroll
+    for (int c = 0; c < N / 4; ++c) {
+        const float4 p = __ldg(&a4[c]), q = __ldg(&b4[c]);
+        x[4 * c] = make_float2(p.x, q.x);
+        x[4 * c + 1] = make_float2(p.y, q.y);
+        x[4 * c + 2] = make_float2(p.z, q.z);
+        x[4 * c + 3] = make_float2(p.w, q.w);
+    }
+}
+template <int N>
+__device__ __forceinline__ void load_two_rows(const double* a, const double* b, double2 (&x)[N]) {
+    const double2* a2 = reinterpret_cast<const double2*>(a);
+    const double2* b2 = reinterpret_cast<const double2*>(b);
+#pragma unroll
+    for (int c = 0; c < N / 2; ++c) {
+        const double2 p = __ldg(&a2[c]), q = __ldg(&b2[c]);
+        x[2 * c] = make_double2(p.x, q.x);
+        x[2 * c + 1] = make_double2(p.y, q.y);
+    }
+}
+
+template <int N, int D, int FPC, int MODE, typename R = float>
+__global__ void __launch_bounds__(Geo<N, D>::TPF * FPC) k_synth(SynParamsT<R> P) {
     using G = Geo<N, D>;
+    using PR = Prec<R>;
+    using C = typename PR::C;
     constexpr int H = G::H, RS = G::RS;
-    extern __shared__ float2 smem[];
+    extern __shared__ __align__(16) unsigned char fsm_raw[];
     const int grp = threadIdx.x / G::TPF, lt = threadIdx.x % G::TPF;
     const int f = blockIdx.x * FPC + grp;
     const bool active = f < P.n_fields;
-    float2* s = smem + grp * G::SMEM_F;
+    C* s = reinterpret_cast<C*>(fsm_raw) + grp * G::SMEM_F;
 
     int input = 0, node = P.id_node;
     bool use_gm = false;
@@ -94,23 +151,23 @@ __global__ void __launch_bounds__(Geo<N, D>::TPF * FPC) k_synth(SynParams P) {
             use_gm = f >= P.n_c;
         }
     }
-    const float2* __restrict__ src = P.spectra + (size_t)input * G::half;
-    const float2* __restrict__ ph = P.phase + (size_t)node * D * N;
+    const C* __restrict__ src = P.spectra + (size_t)input * G::half;
+    const C* __restrict__ ph = P.phase + (size_t)node * D * N;
     // start of row r of this field in the output (rows never straddle a voxel chunk)
-    auto row_ptr = [&](int r) -> float* {
+    auto row_ptr = [&](int r) -> R* {
         if (MODE == SYN_SHIFT) return shifted_field_row<N, D>(P.out, f / P.n_c, f % P.n_c, P.n_c, r * N);
         return P.out + (size_t)f * G::n + (size_t)r * N;
     };
-    float2 x[N];
+    C x[N];
 
     if (D == 3) {
         // axis 0: columns (k1, k2), k2 < N/2 (the input's half-axis Nyquist is zero)
         if (active) {
             const int k1 = lt / H, k2 = lt % H;
-            const float2 w12 = cmul(__ldg(&ph[N + k1]), __ldg(&ph[2 * N + k2]));
+            const C w12 = cmul(__ldg(&ph[N + k1]), __ldg(&ph[2 * N + k2]));
 #pragma unroll
             for (int k0 = 0; k0 < N; ++k0) {
-                float2 v = cmul(__ldg(&src[(k0 * N + k1) * G::NH + k2]), cmul(w12, __ldg(&ph[k0])));
+                C v = cmul(__ldg(&src[(k0 * N + k1) * G::NH + k2]), cmul(w12, __ldg(&ph[k0])));
                 if (MODE == SYN_PREP && use_gm) {
                     const int a = wrapk(k0, N), b = wrapk(k1, N);
                     v = cscale(v, __ldg(&P.gm[a * a + b * b + k2 * k2]));
@@ -135,33 +192,27 @@ __global__ void __launch_bounds__(Geo<N, D>::TPF * FPC) k_synth(SynParams P) {
         // axis 2: complex-to-real of rows (i0, i1) and (i0, i1 + N/2) together
         if (active) {
             const int i0 = lt / H, i1 = lt % H;
-            const float2* r1 = s + (i0 * N + i1) * RS;
-            const float2* r2 = s + (i0 * N + i1 + H) * RS;
-            x[0] = make_float2(r1[0].x, r2[0].x);
-            x[H] = make_float2(0.f, 0.f);
+            const C* r1 = s + (i0 * N + i1) * RS;
+            const C* r2 = s + (i0 * N + i1 + H) * RS;
+            x[0] = PR::mk(r1[0].x, r2[0].x);
+            x[H] = PR::mk(R(0), R(0));
 #pragma unroll
             for (int k = 1; k < H; ++k) {
-                const float2 a = r1[k], b = r2[k];
-                x[k] = make_float2(a.x - b.y, a.y + b.x);
-                x[N - k] = make_float2(a.x + b.y, b.x - a.y);
+                const C a = r1[k], b = r2[k];
+                x[k] = PR::mk(a.x - b.y, a.y + b.x);
+                x[N - k] = PR::mk(a.x + b.y, b.x - a.y);
             }
             fft_reg<N, true>(x);
-            float4* o1 = reinterpret_cast<float4*>(row_ptr(i0 * N + i1));
-            float4* o2 = reinterpret_cast<float4*>(row_ptr(i0 * N + i1 + H));
-#pragma unroll
-            for (int c = 0; c < N / 4; ++c) {
-                o1[c] = make_float4(x[4 * c].x, x[4 * c + 1].x, x[4 * c + 2].x, x[4 * c + 3].x);
-                o2[c] = make_float4(x[4 * c].y, x[4 * c + 1].y, x[4 * c + 2].y, x[4 * c + 3].y);
-            }
+            store_two_rows<N>(row_ptr(i0 * N + i1), row_ptr(i0 * N + i1 + H), x);
         }
     } else {
         // axis 0: columns k1 < N/2
         if (active) {
             const int k1 = lt;
-            const float2 w1 = __ldg(&ph[N + k1]);
+            const C w1 = __ldg(&ph[N + k1]);
 #pragma unroll
             for (int k0 = 0; k0 < N; ++k0) {
-                float2 v = cmul(__ldg(&src[k0 * G::NH + k1]), cmul(w1, __ldg(&ph[k0])));
+                C v = cmul(__ldg(&src[k0 * G::NH + k1]), cmul(w1, __ldg(&ph[k0])));
                 if (MODE == SYN_PREP && use_gm) {
                     const int a = wrapk(k0, N);
                     v = cscale(v, __ldg(&P.gm[a * a + k1 * k1]));
@@ -176,24 +227,18 @@ __global__ void __launch_bounds__(Geo<N, D>::TPF * FPC) k_synth(SynParams P) {
         // axis 1: complex-to-real of rows i0 and i0 + N/2
         if (active) {
             const int i0 = lt;
-            const float2* r1 = s + i0 * RS;
-            const float2* r2 = s + (i0 + H) * RS;
-            x[0] = make_float2(r1[0].x, r2[0].x);
-            x[H] = make_float2(0.f, 0.f);
+            const C* r1 = s + i0 * RS;
+            const C* r2 = s + (i0 + H) * RS;
+            x[0] = PR::mk(r1[0].x, r2[0].x);
+            x[H] = PR::mk(R(0), R(0));
 #pragma unroll
             for (int k = 1; k < H; ++k) {
-                const float2 a = r1[k], b = r2[k];
-                x[k] = make_float2(a.x - b.y, a.y + b.x);
-                x[N - k] = make_float2(a.x + b.y, b.x - a.y);
+                const C a = r1[k], b = r2[k];
+                x[k] = PR::mk(a.x - b.y, a.y + b.x);
+                x[N - k] = PR::mk(a.x + b.y, b.x - a.y);
             }
             fft_reg<N, true>(x);
-            float4* o1 = reinterpret_cast<float4*>(row_ptr(i0));
-            float4* o2 = reinterpret_cast<float4*>(row_ptr(i0 + H));
-#pragma unroll
-            for (int c = 0; c < N / 4; ++c) {
-                o1[c] = make_float4(x[4 * c].x, x[4 * c + 1].x, x[4 * c + 2].x, x[4 * c + 3].x);
-                o2[c] = make_float4(x[4 * c].y, x[4 * c + 1].y, x[4 * c + 2].y, x[4 * c + 3].y);
-            }
+            store_two_rows<N>(row_ptr(i0), row_ptr(i0 + H), x);
         }
     }
 }
@@ -204,53 +249,50 @@ __global__ void __launch_bounds__(Geo<N, D>::TPF * FPC) k_synth(SynParams P) {
 // of the q-block, Qhat+_u += c_q(|k|^2) (-1)^k DFT[P_{q,u}]  (c_q includes 1/n).
 enum { ANA_SPECTRUM = 0, ANA_ACCUM = 1 };
 
-struct AnaParams {
-    const float* in;     // SPECTRUM: [n_fields][n]; ACCUM: [nq][U][n]
-    float2* out;         // [n_fields][half]
-    const float* ctab;   // [N_rho][SMAX+1]
+template <typename R>
+struct AnaParamsT {
+    using C = typename Prec<R>::C;
+    const R* in;         // SPECTRUM: [n_fields][n]; ACCUM: [nq][U][n]
+    C* out;              // [n_fields][half]
+    const R* ctab;       // [N_rho][SMAX+1]
     int n_fields, nq, q0, U;
-    float inv_n;
+    R inv_n;
 };
+using AnaParams = AnaParamsT<float>;
 
-template <int N, int D, int FPC, int MODE>
-__global__ void __launch_bounds__(Geo<N, D>::TPF * FPC) k_analysis(AnaParams P) {
+template <int N, int D, int FPC, int MODE, typename R = float>
+__global__ void __launch_bounds__(Geo<N, D>::TPF * FPC) k_analysis(AnaParamsT<R> P) {
     using G = Geo<N, D>;
+    using PR = Prec<R>;
+    using C = typename PR::C;
     constexpr int H = G::H, RS = G::RS, NH = G::NH;
-    extern __shared__ float2 smem[];
+    extern __shared__ __align__(16) unsigned char fsm_raw[];
     const int grp = threadIdx.x / G::TPF, lt = threadIdx.x % G::TPF;
     const int f = blockIdx.x * FPC + grp;
     const bool active = f < P.n_fields;
-    float2* s = smem + grp * G::SMEM_F;
-    float2* __restrict__ dst = P.out + (size_t)f * G::half;
-    float2 x[N];
+    C* s = reinterpret_cast<C*>(fsm_raw) + grp * G::SMEM_F;
+    C* __restrict__ dst = P.out + (size_t)f * G::half;
+    C x[N];
     const int n_iter = (MODE == ANA_ACCUM) ? P.nq : 1;
+    const R HALF = R(0.5);
 
     for (int qq = 0; qq < n_iter; ++qq) {
-        const float* __restrict__ src =
+        const R* __restrict__ src =
             (MODE == ANA_ACCUM) ? P.in + ((size_t)qq * P.U + f) * G::n : P.in + (size_t)f * G::n;
-        const float* __restrict__ ct = P.ctab + (size_t)(P.q0 + qq) * (G::SMAX + 1);
+        const R* __restrict__ ct = P.ctab + (size_t)(P.q0 + qq) * (G::SMAX + 1);
         // last axis: real-to-complex of two rows at once
         if (active) {
             const int row = (D == 3) ? (lt / H) * N + (lt % H) : lt;   // (i0, i1) or i0
-            const float4* a4 = reinterpret_cast<const float4*>(src + row * N);
-            const float4* b4 = reinterpret_cast<const float4*>(src + (row + H) * N);
-#pragma unroll
-            for (int c = 0; c < N / 4; ++c) {
-                const float4 a = __ldg(&a4[c]), b = __ldg(&b4[c]);
-                x[4 * c] = make_float2(a.x, b.x);
-                x[4 * c + 1] = make_float2(a.y, b.y);
-                x[4 * c + 2] = make_float2(a.z, b.z);
-                x[4 * c + 3] = make_float2(a.w, b.w);
-            }
+            load_two_rows<N>(src + row * N, src + (row + H) * N, x);
             fft_reg<N, false>(x);
-            float2* r1 = s + row * RS;
-            float2* r2 = s + (row + H) * RS;
+            C* r1 = s + row * RS;
+            C* r2 = s + (row + H) * RS;
 #pragma unroll
             for (int k = 0; k <= H; ++k) {
-                const float2 z = x[k], zc = x[(N - k) % N];
+                const C z = x[k], zc = x[(N - k) % N];
                 // X1 = (Z_k + conj Z_{N-k}) / 2,  X2 = (Z_k - conj Z_{N-k}) / (2i)
-                r1[k] = make_float2(0.5f * (z.x + zc.x), 0.5f * (z.y - zc.y));
-                r2[k] = make_float2(0.5f * (z.y + zc.y), -0.5f * (z.x - zc.x));
+                r1[k] = PR::mk(HALF * (z.x + zc.x), HALF * (z.y - zc.y));
+                r2[k] = PR::mk(HALF * (z.y + zc.y), -HALF * (z.x - zc.x));
             }
         }
         __syncthreads();
@@ -281,14 +323,14 @@ __global__ void __launch_bounds__(Geo<N, D>::TPF * FPC) k_analysis(AnaParams P) 
                     const int par = (k0 + k1 + k2) & 1;
                     if (MODE == ANA_SPECTRUM) {
                         const bool nyq = (k0 == H) || (k2 == H) || (D == 3 && k1 == H);
-                        const float sc = nyq ? 0.f : (par ? -P.inv_n : P.inv_n);
+                        const R sc = nyq ? R(0) : (par ? -P.inv_n : P.inv_n);
                         dst[idx] = cscale(x[k0], sc);
                     } else {
                         const int a = wrapk(k0, N), b = (D == 3) ? wrapk(k1, N) : 0;
-                        const float c0 = __ldg(&ct[a * a + b * b + k2 * k2]);
-                        const float sc = par ? -c0 : c0;
-                        const float2 old = dst[idx];
-                        dst[idx] = make_float2(fmaf(x[k0].x, sc, old.x), fmaf(x[k0].y, sc, old.y));
+                        const R c0 = __ldg(&ct[a * a + b * b + k2 * k2]);
+                        const R sc = par ? -c0 : c0;
+                        const C old = dst[idx];
+                        dst[idx] = PR::mk(PR::fma_(x[k0].x, sc, old.x), PR::fma_(x[k0].y, sc, old.y));
                     }
                 }
             }
@@ -300,15 +342,18 @@ __global__ void __launch_bounds__(Geo<N, D>::TPF * FPC) k_analysis(AnaParams P) 
 // Outputs of the output kernels: gain field of every slot (complex-to-real of
 // Qhat+ with all modes, Nyquist included) minus the loss f_N(l) * Lambda(j),
 // written for every ordered pair (e, j, l) that maps to the slot.
-struct OutParams {
-    const float2* qhat;   // [U][half]
-    const float* fN;      // [n_c][n]
-    const float* lam;     // [n_c][n]
+template <typename R>
+struct OutParamsT {
+    using C = typename Prec<R>::C;
+    const C* qhat;        // [U][half]
+    const R* fN;          // [n_c][n]
+    const R* lam;         // [n_c][n]
     const int* out_start; // [U+1]
     const int4* outs;     // (e, jloc, lloc, 0)
-    float* Q;             // [n_pairs][n]
+    R* Q;                 // [n_pairs][n]
     int U;
 };
+using OutParams = OutParamsT<float>;
 
 // ------------------------------------------------------------------ 3D field kernels on a CTA cluster
 // Same transforms as k_synth / k_analysis / k_output for d = 3, with one field
@@ -647,17 +692,56 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(ClusterGeo<N, CL>::
 // ------------------------------------------------------------------ output (single-CTA fields)
 
 
-template <int N, int D, int FPC>
-__global__ void __launch_bounds__(Geo<N, D>::TPF * FPC) k_output(OutParams P) {
+// Gain minus loss for two rows: q = x.(x|y) - f * lam, 16-byte accesses.
+template <int N>
+__device__ __forceinline__ void gain_minus_loss_rows(const float* f1, const float* f2, const float* l1,
+                                                     const float* l2, float* q1, float* q2, const float2 (&x)[N]) {
+    const float4* F1 = reinterpret_cast<const float4*>(f1);
+    const float4* F2 = reinterpret_cast<const float4*>(f2);
+    const float4* L1 = reinterpret_cast<const float4*>(l1);
+    const float4* L2 = reinterpret_cast<const float4*>(l2);
+    float4* Q1 = reinterpret_cast<float4*>(q1);
+    float4* Q2 = reinterpret_cast<float4*>(q2);
+#pragma unroll
+    for (int c = 0; c < N / 4; ++c) {
+        const float4 a = __ldg(&F1[c]), b = __ldg(&L1[c]), a2 = __ldg(&F2[c]), b2 = __ldg(&L2[c]);
+        Q1[c] = make_float4(fmaf(-a.x, b.x, x[4 * c].x), fmaf(-a.y, b.y, x[4 * c + 1].x),
+                            fmaf(-a.z, b.z, x[4 * c + 2].x), fmaf(-a.w, b.w, x[4 * c + 3].x));
+        Q2[c] = make_float4(fmaf(-a2.x, b2.x, x[4 * c].y), fmaf(-a2.y, b2.y, x[4 * c + 1].y),
+                            fmaf(-a2.z, b2.z, x[4 * c + 2].y), fmaf(-a2.w, b2.w, x[4 * c + 3].y));
+    }
+}
+template <int N>
+__device__ __forceinline__ void gain_minus_loss_rows(const double* f1, const double* f2, const double* l1,
+                                                     const double* l2, double* q1, double* q2,
+                                                     const double2 (&x)[N]) {
+    const double2* F1 = reinterpret_cast<const double2*>(f1);
+    const double2* F2 = reinterpret_cast<const double2*>(f2);
+    const double2* L1 = reinterpret_cast<const double2*>(l1);
+    const double2* L2 = reinterpret_cast<const double2*>(l2);
+    double2* Q1 = reinterpret_cast<double2*>(q1);
+    double2* Q2 = reinterpret_cast<double2*>(q2);
+#pragma unroll
+    for (int c = 0; c < N / 2; ++c) {
+        const double2 a = __ldg(&F1[c]), b = __ldg(&L1[c]), a2 = __ldg(&F2[c]), b2 = __ldg(&L2[c]);
+        Q1[c] = make_double2(fma(-a.x, b.x, x[2 * c].x), fma(-a.y, b.y, x[2 * c + 1].x));
+        Q2[c] = make_double2(fma(-a2.x, b2.x, x[2 * c].y), fma(-a2.y, b2.y, x[2 * c + 1].y));
+    }
+}
+
+template <int N, int D, int FPC, typename R = float>
+__global__ void __launch_bounds__(Geo<N, D>::TPF * FPC) k_output(OutParamsT<R> P) {
     using G = Geo<N, D>;
+    using PR = Prec<R>;
+    using C = typename PR::C;
     constexpr int H = G::H, RS = G::RS, NH = G::NH;
-    extern __shared__ float2 smem[];
+    extern __shared__ __align__(16) unsigned char fsm_raw[];
     const int grp = threadIdx.x / G::TPF, lt = threadIdx.x % G::TPF;
     const int u = blockIdx.x * FPC + grp;
     const bool active = u < P.U;
-    float2* s = smem + grp * G::SMEM_F;
-    const float2* __restrict__ src = P.qhat + (size_t)u * G::half;
-    float2 x[N];
+    C* s = reinterpret_cast<C*>(fsm_raw) + grp * G::SMEM_F;
+    const C* __restrict__ src = P.qhat + (size_t)u * G::half;
+    C x[N];
     // axis 0 (all columns, Nyquist included), sign (-1)^k from the index parity
     if (active) {
         for (int c = lt; c < G::COLS; c += G::TPF) {
@@ -665,8 +749,8 @@ __global__ void __launch_bounds__(Geo<N, D>::TPF * FPC) k_output(OutParams P) {
 #pragma unroll
             for (int k0 = 0; k0 < N; ++k0) {
                 const int idx = (D == 3) ? (k0 * N + k1) * NH + k2 : k0 * NH + k2;
-                const float2 v = src[idx];
-                x[k0] = ((k0 + k1 + k2) & 1) ? make_float2(-v.x, -v.y) : v;
+                const C v = src[idx];
+                x[k0] = ((k0 + k1 + k2) & 1) ? PR::mk(-v.x, -v.y) : v;
             }
             fft_reg<N, true>(x);
 #pragma unroll
@@ -690,34 +774,25 @@ __global__ void __launch_bounds__(Geo<N, D>::TPF * FPC) k_output(OutParams P) {
     if (!active) return;
     const int row = (D == 3) ? (lt / H) * N + (lt % H) : lt;
     {
-        const float2* r1 = s + row * RS;
-        const float2* r2 = s + (row + H) * RS;
-        x[0] = make_float2(r1[0].x, r2[0].x);
-        x[H] = make_float2(r1[H].x, r2[H].x);
+        const C* r1 = s + row * RS;
+        const C* r2 = s + (row + H) * RS;
+        x[0] = PR::mk(r1[0].x, r2[0].x);
+        x[H] = PR::mk(r1[H].x, r2[H].x);
 #pragma unroll
         for (int k = 1; k < H; ++k) {
-            const float2 a = r1[k], b = r2[k];
-            x[k] = make_float2(a.x - b.y, a.y + b.x);
-            x[N - k] = make_float2(a.x + b.y, b.x - a.y);
+            const C a = r1[k], b = r2[k];
+            x[k] = PR::mk(a.x - b.y, a.y + b.x);
+            x[N - k] = PR::mk(a.x + b.y, b.x - a.y);
         }
         fft_reg<N, true>(x);
     }
     for (int o = P.out_start[u]; o < P.out_start[u + 1]; ++o) {
         const int4 e = P.outs[o];
-        const float4* f1 = reinterpret_cast<const float4*>(P.fN + (size_t)e.z * G::n + row * N);
-        const float4* f2 = reinterpret_cast<const float4*>(P.fN + (size_t)e.z * G::n + (row + H) * N);
-        const float4* l1 = reinterpret_cast<const float4*>(P.lam + (size_t)e.y * G::n + row * N);
-        const float4* l2 = reinterpret_cast<const float4*>(P.lam + (size_t)e.y * G::n + (row + H) * N);
-        float4* q1 = reinterpret_cast<float4*>(P.Q + (size_t)e.x * G::n + row * N);
-        float4* q2 = reinterpret_cast<float4*>(P.Q + (size_t)e.x * G::n + (row + H) * N);
-#pragma unroll
-        for (int c = 0; c < N / 4; ++c) {
-            const float4 a = __ldg(&f1[c]), b = __ldg(&l1[c]), a2 = __ldg(&f2[c]), b2 = __ldg(&l2[c]);
-            q1[c] = make_float4(fmaf(-a.x, b.x, x[4 * c].x), fmaf(-a.y, b.y, x[4 * c + 1].x),
-                                fmaf(-a.z, b.z, x[4 * c + 2].x), fmaf(-a.w, b.w, x[4 * c + 3].x));
-            q2[c] = make_float4(fmaf(-a2.x, b2.x, x[4 * c].y), fmaf(-a2.y, b2.y, x[4 * c + 1].y),
-                                fmaf(-a2.z, b2.z, x[4 * c + 2].y), fmaf(-a2.w, b2.w, x[4 * c + 3].y));
-        }
+        const R* fl = P.fN + (size_t)e.z * G::n;
+        const R* lj = P.lam + (size_t)e.y * G::n;
+        R* q = P.Q + (size_t)e.x * G::n;
+        gain_minus_loss_rows<N>(fl + row * N, fl + (row + H) * N, lj + row * N, lj + (row + H) * N, q + row * N,
+                                q + (row + H) * N, x);
     }
 }
 
@@ -739,15 +814,17 @@ struct Tile {
     int j0, l0;
 };
 
-struct ConParams {
-    const float* A;        // [nq][M][n_c][n]
-    float* P;              // [nq][U][n]
+template <typename R>
+struct ConParamsT {
+    const R* A;            // [nq][M][n_c][n]
+    R* P;                  // [nq][U][n]
     const Tile* tiles;
-    const float* w;        // [M/2] weight of each antipodal direction pair
+    const R* w;            // [M/2] weight of each antipodal direction pair
     const int2* dpair;     // [M/2] (p, antipode(p)) with p < antipode(p)
     int* err;              // device error word
     int n_dpair, M, n_c, U, n;
 };
+using ConParams = ConParamsT<float>;
 
 // A CTA owns VC consecutive voxels (one per thread); for
 // every antipodal pair one warp issues 1-D bulk copies of the 2 x NR field
@@ -761,19 +838,21 @@ struct ContractShape {
     static constexpr int NACC = (KIND == TILE_TRI) ? TJ * (TJ + 1) / 2 : (KIND == TILE_FULL ? TJ * TL : TJ);
 };
 
-template <int KIND, int TJ, int TL, int VC, int STAGES>
-__global__ void __launch_bounds__(VC, 1) k_contract_pipe(ConParams C) {
+template <int KIND, int TJ, int TL, int VC, int STAGES, typename R = float>
+__global__ void __launch_bounds__(VC, 1) k_contract_pipe(ConParamsT<R> C) {
     using CS = ContractShape<KIND, TJ, TL>;
+    using PR = Prec<R>;
     constexpr int NR = CS::NR, ROWS = CS::ROWS, NACC = CS::NACC;
-    constexpr uint32_t STAGE_BYTES = ROWS * VC * sizeof(float);
-    extern __shared__ __align__(128) float sbuf[];                // [STAGES][ROWS][VC]
+    constexpr uint32_t STAGE_BYTES = ROWS * VC * sizeof(R);
+    extern __shared__ __align__(128) unsigned char csm_raw[];
+    R* sbuf = reinterpret_cast<R*>(csm_raw);                      // [STAGES][ROWS][VC]
     __shared__ uint64_t bars[STAGES];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const Tile& tl = C.tiles[blockIdx.y];
     const int nch = C.n / VC;                                     // VC is the layout's voxel chunk
     const size_t blk = (size_t)C.n_c * VC;                        // one (slot, chunk) block
     // block of (slot = qq*M + p, chunk = blockIdx.x)
-    auto block_of = [&](int p) -> const float* {
+    auto block_of = [&](int p) -> const R* {
         return C.A + (((size_t)blockIdx.z * C.M + p) * nch + blockIdx.x) * blk;
     };
     const int npairs = C.n_dpair;
@@ -786,7 +865,7 @@ __global__ void __launch_bounds__(VC, 1) k_contract_pipe(ConParams C) {
     auto issue = [&](int k) {                                     // warp 0 only
         const int s = k % STAGES;
         const int2 d = C.dpair[k];
-        float* dstp = sbuf + (size_t)s * ROWS * VC;
+        R* dstp = sbuf + (size_t)s * ROWS * VC;
         if (lane == 0) mbar_arrive_expect_tx(&bars[s], STAGE_BYTES);
         __syncwarp();
         if (KIND == TILE_LIST) {
@@ -794,20 +873,20 @@ __global__ void __launch_bounds__(VC, 1) k_contract_pipe(ConParams C) {
                 const int i = r < NR ? r : r - NR;
                 const int row = i < TJ ? tl.ja[i] : tl.lb[i - TJ];
                 bulk_g2s(dstp + (size_t)r * VC, block_of(r < NR ? d.x : d.y) + (size_t)row * VC,
-                         VC * sizeof(float), &bars[s]);
+                         VC * sizeof(R), &bars[s]);
             }
         } else if (lane < 2) {
-            const float* b = block_of(lane == 0 ? d.x : d.y);
-            float* o = dstp + (size_t)lane * NR * VC;
-            bulk_g2s(o, b + (size_t)tl.j0 * VC, TJ * VC * sizeof(float), &bars[s]);
-            if (KIND == TILE_FULL) bulk_g2s(o + TJ * VC, b + (size_t)tl.l0 * VC, TL * VC * sizeof(float), &bars[s]);
+            const R* b = block_of(lane == 0 ? d.x : d.y);
+            R* o = dstp + (size_t)lane * NR * VC;
+            bulk_g2s(o, b + (size_t)tl.j0 * VC, TJ * VC * sizeof(R), &bars[s]);
+            if (KIND == TILE_FULL) bulk_g2s(o + TJ * VC, b + (size_t)tl.l0 * VC, TL * VC * sizeof(R), &bars[s]);
         }
     };
     if (warp == 0)
         for (int k = 0; k < STAGES && k < npairs; ++k) issue(k);
-    float acc[NACC];
+    R acc[NACC];
 #pragma unroll
-    for (int i = 0; i < NACC; ++i) acc[i] = 0.f;
+    for (int i = 0; i < NACC; ++i) acc[i] = R(0);
     for (int k = 0; k < npairs; ++k) {
         const int s = k % STAGES;
         const bool ok = mbar_wait_bounded(&bars[s], (uint32_t)(k / STAGES) & 1u);
@@ -821,9 +900,9 @@ __global__ void __launch_bounds__(VC, 1) k_contract_pipe(ConParams C) {
             __syncthreads();
             return;
         }
-        const float* __restrict__ xs = sbuf + (size_t)s * ROWS * VC + t;
-        const float wk = __ldg(&C.w[k]);
-        float xp[NR], xq[NR];
+        const R* __restrict__ xs = sbuf + (size_t)s * ROWS * VC + t;
+        const R wk = __ldg(&C.w[k]);
+        R xp[NR], xq[NR];
 #pragma unroll
         for (int i = 0; i < NR; ++i) {
             xp[i] = wk * xs[i * VC];
@@ -835,7 +914,7 @@ __global__ void __launch_bounds__(VC, 1) k_contract_pipe(ConParams C) {
             for (int x = 0; x < TJ; ++x)
 #pragma unroll
                 for (int y = x; y < TJ; ++y) {
-                    acc[i] = fmaf(xp[x], xq[y], fmaf(xq[x], xp[y], acc[i]));
+                    acc[i] = PR::fma_(xp[x], xq[y], PR::fma_(xq[x], xp[y], acc[i]));
                     ++i;
                 }
         } else if (KIND == TILE_FULL) {
@@ -843,10 +922,11 @@ __global__ void __launch_bounds__(VC, 1) k_contract_pipe(ConParams C) {
             for (int x = 0; x < TJ; ++x)
 #pragma unroll
                 for (int y = 0; y < TL; ++y)
-                    acc[x * TL + y] = fmaf(xp[x], xq[TJ + y], fmaf(xq[x], xp[TJ + y], acc[x * TL + y]));
+                    acc[x * TL + y] = PR::fma_(xp[x], xq[TJ + y], PR::fma_(xq[x], xp[TJ + y], acc[x * TL + y]));
         } else {
 #pragma unroll
-            for (int i = 0; i < TJ; ++i) acc[i] = fmaf(xp[i], xq[TJ + i], fmaf(xq[i], xp[TJ + i], acc[i]));
+            for (int i = 0; i < TJ; ++i)
+                acc[i] = PR::fma_(xp[i], xq[TJ + i], PR::fma_(xq[i], xp[TJ + i], acc[i]));
         }
         __syncthreads();                                          // stage s fully read
         if (warp == 0 && k + STAGES < npairs) {
@@ -855,7 +935,7 @@ __global__ void __launch_bounds__(VC, 1) k_contract_pipe(ConParams C) {
         }
     }
     const size_t n = (size_t)C.n;
-    float* __restrict__ Pq = C.P + (size_t)blockIdx.z * C.U * n + (size_t)blockIdx.x * VC + t;
+    R* __restrict__ Pq = C.P + (size_t)blockIdx.z * C.U * n + (size_t)blockIdx.x * VC + t;
     const int cnt = (KIND == TILE_LIST) ? tl.count : NACC;
 #pragma unroll
     for (int i = 0; i < NACC; ++i)
@@ -924,42 +1004,43 @@ __global__ void k_selftest_wait_timeout(int* err) {
 // ------------------------------------------------------------------ projection
 // partial[vs][k][pr] = sum_{v in slice vs} V_k(v) Q_pr(v); the reduce kernel sums
 // the slices in a fixed order and applies dv^D (midpoint rule).
-template <int PB, int RT>
-__global__ void __launch_bounds__(256) k_project(const float* __restrict__ V, const float* __restrict__ Q,
-                                                 float* __restrict__ partial, int r, int n, int n_slices) {
+template <int PB, int RT, typename R = float>
+__global__ void __launch_bounds__(256) k_project(const R* __restrict__ V, const R* __restrict__ Q,
+                                                 R* __restrict__ partial, int r, int n, int n_slices) {
+    using PR = Prec<R>;
     const int pr0 = blockIdx.x * PB, vs = blockIdx.y, k0 = blockIdx.z * RT;
     const int r2 = r * r;
     const int v0 = (int)((long long)n * vs / n_slices), v1 = (int)((long long)n * (vs + 1) / n_slices);
-    float acc[PB][RT];
+    R acc[PB][RT];
 #pragma unroll
     for (int i = 0; i < PB; ++i)
 #pragma unroll
-        for (int j = 0; j < RT; ++j) acc[i][j] = 0.f;
+        for (int j = 0; j < RT; ++j) acc[i][j] = R(0);
     for (int v = v0 + threadIdx.x; v < v1; v += 256) {
-        float q[PB], w[RT];
+        R q[PB], w[RT];
 #pragma unroll
-        for (int i = 0; i < PB; ++i) q[i] = (pr0 + i < r2) ? __ldg(&Q[(size_t)(pr0 + i) * n + v]) : 0.f;
+        for (int i = 0; i < PB; ++i) q[i] = (pr0 + i < r2) ? __ldg(&Q[(size_t)(pr0 + i) * n + v]) : R(0);
 #pragma unroll
-        for (int j = 0; j < RT; ++j) w[j] = (k0 + j < r) ? __ldg(&V[(size_t)(k0 + j) * n + v]) : 0.f;
+        for (int j = 0; j < RT; ++j) w[j] = (k0 + j < r) ? __ldg(&V[(size_t)(k0 + j) * n + v]) : R(0);
 #pragma unroll
         for (int i = 0; i < PB; ++i)
 #pragma unroll
-            for (int j = 0; j < RT; ++j) acc[i][j] = fmaf(q[i], w[j], acc[i][j]);
+            for (int j = 0; j < RT; ++j) acc[i][j] = PR::fma_(q[i], w[j], acc[i][j]);
     }
-    __shared__ float red[8][PB * RT];
+    __shared__ R red[8][PB * RT];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int i = 0; i < PB; ++i)
 #pragma unroll
         for (int j = 0; j < RT; ++j) {
-            float t = acc[i][j];
+            R t = acc[i][j];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
             if (lane == 0) red[warp][i * RT + j] = t;
         }
     __syncthreads();
     for (int e = threadIdx.x; e < PB * RT; e += 256) {
-        float t = 0.f;
+        R t = R(0);
 #pragma unroll
         for (int w = 0; w < 8; ++w) t += red[w][e];
         const int i = e / RT, j = e % RT;
@@ -967,11 +1048,12 @@ __global__ void __launch_bounds__(256) k_project(const float* __restrict__ V, co
     }
 }
 
-__global__ void k_project_reduce(const float* __restrict__ partial, float* __restrict__ T, int count,
-                                 int n_slices, float scale) {
+template <typename R = float>
+__global__ void k_project_reduce(const R* __restrict__ partial, R* __restrict__ T, int count, int n_slices,
+                                 R scale) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= count) return;
-    float t = 0.f;
+    R t = R(0);
     for (int s = 0; s < n_slices; ++s) t += partial[(size_t)s * count + i];
     T[i] = t * scale;
 }

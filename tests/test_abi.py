@@ -80,6 +80,9 @@ def test_null_handles_are_rejected(B):
     assert lib.boltz_grid_init(None, 32, 3, 8.0, 8.0, 1.0, 32, 38, None) == B.BOLTZ_EINVAL
     z = ctypes.c_size_t()
     assert lib.boltz_workspace_size(None, 1, None, None, 0, 0, ctypes.byref(z)) == B.BOLTZ_EINVAL
+    assert lib.boltz_spectrum_f64(None, None, 1, None, None) == B.BOLTZ_EINVAL
+    assert lib.boltz_collide_batched_f64(None, None, 1, None, None, 1, None, 0, None) == B.BOLTZ_EINVAL
+    assert lib.boltz_project_f64(None, None, 4, None, None, None) == B.BOLTZ_EINVAL
 
 
 @pytest.mark.parametrize("d,M", [(2, 16), (2, 64), (3, 6), (3, 14), (3, 26), (3, 38), (3, 50), (3, 86)])
