@@ -163,7 +163,9 @@ def oracle_sample(cfg_name, r=4):
     return fields, pairs, "the single evaluation"
 
 
-def time_oracle(cfg_name, r=4):
+def time_oracle(cfg_name, r=4, results=None):
+    """Times the oracle on the bounded sample; when `results` is a dict it
+    receives the sample and the oracle's outputs (full evaluations only)."""
     from oracle import collision as C
     from oracle import quadrature as Qd
     N, d, L, R, gamma, n_rho, M, kind, size = CONFIGS[cfg_name]
@@ -180,9 +182,29 @@ def time_oracle(cfg_name, r=4):
         return 1.0 / dt, dt, f"one pair over 1 of the {n_rho} radial nodes, time x {n_rho}"
     prob = C.Problem(N=N, d=d, L=L, R=R, gamma=gamma, n_rho=n_rho, M=M)
     t0 = time.perf_counter()
-    C.collide_fields(prob, fields.astype(np.float64), pairs)
+    Q, Qp, Qm = C.collide_fields(prob, fields.astype(np.float64), pairs, return_parts=True)
     dt = time.perf_counter() - t0
+    if results is not None:
+        results.update(fields=fields, pairs=pairs, Q=Q, scale=C.scale(Q, Qp, Qm))
     return len(pairs) / dt, dt, desc
+
+
+def sample_errors(B, g, results, forms):
+    """Relative L-infinity error of each form on the oracle's sample, per
+    result normalised by s = max(max|Q|, max|Q+|, max|Q-|) of the oracle;
+    reports the largest over the sample."""
+    import torch
+    f = torch.tensor(results["fields"], dtype=torch.float32, device="cuda")
+    pj = [p[0] for p in results["pairs"]]
+    pl = [p[1] for p in results["pairs"]]
+    spec = B.boltz_spectrum(g, f)
+    out = {}
+    for name, form in forms.items():
+        Qg = B.boltz_collide_batched(g, spec, pj, pl, form=form).cpu().numpy().astype(np.float64)
+        ax = tuple(range(1, Qg.ndim))
+        out[name] = float(np.max(np.max(np.abs(Qg - results["Q"]), axis=ax) / results["scale"]))
+    B.boltz_sync_status(g)
+    return out
 
 
 def host_cores():
@@ -253,6 +275,7 @@ def main():
     ap.add_argument("--config", default="c2", choices=sorted(CONFIGS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-split", action="store_true")
     ap.add_argument("--field-budget-mb", type=int, default=0,
                     help="fix the schedule instead of autotuning it (e.g. for profiling runs)")
     args = ap.parse_args()
@@ -399,6 +422,52 @@ def main():
         plain["batched_speedup"] = value / world / plain["value"]
         B.boltz_profile_read(g, reset=True)
 
+    # split-precision form (BF16x3 DFT-as-GEMM shifted fields on the tensor cores), same batch
+    split = None
+    split_ok = (N, d) == (32, 3)
+    if split_ok and not args.no_split:
+        Qs = torch.empty_like(Q)
+        split_mb = args.field_budget_mb or B.boltz_autotune(g, spec, pj, pl, Q_scratch=Qs, form=B.BOLTZ_FORM_SPLIT_BF16,
+                                                           cache_path=os.environ.get("BOLTZ_TUNE_CACHE"))
+
+        def step_split():
+            B.boltz_spectrum(g, f_dev, out=spec)
+            B.boltz_collide_batched(g, spec, pj, pl, form=B.BOLTZ_FORM_SPLIT_BF16, out=Qs)
+            if kind == "pairs":
+                B.boltz_project(g, f_dev, Qs, out=T)
+        for _ in range(args.warmup):
+            step_split()
+        torch.cuda.synchronize()
+        B.boltz_profile_read(g, reset=True)
+        ts = timed(step_split, args.steps)
+        B.boltz_profile_read(g, reset=True)
+        B.boltz_profile_enable(g, True)
+        timed(step_split, max(3, args.steps // 4))
+        prof_s = B.boltz_profile_read(g, reset=True)
+        B.boltz_profile_enable(g, False)
+        B.boltz_sync_status(g)
+        ls, mss = prof_s["shift"]
+        fields_per_launch = n_rho * M * n_in / (ls / max(3, args.steps // 4))
+        # executed tensor work: 3 passes x (N^2/128 tiles) x (2N/16 K-steps) x 2*128*(2N)*16 per field
+        tc_flops_field = 3 * (N * N // 128) * (2 * N // 16) * 2 * 128 * (2 * N) * 16
+        tc_achieved = tc_flops_field * fields_per_launch / (mss / ls * 1e-3) / 1e12
+        bf16_peak, peak_src = 1900.0, "fallback 1.9 PFLOP/s dense BF16 burst (no MEASURED_PEAKS.json)"
+        try:
+            with open(MEASURED_PEAKS) as fh:
+                mp = json.load(fh)
+            if mp.get("bf16_tflops"):
+                bf16_peak, peak_src = float(mp["bf16_tflops"]), "MEASURED_PEAKS.json bf16_tflops (burst)"
+        except (OSError, ValueError):
+            pass
+        split = {"value": len(pairs) * len(ts) / (sum(ts) / 1e3), "unit": "evals/s", "ms_per_step": sum(ts) / len(ts),
+                 "dtype": "bf16x3 split (FP32 accumulate) for the shifted fields, f32 elsewhere",
+                 "autotuned_field_budget_mb": split_mb,
+                 "shift_kernel": {"kernel": "k_shift_split (tcgen05 kind::f16, 3 GEMM passes per field)",
+                                  "tensor_tflops_executed": tc_achieved, "peak": bf16_peak,
+                                  "frac": tc_achieved / bf16_peak, "peak_source": peak_src,
+                                  "share_of_step": mss / max(sum(ms for _, ms in prof_s.values()), 1e-9)}}
+        split["speedup_vs_fp32_batched"] = split["value"] / (value / world)
+
     # roofline of the dominant kernel (the shifted-field inverse transforms)
     props = torch.cuda.get_device_properties(dev)
     clocks = clk.summary()
@@ -426,10 +495,19 @@ def main():
     step_flops = sum(fl.values())
 
     cpu = None
+    errors = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, dt, desc = time_oracle(args.config)
+        res = {}
+        rate, dt, desc = time_oracle(args.config, results=res)
         cpu = {"value": rate, "unit": "evals/s", "cores": host_cores(), "kind": "oracle",
                "sample": f"{desc}; {dt:.1f} s of FP64 numpy/BLAS on the host"}
+        if res:
+            forms = {"fp32_batched": B.BOLTZ_FORM_BATCHED, "fp32_plain": B.BOLTZ_FORM_PLAIN}
+            if split_ok:
+                forms["split_bf16"] = B.BOLTZ_FORM_SPLIT_BF16
+            errors = sample_errors(B, g, res, forms)
+            errors["normalisation"] = "max over the oracle sample of max|Q_gpu - Q_oracle| / max(|Q|,|Q+|,|Q-|)"
+            errors["sample"] = desc
 
     if rank == 0:
         line = {
@@ -450,6 +528,8 @@ def main():
             "clocks": clocks,
             "e2e": e2e,
             "plain_fp32": plain,
+            "split_bf16": split,
+            "error_vs_oracle": errors,
             "cpu_baseline": cpu,
             "wall_s_timed_region": wall,
         }

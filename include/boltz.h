@@ -86,7 +86,19 @@ typedef enum {
     /* Plain per-evaluation form: two inverse transforms per (rho, sigma) node
      * and evaluation, nothing shared between evaluations.  FP32.  Same result
      * up to FP32 rounding; kept as the comparison baseline. */
-    BOLTZ_FORM_PLAIN = 1
+    BOLTZ_FORM_PLAIN = 1,
+    /* Batched form with split-precision shifted fields: each shifted field
+     * g_N(v - rho sigma / 2) is computed as three per-axis GEMMs with the
+     * N x N shift-interpolation matrices of the grid (the DFT-as-GEMM form of
+     * the inverse transforms) on the tensor cores, with both operands split
+     * into BF16 pairs x = hi + lo, three products per pair (hi*hi, lo*hi,
+     * hi*lo) and FP32 accumulation.  Every other step is the FP32 batched
+     * form.  Error against an FP64 evaluation ~1e-5 of the result scale
+     * (gate 1e-3).  Built for d_v = 3, N = 32; other grids return
+     * BOLTZ_EUNSUPPORTED.  The first call on a grid builds its per-node
+     * matrices (24 KB per (rho, sigma) node, device memory kept until the
+     * grid is destroyed). */
+    BOLTZ_FORM_SPLIT_BF16 = 2
 } boltz_form;
 
 typedef struct {

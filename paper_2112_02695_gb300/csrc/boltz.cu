@@ -21,6 +21,7 @@
 #include "boltz.h"
 #include "kernels.cuh"
 #include "quadrature.hpp"
+#include "split.cuh"
 #include "tc_kernels.cuh"
 #include "wide2d.cuh"
 
@@ -57,7 +58,7 @@ struct Plan {
     int max_nc = 0, max_U = 0;
     size_t plan_bytes = 0;
     // workspace layout (byte offsets)
-    size_t off_plan = 0, off_A = 0, off_P = 0, off_qhat = 0, off_fN = 0, off_lam = 0, total = 0;
+    size_t off_plan = 0, off_A = 0, off_P = 0, off_qhat = 0, off_fN = 0, off_lam = 0, off_img = 0, total = 0;
 };
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -65,7 +66,7 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 }  // namespace
 
 struct boltz_grid_s {
-    int N = 0, D = 0, n_rho = 0, M = 0, device = 0;
+    int N = 0, D = 0, n_rho = 0, M = 0, device = 0, sms = 1;
     double L = 0, R = 0, gamma = 0, b = 0;
     int n = 0, half = 0, smax = 0;
     std::vector<double> rho, w_rho;
@@ -81,6 +82,8 @@ struct boltz_grid_s {
     double* d_ctab64 = nullptr;
     double* d_gm64 = nullptr;
     double* d_w64 = nullptr;
+    // split-precision form: per-node BF16 shift matrices (built on first use)
+    uint8_t* d_smat = nullptr;
     int* d_err = nullptr;        // device error word (bit kErrTimeout: a bounded wait gave up)
     // workspace
     char* d_ws = nullptr;
@@ -114,6 +117,13 @@ bool supported_shape(int N, int D) {
 // Shapes of the FP64 check build: single-CTA fields whose shifted-field
 // voxel chunk is 256 (3D 8^3, 16^3; 2D 16^2, 32^2).
 bool fp64_shape(int N, int D) { return D == 3 ? (N == 8 || N == 16) : (N == 16 || N == 32); }
+
+// Shapes of the split-precision form (the whole field is one tensor-core operand in shared memory).
+bool split_shape(int N, int D) { return D == 3 && N == 32; }
+
+bool valid_form(int form) {
+    return form == BOLTZ_FORM_BATCHED || form == BOLTZ_FORM_PLAIN || form == BOLTZ_FORM_SPLIT_BF16;
+}
 
 // voxels per chunk of the shifted-field layout (must match Geo<N, D>::VCH)
 int voxel_chunk(int N, int D) {
@@ -317,6 +327,8 @@ boltz_status build_plan(const boltz_grid_s* g, int n_inputs, const int32_t* pj, 
     w = align_up(w + size_t(plan.max_nc) * field_bytes, 256);
     plan.off_lam = w;
     w = align_up(w + size_t(plan.max_nc) * field_bytes, 256);
+    plan.off_img = w;     // pre-split inputs of the split-precision form
+    if (form == BOLTZ_FORM_SPLIT_BF16) w = align_up(w + size_t(plan.max_nc) * SplitGeo<32>::A_BYTES, 256);
     plan.total = w;
     return BOLTZ_OK;
 }
@@ -711,13 +723,94 @@ boltz_status prepare_plan(boltz_grid_s* g, int n_inputs, const int32_t* pj, cons
     return BOLTZ_OK;
 }
 
+// ---------------------------------------------------------------- split-precision form
+
+// FP32 -> BF16, round to nearest even (finite inputs).
+uint16_t bf16_rne(float x) {
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    u += 0x7fffu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+
+float bf16_value(uint16_t h) {
+    const uint32_t u = (uint32_t)h << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+
+// Per-node B' operands of the split-precision form: for node (q, p) and axis
+// a the shift-interpolation matrix S(s)[i][m] = (1/N) sum_{|k| < N/2}
+// exp(i pi k ((i - m) dv - s) / L), s = rho_q sigma_{p,a} / 2 (real: the
+// Nyquist mode is excluded), split into BF16 hi/lo and laid out as the
+// K-major core-matrix operand described in split.cuh.  Built once per grid
+// (synchronous; never during stream capture).
+boltz_status ensure_split_tables(boltz_grid_s* g) {
+    if (g->d_smat) return BOLTZ_OK;
+    using S = SplitGeo<32>;
+    const int N = g->N, nodes = g->n_rho * g->M;
+    std::vector<uint16_t> img(size_t(nodes) * S::B_BYTES / 2, 0);
+    std::vector<double> sv(N);
+    for (int node = 0; node < nodes; ++node) {
+        for (int a = 0; a < 3; ++a) {
+            const double sh = 0.5 * g->rho[node / g->M] * g->dir.sigma[(node % g->M) * 3 + a];
+            for (int d = 0; d < N; ++d) {            // d = (i - m) mod N
+                double acc = 1.0;
+                for (int k = 1; k < N / 2; ++k) acc += 2.0 * std::cos(kPi * k * (2.0 * d / N - sh / g->L));
+                sv[d] = acc / N;
+            }
+            uint16_t* B = img.data() + (size_t(node) * S::B_BYTES + size_t(a) * S::B_AXIS_BYTES) / 2;
+            for (int n = 0; n < S::NB; ++n) {
+                const int i = n % N;
+                for (int kp = 0; kp < S::KP; ++kp) {
+                    const int m = kp / 2;
+                    const double sim = sv[(i - m + N) % N];
+                    const uint16_t hi = bf16_rne((float)sim);
+                    const uint16_t lo = bf16_rne((float)(sim - (double)bf16_value(hi)));
+                    const uint16_t v = n < N ? hi : ((kp & 1) ? (uint16_t)0 : lo);
+                    const size_t off = (size_t(n / 8) * S::KCORES + kp / 8) * 128 + (n % 8) * 16 + (kp % 8) * 2;
+                    B[off / 2] = v;
+                }
+            }
+        }
+    }
+    uint8_t* d = nullptr;
+    if (cudaMalloc(&d, img.size() * 2) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return BOLTZ_ENOMEM;
+    }
+    if (cudaMemcpy(d, img.data(), img.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess ||
+        set_smem(k_shift_split<32>, SplitGeo<32>::SMEM) != cudaSuccess) {
+        cudaFree(d);
+        return BOLTZ_ECUDA;
+    }
+    g->d_smat = d;
+    return BOLTZ_OK;
+}
+
+void launch_split_input(const float* fN, uint8_t* img, int nc, cudaStream_t st) {
+    const size_t total = size_t(nc) * 32 * 32 * 32;
+    const int grid = (int)std::min<size_t>((total + 255) / 256, 4096);
+    k_split_input<32><<<grid, 256, 0, st>>>(fN, img, nc);
+}
+
+void launch_shift_split(const SplitParams& p, int sms, cudaStream_t st) {
+    const int grid = std::max(1, std::min(p.n_fields, sms));     // one CTA per SM, contiguous field ranges
+    k_shift_split<32><<<grid, kSplitThreads, SplitGeo<32>::SMEM, st>>>(p);
+}
+
 // One batched evaluation in precision R (float: the product path; double:
 // the FP64 check build, same kernels and schedule).
 template <typename R>
 boltz_status run_batched(boltz_grid_s* g, const typename Prec<R>::C* spectra, int n_inputs, const int32_t* pj,
                          const int32_t* pl, int n_pairs, R* Q_out, int form, cudaStream_t st) {
     using C = typename Prec<R>::C;
-    boltz_status s0 = prepare_plan(g, n_inputs, pj, pl, n_pairs, form, 0, st, sizeof(R));
+    const bool split = form == BOLTZ_FORM_SPLIT_BF16;
+    if (split && (sizeof(R) != 4 || !split_shape(g->N, g->D))) return BOLTZ_EUNSUPPORTED;
+    boltz_status s0;
+    if (split && (s0 = ensure_split_tables(g)) != BOLTZ_OK) return s0;
+    s0 = prepare_plan(g, n_inputs, pj, pl, n_pairs, form, 0, st, sizeof(R));
     if (s0 != BOLTZ_OK) return s0;
     const Plan& plan = g->last_plan;
     const DispatchT<R>* dp = dispatch_of(g->N, g->D, R(0));
@@ -748,6 +841,14 @@ boltz_status run_batched(boltz_grid_s* g, const typename Prec<R>::C* spectra, in
             dp->synth(sp, SYN_PREP, st);
         }
         const R* lam_c = fN + size_t(nc) * g->n;
+        uint8_t* img = reinterpret_cast<uint8_t*>(ws + plan.off_img);
+        (void)img;
+        if constexpr (sizeof(R) == 4) {
+            if (split) {
+                ProfScope ps(g, BOLTZ_KCLASS_PREP, st);
+                launch_split_input(fN, img, nc, st);
+            }
+        }
         BZ_CUDA(cudaMemsetAsync(qhat, 0, size_t(c.U) * g->half * sizeof(C), st));
         // Node blocks run synth -> contract on the caller's stream and the radial
         // step on the side stream, with P double-buffered: the radial step of
@@ -766,7 +867,16 @@ boltz_status run_batched(boltz_grid_s* g, const typename Prec<R>::C* spectra, in
             ss.n_fields = nq * g->M * nc;
             {
                 ProfScope ps(g, BOLTZ_KCLASS_SHIFT, st);
-                dp->synth(ss, SYN_SHIFT, st);
+                if constexpr (sizeof(R) == 4) {
+                    if (split) {
+                        SplitParams spp{img, g->d_smat, A, g->d_err, nc, g->M, q0, ss.n_fields};
+                        launch_shift_split(spp, g->sms, st);
+                    } else {
+                        dp->synth(ss, SYN_SHIFT, st);
+                    }
+                } else {
+                    dp->synth(ss, SYN_SHIFT, st);
+                }
             }
             if (blk >= 2) BZ_CUDA(cudaStreamWaitEvent(st, g->ev_free[b], 0));
             ConParamsT<R> cp{};
@@ -1168,7 +1278,8 @@ boltz_status boltz_grid_init(boltz_grid* out, int N, int d_v, double L, double R
         boltz_grid_destroy(g);
         return s;
     };
-    if (cudaGetDevice(&g->device) != cudaSuccess) {
+    if (cudaGetDevice(&g->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, g->device) != cudaSuccess) {
         (void)cudaGetLastError();
         delete g;
         return BOLTZ_ECUDA;
@@ -1248,6 +1359,7 @@ boltz_status boltz_grid_destroy(boltz_grid g) {
     cudaFree(g->d_ctab64);
     cudaFree(g->d_gm64);
     cudaFree(g->d_w64);
+    cudaFree(g->d_smat);
     cudaFree(g->d_ws);
     delete g;
     return BOLTZ_OK;
@@ -1274,7 +1386,8 @@ boltz_status boltz_spectrum(boltz_grid g, const float* f, int n_inputs, void* sp
 
 boltz_status boltz_workspace_size(boltz_grid g, int n_inputs, const int32_t* pair_j, const int32_t* pair_l,
                                   int n_pairs, int form, size_t* bytes) {
-    if (!g || !bytes || (form != BOLTZ_FORM_BATCHED && form != BOLTZ_FORM_PLAIN)) return BOLTZ_EINVAL;
+    if (!g || !bytes || !valid_form(form)) return BOLTZ_EINVAL;
+    if (form == BOLTZ_FORM_SPLIT_BF16 && !split_shape(g->N, g->D)) return BOLTZ_EUNSUPPORTED;
     boltz_status s = check_pairs(n_inputs, pair_j, pair_l, n_pairs);
     if (s != BOLTZ_OK) return s;
     if (n_pairs == 0) {
@@ -1289,7 +1402,7 @@ boltz_status boltz_workspace_size(boltz_grid g, int n_inputs, const int32_t* pai
 
 boltz_status boltz_collide_batched(boltz_grid g, const void* spectra, int n_inputs, const int32_t* pair_j,
                                    const int32_t* pair_l, int n_pairs, float* Q_out, int form, void* stream) {
-    if (!g || (form != BOLTZ_FORM_BATCHED && form != BOLTZ_FORM_PLAIN)) return BOLTZ_EINVAL;
+    if (!g || !valid_form(form)) return BOLTZ_EINVAL;
     boltz_status s = check_pairs(n_inputs, pair_j, pair_l, n_pairs);
     if (s != BOLTZ_OK) return s;
     if (n_pairs == 0) return BOLTZ_OK;
@@ -1362,7 +1475,7 @@ boltz_status boltz_spectrum_f64(boltz_grid g, const double* f, int n_inputs, voi
 
 boltz_status boltz_collide_batched_f64(boltz_grid g, const void* spectra, int n_inputs, const int32_t* pair_j,
                                        const int32_t* pair_l, int n_pairs, double* Q_out, int form, void* stream) {
-    if (!g || (form != BOLTZ_FORM_BATCHED && form != BOLTZ_FORM_PLAIN)) return BOLTZ_EINVAL;
+    if (!g || !valid_form(form)) return BOLTZ_EINVAL;
     if (!fp64_shape(g->N, g->D)) return BOLTZ_EUNSUPPORTED;
     boltz_status s = check_pairs(n_inputs, pair_j, pair_l, n_pairs);
     if (s != BOLTZ_OK) return s;
@@ -1434,7 +1547,7 @@ boltz_status boltz_moments(boltz_grid g, const float* Q, int n_fields, double* o
 }
 
 boltz_status boltz_batch_plan(boltz_batch* out, const boltz_work* items, int n_items, int form) {
-    if (!out || !items || n_items <= 0 || (form != BOLTZ_FORM_BATCHED && form != BOLTZ_FORM_PLAIN))
+    if (!out || !items || n_items <= 0 || !valid_form(form))
         return BOLTZ_EINVAL;
     for (int i = 0; i < n_items; ++i) {
         const boltz_work& w = items[i];
@@ -1444,6 +1557,10 @@ boltz_status boltz_batch_plan(boltz_batch* out, const boltz_work* items, int n_i
         if (w.V && (!w.T_out || w.r < 1 || w.r > 64 || w.r * w.r != w.n_pairs)) return BOLTZ_EINVAL;
         for (int k = 0; k < i; ++k)
             if (items[k].grid == w.grid) return BOLTZ_EINVAL;      // one item per grid
+        if (form == BOLTZ_FORM_SPLIT_BF16) {
+            if (!split_shape(w.grid->N, w.grid->D)) return BOLTZ_EUNSUPPORTED;
+            if ((s = ensure_split_tables(w.grid)) != BOLTZ_OK) return s;
+        }
     }
     boltz_batch_s* b = new (std::nothrow) boltz_batch_s();
     if (!b) return BOLTZ_ENOMEM;
@@ -1544,7 +1661,7 @@ boltz_status boltz_batch_destroy(boltz_batch b) {
 boltz_status boltz_autotune(boltz_grid g, const void* spectra, int n_inputs, const int32_t* pair_j,
                             const int32_t* pair_l, int n_pairs, float* Q_scratch, int form, const char* cache_path,
                             void* stream, int* chosen_mb) {
-    if (!g || (form != BOLTZ_FORM_BATCHED && form != BOLTZ_FORM_PLAIN)) return BOLTZ_EINVAL;
+    if (!g || !valid_form(form)) return BOLTZ_EINVAL;
     boltz_status s = check_pairs(n_inputs, pair_j, pair_l, n_pairs);
     if (s != BOLTZ_OK) return s;
     if (n_pairs == 0 || !spectra || !Q_scratch) return BOLTZ_EINVAL;
