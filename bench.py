@@ -424,7 +424,7 @@ def main():
 
     # split-precision form (BF16x3 DFT-as-GEMM shifted fields on the tensor cores), same batch
     split = None
-    split_ok = (N, d) == (32, 3)
+    split_ok = d == 3 and N in (32, 64)
     if split_ok and not args.no_split:
         Qs = torch.empty_like(Q)
         split_mb = args.field_budget_mb or B.boltz_autotune(g, spec, pj, pl, Q_scratch=Qs, form=B.BOLTZ_FORM_SPLIT_BF16,
@@ -448,7 +448,7 @@ def main():
         B.boltz_sync_status(g)
         ls, mss = prof_s["shift"]
         fields_per_launch = n_rho * M * n_in / (ls / max(3, args.steps // 4))
-        # executed tensor work: 3 passes x (N^2/128 tiles) x (2N/16 K-steps) x 2*128*(2N)*16 per field
+        # executed tensor work: 3 passes x (N^2/128 tiles, all CTAs) x (2N/16 K-steps) x 2*128*(2N)*16 per field
         tc_flops_field = 3 * (N * N // 128) * (2 * N // 16) * 2 * 128 * (2 * N) * 16
         tc_achieved = tc_flops_field * fields_per_launch / (mss / ls * 1e-3) / 1e12
         bf16_peak, peak_src = 1900.0, "fallback 1.9 PFLOP/s dense BF16 burst (no MEASURED_PEAKS.json)"

@@ -84,6 +84,7 @@ struct boltz_grid_s {
     double* d_w64 = nullptr;
     // split-precision form: per-node BF16 shift matrices (built on first use)
     uint8_t* d_smat = nullptr;
+    int split_clusters = 1;           // resident clusters of the split kernel
     int* d_err = nullptr;        // device error word (bit kErrTimeout: a bounded wait gave up)
     // workspace
     char* d_ws = nullptr;
@@ -118,8 +119,21 @@ bool supported_shape(int N, int D) {
 // voxel chunk is 256 (3D 8^3, 16^3; 2D 16^2, 32^2).
 bool fp64_shape(int N, int D) { return D == 3 ? (N == 8 || N == 16) : (N == 16 || N == 32); }
 
-// Shapes of the split-precision form (the whole field is one tensor-core operand in shared memory).
-bool split_shape(int N, int D) { return D == 3 && N == 32; }
+// Shapes of the split-precision form: 3D 32^3 (one CTA per field)
+// and 64^3 (clusters of 8 CTAs, 1/8 of the field each).
+bool split_shape(int N, int D) { return D == 3 && (N == 32 || N == 64); }
+
+#ifndef BOLTZ_SPLIT_CL32
+#define BOLTZ_SPLIT_CL32 1
+#endif
+constexpr int kSplitCL32 = BOLTZ_SPLIT_CL32;   // CTAs per 32^3 field in the split form (1: measured faster than 2)
+constexpr int kSplitCL64 = 8;
+
+// Bytes of one pre-split input image (all CTAs' parts) of the split form.
+size_t split_image_bytes(int N) {
+    return N == 64 ? size_t(kSplitCL64) * SplitGeo<64, kSplitCL64>::A_BYTES
+                   : size_t(kSplitCL32) * SplitGeo<32, kSplitCL32>::A_BYTES;
+}
 
 bool valid_form(int form) {
     return form == BOLTZ_FORM_BATCHED || form == BOLTZ_FORM_PLAIN || form == BOLTZ_FORM_SPLIT_BF16;
@@ -328,7 +342,7 @@ boltz_status build_plan(const boltz_grid_s* g, int n_inputs, const int32_t* pj, 
     plan.off_lam = w;
     w = align_up(w + size_t(plan.max_nc) * field_bytes, 256);
     plan.off_img = w;     // pre-split inputs of the split-precision form
-    if (form == BOLTZ_FORM_SPLIT_BF16) w = align_up(w + size_t(plan.max_nc) * SplitGeo<32>::A_BYTES, 256);
+    if (form == BOLTZ_FORM_SPLIT_BF16) w = align_up(w + size_t(plan.max_nc) * split_image_bytes(g->N), 256);
     plan.total = w;
     return BOLTZ_OK;
 }
@@ -746,11 +760,11 @@ float bf16_value(uint16_t h) {
 // Nyquist mode is excluded), split into BF16 hi/lo and laid out as the
 // K-major core-matrix operand described in split.cuh.  Built once per grid
 // (synchronous; never during stream capture).
-boltz_status ensure_split_tables(boltz_grid_s* g) {
-    if (g->d_smat) return BOLTZ_OK;
-    using S = SplitGeo<32>;
-    const int N = g->N, nodes = g->n_rho * g->M;
-    std::vector<uint16_t> img(size_t(nodes) * S::B_BYTES / 2, 0);
+template <int N, int CL>
+void fill_split_tables(const boltz_grid_s* g, std::vector<uint16_t>& img) {
+    using S = SplitGeo<N, CL>;                    // B' depends on N only
+    const int nodes = g->n_rho * g->M;
+    img.assign(size_t(nodes) * S::B_BYTES / 2, 0);
     std::vector<double> sv(N);
     for (int node = 0; node < nodes; ++node) {
         for (int a = 0; a < 3; ++a) {
@@ -760,28 +774,81 @@ boltz_status ensure_split_tables(boltz_grid_s* g) {
                 for (int k = 1; k < N / 2; ++k) acc += 2.0 * std::cos(kPi * k * (2.0 * d / N - sh / g->L));
                 sv[d] = acc / N;
             }
+            uint16_t hi[N], lo[N];
+            for (int d = 0; d < N; ++d) {
+                hi[d] = bf16_rne((float)sv[d]);
+                lo[d] = bf16_rne((float)(sv[d] - (double)bf16_value(hi[d])));
+            }
             uint16_t* B = img.data() + (size_t(node) * S::B_BYTES + size_t(a) * S::B_AXIS_BYTES) / 2;
             for (int n = 0; n < S::NB; ++n) {
                 const int i = n % N;
                 for (int kp = 0; kp < S::KP; ++kp) {
-                    const int m = kp / 2;
-                    const double sim = sv[(i - m + N) % N];
-                    const uint16_t hi = bf16_rne((float)sim);
-                    const uint16_t lo = bf16_rne((float)(sim - (double)bf16_value(hi)));
-                    const uint16_t v = n < N ? hi : ((kp & 1) ? (uint16_t)0 : lo);
+                    const int d = (i - kp / 2 + N) % N;
+                    const uint16_t v = n < N ? hi[d] : ((kp & 1) ? (uint16_t)0 : lo[d]);
                     const size_t off = (size_t(n / 8) * S::KCORES + kp / 8) * 128 + (n % 8) * 16 + (kp % 8) * 2;
                     B[off / 2] = v;
                 }
             }
         }
     }
+}
+
+// Clusters of the split kernel that fit on the device at once (all resident).
+template <int N, int CL>
+int resident_split_clusters(int sms) {
+    using S = SplitGeo<N, CL>;
+    if constexpr (CL == 1) {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_shift_split<N, CL>, kSplitThreads, S::SMEM) !=
+                cudaSuccess ||
+            per_sm < 1) {
+            (void)cudaGetLastError();
+            return sms;
+        }
+        return per_sm * sms;
+    } else {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(CL * 64, 1, 1);
+        cfg.blockDim = dim3(kSplitThreads, 1, 1);
+        cfg.dynamicSmemBytes = S::SMEM;
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, k_shift_split<N, CL>, &cfg) != cudaSuccess || n < 1) {
+            (void)cudaGetLastError();
+            return std::max(1, sms / CL);
+        }
+        return n;
+    }
+}
+
+// Per-node B' operands of the split-precision form: for node (q, p) and axis
+// a the shift-interpolation matrix S(s)[i][m] = (1/N) sum_{|k| < N/2}
+// exp(i pi k ((i - m) dv - s) / L), s = rho_q sigma_{p,a} / 2 (real: the
+// Nyquist mode is excluded), split into BF16 hi/lo and laid out as the
+// K-major core-matrix operand described in split.cuh.  Built once per grid
+// (synchronous; never during stream capture).
+boltz_status ensure_split_tables(boltz_grid_s* g) {
+    if (g->d_smat) return BOLTZ_OK;
+    std::vector<uint16_t> img;
+    cudaError_t e;
+    if (g->N == 64) {
+        fill_split_tables<64, kSplitCL64>(g, img);
+        e = set_smem(k_shift_split<64, kSplitCL64>, SplitGeo<64, kSplitCL64>::SMEM);
+        if (e == cudaSuccess) g->split_clusters = resident_split_clusters<64, kSplitCL64>(g->sms);
+    } else {
+        fill_split_tables<32, kSplitCL32>(g, img);
+        e = set_smem(k_shift_split<32, kSplitCL32>, SplitGeo<32, kSplitCL32>::SMEM);
+        if (e == cudaSuccess) g->split_clusters = resident_split_clusters<32, kSplitCL32>(g->sms);
+    }
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return BOLTZ_ECUDA;
+    }
     uint8_t* d = nullptr;
     if (cudaMalloc(&d, img.size() * 2) != cudaSuccess) {
         (void)cudaGetLastError();
         return BOLTZ_ENOMEM;
     }
-    if (cudaMemcpy(d, img.data(), img.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess ||
-        set_smem(k_shift_split<32>, SplitGeo<32>::SMEM) != cudaSuccess) {
+    if (cudaMemcpy(d, img.data(), img.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess) {
         cudaFree(d);
         return BOLTZ_ECUDA;
     }
@@ -789,15 +856,20 @@ boltz_status ensure_split_tables(boltz_grid_s* g) {
     return BOLTZ_OK;
 }
 
-void launch_split_input(const float* fN, uint8_t* img, int nc, cudaStream_t st) {
-    const size_t total = size_t(nc) * 32 * 32 * 32;
+void launch_split_input(int N, const float* fN, uint8_t* img, int nc, cudaStream_t st) {
+    const size_t total = size_t(nc) * N * N * N;
     const int grid = (int)std::min<size_t>((total + 255) / 256, 4096);
-    k_split_input<32><<<grid, 256, 0, st>>>(fN, img, nc);
+    if (N == 64) k_split_input<64, kSplitCL64><<<grid, 256, 0, st>>>(fN, img, nc);
+    else k_split_input<32, kSplitCL32><<<grid, 256, 0, st>>>(fN, img, nc);
 }
 
-void launch_shift_split(const SplitParams& p, int sms, cudaStream_t st) {
-    const int grid = std::max(1, std::min(p.n_fields, sms));     // one CTA per SM, contiguous field ranges
-    k_shift_split<32><<<grid, kSplitThreads, SplitGeo<32>::SMEM, st>>>(p);
+// Persistent launch: every resident cluster takes a contiguous range of fields.
+void launch_shift_split(int N, const SplitParams& p, int clusters, cudaStream_t st) {
+    const int ncl = std::max(1, std::min(p.n_fields, clusters));
+    if (N == 64)
+        k_shift_split<64, kSplitCL64><<<ncl * kSplitCL64, kSplitThreads, SplitGeo<64, kSplitCL64>::SMEM, st>>>(p);
+    else
+        k_shift_split<32, kSplitCL32><<<ncl * kSplitCL32, kSplitThreads, SplitGeo<32, kSplitCL32>::SMEM, st>>>(p);
 }
 
 // One batched evaluation in precision R (float: the product path; double:
@@ -846,7 +918,7 @@ boltz_status run_batched(boltz_grid_s* g, const typename Prec<R>::C* spectra, in
         if constexpr (sizeof(R) == 4) {
             if (split) {
                 ProfScope ps(g, BOLTZ_KCLASS_PREP, st);
-                launch_split_input(fN, img, nc, st);
+                launch_split_input(g->N, fN, img, nc, st);
             }
         }
         BZ_CUDA(cudaMemsetAsync(qhat, 0, size_t(c.U) * g->half * sizeof(C), st));
@@ -870,7 +942,7 @@ boltz_status run_batched(boltz_grid_s* g, const typename Prec<R>::C* spectra, in
                 if constexpr (sizeof(R) == 4) {
                     if (split) {
                         SplitParams spp{img, g->d_smat, A, g->d_err, nc, g->M, q0, ss.n_fields};
-                        launch_shift_split(spp, g->sms, st);
+                        launch_shift_split(g->N, spp, g->split_clusters, st);
                     } else {
                         dp->synth(ss, SYN_SHIFT, st);
                     }

@@ -73,6 +73,30 @@ def test_split_full_size_c2_sampled_pairs(B):
     assert np.max(np.abs(Ts.reshape(16, 256) - T64)) / np.max(np.abs(T64)) < 1e-5
 
 
+def test_split_64cube_small_quadrature(B):
+    """64^3 on [-10,10]^3 (8-CTA clusters per field, the pass-2 -> 3 operand
+    exchanged through distributed shared memory), N_rho=2 x M=6."""
+    cfg = (64, 3, 10.0, 10.0, 1.0, 2, 6)
+    F = as_fp32(W.random_fields(64, 3, 10.0, 2, seed=64))
+    pairs = [(0, 1), (1, 0), (1, 1)]
+    Qs = gpu_collide(B, cfg, F, pairs, form=SPLIT)
+    _, Qo, s = oracle_collide(cfg, F, pairs)
+    assert rel_err(Qs, Qo, s).max() < TOL_SPLIT
+
+
+def test_split_c4_full_size_matches_fp32_form(B):
+    """C4 workload (64^3, N_rho=32 x M=86, rank 8, seed 2113): all 64 pairs in
+    the split form against the FP32 batched form (which meets 1e-5 against the
+    oracle's gain symmetry and bilinearity in the FP32 parity tests)."""
+    cfg = (64, 3, 10.0, 10.0, 1.0, 32, 86)
+    V = as_fp32(W.hermite_maxwellian_basis(64, 3, 10.0, 8, seed=2113))
+    pairs = [(j, l) for j in range(8) for l in range(8)]
+    Qs = gpu_collide(B, cfg, V, pairs, form=SPLIT)
+    Qf = gpu_collide(B, cfg, V, pairs, form=0)
+    scale = np.max(np.abs(Qf), axis=(1, 2, 3))
+    assert (np.max(np.abs(Qs - Qf), axis=(1, 2, 3)) / scale).max() < TOL_SPLIT
+
+
 def test_split_form_rejected_where_not_built(B):
     import torch
     g = B.boltz_grid_init(16, 3, 8.0, 8.0, 1.0, 2, 6)
