@@ -9,5 +9,7 @@ Modules:
               derived from their moment equations.
   collision   the separated algorithm step by step (plain separable DFTs),
               the brute-force direct sum, projection and moments.
+  lowrank     the low-rank step pieces that consume the batch: K- and
+              L-step collision terms, weighted QR, SVD rank truncation.
 """
-from . import quadrature, collision  # noqa: F401
+from . import quadrature, collision, lowrank  # noqa: F401
