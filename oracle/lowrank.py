@@ -12,6 +12,8 @@ projection the collision library returns.
 
   K-step collision term (Sec. 2.4, K-step (b)):
       C_j(x) = sum_{m,n} T_jmn K_m(x) K_n(x)
+  S-step collision term (Sec. 2.4, S-step (a)):
+      D_ij = sum_{m,n} T_jmn sum_l ( sum_k E_ikl S_km ) S_ln
   L-step coupling and collision term (Sec. 2.4, L-step (b)):
       C_ipq = sum_n ( sum_m E_imn S_mp ) S_nq,   E_imn = <X_i X_m X_n>_x
       G_i(v) = sum_{p,q} Q(V_p, V_q)(v) C_ipq
@@ -62,6 +64,25 @@ def lstep_coupling(E: np.ndarray, S: np.ndarray) -> np.ndarray:
             for q in range(r):
                 C[i, p, q] = np.dot(inner[i, p], S[:, q])
     return C
+
+
+def sstep_collision(T: np.ndarray, E: np.ndarray, S: np.ndarray) -> np.ndarray:
+    """S-step collision term (Sec. 2.4, S-step (a)), in the paper's order:
+    D_ij = sum_{m,n} T_jmn sum_l ( sum_k E_ikl S_km ) S_ln."""
+    T = np.asarray(T, dtype=np.float64)
+    E = np.asarray(E, dtype=np.float64)
+    S = np.asarray(S, dtype=np.float64)
+    r = S.shape[0]
+    D = np.zeros((r, r))
+    for i in range(r):
+        inner = np.zeros((r, r))               # inner[m, l] = sum_k E_ikl S_km
+        for m in range(r):
+            for l in range(r):
+                inner[m, l] = np.dot(E[i, :, l], S[:, m])
+        M = inner @ S                          # M[m, n] = sum_l inner[m, l] S_ln
+        for j in range(r):
+            D[i, j] = np.sum(T[j] * M)
+    return D
 
 
 def triple_products(X: np.ndarray, w: float) -> np.ndarray:

@@ -124,3 +124,29 @@ def test_rotation_keeps_orthonormality_and_identity():
     Z = LR.rotate(Y, U, 3)
     assert np.allclose(w * Z @ Z.T, np.eye(3), atol=1e-12)
     assert np.allclose(LR.rotate(Y, np.eye(r), r), Y)
+
+
+def test_sstep_term_equals_projection_of_the_kstep_term():
+    """D_ij = <X_i V_j, Q(f, f)>_{x,v} with f = sum X_k S_kl V_l, i.e.
+    w_x sum_x X_i(x) C_j(x) with C the K-step term of K_m = sum_k X_k S_km."""
+    rng = np.random.default_rng(10)
+    r, nx, w = 4, 11, 0.3
+    T = rng.standard_normal((r, r, r))
+    X = rng.standard_normal((r, nx))
+    S = rng.standard_normal((r, r))
+    E = LR.triple_products(X, w)
+    got = LR.sstep_collision(T, E, S)
+    K = S.T @ X                                # K_m(x) = sum_k X_k(x) S_km
+    Ck = LR.kstep_collision(T, K)              # [r][nx]
+    want = w * X @ Ck.T                        # D_ij = w sum_x X_i(x) C_j(x)
+    assert np.max(np.abs(got - want)) <= 1e-12 * np.max(np.abs(want))
+
+
+def test_coupling_closed_form():
+    """With E_imn = delta_im delta_in and S = identity, C_ipq = delta_ip delta_iq."""
+    r = 5
+    E = np.zeros((r, r, r))
+    for i in range(r):
+        E[i, i, i] = 1.0
+    C = LR.lstep_coupling(E, np.eye(r))
+    assert np.array_equal(C, E)
