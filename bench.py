@@ -207,6 +207,51 @@ def sample_errors(B, g, results, forms):
     return out
 
 
+def lowrank_consumers(B, T, Q, r, n_v, flush, dev, n_x=1000, reps=20):
+    """Times the consumers of one pair batch on its own T and Q: K-step term
+    over n_x cells (the paper's 1D shock runs use 1000 cells), L-step term,
+    FP64 QR of K and of L, SVD truncation and the two rotations.  Each call
+    is timed alone with CUDA events after an L2 flush."""
+    import torch
+    rng = np.random.default_rng(5)
+    K = torch.tensor(rng.standard_normal((r, n_x)), dtype=torch.float32, device=dev)
+    C = torch.tensor(rng.standard_normal((r, r, r)), dtype=torch.float32, device=dev)
+    Kd = torch.tensor(rng.standard_normal((r, n_x)), dtype=torch.float64, device=dev)
+    Ld = torch.tensor(rng.standard_normal((r, n_v)), dtype=torch.float64, device=dev)
+    S = torch.tensor(rng.standard_normal((r, r)), dtype=torch.float64, device=dev)
+    U, _, Qm, _, _ = B.boltz_svd_truncate_f64(S, 0.0)
+    ops = {
+        "kstep_collision": (lambda: B.boltz_kstep_collision(T, K), 2.0 * r ** 3 * n_x, 4.0 * (2 * r * n_x + r ** 3)),
+        "coupling_and_sstep": (lambda: B.boltz_lowrank_coupling(C, C[0], T), 4.0 * r ** 4 + 2.0 * r ** 4,
+                               4.0 * (3 * r ** 3 + r * r)),
+        "lstep_collision": (lambda: B.boltz_lstep_collision(Q, C), 2.0 * r ** 3 * n_v, 4.0 * (r * r + r) * n_v),
+        "qr_f64_K": (lambda: B.boltz_qr_f64(Kd, 0.06), 8.0 * r * r * n_x, 8.0 * 6 * r * n_x),
+        "qr_f64_L": (lambda: B.boltz_qr_f64(Ld, 0.125), 8.0 * r * r * n_v, 8.0 * 6 * r * n_v),
+        "svd_truncate_f64": (lambda: B.boltz_svd_truncate_f64(S, 1e-8), None, None),
+        "rotate_f64_V": (lambda: B.boltz_basis_rotate_f64(Ld, Qm, r), 2.0 * r * r * n_v, 8.0 * 2 * r * n_v),
+    }
+    out = {"rank": r, "n_x": n_x, "n_v": n_v}
+    for name, (fn, flops, nbytes) in ops.items():
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        us = 1e3 * float(np.median(ts))
+        rec = {"us": us}
+        if flops:
+            rec["gflop_s"] = flops / (us * 1e-6) / 1e9
+            rec["gb_s"] = nbytes / (us * 1e-6) / 1e9
+        out[name] = rec
+    return out
+
+
 def host_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -468,6 +513,12 @@ def main():
                                   "share_of_step": mss / max(sum(ms for _, ms in prof_s.values()), 1e-9)}}
         split["speedup_vs_fp32_batched"] = split["value"] / (value / world)
 
+    # low-rank step consumers of this batch (Sec. 2.4 K- and L-step collision terms,
+    # FP64 QR of K and L, Sec. 3.2 SVD truncation and basis rotation), L2 flushed before each call
+    lowrank = None
+    if kind == "pairs":
+        lowrank = lowrank_consumers(B, T, Q, n_in, N ** d, flush, dev)
+
     # roofline of the dominant kernel (the shifted-field inverse transforms)
     props = torch.cuda.get_device_properties(dev)
     clocks = clk.summary()
@@ -529,6 +580,7 @@ def main():
             "e2e": e2e,
             "plain_fp32": plain,
             "split_bf16": split,
+            "lowrank_step_consumers": lowrank,
             "error_vs_oracle": errors,
             "cpu_baseline": cpu,
             "wall_s_timed_region": wall,

@@ -388,6 +388,81 @@ boltz_status boltz_profile_enable(boltz_grid g, int enable);
  */
 boltz_status boltz_profile_read(boltz_grid g, int reset, long long* launches, double* ms);
 
+/*
+ * ---- Low-rank step consumers of the collision batch (paper Sec. 2, eqs.
+ * "eqn:K-step detailed" and "eqn:L-step detailed"; Sec. 2.4, the fully
+ * discrete scheme; Sec. 3.2, dropping basis).  They take no grid handle.
+ * Functions of x or v are stored as rows ([r][n], r in 1..64); every pointer
+ * is device memory; work is queued on `stream`.  Errors: BOLTZ_EINVAL
+ * (ranges, NULL pointers), BOLTZ_ECUDA.
+ *
+ * K-step collision term:  C_out[j][x] = sum_{m,n} T[j][m][n] K[m][x] K[n][x]
+ *   T  float32 [r][r][r] (boltz_project's T_out: T[j][m][n] = <V_j Q(V_m,V_n)>_v)
+ *   K  float32 [r][n_x]  K_m(x) = sum_i X_i(x) S_im;  C_out float32 [r][n_x]
+ */
+boltz_status boltz_kstep_collision(const float* T, int r, const float* K, int n_x, float* C_out,
+                                   void* stream);
+
+/*
+ * L-step collision term:  G_out[i][v] = sum_{p,q} C[i][p][q] Q[p r + q][v]
+ *   Q  float32 [r*r][n_v]  (boltz_collide_batched over all ordered pairs (p, q))
+ *   C  float32 [r][r][r]   C_ipq = sum_n (sum_m <X_i X_m X_n>_x S_mp) S_nq
+ *   G_out float32 [r][n_v]
+ */
+boltz_status boltz_lstep_collision(const float* Q, int r, const float* C, int n_v, float* G_out,
+                                   void* stream);
+
+/*
+ * r^4 couplings of the S- and L-steps (Sec. 2.4, S-step (a), L-step (b)):
+ *   C_out[i][p][q] = sum_n ( sum_m E[i][m][n] S[m][p] ) S[n][q]
+ *   and, when T is not NULL, the S-step collision term
+ *   D_out[i][j] = sum_{m,n} T[j][m][n] C_out[i][m][n]
+ *               = sum_{m,n} T_jmn sum_l ( sum_k E_ikl S_km ) S_ln.
+ *   E  float32 [r][r][r]  E_imn = <X_i X_m X_n>_x;  S float32 [r][r]
+ *   T  float32 [r][r][r] or NULL;  C_out float32 [r][r][r];  D_out float32 [r][r]
+ * C_out is the coupling boltz_lstep_collision takes.
+ */
+boltz_status boltz_lowrank_coupling(const float* E, const float* S, int r, const float* T,
+                                    float* C_out, float* D_out, void* stream);
+
+/*
+ * QR of the K- and L-steps in FP64 (Cholesky-QR2: Gram matrix, Cholesky
+ * factor and triangular solve, done twice):  W_j = sum_i Y_i R[i][j] with
+ * w sum_x Y_i(x) Y_k(x) = delta_ik (w = the midpoint-rule cell volume) and R
+ * upper triangular with a positive diagonal.  For the K-step X = Y, S = R;
+ * for the L-step (L_i = sum_j S_ij V_j) V = Y, S = R^T.
+ *   W, Y       float64 [r][n] (Y may equal W), n >= r
+ *   R          float64 [r][r] row-major
+ *   workspace  device bytes from boltz_qr_f64_workspace(r, n)
+ *   info       int32: 0, or k + 1 when the k-th pivot was not positive
+ *              (the functions are linearly dependent to working precision;
+ *              Y and R are then NaN)
+ */
+boltz_status boltz_qr_f64_workspace(int r, int n, size_t* bytes);
+boltz_status boltz_qr_f64(const double* W, int r, int n, double w, double* Y, double* R,
+                          void* workspace, int* info, void* stream);
+
+/*
+ * Rank truncation of Sec. 3.2 in FP64: S = U diag(sigma) Q^T with sigma
+ * descending (one-sided Jacobi), r_keep = the number of sigma >= drop_tol.
+ *   S, U, Q  float64 [r][r] row-major (columns of U and Q are the singular
+ *            vectors; a column whose sigma is 0 is returned as zeros in U)
+ *   sigma    float64 [r];  r_keep, info int32 (info 0 = converged, 1 = the
+ *            sweep limit was reached)
+ * Then X_bar = X U[:, :r_keep], V_bar = V Q[:, :r_keep] (boltz_basis_rotate_f64)
+ * and S_bar = diag(sigma[:r_keep]).
+ */
+boltz_status boltz_svd_truncate_f64(const double* S, int r, double drop_tol, double* U, double* sigma,
+                                    double* Q, int* r_keep, int* info, void* stream);
+
+/*
+ * Basis rotation:  X_out[k][x] = sum_i X[i][x] U[i][k], k < r_new <= r.
+ *   X float64 [r][n], U float64 [r][r] row-major, X_out float64 [r_new][n]
+ *   (must not alias X).
+ */
+boltz_status boltz_basis_rotate_f64(const double* X, int r, int n, const double* U, int r_new,
+                                    double* X_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

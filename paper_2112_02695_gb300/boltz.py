@@ -34,6 +34,8 @@ EXPORTED = (
     "boltz_project_noalloc", "boltz_sync_status", "boltz_selftest", "boltz_moments",
     "boltz_batch_plan", "boltz_batch_run", "boltz_batch_kernel_count", "boltz_batch_destroy",
     "boltz_autotune", "boltz_spectrum_f64", "boltz_collide_batched_f64", "boltz_project_f64",
+    "boltz_kstep_collision", "boltz_lstep_collision", "boltz_qr_f64_workspace", "boltz_qr_f64",
+    "boltz_svd_truncate_f64", "boltz_basis_rotate_f64", "boltz_lowrank_coupling",
 )
 
 KERNEL_CLASSES = ("spectrum", "prep", "shift", "contract", "radial", "output", "project")
@@ -95,6 +97,13 @@ def _load() -> ctypes.CDLL:
         "boltz_collide_batched_f64": ([vp, vp, ctypes.c_int, i32p, i32p, ctypes.c_int, vp, ctypes.c_int, vp],
                                       ctypes.c_int),
         "boltz_project_f64": ([vp, vp, ctypes.c_int, vp, vp, vp], ctypes.c_int),
+        "boltz_kstep_collision": ([vp, ctypes.c_int, vp, ctypes.c_int, vp, vp], ctypes.c_int),
+        "boltz_lstep_collision": ([vp, ctypes.c_int, vp, ctypes.c_int, vp, vp], ctypes.c_int),
+        "boltz_qr_f64_workspace": ([ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+        "boltz_qr_f64": ([vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, vp, vp, vp, vp, vp], ctypes.c_int),
+        "boltz_svd_truncate_f64": ([vp, ctypes.c_int, ctypes.c_double, vp, vp, vp, vp, vp, vp], ctypes.c_int),
+        "boltz_basis_rotate_f64": ([vp, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, vp, vp], ctypes.c_int),
+        "boltz_lowrank_coupling": ([vp, vp, ctypes.c_int, vp, vp, vp, vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -435,3 +444,96 @@ def boltz_batch_kernel_count(batch: Batch) -> int:
 
 def boltz_batch_destroy(batch: Batch):
     batch.close()
+
+
+# ----------------------------------------------------------------------------- low-rank step consumers
+
+def boltz_kstep_collision(T, K, out=None, stream=None):
+    """C[j, x] = sum_{m,n} T[j, m, n] K[m, x] K[n, x]: float32 [r, n_x]."""
+    import torch
+    r, n_x = K.shape
+    if tuple(T.shape) != (r, r, r):
+        raise ValueError("T must be [r, r, r] for K [r, n_x]")
+    if out is None:
+        out = torch.empty((r, n_x), dtype=torch.float32, device=K.device)
+    _check(_lib.boltz_kstep_collision(_dev_ptr(T, "float32", "T"), r, _dev_ptr(K, "float32", "K"), n_x,
+                                      _dev_ptr(out, "float32", "out"), _stream_ptr(stream)), "boltz_kstep_collision")
+    return out
+
+
+def boltz_lstep_collision(Q, C, out=None, stream=None):
+    """G[i, v] = sum_{p,q} C[i, p, q] Q[p*r + q, v]: float32 [r, n_v]."""
+    import torch
+    r = C.shape[0]
+    Q2 = Q.reshape(Q.shape[0], -1)
+    if Q2.shape[0] != r * r or tuple(C.shape) != (r, r, r):
+        raise ValueError("Q must hold r*r fields and C be [r, r, r]")
+    n_v = Q2.shape[1]
+    if out is None:
+        out = torch.empty((r, n_v), dtype=torch.float32, device=Q.device)
+    _check(_lib.boltz_lstep_collision(_dev_ptr(Q2, "float32", "Q"), r, _dev_ptr(C, "float32", "C"), n_v,
+                                      _dev_ptr(out, "float32", "out"), _stream_ptr(stream)), "boltz_lstep_collision")
+    return out
+
+
+def boltz_qr_f64(W, w: float, Y=None, stream=None):
+    """W [r, n] float64 -> (Y [r, n], R [r, r], info int32 tensor [1]) with
+    W_j = sum_i Y_i R[i, j] and w Y Y^T = I."""
+    import torch
+    r, n = W.shape
+    ws = ctypes.c_size_t()
+    _check(_lib.boltz_qr_f64_workspace(r, n, ctypes.byref(ws)), "boltz_qr_f64_workspace")
+    work = torch.empty(ws.value, dtype=torch.uint8, device=W.device)
+    if Y is None:
+        Y = torch.empty_like(W)
+    R = torch.empty((r, r), dtype=torch.float64, device=W.device)
+    info = torch.empty(1, dtype=torch.int32, device=W.device)
+    _check(_lib.boltz_qr_f64(_dev_ptr(W, "float64", "W"), r, n, float(w), _dev_ptr(Y, "float64", "Y"),
+                             _dev_ptr(R, "float64", "R"), ctypes.c_void_p(work.data_ptr()),
+                             _dev_ptr(info, "int32", "info"), _stream_ptr(stream)), "boltz_qr_f64")
+    return Y, R, info
+
+
+def boltz_svd_truncate_f64(S, drop_tol: float, stream=None):
+    """S [r, r] float64 -> (U, sigma, Q, r_keep, info); r_keep and info are
+    int32 device tensors [1]."""
+    import torch
+    r = S.shape[0]
+    dev = S.device
+    U = torch.empty((r, r), dtype=torch.float64, device=dev)
+    Qm = torch.empty((r, r), dtype=torch.float64, device=dev)
+    sigma = torch.empty(r, dtype=torch.float64, device=dev)
+    rk = torch.empty(1, dtype=torch.int32, device=dev)
+    info = torch.empty(1, dtype=torch.int32, device=dev)
+    _check(_lib.boltz_svd_truncate_f64(_dev_ptr(S, "float64", "S"), r, float(drop_tol), _dev_ptr(U, "float64", "U"),
+                                       _dev_ptr(sigma, "float64", "sigma"), _dev_ptr(Qm, "float64", "Q"),
+                                       _dev_ptr(rk, "int32", "r_keep"), _dev_ptr(info, "int32", "info"),
+                                       _stream_ptr(stream)), "boltz_svd_truncate_f64")
+    return U, sigma, Qm, rk, info
+
+
+def boltz_basis_rotate_f64(X, U, r_new: int, out=None, stream=None):
+    """X_out[k] = sum_i X[i] U[i, k] for k < r_new: float64 [r_new, n]."""
+    import torch
+    r, n = X.shape
+    if out is None:
+        out = torch.empty((r_new, n), dtype=torch.float64, device=X.device)
+    _check(_lib.boltz_basis_rotate_f64(_dev_ptr(X, "float64", "X"), r, n, _dev_ptr(U, "float64", "U"), int(r_new),
+                                       _dev_ptr(out, "float64", "out"), _stream_ptr(stream)),
+           "boltz_basis_rotate_f64")
+    return out
+
+
+def boltz_lowrank_coupling(E, S, T=None, stream=None):
+    """C [r, r, r] (the L-step coupling) and, with T, D [r, r] (the S-step
+    collision term), both float32."""
+    import torch
+    r = S.shape[0]
+    C = torch.empty((r, r, r), dtype=torch.float32, device=S.device)
+    D = torch.empty((r, r), dtype=torch.float32, device=S.device) if T is not None else None
+    _check(_lib.boltz_lowrank_coupling(_dev_ptr(E, "float32", "E"), _dev_ptr(S, "float32", "S"), r,
+                                       _dev_ptr(T, "float32", "T") if T is not None else None,
+                                       _dev_ptr(C, "float32", "C"),
+                                       _dev_ptr(D, "float32", "D") if D is not None else None,
+                                       _stream_ptr(stream)), "boltz_lowrank_coupling")
+    return C, D

@@ -20,6 +20,7 @@
 
 #include "boltz.h"
 #include "kernels.cuh"
+#include "lowrank.cuh"
 #include "quadrature.hpp"
 #include "split.cuh"
 #include "tc_kernels.cuh"
@@ -1213,6 +1214,54 @@ void destroy_batch(boltz_batch_s* b) {
 
 }  // namespace
 
+// ==================================================================== low-rank step consumers
+
+namespace {
+
+// The FP64 r x r kernels use more than 48 KB of dynamic shared memory: set once per device.
+boltz_status ensure_lowrank_attrs() {
+    static std::mutex mu;
+    static std::set<int> done;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return BOLTZ_ECUDA;
+    }
+    std::lock_guard<std::mutex> lock(mu);
+    if (done.count(dev)) return BOLTZ_OK;
+    if (set_smem(k_chol_f64, kCholSmem) != cudaSuccess || set_smem(k_svd_jacobi_f64, kSvdSmem) != cudaSuccess ||
+        set_smem(k_lstep_collision<64>, lstep_smem<64>()) != cudaSuccess ||
+        set_smem(k_lr_coupling, kCouplingSmem) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return BOLTZ_ECUDA;
+    }
+    done.insert(dev);
+    return BOLTZ_OK;
+}
+
+int qr_slices(int n) { return std::max(1, std::min(512, n / 128)); }
+
+size_t qr_workspace_bytes(int r, int n) {
+    return align_up(size_t(qr_slices(n) + 2) * r * r * sizeof(double), 256);
+}
+
+template <int RMAX>
+void launch_qr(const double* W, int r, int n, double w, double* Y, double* R, char* ws, int* info, cudaStream_t st) {
+    const int ns = qr_slices(n);
+    double* part = reinterpret_cast<double*>(ws);
+    double* Rinv = part + size_t(ns) * r * r;
+    double* R1 = Rinv + size_t(r) * r;
+    const int grid = (n + kLrThreads - 1) / kLrThreads;
+    k_gram_f64<<<ns, kLrThreads, 0, st>>>(W, r, n, ns, part);
+    k_chol_f64<<<1, 64, kCholSmem, st>>>(part, ns, r, w, nullptr, R1, Rinv, info);
+    k_apply_rinv_f64<RMAX><<<grid, kLrThreads, 0, st>>>(W, Rinv, r, n, Y);
+    k_gram_f64<<<ns, kLrThreads, 0, st>>>(Y, r, n, ns, part);
+    k_chol_f64<<<1, 64, kCholSmem, st>>>(part, ns, r, w, R1, R, Rinv, info);
+    k_apply_rinv_f64<RMAX><<<grid, kLrThreads, 0, st>>>(Y, Rinv, r, n, Y);
+}
+
+}  // namespace
+
 // ==================================================================== C ABI
 
 extern "C" {
@@ -1837,6 +1886,99 @@ boltz_status boltz_profile_read(boltz_grid g, int reset, long long* launches, do
         g->prof_events.clear();
         for (int c = 0; c < BOLTZ_KCLASS_COUNT; ++c) g->launches[c] = 0;
     }
+    return BOLTZ_OK;
+}
+
+boltz_status boltz_kstep_collision(const float* T, int r, const float* K, int n_x, float* C_out, void* stream) {
+    if (r < 1 || r > 64 || n_x < 0) return BOLTZ_EINVAL;
+    if (n_x == 0) return BOLTZ_OK;
+    if (!T || !K || !C_out) return BOLTZ_EINVAL;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    // j-chunks of at most 48 KB of T; enough block rows to give every SM work
+    const int gx = (n_x + kLrThreads - 1) / kLrThreads;
+    const int jmax = std::max(1, std::min(r, 12288 / (r * r)));
+    const int jt = std::max(1, std::min(jmax, (r * gx + 303) / 304));
+    const dim3 grid(gx, (r + jt - 1) / jt);
+    const size_t smem = size_t(jt) * r * r * sizeof(float);
+    if (r <= 16) k_kstep_collision<16><<<grid, kLrThreads, smem, st>>>(T, K, C_out, r, n_x, jt);
+    else if (r <= 32) k_kstep_collision<32><<<grid, kLrThreads, smem, st>>>(T, K, C_out, r, n_x, jt);
+    else k_kstep_collision<64><<<grid, kLrThreads, smem, st>>>(T, K, C_out, r, n_x, jt);
+    BZ_CUDA(cudaGetLastError());
+    return BOLTZ_OK;
+}
+
+boltz_status boltz_lstep_collision(const float* Q, int r, const float* C, int n_v, float* G_out, void* stream) {
+    if (r < 1 || r > 64 || n_v < 0) return BOLTZ_EINVAL;
+    if (n_v == 0) return BOLTZ_OK;
+    if (!Q || !C || !G_out) return BOLTZ_EINVAL;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    boltz_status s = ensure_lowrank_attrs();
+    if (s != BOLTZ_OK) return s;
+    const int grid = (n_v + kLstepVB - 1) / kLstepVB;
+    if (r <= 16) k_lstep_collision<16><<<grid, kLrThreads, lstep_smem<16>(), st>>>(Q, C, G_out, r, n_v);
+    else if (r <= 32) k_lstep_collision<32><<<grid, kLrThreads, lstep_smem<32>(), st>>>(Q, C, G_out, r, n_v);
+    else k_lstep_collision<64><<<grid, kLrThreads, lstep_smem<64>(), st>>>(Q, C, G_out, r, n_v);
+    BZ_CUDA(cudaGetLastError());
+    return BOLTZ_OK;
+}
+
+boltz_status boltz_lowrank_coupling(const float* E, const float* S, int r, const float* T, float* C_out,
+                                    float* D_out, void* stream) {
+    if (r < 1 || r > 64 || !E || !S || !C_out || (T && !D_out)) return BOLTZ_EINVAL;
+    boltz_status s = ensure_lowrank_attrs();
+    if (s != BOLTZ_OK) return s;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    k_lr_coupling<<<r, kLrThreads, kCouplingSmem, st>>>(E, S, T, r, C_out, D_out);
+    BZ_CUDA(cudaGetLastError());
+    return BOLTZ_OK;
+}
+
+boltz_status boltz_qr_f64_workspace(int r, int n, size_t* bytes) {
+    if (r < 1 || r > 64 || n < r || !bytes) return BOLTZ_EINVAL;
+    *bytes = qr_workspace_bytes(r, n);
+    return BOLTZ_OK;
+}
+
+boltz_status boltz_qr_f64(const double* W, int r, int n, double w, double* Y, double* R, void* workspace,
+                          int* info, void* stream) {
+    if (r < 1 || r > 64 || n < r || !(w > 0) || !std::isfinite(w) || !W || !Y || !R || !workspace || !info)
+        return BOLTZ_EINVAL;
+    boltz_status s = ensure_lowrank_attrs();
+    if (s != BOLTZ_OK) return s;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    BZ_CUDA(cudaMemsetAsync(info, 0, sizeof(int), st));
+    char* ws = static_cast<char*>(workspace);
+    if (r <= 16) launch_qr<16>(W, r, n, w, Y, R, ws, info, st);
+    else if (r <= 32) launch_qr<32>(W, r, n, w, Y, R, ws, info, st);
+    else launch_qr<64>(W, r, n, w, Y, R, ws, info, st);
+    BZ_CUDA(cudaGetLastError());
+    return BOLTZ_OK;
+}
+
+boltz_status boltz_svd_truncate_f64(const double* S, int r, double drop_tol, double* U, double* sigma, double* Q,
+                                    int* r_keep, int* info, void* stream) {
+    if (r < 1 || r > 64 || !(drop_tol >= 0) || !std::isfinite(drop_tol) || !S || !U || !sigma || !Q || !r_keep ||
+        !info)
+        return BOLTZ_EINVAL;
+    boltz_status s = ensure_lowrank_attrs();
+    if (s != BOLTZ_OK) return s;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    k_svd_jacobi_f64<<<1, 1024, kSvdSmem, st>>>(S, r, drop_tol, U, sigma, Q, r_keep, info);
+    BZ_CUDA(cudaGetLastError());
+    return BOLTZ_OK;
+}
+
+boltz_status boltz_basis_rotate_f64(const double* X, int r, int n, const double* U, int r_new, double* X_out,
+                                    void* stream) {
+    if (r < 1 || r > 64 || n < 0 || r_new < 0 || r_new > r) return BOLTZ_EINVAL;
+    if (n == 0 || r_new == 0) return BOLTZ_OK;
+    if (!X || !U || !X_out || X_out == X) return BOLTZ_EINVAL;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int grid = (n + kLrThreads - 1) / kLrThreads;
+    if (r <= 16) k_rotate_f64<16><<<grid, kLrThreads, 0, st>>>(X, U, r, r_new, n, X_out);
+    else if (r <= 32) k_rotate_f64<32><<<grid, kLrThreads, 0, st>>>(X, U, r, r_new, n, X_out);
+    else k_rotate_f64<64><<<grid, kLrThreads, 0, st>>>(X, U, r, r_new, n, X_out);
+    BZ_CUDA(cudaGetLastError());
     return BOLTZ_OK;
 }
 

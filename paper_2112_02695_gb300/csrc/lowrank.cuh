@@ -1,0 +1,461 @@
+// Kernels of the low-rank step pieces that consume the collision batch
+// (paper Sec. 2, eqs. "eqn:K-step detailed" and "eqn:L-step detailed";
+// Sec. 2.4, the fully discrete scheme; Sec. 3.2, dropping basis).
+//
+// Functions of x or v are rows: K [r][n_x], V [r][n_v]; r <= 64.
+//   k_kstep_collision   C_j(x) = sum_{m,n} T_jmn K_m(x) K_n(x)            (FP32)
+//   k_lstep_collision   G_i(v) = sum_{p,q} C_ipq Q_{p r + q}(v)             (FP32)
+//   Cholesky-QR2        W_j = sum_i Y_i R_ij, <Y_i, Y_k> = w sum Y_i Y_k = delta  (FP64;
+//                       Fukaya et al., "CholeskyQR2", 2014: Gram matrix,
+//                       Cholesky factor, triangular solve, done twice)
+//   k_svd_jacobi_f64    S = U Sigma Q^T by one-sided (Hestenes) Jacobi rotations
+//                       in round-robin pair order, singular values sorted
+//                       descending; r' = #{sigma >= drop_tol}               (FP64)
+//   k_rotate_f64        X_bar_k = sum_i X_i U_ik, k < r'                    (FP64)
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace boltz_dev {
+
+constexpr int kLrThreads = 256;
+
+// ---------------------------------------------------------------- K-step collision term
+// One thread per cell; K_m(x) of the cell in registers; block row y takes the
+// output slices j in chunks of jt (T[j0 .. j0 + jt) staged in shared memory,
+// jt r^2 floats <= 48 KB), chunks y, y + gridDim.y, ...
+template <int RMAX>
+__global__ void __launch_bounds__(kLrThreads) k_kstep_collision(const float* __restrict__ T,
+                                                               const float* __restrict__ K, float* __restrict__ out,
+                                                               int r, int n, int jt) {
+    extern __shared__ float lr_smem[];
+    const int x = blockIdx.x * kLrThreads + threadIdx.x;
+    float k[RMAX];
+#pragma unroll
+    for (int m = 0; m < RMAX; ++m) k[m] = (m < r && x < n) ? __ldg(&K[(size_t)m * n + x]) : 0.f;
+    const int rr = r * r;
+    for (int j0 = blockIdx.y * jt; j0 < r; j0 += gridDim.y * jt) {
+        const int jn = min(jt, r - j0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < jn * rr; e += kLrThreads) lr_smem[e] = __ldg(&T[(size_t)j0 * rr + e]);
+        __syncthreads();
+        for (int jj = 0; jj < jn; ++jj) {
+            const float* Tj = lr_smem + jj * rr;
+            float acc = 0.f;
+#pragma unroll
+            for (int m = 0; m < RMAX; ++m) {
+                if (m < r) {
+                    float inner = 0.f;
+#pragma unroll
+                    for (int q = 0; q < RMAX; ++q)
+                        if (q < r) inner = fmaf(Tj[m * r + q], k[q], inner);
+                    acc = fmaf(k[m], inner, acc);
+                }
+            }
+            if (x < n) out[(size_t)(j0 + jj) * n + x] = acc;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- L-step collision term
+// A block owns 64 voxels; its 256 threads split the r^2 pair index into
+// LSL = 4 interleaved slices (thread = voxel + 64 slice), each accumulating
+// the r outputs of its voxel over its slice in registers; the slices are
+// summed through shared memory in a fixed order.  C is staged in chunks of
+// 64 pair columns; every Q value is read once, by 64-voxel coalesced loads.
+constexpr int kLstepPC = 64;
+constexpr int kLstepVB = 64;
+constexpr int kLstepSL = kLrThreads / kLstepVB;
+
+template <int RMAX>
+constexpr size_t lstep_smem() {
+    return (size_t(RMAX) * kLstepPC + size_t(kLstepSL - 1) * kLstepVB * RMAX) * sizeof(float);
+}
+
+template <int RMAX>
+__global__ void __launch_bounds__(kLrThreads) k_lstep_collision(const float* __restrict__ Q,
+                                                               const float* __restrict__ C, float* __restrict__ out,
+                                                               int r, int n) {
+    extern __shared__ float lst_smem[];
+    float* Cs = lst_smem;                                     // [RMAX][PC]
+    float* red = lst_smem + RMAX * kLstepPC;                  // [SL-1][RMAX][VB]
+    const int lv = threadIdx.x % kLstepVB, sl = threadIdx.x / kLstepVB;
+    const int v = blockIdx.x * kLstepVB + lv;
+    const int rr = r * r;
+    float acc[RMAX];
+#pragma unroll
+    for (int i = 0; i < RMAX; ++i) acc[i] = 0.f;
+    for (int pq0 = 0; pq0 < rr; pq0 += kLstepPC) {
+        const int pn = min(kLstepPC, rr - pq0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < r * kLstepPC; e += kLrThreads) {
+            const int i = e / kLstepPC, c = e % kLstepPC;
+            Cs[i * kLstepPC + c] = c < pn ? __ldg(&C[(size_t)i * rr + pq0 + c]) : 0.f;
+        }
+        __syncthreads();
+        if (v < n) {
+#pragma unroll 4
+            for (int c = sl; c < pn; c += kLstepSL) {
+                const float qv = __ldg(&Q[(size_t)(pq0 + c) * n + v]);
+#pragma unroll
+                for (int i = 0; i < RMAX; ++i)
+                    if (i < r) acc[i] = fmaf(Cs[i * kLstepPC + c], qv, acc[i]);
+            }
+        }
+    }
+    if (sl > 0) {
+#pragma unroll
+        for (int i = 0; i < RMAX; ++i) red[((sl - 1) * RMAX + i) * kLstepVB + lv] = acc[i];
+    }
+    __syncthreads();
+    if (sl == 0 && v < n) {
+#pragma unroll
+        for (int i = 0; i < RMAX; ++i) {
+            if (i < r) {
+                float t = acc[i];
+#pragma unroll
+                for (int k = 0; k < kLstepSL - 1; ++k) t += red[(k * RMAX + i) * kLstepVB + lv];
+                out[(size_t)i * n + v] = t;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- r^4 couplings of the S- and L-steps
+// Block i: M_i[m][n] = sum_l ( sum_k E_ikl S_km ) S_ln  (the same form as the
+// L-step's C_ipq = sum_n (sum_m E_imn S_mp) S_nq, with E symmetric in its
+// last two indices), staged in shared memory; C_out[i] = M_i.  When T is
+// given, also D[i][j] = sum_{m,n} T_jmn M_i[m][n] (the S-step collision term).
+constexpr size_t kCouplingSmem = 3 * 64 * 64 * sizeof(float);
+
+__global__ void __launch_bounds__(kLrThreads) k_lr_coupling(const float* __restrict__ E, const float* __restrict__ S,
+                                                           const float* __restrict__ T, int r,
+                                                           float* __restrict__ C_out, float* __restrict__ D) {
+    extern __shared__ float cp_smem[];
+    float* Ei = cp_smem;                 // [r][r]  E_i k l
+    float* Ss = cp_smem + 64 * 64;       // [r][r]
+    float* In = cp_smem + 2 * 64 * 64;   // [r][r]  inner[m][l]
+    const int i = blockIdx.x, rr = r * r;
+    for (int e = threadIdx.x; e < rr; e += kLrThreads) {
+        Ei[e] = __ldg(&E[(size_t)i * rr + e]);
+        Ss[e] = __ldg(&S[e]);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < rr; e += kLrThreads) {      // inner[m][l] = sum_k E_ikl S_km
+        const int m = e / r, l = e % r;
+        float a = 0.f;
+        for (int k = 0; k < r; ++k) a = fmaf(Ei[k * r + l], Ss[k * r + m], a);
+        In[e] = a;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < rr; e += kLrThreads) {      // M[m][n] = sum_l inner[m][l] S_ln
+        const int m = e / r, n = e % r;
+        float a = 0.f;
+        for (int l = 0; l < r; ++l) a = fmaf(In[m * r + l], Ss[l * r + n], a);
+        Ei[e] = a;                                          // E_i is no longer needed
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < rr; e += kLrThreads) C_out[(size_t)i * rr + e] = Ei[e];
+    if (T) {
+        for (int j = threadIdx.x; j < r; j += kLrThreads) {
+            float a = 0.f;
+            for (int e = 0; e < rr; ++e) a = fmaf(__ldg(&T[(size_t)j * rr + e]), Ei[e], a);
+            D[(size_t)i * r + j] = a;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- Cholesky-QR2 (FP64)
+constexpr int kGramVT = 32;         // staged columns of W per step
+
+// part[slice][a][b] = sum_{v in slice} W_a(v) W_b(v)  (both triangles written)
+__global__ void __launch_bounds__(kLrThreads) k_gram_f64(const double* __restrict__ W, int r, int n, int nslices,
+                                                        double* __restrict__ part) {
+    __shared__ double Ws[64 * kGramVT];
+    const int s = blockIdx.x;
+    const int v0 = (int)((long long)n * s / nslices), v1 = (int)((long long)n * (s + 1) / nslices);
+    const int npairs = r * (r + 1) / 2;
+    constexpr int PT = (64 * 65 / 2 + kLrThreads - 1) / kLrThreads;     // pairs per thread (max)
+    double acc[PT];
+    int pa[PT], pb[PT];
+#pragma unroll
+    for (int k = 0; k < PT; ++k) {
+        acc[k] = 0.0;
+        int e = threadIdx.x + k * kLrThreads, a = 0;
+        if (e < npairs) {
+            while (e >= r - a) {               // e -> (a, b), a <= b, row-major upper triangle
+                e -= r - a;
+                ++a;
+            }
+        }
+        pa[k] = a;
+        pb[k] = a + e;
+    }
+    for (int c0 = v0; c0 < v1; c0 += kGramVT) {
+        const int cn = min(kGramVT, v1 - c0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < r * kGramVT; e += kLrThreads) {
+            const int a = e / kGramVT, c = e % kGramVT;
+            Ws[a * kGramVT + c] = c < cn ? __ldg(&W[(size_t)a * n + c0 + c]) : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < PT; ++k) {
+            if (threadIdx.x + k * kLrThreads >= npairs) break;
+            const double* wa = Ws + pa[k] * kGramVT;
+            const double* wb = Ws + pb[k] * kGramVT;
+            double t = acc[k];
+#pragma unroll 8
+            for (int c = 0; c < kGramVT; ++c) t = fma(wa[c], wb[c], t);
+            acc[k] = t;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < PT; ++k) {
+        if (threadIdx.x + k * kLrThreads >= npairs) break;
+        part[((size_t)s * r + pa[k]) * r + pb[k]] = acc[k];
+        part[((size_t)s * r + pb[k]) * r + pa[k]] = acc[k];
+    }
+}
+
+// One CTA: G = w sum_s part[s] (fixed order), G = R^T R (R upper, positive
+// diagonal), Rinv = R^-1; when Rprev is given, Rout = R Rprev (the factor of
+// the two passes; Rout must not alias Rprev), else Rout = R.  When pivot k is
+// not positive, info (zeroed by the caller) receives k + 1 unless an earlier
+// pass already failed, and R, Rinv are NaN.
+constexpr size_t kCholSmem = 3 * 64 * 64 * sizeof(double);
+
+__global__ void __launch_bounds__(64) k_chol_f64(const double* __restrict__ part, int nslices, int r, double w,
+                                                 const double* __restrict__ Rprev, double* __restrict__ Rout,
+                                                 double* __restrict__ Rinv, int* __restrict__ info) {
+    extern __shared__ double chol_smem[];
+    double* G = chol_smem;                         // [64 * 64] each
+    double* Rs = chol_smem + 64 * 64;
+    double* Xs = chol_smem + 2 * 64 * 64;
+    __shared__ int bad;
+    const int t = threadIdx.x;
+    if (t == 0) bad = 0;
+    for (int e = t; e < r * r; e += 64) {
+        double g = 0.0;
+        for (int s = 0; s < nslices; ++s) g += part[(size_t)s * r * r + e];
+        G[e] = w * g;
+        Rs[e] = 0.0;
+    }
+    __syncthreads();
+    for (int k = 0; k < r; ++k) {
+        if (t == 0) {
+            double d = G[k * r + k];
+            for (int i = 0; i < k; ++i) d -= Rs[i * r + k] * Rs[i * r + k];
+            if (!(d > 0.0)) {
+                bad = k + 1;
+                d = 0.0;
+            }
+            Rs[k * r + k] = sqrt(d);
+        }
+        __syncthreads();
+        if (bad) break;
+        for (int j = k + 1 + t; j < r; j += 64) {
+            double a = G[k * r + j];
+            for (int i = 0; i < k; ++i) a -= Rs[i * r + k] * Rs[i * r + j];
+            Rs[k * r + j] = a / Rs[k * r + k];
+        }
+        __syncthreads();
+    }
+    if (bad) {
+        if (t == 0 && *info == 0) *info = bad;     // the first failing pass is reported
+        const double nan = __longlong_as_double(0x7ff8000000000000ll);
+        for (int e = t; e < r * r; e += 64) {
+            Rout[e] = nan;
+            Rinv[e] = nan;
+        }
+        return;
+    }
+    // Rinv by back substitution, one column per thread: R X = I
+    for (int j = t; j < r; j += 64) {
+        for (int i = r - 1; i >= 0; --i) {
+            double a = (i == j) ? 1.0 : 0.0;
+            for (int k = i + 1; k <= j; ++k) a -= Rs[i * r + k] * Xs[k * r + j];
+            Xs[i * r + j] = (i <= j) ? a / Rs[i * r + i] : 0.0;
+        }
+    }
+    __syncthreads();
+    for (int e = t; e < r * r; e += 64) {
+        Rinv[e] = Xs[e];
+        const int i = e / r, j = e % r;
+        double o = Rs[e];
+        if (Rprev) {
+            o = 0.0;
+            for (int k = i; k <= j; ++k) o += Rs[i * r + k] * Rprev[k * r + j];
+        }
+        Rout[e] = o;
+    }
+}
+
+// Y_k(v) = sum_{i <= k} W_i(v) Rinv_ik; in place allowed (Y == W): each
+// thread reads its voxel's r values before writing.
+template <int RMAX>
+__global__ void __launch_bounds__(kLrThreads) k_apply_rinv_f64(const double* W, const double* __restrict__ Rinv,
+                                                              int r, int n, double* Y) {
+    __shared__ double Ri[64 * 64];
+    for (int e = threadIdx.x; e < r * r; e += kLrThreads) Ri[e] = Rinv[e];
+    __syncthreads();
+    const int v = blockIdx.x * kLrThreads + threadIdx.x;
+    if (v >= n) return;
+    double w[RMAX];
+#pragma unroll
+    for (int i = 0; i < RMAX; ++i) w[i] = (i < r) ? W[(size_t)i * n + v] : 0.0;
+#pragma unroll 4
+    for (int k = 0; k < RMAX; ++k) {
+        if (k >= r) break;
+        double y = 0.0;
+#pragma unroll
+        for (int i = 0; i < RMAX; ++i)
+            if (i <= k) y = fma(w[i], Ri[i * r + k], y);
+        Y[(size_t)k * n + v] = y;
+    }
+}
+
+// ---------------------------------------------------------------- one-sided Jacobi SVD (FP64)
+// One CTA of 32 warps: in every round of a sweep the columns are paired by
+// the round-robin schedule and warp p rotates pair p (lanes split the r
+// entries, dot products by shuffles).  A sweep without a rotation ends it.
+constexpr int kSvdMaxSweeps = 60;
+constexpr size_t kSvdSmem = 2 * 64 * 64 * sizeof(double);
+
+__global__ void __launch_bounds__(1024) k_svd_jacobi_f64(const double* __restrict__ S, int r, double drop_tol,
+                                                        double* __restrict__ U, double* __restrict__ sigma,
+                                                        double* __restrict__ Qm, int* __restrict__ r_keep,
+                                                        int* __restrict__ info) {
+    extern __shared__ double svd_smem[];
+    double* A = svd_smem;                          // column-major: column c at c*64
+    double* V = svd_smem + 64 * 64;
+    __shared__ double sv[64];
+    __shared__ int order[64];
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int m = (r + 1) & ~1;                   // even number of columns (one idle column if r is odd)
+    for (int e = t; e < 64 * 64; e += 1024) {
+        const int c = e / 64, i = e % 64;
+        A[e] = (c < r && i < r) ? S[i * r + c] : 0.0;
+        V[e] = (c == i && c < r) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    int sweep = 0;
+    bool converged = false;
+    for (; sweep < kSvdMaxSweeps && !converged; ++sweep) {
+        int rotated = 0;
+        for (int round = 0; round < m - 1; ++round) {
+            // round-robin: position 0 fixed, the others rotate
+            if (warp < m / 2) {
+                auto slot = [&](int pos) { return pos == 0 ? 0 : 1 + (pos - 1 + round) % (m - 1); };
+                int p = slot(warp), q = slot(m - 1 - warp);
+                if (p > q) {
+                    const int tmp = p;
+                    p = q;
+                    q = tmp;
+                }
+                if (q < r) {
+                    // FP64 issues slowly on this GPU: reduce to lane 0 with predicated adds,
+                    // compute the rotation there only, broadcast (c, s)
+                    double al = 0.0, be = 0.0, ga = 0.0;
+                    for (int i = lane; i < r; i += 32) {
+                        const double x = A[p * 64 + i], y = A[q * 64 + i];
+                        al = fma(x, x, al);
+                        be = fma(y, y, be);
+                        ga = fma(x, y, ga);
+                    }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        const double a2 = __shfl_down_sync(0xffffffffu, al, o);
+                        const double b2 = __shfl_down_sync(0xffffffffu, be, o);
+                        const double g2 = __shfl_down_sync(0xffffffffu, ga, o);
+                        if (lane < o && lane + o < r) {
+                            al += a2;
+                            be += b2;
+                            ga += g2;
+                        }
+                    }
+                    double c = 1.0, s = 0.0;
+                    int rot = 0;
+                    if (lane == 0 && ga != 0.0 && ga * ga > 1e-30 * (al * be)) {
+                        const double zeta = (be - al) / (2.0 * ga);
+                        const double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
+                        c = rsqrt(fma(tt, tt, 1.0));
+                        s = c * tt;
+                        rot = 1;
+                    }
+                    rot = __shfl_sync(0xffffffffu, rot, 0);
+                    if (rot) {
+                        c = __shfl_sync(0xffffffffu, c, 0);
+                        s = __shfl_sync(0xffffffffu, s, 0);
+                        for (int i = lane; i < r; i += 32) {
+                            const double x = A[p * 64 + i], y = A[q * 64 + i];
+                            A[p * 64 + i] = c * x - s * y;
+                            A[q * 64 + i] = s * x + c * y;
+                            const double vx = V[p * 64 + i], vy = V[q * 64 + i];
+                            V[p * 64 + i] = c * vx - s * vy;
+                            V[q * 64 + i] = s * vx + c * vy;
+                        }
+                        rotated = 1;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        converged = !__syncthreads_or(rotated);
+    }
+    // singular values = column norms; sort descending (one thread, r <= 64)
+    if (t < r) {
+        double nn = 0.0;
+        for (int i = 0; i < r; ++i) nn = fma(A[t * 64 + i], A[t * 64 + i], nn);
+        sv[t] = sqrt(nn);
+    }
+    __syncthreads();
+    if (t == 0) {
+        for (int i = 0; i < r; ++i) order[i] = i;
+        for (int i = 0; i < r; ++i) {
+            int best = i;
+            for (int j = i + 1; j < r; ++j)
+                if (sv[order[j]] > sv[order[best]]) best = j;
+            const int tmp = order[i];
+            order[i] = order[best];
+            order[best] = tmp;
+        }
+        int keep = 0;
+        for (int i = 0; i < r; ++i) keep += sv[order[i]] >= drop_tol ? 1 : 0;
+        *r_keep = keep;
+        *info = converged ? 0 : 1;
+    }
+    __syncthreads();
+    for (int e = t; e < r * r; e += 1024) {
+        const int i = e / r, k = e % r;          // row i, output column k
+        const int c = order[k];
+        const double s = sv[c];
+        U[e] = s > 0.0 ? A[c * 64 + i] / s : 0.0;
+        Qm[e] = V[c * 64 + i];
+        if (i == 0) sigma[k] = s;
+    }
+}
+
+// X_bar_k(x) = sum_i X_i(x) U_ik, k < r_new (U row-major r x r, ld r)
+template <int RMAX>
+__global__ void __launch_bounds__(kLrThreads) k_rotate_f64(const double* __restrict__ X, const double* __restrict__ U,
+                                                          int r, int r_new, int n, double* __restrict__ out) {
+    __shared__ double Us[64 * 64];
+    for (int e = threadIdx.x; e < r * r; e += kLrThreads) Us[e] = U[e];
+    __syncthreads();
+    const int x = blockIdx.x * kLrThreads + threadIdx.x;
+    if (x >= n) return;
+    double xv[RMAX];
+#pragma unroll
+    for (int i = 0; i < RMAX; ++i) xv[i] = (i < r) ? __ldg(&X[(size_t)i * n + x]) : 0.0;
+    for (int k = 0; k < r_new; ++k) {
+        double y = 0.0;
+#pragma unroll
+        for (int i = 0; i < RMAX; ++i)
+            if (i < r) y = fma(xv[i], Us[i * r + k], y);
+        out[(size_t)k * n + x] = y;
+    }
+}
+
+}  // namespace boltz_dev

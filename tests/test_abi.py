@@ -83,6 +83,14 @@ def test_null_handles_are_rejected(B):
     assert lib.boltz_spectrum_f64(None, None, 1, None, None) == B.BOLTZ_EINVAL
     assert lib.boltz_collide_batched_f64(None, None, 1, None, None, 1, None, 0, None) == B.BOLTZ_EINVAL
     assert lib.boltz_project_f64(None, None, 4, None, None, None) == B.BOLTZ_EINVAL
+    assert lib.boltz_kstep_collision(None, 4, None, 10, None, None) == B.BOLTZ_EINVAL
+    assert lib.boltz_kstep_collision(None, 65, None, 10, None, None) == B.BOLTZ_EINVAL
+    assert lib.boltz_lstep_collision(None, 0, None, 10, None, None) == B.BOLTZ_EINVAL
+    assert lib.boltz_qr_f64(None, 4, 100, 0.5, None, None, None, None, None) == B.BOLTZ_EINVAL
+    assert lib.boltz_svd_truncate_f64(None, 4, 1e-6, None, None, None, None, None, None) == B.BOLTZ_EINVAL
+    assert lib.boltz_basis_rotate_f64(None, 4, 10, None, 5, None, None) == B.BOLTZ_EINVAL
+    assert lib.boltz_qr_f64_workspace(4, 3, ctypes.byref(z)) == B.BOLTZ_EINVAL      # n < r
+    assert lib.boltz_qr_f64_workspace(16, 32768, ctypes.byref(z)) == B.BOLTZ_OK and z.value > 0
 
 
 @pytest.mark.parametrize("d,M", [(2, 16), (2, 64), (3, 6), (3, 14), (3, 26), (3, 38), (3, 50), (3, 86)])
