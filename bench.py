@@ -518,6 +518,18 @@ def main():
     lowrank = None
     if kind == "pairs":
         lowrank = lowrank_consumers(B, T, Q, n_in, N ** d, flush, dev)
+    mott = None
+    if kind == "cells":
+        # Sec. 4.2 closure of the same shock: alpha from the two cross evaluations of the end states
+        from paper_2112_02695_gb300 import workloads as W
+        (rL, uL, TL), (rR, uR, TR) = W.rankine_hugoniot(d, 3.0)
+        fLR = torch.tensor(np.stack(W.shock_states_fields(N, d, L)), dtype=torch.float32, device=dev)
+        specLR = B.boltz_spectrum(g, fLR)
+        B.boltz_mott_smith(g, specLR, rL, uL, TL, TR)
+        t0 = time.perf_counter()
+        al, be, _ = B.boltz_mott_smith(g, specLR, rL, uL, TL, TR)
+        mott = {"alpha": al, "beta": be, "ms": 1e3 * (time.perf_counter() - t0),
+                "note": "two cross evaluations + FP64 v_1^2 moment, host-timed including the readback"}
 
     # roofline of the dominant kernel (the shifted-field inverse transforms)
     props = torch.cuda.get_device_properties(dev)
@@ -581,6 +593,7 @@ def main():
             "plain_fp32": plain,
             "split_bf16": split,
             "lowrank_step_consumers": lowrank,
+            "mott_smith": mott,
             "error_vs_oracle": errors,
             "cpu_baseline": cpu,
             "wall_s_timed_region": wall,

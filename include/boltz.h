@@ -284,6 +284,24 @@ boltz_status boltz_batch_destroy(boltz_batch b);
 boltz_status boltz_moments(boltz_grid g, const float* Q, int n_fields, double* out, void* stream);
 
 /*
+ * Mott-Smith strong-shock closure (paper Sec. 4.2, eq. "eqn:alpha"): with
+ * input 0 = f_L (upstream) and input 1 = f_R (downstream), drifting along
+ * velocity axis 0,
+ *   alpha = int v_1^2 ( Q(f_L, f_R) + Q(f_R, f_L) ) dv   (the two cross
+ *           evaluations of the batch, then an FP64 moment on the device)
+ *   beta  = alpha / ((d_v - 1) rho_L u_L R_gas (T_L - T_R)),
+ * so that a(x_1) = 1 / (exp(beta x_1) + 1) in f = a f_L + (1 - a) f_R.
+ *   spectra    device complex64 [2][half] (see boltz_spectrum)
+ *   Q_scratch  device float32 [2][N^d], receives Q(f_L, f_R), Q(f_R, f_L)
+ *   alpha, beta  HOST double
+ * Synchronises `stream`.  Errors: BOLTZ_EINVAL (NULL pointers, T_L == T_R or
+ * another zero factor in beta's denominator), BOLTZ_ENOMEM, BOLTZ_ECUDA.
+ */
+boltz_status boltz_mott_smith(boltz_grid g, const void* spectra, double rho_L, double u_L, double T_L,
+                              double T_R, double R_gas, float* Q_scratch, double* alpha, double* beta,
+                              void* stream);
+
+/*
  * Allocation-free variant of boltz_project (the paper has no counterpart; this
  * is a deployment aid).  Same arguments, layout and result as boltz_project
  * (up to the order of FP32 summation), but it never allocates device memory:

@@ -35,7 +35,7 @@ EXPORTED = (
     "boltz_batch_plan", "boltz_batch_run", "boltz_batch_kernel_count", "boltz_batch_destroy",
     "boltz_autotune", "boltz_spectrum_f64", "boltz_collide_batched_f64", "boltz_project_f64",
     "boltz_kstep_collision", "boltz_lstep_collision", "boltz_qr_f64_workspace", "boltz_qr_f64",
-    "boltz_svd_truncate_f64", "boltz_basis_rotate_f64", "boltz_lowrank_coupling",
+    "boltz_svd_truncate_f64", "boltz_basis_rotate_f64", "boltz_lowrank_coupling", "boltz_mott_smith",
 )
 
 KERNEL_CLASSES = ("spectrum", "prep", "shift", "contract", "radial", "output", "project")
@@ -104,6 +104,9 @@ def _load() -> ctypes.CDLL:
         "boltz_svd_truncate_f64": ([vp, ctypes.c_int, ctypes.c_double, vp, vp, vp, vp, vp, vp], ctypes.c_int),
         "boltz_basis_rotate_f64": ([vp, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, vp, vp], ctypes.c_int),
         "boltz_lowrank_coupling": ([vp, vp, ctypes.c_int, vp, vp, vp, vp], ctypes.c_int),
+        "boltz_mott_smith": ([vp, vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                              ctypes.c_double, vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                              vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -537,3 +540,18 @@ def boltz_lowrank_coupling(E, S, T=None, stream=None):
                                        _dev_ptr(D, "float32", "D") if D is not None else None,
                                        _stream_ptr(stream)), "boltz_lowrank_coupling")
     return C, D
+
+
+def boltz_mott_smith(grid: Grid, spectra, rho_L: float, u_L: float, T_L: float, T_R: float, R_gas: float = 1.0,
+                     Q_scratch=None, stream=None):
+    """(alpha, beta, Q) of the Mott-Smith closure; spectra = [f_L, f_R]."""
+    import torch
+    if spectra.shape[0] != 2:
+        raise ValueError("spectra must hold f_L and f_R")
+    if Q_scratch is None:
+        Q_scratch = torch.empty((2,) + grid.shape, dtype=torch.float32, device=spectra.device)
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(_lib.boltz_mott_smith(grid.handle, _dev_ptr(spectra, "complex64", "spectra"), float(rho_L), float(u_L),
+                                 float(T_L), float(T_R), float(R_gas), _dev_ptr(Q_scratch, "float32", "Q_scratch"),
+                                 ctypes.byref(a), ctypes.byref(b), _stream_ptr(stream)), "boltz_mott_smith")
+    return a.value, b.value, Q_scratch

@@ -85,6 +85,7 @@ struct boltz_grid_s {
     double* d_w64 = nullptr;
     // split-precision form: per-node BF16 shift matrices (built on first use)
     uint8_t* d_smat = nullptr;
+    double* d_scalar = nullptr;       // small device results read back by the host (Mott-Smith alpha)
     int split_clusters = 1;           // resident clusters of the split kernel
     int* d_err = nullptr;        // device error word (bit kErrTimeout: a bounded wait gave up)
     // workspace
@@ -1481,6 +1482,7 @@ boltz_status boltz_grid_destroy(boltz_grid g) {
     cudaFree(g->d_gm64);
     cudaFree(g->d_w64);
     cudaFree(g->d_smat);
+    cudaFree(g->d_scalar);
     cudaFree(g->d_ws);
     delete g;
     return BOLTZ_OK;
@@ -1652,6 +1654,35 @@ boltz_status boltz_lowrank_step_host(boltz_grid g, const float* V_host, int r, f
     if (Q_host) BZ_CUDA(cudaMemcpyAsync(Q_host, dQ, size_t(r2) * nb, cudaMemcpyDeviceToHost, st));
     BZ_CUDA(cudaMemcpyAsync(T_host, dT, size_t(r) * r2 * 4, cudaMemcpyDeviceToHost, st));
     BZ_CUDA(cudaStreamSynchronize(st));
+    return BOLTZ_OK;
+}
+
+boltz_status boltz_mott_smith(boltz_grid g, const void* spectra, double rho_L, double u_L, double T_L, double T_R,
+                              double R_gas, float* Q_scratch, double* alpha, double* beta, void* stream) {
+    if (!g || !spectra || !Q_scratch || !alpha || !beta) return BOLTZ_EINVAL;
+    const double denom = (g->D - 1) * rho_L * u_L * R_gas * (T_L - T_R);
+    if (!std::isfinite(denom) || denom == 0.0) return BOLTZ_EINVAL;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (!g->d_scalar) {
+        if (cudaMalloc(&g->d_scalar, 8 * sizeof(double)) != cudaSuccess) {
+            (void)cudaGetLastError();
+            g->d_scalar = nullptr;
+            return BOLTZ_ENOMEM;
+        }
+    }
+    const int32_t pj[2] = {0, 1}, pl[2] = {1, 0};     // Q(f_L, f_R), Q(f_R, f_L)
+    boltz_status s = run_batched(g, reinterpret_cast<const float2*>(spectra), 2, pj, pl, 2, Q_scratch,
+                                 BOLTZ_FORM_BATCHED, st);
+    if (s != BOLTZ_OK) return s;
+    const double dv = 2.0 * g->L / g->N;
+    if (g->D == 3) k_axis0_second_moment<3><<<1, 256, 0, st>>>(Q_scratch, 2, g->N, g->L, dv, g->d_scalar);
+    else k_axis0_second_moment<2><<<1, 256, 0, st>>>(Q_scratch, 2, g->N, g->L, dv, g->d_scalar);
+    BZ_CUDA(cudaGetLastError());
+    double a = 0.0;
+    BZ_CUDA(cudaMemcpyAsync(&a, g->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, st));
+    BZ_CUDA(cudaStreamSynchronize(st));
+    *alpha = a;
+    *beta = a / denom;
     return BOLTZ_OK;
 }
 

@@ -985,6 +985,31 @@ __global__ void __launch_bounds__(256) k_moments(const float* __restrict__ Q, do
     }
 }
 
+// out[0] = dv^D sum_f sum_v v_1^2 Q_f(v): the v_1^2 moment (v_1 = velocity axis 0)
+// summed over n_fields fields, FP64, one CTA, fixed order (paper Sec. 4.2).
+template <int D>
+__global__ void __launch_bounds__(256) k_axis0_second_moment(const float* __restrict__ Q, int n_fields, int N,
+                                                             double L, double dv, double* __restrict__ out) {
+    const int n = (D == 3) ? N * N * N : N * N;
+    const int plane = n / N;
+    double acc = 0.0;
+    for (int f = 0; f < n_fields; ++f) {
+        const float* q = Q + (size_t)f * n;
+        for (int v = threadIdx.x; v < n; v += 256) {
+            const double v0 = -L + (v / plane) * dv;
+            acc = fma(v0 * v0, (double)q[v], acc);
+        }
+    }
+    __shared__ double red[256];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = pow(dv, (double)D) * red[0];
+}
+
 // ------------------------------------------------------------------ failure-path self-test
 // One CTA announces an incoming transfer on an mbarrier and never issues it:
 // the bounded wait runs out, the kernel records a timeout in the error word

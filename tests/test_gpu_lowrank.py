@@ -179,3 +179,27 @@ def test_coupling_and_sstep_term(B, r):
     assert np.max(np.abs(Dg.cpu().numpy() - Do) / Ds) < 1e-5
     C2, D2 = B.boltz_lowrank_coupling(d(E), d(S))
     assert D2 is None and np.array_equal(C2.cpu().numpy(), Cg.cpu().numpy())
+
+
+def test_mott_smith_alpha_beta(B):
+    """Sec. 4.2 closure on the GPU (Mach-3 Rankine-Hugoniot states, 32^3,
+    hard spheres) against the oracle's alpha and beta."""
+    import torch
+    from gpu_helpers import as_fp32
+    from oracle import collision as C
+    from oracle import mott_smith as MS
+    from paper_2112_02695_gb300 import workloads as W
+    cfg = (32, 3, 8.0, 8.0, 1.0, 6, 14)
+    (rL, uL, TL), (rR, uR, TR) = W.rankine_hugoniot(3, 3.0)
+    fL, fR = (as_fp32(f) for f in W.shock_states_fields(32, 3, 8.0))
+    g = B.boltz_grid_init(*cfg)
+    try:
+        spec = B.boltz_spectrum(g, torch.tensor(np.stack([fL, fR]), dtype=torch.float32, device="cuda"))
+        al, be, _ = B.boltz_mott_smith(g, spec, rL, uL, TL, TR)
+    finally:
+        g.close()
+    prob = C.Problem(N=32, d=3, L=8.0, R=8.0, gamma=1.0, n_rho=6, M=14)
+    al_o = MS.alpha(prob, fL, fR)
+    assert abs(al - al_o) <= 1e-4 * abs(al_o)
+    assert abs(be - MS.beta(al_o, 3, rL, uL, TL, TR)) <= 1e-4 * abs(be)
+    assert al < 0 and be > 0
