@@ -11,5 +11,8 @@ Modules:
               the brute-force direct sum, projection and moments.
   lowrank     the low-rank step pieces that consume the batch: K- and
               L-step collision terms, weighted QR, SVD rank truncation.
+  mott_smith  the strong-shock closure alpha, beta of Sec. 4.2.
+  carleman    the Carleman-form fast spectral operator for gamma = d - 2
+              (the Mouhot-Pareschi algorithm the paper's experiments use).
 """
-from . import quadrature, collision, lowrank  # noqa: F401
+from . import quadrature, collision, lowrank, mott_smith, carleman  # noqa: F401
