@@ -321,6 +321,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-split", action="store_true")
+    ap.add_argument("--no-carleman", action="store_true")
     ap.add_argument("--field-budget-mb", type=int, default=0,
                     help="fix the schedule instead of autotuning it (e.g. for profiling runs)")
     args = ap.parse_args()
@@ -513,6 +514,35 @@ def main():
                                   "share_of_step": mss / max(sum(ms for _, ms in prof_s.values()), 1e-9)}}
         split["speedup_vs_fp32_batched"] = split["value"] / (value / world)
 
+    # Carleman form (the paper's own fast method, gamma = d - 2 only) on the same batch
+    carleman = None
+    if abs(gamma - (d - 2)) < 1e-12 and not (d == 2 and N == 128) and not args.no_carleman:
+        Qc = torch.empty_like(Q)
+
+        def step_carleman():
+            B.boltz_spectrum(g, f_dev, out=spec)
+            B.boltz_collide_batched(g, spec, pj, pl, form=B.BOLTZ_FORM_CARLEMAN, out=Qc)
+            if kind == "pairs":
+                B.boltz_project(g, f_dev, Qc, out=T)
+        for _ in range(args.warmup):
+            step_carleman()
+        torch.cuda.synchronize()
+        B.boltz_profile_read(g, reset=True)
+        tc = timed(step_carleman, args.steps)
+        B.boltz_profile_read(g, reset=True)
+        B.boltz_profile_enable(g, True)
+        timed(step_carleman, max(3, args.steps // 4))
+        prof_c = B.boltz_profile_read(g, reset=True)
+        B.boltz_profile_enable(g, False)
+        B.boltz_sync_status(g)
+        tot_c = sum(ms for _, ms in prof_c.values())
+        carleman = {"value": len(pairs) * len(tc) / (sum(tc) / 1e3), "unit": "evals/s",
+                    "ms_per_step": sum(tc) / len(tc),
+                    "method": f"Carleman form: {M // 2} half-sphere directions x 2 multipliers per input, "
+                              "truncation |x|,|y| <= R, no radial quadrature and no forward transform",
+                    "kernel_shares": {k: round(ms / tot_c, 4) for k, (_, ms) in prof_c.items() if ms > 0}}
+        carleman["speedup_vs_separated_fp32"] = carleman["value"] / (value / world)
+
     # low-rank step consumers of this batch (Sec. 2.4 K- and L-step collision terms,
     # FP64 QR of K and L, Sec. 3.2 SVD truncation and basis rotation), L2 flushed before each call
     lowrank = None
@@ -571,6 +601,13 @@ def main():
             errors = sample_errors(B, g, res, forms)
             errors["normalisation"] = "max over the oracle sample of max|Q_gpu - Q_oracle| / max(|Q|,|Q+|,|Q-|)"
             errors["sample"] = desc
+            if carleman is not None:
+                from oracle import carleman as CMO
+                from oracle import collision as COL
+                pc = CMO.CarlemanProblem(N=N, d=d, L=L, R=R, M=M)
+                Qo, Qop, Qom = CMO.collide_fields(pc, res["fields"].astype(np.float64), res["pairs"], return_parts=True)
+                errors["carleman_vs_its_oracle"] = sample_errors(
+                    B, g, dict(res, Q=Qo, scale=COL.scale(Qo, Qop, Qom)), {"carleman": B.BOLTZ_FORM_CARLEMAN})["carleman"]
 
     if rank == 0:
         line = {
@@ -592,6 +629,7 @@ def main():
             "e2e": e2e,
             "plain_fp32": plain,
             "split_bf16": split,
+            "carleman_form": carleman,
             "lowrank_step_consumers": lowrank,
             "mott_smith": mott,
             "error_vs_oracle": errors,

@@ -98,7 +98,23 @@ typedef enum {
      * BOLTZ_EUNSUPPORTED.  The first call on a grid builds its per-node
      * matrices (24 KB per (rho, sigma) node, device memory kept until the
      * grid is destroyed). */
-    BOLTZ_FORM_SPLIT_BF16 = 2
+    BOLTZ_FORM_SPLIT_BF16 = 2,
+    /* Carleman form (the Mouhot-Pareschi fast spectral method the paper's
+     * experiments use; Sec. 2.1, Sec. 5), defined for gamma = d_v - 2 only
+     * (2D Maxwell molecules, 3D hard spheres): with x = v' - v, y = v'_* - v
+     * the gain is int int 2^{d-1} b delta(x.y) g(v+y) f(v+x) dx dy over
+     * |x|, |y| <= R (a different truncation from the other forms' |q| <= R),
+     * split over one direction e_p of every antipodal pair of the grid's rule
+     * (M/2 directions) into the product of the g-side multiplier
+     * psi(pi |l - (l.e_p)e_p| / L) and the f-side multiplier
+     * phi(pi m.e_p / L) (closed forms), so that no radial quadrature is
+     * needed: 2 inverse transforms per direction and input and no forward
+     * transform.  The loss uses the same discrete kernel at m = l (mass is
+     * conserved to rounding).  N_rho of the grid is unused.  FP32.
+     * gamma != d_v - 2: BOLTZ_EINVAL; the 2D 128^2 grid: BOLTZ_EUNSUPPORTED.
+     * The first call builds per-mode tables (M + 1 real values per spectral
+     * mode, device memory kept until the grid is destroyed). */
+    BOLTZ_FORM_CARLEMAN = 3
 } boltz_form;
 
 typedef struct {

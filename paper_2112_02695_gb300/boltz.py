@@ -26,6 +26,7 @@ BOLTZ_ENONFINITE = 6
 BOLTZ_FORM_BATCHED = 0
 BOLTZ_FORM_PLAIN = 1
 BOLTZ_FORM_SPLIT_BF16 = 2
+BOLTZ_FORM_CARLEMAN = 3
 
 EXPORTED = (
     "boltz_abi_version", "boltz_status_string", "boltz_grid_init", "boltz_grid_destroy",

@@ -86,6 +86,12 @@ struct boltz_grid_s {
     // split-precision form: per-node BF16 shift matrices (built on first use)
     uint8_t* d_smat = nullptr;
     double* d_scalar = nullptr;       // small device results read back by the host (Mott-Smith alpha)
+    // Carleman form (gamma = d - 2): per-mode multipliers of the M/2 half-sphere
+    // directions (g side, then f side), the per-mode loss table, weights and slot pairs
+    float* d_cm_mult = nullptr;       // [M][half]
+    float* d_cm_gm = nullptr;         // [half]
+    float* d_cm_w = nullptr;          // [M/2]
+    int2* d_cm_dpair = nullptr;       // [M/2]
     int split_clusters = 1;           // resident clusters of the split kernel
     int* d_err = nullptr;        // device error word (bit kErrTimeout: a bounded wait gave up)
     // workspace
@@ -138,8 +144,14 @@ size_t split_image_bytes(int N) {
 }
 
 bool valid_form(int form) {
-    return form == BOLTZ_FORM_BATCHED || form == BOLTZ_FORM_PLAIN || form == BOLTZ_FORM_SPLIT_BF16;
+    return form == BOLTZ_FORM_BATCHED || form == BOLTZ_FORM_PLAIN || form == BOLTZ_FORM_SPLIT_BF16 ||
+           form == BOLTZ_FORM_CARLEMAN;
 }
+
+// The Carleman form exists for gamma = d - 2 only; it is built for every
+// shape but the 2D 128^2 grid (whose transforms use 4-lane line groups).
+bool carleman_kernel(double gamma, int D) { return std::fabs(gamma - (D - 2)) < 1e-12; }
+bool carleman_shape(int N, int D) { return !(D == 2 && N == 128); }
 
 // voxels per chunk of the shifted-field layout (must match Geo<N, D>::VCH)
 int voxel_chunk(int N, int D) {
@@ -155,8 +167,12 @@ int voxel_chunk(int N, int D) {
 // PLAIN: every evaluation gets its own two inputs and its own slot.
 // elem: bytes per real (4 for the FP32 path, 8 for the FP64 check build, whose
 // triangle and full tiles are 8 wide to bound the accumulator registers).
+boltz_status build_plan_carleman(const boltz_grid_s* g, const int32_t* pj, const int32_t* pl, int n_pairs,
+                                 Plan& plan);
+
 boltz_status build_plan(const boltz_grid_s* g, int n_inputs, const int32_t* pj, const int32_t* pl, int n_pairs,
                         int form, Plan& plan, size_t elem = 4) {
+    if (form == BOLTZ_FORM_CARLEMAN) return build_plan_carleman(g, pj, pl, n_pairs, plan);
     plan = Plan();
     const size_t field_bytes = size_t(g->n) * elem;
     // inputs per chunk: enough for one radial node's shifted fields to fit the L2-sized
@@ -349,6 +365,149 @@ boltz_status build_plan(const boltz_grid_s* g, int n_inputs, const int32_t* pj, 
     return BOLTZ_OK;
 }
 
+// Plan of the Carleman form: every distinct ordered pair (j, l) has its own
+// gain slot (the form is not symmetric in g and f); chunks of inputs as in the
+// batched form; complete T x T blocks of ordered pairs become FULL strips of
+// 8 x T, the rest LIST tiles of 16; one slot group of M fields per input
+// (M/2 g-side and M/2 f-side multipliers).
+boltz_status build_plan_carleman(const boltz_grid_s* g, const int32_t* pj, const int32_t* pl, int n_pairs,
+                                 Plan& plan) {
+    plan = Plan();
+    const size_t field_bytes = size_t(g->n) * 4;
+    int nc_cap = (int)std::max<size_t>(16, g->field_budget / (field_bytes * g->M));
+    nc_cap = std::min(nc_cap, 64);
+    std::map<std::pair<int, int>, int> slot_of;
+    std::vector<std::pair<int, int>> slots;
+    std::vector<std::vector<int>> slot_outs;
+    for (int e = 0; e < n_pairs; ++e) {
+        auto it = slot_of.find({pj[e], pl[e]});
+        int s;
+        if (it == slot_of.end()) {
+            s = (int)slots.size();
+            slot_of[{pj[e], pl[e]}] = s;
+            slots.push_back({pj[e], pl[e]});
+            slot_outs.emplace_back();
+        } else {
+            s = it->second;
+        }
+        slot_outs[s].push_back(e);
+    }
+    std::vector<std::vector<int>> chunk_slots;
+    std::vector<std::set<int>> chunk_inputs;
+    for (int s = 0; s < (int)slots.size(); ++s) {
+        const int a = slots[s].first, b = slots[s].second;
+        bool placed = false;
+        if (!chunk_slots.empty()) {
+            std::set<int>& cur = chunk_inputs.back();
+            const int grow = (cur.count(a) ? 0 : 1) + (a != b && !cur.count(b) ? 1 : 0);
+            if ((int)cur.size() + grow <= nc_cap) {
+                cur.insert(a);
+                cur.insert(b);
+                chunk_slots.back().push_back(s);
+                placed = true;
+            }
+        }
+        if (!placed) {
+            chunk_slots.push_back({s});
+            chunk_inputs.push_back({a, b});
+        }
+    }
+    for (size_t ci = 0; ci < chunk_slots.size(); ++ci) {
+        ChunkPlan c;
+        c.inputs.assign(chunk_inputs[ci].begin(), chunk_inputs[ci].end());
+        std::map<int, int> loc;
+        for (int i = 0; i < (int)c.inputs.size(); ++i) loc[c.inputs[i]] = i;
+        const int nc = (int)c.inputs.size();
+        std::map<std::pair<int, int>, int> local;       // ordered local pair -> global slot
+        for (int s : chunk_slots[ci]) local[{loc[slots[s].first], loc[slots[s].second]}] = s;
+        const int T = nc >= 16 ? 16 : 8;
+        c.tile_T = T;
+        std::vector<std::pair<int, int>> order;
+        std::set<std::pair<int, int>> covered;
+        if (nc >= 8) {
+            const int nb = nc / T;
+            for (int J = 0; J < nb; ++J)
+                for (int Lb = 0; Lb < nb; ++Lb) {
+                    bool full = true;
+                    for (int x = 0; x < T && full; ++x)
+                        for (int y = 0; y < T && full; ++y) full = local.count({J * T + x, Lb * T + y}) > 0;
+                    if (!full) continue;
+                    for (int x0 = 0; x0 < T; x0 += 8) {
+                        Tile t;
+                        std::memset(&t, 0, sizeof(t));
+                        t.slot0 = (int)order.size();
+                        t.j0 = J * T + x0;
+                        t.l0 = Lb * T;
+                        for (int x = 0; x < 8; ++x)
+                            for (int y = 0; y < T; ++y) {
+                                order.push_back({t.j0 + x, t.l0 + y});
+                                covered.insert({t.j0 + x, t.l0 + y});
+                            }
+                        t.count = 8 * T;
+                        c.tiles[TILE_FULL].push_back(t);
+                    }
+                }
+        }
+        std::vector<std::pair<int, int>> rest;
+        for (auto& kv : local)
+            if (!covered.count(kv.first)) rest.push_back(kv.first);
+        for (size_t t0 = 0; t0 < rest.size(); t0 += 16) {
+            Tile t;
+            std::memset(&t, 0, sizeof(t));
+            t.slot0 = (int)order.size();
+            t.count = (int)std::min<size_t>(16, rest.size() - t0);
+            for (int i = 0; i < 16; ++i) {
+                const auto& pr = rest[t0 + std::min(i, t.count - 1)];
+                t.ja[i] = pr.first;
+                t.lb[i] = pr.second;
+            }
+            for (int i = 0; i < t.count; ++i) order.push_back(rest[t0 + i]);
+            c.tiles[TILE_LIST].push_back(t);
+        }
+        c.U = (int)order.size();
+        c.out_start.resize(c.U + 1);
+        for (int u = 0; u < c.U; ++u) {
+            c.out_start[u] = (int)c.outs.size();
+            for (int e : slot_outs[local[order[u]]]) c.outs.push_back(make_int4(e, loc[pj[e]], loc[pl[e]], 0));
+        }
+        c.out_start[c.U] = (int)c.outs.size();
+        plan.chunks.push_back(std::move(c));
+    }
+    for (auto& c : plan.chunks) {
+        plan.max_nc = std::max(plan.max_nc, (int)c.inputs.size());
+        plan.max_U = std::max(plan.max_U, c.U);
+    }
+    plan.nq = 1;
+    size_t off = 0;
+    for (auto& c : plan.chunks) {
+        c.off_inputs = off;
+        off = align_up(off + c.inputs.size() * sizeof(int), 256);
+        for (int k = 0; k < 3; ++k) {
+            c.off_tiles[k] = off;
+            off = align_up(off + c.tiles[k].size() * sizeof(Tile), 256);
+        }
+        c.off_start = off;
+        off = align_up(off + c.out_start.size() * sizeof(int), 256);
+        c.off_outs = off;
+        off = align_up(off + c.outs.size() * sizeof(int4), 256);
+    }
+    plan.plan_bytes = off;
+    size_t w = align_up(off, 256);
+    plan.off_plan = 0;
+    plan.off_A = w;
+    w = align_up(w + size_t(g->M) * plan.max_nc * field_bytes, 256);
+    plan.off_P = w;
+    w = align_up(w + size_t(plan.max_U) * field_bytes, 256);
+    plan.off_qhat = w;
+    plan.off_fN = w;
+    w = align_up(w + size_t(plan.max_nc) * field_bytes, 256);
+    plan.off_lam = w;
+    w = align_up(w + size_t(plan.max_nc) * field_bytes, 256);
+    plan.off_img = w;
+    plan.total = w;
+    return BOLTZ_OK;
+}
+
 boltz_status ensure_workspace(boltz_grid_s* g, size_t bytes, cudaStream_t stream) {
     if (bytes <= g->ws_cap) return BOLTZ_OK;
     if (bytes > g->ws_max) return BOLTZ_ENOMEM;
@@ -456,12 +615,14 @@ struct Launch {
             using CG = ClusterGeo<N, CL>;
             if ((e = set_smem(k_synth_cl<N, CL, SYN_SHIFT>, CG::SMEM)) != cudaSuccess) return e;
             if ((e = set_smem(k_synth_cl<N, CL, SYN_PREP>, CG::SMEM)) != cudaSuccess) return e;
+            if ((e = set_smem(k_synth_cl<N, CL, SYN_MULT>, CG::SMEM)) != cudaSuccess) return e;
             if ((e = set_smem(k_analysis_cl<N, CL, ANA_SPECTRUM>, CG::SMEM)) != cudaSuccess) return e;
             if ((e = set_smem(k_analysis_cl<N, CL, ANA_ACCUM>, CG::SMEM)) != cudaSuccess) return e;
             return set_smem(k_output_cl<N, CL>, CG::SMEM);
         } else {
             if ((e = set_smem(k_synth<N, D, FPC, SYN_SHIFT>, SMEM)) != cudaSuccess) return e;
             if ((e = set_smem(k_synth<N, D, FPC, SYN_PREP>, SMEM)) != cudaSuccess) return e;
+            if ((e = set_smem(k_synth<N, D, FPC, SYN_MULT>, SMEM)) != cudaSuccess) return e;
             if ((e = set_smem(k_analysis<N, D, FPC, ANA_SPECTRUM>, SMEM)) != cudaSuccess) return e;
             if ((e = set_smem(k_analysis<N, D, FPC, ANA_ACCUM>, SMEM)) != cudaSuccess) return e;
             return set_smem(k_output<N, D, FPC>, SMEM);
@@ -476,12 +637,16 @@ struct Launch {
             using CG = ClusterGeo<N, CL>;
             if (mode == SYN_SHIFT)
                 k_synth_cl<N, CL, SYN_SHIFT><<<CL * p.n_fields, CG::NT, CG::SMEM, st>>>(p);
+            else if (mode == SYN_MULT)
+                k_synth_cl<N, CL, SYN_MULT><<<CL * p.n_fields, CG::NT, CG::SMEM, st>>>(p);
             else
                 k_synth_cl<N, CL, SYN_PREP><<<CL * p.n_fields, CG::NT, CG::SMEM, st>>>(p);
         } else {
             const int grid = (p.n_fields + FPC - 1) / FPC;
             if (mode == SYN_SHIFT)
                 k_synth<N, D, FPC, SYN_SHIFT><<<grid, BLOCK, SMEM, st>>>(p);
+            else if (mode == SYN_MULT)
+                k_synth<N, D, FPC, SYN_MULT><<<grid, BLOCK, SMEM, st>>>(p);
             else
                 k_synth<N, D, FPC, SYN_PREP><<<grid, BLOCK, SMEM, st>>>(p);
         }
@@ -697,6 +862,50 @@ TablesT<double> tables_of(const boltz_grid_s* g, double) {
     return {g->d_phase64, g->d_ctab64, g->d_gm64, g->d_w64};
 }
 
+// Asymmetric contraction of the Carleman form (FULL 8 x T strips and LIST 16).
+template <int KIND, int TJ, int TL, int VC>
+struct ContractLaunchA {
+    static constexpr int ROWS = ContractShape<KIND, TJ, TL>::ROWS;
+    static constexpr int STAGES = (ROWS * VC * 4 * 4 <= (192 << 10)) ? 4 : 3;
+    static constexpr size_t SMEM = size_t(STAGES) * ROWS * VC * sizeof(float);
+    static cudaError_t prepare() { return set_smem(k_contract_pipe<KIND, TJ, TL, VC, STAGES, float, true>, SMEM); }
+    static void launch(const ConParams& cp, int n_tiles, cudaStream_t st) {
+        dim3 grid(cp.n / VC, n_tiles, 1);
+        k_contract_pipe<KIND, TJ, TL, VC, STAGES, float, true><<<grid, VC, SMEM, st>>>(cp);
+    }
+};
+
+template <int VC>
+cudaError_t prepare_contract_asym_vc() {
+    cudaError_t e;
+    if ((e = ContractLaunchA<TILE_FULL, 8, 16, VC>::prepare()) != cudaSuccess) return e;
+    if ((e = ContractLaunchA<TILE_FULL, 8, 8, VC>::prepare()) != cudaSuccess) return e;
+    return ContractLaunchA<TILE_LIST, 16, 16, VC>::prepare();
+}
+
+template <int VC>
+void launch_contract_asym_vc(int kind, int T, const ConParams& cp, int n_tiles, cudaStream_t st) {
+    if (kind == TILE_FULL) {
+        if (T == 16) ContractLaunchA<TILE_FULL, 8, 16, VC>::launch(cp, n_tiles, st);
+        else ContractLaunchA<TILE_FULL, 8, 8, VC>::launch(cp, n_tiles, st);
+    } else {
+        ContractLaunchA<TILE_LIST, 16, 16, VC>::launch(cp, n_tiles, st);
+    }
+}
+
+void launch_contract_asym(int vch, int kind, int T, const ConParams& cp, int n_tiles, cudaStream_t st) {
+    if (vch == 256) launch_contract_asym_vc<256>(kind, T, cp, n_tiles, st);
+    else if (vch == 288) launch_contract_asym_vc<288>(kind, T, cp, n_tiles, st);
+    else launch_contract_asym_vc<64>(kind, T, cp, n_tiles, st);
+}
+
+cudaError_t prepare_contract_asym() {
+    cudaError_t e;
+    if ((e = prepare_contract_asym_vc<256>()) != cudaSuccess) return e;
+    if ((e = prepare_contract_asym_vc<288>()) != cudaSuccess) return e;
+    return prepare_contract_asym_vc<64>();
+}
+
 boltz_status check_pairs(int n_inputs, const int32_t* pj, const int32_t* pl, int n_pairs) {
     if (n_pairs < 0) return BOLTZ_EINVAL;
     if (n_pairs == 0) return BOLTZ_OK;
@@ -874,12 +1083,186 @@ void launch_shift_split(int N, const SplitParams& p, int clusters, cudaStream_t 
         k_shift_split<32, kSplitCL32><<<ncl * kSplitCL32, kSplitThreads, SplitGeo<32, kSplitCL32>::SMEM, st>>>(p);
 }
 
+// ---------------------------------------------------------------- Carleman form
+
+// int_{-R}^{R} |rho|^{d-2} exp(i rho s) drho (real, even in s)
+double carleman_phi(int d, double R, double s) {
+    if (std::fabs(s) < 1e-6) return d == 2 ? 2.0 * R - R * R * R * s * s / 3.0 : R * R - R * R * R * R * s * s / 4.0;
+    if (d == 2) return 2.0 * std::sin(R * s) / s;
+    return 2.0 * (R * std::sin(R * s) / s + (std::cos(R * s) - 1.0) / (s * s));
+}
+
+// integral of exp(i y.t) over the (d-1)-ball of radius R perpendicular to e, t = |t|
+double carleman_psi(int d, double R, double t) {
+    t = std::fabs(t);
+    if (t < 1e-6) return d == 2 ? 2.0 * R - R * R * R * t * t / 3.0 : kPi * R * R * (1.0 - R * R * t * t / 8.0);
+    if (d == 2) return 2.0 * std::sin(R * t) / t;
+    return 2.0 * kPi * R * std::cyl_bessel_j(1.0, R * t) / t;
+}
+
+// Tables of the Carleman form (built once per grid, synchronously):
+//   mult[p][k]      = (-1)^k psi(pi |k - (k.e_p) e_p| / L)   g side, p < M/2
+//   mult[M/2+p][k]  = (-1)^k phi(pi k.e_p / L)                f side
+//   (zero at the Nyquist indices), gm[k] = Bt sum_p w_p phi psi (the loss
+//   uses the same discrete beta at m = l), w = Bt w_p, Bt = 2^{d-1} b, over one
+//   direction e_p of every antipodal pair of the grid's rule.
+boltz_status ensure_carleman_tables(boltz_grid_s* g) {
+    if (g->d_cm_mult) return BOLTZ_OK;
+    const int N = g->N, D = g->D, H = N / 2, NH = H + 1;
+    std::vector<int> dirs;
+    for (int p = 0; p < g->M; ++p)
+        if (g->dir.antipode[p] > p) dirs.push_back(p);
+    const int M2 = (int)dirs.size();
+    const double Bt = std::pow(2.0, D - 1) * g->b;
+    const size_t half = g->half;
+    std::vector<float> mult(size_t(2) * M2 * half), gm(half), w(M2);
+    std::vector<int2> dp(M2);
+    for (size_t idx = 0; idx < half; ++idx) {
+        int k0, k1 = 0, k2;
+        if (D == 3) {
+            k0 = (int)(idx / (size_t(N) * NH));
+            k1 = (int)((idx / NH) % N);
+            k2 = (int)(idx % NH);
+        } else {
+            k0 = (int)(idx / NH);
+            k2 = (int)(idx % NH);
+        }
+        const bool nyq = k0 == H || k2 == H || (D == 3 && k1 == H);
+        const double sg = ((k0 + k1 + k2) & 1) ? -1.0 : 1.0;
+        double kv[3] = {(double)(k0 < H ? k0 : k0 - N), 0.0, 0.0};
+        if (D == 3) {
+            kv[1] = k1 < H ? k1 : k1 - N;
+            kv[2] = k2;
+        } else {
+            kv[1] = k2;
+        }
+        double k2sum = 0.0;
+        for (int a = 0; a < D; ++a) k2sum += kv[a] * kv[a];
+        double loss = 0.0;
+        for (int q = 0; q < M2; ++q) {
+            const double* e = &g->dir.sigma[size_t(dirs[q]) * D];
+            double ke = 0.0;
+            for (int a = 0; a < D; ++a) ke += kv[a] * e[a];
+            const double perp = std::sqrt(std::max(0.0, k2sum - ke * ke));
+            const double ph = carleman_phi(D, g->R, kPi * ke / g->L);
+            const double ps = carleman_psi(D, g->R, kPi * perp / g->L);
+            mult[size_t(q) * half + idx] = nyq ? 0.f : (float)(sg * ps);
+            mult[size_t(M2 + q) * half + idx] = nyq ? 0.f : (float)(sg * ph);
+            loss += g->dir.w[dirs[q]] * ph * ps;
+        }
+        gm[idx] = (float)(Bt * loss);
+    }
+    for (int q = 0; q < M2; ++q) {
+        w[q] = (float)(Bt * g->dir.w[dirs[q]]);
+        dp[q] = make_int2(q, M2 + q);
+    }
+    auto fail = [&](boltz_status st) {
+        cudaFree(g->d_cm_mult);
+        cudaFree(g->d_cm_gm);
+        cudaFree(g->d_cm_w);
+        cudaFree(g->d_cm_dpair);
+        g->d_cm_mult = nullptr;
+        g->d_cm_gm = nullptr;
+        g->d_cm_w = nullptr;
+        g->d_cm_dpair = nullptr;
+        (void)cudaGetLastError();
+        return st;
+    };
+    if (cudaMalloc(&g->d_cm_mult, mult.size() * 4) != cudaSuccess || cudaMalloc(&g->d_cm_gm, gm.size() * 4) != cudaSuccess ||
+        cudaMalloc(&g->d_cm_w, w.size() * 4) != cudaSuccess || cudaMalloc(&g->d_cm_dpair, dp.size() * sizeof(int2)) != cudaSuccess)
+        return fail(BOLTZ_ENOMEM);
+    if (cudaMemcpy(g->d_cm_mult, mult.data(), mult.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(g->d_cm_gm, gm.data(), gm.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(g->d_cm_w, w.data(), w.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(g->d_cm_dpair, dp.data(), dp.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess ||
+        prepare_contract_asym() != cudaSuccess)
+        return fail(BOLTZ_ECUDA);
+    return BOLTZ_OK;
+}
+
+// One evaluation batch in the Carleman form: per chunk f_N and Lambda (per-mode
+// loss table), the M multiplier fields of every input in one launch, the
+// asymmetric contraction into one slot per ordered pair, and the output
+// Q = P - f_N Lambda (no forward transform).
+boltz_status run_carleman(boltz_grid_s* g, const float2* spectra, int n_inputs, const int32_t* pj,
+                          const int32_t* pl, int n_pairs, float* Q_out, cudaStream_t st) {
+    if (!carleman_kernel(g->gamma, g->D)) return BOLTZ_EINVAL;
+    if (!carleman_shape(g->N, g->D)) return BOLTZ_EUNSUPPORTED;
+    boltz_status s0 = ensure_carleman_tables(g);
+    if (s0 != BOLTZ_OK) return s0;
+    s0 = prepare_plan(g, n_inputs, pj, pl, n_pairs, BOLTZ_FORM_CARLEMAN, 0, st, 4);
+    if (s0 != BOLTZ_OK) return s0;
+    const Plan& plan = g->last_plan;
+    const Dispatch* dp = dispatch_for(g->N, g->D);
+    char* ws = g->d_ws;
+    float* A = reinterpret_cast<float*>(ws + plan.off_A);
+    float* Pbuf = reinterpret_cast<float*>(ws + plan.off_P);
+    float* fN = reinterpret_cast<float*>(ws + plan.off_fN);
+    for (const auto& c : plan.chunks) {
+        const int nc = (int)c.inputs.size();
+        SynParams sp{};
+        sp.spectra = spectra;
+        sp.inputs = reinterpret_cast<const int*>(ws + plan.off_plan + c.off_inputs);
+        sp.phase = g->d_phase;
+        sp.gm = g->d_gm;
+        sp.gm_full = g->d_cm_gm;
+        sp.n_c = nc;
+        sp.M = g->M;
+        sp.id_node = g->n_rho * g->M;
+        sp.out = fN;
+        sp.n_fields = 2 * nc;
+        {
+            ProfScope ps(g, BOLTZ_KCLASS_PREP, st);
+            dp->synth(sp, SYN_PREP, st);
+        }
+        SynParams sm = sp;
+        sm.gm_full = nullptr;
+        sm.mult = g->d_cm_mult;
+        sm.out = A;
+        sm.n_fields = g->M * nc;
+        {
+            ProfScope ps(g, BOLTZ_KCLASS_SHIFT, st);
+            dp->synth(sm, SYN_MULT, st);
+        }
+        ConParams cp{};
+        cp.A = A;
+        cp.P = Pbuf;
+        cp.w = g->d_cm_w;
+        cp.dpair = g->d_cm_dpair;
+        cp.err = g->d_err;
+        cp.n_dpair = g->M / 2;
+        cp.M = g->M;
+        cp.n_c = nc;
+        cp.U = c.U;
+        cp.n = g->n;
+        for (int k : {TILE_FULL, TILE_LIST}) {
+            if (c.tiles[k].empty()) continue;
+            cp.tiles = reinterpret_cast<const Tile*>(ws + plan.off_plan + c.off_tiles[k]);
+            ProfScope ps(g, BOLTZ_KCLASS_CONTRACT, st);
+            launch_contract_asym(voxel_chunk(g->N, g->D), k, k == TILE_LIST ? 16 : c.tile_T, cp,
+                                 (int)c.tiles[k].size(), st);
+        }
+        ProfScope ps(g, BOLTZ_KCLASS_OUTPUT, st);
+        const dim3 grid((g->n / 4 + 255) / 256, c.U);
+        k_carleman_output<<<grid, 256, 0, st>>>(Pbuf, fN, fN + size_t(nc) * g->n,
+                                                 reinterpret_cast<const int*>(ws + plan.off_plan + c.off_start),
+                                                 reinterpret_cast<const int4*>(ws + plan.off_plan + c.off_outs), Q_out,
+                                                 g->n);
+    }
+    BZ_CUDA(cudaGetLastError());
+    return BOLTZ_OK;
+}
+
 // One batched evaluation in precision R (float: the product path; double:
 // the FP64 check build, same kernels and schedule).
 template <typename R>
 boltz_status run_batched(boltz_grid_s* g, const typename Prec<R>::C* spectra, int n_inputs, const int32_t* pj,
                          const int32_t* pl, int n_pairs, R* Q_out, int form, cudaStream_t st) {
     using C = typename Prec<R>::C;
+    if (form == BOLTZ_FORM_CARLEMAN) {
+        if constexpr (sizeof(R) == 4) return run_carleman(g, spectra, n_inputs, pj, pl, n_pairs, Q_out, st);
+        else return BOLTZ_EUNSUPPORTED;
+    }
     const bool split = form == BOLTZ_FORM_SPLIT_BF16;
     if (split && (sizeof(R) != 4 || !split_shape(g->N, g->D))) return BOLTZ_EUNSUPPORTED;
     boltz_status s0;
@@ -1483,6 +1866,10 @@ boltz_status boltz_grid_destroy(boltz_grid g) {
     cudaFree(g->d_w64);
     cudaFree(g->d_smat);
     cudaFree(g->d_scalar);
+    cudaFree(g->d_cm_mult);
+    cudaFree(g->d_cm_gm);
+    cudaFree(g->d_cm_w);
+    cudaFree(g->d_cm_dpair);
     cudaFree(g->d_ws);
     delete g;
     return BOLTZ_OK;
@@ -1511,6 +1898,8 @@ boltz_status boltz_workspace_size(boltz_grid g, int n_inputs, const int32_t* pai
                                   int n_pairs, int form, size_t* bytes) {
     if (!g || !bytes || !valid_form(form)) return BOLTZ_EINVAL;
     if (form == BOLTZ_FORM_SPLIT_BF16 && !split_shape(g->N, g->D)) return BOLTZ_EUNSUPPORTED;
+    if (form == BOLTZ_FORM_CARLEMAN && !carleman_kernel(g->gamma, g->D)) return BOLTZ_EINVAL;
+    if (form == BOLTZ_FORM_CARLEMAN && !carleman_shape(g->N, g->D)) return BOLTZ_EUNSUPPORTED;
     boltz_status s = check_pairs(n_inputs, pair_j, pair_l, n_pairs);
     if (s != BOLTZ_OK) return s;
     if (n_pairs == 0) {
@@ -1712,6 +2101,11 @@ boltz_status boltz_batch_plan(boltz_batch* out, const boltz_work* items, int n_i
         if (form == BOLTZ_FORM_SPLIT_BF16) {
             if (!split_shape(w.grid->N, w.grid->D)) return BOLTZ_EUNSUPPORTED;
             if ((s = ensure_split_tables(w.grid)) != BOLTZ_OK) return s;
+        }
+        if (form == BOLTZ_FORM_CARLEMAN) {
+            if (!carleman_kernel(w.grid->gamma, w.grid->D)) return BOLTZ_EINVAL;
+            if (!carleman_shape(w.grid->N, w.grid->D)) return BOLTZ_EUNSUPPORTED;
+            if ((s = ensure_carleman_tables(w.grid)) != BOLTZ_OK) return s;
         }
     }
     boltz_batch_s* b = new (std::nothrow) boltz_batch_s();

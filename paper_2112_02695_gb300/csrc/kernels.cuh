@@ -66,7 +66,10 @@ __device__ __forceinline__ int wrapk(int i, int N) { return i < N / 2 ? i : i - 
 // g_j,N(v - rho_q sigma_p / 2) for every (node in the q-block, direction,
 // chunk input); PREP: f_N (identity node) and Lambda_g (identity node times
 // the loss multiplier G-(|l|^2)) for every chunk input.
-enum { SYN_SHIFT = 0, SYN_PREP = 1 };
+// MULT: the Carleman-form fields IDFT(m_s * ghat) for every (slot s, chunk input)
+// with real per-mode multiplier tables m_s (which carry the (-1)^k grid sign
+// and are zero at the Nyquist indices).
+enum { SYN_SHIFT = 0, SYN_PREP = 1, SYN_MULT = 2 };
 
 template <typename R>
 struct SynParamsT {
@@ -74,8 +77,10 @@ struct SynParamsT {
     const C* spectra;       // [n_inputs][half]
     const int* inputs;      // chunk-local -> global input index [n_c]
     const C* phase;         // [nodes][D][N]: (-1)^k exp(-i pi k s_a / L), zero at the Nyquist index
-    const R* gm;            // [SMAX+1] loss multiplier
-    R* out;                 // SHIFT: [nq][M][n_c][n]; PREP: [2][n_c][n]
+    const R* gm;            // [SMAX+1] loss multiplier (function of |l|^2)
+    const R* gm_full;       // PREP: [half] loss multiplier per mode, or null (then gm)
+    const R* mult;          // MULT: [slots][half] multipliers
+    R* out;                 // SHIFT: [nq][M][n_c][n]; MULT: [slots][n_c][n]; PREP: [2][n_c][n]
     int n_c, M, q0, id_node, n_fields;
 };
 using SynParams = SynParamsT<float>;
@@ -155,9 +160,10 @@ __global__ void __launch_bounds__(Geo<N, D>::TPF * FPC) k_synth(SynParamsT<R> P)
     const C* __restrict__ ph = P.phase + (size_t)node * D * N;
     // start of row r of this field in the output (rows never straddle a voxel chunk)
     auto row_ptr = [&](int r) -> R* {
-        if (MODE == SYN_SHIFT) return shifted_field_row<N, D>(P.out, f / P.n_c, f % P.n_c, P.n_c, r * N);
+        if (MODE != SYN_PREP) return shifted_field_row<N, D>(P.out, f / P.n_c, f % P.n_c, P.n_c, r * N);
         return P.out + (size_t)f * G::n + (size_t)r * N;
     };
+    const R* __restrict__ mu = (MODE == SYN_MULT) ? P.mult + (size_t)(active ? f / P.n_c : 0) * G::half : nullptr;
     C x[N];
 
     if (D == 3) {
@@ -167,10 +173,16 @@ __global__ void __launch_bounds__(Geo<N, D>::TPF * FPC) k_synth(SynParamsT<R> P)
             const C w12 = cmul(__ldg(&ph[N + k1]), __ldg(&ph[2 * N + k2]));
 #pragma unroll
             for (int k0 = 0; k0 < N; ++k0) {
-                C v = cmul(__ldg(&src[(k0 * N + k1) * G::NH + k2]), cmul(w12, __ldg(&ph[k0])));
-                if (MODE == SYN_PREP && use_gm) {
-                    const int a = wrapk(k0, N), b = wrapk(k1, N);
-                    v = cscale(v, __ldg(&P.gm[a * a + b * b + k2 * k2]));
+                const int idx = (k0 * N + k1) * G::NH + k2;
+                C v;
+                if constexpr (MODE == SYN_MULT) {
+                    v = cscale(__ldg(&src[idx]), __ldg(&mu[idx]));
+                } else {
+                    v = cmul(__ldg(&src[idx]), cmul(w12, __ldg(&ph[k0])));
+                    if (MODE == SYN_PREP && use_gm) {
+                        const int a = wrapk(k0, N), b = wrapk(k1, N);
+                        v = cscale(v, P.gm_full ? __ldg(&P.gm_full[idx]) : __ldg(&P.gm[a * a + b * b + k2 * k2]));
+                    }
                 }
                 x[k0] = v;
             }
@@ -212,10 +224,16 @@ __global__ void __launch_bounds__(Geo<N, D>::TPF * FPC) k_synth(SynParamsT<R> P)
             const C w1 = __ldg(&ph[N + k1]);
 #pragma unroll
             for (int k0 = 0; k0 < N; ++k0) {
-                C v = cmul(__ldg(&src[k0 * G::NH + k1]), cmul(w1, __ldg(&ph[k0])));
-                if (MODE == SYN_PREP && use_gm) {
-                    const int a = wrapk(k0, N);
-                    v = cscale(v, __ldg(&P.gm[a * a + k1 * k1]));
+                const int idx = k0 * G::NH + k1;
+                C v;
+                if constexpr (MODE == SYN_MULT) {
+                    v = cscale(__ldg(&src[idx]), __ldg(&mu[idx]));
+                } else {
+                    v = cmul(__ldg(&src[idx]), cmul(w1, __ldg(&ph[k0])));
+                    if (MODE == SYN_PREP && use_gm) {
+                        const int a = wrapk(k0, N);
+                        v = cscale(v, P.gm_full ? __ldg(&P.gm_full[idx]) : __ldg(&P.gm[a * a + k1 * k1]));
+                    }
                 }
                 x[k0] = v;
             }
@@ -446,12 +464,19 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(ClusterGeo<N, CL>::
     if (active) {
         const int k1 = rank * PP + lt / H, k2 = lt % H;
         const float2 w12 = cmul(phs[N + k1], phs[2 * N + k2]);
+        const float* __restrict__ mu = (MODE == SYN_MULT) ? P.mult + (size_t)(f / P.n_c) * G::half : nullptr;
 #pragma unroll
         for (int k0 = 0; k0 < N; ++k0) {
-            float2 v = cmul(__ldg(&src[(k0 * N + k1) * G::NH + k2]), cmul(w12, phs[k0]));
-            if (MODE == SYN_PREP && use_gm) {
-                const int a = wrapk(k0, N), b = wrapk(k1, N);
-                v = cscale(v, __ldg(&P.gm[a * a + b * b + k2 * k2]));
+            const int idx = (k0 * N + k1) * G::NH + k2;
+            float2 v;
+            if constexpr (MODE == SYN_MULT) {
+                v = cscale(__ldg(&src[idx]), __ldg(&mu[idx]));
+            } else {
+                v = cmul(__ldg(&src[idx]), cmul(w12, phs[k0]));
+                if (MODE == SYN_PREP && use_gm) {
+                    const int a = wrapk(k0, N), b = wrapk(k1, N);
+                    v = cscale(v, P.gm_full ? __ldg(&P.gm_full[idx]) : __ldg(&P.gm[a * a + b * b + k2 * k2]));
+                }
             }
             x[k0] = v;
         }
@@ -499,7 +524,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(ClusterGeo<N, CL>::
     __syncthreads();
     if (active) {
         const int v0 = rank * CG::PART_N + 2 * lt;
-        if (MODE == SYN_SHIFT)
+        if (MODE != SYN_PREP)
             staged_copy<N, CL, true>(stg, shifted_field_row<N, 3>(P.out, f / P.n_c, f % P.n_c, P.n_c, v0),
                                      (size_t)(2 * NT / G::VCH) * P.n_c * G::VCH, lt);
         else
@@ -838,7 +863,10 @@ struct ContractShape {
     static constexpr int NACC = (KIND == TILE_TRI) ? TJ * (TJ + 1) / 2 : (KIND == TILE_FULL ? TJ * TL : TJ);
 };
 
-template <int KIND, int TJ, int TL, int VC, int STAGES, typename R = float>
+// ASYM (the Carleman form): slot x of a direction pair holds the g-side fields
+// and slot y the f-side fields, and only P[j,l] += w A_x[j] A_y[l] is summed
+// (FULL and LIST tiles; every ordered pair has its own gain slot).
+template <int KIND, int TJ, int TL, int VC, int STAGES, typename R = float, bool ASYM = false>
 __global__ void __launch_bounds__(VC, 1) k_contract_pipe(ConParamsT<R> C) {
     using CS = ContractShape<KIND, TJ, TL>;
     using PR = Prec<R>;
@@ -921,12 +949,16 @@ __global__ void __launch_bounds__(VC, 1) k_contract_pipe(ConParamsT<R> C) {
 #pragma unroll
             for (int x = 0; x < TJ; ++x)
 #pragma unroll
-                for (int y = 0; y < TL; ++y)
-                    acc[x * TL + y] = PR::fma_(xp[x], xq[TJ + y], PR::fma_(xq[x], xp[TJ + y], acc[x * TL + y]));
+                for (int y = 0; y < TL; ++y) {
+                    if constexpr (ASYM) acc[x * TL + y] = PR::fma_(xp[x], xq[TJ + y], acc[x * TL + y]);
+                    else acc[x * TL + y] = PR::fma_(xp[x], xq[TJ + y], PR::fma_(xq[x], xp[TJ + y], acc[x * TL + y]));
+                }
         } else {
 #pragma unroll
-            for (int i = 0; i < TJ; ++i)
-                acc[i] = PR::fma_(xp[i], xq[TJ + i], PR::fma_(xq[i], xp[TJ + i], acc[i]));
+            for (int i = 0; i < TJ; ++i) {
+                if constexpr (ASYM) acc[i] = PR::fma_(xp[i], xq[TJ + i], acc[i]);
+                else acc[i] = PR::fma_(xp[i], xq[TJ + i], PR::fma_(xq[i], xp[TJ + i], acc[i]));
+            }
         }
         __syncthreads();                                          // stage s fully read
         if (warp == 0 && k + STAGES < npairs) {
@@ -940,6 +972,27 @@ __global__ void __launch_bounds__(VC, 1) k_contract_pipe(ConParamsT<R> C) {
 #pragma unroll
     for (int i = 0; i < NACC; ++i)
         if (i < cnt) Pq[(size_t)(tl.slot0 + i) * n] = acc[i];
+}
+
+// ------------------------------------------------------------------ Carleman-form output
+// Q[e](v) = P[u](v) - f_N[l](v) Lambda[j](v) for every ordered pair e = (j, l)
+// of slot u (no forward transform: the gain's grid values are the weighted sum
+// of products itself).  Blocks (voxel quarter-chunk, slot).
+__global__ void __launch_bounds__(256) k_carleman_output(const float* __restrict__ Pg, const float* __restrict__ fN,
+                                                          const float* __restrict__ lam,
+                                                          const int* __restrict__ out_start,
+                                                          const int4* __restrict__ outs, float* __restrict__ Q, int n) {
+    const int u = blockIdx.y;
+    const int v4 = blockIdx.x * 256 + threadIdx.x;           // float4 index
+    if (v4 * 4 >= n) return;
+    const float4 p = __ldg(reinterpret_cast<const float4*>(Pg + (size_t)u * n) + v4);
+    for (int o = out_start[u]; o < out_start[u + 1]; ++o) {
+        const int4 e = outs[o];
+        const float4 a = __ldg(reinterpret_cast<const float4*>(fN + (size_t)e.z * n) + v4);
+        const float4 b = __ldg(reinterpret_cast<const float4*>(lam + (size_t)e.y * n) + v4);
+        reinterpret_cast<float4*>(Q + (size_t)e.x * n)[v4] =
+            make_float4(fmaf(-a.x, b.x, p.x), fmaf(-a.y, b.y, p.y), fmaf(-a.z, b.z, p.z), fmaf(-a.w, b.w, p.w));
+    }
 }
 
 // ------------------------------------------------------------------ FP64 moment sums
