@@ -322,6 +322,8 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-split", action="store_true")
     ap.add_argument("--no-carleman", action="store_true")
+    ap.add_argument("--form", default="batched", choices=["batched", "split", "carleman"],
+                    help="form of the headline measurement (the other arms run only with the default)")
     ap.add_argument("--field-budget-mb", type=int, default=0,
                     help="fix the schedule instead of autotuning it (e.g. for profiling runs)")
     args = ap.parse_args()
@@ -364,6 +366,8 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     from paper_2112_02695_gb300 import boltz as B
+    FORM = {"batched": B.BOLTZ_FORM_BATCHED, "split": B.BOLTZ_FORM_SPLIT_BF16,
+            "carleman": B.BOLTZ_FORM_CARLEMAN}[args.form]
 
     fields, pairs = make_inputs(args.config)
     n_in = fields.shape[0]
@@ -382,11 +386,12 @@ def main():
     if args.field_budget_mb > 0:
         tuned_mb = args.field_budget_mb
     else:
-        tuned_mb = B.boltz_autotune(g, spec, pj, pl, Q_scratch=Q, cache_path=os.environ.get("BOLTZ_TUNE_CACHE"))
+        tuned_mb = B.boltz_autotune(g, spec, pj, pl, Q_scratch=Q, form=FORM,
+                                    cache_path=os.environ.get("BOLTZ_TUNE_CACHE"))
 
     def step():
         B.boltz_spectrum(g, f_dev, out=spec)
-        B.boltz_collide_batched(g, spec, pj, pl, out=Q)
+        B.boltz_collide_batched(g, spec, pj, pl, form=FORM, out=Q)
         if kind == "pairs":
             B.boltz_project(g, f_dev, Q, out=T)
 
@@ -433,7 +438,7 @@ def main():
 
     # end to end through the public C API from pinned host buffers
     e2e = None
-    if kind == "pairs":
+    if kind == "pairs" and args.form == "batched":     # boltz_lowrank_step_host runs the batched form
         Vh = torch.tensor(fields).pin_memory()
         Qh = torch.empty((len(pairs),) + g.shape, dtype=torch.float32).pin_memory()
         Th = torch.empty((n_in, n_in, n_in), dtype=torch.float32).pin_memory()
@@ -452,7 +457,7 @@ def main():
 
     # plain per-evaluation FP32 form on the same batch
     plain = None
-    if not args.no_plain:
+    if not args.no_plain and args.form == "batched":
         Qp = torch.empty_like(Q)
 
         def step_plain():
@@ -471,7 +476,7 @@ def main():
     # split-precision form (BF16x3 DFT-as-GEMM shifted fields on the tensor cores), same batch
     split = None
     split_ok = d == 3 and N in (32, 64)
-    if split_ok and not args.no_split:
+    if split_ok and not args.no_split and args.form == "batched":
         Qs = torch.empty_like(Q)
         split_mb = args.field_budget_mb or B.boltz_autotune(g, spec, pj, pl, Q_scratch=Qs, form=B.BOLTZ_FORM_SPLIT_BF16,
                                                            cache_path=os.environ.get("BOLTZ_TUNE_CACHE"))
@@ -516,7 +521,8 @@ def main():
 
     # Carleman form (the paper's own fast method, gamma = d - 2 only) on the same batch
     carleman = None
-    if abs(gamma - (d - 2)) < 1e-12 and not (d == 2 and N == 128) and not args.no_carleman:
+    if (abs(gamma - (d - 2)) < 1e-12 and not (d == 2 and N == 128) and not args.no_carleman
+            and args.form == "batched"):
         Qc = torch.empty_like(Q)
 
         def step_carleman():
@@ -546,7 +552,7 @@ def main():
     # low-rank step consumers of this batch (Sec. 2.4 K- and L-step collision terms,
     # FP64 QR of K and L, Sec. 3.2 SVD truncation and basis rotation), L2 flushed before each call
     lowrank = None
-    if kind == "pairs":
+    if kind == "pairs" and args.form == "batched":
         lowrank = lowrank_consumers(B, T, Q, n_in, N ** d, flush, dev)
     mott = None
     if kind == "cells":
@@ -567,6 +573,12 @@ def main():
     max_mhz = clocks.get("sm_max_mhz") or 2070.0
     alu_peak = props.multi_processor_count * 128 * 2 * max_mhz * 1e6 / 1e12    # TFLOP/s FP32
     fl = algorithmic_flops(args.config, n_in, pairs)
+    if args.form == "carleman":
+        # M multiplier fields per input (one real multiply per mode), no radial step
+        ft = flops_per_transform(N ** d)
+        fl["shift"] = M * n_in * (ft + 2 * N ** d)
+        fl["radial"] = 0
+        fl["contract"] = (M // 2) * 2 * len(set(pairs)) * N ** d
     launches_s, ms_s = prof["shift"]
     shift_launches_per_step = launches_s / args.steps
     avg_launch_ms = ms_s / max(launches_s, 1)
@@ -575,12 +587,14 @@ def main():
     traffic = None
     try:
         with open(TRAFFIC_FILE) as fh:
-            tr = json.load(fh)
+            entries = json.load(fh)
         ksrc = open(os.path.join(ROOT, "paper_2112_02695_gb300", "csrc", "kernels.cuh"), "rb").read()
         fsrc = open(os.path.join(ROOT, "paper_2112_02695_gb300", "csrc", "fft.cuh"), "rb").read()
-        if (tr.get("source_sha256") == hashlib.sha256(ksrc + fsrc).hexdigest()
-                and tr.get("config") == args.config):
-            traffic = tr["bytes_per_launch"]
+        digest = hashlib.sha256(ksrc + fsrc).hexdigest()
+        for tr in entries:
+            if (tr.get("source_sha256") == digest and tr.get("config") == args.config
+                    and tr.get("form", "batched") == args.form and tr.get("field_budget_mb") == tuned_mb):
+                traffic = tr["bytes_per_launch"]
     except (OSError, ValueError, KeyError):
         traffic = None
     total_ms_prof = sum(ms for _, ms in prof.values())
@@ -613,14 +627,16 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "vs_baseline": None, "dtype": "bf16x3+f32" if args.form == "split" else "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD_NAMES[args.config], "evals_per_step": len(pairs),
-                       "autotuned_field_budget_mb": tuned_mb,
+                       "autotuned_field_budget_mb": tuned_mb, "form": args.form,
                        "l2": "flushed between timed steps (512 MB write outside the timed events)",
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                          "frac": achieved / alu_peak, "traffic": traffic,
-                         "kernel": "k_synth (phase-weighted inverse 3D transforms of the shifted fields)",
+                         "kernel": {"batched": "k_synth (phase-weighted inverse 3D transforms of the shifted fields)",
+                                    "carleman": "k_synth SYN_MULT (multiplier-weighted inverse 3D transforms)",
+                                    "split": "k_shift_split (tensor cores; algorithmic FFT flops over its time)"}[args.form],
                          "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz",
                          "step_alu_frac": (step_flops / (ms_per_step * 1e-3) / 1e12) / alu_peak},
             "kernel_shares": shares,
