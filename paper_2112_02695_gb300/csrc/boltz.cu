@@ -865,7 +865,7 @@ TablesT<double> tables_of(const boltz_grid_s* g, double) {
 // Asymmetric contraction of the Carleman form (FULL 8 x T strips and LIST 16).
 template <int KIND, int TJ, int TL, int VC>
 struct ContractLaunchA {
-    static constexpr int ROWS = ContractShape<KIND, TJ, TL>::ROWS;
+    static constexpr int ROWS = ContractShapeA<KIND, TJ, TL>::ROWS;
     static constexpr int STAGES = (ROWS * VC * 4 * 4 <= (192 << 10)) ? 4 : 3;
     static constexpr size_t SMEM = size_t(STAGES) * ROWS * VC * sizeof(float);
     static cudaError_t prepare() { return set_smem(k_contract_pipe<KIND, TJ, TL, VC, STAGES, float, true>, SMEM); }

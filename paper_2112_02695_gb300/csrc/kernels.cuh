@@ -863,14 +863,24 @@ struct ContractShape {
     static constexpr int NACC = (KIND == TILE_TRI) ? TJ * (TJ + 1) / 2 : (KIND == TILE_FULL ? TJ * TL : TJ);
 };
 
+// The asymmetric sum reads only the g-side j rows of slot x and the f-side l
+// rows of slot y: TJ + TL rows per stage (FULL) or 2 TJ (LIST).
+template <int KIND, int TJ, int TL>
+struct ContractShapeA {
+    static constexpr int ROWS = (KIND == TILE_FULL) ? TJ + TL : 2 * TJ;
+    static constexpr int NACC = (KIND == TILE_FULL) ? TJ * TL : TJ;
+};
+
 // ASYM (the Carleman form): slot x of a direction pair holds the g-side fields
 // and slot y the f-side fields, and only P[j,l] += w A_x[j] A_y[l] is summed
 // (FULL and LIST tiles; every ordered pair has its own gain slot).
 template <int KIND, int TJ, int TL, int VC, int STAGES, typename R = float, bool ASYM = false>
 __global__ void __launch_bounds__(VC, 1) k_contract_pipe(ConParamsT<R> C) {
     using CS = ContractShape<KIND, TJ, TL>;
+    using CA = ContractShapeA<KIND, TJ, TL>;
     using PR = Prec<R>;
-    constexpr int NR = CS::NR, ROWS = CS::ROWS, NACC = CS::NACC;
+    static_assert(!ASYM || KIND != TILE_TRI, "the asymmetric sum has no triangular tiles");
+    constexpr int NR = CS::NR, ROWS = ASYM ? CA::ROWS : CS::ROWS, NACC = ASYM ? CA::NACC : CS::NACC;
     constexpr uint32_t STAGE_BYTES = ROWS * VC * sizeof(R);
     extern __shared__ __align__(128) unsigned char csm_raw[];
     R* sbuf = reinterpret_cast<R*>(csm_raw);                      // [STAGES][ROWS][VC]
@@ -896,7 +906,19 @@ __global__ void __launch_bounds__(VC, 1) k_contract_pipe(ConParamsT<R> C) {
         R* dstp = sbuf + (size_t)s * ROWS * VC;
         if (lane == 0) mbar_arrive_expect_tx(&bars[s], STAGE_BYTES);
         __syncwarp();
-        if (KIND == TILE_LIST) {
+        if constexpr (ASYM) {
+            // rows [0, TJ): slot x (g side) rows j; then slot y (f side) rows l
+            if (KIND == TILE_LIST) {
+                for (int r = lane; r < ROWS; r += 32) {
+                    const int row = r < TJ ? tl.ja[r] : tl.lb[r - TJ];
+                    bulk_g2s(dstp + (size_t)r * VC, block_of(r < TJ ? d.x : d.y) + (size_t)row * VC,
+                             VC * sizeof(R), &bars[s]);
+                }
+            } else if (lane == 0) {
+                bulk_g2s(dstp, block_of(d.x) + (size_t)tl.j0 * VC, TJ * VC * sizeof(R), &bars[s]);
+                bulk_g2s(dstp + TJ * VC, block_of(d.y) + (size_t)tl.l0 * VC, TL * VC * sizeof(R), &bars[s]);
+            }
+        } else if (KIND == TILE_LIST) {
             for (int r = lane; r < ROWS; r += 32) {
                 const int i = r < NR ? r : r - NR;
                 const int row = i < TJ ? tl.ja[i] : tl.lb[i - TJ];
@@ -930,6 +952,23 @@ __global__ void __launch_bounds__(VC, 1) k_contract_pipe(ConParamsT<R> C) {
         }
         const R* __restrict__ xs = sbuf + (size_t)s * ROWS * VC + t;
         const R wk = __ldg(&C.w[k]);
+        if constexpr (ASYM) {
+            constexpr int NL = (KIND == TILE_FULL) ? TL : TJ;
+            R xj[TJ], xl[NL];
+#pragma unroll
+            for (int i = 0; i < TJ; ++i) xj[i] = wk * xs[i * VC];
+#pragma unroll
+            for (int i = 0; i < NL; ++i) xl[i] = xs[(TJ + i) * VC];
+            if (KIND == TILE_FULL) {
+#pragma unroll
+                for (int x = 0; x < TJ; ++x)
+#pragma unroll
+                    for (int y = 0; y < NL; ++y) acc[x * NL + y] = PR::fma_(xj[x], xl[y], acc[x * NL + y]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < TJ; ++i) acc[i] = PR::fma_(xj[i], xl[i], acc[i]);
+            }
+        } else {
         R xp[NR], xq[NR];
 #pragma unroll
         for (int i = 0; i < NR; ++i) {
@@ -949,16 +988,12 @@ __global__ void __launch_bounds__(VC, 1) k_contract_pipe(ConParamsT<R> C) {
 #pragma unroll
             for (int x = 0; x < TJ; ++x)
 #pragma unroll
-                for (int y = 0; y < TL; ++y) {
-                    if constexpr (ASYM) acc[x * TL + y] = PR::fma_(xp[x], xq[TJ + y], acc[x * TL + y]);
-                    else acc[x * TL + y] = PR::fma_(xp[x], xq[TJ + y], PR::fma_(xq[x], xp[TJ + y], acc[x * TL + y]));
-                }
+                for (int y = 0; y < TL; ++y)
+                    acc[x * TL + y] = PR::fma_(xp[x], xq[TJ + y], PR::fma_(xq[x], xp[TJ + y], acc[x * TL + y]));
         } else {
 #pragma unroll
-            for (int i = 0; i < TJ; ++i) {
-                if constexpr (ASYM) acc[i] = PR::fma_(xp[i], xq[TJ + i], acc[i]);
-                else acc[i] = PR::fma_(xp[i], xq[TJ + i], PR::fma_(xq[i], xp[TJ + i], acc[i]));
-            }
+            for (int i = 0; i < TJ; ++i) acc[i] = PR::fma_(xp[i], xq[TJ + i], PR::fma_(xq[i], xp[TJ + i], acc[i]));
+        }
         }
         __syncthreads();                                          // stage s fully read
         if (warp == 0 && k + STAGES < npairs) {
