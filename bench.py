@@ -281,6 +281,12 @@ def run_mixed(args, world, rank, local_rank):
                           pair_j=pj, pair_l=pl, Q_out=torch.empty((r * r,) + g.shape, device=dev), V=V,
                           T_out=torch.empty((r, r, r), device=dev)))
         evals += r * r
+    # each grid's schedule autotuned on its own item before the graph is captured
+    for it in items:
+        B.boltz_spectrum(it["grid"], it["fields"], out=it["spectra"])
+        B.boltz_autotune(it["grid"], it["spectra"], it["pair_j"], it["pair_l"], Q_scratch=it["Q_out"],
+                         cache_path=os.environ.get("BOLTZ_TUNE_CACHE"))
+    torch.cuda.synchronize()
     batch = B.boltz_batch_plan(items)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     for _ in range(args.warmup):
