@@ -1637,10 +1637,10 @@ void launch_qr(const double* W, int r, int n, double w, double* Y, double* R, ch
     double* R1 = Rinv + size_t(r) * r;
     const int grid = (n + kLrThreads - 1) / kLrThreads;
     k_gram_f64<<<ns, kLrThreads, 0, st>>>(W, r, n, ns, part);
-    k_chol_f64<<<1, 64, kCholSmem, st>>>(part, ns, r, w, nullptr, R1, Rinv, info);
+    k_chol_f64<<<1, kCholThreads, kCholSmem, st>>>(part, ns, r, w, nullptr, R1, Rinv, info);
     k_apply_rinv_f64<RMAX><<<grid, kLrThreads, 0, st>>>(W, Rinv, r, n, Y);
     k_gram_f64<<<ns, kLrThreads, 0, st>>>(Y, r, n, ns, part);
-    k_chol_f64<<<1, 64, kCholSmem, st>>>(part, ns, r, w, R1, R, Rinv, info);
+    k_chol_f64<<<1, kCholThreads, kCholSmem, st>>>(part, ns, r, w, R1, R, Rinv, info);
     k_apply_rinv_f64<RMAX><<<grid, kLrThreads, 0, st>>>(Y, Rinv, r, n, Y);
 }
 

@@ -226,21 +226,29 @@ __global__ void __launch_bounds__(kLrThreads) k_gram_f64(const double* __restric
 // pass already failed, and R, Rinv are NaN.
 constexpr size_t kCholSmem = 3 * 64 * 64 * sizeof(double);
 
-__global__ void __launch_bounds__(64) k_chol_f64(const double* __restrict__ part, int nslices, int r, double w,
-                                                 const double* __restrict__ Rprev, double* __restrict__ Rout,
-                                                 double* __restrict__ Rinv, int* __restrict__ info) {
+constexpr int kCholThreads = 1024;
+
+__global__ void __launch_bounds__(kCholThreads) k_chol_f64(const double* __restrict__ part, int nslices, int r, double w,
+                                                          const double* __restrict__ Rprev, double* __restrict__ Rout,
+                                                          double* __restrict__ Rinv, int* __restrict__ info) {
     extern __shared__ double chol_smem[];
     double* G = chol_smem;                         // [64 * 64] each
     double* Rs = chol_smem + 64 * 64;
     double* Xs = chol_smem + 2 * 64 * 64;
     __shared__ int bad;
-    const int t = threadIdx.x;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    constexpr int NW = kCholThreads / 32;
     if (t == 0) bad = 0;
-    for (int e = t; e < r * r; e += 64) {
+    // G = w sum_s part[s]: one warp per entry, lanes over the slices, fixed-order tree
+    for (int e = warp; e < r * r; e += NW) {
         double g = 0.0;
-        for (int s = 0; s < nslices; ++s) g += part[(size_t)s * r * r + e];
-        G[e] = w * g;
-        Rs[e] = 0.0;
+        for (int s = lane; s < nslices; s += 32) g += part[(size_t)s * r * r + e];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) g += __shfl_down_sync(0xffffffffu, g, o);
+        if (lane == 0) {
+            G[e] = w * g;
+            Rs[e] = 0.0;
+        }
     }
     __syncthreads();
     for (int k = 0; k < r; ++k) {
@@ -255,7 +263,7 @@ __global__ void __launch_bounds__(64) k_chol_f64(const double* __restrict__ part
         }
         __syncthreads();
         if (bad) break;
-        for (int j = k + 1 + t; j < r; j += 64) {
+        for (int j = k + 1 + t; j < r; j += kCholThreads) {
             double a = G[k * r + j];
             for (int i = 0; i < k; ++i) a -= Rs[i * r + k] * Rs[i * r + j];
             Rs[k * r + j] = a / Rs[k * r + k];
@@ -265,14 +273,14 @@ __global__ void __launch_bounds__(64) k_chol_f64(const double* __restrict__ part
     if (bad) {
         if (t == 0 && *info == 0) *info = bad;     // the first failing pass is reported
         const double nan = __longlong_as_double(0x7ff8000000000000ll);
-        for (int e = t; e < r * r; e += 64) {
+        for (int e = t; e < r * r; e += kCholThreads) {
             Rout[e] = nan;
             Rinv[e] = nan;
         }
         return;
     }
     // Rinv by back substitution, one column per thread: R X = I
-    for (int j = t; j < r; j += 64) {
+    for (int j = t; j < r; j += kCholThreads) {
         for (int i = r - 1; i >= 0; --i) {
             double a = (i == j) ? 1.0 : 0.0;
             for (int k = i + 1; k <= j; ++k) a -= Rs[i * r + k] * Xs[k * r + j];
@@ -280,7 +288,7 @@ __global__ void __launch_bounds__(64) k_chol_f64(const double* __restrict__ part
         }
     }
     __syncthreads();
-    for (int e = t; e < r * r; e += 64) {
+    for (int e = t; e < r * r; e += kCholThreads) {
         Rinv[e] = Xs[e];
         const int i = e / r, j = e % r;
         double o = Rs[e];
@@ -319,33 +327,32 @@ __global__ void __launch_bounds__(kLrThreads) k_apply_rinv_f64(const double* W, 
 // ---------------------------------------------------------------- one-sided Jacobi SVD (FP64)
 // One CTA of 32 warps: in every round of a sweep the columns are paired by
 // the round-robin schedule and warp p rotates pair p (lanes split the r
-// entries, dot products by shuffles).  A sweep without a rotation ends it.
-constexpr int kSvdMaxSweeps = 60;
-constexpr size_t kSvdSmem = 2 * 64 * 64 * sizeof(double);
+// entries, dot products by shuffles, the rotation computed in one lane).  A
+// sweep without a rotation ends the iteration.  FP64 issues at a small
+// fraction of the FP32 rate on this GPU, so the sweeps first run in FP32 on a
+// rounded copy; the accumulated rotations are re-orthonormalised in FP64
+// (V <- V (I - E/2), E = V^T V - I, twice) and the FP64 sweeps then start from
+// A = S V, which is already diagonal to FP32 accuracy.
+constexpr int kSvdMaxSweeps = 40;
+constexpr size_t kSvdSmem = 2 * 64 * 64 * sizeof(double) + 2 * 64 * 64 * sizeof(float) + 64 * 64 * sizeof(double);
 
-__global__ void __launch_bounds__(1024) k_svd_jacobi_f64(const double* __restrict__ S, int r, double drop_tol,
-                                                        double* __restrict__ U, double* __restrict__ sigma,
-                                                        double* __restrict__ Qm, int* __restrict__ r_keep,
-                                                        int* __restrict__ info) {
-    extern __shared__ double svd_smem[];
-    double* A = svd_smem;                          // column-major: column c at c*64
-    double* V = svd_smem + 64 * 64;
-    __shared__ double sv[64];
-    __shared__ int order[64];
-    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+template <typename T>
+__device__ __forceinline__ T jac_rsqrt(T x);
+template <>
+__device__ __forceinline__ float jac_rsqrt(float x) { return rsqrtf(x); }
+template <>
+__device__ __forceinline__ double jac_rsqrt(double x) { return rsqrt(x); }
+
+// Sweeps on column-major A, V (column c at c*64) until no pair has
+// |a_p . a_q| > tol * |a_p| |a_q|; returns whether that happened.
+template <typename T>
+__device__ bool jacobi_sweeps(T* A, T* V, int r, T tol, int max_sweeps) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m = (r + 1) & ~1;                   // even number of columns (one idle column if r is odd)
-    for (int e = t; e < 64 * 64; e += 1024) {
-        const int c = e / 64, i = e % 64;
-        A[e] = (c < r && i < r) ? S[i * r + c] : 0.0;
-        V[e] = (c == i && c < r) ? 1.0 : 0.0;
-    }
-    __syncthreads();
-    int sweep = 0;
-    bool converged = false;
-    for (; sweep < kSvdMaxSweeps && !converged; ++sweep) {
+    const T tol2 = tol * tol;
+    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
         int rotated = 0;
         for (int round = 0; round < m - 1; ++round) {
-            // round-robin: position 0 fixed, the others rotate
             if (warp < m / 2) {
                 auto slot = [&](int pos) { return pos == 0 ? 0 : 1 + (pos - 1 + round) % (m - 1); };
                 int p = slot(warp), q = slot(m - 1 - warp);
@@ -355,32 +362,30 @@ __global__ void __launch_bounds__(1024) k_svd_jacobi_f64(const double* __restric
                     q = tmp;
                 }
                 if (q < r) {
-                    // FP64 issues slowly on this GPU: reduce to lane 0 with predicated adds,
-                    // compute the rotation there only, broadcast (c, s)
-                    double al = 0.0, be = 0.0, ga = 0.0;
+                    T al = T(0), be = T(0), ga = T(0);
                     for (int i = lane; i < r; i += 32) {
-                        const double x = A[p * 64 + i], y = A[q * 64 + i];
+                        const T x = A[p * 64 + i], y = A[q * 64 + i];
                         al = fma(x, x, al);
                         be = fma(y, y, be);
                         ga = fma(x, y, ga);
                     }
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) {
-                        const double a2 = __shfl_down_sync(0xffffffffu, al, o);
-                        const double b2 = __shfl_down_sync(0xffffffffu, be, o);
-                        const double g2 = __shfl_down_sync(0xffffffffu, ga, o);
+                        const T a2 = __shfl_down_sync(0xffffffffu, al, o);
+                        const T b2 = __shfl_down_sync(0xffffffffu, be, o);
+                        const T g2 = __shfl_down_sync(0xffffffffu, ga, o);
                         if (lane < o && lane + o < r) {
                             al += a2;
                             be += b2;
                             ga += g2;
                         }
                     }
-                    double c = 1.0, s = 0.0;
+                    T c = T(1), s = T(0);
                     int rot = 0;
-                    if (lane == 0 && ga != 0.0 && ga * ga > 1e-30 * (al * be)) {
-                        const double zeta = (be - al) / (2.0 * ga);
-                        const double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
-                        c = rsqrt(fma(tt, tt, 1.0));
+                    if (lane == 0 && ga != T(0) && ga * ga > tol2 * (al * be)) {
+                        const T zeta = (be - al) / (T(2) * ga);
+                        const T tt = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(fma(zeta, zeta, T(1))));
+                        c = jac_rsqrt(fma(tt, tt, T(1)));
                         s = c * tt;
                         rot = 1;
                     }
@@ -389,10 +394,10 @@ __global__ void __launch_bounds__(1024) k_svd_jacobi_f64(const double* __restric
                         c = __shfl_sync(0xffffffffu, c, 0);
                         s = __shfl_sync(0xffffffffu, s, 0);
                         for (int i = lane; i < r; i += 32) {
-                            const double x = A[p * 64 + i], y = A[q * 64 + i];
+                            const T x = A[p * 64 + i], y = A[q * 64 + i];
                             A[p * 64 + i] = c * x - s * y;
                             A[q * 64 + i] = s * x + c * y;
-                            const double vx = V[p * 64 + i], vy = V[q * 64 + i];
+                            const T vx = V[p * 64 + i], vy = V[q * 64 + i];
                             V[p * 64 + i] = c * vx - s * vy;
                             V[q * 64 + i] = s * vx + c * vy;
                         }
@@ -402,8 +407,69 @@ __global__ void __launch_bounds__(1024) k_svd_jacobi_f64(const double* __restric
             }
             __syncthreads();
         }
-        converged = !__syncthreads_or(rotated);
+        if (!__syncthreads_or(rotated)) return true;
     }
+    return false;
+}
+
+__global__ void __launch_bounds__(1024) k_svd_jacobi_f64(const double* __restrict__ S, int r, double drop_tol,
+                                                        double* __restrict__ U, double* __restrict__ sigma,
+                                                        double* __restrict__ Qm, int* __restrict__ r_keep,
+                                                        int* __restrict__ info) {
+    extern __shared__ double svd_smem[];
+    double* A = svd_smem;                          // column-major: column c at c*64
+    double* V = svd_smem + 64 * 64;
+    float* Af = reinterpret_cast<float*>(svd_smem + 2 * 64 * 64);
+    float* Vf = Af + 64 * 64;
+    double* E = svd_smem + 2 * 64 * 64 + 64 * 64;  // after the two float arrays (64*64 doubles' room)
+    __shared__ double sv[64];
+    __shared__ int order[64];
+    const int t = threadIdx.x;
+    for (int e = t; e < 64 * 64; e += 1024) {
+        const int c = e / 64, i = e % 64;
+        Af[e] = (c < r && i < r) ? (float)S[i * r + c] : 0.f;
+        Vf[e] = (c == i && c < r) ? 1.f : 0.f;
+    }
+    __syncthreads();
+    (void)jacobi_sweeps<float>(Af, Vf, r, 1e-6f, kSvdMaxSweeps);
+    // V = Vf re-orthonormalised in FP64: V <- V (I - E/2), E = V^T V - I, twice
+    for (int e = t; e < 64 * 64; e += 1024) V[e] = (double)Vf[e];
+    __syncthreads();
+    for (int it = 0; it < 2; ++it) {
+        for (int e = t; e < r * r; e += 1024) {
+            const int a = e / r, b = e % r;
+            double g = 0.0;
+            for (int i = 0; i < r; ++i) g = fma(V[a * 64 + i], V[b * 64 + i], g);
+            E[a * 64 + b] = g - (a == b ? 1.0 : 0.0);
+        }
+        __syncthreads();
+        for (int e = t; e < r * r; e += 1024) {          // new column c, row i
+            const int c = e / r, i = e % r;
+            double v = V[c * 64 + i];
+            for (int k = 0; k < r; ++k) v = fma(-0.5 * V[k * 64 + i], E[k * 64 + c], v);
+            A[c * 64 + i] = v;                               // A as scratch for the new V
+        }
+        __syncthreads();
+        for (int e = t; e < r * r; e += 1024) {
+            const int c = e / r, i = e % r;
+            V[c * 64 + i] = A[c * 64 + i];
+        }
+        __syncthreads();
+    }
+    // A = S V, then the FP64 sweeps
+    for (int e = t; e < 64 * 64; e += 1024) {
+        const int c = e / 64, i = e % 64;
+        double a = 0.0;
+        if (c < r && i < r)
+            for (int k = 0; k < r; ++k) a = fma(S[i * r + k], V[c * 64 + k], a);
+        A[e] = a;
+    }
+    for (int e = t; e < 64 * 64; e += 1024) {
+        const int c = e / 64, i = e % 64;
+        if (c >= r || i >= r) V[e] = 0.0;
+    }
+    __syncthreads();
+    const bool converged = jacobi_sweeps<double>(A, V, r, 1e-15, kSvdMaxSweeps);
     // singular values = column norms; sort descending (one thread, r <= 64)
     if (t < r) {
         double nn = 0.0;
