@@ -376,8 +376,9 @@ using OutParams = OutParamsT<float>;
 // ------------------------------------------------------------------ 3D field kernels on a CTA cluster
 // Same transforms as k_synth / k_analysis / k_output for d = 3, with one field
 // spread over a cluster of CL CTAs: CTA r holds the PP = N/CL planes i0 in
-// [r PP, r PP + PP) in shared memory (for 32^3 two CTAs of 71 KB, three per
-// SM; for 64^3 eight CTAs of 134 KB).  The transform along axis 0 is the only
+// [r PP, r PP + PP) in shared memory (for 32^3 the synthesis runs on four
+// CTAs of 35 KB, six per SM, the analysis and output on two CTAs of 71 KB,
+// three per SM; for 64^3 eight CTAs of 134 KB).  The transform along axis 0 is the only
 // one that crosses planes; it reads or writes the other CTAs' planes through
 // distributed shared memory, between cluster barriers.  A CTA's part of a
 // real field is one contiguous block of global memory; it is moved through a
@@ -398,7 +399,7 @@ struct ClusterGeo {
     static constexpr int PART_N = PP * N * N;    // floats of a field held by one CTA
     static constexpr int COLS = PP * (H + 1);    // columns of a CTA incl. the half-axis Nyquist
     static constexpr size_t SMEM = size_t(PP) * PS * sizeof(float2) + 3 * N * sizeof(float2);
-    static constexpr int MINB = (SMEM <= (72u << 10)) ? 3 : 1;
+    static constexpr int MINB = (SMEM <= (36u << 10)) ? 6 : ((SMEM <= (72u << 10)) ? 3 : 1);
     static_assert(size_t(PP) * N * RR * sizeof(float) <= size_t(PP) * PS * sizeof(float2), "staging fits");
     static_assert((2 * NT) % N == 0 && (2 * NT) % Geo<N, 3>::VCH == 0 && PART_N % (2 * NT) == 0, "copy strides");
 };
