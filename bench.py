@@ -596,7 +596,8 @@ def main():
             entries = json.load(fh)
         ksrc = open(os.path.join(ROOT, "paper_2112_02695_gb300", "csrc", "kernels.cuh"), "rb").read()
         fsrc = open(os.path.join(ROOT, "paper_2112_02695_gb300", "csrc", "fft.cuh"), "rb").read()
-        digest = hashlib.sha256(ksrc + fsrc).hexdigest()
+        lsrc = open(os.path.join(ROOT, "paper_2112_02695_gb300", "csrc", "boltz.cu"), "rb").read()
+        digest = hashlib.sha256(ksrc + fsrc + lsrc).hexdigest()
         for tr in entries:
             if (tr.get("source_sha256") == digest and tr.get("config") == args.config
                     and tr.get("form", "batched") == args.form and tr.get("field_budget_mb") == tuned_mb):

@@ -230,10 +230,11 @@ boltz_status boltz_project_f64(boltz_grid g, const double* V, int r, const doubl
 
 /*
  * Autotuner of the batch schedule.  The tunable is the device memory budget
- * for the shifted fields of one radial block (48, 96, 192 or 384 MB): it
- * sets how many inputs share a chunk (so how often shifted fields are
+ * for the shifted fields of one radial block (48, 96, 192, 384 or 768 MB):
+ * it sets how many inputs share a chunk (so how often shifted fields are
  * recomputed) and how many radial nodes one launch covers (so how long the
- * launch chain is and whether the fields stay in the 126 MB L2).  Each
+ * launch chain is, whether the fields stay in the 126 MB L2, and how evenly
+ * the launches' CTAs fill the last wave on the SMs).  Each
  * candidate runs the given batch three times on `stream` (the first untimed)
  * and the fastest is kept in the grid for later calls.  With a cache path,
  * the choice is read from and written to a JSON file keyed by

@@ -1526,7 +1526,7 @@ namespace {
 
 // Candidate budgets (MB) for the shifted fields of one radial block: they set
 // how many inputs share a chunk and how many radial nodes a launch covers.
-const int kBudgetCandidatesMB[] = {48, 96, 192, 384};
+const int kBudgetCandidatesMB[] = {48, 96, 192, 384, 768};
 
 // Minimal persistent cache: one JSON object {"key": value, ...} of integers.
 std::map<std::string, long> read_cache(const char* path) {

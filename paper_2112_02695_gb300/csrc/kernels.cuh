@@ -377,31 +377,35 @@ using OutParams = OutParamsT<float>;
 // Same transforms as k_synth / k_analysis / k_output for d = 3, with one field
 // spread over a cluster of CL CTAs: CTA r holds the PP = N/CL planes i0 in
 // [r PP, r PP + PP) in shared memory (for 32^3 the synthesis runs on four
-// CTAs of 35 KB, six per SM, the analysis and output on two CTAs of 71 KB,
-// three per SM; for 64^3 eight CTAs of 134 KB).  The transform along axis 0 is the only
-// one that crosses planes; it reads or writes the other CTAs' planes through
-// distributed shared memory, between cluster barriers.  A CTA's part of a
-// real field is one contiguous block of global memory; it is moved through a
-// staging copy in shared memory (rows padded to N+2 floats) so that every
-// warp reads or writes 256 contiguous bytes, and the node's three phase rows
-// are staged once per CTA.  Planes are padded by 8 complex entries so that
-// the plane groups a warp touches fall on different banks.
+// CTAs of 37 KB, six per SM, the analysis and output on two CTAs of 73 KB,
+// three per SM; for 64^3 eight CTAs of 138 KB).  The transform along axis 0
+// is the only one that crosses planes; it reads or writes the other CTAs'
+// planes through distributed shared memory, between cluster barriers.  A
+// CTA's part of a real field is one contiguous block of global memory; it is
+// moved through a staging copy in shared memory (rows padded to N+4 floats)
+// so that every warp reads or writes 512 contiguous bytes with 16-byte
+// accesses, and the node's three phase rows are staged once per CTA.  Complex
+// rows have an even stride (N/2 + 2 entries), so the real-to-complex and
+// complex-to-real passes move two entries per 16-byte access.  Planes are
+// padded by 8 complex entries so that the plane groups a warp touches fall on
+// different banks, except for 32^3, where the two planes a warp touches need
+// two wavefronts anyway and the padding would cost the sixth CTA per SM.
 namespace cg = cooperative_groups;
 
 template <int N, int CL>
 struct ClusterGeo {
     static constexpr int H = N / 2;
     static constexpr int PP = N / CL;            // planes per CTA
-    static constexpr int RS = H + 1;             // complex row stride
-    static constexpr int PS = N * RS + 8;        // complex plane stride
-    static constexpr int RR = N + 2;             // staged real row stride (floats)
+    static constexpr int RS = H + 2;             // complex row stride (even: rows start on 16 bytes)
+    static constexpr int PS = N * RS + (N == 32 ? 0 : 8);   // complex plane stride
+    static constexpr int RR = N + 4;             // staged real row stride (floats, 16-byte rows)
     static constexpr int NT = PP * H;            // threads per CTA
     static constexpr int PART_N = PP * N * N;    // floats of a field held by one CTA
     static constexpr int COLS = PP * (H + 1);    // columns of a CTA incl. the half-axis Nyquist
     static constexpr size_t SMEM = size_t(PP) * PS * sizeof(float2) + 3 * N * sizeof(float2);
-    static constexpr int MINB = (SMEM <= (36u << 10)) ? 6 : ((SMEM <= (72u << 10)) ? 3 : 1);
+    static constexpr int MINB = (SMEM <= (37u << 10)) ? 6 : ((SMEM <= (74u << 10)) ? 3 : 1);
     static_assert(size_t(PP) * N * RR * sizeof(float) <= size_t(PP) * PS * sizeof(float2), "staging fits");
-    static_assert((2 * NT) % N == 0 && (2 * NT) % Geo<N, 3>::VCH == 0 && PART_N % (2 * NT) == 0, "copy strides");
+    static_assert((4 * NT) % N == 0 && (4 * NT) % Geo<N, 3>::VCH == 0 && PART_N % (4 * NT) == 0, "copy strides");
 };
 
 // pointers to the plane buffers of every CTA of the cluster (index = rank)
@@ -412,22 +416,65 @@ __device__ __forceinline__ void cluster_planes(cg::cluster_group& cluster, float
 }
 
 // Coalesced move of this CTA's part of a real field between a staging area in
-// shared memory (rows of N floats padded to RR) and global memory: thread lt
-// moves floats L = 2 lt + 2 NT it; both addresses advance by constants.
+// shared memory (rows of N floats padded to RR) and global memory, 16 bytes a
+// thread: thread lt moves floats L = 4 lt + 4 NT it; both addresses advance
+// by constants.
 template <int N, int CL, bool TO_GLOBAL>
 __device__ __forceinline__ void staged_copy(float* stg, float* gptr, size_t g_step, int lt) {
     using CG = ClusterGeo<N, CL>;
-    constexpr int ITER = CG::PART_N / (2 * CG::NT);
-    constexpr int S_STEP = (2 * CG::NT / N) * CG::RR;
-    const int L0 = 2 * lt;
+    constexpr int ITER = CG::PART_N / (4 * CG::NT);
+    constexpr int S_STEP = (4 * CG::NT / N) * CG::RR;
+    const int L0 = 4 * lt;
     float* sp = stg + (L0 / N) * CG::RR + (L0 % N);
 #pragma unroll 8
     for (int it = 0; it < ITER; ++it) {
-        float2* g = reinterpret_cast<float2*>(gptr + it * g_step);
-        float2* sm = reinterpret_cast<float2*>(sp + it * S_STEP);
+        float4* g = reinterpret_cast<float4*>(gptr + it * g_step);
+        float4* sm = reinterpret_cast<float4*>(sp + it * S_STEP);
         if (TO_GLOBAL) *g = *sm;
         else *sm = __ldg(g);
     }
+}
+
+// Two rows of N reals staged in shared memory (16-byte aligned) into the two
+// halves of a complex register line: x[c] = (a[c], b[c]).
+template <int N>
+__device__ __forceinline__ void load_two_rows_smem(const float* a, const float* b, float2 (&x)[N]) {
+    const float4* a4 = reinterpret_cast<const float4*>(a);
+    const float4* b4 = reinterpret_cast<const float4*>(b);
+#pragma unroll
+    for (int c = 0; c < N / 4; ++c) {
+        const float4 p = a4[c], q = b4[c];
+        x[4 * c] = make_float2(p.x, q.x);
+        x[4 * c + 1] = make_float2(p.y, q.y);
+        x[4 * c + 2] = make_float2(p.z, q.z);
+        x[4 * c + 3] = make_float2(p.w, q.w);
+    }
+}
+
+// Complex-to-real input line from two half-spectrum rows r1, r2 (entries
+// 0..N/2, read 16 bytes at a time): x[k] = r1[k] + i r2[k] and
+// x[N-k] = conj(r1[k]) + i conj(r2[k]), so that one complex inverse transform
+// gives row 1 in the real and row 2 in the imaginary parts.  The Nyquist
+// entries r[N/2] are read only when NYQ (they are zero in the shifted fields).
+template <int N, bool NYQ>
+__device__ __forceinline__ void c2r_pack_rows(const float2* r1, const float2* r2, float2 (&x)[N]) {
+    constexpr int H = N / 2;
+    const float4* a4 = reinterpret_cast<const float4*>(r1);
+    const float4* b4 = reinterpret_cast<const float4*>(r2);
+#pragma unroll
+    for (int c = 0; c < H / 2; ++c) {
+        const float4 a = a4[c], b = b4[c];           // entries k = 2c and 2c + 1 of both rows
+        const int k = 2 * c;
+        if (k == 0) {
+            x[0] = make_float2(a.x, b.x);
+        } else {
+            x[k] = make_float2(a.x - b.y, a.y + b.x);
+            x[N - k] = make_float2(a.x + b.y, b.x - a.y);
+        }
+        x[k + 1] = make_float2(a.z - b.w, a.w + b.z);
+        x[N - k - 1] = make_float2(a.z + b.w, b.z - a.w);
+    }
+    x[H] = NYQ ? make_float2(r1[H].x, r2[H].x) : make_float2(0.f, 0.f);
 }
 
 template <int N, int CL, int MODE>
@@ -499,37 +546,20 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(ClusterGeo<N, CL>::
     // axis 2: complex-to-real of rows (p0, i1) and (p0, i1 + N/2)
     const int p0 = lt / H, i1 = lt % H;
     if (active) {
-        const float2* r1 = smem + p0 * PS + i1 * RS;
-        const float2* r2 = smem + p0 * PS + (i1 + H) * RS;
-        x[0] = make_float2(r1[0].x, r2[0].x);
-        x[H] = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int k = 1; k < H; ++k) {
-            const float2 a = r1[k], b = r2[k];
-            x[k] = make_float2(a.x - b.y, a.y + b.x);
-            x[N - k] = make_float2(a.x + b.y, b.x - a.y);
-        }
+        c2r_pack_rows<N, false>(smem + p0 * PS + i1 * RS, smem + p0 * PS + (i1 + H) * RS, x);
         fft_reg<N, true>(x);
     }
     __syncthreads();                              // every row is read before staging overwrites the planes
     float* stg = reinterpret_cast<float*>(smem);
-    if (active) {
-        float2* o1 = reinterpret_cast<float2*>(stg + (p0 * N + i1) * RR);
-        float2* o2 = reinterpret_cast<float2*>(stg + (p0 * N + i1 + H) * RR);
-#pragma unroll
-        for (int c = 0; c < N / 2; ++c) {
-            o1[c] = make_float2(x[2 * c].x, x[2 * c + 1].x);
-            o2[c] = make_float2(x[2 * c].y, x[2 * c + 1].y);
-        }
-    }
+    if (active) store_two_rows<N>(stg + (p0 * N + i1) * RR, stg + (p0 * N + i1 + H) * RR, x);
     __syncthreads();
     if (active) {
-        const int v0 = rank * CG::PART_N + 2 * lt;
+        const int v0 = rank * CG::PART_N + 4 * lt;
         if (MODE != SYN_PREP)
             staged_copy<N, CL, true>(stg, shifted_field_row<N, 3>(P.out, f / P.n_c, f % P.n_c, P.n_c, v0),
-                                     (size_t)(2 * NT / G::VCH) * P.n_c * G::VCH, lt);
+                                     (size_t)(4 * NT / G::VCH) * P.n_c * G::VCH, lt);
         else
-            staged_copy<N, CL, true>(stg, P.out + (size_t)f * G::n + v0, 2 * NT, lt);
+            staged_copy<N, CL, true>(stg, P.out + (size_t)f * G::n + v0, 4 * NT, lt);
     }
 }
 
@@ -558,30 +588,27 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(ClusterGeo<N, CL>::
             (size_t)rank * CG::PART_N;
         const float* __restrict__ ct = P.ctab + (size_t)(P.q0 + qq) * (G::SMAX + 1);
         // stage this CTA's part of the real field (coalesced), then R2C along the last axis
-        if (active) staged_copy<N, CL, false>(stg, const_cast<float*>(src) + 2 * lt, 2 * NT, lt);
+        if (active) staged_copy<N, CL, false>(stg, const_cast<float*>(src) + 4 * lt, 4 * NT, lt);
         __syncthreads();
         const int p0 = lt / H, i1 = lt % H;
-        if (active) {
-            const float2* a2 = reinterpret_cast<const float2*>(stg + (p0 * N + i1) * RR);
-            const float2* b2 = reinterpret_cast<const float2*>(stg + (p0 * N + i1 + H) * RR);
-#pragma unroll
-            for (int c = 0; c < N / 2; ++c) {
-                const float2 a = a2[c], b = b2[c];
-                x[2 * c] = make_float2(a.x, b.x);
-                x[2 * c + 1] = make_float2(a.y, b.y);
-            }
-        }
+        if (active) load_two_rows_smem<N>(stg + (p0 * N + i1) * RR, stg + (p0 * N + i1 + H) * RR, x);
         __syncthreads();                          // staged rows consumed before the planes are written
         if (active) {
             fft_reg<N, false>(x);
-            float2* r1 = smem + p0 * PS + i1 * RS;
-            float2* r2 = smem + p0 * PS + (i1 + H) * RS;
+            // half spectra of the two rows: R1[k] = (X[k] + conj X[N-k]) / 2,
+            // R2[k] = (X[k] - conj X[N-k]) / 2i, entries k and k + 1 stored together
+            float4* r1 = reinterpret_cast<float4*>(smem + p0 * PS + i1 * RS);
+            float4* r2 = reinterpret_cast<float4*>(smem + p0 * PS + (i1 + H) * RS);
 #pragma unroll
-            for (int k = 0; k <= H; ++k) {
-                const float2 z = x[k], zc = x[(N - k) % N];
-                r1[k] = make_float2(0.5f * (z.x + zc.x), 0.5f * (z.y - zc.y));
-                r2[k] = make_float2(0.5f * (z.y + zc.y), -0.5f * (z.x - zc.x));
+            for (int c = 0; c < H / 2; ++c) {
+                const int k = 2 * c;
+                const float2 z = x[k], zc = x[(N - k) % N], w = x[k + 1], wc = x[N - k - 1];
+                r1[c] = make_float4(0.5f * (z.x + zc.x), 0.5f * (z.y - zc.y), 0.5f * (w.x + wc.x), 0.5f * (w.y - wc.y));
+                r2[c] = make_float4(0.5f * (z.y + zc.y), -0.5f * (z.x - zc.x), 0.5f * (w.y + wc.y), -0.5f * (w.x - wc.x));
             }
+            const float2 z = x[H];
+            reinterpret_cast<float2*>(r1)[H] = make_float2(z.x, 0.f);
+            reinterpret_cast<float2*>(r2)[H] = make_float2(z.y, 0.f);
         }
         __syncthreads();
         // axis 1 on this CTA's planes
@@ -670,34 +697,17 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(ClusterGeo<N, CL>::
     __syncthreads();
     const int p0 = lt / H, i1 = lt % H;
     if (active) {
-        const float2* r1 = smem + p0 * PS + i1 * RS;
-        const float2* r2 = smem + p0 * PS + (i1 + H) * RS;
-        x[0] = make_float2(r1[0].x, r2[0].x);
-        x[H] = make_float2(r1[H].x, r2[H].x);
-#pragma unroll
-        for (int k = 1; k < H; ++k) {
-            const float2 a = r1[k], b = r2[k];
-            x[k] = make_float2(a.x - b.y, a.y + b.x);
-            x[N - k] = make_float2(a.x + b.y, b.x - a.y);
-        }
+        c2r_pack_rows<N, true>(smem + p0 * PS + i1 * RS, smem + p0 * PS + (i1 + H) * RS, x);
         fft_reg<N, true>(x);
     }
     __syncthreads();
     float* stg = reinterpret_cast<float*>(smem);  // gain rows of this CTA's part
-    if (active) {
-        float2* o1 = reinterpret_cast<float2*>(stg + (p0 * N + i1) * RR);
-        float2* o2 = reinterpret_cast<float2*>(stg + (p0 * N + i1 + H) * RR);
-#pragma unroll
-        for (int c = 0; c < N / 2; ++c) {
-            o1[c] = make_float2(x[2 * c].x, x[2 * c + 1].x);
-            o2[c] = make_float2(x[2 * c].y, x[2 * c + 1].y);
-        }
-    }
+    if (active) store_two_rows<N>(stg + (p0 * N + i1) * RR, stg + (p0 * N + i1 + H) * RR, x);
     __syncthreads();
     if (!active) return;
-    constexpr int ITER = CG::PART_N / (2 * NT);
-    constexpr int S_STEP = (2 * NT / N) * RR;
-    const int L0 = 2 * lt;
+    constexpr int ITER = CG::PART_N / (4 * NT);
+    constexpr int S_STEP = (4 * NT / N) * RR;
+    const int L0 = 4 * lt;
     const float* sp = stg + (L0 / N) * RR + (L0 % N);
     const size_t v0 = (size_t)rank * CG::PART_N + L0;
     for (int o = P.out_start[u]; o < P.out_start[u + 1]; ++o) {
@@ -707,10 +717,11 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(ClusterGeo<N, CL>::
         float* q = P.Q + (size_t)e.x * G::n + v0;
 #pragma unroll 4
         for (int it = 0; it < ITER; ++it) {
-            const float2 gsum = *reinterpret_cast<const float2*>(sp + it * S_STEP);
-            const float2 a = __ldg(reinterpret_cast<const float2*>(fl + (size_t)it * 2 * NT));
-            const float2 b = __ldg(reinterpret_cast<const float2*>(lj + (size_t)it * 2 * NT));
-            *reinterpret_cast<float2*>(q + (size_t)it * 2 * NT) = make_float2(fmaf(-a.x, b.x, gsum.x), fmaf(-a.y, b.y, gsum.y));
+            const float4 g4 = *reinterpret_cast<const float4*>(sp + it * S_STEP);
+            const float4 a = __ldg(reinterpret_cast<const float4*>(fl + (size_t)it * 4 * NT));
+            const float4 b = __ldg(reinterpret_cast<const float4*>(lj + (size_t)it * 4 * NT));
+            *reinterpret_cast<float4*>(q + (size_t)it * 4 * NT) =
+                make_float4(fmaf(-a.x, b.x, g4.x), fmaf(-a.y, b.y, g4.y), fmaf(-a.z, b.z, g4.z), fmaf(-a.w, b.w, g4.w));
         }
     }
 }
@@ -890,9 +901,12 @@ __global__ void __launch_bounds__(VC, 1) k_contract_pipe(ConParamsT<R> C) {
     const Tile& tl = C.tiles[blockIdx.y];
     const int nch = C.n / VC;                                     // VC is the layout's voxel chunk
     const size_t blk = (size_t)C.n_c * VC;                        // one (slot, chunk) block
-    // block of (slot = qq*M + p, chunk = blockIdx.x)
+    // radial node of the block: the last node first, since its fields were the
+    // last ones written and are the likeliest to still be in L2
+    const int qz = (int)(gridDim.z - 1 - blockIdx.z);
+    // block of (slot = qz*M + p, chunk = blockIdx.x)
     auto block_of = [&](int p) -> const R* {
-        return C.A + (((size_t)blockIdx.z * C.M + p) * nch + blockIdx.x) * blk;
+        return C.A + (((size_t)qz * C.M + p) * nch + blockIdx.x) * blk;
     };
     const int npairs = C.n_dpair;
     if (t == 0) {
@@ -1003,7 +1017,7 @@ __global__ void __launch_bounds__(VC, 1) k_contract_pipe(ConParamsT<R> C) {
         }
     }
     const size_t n = (size_t)C.n;
-    R* __restrict__ Pq = C.P + (size_t)blockIdx.z * C.U * n + (size_t)blockIdx.x * VC + t;
+    R* __restrict__ Pq = C.P + (size_t)qz * C.U * n + (size_t)blockIdx.x * VC + t;
     const int cnt = (KIND == TILE_LIST) ? tl.count : NACC;
 #pragma unroll
     for (int i = 0; i < NACC; ++i)
