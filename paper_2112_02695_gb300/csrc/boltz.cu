@@ -589,14 +589,23 @@ cudaError_t set_smem(K kernel, size_t bytes) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// Clusters of more than 8 CTAs (the portable limit) must be allowed per kernel.
+template <typename K>
+cudaError_t allow_big_cluster(K kernel) {
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+}
+
 template <int N, int D>
 struct Launch {
     using G = Geo<N, D>;
     // 3D fields of 32^3, 48^3 and 64^3 run on clusters of CL CTAs (2, 4 and 8 CTAs
-    // per field); the synthesis uses clusters of CLS CTAs (4 for 32^3: smaller
-    // CTAs, six per SM, overlap the transform phases of more fields and measured
-    // 5% faster per step than two); smaller fields run FPC to a CTA
-    static constexpr int CLS = (D == 3 && N == 32) ? 4 : ((D == 3 && N == 64) ? 8 : ((D == 3 && N == 48) ? 4 : 0));
+    // per field); the synthesis uses clusters of CLS CTAs: 4 for 32^3 (smaller
+    // CTAs, six per SM, overlap the transform phases of more fields: 5% faster
+    // per step than two) and 16 for 64^3 (a cluster must fit in one GPC: 8-CTA
+    // clusters of one 141 KB CTA per SM left a sixth of the SMs idle, 16-CTA
+    // clusters of 71 KB CTAs run three per SM: 29% faster per step); smaller
+    // fields run FPC to a CTA
+    static constexpr int CLS = (D == 3 && N == 32) ? 4 : ((D == 3 && N == 64) ? 16 : ((D == 3 && N == 48) ? 4 : 0));
     static constexpr int CL = (D == 3 && N == 32) ? 2 : ((D == 3 && N == 64) ? 8 : ((D == 3 && N == 48) ? 4 : 0));
     static constexpr int FPC = (D == 3) ? (N == 24 ? 1 : (N == 16 ? 4 : 8))
                                         : (N == 64 ? 4 : ((N == 32 || N == 48) ? 16 : (N == 8 ? 64 : 32)));
@@ -620,6 +629,11 @@ struct Launch {
             if ((e = set_smem(k_synth_cl<N, CLS, SYN_SHIFT>, CGS::SMEM)) != cudaSuccess) return e;
             if ((e = set_smem(k_synth_cl<N, CLS, SYN_PREP>, CGS::SMEM)) != cudaSuccess) return e;
             if ((e = set_smem(k_synth_cl<N, CLS, SYN_MULT>, CGS::SMEM)) != cudaSuccess) return e;
+            if constexpr (CLS > 8) {
+                if ((e = allow_big_cluster(k_synth_cl<N, CLS, SYN_SHIFT>)) != cudaSuccess) return e;
+                if ((e = allow_big_cluster(k_synth_cl<N, CLS, SYN_PREP>)) != cudaSuccess) return e;
+                if ((e = allow_big_cluster(k_synth_cl<N, CLS, SYN_MULT>)) != cudaSuccess) return e;
+            }
             if ((e = set_smem(k_analysis_cl<N, CL, ANA_SPECTRUM>, CG::SMEM)) != cudaSuccess) return e;
             if ((e = set_smem(k_analysis_cl<N, CL, ANA_ACCUM>, CG::SMEM)) != cudaSuccess) return e;
             return set_smem(k_output_cl<N, CL>, CG::SMEM);
