@@ -598,15 +598,19 @@ cudaError_t allow_big_cluster(K kernel) {
 template <int N, int D>
 struct Launch {
     using G = Geo<N, D>;
-    // 3D fields of 32^3, 48^3 and 64^3 run on clusters of CL CTAs (2, 4 and 8 CTAs
-    // per field); the synthesis uses clusters of CLS CTAs: 4 for 32^3 (smaller
-    // CTAs, six per SM, overlap the transform phases of more fields: 5% faster
-    // per step than two) and 16 for 64^3 (a cluster must fit in one GPC: 8-CTA
-    // clusters of one 141 KB CTA per SM left a sixth of the SMs idle, 16-CTA
-    // clusters of 71 KB CTAs run three per SM: 29% faster per step); smaller
-    // fields run FPC to a CTA
-    static constexpr int CLS = (D == 3 && N == 32) ? 4 : ((D == 3 && N == 64) ? 16 : ((D == 3 && N == 48) ? 4 : 0));
-    static constexpr int CL = (D == 3 && N == 32) ? 2 : ((D == 3 && N == 64) ? 8 : ((D == 3 && N == 48) ? 4 : 0));
+    // 3D fields of 32^3, 48^3 and 64^3 run on clusters of CL CTAs (2, 8 and 16
+    // CTAs per field); the synthesis uses clusters of CLS CTAs (4, 8, 16).  A
+    // cluster must fit in one GPC (19 SMs), so a cluster shape wastes the SMs
+    // left over after whole clusters: 8-CTA clusters of one 141 KB CTA per SM
+    // (the former 64^3 shape) ran only 15 clusters at a time, a sixth of the
+    // SMs idle, while 16-CTA clusters of 71 KB CTAs (three per SM) use all but
+    // 9 of a GPC's 57 slots and ran the C4 step 29% faster; 48^3 on 8 CTAs of
+    // 60 KB (three per SM) is 4% faster on the mixed batch than 4 CTAs of
+    // 118 KB.  For 32^3, 4-CTA synthesis clusters (six per SM) overlap the
+    // transform phases of more fields and were 5% faster per step than pairs.
+    // Smaller fields run FPC to a CTA
+    static constexpr int CLS = (D == 3 && N == 32) ? 4 : ((D == 3 && N == 64) ? 16 : ((D == 3 && N == 48) ? 8 : 0));
+    static constexpr int CL = (D == 3 && N == 32) ? 2 : ((D == 3 && N == 64) ? 16 : ((D == 3 && N == 48) ? 8 : 0));
     static constexpr int FPC = (D == 3) ? (N == 24 ? 1 : (N == 16 ? 4 : 8))
                                         : (N == 64 ? 4 : ((N == 32 || N == 48) ? 16 : (N == 8 ? 64 : 32)));
     static constexpr int BLOCK = G::TPF * FPC;
@@ -636,6 +640,11 @@ struct Launch {
             }
             if ((e = set_smem(k_analysis_cl<N, CL, ANA_SPECTRUM>, CG::SMEM)) != cudaSuccess) return e;
             if ((e = set_smem(k_analysis_cl<N, CL, ANA_ACCUM>, CG::SMEM)) != cudaSuccess) return e;
+            if constexpr (CL > 8) {
+                if ((e = allow_big_cluster(k_analysis_cl<N, CL, ANA_SPECTRUM>)) != cudaSuccess) return e;
+                if ((e = allow_big_cluster(k_analysis_cl<N, CL, ANA_ACCUM>)) != cudaSuccess) return e;
+                if ((e = allow_big_cluster(k_output_cl<N, CL>)) != cudaSuccess) return e;
+            }
             return set_smem(k_output_cl<N, CL>, CG::SMEM);
         } else {
             if ((e = set_smem(k_synth<N, D, FPC, SYN_SHIFT>, SMEM)) != cudaSuccess) return e;

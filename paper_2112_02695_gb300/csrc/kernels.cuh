@@ -378,7 +378,8 @@ using OutParams = OutParamsT<float>;
 // spread over a cluster of CL CTAs: CTA r holds the PP = N/CL planes i0 in
 // [r PP, r PP + PP) in shared memory (for 32^3 the synthesis runs on four
 // CTAs of 37 KB, six per SM, the analysis and output on two CTAs of 73 KB,
-// three per SM; for 64^3 eight CTAs of 138 KB).  The transform along axis 0
+// three per SM; 48^3 on eight CTAs of 60 KB; 64^3 on sixteen CTAs of 71 KB,
+// a cluster size beyond the portable 8).  The transform along axis 0
 // is the only one that crosses planes; it reads or writes the other CTAs'
 // planes through distributed shared memory, between cluster barriers.  A
 // CTA's part of a real field is one contiguous block of global memory; it is
