@@ -2066,9 +2066,17 @@ boltz_status boltz_lowrank_step_host(boltz_grid g, const float* V_host, int r, f
     BZ_CUDA(cudaMemcpyAsync(dV, V_host, size_t(r) * nb, cudaMemcpyHostToDevice, st));
     if ((s = boltz_spectrum(g, dV, r, dS, stream)) != BOLTZ_OK) return s;
     if ((s = run_batched(g, dS, r, pj.data(), pl.data(), r2, dQ, BOLTZ_FORM_BATCHED, st)) != BOLTZ_OK) return s;
+    // Q goes back to the host on the side stream while the projection (which
+    // only reads Q) runs on the caller's stream
+    if (Q_host) {
+        BZ_CUDA(cudaEventRecord(g->ev_fork, st));
+        BZ_CUDA(cudaStreamWaitEvent(g->side, g->ev_fork, 0));
+        BZ_CUDA(cudaMemcpyAsync(Q_host, dQ, size_t(r2) * nb, cudaMemcpyDeviceToHost, g->side));
+        BZ_CUDA(cudaEventRecord(g->ev_join, g->side));
+    }
     if ((s = run_project(g, dV, r, dQ, dT, dP, st)) != BOLTZ_OK) return s;
-    if (Q_host) BZ_CUDA(cudaMemcpyAsync(Q_host, dQ, size_t(r2) * nb, cudaMemcpyDeviceToHost, st));
     BZ_CUDA(cudaMemcpyAsync(T_host, dT, size_t(r) * r2 * 4, cudaMemcpyDeviceToHost, st));
+    if (Q_host) BZ_CUDA(cudaStreamWaitEvent(st, g->ev_join, 0));
     BZ_CUDA(cudaStreamSynchronize(st));
     return BOLTZ_OK;
 }
