@@ -14,5 +14,7 @@ Modules:
   mott_smith  the strong-shock closure alpha, beta of Sec. 4.2.
   carleman    the Carleman-form fast spectral operator for gamma = d - 2
               (the Mouhot-Pareschi algorithm the paper's experiments use).
+  shock       the 1D normal shock end to end: full-tensor upwind scheme and
+              the adaptive low-rank K-S-L scheme with its boundary treatment.
 """
-from . import quadrature, collision, lowrank, mott_smith, carleman  # noqa: F401
+from . import quadrature, collision, lowrank, mott_smith, carleman, shock  # noqa: F401
