@@ -498,6 +498,47 @@ boltz_status boltz_svd_truncate_f64(const double* S, int r, double drop_tol, dou
 boltz_status boltz_basis_rotate_f64(const double* X, int r, int n, const double* U, int r_new,
                                     double* X_out, void* stream);
 
+/*
+ * 1D normal shock solved end to end (paper Sec. 4 problem; Sec. 2.3 upwind
+ * transport and projected inflow boundary; Sec. 2.4 fully discrete K-S-L
+ * scheme; Sec. 3 adding and dropping basis).  x in [-L_x, L_x] with n_x
+ * cells, the velocity grid and collision operator of `g` (form as in
+ * boltz_collide_batched), inflow f = f_L for v_1 > 0 at the left end and
+ * f = f_R for v_1 < 0 at the right end.  All state is FP64 on the device;
+ * the collision terms come from the FP32 collision batch.
+ *   boltz_shock_create   f_L, f_R HOST float64 [N^d] (values on the grid);
+ *                        r_max in 3..64 bounds the rank after adding the
+ *                        boundary basis (r + 2 <= r_max).  Allocates the
+ *                        solver's device workspace once.
+ *   boltz_shock_full_step  n_steps forward-Euler steps of the full-tensor
+ *                        upwind scheme: f DEVICE float64 [n_x][N^d], in place.
+ *   boltz_shock_lowrank_step  one adaptive low-rank step: X DEVICE float64
+ *                        [r_max][n_x], S DEVICE float64 [r][r] (packed, room
+ *                        for r_max^2), V DEVICE float64 [r_max][N^d], *r (HOST)
+ *                        the rank in and out; f = sum_ij X_i S_ij V_j with
+ *                        dx sum X_i X_k = delta, dv^d sum V_j V_l = delta.
+ *                        Adds the boundary Maxwellians to V (Gram-Schmidt,
+ *                        twice; a vector keeping under 1e-10 of its norm is
+ *                        already in span(V) and is not added), K-, S- and
+ *                        L-steps with FP64 Cholesky-QR2, then keeps the
+ *                        singular values of S >= drop_tol.  Synchronises
+ *                        `stream` (the new rank is read back).
+ *   boltz_shock_reconstruct  f DEVICE float64 [n_x][N^d] = X^T S V.
+ * Errors: BOLTZ_EINVAL (sizes, r + 2 > r_max or > n_x, non-finite dt),
+ * BOLTZ_ENONFINITE (a QR met linearly dependent rows; the factors are then
+ * left unchanged), BOLTZ_ENOMEM,
+ * BOLTZ_ECUDA.
+ */
+typedef struct boltz_shock_s* boltz_shock;
+boltz_status boltz_shock_create(boltz_grid g, int n_x, double L_x, const double* f_L, const double* f_R,
+                                int r_max, int form, boltz_shock* out);
+boltz_status boltz_shock_destroy(boltz_shock s);
+boltz_status boltz_shock_full_step(boltz_shock s, double* f, int n_steps, double dt, void* stream);
+boltz_status boltz_shock_lowrank_step(boltz_shock s, double* X, double* S, double* V, int* r, double dt,
+                                      double drop_tol, void* stream);
+boltz_status boltz_shock_reconstruct(boltz_shock s, const double* X, const double* S, const double* V, int r,
+                                     double* f, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

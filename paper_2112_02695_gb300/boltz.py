@@ -37,6 +37,8 @@ EXPORTED = (
     "boltz_autotune", "boltz_spectrum_f64", "boltz_collide_batched_f64", "boltz_project_f64",
     "boltz_kstep_collision", "boltz_lstep_collision", "boltz_qr_f64_workspace", "boltz_qr_f64",
     "boltz_svd_truncate_f64", "boltz_basis_rotate_f64", "boltz_lowrank_coupling", "boltz_mott_smith",
+    "boltz_shock_create", "boltz_shock_destroy", "boltz_shock_full_step", "boltz_shock_lowrank_step",
+    "boltz_shock_reconstruct",
 )
 
 KERNEL_CLASSES = ("spectrum", "prep", "shift", "contract", "radial", "output", "project")
@@ -108,6 +110,13 @@ def _load() -> ctypes.CDLL:
         "boltz_mott_smith": ([vp, vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                               ctypes.c_double, vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                               vp], ctypes.c_int),
+        "boltz_shock_create": ([vp, ctypes.c_int, ctypes.c_double, vp, vp, ctypes.c_int, ctypes.c_int,
+                                ctypes.POINTER(vp)], ctypes.c_int),
+        "boltz_shock_destroy": ([vp], ctypes.c_int),
+        "boltz_shock_full_step": ([vp, vp, ctypes.c_int, ctypes.c_double, vp], ctypes.c_int),
+        "boltz_shock_lowrank_step": ([vp, vp, vp, vp, ctypes.POINTER(ctypes.c_int), ctypes.c_double,
+                                      ctypes.c_double, vp], ctypes.c_int),
+        "boltz_shock_reconstruct": ([vp, vp, vp, vp, ctypes.c_int, vp, vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -556,3 +565,60 @@ def boltz_mott_smith(grid: Grid, spectra, rho_L: float, u_L: float, T_L: float, 
                                  float(T_L), float(T_R), float(R_gas), _dev_ptr(Q_scratch, "float32", "Q_scratch"),
                                  ctypes.byref(a), ctypes.byref(b), _stream_ptr(stream)), "boltz_mott_smith")
     return a.value, b.value, Q_scratch
+
+
+class Shock:
+    """Owning wrapper of a boltz_shock handle (1D normal shock solver)."""
+
+    def __init__(self, handle, grid, n_x, L_x, r_max):
+        self.handle, self.grid, self.n_x, self.L_x, self.r_max = handle, grid, n_x, L_x, r_max
+
+    def close(self):
+        if self.handle:
+            _lib.boltz_shock_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def boltz_shock_create(grid: Grid, n_x: int, L_x: float, f_L, f_R, r_max: int, form: int = BOLTZ_FORM_BATCHED):
+    """f_L, f_R: host float64 arrays of N^d values (the inflow Maxwellians on the grid)."""
+    import numpy as np
+    fl = np.ascontiguousarray(f_L, dtype=np.float64).reshape(-1)
+    fr = np.ascontiguousarray(f_R, dtype=np.float64).reshape(-1)
+    if fl.size != grid.n or fr.size != grid.n:
+        raise ValueError("f_L and f_R must hold N^d values")
+    h = ctypes.c_void_p()
+    _check(_lib.boltz_shock_create(grid.handle, int(n_x), float(L_x), fl.ctypes.data_as(ctypes.c_void_p),
+                                   fr.ctypes.data_as(ctypes.c_void_p), int(r_max), int(form), ctypes.byref(h)),
+           "boltz_shock_create")
+    return Shock(h, grid, n_x, L_x, r_max)
+
+
+def boltz_shock_full_step(shock: Shock, f, n_steps: int, dt: float, stream=None):
+    """f: device float64 [n_x, N^d], advanced n_steps full-tensor steps in place."""
+    _check(_lib.boltz_shock_full_step(shock.handle, _dev_ptr(f, "float64", "f"), int(n_steps), float(dt),
+                                      _stream_ptr(stream)), "boltz_shock_full_step")
+    return f
+
+
+def boltz_shock_lowrank_step(shock: Shock, X, S, V, r: int, dt: float, drop_tol: float, stream=None) -> int:
+    """One adaptive low-rank step on device float64 factors X [r_max, n_x],
+    S [r_max * r_max] (packed [r][r]), V [r_max, N^d]; returns the new rank."""
+    rr = ctypes.c_int(int(r))
+    _check(_lib.boltz_shock_lowrank_step(shock.handle, _dev_ptr(X, "float64", "X"), _dev_ptr(S, "float64", "S"),
+                                         _dev_ptr(V, "float64", "V"), ctypes.byref(rr), float(dt), float(drop_tol),
+                                         _stream_ptr(stream)), "boltz_shock_lowrank_step")
+    return rr.value
+
+
+def boltz_shock_reconstruct(shock: Shock, X, S, V, r: int, f, stream=None):
+    """f [n_x, N^d] = X^T S V (device float64)."""
+    _check(_lib.boltz_shock_reconstruct(shock.handle, _dev_ptr(X, "float64", "X"), _dev_ptr(S, "float64", "S"),
+                                        _dev_ptr(V, "float64", "V"), int(r), _dev_ptr(f, "float64", "f"),
+                                        _stream_ptr(stream)), "boltz_shock_reconstruct")
+    return f

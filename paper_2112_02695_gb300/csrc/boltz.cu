@@ -22,6 +22,7 @@
 #include "kernels.cuh"
 #include "lowrank.cuh"
 #include "quadrature.hpp"
+#include "shock.cuh"
 #include "split.cuh"
 #include "tc_kernels.cuh"
 #include "wide2d.cuh"
@@ -2438,6 +2439,259 @@ boltz_status boltz_basis_rotate_f64(const double* X, int r, int n, const double*
     if (r <= 16) k_rotate_f64<16><<<grid, kLrThreads, 0, st>>>(X, U, r, r_new, n, X_out);
     else if (r <= 32) k_rotate_f64<32><<<grid, kLrThreads, 0, st>>>(X, U, r, r_new, n, X_out);
     else k_rotate_f64<64><<<grid, kLrThreads, 0, st>>>(X, U, r, r_new, n, X_out);
+    BZ_CUDA(cudaGetLastError());
+    return BOLTZ_OK;
+}
+
+}  // extern "C"
+
+// ==================================================================== 1D normal shock
+
+struct boltz_shock_s {
+    boltz_grid g = nullptr;
+    int n_x = 0, n_v = 0, r_max = 0, rb = 0, form = 0;
+    double dx = 0, wv = 0;
+    char* mem = nullptr;
+    double *fL = nullptr, *fR = nullptr, *v1 = nullptr;
+    // full tensor
+    double* f_next = nullptr;
+    float *fx32 = nullptr, *Qx = nullptr;
+    void* spec_x = nullptr;
+    std::vector<int32_t> pair_x;
+    // low rank
+    double *Vh = nullptr, *K = nullptr, *K1 = nullptr, *X1 = nullptr, *S1 = nullptr, *S2 = nullptr, *L = nullptr,
+           *L1 = nullptr, *Kt = nullptr, *Vn = nullptr, *R = nullptr, *Sn = nullptr, *U = nullptr, *Qm = nullptr,
+           *sig = nullptr, *Xt = nullptr, *Ap = nullptr, *Am = nullptr, *Pl = nullptr, *Pr = nullptr, *bl = nullptr,
+           *br = nullptr, *gL = nullptr, *gR = nullptr, *Bp = nullptr, *Bm = nullptr, *cvec = nullptr,
+           *nrm = nullptr;
+    float *V32 = nullptr, *Q32 = nullptr, *T32 = nullptr, *K32 = nullptr, *C32 = nullptr, *E32 = nullptr,
+          *S32 = nullptr, *D32 = nullptr, *Cs32 = nullptr, *G32 = nullptr;
+    void* spec_v = nullptr;
+    void* qr_ws = nullptr;
+    int* d_int = nullptr;                 // [0] QR info (K), [1] QR info (L), [2] r_keep, [3] SVD info
+};
+
+namespace {
+
+int sh_grid(size_t n) { return (int)std::min<size_t>((n + boltz_dev::kShT - 1) / boltz_dev::kShT, 4096); }
+
+// Upwind boundary values of K (Sec. 2.3): needs the velocity Grams of the current basis.
+void sh_ghosts(boltz_shock s, const double* Kx, int r, cudaStream_t st) {
+    boltz_dev::k_sh_ghosts<<<1, 64, 0, st>>>(Kx, r, s->n_x, s->Pl, s->Pr, s->bl, s->br, s->gL, s->gR);
+}
+
+}  // namespace
+
+extern "C" {
+
+boltz_status boltz_shock_create(boltz_grid g, int n_x, double L_x, const double* f_L, const double* f_R, int r_max,
+                                int form, boltz_shock* out) {
+    if (!g || !out || !f_L || !f_R || n_x < 2 || !(L_x > 0) || !std::isfinite(L_x) || r_max < 3 || r_max > 64 ||
+        !valid_form(form))
+        return BOLTZ_EINVAL;
+    boltz_shock s = new (std::nothrow) boltz_shock_s;
+    if (!s) return BOLTZ_ENOMEM;
+    s->g = g;
+    s->n_x = n_x;
+    s->n_v = g->n;
+    s->r_max = r_max;
+    s->form = form;
+    s->dx = 2.0 * L_x / n_x;
+    s->wv = std::pow(2.0 * g->L / g->N, g->D);
+    const size_t nv = s->n_v, nx = n_x, rm = r_max, half = g->half;
+    size_t qr_bytes = 0;
+    boltz_qr_f64_workspace(r_max, (int)std::max<size_t>(std::max(nx, nv), rm), &qr_bytes);
+    // one allocation, 256-byte aligned pieces
+    std::vector<std::pair<void**, size_t>> parts = {
+        {(void**)&s->fL, nv * 8}, {(void**)&s->fR, nv * 8}, {(void**)&s->v1, nv * 8},
+        {(void**)&s->f_next, nx * nv * 8}, {(void**)&s->fx32, nx * nv * 4}, {(void**)&s->Qx, nx * nv * 4},
+        {(void**)&s->spec_x, nx * half * 8},
+        {(void**)&s->Vh, rm * nv * 8}, {(void**)&s->K, rm * nx * 8}, {(void**)&s->K1, rm * nx * 8},
+        {(void**)&s->X1, rm * nx * 8}, {(void**)&s->S1, rm * rm * 8}, {(void**)&s->S2, rm * rm * 8},
+        {(void**)&s->L, rm * nv * 8}, {(void**)&s->L1, rm * nv * 8}, {(void**)&s->Kt, rm * nx * 8},
+        {(void**)&s->Vn, rm * nv * 8}, {(void**)&s->R, rm * rm * 8}, {(void**)&s->Sn, rm * rm * 8},
+        {(void**)&s->U, rm * rm * 8}, {(void**)&s->Qm, rm * rm * 8}, {(void**)&s->sig, rm * 8},
+        {(void**)&s->Xt, rm * nx * 8}, {(void**)&s->Ap, rm * rm * 8}, {(void**)&s->Am, rm * rm * 8},
+        {(void**)&s->Pl, rm * rm * 8}, {(void**)&s->Pr, rm * rm * 8}, {(void**)&s->bl, rm * 8},
+        {(void**)&s->br, rm * 8}, {(void**)&s->gL, rm * 8}, {(void**)&s->gR, rm * 8},
+        {(void**)&s->Bp, rm * rm * 8}, {(void**)&s->Bm, rm * rm * 8}, {(void**)&s->cvec, rm * 8},
+        {(void**)&s->nrm, 4 * 8},
+        {(void**)&s->V32, rm * nv * 4}, {(void**)&s->Q32, rm * rm * nv * 4}, {(void**)&s->T32, rm * rm * rm * 4},
+        {(void**)&s->K32, rm * nx * 4}, {(void**)&s->C32, rm * nx * 4}, {(void**)&s->E32, rm * rm * rm * 4},
+        {(void**)&s->S32, rm * rm * 4}, {(void**)&s->D32, rm * rm * 4}, {(void**)&s->Cs32, rm * rm * rm * 4},
+        {(void**)&s->G32, rm * nv * 4}, {(void**)&s->spec_v, rm * half * 8}, {&s->qr_ws, qr_bytes},
+        {(void**)&s->d_int, 64}};
+    size_t total = 0;
+    for (auto& pt : parts) total = align_up(total + pt.second, 256);
+    if (cudaMalloc(&s->mem, total) != cudaSuccess) {
+        (void)cudaGetLastError();
+        delete s;
+        return BOLTZ_ENOMEM;
+    }
+    size_t off = 0;
+    for (auto& pt : parts) {
+        *pt.first = s->mem + off;
+        off = align_up(off + pt.second, 256);
+    }
+    // inflow Maxwellians and the v_1 coordinate of every grid point (axis 0 is v_1)
+    std::vector<double> v1(nv);
+    const double dv = 2.0 * g->L / g->N;
+    const size_t inner = nv / g->N;
+    for (size_t k = 0; k < nv; ++k) v1[k] = -g->L + (double)(k / inner) * dv;
+    if (cudaMemcpy(s->fL, f_L, nv * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(s->fR, f_R, nv * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(s->v1, v1.data(), nv * 8, cudaMemcpyHostToDevice) != cudaSuccess) {
+        boltz_shock_destroy(s);
+        return BOLTZ_ECUDA;
+    }
+    // rank of the boundary data F_b = [f_L; f_R] (Sec. 3.1: singular values >= 1e-10 kept),
+    // from its 2 x 2 Gram matrix on the device
+    boltz_dev::k_sh_rowdots<<<1, boltz_dev::kShT>>>(s->fL, (int)nv, s->fL, 1.0, s->cvec);
+    boltz_dev::k_sh_rowdots<<<1, boltz_dev::kShT>>>(s->fL, (int)nv, s->fR, 1.0, s->cvec + 1);
+    boltz_dev::k_sh_rowdots<<<1, boltz_dev::kShT>>>(s->fR, (int)nv, s->fR, 1.0, s->cvec + 2);
+    double gm[3];
+    if (cudaMemcpy(gm, s->cvec, 3 * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        boltz_shock_destroy(s);
+        return BOLTZ_ECUDA;
+    }
+    const double a = gm[0], b = gm[1], d = gm[2];
+    const double mid = 0.5 * (a + d), rad = std::sqrt(0.25 * (a - d) * (a - d) + b * b);
+    s->rb = (std::sqrt(std::max(mid + rad, 0.0)) >= 1e-10) + (std::sqrt(std::max(mid - rad, 0.0)) >= 1e-10);
+    s->pair_x.resize(n_x);
+    for (int p = 0; p < n_x; ++p) s->pair_x[p] = p;
+    *out = s;
+    return BOLTZ_OK;
+}
+
+boltz_status boltz_shock_destroy(boltz_shock s) {
+    if (!s) return BOLTZ_OK;
+    cudaDeviceSynchronize();
+    cudaFree(s->mem);
+    delete s;
+    return BOLTZ_OK;
+}
+
+boltz_status boltz_shock_full_step(boltz_shock s, double* f, int n_steps, double dt, void* stream) {
+    if (!s || !f || n_steps < 0 || !(dt > 0) || !std::isfinite(dt)) return BOLTZ_EINVAL;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const size_t n = (size_t)s->n_x * s->n_v;
+    for (int k = 0; k < n_steps; ++k) {
+        boltz_dev::k_sh_to_f32<<<sh_grid(n), boltz_dev::kShT, 0, st>>>(f, s->fx32, n);
+        boltz_status rs = boltz_spectrum(s->g, s->fx32, s->n_x, s->spec_x, stream);
+        if (rs != BOLTZ_OK) return rs;
+        rs = boltz_collide_batched(s->g, s->spec_x, s->n_x, s->pair_x.data(), s->pair_x.data(), s->n_x, s->Qx,
+                                   s->form, stream);
+        if (rs != BOLTZ_OK) return rs;
+        boltz_dev::k_sh_full<<<sh_grid(n), boltz_dev::kShT, 0, st>>>(f, s->Qx, s->fL, s->fR, s->v1, s->n_x, s->n_v,
+                                                                     dt, s->dx, s->f_next);
+        BZ_CUDA(cudaMemcpyAsync(f, s->f_next, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    }
+    BZ_CUDA(cudaGetLastError());
+    return BOLTZ_OK;
+}
+
+boltz_status boltz_shock_lowrank_step(boltz_shock s, double* X, double* S, double* V, int* r_io, double dt,
+                                      double drop_tol, void* stream) {
+    if (!s || !X || !S || !V || !r_io || !(dt > 0) || !std::isfinite(dt) || !(drop_tol >= 0) ||
+        !std::isfinite(drop_tol))
+        return BOLTZ_EINVAL;
+    const int r = *r_io, nx = s->n_x, nv = s->n_v;
+    if (r < 1 || r + s->rb > s->r_max || r + s->rb > nx) return BOLTZ_EINVAL;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    using namespace boltz_dev;
+    const int T = kShT;
+    boltz_status rs;
+    // 0. add basis (Sec. 3.1): V_hat = [V; f_L, f_R orthonormalised against V by Gram-Schmidt, twice].
+    // A boundary vector that keeps less than 1e-10 of its norm lies in span(V) already and is not
+    // appended (it would carry no weight and make the K-step QR singular).
+    BZ_CUDA(cudaMemcpyAsync(s->Vh, V, (size_t)r * nv * 8, cudaMemcpyDeviceToDevice, st));
+    int rh = r;
+    for (int k = 0; k < s->rb; ++k) {
+        double* b = s->Vh + (size_t)rh * nv;
+        const double* src = k == 0 ? s->fL : s->fR;
+        BZ_CUDA(cudaMemcpyAsync(b, src, (size_t)nv * 8, cudaMemcpyDeviceToDevice, st));
+        k_sh_rowdots<<<1, T, 0, st>>>(src, nv, src, 1.0, s->nrm);
+        for (int pass = 0; pass < 2; ++pass) {
+            k_sh_rowdots<<<rh, T, 0, st>>>(s->Vh, nv, b, s->wv, s->cvec);
+            k_sh_subtract<<<sh_grid(nv), T, 0, st>>>(b, s->Vh, s->cvec, rh, nv);
+        }
+        k_sh_rowdots<<<1, T, 0, st>>>(b, nv, b, 1.0, s->nrm + 1);
+        double hn[2];
+        BZ_CUDA(cudaMemcpyAsync(hn, s->nrm, sizeof(hn), cudaMemcpyDeviceToHost, st));
+        BZ_CUDA(cudaStreamSynchronize(st));
+        if (!(hn[1] > 1e-20 * hn[0])) continue;
+        k_sh_normalize<<<1, T, 0, st>>>(b, nv, s->wv);
+        ++rh;
+    }
+    // K = X^T S on the old rows, zero on the added ones (the added directions carry no weight)
+    k_sh_comb<false><<<sh_grid((size_t)r * nx), T, 0, st>>>(X, r, nx, S, r, r, s->K);
+    if (rh > r) BZ_CUDA(cudaMemsetAsync(s->K + (size_t)r * nx, 0, (size_t)(rh - r) * nx * 8, st));
+    // velocity Grams of V_hat, boundary projections
+    k_sh_vgram<<<dim3(rh, rh + 1), T, 0, st>>>(s->Vh, rh, nv, s->v1, s->fL, s->fR, s->wv, s->Ap, s->Am, s->Pl, s->Pr,
+                                              s->bl, s->br);
+    // collision batch of all ordered pairs of V_hat and its projection T_jmn
+    k_sh_to_f32<<<sh_grid((size_t)rh * nv), T, 0, st>>>(s->Vh, s->V32, (size_t)rh * nv);
+    if ((rs = boltz_spectrum(s->g, s->V32, rh, s->spec_v, stream)) != BOLTZ_OK) return rs;
+    std::vector<int32_t> pm(rh * rh), pn(rh * rh);
+    for (int k = 0; k < rh * rh; ++k) {
+        pm[k] = k / rh;
+        pn[k] = k % rh;
+    }
+    if ((rs = boltz_collide_batched(s->g, s->spec_v, rh, pm.data(), pn.data(), rh * rh, s->Q32, s->form, stream)) !=
+        BOLTZ_OK)
+        return rs;
+    if ((rs = boltz_project(s->g, s->V32, rh, s->Q32, s->T32, stream)) != BOLTZ_OK) return rs;
+    // 1. K-step (Sec. 2.4 K-step): Euler with the upwind transport and the collision term, then QR
+    sh_ghosts(s, s->K, rh, st);
+    k_sh_to_f32<<<sh_grid((size_t)rh * nx), T, 0, st>>>(s->K, s->K32, (size_t)rh * nx);
+    if ((rs = boltz_kstep_collision(s->T32, rh, s->K32, nx, s->C32, stream)) != BOLTZ_OK) return rs;
+    k_sh_kupdate<<<sh_grid((size_t)rh * nx), T, 0, st>>>(s->K, s->C32, s->Ap, s->Am, s->gL, s->gR, rh, nx, dt, s->dx,
+                                                         s->K1);
+    if ((rs = boltz_qr_f64(s->K1, rh, nx, s->dx, s->X1, s->S1, s->qr_ws, s->d_int, stream)) != BOLTZ_OK) return rs;
+    // 2. S-step (Sec. 2.4 S-step): transport through the updated K, collision term with S1
+    sh_ghosts(s, s->K1, rh, st);
+    k_sh_xgram<<<dim3(rh, rh), T, 0, st>>>(s->X1, s->K1, s->gL, s->gR, rh, nx, s->dx, s->Bp, s->Bm);
+    k_sh_transpose<<<sh_grid((size_t)rh * nx), T, 0, st>>>(s->X1, rh, nx, s->Xt);
+    k_sh_triple<<<dim3(rh, rh), 64, 0, st>>>(s->Xt, rh, nx, s->dx, s->E32);
+    k_sh_to_f32<<<1, T, 0, st>>>(s->S1, s->S32, (size_t)rh * rh);
+    if ((rs = boltz_lowrank_coupling(s->E32, s->S32, rh, s->T32, s->Cs32, s->D32, stream)) != BOLTZ_OK) return rs;
+    k_sh_supdate<<<1, 1024, 0, st>>>(s->S1, s->Ap, s->Am, s->Bp, s->Bm, s->D32, rh, dt, s->S2);
+    // 3. L-step (Sec. 2.4 L-step): L = S2 V, transport through K~ = X'^T S2, collision term, then QR
+    k_sh_comb<true><<<sh_grid((size_t)rh * nv), T, 0, st>>>(s->Vh, rh, nv, s->S2, rh, rh, s->L);
+    k_sh_comb<false><<<sh_grid((size_t)rh * nx), T, 0, st>>>(s->X1, rh, nx, s->S2, rh, rh, s->Kt);
+    sh_ghosts(s, s->Kt, rh, st);
+    k_sh_xgram<<<dim3(rh, rh), T, 0, st>>>(s->X1, s->Kt, s->gL, s->gR, rh, nx, s->dx, s->Bp, s->Bm);
+    k_sh_to_f32<<<1, T, 0, st>>>(s->S2, s->S32, (size_t)rh * rh);
+    if ((rs = boltz_lowrank_coupling(s->E32, s->S32, rh, nullptr, s->Cs32, nullptr, stream)) != BOLTZ_OK) return rs;
+    if ((rs = boltz_lstep_collision(s->Q32, rh, s->Cs32, nv, s->G32, stream)) != BOLTZ_OK) return rs;
+    k_sh_lupdate<<<sh_grid((size_t)rh * nv), T, 0, st>>>(s->L, s->Vh, s->v1, s->Bp, s->Bm, s->G32, rh, nv, dt, s->L1);
+    if ((rs = boltz_qr_f64(s->L1, rh, nv, s->wv, s->Vn, s->R, s->qr_ws, s->d_int + 1, stream)) != BOLTZ_OK) return rs;
+    k_sh_transpose<<<1, T, 0, st>>>(s->R, rh, rh, s->Sn);          // L_i = sum_j R_ji V'_j
+    // 4. drop (Sec. 3.2): SVD of S, keep sigma >= drop_tol, rotate the bases
+    if ((rs = boltz_svd_truncate_f64(s->Sn, rh, drop_tol, s->U, s->sig, s->Qm, s->d_int + 2, s->d_int + 3,
+                                     stream)) != BOLTZ_OK)
+        return rs;
+    int hinfo[4] = {0, 0, 0, 0};
+    BZ_CUDA(cudaMemcpyAsync(hinfo, s->d_int, sizeof(hinfo), cudaMemcpyDeviceToHost, st));
+    BZ_CUDA(cudaStreamSynchronize(st));
+    if (hinfo[0] != 0 || hinfo[1] != 0) return BOLTZ_ENONFINITE;       // a QR met linearly dependent rows
+    const int rk = hinfo[2];
+    if (rk < 1) return BOLTZ_ENONFINITE;
+    if ((rs = boltz_basis_rotate_f64(s->X1, rh, nx, s->U, rk, X, stream)) != BOLTZ_OK) return rs;
+    if ((rs = boltz_basis_rotate_f64(s->Vn, rh, nv, s->Qm, rk, V, stream)) != BOLTZ_OK) return rs;
+    k_sh_diag<<<1, T, 0, st>>>(s->sig, rk, S);
+    BZ_CUDA(cudaGetLastError());
+    *r_io = rk;
+    return BOLTZ_OK;
+}
+
+boltz_status boltz_shock_reconstruct(boltz_shock s, const double* X, const double* S, const double* V, int r,
+                                     double* f, void* stream) {
+    if (!s || !X || !S || !V || !f || r < 1 || r > s->r_max) return BOLTZ_EINVAL;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int T = boltz_dev::kShT, nx = s->n_x, nv = s->n_v;
+    boltz_dev::k_sh_comb<true><<<sh_grid((size_t)r * nv), T, 0, st>>>(V, r, nv, S, r, r, s->L);
+    boltz_dev::k_sh_outer<<<sh_grid((size_t)nx * nv), T, 0, st>>>(X, s->L, r, nx, nv, f);
     BZ_CUDA(cudaGetLastError());
     return BOLTZ_OK;
 }

@@ -1,0 +1,285 @@
+// Kernels of the 1D normal-shock solver (paper Sec. 2.3: first-order upwind
+// transport and the projected inflow boundary; Sec. 2.4: the fully discrete
+// K-S-L scheme; Sec. 3: adding and dropping basis).  The factor algebra is
+// FP64; the collision terms come from the FP32 collision batch.
+//
+// Storage: functions of x or v are rows, X [r][n_x], K [r][n_x], V [r][n_v],
+// L [r][n_v]; small matrices are row-major.  Inner products are the midpoint
+// rules <a, b>_x = dx sum_x a b and <a, b>_v = w sum_v a b (w = dv^d).
+// Upwind differences with boundary values g_L, g_R (one per row):
+//   D+ K(x_p) = (K(x_p) - K(x_{p-1})) / dx,  D- K(x_p) = (K(x_{p+1}) - K(x_p)) / dx,
+//   K(x_0) = g_L, K(x_{N+1}) = g_R.
+// Every reduction runs in a fixed order (run-to-run identical results).
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace boltz_dev {
+
+constexpr int kShT = 256;
+
+// Sum of one double per thread over a block of kShT threads, fixed order;
+// the result is valid in thread 0.
+__device__ __forceinline__ double sh_block_sum(double v, double* red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < kShT / 32; ++k) s += red[k];
+    return s;
+}
+
+__global__ void k_sh_to_f32(const double* __restrict__ in, float* __restrict__ out, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        out[i] = (float)in[i];
+}
+
+// Full-tensor forward-Euler upwind step (Sec. 2.3, eq. "scheme:fullupwind"):
+//   g = f - dt/dx (v1+ (f - f_left) + v1- (f_right - f)) + dt Q,
+// ghost cells f_L (left) and f_R (right).
+__global__ void k_sh_full(const double* __restrict__ f, const float* __restrict__ Q, const double* __restrict__ fL,
+                          const double* __restrict__ fR, const double* __restrict__ v1, int n_x, int n_v, double dt,
+                          double dx, double* __restrict__ g) {
+    const size_t total = (size_t)n_x * n_v;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+        const int p = (int)(t / n_v), v = (int)(t % n_v);
+        const double c = f[t];
+        const double l = p > 0 ? f[t - n_v] : fL[v];
+        const double r = p < n_x - 1 ? f[t + n_v] : fR[v];
+        const double a = v1[v], ap = fmax(a, 0.0), am = fmin(a, 0.0);
+        g[t] = c - dt / dx * (ap * (c - l) + am * (r - c)) + dt * (double)Q[t];
+    }
+}
+
+// out_j = sum_i coef(i, j) in_i for j < r_out, coef(i, j) = A[i][j] (A_ROWS false:
+// out = A^T in) or A[j][i] (A_ROWS true: out = A in); A has leading dimension lda.
+template <bool A_ROWS>
+__global__ void k_sh_comb(const double* __restrict__ in, int r_in, int n, const double* __restrict__ A, int lda,
+                          int r_out, double* __restrict__ out) {
+    const size_t total = (size_t)r_out * n;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+        const int j = (int)(t / n), x = (int)(t % n);
+        double acc = 0.0;
+        for (int i = 0; i < r_in; ++i) acc = fma(A_ROWS ? A[(size_t)j * lda + i] : A[(size_t)i * lda + j], in[(size_t)i * n + x], acc);
+        out[t] = acc;
+    }
+}
+
+// Velocity Gram matrices and boundary projections, block (j, l):
+//   l < r:  Ap[j][l] = w sum v1+ V_j V_l,  Am[j][l] = w sum v1- V_j V_l,
+//           Pl[j][l] = w sum 1{v1 <= 0} V_j V_l,  Pr[j][l] = w sum 1{v1 >= 0} V_j V_l
+//   l == r: bl[j] = w sum f_L 1{v1 > 0} V_j,  br[j] = w sum f_R 1{v1 < 0} V_j
+__global__ void __launch_bounds__(kShT) k_sh_vgram(const double* __restrict__ V, int r, int n_v,
+                                                  const double* __restrict__ v1, const double* __restrict__ fL,
+                                                  const double* __restrict__ fR, double w, double* Ap, double* Am,
+                                                  double* Pl, double* Pr, double* bl, double* br) {
+    __shared__ double red[kShT / 32];
+    const int j = blockIdx.x, l = blockIdx.y;
+    const double* Vj = V + (size_t)j * n_v;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    if (l < r) {
+        const double* Vl = V + (size_t)l * n_v;
+        for (int v = threadIdx.x; v < n_v; v += kShT) {
+            const double a = v1[v], p = Vj[v] * Vl[v];
+            s0 = fma(fmax(a, 0.0), p, s0);
+            s1 = fma(fmin(a, 0.0), p, s1);
+            s2 += a <= 0.0 ? p : 0.0;
+            s3 += a >= 0.0 ? p : 0.0;
+        }
+    } else {
+        for (int v = threadIdx.x; v < n_v; v += kShT) {
+            const double a = v1[v];
+            s0 = fma(a > 0.0 ? fL[v] : 0.0, Vj[v], s0);
+            s1 = fma(a < 0.0 ? fR[v] : 0.0, Vj[v], s1);
+        }
+    }
+    s0 = sh_block_sum(s0, red);
+    s1 = sh_block_sum(s1, red);
+    if (l < r) {
+        s2 = sh_block_sum(s2, red);
+        s3 = sh_block_sum(s3, red);
+        if (threadIdx.x == 0) {
+            Ap[j * r + l] = w * s0;
+            Am[j * r + l] = w * s1;
+            Pl[j * r + l] = w * s2;
+            Pr[j * r + l] = w * s3;
+        }
+    } else if (threadIdx.x == 0) {
+        bl[j] = w * s0;
+        br[j] = w * s1;
+    }
+}
+
+// Boundary values of K (Sec. 2.3, eq. "boundary general"; outflow part from
+// the first interior cell): g_L[j] = bl[j] + sum_l K_l(x_1) Pl[l][j],
+// g_R[j] = br[j] + sum_l K_l(x_N) Pr[l][j].  One block, thread j.
+__global__ void k_sh_ghosts(const double* __restrict__ K, int r, int n_x, const double* __restrict__ Pl,
+                            const double* __restrict__ Pr, const double* __restrict__ bl,
+                            const double* __restrict__ br, double* gL, double* gR) {
+    for (int j = threadIdx.x; j < r; j += blockDim.x) {
+        double a = bl[j], b = br[j];
+        for (int l = 0; l < r; ++l) {
+            a = fma(K[(size_t)l * n_x], Pl[l * r + j], a);
+            b = fma(K[(size_t)l * n_x + n_x - 1], Pr[l * r + j], b);
+        }
+        gL[j] = a;
+        gR[j] = b;
+    }
+}
+
+__device__ __forceinline__ double sh_dplus(const double* K, int n_x, const double* gL, int l, int x, double dx) {
+    const double* Kl = K + (size_t)l * n_x;
+    return (Kl[x] - (x > 0 ? Kl[x - 1] : gL[l])) / dx;
+}
+__device__ __forceinline__ double sh_dminus(const double* K, int n_x, const double* gR, int l, int x, double dx) {
+    const double* Kl = K + (size_t)l * n_x;
+    return ((x < n_x - 1 ? Kl[x + 1] : gR[l]) - Kl[x]) / dx;
+}
+
+// K-step Euler update (Sec. 2.4, K-step (b), upwind form of Sec. 2.3):
+//   K1_j(x) = K_j(x) - dt sum_l (Ap[j][l] D+ K_l(x) + Am[j][l] D- K_l(x)) + dt C_j(x)
+__global__ void k_sh_kupdate(const double* __restrict__ K, const float* __restrict__ C, const double* __restrict__ Ap,
+                             const double* __restrict__ Am, const double* __restrict__ gL,
+                             const double* __restrict__ gR, int r, int n_x, double dt, double dx,
+                             double* __restrict__ K1) {
+    const size_t total = (size_t)r * n_x;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+        const int j = (int)(t / n_x), x = (int)(t % n_x);
+        double tr = 0.0;
+        for (int l = 0; l < r; ++l)
+            tr = fma(Ap[j * r + l], sh_dplus(K, n_x, gL, l, x, dx), fma(Am[j * r + l], sh_dminus(K, n_x, gR, l, x, dx), tr));
+        K1[t] = K[t] - dt * tr + dt * (double)C[t];
+    }
+}
+
+// Space Gram matrices of the transport, block (i, l):
+//   Bp[i][l] = dx sum_x X_i(x) D+ K_l(x),  Bm[i][l] = dx sum_x X_i(x) D- K_l(x)
+__global__ void __launch_bounds__(kShT) k_sh_xgram(const double* __restrict__ X, const double* __restrict__ K,
+                                                  const double* __restrict__ gL, const double* __restrict__ gR,
+                                                  int r, int n_x, double dx, double* Bp, double* Bm) {
+    __shared__ double red[kShT / 32];
+    const int i = blockIdx.x, l = blockIdx.y;
+    const double* Xi = X + (size_t)i * n_x;
+    double sp = 0.0, sm = 0.0;
+    for (int x = threadIdx.x; x < n_x; x += kShT) {
+        sp = fma(Xi[x], sh_dplus(K, n_x, gL, l, x, dx), sp);
+        sm = fma(Xi[x], sh_dminus(K, n_x, gR, l, x, dx), sm);
+    }
+    sp = sh_block_sum(sp, red);
+    sm = sh_block_sum(sm, red);
+    if (threadIdx.x == 0) {
+        Bp[i * r + l] = dx * sp;
+        Bm[i * r + l] = dx * sm;
+    }
+}
+
+__global__ void k_sh_transpose(const double* __restrict__ in, int rows, int cols, double* __restrict__ out) {
+    const size_t total = (size_t)rows * cols;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+        const int a = (int)(t / cols), b = (int)(t % cols);
+        out[(size_t)b * rows + a] = in[t];
+    }
+}
+
+// Triple products E[i][m][n] = dx sum_x X_i X_m X_n from Xt [n_x][r]; block
+// (i, m), thread n (FP32 result for the r^4 coupling kernel).
+__global__ void k_sh_triple(const double* __restrict__ Xt, int r, int n_x, double dx, float* __restrict__ E) {
+    const int i = blockIdx.x, m = blockIdx.y;
+    for (int n = threadIdx.x; n < r; n += blockDim.x) {
+        double acc = 0.0;
+        for (int x = 0; x < n_x; ++x) {
+            const double* row = Xt + (size_t)x * r;
+            acc = fma(row[i] * row[m], row[n], acc);
+        }
+        E[((size_t)i * r + m) * r + n] = (float)(dx * acc);
+    }
+}
+
+// S-step Euler update (Sec. 2.4, S-step (a)):
+//   S2[i][j] = S1[i][j] + dt sum_l (Ap[j][l] Bp[i][l] + Am[j][l] Bm[i][l]) - dt D[i][j]
+__global__ void k_sh_supdate(const double* __restrict__ S1, const double* __restrict__ Ap, const double* __restrict__ Am,
+                             const double* __restrict__ Bp, const double* __restrict__ Bm, const float* __restrict__ D,
+                             int r, double dt, double* __restrict__ S2) {
+    for (int t = threadIdx.x; t < r * r; t += blockDim.x) {
+        const int i = t / r, j = t % r;
+        double tr = 0.0;
+        for (int l = 0; l < r; ++l) tr = fma(Ap[j * r + l], Bp[i * r + l], fma(Am[j * r + l], Bm[i * r + l], tr));
+        S2[t] = S1[t] + dt * tr - dt * (double)D[t];
+    }
+}
+
+// L-step Euler update (Sec. 2.4, L-step (b), upwind form of Sec. 2.3):
+//   L1_i(v) = L_i(v) - dt (v1+ sum_l Bp[i][l] V_l(v) + v1- sum_l Bm[i][l] V_l(v)) + dt G_i(v)
+__global__ void k_sh_lupdate(const double* __restrict__ L, const double* __restrict__ V, const double* __restrict__ v1,
+                             const double* __restrict__ Bp, const double* __restrict__ Bm, const float* __restrict__ G,
+                             int r, int n_v, double dt, double* __restrict__ L1) {
+    const size_t total = (size_t)r * n_v;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(t / n_v), v = (int)(t % n_v);
+        double sp = 0.0, sm = 0.0;
+        for (int l = 0; l < r; ++l) {
+            const double Vl = V[(size_t)l * n_v + v];
+            sp = fma(Bp[i * r + l], Vl, sp);
+            sm = fma(Bm[i * r + l], Vl, sm);
+        }
+        const double a = v1[v];
+        L1[t] = L[t] - dt * (fmax(a, 0.0) * sp + fmin(a, 0.0) * sm) + dt * (double)G[t];
+    }
+}
+
+// Gram-Schmidt pieces of the basis augmentation (Sec. 3.1):
+//   c[j] = w sum_v V_j(v) b(v)        (block j)
+__global__ void __launch_bounds__(kShT) k_sh_rowdots(const double* __restrict__ V, int n, const double* __restrict__ b,
+                                                    double w, double* __restrict__ c) {
+    __shared__ double red[kShT / 32];
+    const double* Vj = V + (size_t)blockIdx.x * n;
+    double s = 0.0;
+    for (int v = threadIdx.x; v < n; v += kShT) s = fma(Vj[v], b[v], s);
+    s = sh_block_sum(s, red);
+    if (threadIdx.x == 0) c[blockIdx.x] = w * s;
+}
+
+//   b(v) -= sum_{j < r} c[j] V_j(v)
+__global__ void k_sh_subtract(double* __restrict__ b, const double* __restrict__ V, const double* __restrict__ c, int r,
+                              int n) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        double s = b[v];
+        for (int j = 0; j < r; ++j) s = fma(-c[j], V[(size_t)j * n + v], s);
+        b[v] = s;
+    }
+}
+
+//   b /= sqrt(w sum b^2) (one block; a zero vector stays zero)
+__global__ void __launch_bounds__(kShT) k_sh_normalize(double* __restrict__ b, int n, double w) {
+    __shared__ double red[kShT / 32];
+    __shared__ double scale;
+    double s = 0.0;
+    for (int v = threadIdx.x; v < n; v += kShT) s = fma(b[v], b[v], s);
+    s = sh_block_sum(s, red);
+    if (threadIdx.x == 0) scale = s > 0.0 ? 1.0 / sqrt(w * s) : 0.0;
+    __syncthreads();
+    for (int v = threadIdx.x; v < n; v += kShT) b[v] *= scale;
+}
+
+// S = diag(sigma[:r]) (packed [r][r])
+__global__ void k_sh_diag(const double* __restrict__ sigma, int r, double* __restrict__ S) {
+    for (int t = threadIdx.x; t < r * r; t += blockDim.x) S[t] = (t / r == t % r) ? sigma[t / r] : 0.0;
+}
+
+// f[x][v] = sum_i X_i(x) L_i(v)
+__global__ void k_sh_outer(const double* __restrict__ X, const double* __restrict__ L, int r, int n_x, int n_v,
+                           double* __restrict__ f) {
+    const size_t total = (size_t)n_x * n_v;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(t / n_v), v = (int)(t % n_v);
+        double acc = 0.0;
+        for (int i = 0; i < r; ++i) acc = fma(X[(size_t)i * n_x + x], L[(size_t)i * n_v + v], acc);
+        f[t] = acc;
+    }
+}
+
+}  // namespace boltz_dev

@@ -91,6 +91,13 @@ def test_null_handles_are_rejected(B):
     assert lib.boltz_basis_rotate_f64(None, 4, 10, None, 5, None, None) == B.BOLTZ_EINVAL
     assert lib.boltz_qr_f64_workspace(4, 3, ctypes.byref(z)) == B.BOLTZ_EINVAL      # n < r
     assert lib.boltz_qr_f64_workspace(16, 32768, ctypes.byref(z)) == B.BOLTZ_OK and z.value > 0
+    h = ctypes.c_void_p()
+    assert lib.boltz_shock_create(None, 16, 6.0, None, None, 16, 0, ctypes.byref(h)) == B.BOLTZ_EINVAL
+    assert lib.boltz_shock_destroy(None) == B.BOLTZ_OK
+    assert lib.boltz_shock_full_step(None, None, 1, 0.01, None) == B.BOLTZ_EINVAL
+    r = ctypes.c_int(4)
+    assert lib.boltz_shock_lowrank_step(None, None, None, None, ctypes.byref(r), 0.01, 1e-6, None) == B.BOLTZ_EINVAL
+    assert lib.boltz_shock_reconstruct(None, None, None, None, 4, None, None) == B.BOLTZ_EINVAL
 
 
 @pytest.mark.parametrize("d,M", [(2, 16), (2, 64), (3, 6), (3, 14), (3, 26), (3, 38), (3, 50), (3, 86)])

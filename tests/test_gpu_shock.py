@@ -1,0 +1,153 @@
+"""GPU parity of the 1D normal-shock solver (boltz_shock_*) against
+oracle/shock.py: the full-tensor upwind steps and the adaptive low-rank steps
+(add basis, K-, S-, L-steps, drop), 2D velocity grid 16^2 on [-10, 10]^2,
+Maxwell molecules, 16 cells on [-6, 6], Mach 1.4.
+
+The GPU keeps every factor in FP64; the collision terms come from the FP32
+batch (relative error ~1e-6 of their scale), so the gate is on the change of
+f over the steps: max |f_gpu - f_oracle| <= 1e-5 x max |f_oracle - f_0|
+(full tensor) and 1e-4 x (low rank, whose K-, S- and L-step collision terms
+pass through FP32 couplings as well).  The ranks after every drop must be
+equal; the drop tolerances are chosen a factor >= 3 away from every singular
+value the oracle produces."""
+import numpy as np
+import pytest
+
+from gpu_helpers import require_gpu
+
+pytestmark = pytest.mark.gpu
+N_X, N, L_X, DT = 16, 16, 6.0, 0.005
+
+
+def make(B, mach=1.4, r_max=16, form=0):
+    from oracle import collision as C
+    from oracle import shock as SH
+    vel = C.Problem(N=N, d=2, L=10.0, R=10.0, gamma=0.0, n_rho=6, M=12)
+    sp = SH.ShockProblem(vel=vel, n_x=N_X, L_x=L_X, mach=mach)
+    g = B.boltz_grid_init(N, 2, 10.0, 10.0, 0.0, 6, 12)
+    fL, fR = sp.boundary()
+    return sp, g, B.boltz_shock_create(g, N_X, L_X, fL, fR, r_max, form)
+
+
+def test_full_tensor_steps_match_oracle():
+    import torch
+    from oracle import shock as SH
+    B = require_gpu()
+    sp, g, sh = make(B)
+    try:
+        f0 = sp.initial()
+        f = torch.tensor(f0, dtype=torch.float64, device="cuda")
+        B.boltz_shock_full_step(sh, f, 3, DT)
+        torch.cuda.synchronize()
+        got = f.cpu().numpy()
+    finally:
+        sh.close()
+        g.close()
+    want = f0.copy()
+    for _ in range(3):
+        want = SH.full_step(sp, want, DT)
+    assert np.max(np.abs(got - want)) <= 1e-5 * np.max(np.abs(want - f0))
+
+
+def _lowrank_run(B, drop_tol, steps, r0=4, mach=1.4):
+    import torch
+    from oracle import shock as SH
+    sp, g, sh = make(B, mach=mach)
+    try:
+        f0 = sp.initial()
+        X, S, V = SH.factor(sp, f0, r0)
+        rm = sh.r_max
+        Xd = torch.zeros((rm, N_X), dtype=torch.float64, device="cuda")
+        Vd = torch.zeros((rm, N * N), dtype=torch.float64, device="cuda")
+        Sd = torch.zeros(rm * rm, dtype=torch.float64, device="cuda")
+        Xd[:r0] = torch.tensor(X)
+        Vd[:r0] = torch.tensor(V)
+        Sd[: r0 * r0] = torch.tensor(S.ravel())
+        r = r0
+        fd = torch.empty((N_X, N * N), dtype=torch.float64, device="cuda")
+        out = []
+        for step in range(steps):
+            (X, S, V), parts = SH.lowrank_step(sp, X, S, V, DT, drop_tol, SH.random_xh(N_X, seed=step),
+                                               return_parts=True)
+            sig = parts["sigma"]
+            assert np.min(np.abs(np.log10(sig[sig > 0] / drop_tol))) > np.log10(3.0)
+            r = B.boltz_shock_lowrank_step(sh, Xd, Sd, Vd, r, DT, drop_tol)
+            B.boltz_shock_reconstruct(sh, Xd, Sd, Vd, r, fd)
+            torch.cuda.synchronize()
+            out.append((r, S.shape[0], fd.cpu().numpy(), SH.reconstruct(X, S, V)))
+        Xg = Xd[:r].cpu().numpy()
+        Vg = Vd[:r].cpu().numpy()
+        return sp, f0, out, Xg, Vg
+    finally:
+        sh.close()
+        g.close()
+
+
+def test_lowrank_steps_match_oracle_fixed_rank():
+    """drop_tol between sigma_4 and sigma_5: the two added boundary directions
+    are dropped again every step, the rank stays 4."""
+    B = require_gpu()
+    sp, f0, out, Xg, Vg = _lowrank_run(B, 1e-5, 3)
+    for r_gpu, r_orc, fg, fo in out:
+        assert r_gpu == r_orc == 4
+        assert np.max(np.abs(fg - fo)) <= 1e-4 * np.max(np.abs(fo - f0))
+    # the returned bases are orthonormal under the midpoint rules
+    assert np.allclose(sp.dx * Xg @ Xg.T, np.eye(len(Xg)), atol=1e-11)
+    assert np.allclose(sp.wv * Vg @ Vg.T, np.eye(len(Vg)), atol=1e-11)
+
+
+def test_lowrank_steps_match_oracle_growing_rank():
+    """A small drop_tol keeps the new boundary information: the rank grows by
+    two per step (4 -> 6 -> 8)."""
+    B = require_gpu()
+    sp, f0, out, Xg, Vg = _lowrank_run(B, 1e-7, 2)
+    assert [o[0] for o in out] == [o[1] for o in out] == [6, 8]
+    for r_gpu, r_orc, fg, fo in out:
+        assert np.max(np.abs(fg - fo)) <= 1e-4 * np.max(np.abs(fo - f0))
+
+
+def test_uniform_state_stays_uniform():
+    """Mach 1 (f_L = f_R, uniform initial Maxwellian): the boundary vector lies
+    in span(V) and is not added; the state changes only by dt Q(M, M)."""
+    import torch
+    from oracle import shock as SH
+    B = require_gpu()
+    sp, g, sh = make(B, mach=1.0)
+    try:
+        f0 = sp.initial()
+        X, S, V = SH.factor(sp, f0, 1)
+        Xd = torch.zeros((sh.r_max, N_X), dtype=torch.float64, device="cuda")
+        Vd = torch.zeros((sh.r_max, N * N), dtype=torch.float64, device="cuda")
+        Sd = torch.zeros(sh.r_max ** 2, dtype=torch.float64, device="cuda")
+        Xd[:1] = torch.tensor(X)
+        Vd[:1] = torch.tensor(V)
+        Sd[:1] = float(S[0, 0])
+        r = B.boltz_shock_lowrank_step(sh, Xd, Sd, Vd, 1, 0.01, 1e-6)
+        fd = torch.empty((N_X, N * N), dtype=torch.float64, device="cuda")
+        B.boltz_shock_reconstruct(sh, Xd, Sd, Vd, r, fd)
+        torch.cuda.synchronize()
+        qscale = np.abs(SH.collide_cells(sp, f0[:1])).max()
+        assert r == 1
+        assert np.max(np.abs(fd.cpu().numpy() - f0)) <= 0.01 * qscale * 1.01 + 1e-12
+    finally:
+        sh.close()
+        g.close()
+
+
+def test_rejections():
+    import torch
+    B = require_gpu()
+    sp, g, sh = make(B, r_max=6)
+    try:
+        Xd = torch.zeros((6, N_X), dtype=torch.float64, device="cuda")
+        Vd = torch.zeros((6, N * N), dtype=torch.float64, device="cuda")
+        Sd = torch.zeros(36, dtype=torch.float64, device="cuda")
+        with pytest.raises(B.BoltzError) as ei:
+            B.boltz_shock_lowrank_step(sh, Xd, Sd, Vd, 5, DT, 1e-6)      # 5 + 2 > r_max
+        assert ei.value.status == B.BOLTZ_EINVAL
+        with pytest.raises(B.BoltzError) as ei:
+            B.boltz_shock_full_step(sh, torch.zeros((N_X, N * N), dtype=torch.float64, device="cuda"), 1, -1.0)
+        assert ei.value.status == B.BOLTZ_EINVAL
+    finally:
+        sh.close()
+        g.close()
