@@ -35,7 +35,10 @@ CONFIGS = {
     "c1": (32, 2, 8.0, 8.0, 0.0, 16, 16, "bkw", 1),
     "c4": (64, 3, 10.0, 10.0, 1.0, 32, 86, "pairs", 8),
     "c5": (0, 0, 8.0, 8.0, 0.0, 0, 0, "mixed", 0),
+    "shock": (32, 2, 13.11, 13.11, 0.0, 16, 16, "shock", 1000),
 }
+# 1D normal shock (Sec. 5.2 set-up, Mach 1.4): x in [-30, 30] with 1000 cells
+SHOCK = dict(L_x=30.0, mach=1.4, alpha=0.5, dt=0.004, r0=2, r_max=64, drop_tol=1e-6)
 # mixed batch: (N, d, gamma, M, r); R = L = 8, N_rho = N, bases seeded 2114 + i
 C5_GRIDS = [(24, 3, 0.0, 38, 32), (32, 3, 1.0, 38, 16), (48, 3, 0.0, 86, 8), (64, 3, 1.0, 86, 4),
             (64, 2, 0.0, 16, 16), (128, 2, 1.0, 16, 8)]
@@ -44,9 +47,11 @@ WORKLOAD_NAMES = {
     "c3": "full-tensor-grid batch: 512 normal-shock cells (Mach 3, d=3), 3D 32^3, gamma=1, R=8, N_rho=32 x M=38",
     "c1": "single homogeneous Q(f,f): 2D 32^2 on [-8,8]^2, Maxwell molecules, R=8, N_rho=16 x M=16, BKW t0=0.5",
     "c4": "precision-variant workload, FP32 path: 3D 64^3 on [-10,10]^3, gamma=1, R=10, N_rho=32 x M=86, rank 8 -> 64 pairs + r^3",
+    "shock": "1D normal shock end to end (Mach 1.4, x in [-30,30], 1000 cells; 2D 32^2 on [-13.11,13.11]^2, Maxwell molecules, R=13.11, N_rho=16 x M=16): adaptive low-rank K-S-L steps vs full-tensor upwind steps from the same bimodal initial state, dt=0.004, drop_tol=1e-6",
     "c5": "uneven mixed batch in one captured CUDA graph: 3D N=24 r=32 M=38 g=0 | 3D N=32 r=16 M=38 g=1 | 3D N=48 r=8 M=86 g=0 | 3D N=64 r=4 M=86 g=1 | 2D N=64 r=16 M=16 g=0 | 2D N=128 r=8 M=16 g=1; N_rho=N, R=L=8; spectra + all r^2 pairs + r^3 per grid",
 }
 METRIC = "collision evals/s at 32^3 (batch 256) & % roofline; fast form vs plain FP32"
+SHOCK_METRIC = "1D normal shock time steps/s (adaptive low rank), with the full-tensor rate beside it"
 L2_FLUSH_BYTES = 512 << 20
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "shift_kernel_traffic.json")
@@ -163,12 +168,32 @@ def oracle_sample(cfg_name, r=4):
     return fields, pairs, "the single evaluation"
 
 
+def shock_oracle_step():
+    """The FP64 oracle's adaptive low-rank step of the shock workload from the
+    rank-2 bimodal initial state (a bounded sample: one step, all 1000 cells)."""
+    from oracle import collision as C
+    from oracle import shock as SH
+    N, d, L, R, gamma, n_rho, M, kind, size = CONFIGS["shock"]
+    sp = SH.ShockProblem(vel=C.Problem(N=N, d=d, L=L, R=R, gamma=gamma, n_rho=n_rho, M=M), n_x=size,
+                         L_x=SHOCK["L_x"], mach=SHOCK["mach"], alpha=SHOCK["alpha"])
+    fL, fR = sp.boundary()
+    s = (np.tanh(SHOCK["alpha"] * sp.x) + 1.0) / 2.0
+    f0 = np.outer(1.0 - s, fL) + np.outer(s, fR)
+    X, S, V = SH.factor(sp, f0, SHOCK["r0"])
+    t0 = time.perf_counter()
+    SH.lowrank_step(sp, X, S, V, SHOCK["dt"], SHOCK["drop_tol"], SH.random_xh(size))
+    dt = time.perf_counter() - t0
+    return 1.0 / dt, dt, "one adaptive low-rank step (rank 2 + 2 boundary directions, all 1000 cells)"
+
+
 def time_oracle(cfg_name, r=4, results=None):
     """Times the oracle on the bounded sample; when `results` is a dict it
     receives the sample and the oracle's outputs (full evaluations only)."""
     from oracle import collision as C
     from oracle import quadrature as Qd
     N, d, L, R, gamma, n_rho, M, kind, size = CONFIGS[cfg_name]
+    if kind == "shock":
+        return shock_oracle_step()
     fields, pairs, desc = oracle_sample(cfg_name, r)
     if N >= 64:
         # one evaluation costs ~4 TFLOP of FP64 here: time one pair over the first radial
@@ -317,6 +342,97 @@ def run_mixed(args, world, rank, local_rank):
         g.close()
 
 
+def run_shock(args, world, rank, local_rank):
+    """1D normal shock end to end: W + K adaptive low-rank steps and W + K
+    full-tensor steps from the same bimodal state f0 = (1 - s) f_L + s f_R
+    (exactly rank 2, so the initial factors come from two QRs on the device);
+    the K timed steps of each are bracketed by CUDA events.  Reported: low-rank
+    steps/s (value), full-tensor steps/s, the ranks, and the distance between
+    the two solutions after the run."""
+    import torch
+    from paper_2112_02695_gb300 import boltz as B
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    N, d, L, R, gamma, n_rho, M, kind, n_x = CONFIGS["shock"]
+    cfg = SHOCK
+    g = B.boltz_grid_init(N, d, L, R, gamma, n_rho, M)
+    n_v = N ** d
+    dv = 2.0 * L / N
+    axis = -L + np.arange(N) * dv
+    v1, v2 = np.meshgrid(axis, axis, indexing="ij")
+    g_ = 1.0 + 2.0 / d
+    m2 = cfg["mach"] ** 2
+    rl, ul, tl = 1.0, cfg["mach"] * np.sqrt(g_), 1.0
+    rr = rl * (d + 1.0) * m2 / (m2 + d)
+    ur, tr = ul * (m2 + d) / ((d + 1.0) * m2), tl * ((d + 2.0) * m2 - 1.0) * (m2 + d) / ((d + 1.0) ** 2 * m2)
+    maxw = lambda rho, u, T: (rho / (2 * np.pi * T) * np.exp(-((v1 - u) ** 2 + v2 ** 2) / (2 * T))).reshape(-1)
+    fL, fR = maxw(rl, ul, tl), maxw(rr, ur, tr)
+    sh = B.boltz_shock_create(g, n_x, cfg["L_x"], fL, fR, cfg["r_max"], B.BOLTZ_FORM_BATCHED)
+    dx = 2.0 * cfg["L_x"] / n_x
+    x = -cfg["L_x"] + (np.arange(n_x) + 0.5) * dx
+    s = (np.tanh(cfg["alpha"] * x) + 1.0) / 2.0
+    rm = cfg["r_max"]
+    Xd = torch.zeros((rm, n_x), dtype=torch.float64, device=dev)
+    Vd = torch.zeros((rm, n_v), dtype=torch.float64, device=dev)
+    Sd = torch.zeros(rm * rm, dtype=torch.float64, device=dev)
+    Yx, Rx, ix = B.boltz_qr_f64(torch.tensor(np.stack([1.0 - s, s]), device=dev), dx)
+    Yv, Rv, iv = B.boltz_qr_f64(torch.tensor(np.stack([fL, fR]), device=dev), dv ** d)
+    Xd[:2] = Yx
+    Vd[:2] = Yv
+    Sd[:4] = (Rx @ Rv.T).reshape(-1)                  # f0 = sum_ij X_i (R_x R_v^T)_ij V_j
+    r = 2
+    f_full = torch.empty((n_x, n_v), dtype=torch.float64, device=dev)
+    B.boltz_shock_reconstruct(sh, Xd, Sd, Vd, r, f_full)
+    f0 = f_full.clone()
+    dt, tol = cfg["dt"], cfg["drop_tol"]
+    ranks = []
+    for _ in range(args.warmup):
+        r = B.boltz_shock_lowrank_step(sh, Xd, Sd, Vd, r, dt, tol)
+    B.boltz_shock_full_step(sh, f_full, args.warmup, dt)
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    with ClockSampler(local_rank) as clk:
+        e[0].record()
+        for _ in range(args.steps):
+            r = B.boltz_shock_lowrank_step(sh, Xd, Sd, Vd, r, dt, tol)
+            ranks.append(r)
+        e[1].record()
+        e[2].record()
+        B.boltz_shock_full_step(sh, f_full, args.steps, dt)
+        e[3].record()
+        torch.cuda.synchronize()
+    lr_ms, full_ms = e[0].elapsed_time(e[1]), e[2].elapsed_time(e[3])
+    f_lr = torch.empty_like(f_full)
+    B.boltz_shock_reconstruct(sh, Xd, Sd, Vd, r, f_lr)
+    torch.cuda.synchronize()
+    diff = (f_lr - f_full).norm().item()
+    rel_change = diff / max((f_full - f0).norm().item(), 1e-300)
+    rel = diff / f_full.norm().item()
+    rho_lr = f_lr.sum(dim=1) * dv ** d
+    rho_full = f_full.sum(dim=1) * dv ** d
+    cpu = None
+    if not args.no_cpu_baseline:
+        rate, tsec, desc = shock_oracle_step()
+        cpu = {"value": rate, "unit": "steps/s", "cores": host_cores(), "kind": "oracle", "sample": desc}
+    if rank == 0:
+        print(json.dumps({
+            "metric": SHOCK_METRIC,
+            "value": args.steps / (lr_ms / 1e3), "unit": "steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": lr_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64 factors, f32 collision batch", "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAMES["shock"], "n_x": n_x, "n_v": n_v, "dt": dt, "drop_tol": tol,
+                       "l2": "state larger than L2 is not the point here: steps run back to back"},
+            "full_tensor": {"value": args.steps / (full_ms / 1e3), "unit": "steps/s",
+                            "ms_per_step": full_ms / args.steps},
+            "speedup_lowrank_vs_full": full_ms / lr_ms,
+            "rank": {"first": ranks[0] if ranks else r, "last": r, "max": max(ranks) if ranks else r},
+            "lowrank_vs_full": {"rel_l2_f": rel, "rel_l2_of_the_change": rel_change,
+                                "max_density_diff": (rho_lr - rho_full).abs().max().item()},
+            "cpu_baseline": cpu, "clocks": clk.summary()}))
+    sh.close()
+    g.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -347,22 +463,30 @@ def main():
             rate, dt, desc = time_oracle(args.config, r=3)
             if i >= args.warmup:
                 ev.append(dt)
-        _, pairs_s, desc = oracle_sample(args.config, r=3)
-        value = len(pairs_s) * len(ev) / sum(ev)
+        if kind == "shock":
+            desc = shock_oracle_step()[2]
+            value, unit = len(ev) / sum(ev), "steps/s"
+        else:
+            _, pairs_s, desc = oracle_sample(args.config, r=3)
+            value, unit = len(pairs_s) * len(ev) / sum(ev), "evals/s"
         cores = host_cores()
         print(json.dumps({
-            "impl": "reference", "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": 0,
+            "impl": "reference", "metric": SHOCK_METRIC if kind == "shock" else METRIC, "value": value,
+            "unit": unit, "n_gpus": 0,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(ev) / len(ev),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD_NAMES[args.config], "sample": desc},
-            "cpu_baseline": {"value": value, "unit": "evals/s", "cores": cores, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": unit, "cores": cores, "kind": "oracle",
                              "sample": desc},
-            "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         }))
         return
 
     if kind == "mixed":
         run_mixed(args, world, rank, local_rank)
+        return
+    if kind == "shock":
+        run_shock(args, world, rank, local_rank)
         return
 
     import torch
