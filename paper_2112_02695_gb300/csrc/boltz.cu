@@ -2461,7 +2461,7 @@ struct boltz_shock_s {
     // low rank
     double *Vh = nullptr, *K = nullptr, *K1 = nullptr, *X1 = nullptr, *S1 = nullptr, *S2 = nullptr, *L = nullptr,
            *L1 = nullptr, *Kt = nullptr, *Vn = nullptr, *R = nullptr, *Sn = nullptr, *U = nullptr, *Qm = nullptr,
-           *sig = nullptr, *Xt = nullptr, *Ap = nullptr, *Am = nullptr, *Pl = nullptr, *Pr = nullptr, *bl = nullptr,
+           *sig = nullptr, *Ap = nullptr, *Am = nullptr, *Pl = nullptr, *Pr = nullptr, *bl = nullptr,
            *br = nullptr, *gL = nullptr, *gR = nullptr, *Bp = nullptr, *Bm = nullptr, *cvec = nullptr,
            *nrm = nullptr;
     float *V32 = nullptr, *Q32 = nullptr, *T32 = nullptr, *K32 = nullptr, *C32 = nullptr, *E32 = nullptr,
@@ -2511,7 +2511,7 @@ boltz_status boltz_shock_create(boltz_grid g, int n_x, double L_x, const double*
         {(void**)&s->L, rm * nv * 8}, {(void**)&s->L1, rm * nv * 8}, {(void**)&s->Kt, rm * nx * 8},
         {(void**)&s->Vn, rm * nv * 8}, {(void**)&s->R, rm * rm * 8}, {(void**)&s->Sn, rm * rm * 8},
         {(void**)&s->U, rm * rm * 8}, {(void**)&s->Qm, rm * rm * 8}, {(void**)&s->sig, rm * 8},
-        {(void**)&s->Xt, rm * nx * 8}, {(void**)&s->Ap, rm * rm * 8}, {(void**)&s->Am, rm * rm * 8},
+        {(void**)&s->Ap, rm * rm * 8}, {(void**)&s->Am, rm * rm * 8},
         {(void**)&s->Pl, rm * rm * 8}, {(void**)&s->Pr, rm * rm * 8}, {(void**)&s->bl, rm * 8},
         {(void**)&s->br, rm * 8}, {(void**)&s->gL, rm * 8}, {(void**)&s->gR, rm * 8},
         {(void**)&s->Bp, rm * rm * 8}, {(void**)&s->Bm, rm * rm * 8}, {(void**)&s->cvec, rm * 8},
@@ -2651,8 +2651,7 @@ boltz_status boltz_shock_lowrank_step(boltz_shock s, double* X, double* S, doubl
     // 2. S-step (Sec. 2.4 S-step): transport through the updated K, collision term with S1
     sh_ghosts(s, s->K1, rh, st);
     k_sh_xgram<<<dim3(rh, rh), T, 0, st>>>(s->X1, s->K1, s->gL, s->gR, rh, nx, s->dx, s->Bp, s->Bm);
-    k_sh_transpose<<<sh_grid((size_t)rh * nx), T, 0, st>>>(s->X1, rh, nx, s->Xt);
-    k_sh_triple<<<dim3(rh, rh), 64, 0, st>>>(s->Xt, rh, nx, s->dx, s->E32);
+    k_sh_triple<<<dim3(rh, rh), T, 0, st>>>(s->X1, rh, nx, s->dx, s->E32);
     k_sh_to_f32<<<1, T, 0, st>>>(s->S1, s->S32, (size_t)rh * rh);
     if ((rs = boltz_lowrank_coupling(s->E32, s->S32, rh, s->T32, s->Cs32, s->D32, stream)) != BOLTZ_OK) return rs;
     k_sh_supdate<<<1, 1024, 0, st>>>(s->S1, s->Ap, s->Am, s->Bp, s->Bm, s->D32, rh, dt, s->S2);

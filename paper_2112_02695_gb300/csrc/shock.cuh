@@ -185,17 +185,21 @@ __global__ void k_sh_transpose(const double* __restrict__ in, int rows, int cols
     }
 }
 
-// Triple products E[i][m][n] = dx sum_x X_i X_m X_n from Xt [n_x][r]; block
-// (i, m), thread n (FP32 result for the r^4 coupling kernel).
-__global__ void k_sh_triple(const double* __restrict__ Xt, int r, int n_x, double dx, float* __restrict__ E) {
-    const int i = blockIdx.x, m = blockIdx.y;
-    for (int n = threadIdx.x; n < r; n += blockDim.x) {
+// Triple products E[i][m][n] = dx sum_x X_i X_m X_n (FP32 result for the r^4
+// coupling kernel).  Block (i, m); warp w takes n = w, w + 8, ..., its lanes
+// stride over the cells (coalesced rows) and reduce by shuffles.
+__global__ void __launch_bounds__(kShT) k_sh_triple(const double* __restrict__ X, int r, int n_x, double dx,
+                                                   float* __restrict__ E) {
+    const int i = blockIdx.x, m = blockIdx.y, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const double* Xi = X + (size_t)i * n_x;
+    const double* Xm = X + (size_t)m * n_x;
+    for (int n = warp; n < r; n += kShT / 32) {
+        const double* Xn = X + (size_t)n * n_x;
         double acc = 0.0;
-        for (int x = 0; x < n_x; ++x) {
-            const double* row = Xt + (size_t)x * r;
-            acc = fma(row[i] * row[m], row[n], acc);
-        }
-        E[((size_t)i * r + m) * r + n] = (float)(dx * acc);
+        for (int x = lane; x < n_x; x += 32) acc = fma(Xi[x] * Xm[x], Xn[x], acc);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if (lane == 0) E[((size_t)i * r + m) * r + n] = (float)(dx * acc);
     }
 }
 
