@@ -521,8 +521,13 @@ boltz_status boltz_basis_rotate_f64(const double* X, int r, int n, const double*
  *                        twice; a vector keeping under 1e-10 of its norm is
  *                        already in span(V) and is not added), K-, S- and
  *                        L-steps with FP64 Cholesky-QR2, then keeps the
- *                        singular values of S >= drop_tol.  Synchronises
- *                        `stream` (the new rank is read back).
+ *                        singular values of S >= drop_tol.  *err (HOST,
+ *                        may be NULL) receives ||f^{n+1} - f^n||_{x,v} before
+ *                        the drop, from the K, S and L increments and their
+ *                        cross terms (Sec. 5.1, eqs. "err low rank1-2"): the
+ *                        paper's convergence measure, and its drop_tol =
+ *                        c err rule when passed back.  Synchronises `stream`
+ *                        (the new rank is read back).
  *   boltz_shock_reconstruct  f DEVICE float64 [n_x][N^d] = X^T S V.
  * Errors: BOLTZ_EINVAL (sizes, r + 2 > r_max or > n_x, non-finite dt),
  * BOLTZ_ENONFINITE (a QR met linearly dependent rows; the factors are then
@@ -535,7 +540,7 @@ boltz_status boltz_shock_create(boltz_grid g, int n_x, double L_x, const double*
 boltz_status boltz_shock_destroy(boltz_shock s);
 boltz_status boltz_shock_full_step(boltz_shock s, double* f, int n_steps, double dt, void* stream);
 boltz_status boltz_shock_lowrank_step(boltz_shock s, double* X, double* S, double* V, int* r, double dt,
-                                      double drop_tol, void* stream);
+                                      double drop_tol, double* err, void* stream);
 boltz_status boltz_shock_reconstruct(boltz_shock s, const double* X, const double* S, const double* V, int r,
                                      double* f, void* stream);
 

@@ -45,6 +45,8 @@ rules <a, b>_x = dx sum a b and <a, b>_v = dv^d sum a b.  One step:
                   + dt sum_pq C_ipq Q(V_p, V_q),  C_ipq = sum_n (sum_m E_imn S2_mp) S2_nq;
      QR: L_i = sum_j S'_ij V'_j;
   4. drop (Sec. 3.2): S' = U Sigma Q^T, keep sigma >= drop_tol, rotate X', V'.
+The step also returns err = ||f^{n+1} - f^n||_{x,v} before the drop, from the
+increments dK, dS, dL and the cross terms of Sec. 5.1 (f is not rebuilt).
 Initial factors (Sec. 2.4): truncated SVD of f^0 under the two inner products.
 """
 from __future__ import annotations
@@ -245,13 +247,20 @@ def lowrank_step(sp: ShockProblem, X, S, V, dt: float, drop_tol: float, Xh, retu
     L1 = L - dt * (vp * (Bp @ V) + vm * (Bm @ V)) + dt * LR.lstep_collision(Qv, LR.lstep_coupling(E, S2))
     Vn, R = LR.qr_weighted(L1, sp.wv)
     Sn = R.T                                    # L_i = sum_j Sn_ij V'_j
+    # change of f over the step from the increments (Sec. 5.1, eqs. "err low rank1"
+    # and "err low rank2"): dK, dS, dL and the three cross terms
+    dK, dS, dL = K1 - K, S2 - S1, L1 - L
+    P = sp.dx * X1 @ dK.T                       # P_ij = <dK_j, X'_i>_x
+    Qc = sp.wv * dL @ V.T                       # Qc_ij = <dL_i, V_j>_v
+    err2 = (sp.dx * (dK * dK).sum() + (dS * dS).sum() + sp.wv * (dL * dL).sum()
+            + 2.0 * (P * dS).sum() + 2.0 * (dS * Qc).sum() + 2.0 * (P * Qc).sum())
     # drop
     U, sig, Qm, rk = LR.svd_truncate(Sn, drop_tol)
     Xd = LR.rotate(X1, U, rk)
     Vd = LR.rotate(Vn, Qm, rk)
     out = (Xd, np.diag(sig[:rk]), Vd)
     if return_parts:
-        return out, {"rank_before_drop": r, "sigma": sig}
+        return out, {"rank_before_drop": r, "sigma": sig, "err": math.sqrt(max(err2, 0.0))}
     return out
 
 

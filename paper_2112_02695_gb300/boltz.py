@@ -115,7 +115,7 @@ def _load() -> ctypes.CDLL:
         "boltz_shock_destroy": ([vp], ctypes.c_int),
         "boltz_shock_full_step": ([vp, vp, ctypes.c_int, ctypes.c_double, vp], ctypes.c_int),
         "boltz_shock_lowrank_step": ([vp, vp, vp, vp, ctypes.POINTER(ctypes.c_int), ctypes.c_double,
-                                      ctypes.c_double, vp], ctypes.c_int),
+                                      ctypes.c_double, ctypes.POINTER(ctypes.c_double), vp], ctypes.c_int),
         "boltz_shock_reconstruct": ([vp, vp, vp, vp, ctypes.c_int, vp, vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
@@ -606,14 +606,16 @@ def boltz_shock_full_step(shock: Shock, f, n_steps: int, dt: float, stream=None)
     return f
 
 
-def boltz_shock_lowrank_step(shock: Shock, X, S, V, r: int, dt: float, drop_tol: float, stream=None) -> int:
+def boltz_shock_lowrank_step(shock: Shock, X, S, V, r: int, dt: float, drop_tol: float, stream=None):
     """One adaptive low-rank step on device float64 factors X [r_max, n_x],
-    S [r_max * r_max] (packed [r][r]), V [r_max, N^d]; returns the new rank."""
+    S [r_max * r_max] (packed [r][r]), V [r_max, N^d]; returns (new rank,
+    ||f^{n+1} - f^n|| of the step)."""
     rr = ctypes.c_int(int(r))
+    err = ctypes.c_double()
     _check(_lib.boltz_shock_lowrank_step(shock.handle, _dev_ptr(X, "float64", "X"), _dev_ptr(S, "float64", "S"),
                                          _dev_ptr(V, "float64", "V"), ctypes.byref(rr), float(dt), float(drop_tol),
-                                         _stream_ptr(stream)), "boltz_shock_lowrank_step")
-    return rr.value
+                                         ctypes.byref(err), _stream_ptr(stream)), "boltz_shock_lowrank_step")
+    return rr.value, err.value
 
 
 def boltz_shock_reconstruct(shock: Shock, X, S, V, r: int, f, stream=None):

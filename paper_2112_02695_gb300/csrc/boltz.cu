@@ -2463,7 +2463,7 @@ struct boltz_shock_s {
            *L1 = nullptr, *Kt = nullptr, *Vn = nullptr, *R = nullptr, *Sn = nullptr, *U = nullptr, *Qm = nullptr,
            *sig = nullptr, *Ap = nullptr, *Am = nullptr, *Pl = nullptr, *Pr = nullptr, *bl = nullptr,
            *br = nullptr, *gL = nullptr, *gR = nullptr, *Bp = nullptr, *Bm = nullptr, *cvec = nullptr,
-           *nrm = nullptr;
+           *nrm = nullptr, *Pk = nullptr, *Gv = nullptr, *nk = nullptr, *nl = nullptr, *errd = nullptr;
     float *V32 = nullptr, *Q32 = nullptr, *T32 = nullptr, *K32 = nullptr, *C32 = nullptr, *E32 = nullptr,
           *S32 = nullptr, *D32 = nullptr, *Cs32 = nullptr, *G32 = nullptr;
     void* spec_v = nullptr;
@@ -2515,7 +2515,8 @@ boltz_status boltz_shock_create(boltz_grid g, int n_x, double L_x, const double*
         {(void**)&s->Pl, rm * rm * 8}, {(void**)&s->Pr, rm * rm * 8}, {(void**)&s->bl, rm * 8},
         {(void**)&s->br, rm * 8}, {(void**)&s->gL, rm * 8}, {(void**)&s->gR, rm * 8},
         {(void**)&s->Bp, rm * rm * 8}, {(void**)&s->Bm, rm * rm * 8}, {(void**)&s->cvec, rm * 8},
-        {(void**)&s->nrm, 4 * 8},
+        {(void**)&s->nrm, 4 * 8}, {(void**)&s->Pk, rm * rm * 8}, {(void**)&s->Gv, rm * rm * 8},
+        {(void**)&s->nk, rm * 8}, {(void**)&s->nl, rm * 8}, {(void**)&s->errd, 8},
         {(void**)&s->V32, rm * nv * 4}, {(void**)&s->Q32, rm * rm * nv * 4}, {(void**)&s->T32, rm * rm * rm * 4},
         {(void**)&s->K32, rm * nx * 4}, {(void**)&s->C32, rm * nx * 4}, {(void**)&s->E32, rm * rm * rm * 4},
         {(void**)&s->S32, rm * rm * 4}, {(void**)&s->D32, rm * rm * 4}, {(void**)&s->Cs32, rm * rm * rm * 4},
@@ -2591,7 +2592,7 @@ boltz_status boltz_shock_full_step(boltz_shock s, double* f, int n_steps, double
 }
 
 boltz_status boltz_shock_lowrank_step(boltz_shock s, double* X, double* S, double* V, int* r_io, double dt,
-                                      double drop_tol, void* stream) {
+                                      double drop_tol, double* err_out, void* stream) {
     if (!s || !X || !S || !V || !r_io || !(dt > 0) || !std::isfinite(dt) || !(drop_tol >= 0) ||
         !std::isfinite(drop_tol))
         return BOLTZ_EINVAL;
@@ -2666,13 +2667,22 @@ boltz_status boltz_shock_lowrank_step(boltz_shock s, double* X, double* S, doubl
     k_sh_lupdate<<<sh_grid((size_t)rh * nv), T, 0, st>>>(s->L, s->Vh, s->v1, s->Bp, s->Bm, s->G32, rh, nv, dt, s->L1);
     if ((rs = boltz_qr_f64(s->L1, rh, nv, s->wv, s->Vn, s->R, s->qr_ws, s->d_int + 1, stream)) != BOLTZ_OK) return rs;
     k_sh_transpose<<<1, T, 0, st>>>(s->R, rh, rh, s->Sn);          // L_i = sum_j R_ji V'_j
+    // change of f over the step from the increments (Sec. 5.1), before the drop
+    k_sh_dgram<true><<<rh, T, 0, st>>>(nullptr, s->K1, s->K, rh, nx, s->dx, s->nk);
+    k_sh_dgram<true><<<rh, T, 0, st>>>(nullptr, s->L1, s->L, rh, nv, s->wv, s->nl);
+    k_sh_dgram<false><<<dim3(rh, rh), T, 0, st>>>(s->X1, s->K1, s->K, rh, nx, s->dx, s->Pk);
+    k_sh_dgram<false><<<dim3(rh, rh), T, 0, st>>>(s->Vh, s->L1, s->L, rh, nv, s->wv, s->Gv);
+    k_sh_err<<<1, T, 0, st>>>(s->nk, s->nl, s->Pk, s->Gv, s->S1, s->S2, rh, s->errd);
     // 4. drop (Sec. 3.2): SVD of S, keep sigma >= drop_tol, rotate the bases
     if ((rs = boltz_svd_truncate_f64(s->Sn, rh, drop_tol, s->U, s->sig, s->Qm, s->d_int + 2, s->d_int + 3,
                                      stream)) != BOLTZ_OK)
         return rs;
     int hinfo[4] = {0, 0, 0, 0};
+    double herr = 0.0;
     BZ_CUDA(cudaMemcpyAsync(hinfo, s->d_int, sizeof(hinfo), cudaMemcpyDeviceToHost, st));
+    BZ_CUDA(cudaMemcpyAsync(&herr, s->errd, sizeof(double), cudaMemcpyDeviceToHost, st));
     BZ_CUDA(cudaStreamSynchronize(st));
+    if (err_out) *err_out = herr;
     if (hinfo[0] != 0 || hinfo[1] != 0) return BOLTZ_ENONFINITE;       // a QR met linearly dependent rows
     const int rk = hinfo[2];
     if (rk < 1) return BOLTZ_ENONFINITE;

@@ -269,6 +269,47 @@ __global__ void __launch_bounds__(kShT) k_sh_normalize(double* __restrict__ b, i
     for (int v = threadIdx.x; v < n; v += kShT) b[v] *= scale;
 }
 
+// Gram matrix of increments: G[i][j] = w sum_n A_i(n) (B1_j(n) - B0_j(n)),
+// block (i, j); DIAG: j = i only, G[i] = w sum_n (B1_i - B0_i)^2 (A unused).
+template <bool DIAG>
+__global__ void __launch_bounds__(kShT) k_sh_dgram(const double* __restrict__ A, const double* __restrict__ B1,
+                                                  const double* __restrict__ B0, int rB, int n, double w,
+                                                  double* __restrict__ G) {
+    __shared__ double red[kShT / 32];
+    const int i = blockIdx.x, j = DIAG ? blockIdx.x : blockIdx.y;
+    const double* b1 = B1 + (size_t)j * n;
+    const double* b0 = B0 + (size_t)j * n;
+    const double* a = DIAG ? nullptr : A + (size_t)i * n;
+    double s = 0.0;
+    for (int k = threadIdx.x; k < n; k += kShT) {
+        const double d = b1[k] - b0[k];
+        s = fma(DIAG ? d : a[k], d, s);
+    }
+    s = sh_block_sum(s, red);
+    if (threadIdx.x == 0) G[DIAG ? i : i * rB + j] = w * s;
+}
+
+// Change of f over a low-rank step (Sec. 5.1, eqs. "err low rank1" and "err low rank2"):
+//   err^2 = sum_j |dK_j|^2 + sum_ij dS_ij^2 + sum_i |dL_i|^2
+//           + 2 sum_ij P_ij dS_ij + 2 sum_ij dS_ij Qd_ij + 2 sum_ij P_ij Qd_ij,
+// P_ij = <dK_j, X'_i>_x (P[i][j]), Qd_ij = <dL_i, V_j>_v (stored as Gv[j][i]),
+// dS = S2 - S1, |dK_j|^2 = nk[j], |dL_i|^2 = nl[i].  One block; err >= 0.
+__global__ void __launch_bounds__(kShT) k_sh_err(const double* __restrict__ nk, const double* __restrict__ nl,
+                                                const double* __restrict__ P, const double* __restrict__ Gv,
+                                                const double* __restrict__ S1, const double* __restrict__ S2, int r,
+                                                double* __restrict__ err) {
+    __shared__ double red[kShT / 32];
+    double s = 0.0;
+    for (int t = threadIdx.x; t < r * r; t += kShT) {
+        const int i = t / r, j = t % r;
+        const double ds = S2[t] - S1[t], q = Gv[j * r + i];
+        s += ds * ds + 2.0 * P[t] * ds + 2.0 * ds * q + 2.0 * P[t] * q;
+        if (i == j) s += nk[i] + nl[i];
+    }
+    s = sh_block_sum(s, red);
+    if (threadIdx.x == 0) *err = sqrt(fmax(s, 0.0));
+}
+
 // S = diag(sigma[:r]) (packed [r][r])
 __global__ void k_sh_diag(const double* __restrict__ sigma, int r, double* __restrict__ S) {
     for (int t = threadIdx.x; t < r * r; t += blockDim.x) S[t] = (t / r == t % r) ? sigma[t / r] : 0.0;

@@ -96,7 +96,8 @@ def test_null_handles_are_rejected(B):
     assert lib.boltz_shock_destroy(None) == B.BOLTZ_OK
     assert lib.boltz_shock_full_step(None, None, 1, 0.01, None) == B.BOLTZ_EINVAL
     r = ctypes.c_int(4)
-    assert lib.boltz_shock_lowrank_step(None, None, None, None, ctypes.byref(r), 0.01, 1e-6, None) == B.BOLTZ_EINVAL
+    assert lib.boltz_shock_lowrank_step(None, None, None, None, ctypes.byref(r), 0.01, 1e-6, None,
+                                        None) == B.BOLTZ_EINVAL
     assert lib.boltz_shock_reconstruct(None, None, None, None, 4, None, None) == B.BOLTZ_EINVAL
 
 

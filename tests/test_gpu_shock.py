@@ -1,6 +1,7 @@
 """GPU parity of the 1D normal-shock solver (boltz_shock_*) against
 oracle/shock.py: the full-tensor upwind steps and the adaptive low-rank steps
-(add basis, K-, S-, L-steps, drop), 2D velocity grid 16^2 on [-10, 10]^2,
+(add basis, K-, S-, L-steps, drop, the Sec. 5.1 convergence measure), 2D
+velocity grid 16^2 on [-10, 10]^2,
 Maxwell molecules, 16 cells on [-6, 6], Mach 1.4.
 
 The GPU keeps every factor in FP64; the collision terms come from the FP32
@@ -71,9 +72,11 @@ def _lowrank_run(B, drop_tol, steps, r0=4, mach=1.4):
                                                return_parts=True)
             sig = parts["sigma"]
             assert np.min(np.abs(np.log10(sig[sig > 0] / drop_tol))) > np.log10(3.0)
-            r = B.boltz_shock_lowrank_step(sh, Xd, Sd, Vd, r, DT, drop_tol)
+            r, err = B.boltz_shock_lowrank_step(sh, Xd, Sd, Vd, r, DT, drop_tol)
             B.boltz_shock_reconstruct(sh, Xd, Sd, Vd, r, fd)
             torch.cuda.synchronize()
+            # the step's convergence measure (Sec. 5.1) against the oracle's
+            assert abs(err - parts["err"]) <= 1e-3 * parts["err"], (err, parts["err"])
             out.append((r, S.shape[0], fd.cpu().numpy(), SH.reconstruct(X, S, V)))
         Xg = Xd[:r].cpu().numpy()
         Vg = Vd[:r].cpu().numpy()
@@ -122,7 +125,7 @@ def test_uniform_state_stays_uniform():
         Xd[:1] = torch.tensor(X)
         Vd[:1] = torch.tensor(V)
         Sd[:1] = float(S[0, 0])
-        r = B.boltz_shock_lowrank_step(sh, Xd, Sd, Vd, 1, 0.01, 1e-6)
+        r, _ = B.boltz_shock_lowrank_step(sh, Xd, Sd, Vd, 1, 0.01, 1e-6)
         fd = torch.empty((N_X, N * N), dtype=torch.float64, device="cuda")
         B.boltz_shock_reconstruct(sh, Xd, Sd, Vd, r, fd)
         torch.cuda.synchronize()

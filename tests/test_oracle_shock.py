@@ -100,3 +100,17 @@ def test_lowrank_step_is_consistent_with_the_full_tensor_step():
     for a, b in zip(edge[1:], edge[2:]):
         assert 1.6 < a / b < 2.4, edge
     assert inner[0] <= 1e-5 * np.abs(f0).max()
+
+
+def test_convergence_measure_equals_the_norm_of_the_change():
+    """Sec. 5.1: err from the increments and the three cross terms equals
+    ||f^{n+1} - f^n|| of the rebuilt solutions (before the drop)."""
+    sp = problem(n_x=12, mach=1.4)
+    f0 = sp.initial()
+    X, S, V = SH.factor(sp, f0, 4)
+    (X1, S1, V1), parts = SH.lowrank_step(sp, X, S, V, 0.005, 0.0, SH.random_xh(sp.n_x, seed=5),
+                                          return_parts=True)
+    d = SH.reconstruct(X1, S1, V1) - SH.reconstruct(X, S, V)
+    direct = np.sqrt(sp.dx * sp.wv * (d * d).sum())
+    assert parts["err"] == pytest.approx(direct, rel=1e-10)
+    assert direct > 0
