@@ -2047,12 +2047,14 @@ boltz_status boltz_lowrank_step_host(boltz_grid g, const float* V_host, int r, f
             pj[j * r + l] = j;
             pl[j * r + l] = l;
         }
-    Plan plan;
-    boltz_status s = build_plan(g, r, pj.data(), pl.data(), r2, BOLTZ_FORM_BATCHED, plan);
+    // the grid's cached plan of the all-pairs batch (built on the host only when r changes;
+    // run_batched uploads it again if the workspace below has to grow)
+    boltz_status s = prepare_plan(g, r, pj.data(), pl.data(), r2, BOLTZ_FORM_BATCHED, 0, st);
     if (s != BOLTZ_OK) return s;
+    const size_t plan_total = g->last_plan.total;
     // staging after the batched workspace: V, spectra, Q, T, partial sums
     const size_t nb = size_t(g->n) * 4;
-    size_t off_V = align_up(plan.total, 256);
+    size_t off_V = align_up(plan_total, 256);
     size_t off_S = align_up(off_V + size_t(r) * nb, 256);
     size_t off_Q = align_up(off_S + size_t(r) * g->half * 8, 256);
     size_t off_T = align_up(off_Q + size_t(r2) * nb, 256);
