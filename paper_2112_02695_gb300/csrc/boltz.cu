@@ -616,6 +616,12 @@ struct Launch {
                                         : (N == 64 ? 4 : ((N == 32 || N == 48) ? 16 : (N == 8 ? 64 : 32)));
     static constexpr int BLOCK = G::TPF * FPC;
     static constexpr size_t SMEM = size_t(G::SMEM_F) * FPC * sizeof(float2);
+    // 2D analysis and output kernels: about 64 threads a CTA.  Their launches
+    // carry one field per radial slot (U of them, often under a thousand), so
+    // the synthesis's many fields per CTA would leave most SMs idle.
+    static constexpr int FPC_A = (D == 2) ? (64 / G::TPF > 1 ? 64 / G::TPF : 1) : FPC;
+    static constexpr int BLOCK_A = G::TPF * FPC_A;
+    static constexpr size_t SMEM_A = size_t(G::SMEM_F) * FPC_A * sizeof(float2);
 
     // 2D N = 128: lines split over 4-lane groups
     static constexpr bool WIDE = (D == 2 && N == 128);
@@ -651,9 +657,9 @@ struct Launch {
             if ((e = set_smem(k_synth<N, D, FPC, SYN_SHIFT>, SMEM)) != cudaSuccess) return e;
             if ((e = set_smem(k_synth<N, D, FPC, SYN_PREP>, SMEM)) != cudaSuccess) return e;
             if ((e = set_smem(k_synth<N, D, FPC, SYN_MULT>, SMEM)) != cudaSuccess) return e;
-            if ((e = set_smem(k_analysis<N, D, FPC, ANA_SPECTRUM>, SMEM)) != cudaSuccess) return e;
-            if ((e = set_smem(k_analysis<N, D, FPC, ANA_ACCUM>, SMEM)) != cudaSuccess) return e;
-            return set_smem(k_output<N, D, FPC>, SMEM);
+            if ((e = set_smem(k_analysis<N, D, FPC_A, ANA_SPECTRUM>, SMEM_A)) != cudaSuccess) return e;
+            if ((e = set_smem(k_analysis<N, D, FPC_A, ANA_ACCUM>, SMEM_A)) != cudaSuccess) return e;
+            return set_smem(k_output<N, D, FPC_A>, SMEM_A);
         }
     }
     static void synth(const SynParams& p, int mode, cudaStream_t st) {
@@ -691,11 +697,11 @@ struct Launch {
             else
                 k_analysis_cl<N, CL, ANA_ACCUM><<<CL * p.n_fields, CG::NT, CG::SMEM, st>>>(p);
         } else {
-            const int grid = (p.n_fields + FPC - 1) / FPC;
+            const int grid = (p.n_fields + FPC_A - 1) / FPC_A;
             if (mode == ANA_SPECTRUM)
-                k_analysis<N, D, FPC, ANA_SPECTRUM><<<grid, BLOCK, SMEM, st>>>(p);
+                k_analysis<N, D, FPC_A, ANA_SPECTRUM><<<grid, BLOCK_A, SMEM_A, st>>>(p);
             else
-                k_analysis<N, D, FPC, ANA_ACCUM><<<grid, BLOCK, SMEM, st>>>(p);
+                k_analysis<N, D, FPC_A, ANA_ACCUM><<<grid, BLOCK_A, SMEM_A, st>>>(p);
         }
     }
     static void output(const OutParams& p, cudaStream_t st) {
@@ -705,8 +711,8 @@ struct Launch {
             using CG = ClusterGeo<N, CL>;
             k_output_cl<N, CL><<<CL * p.U, CG::NT, CG::SMEM, st>>>(p);
         } else {
-            const int grid = (p.U + FPC - 1) / FPC;
-            k_output<N, D, FPC><<<grid, BLOCK, SMEM, st>>>(p);
+            const int grid = (p.U + FPC_A - 1) / FPC_A;
+            k_output<N, D, FPC_A><<<grid, BLOCK_A, SMEM_A, st>>>(p);
         }
     }
 };
