@@ -186,9 +186,10 @@ def shock_oracle_step():
     return 1.0 / dt, dt, "one adaptive low-rank step (rank 2 + 2 boundary directions, all 1000 cells)"
 
 
-def time_oracle(cfg_name, r=4, results=None):
-    """Times the oracle on the bounded sample; when `results` is a dict it
-    receives the sample and the oracle's outputs (full evaluations only)."""
+def time_oracle(cfg_name, r=4, results=None, max_items=None):
+    """Times the oracle on the bounded sample (its first `max_items` pairs or
+    cells when given); when `results` is a dict it receives the sample and the
+    oracle's outputs (full evaluations only)."""
     from oracle import collision as C
     from oracle import quadrature as Qd
     N, d, L, R, gamma, n_rho, M, kind, size = CONFIGS[cfg_name]
@@ -205,6 +206,9 @@ def time_oracle(cfg_name, r=4, results=None):
         C.collide_fields(prob, fields.astype(np.float64), pairs)
         dt = (time.perf_counter() - t0) * n_rho
         return 1.0 / dt, dt, f"one pair over 1 of the {n_rho} radial nodes, time x {n_rho}"
+    if max_items is not None and kind in ("pairs", "cells") and len(pairs) > max_items:
+        pairs = pairs[:max_items]
+        desc = f"{len(pairs)} evaluation(s) of: {desc}"
     prob = C.Problem(N=N, d=d, L=L, R=R, gamma=gamma, n_rho=n_rho, M=M)
     t0 = time.perf_counter()
     Q, Qp, Qm = C.collide_fields(prob, fields.astype(np.float64), pairs, return_parts=True)
@@ -461,17 +465,23 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        ev = []
+        # per-step sample sized so that the whole run takes about two minutes:
+        # one evaluation timed first, then as many per step as the budget allows
+        n_items = None
+        if kind in ("pairs", "cells"):
+            _, t_one, _ = time_oracle(args.config, r=3, max_items=1)
+            n_items = int(max(1, min(9, (120.0 / (args.warmup + args.steps)) // max(t_one, 1e-9))))
+        ev, items = [], 1
         for i in range(args.warmup + args.steps):
-            rate, dt, desc = time_oracle(args.config, r=3)
+            rate, dt, desc = time_oracle(args.config, r=3, max_items=n_items)
             if i >= args.warmup:
                 ev.append(dt)
+                items = rate * dt
         if kind == "shock":
             desc = shock_oracle_step()[2]
             value, unit = len(ev) / sum(ev), "steps/s"
         else:
-            _, pairs_s, desc = oracle_sample(args.config, r=3)
-            value, unit = len(pairs_s) * len(ev) / sum(ev), "evals/s"
+            value, unit = round(items) * len(ev) / sum(ev), "evals/s"
         cores = host_cores()
         print(json.dumps({
             "impl": "reference", "metric": SHOCK_METRIC if kind == "shock" else METRIC, "value": value,
