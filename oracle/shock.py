@@ -8,7 +8,8 @@ which it shares no code.
 Problem (paper Sec. 4, eqs. "eqn:normalshock", "eqn:normalshockboundary" and
 the Rankine-Hugoniot solution "relation"; set-up of Sec. 5.2): x in
 [-L_x, L_x] with N_x cells x_p = -L_x + (p - 1/2) dx, dx = 2 L_x / N_x;
-velocity grid and collision operator of oracle.collision (R_gas = 1).
+velocity grid and collision operator of oracle.collision, or the Carleman
+form of oracle.carleman on the same grid (R_gas = 1).
 Upstream (rho, u, T)_L = (1, M sqrt(gamma), 1), gamma = (d+2)/d; downstream
 from "relation".  Initial data: the Maxwellian of rho_0, u_0, T_0, each
 blending L into R as (tanh(alpha x) + 1)/2 (reading of the garbled formula of
@@ -56,6 +57,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
+from . import carleman as CM
 from . import collision as C
 from . import lowrank as LR
 
@@ -74,11 +76,17 @@ def shock_states(mach: float, d: int):
 
 @dataclass
 class ShockProblem:
-    vel: C.Problem          # velocity grid and collision operator
+    vel: C.Problem          # velocity grid and (by default) the separated collision operator
     n_x: int
     L_x: float
     mach: float
     alpha: float = 0.5
+    carleman: CM.CarlemanProblem | None = None   # when set, Q is the Carleman form on the same grid
+
+    def collide(self, fields: np.ndarray, pairs) -> np.ndarray:
+        if self.carleman is not None:
+            return CM.collide_fields(self.carleman, fields, pairs)
+        return C.collide_fields(self.vel, fields, pairs)
 
     @property
     def dx(self) -> float:
@@ -136,7 +144,7 @@ class ShockProblem:
 def collide_cells(sp: ShockProblem, f: np.ndarray) -> np.ndarray:
     """Q(f(x_p), f(x_p)) for every cell, [n_x][n_v]."""
     fields = f.reshape((f.shape[0],) + sp.vel.shape)
-    Q = C.collide_fields(sp.vel, fields, [(p, p) for p in range(f.shape[0])])
+    Q = sp.collide(fields, [(p, p) for p in range(f.shape[0])])
     return Q.reshape(f.shape[0], -1)
 
 
@@ -225,7 +233,7 @@ def lowrank_step(sp: ShockProblem, X, S, V, dt: float, drop_tol: float, Xh, retu
     Am = sp.wv * (V * vm) @ V.T
     fields = V.reshape((r,) + sp.vel.shape)
     pairs = [(m, n) for m in range(r) for n in range(r)]
-    Qv = C.collide_fields(sp.vel, fields, pairs).reshape(r * r, -1)
+    Qv = sp.collide(fields, pairs).reshape(r * r, -1)
     T = C.project(sp.vel, fields, Qv.reshape((r * r,) + sp.vel.shape)).reshape(r, r, r)
     # K-step
     K = S.T @ X                                 # K_j = sum_i X_i S_ij

@@ -21,11 +21,17 @@ N_X, N, L_X, DT = 16, 16, 6.0, 0.005
 
 
 def make(B, mach=1.4, r_max=16, form=0):
+    from oracle import carleman as CM
     from oracle import collision as C
     from oracle import shock as SH
     vel = C.Problem(N=N, d=2, L=10.0, R=10.0, gamma=0.0, n_rho=6, M=12)
-    sp = SH.ShockProblem(vel=vel, n_x=N_X, L_x=L_X, mach=mach)
-    g = B.boltz_grid_init(N, 2, 10.0, 10.0, 0.0, 6, 12)
+    if form == 3:      # the Carleman (Mouhot-Pareschi) form the paper's experiments use: R = 6, 16 directions
+        sp = SH.ShockProblem(vel=vel, n_x=N_X, L_x=L_X, mach=mach,
+                             carleman=CM.CarlemanProblem(N=N, d=2, L=10.0, R=6.0, M=16))
+        g = B.boltz_grid_init(N, 2, 10.0, 6.0, 0.0, 1, 16)
+    else:
+        sp = SH.ShockProblem(vel=vel, n_x=N_X, L_x=L_X, mach=mach)
+        g = B.boltz_grid_init(N, 2, 10.0, 10.0, 0.0, 6, 12)
     fL, fR = sp.boundary()
     return sp, g, B.boltz_shock_create(g, N_X, L_X, fL, fR, r_max, form)
 
@@ -50,10 +56,10 @@ def test_full_tensor_steps_match_oracle():
     assert np.max(np.abs(got - want)) <= 1e-5 * np.max(np.abs(want - f0))
 
 
-def _lowrank_run(B, drop_tol, steps, r0=4, mach=1.4):
+def _lowrank_run(B, drop_tol, steps, r0=4, mach=1.4, form=0):
     import torch
     from oracle import shock as SH
-    sp, g, sh = make(B, mach=mach)
+    sp, g, sh = make(B, mach=mach, form=form)
     try:
         f0 = sp.initial()
         X, S, V = SH.factor(sp, f0, r0)
@@ -106,6 +112,32 @@ def test_lowrank_steps_match_oracle_growing_rank():
     sp, f0, out, Xg, Vg = _lowrank_run(B, 1e-7, 2)
     assert [o[0] for o in out] == [o[1] for o in out] == [6, 8]
     for r_gpu, r_orc, fg, fo in out:
+        assert np.max(np.abs(fg - fo)) <= 1e-4 * np.max(np.abs(fo - f0))
+
+
+def test_carleman_form_full_and_lowrank_steps_match_oracle():
+    """The same solver on the Carleman (Mouhot-Pareschi) form of Q, the
+    method of the paper's own experiments (2D Maxwell molecules)."""
+    import torch
+    from oracle import shock as SH
+    B = require_gpu()
+    sp, g, sh = make(B, form=3)
+    try:
+        f0 = sp.initial()
+        f = torch.tensor(f0, dtype=torch.float64, device="cuda")
+        B.boltz_shock_full_step(sh, f, 2, DT)
+        torch.cuda.synchronize()
+        got = f.cpu().numpy()
+    finally:
+        sh.close()
+        g.close()
+    want = f0.copy()
+    for _ in range(2):
+        want = SH.full_step(sp, want, DT)
+    assert np.max(np.abs(got - want)) <= 1e-5 * np.max(np.abs(want - f0))
+    sp, f0, out, Xg, Vg = _lowrank_run(B, 1e-5, 2, form=3)
+    for r_gpu, r_orc, fg, fo in out:
+        assert r_gpu == r_orc
         assert np.max(np.abs(fg - fo)) <= 1e-4 * np.max(np.abs(fo - f0))
 
 
