@@ -72,7 +72,7 @@ typedef enum {
     BOLTZ_ENOMEM = 2,        /* host or device allocation failed               */
     BOLTZ_ECUDA = 3,         /* a CUDA runtime call failed                     */
     BOLTZ_ETIMEOUT = 4,      /* a bounded device wait gave up                  */
-    BOLTZ_EUNSUPPORTED = 5,  /* valid request this build does not implement    */
+    BOLTZ_EUNSUPPORTED = 5,  /* valid request the library does not implement  */
     BOLTZ_ENONFINITE = 6     /* non-finite value detected                      */
 } boltz_status;
 
