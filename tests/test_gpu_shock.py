@@ -20,10 +20,16 @@ pytestmark = pytest.mark.gpu
 N_X, N, L_X, DT = 16, 16, 6.0, 0.005
 
 
-def make(B, mach=1.4, r_max=16, form=0):
+def make(B, mach=1.4, r_max=16, form=0, d=2):
     from oracle import carleman as CM
     from oracle import collision as C
     from oracle import shock as SH
+    if d == 3:         # 3D hard spheres, 16^3 on [-10, 10]^3, N_rho = 4 x M = 14
+        vel = C.Problem(N=N, d=3, L=10.0, R=10.0, gamma=1.0, n_rho=4, M=14)
+        sp = SH.ShockProblem(vel=vel, n_x=12, L_x=L_X, mach=mach)
+        g = B.boltz_grid_init(N, 3, 10.0, 10.0, 1.0, 4, 14)
+        fL, fR = sp.boundary()
+        return sp, g, B.boltz_shock_create(g, 12, L_X, fL, fR, r_max, form)
     vel = C.Problem(N=N, d=2, L=10.0, R=10.0, gamma=0.0, n_rho=6, M=12)
     if form == 3:      # the Carleman (Mouhot-Pareschi) form the paper's experiments use: R = 6, 16 directions
         sp = SH.ShockProblem(vel=vel, n_x=N_X, L_x=L_X, mach=mach,
@@ -56,25 +62,26 @@ def test_full_tensor_steps_match_oracle():
     assert np.max(np.abs(got - want)) <= 1e-5 * np.max(np.abs(want - f0))
 
 
-def _lowrank_run(B, drop_tol, steps, r0=4, mach=1.4, form=0):
+def _lowrank_run(B, drop_tol, steps, r0=4, mach=1.4, form=0, d=2):
     import torch
     from oracle import shock as SH
-    sp, g, sh = make(B, mach=mach, form=form)
+    sp, g, sh = make(B, mach=mach, form=form, d=d)
+    n_x, n_v = sp.n_x, N ** d
     try:
         f0 = sp.initial()
         X, S, V = SH.factor(sp, f0, r0)
         rm = sh.r_max
-        Xd = torch.zeros((rm, N_X), dtype=torch.float64, device="cuda")
-        Vd = torch.zeros((rm, N * N), dtype=torch.float64, device="cuda")
+        Xd = torch.zeros((rm, n_x), dtype=torch.float64, device="cuda")
+        Vd = torch.zeros((rm, n_v), dtype=torch.float64, device="cuda")
         Sd = torch.zeros(rm * rm, dtype=torch.float64, device="cuda")
         Xd[:r0] = torch.tensor(X)
         Vd[:r0] = torch.tensor(V)
         Sd[: r0 * r0] = torch.tensor(S.ravel())
         r = r0
-        fd = torch.empty((N_X, N * N), dtype=torch.float64, device="cuda")
+        fd = torch.empty((n_x, n_v), dtype=torch.float64, device="cuda")
         out = []
         for step in range(steps):
-            (X, S, V), parts = SH.lowrank_step(sp, X, S, V, DT, drop_tol, SH.random_xh(N_X, seed=step),
+            (X, S, V), parts = SH.lowrank_step(sp, X, S, V, DT, drop_tol, SH.random_xh(n_x, seed=step),
                                                return_parts=True)
             sig = parts["sigma"]
             assert np.min(np.abs(np.log10(sig[sig > 0] / drop_tol))) > np.log10(3.0)
@@ -138,6 +145,32 @@ def test_carleman_form_full_and_lowrank_steps_match_oracle():
     sp, f0, out, Xg, Vg = _lowrank_run(B, 1e-5, 2, form=3)
     for r_gpu, r_orc, fg, fo in out:
         assert r_gpu == r_orc
+        assert np.max(np.abs(fg - fo)) <= 1e-4 * np.max(np.abs(fo - f0))
+
+
+def test_3d_hard_spheres_full_and_lowrank_steps_match_oracle():
+    """The same solver on a 3D velocity grid (16^3, hard spheres, 12 cells):
+    two full-tensor steps and two low-rank steps with the rank growing 3 -> 5 -> 7."""
+    import torch
+    from oracle import shock as SH
+    B = require_gpu()
+    sp, g, sh = make(B, d=3)
+    try:
+        f0 = sp.initial()
+        f = torch.tensor(f0, dtype=torch.float64, device="cuda")
+        B.boltz_shock_full_step(sh, f, 2, DT)
+        torch.cuda.synchronize()
+        got = f.cpu().numpy()
+    finally:
+        sh.close()
+        g.close()
+    want = f0.copy()
+    for _ in range(2):
+        want = SH.full_step(sp, want, DT)
+    assert np.max(np.abs(got - want)) <= 1e-5 * np.max(np.abs(want - f0))
+    sp, f0, out, Xg, Vg = _lowrank_run(B, 3e-7, 2, r0=3, d=3)
+    assert [o[0] for o in out] == [o[1] for o in out] == [5, 7]
+    for r_gpu, r_orc, fg, fo in out:
         assert np.max(np.abs(fg - fo)) <= 1e-4 * np.max(np.abs(fo - f0))
 
 
