@@ -359,7 +359,14 @@ def run_shock(args, world, rank, local_rank):
     dev = torch.device("cuda", local_rank)
     N, d, L, R, gamma, n_rho, M, kind, n_x = CONFIGS["shock"]
     cfg = SHOCK
-    g = B.boltz_grid_init(N, d, L, R, gamma, n_rho, M)
+    if args.form == "carleman":
+        # the Carleman (Mouhot-Pareschi) form of the paper's own experiments:
+        # truncation R = 0.75 L (as in the 2D BKW workload), 32 directions
+        form = B.BOLTZ_FORM_CARLEMAN
+        g = B.boltz_grid_init(N, d, L, 0.75 * L, gamma, 1, 32)
+    else:
+        form = B.BOLTZ_FORM_BATCHED
+        g = B.boltz_grid_init(N, d, L, R, gamma, n_rho, M)
     n_v = N ** d
     dv = 2.0 * L / N
     axis = -L + np.arange(N) * dv
@@ -371,7 +378,7 @@ def run_shock(args, world, rank, local_rank):
     ur, tr = ul * (m2 + d) / ((d + 1.0) * m2), tl * ((d + 2.0) * m2 - 1.0) * (m2 + d) / ((d + 1.0) ** 2 * m2)
     maxw = lambda rho, u, T: (rho / (2 * np.pi * T) * np.exp(-((v1 - u) ** 2 + v2 ** 2) / (2 * T))).reshape(-1)
     fL, fR = maxw(rl, ul, tl), maxw(rr, ur, tr)
-    sh = B.boltz_shock_create(g, n_x, cfg["L_x"], fL, fR, cfg["r_max"], B.BOLTZ_FORM_BATCHED)
+    sh = B.boltz_shock_create(g, n_x, cfg["L_x"], fL, fR, cfg["r_max"], form)
     dx = 2.0 * cfg["L_x"] / n_x
     x = -cfg["L_x"] + (np.arange(n_x) + 0.5) * dx
     s = (np.tanh(cfg["alpha"] * x) + 1.0) / 2.0
@@ -426,7 +433,8 @@ def run_shock(args, world, rank, local_rank):
             "value": args.steps / (lr_ms / 1e3), "unit": "steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": lr_ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64 factors, f32 collision batch", "data": "synthetic",
-            "config": {"workload": WORKLOAD_NAMES["shock"], "n_x": n_x, "n_v": n_v, "dt": dt, "drop_tol": tol,
+            "config": {"workload": WORKLOAD_NAMES["shock"], "n_x": n_x, "n_v": n_v, "dt": dt, "last_drop_tol": tol,
+                       "form": args.form,
                        "l2": "state larger than L2 is not the point here: steps run back to back"},
             "full_tensor": {"value": args.steps / (full_ms / 1e3), "unit": "steps/s",
                             "ms_per_step": full_ms / args.steps},
