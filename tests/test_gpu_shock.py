@@ -174,6 +174,84 @@ def test_3d_hard_spheres_full_and_lowrank_steps_match_oracle():
         assert np.max(np.abs(fg - fo)) <= 1e-4 * np.max(np.abs(fo - f0))
 
 
+def _paper_size(B, form=0):
+    """The benchmark's shock: Mach 1.4, 1000 cells on [-30, 30], 2D 32^2 on [-13.11, 13.11]^2."""
+    from oracle import collision as C
+    from oracle import shock as SH
+    vel = C.Problem(N=32, d=2, L=13.11, R=13.11, gamma=0.0, n_rho=16, M=16)
+    sp = SH.ShockProblem(vel=vel, n_x=1000, L_x=30.0, mach=1.4)
+    g = B.boltz_grid_init(32, 2, 13.11, 13.11, 0.0, 16, 16)
+    fL, fR = sp.boundary()
+    return sp, g, B.boltz_shock_create(g, 1000, 30.0, fL, fR, 64, form)
+
+
+def test_full_size_full_tensor_step_sampled_cells():
+    """One full-tensor step at the benchmark size; cells at both boundaries and
+    in the shock are checked one by one (a cell's upwind update needs only its
+    neighbours and its own Q(f, f))."""
+    import torch
+    from oracle import shock as SH
+    B = require_gpu()
+    sp, g, sh = _paper_size(B)
+    try:
+        f0 = sp.initial()
+        f = torch.tensor(f0, dtype=torch.float64, device="cuda")
+        B.boltz_shock_full_step(sh, f, 1, 0.004)
+        torch.cuda.synchronize()
+        got = f.cpu().numpy()
+    finally:
+        sh.close()
+        g.close()
+    fL, fR = sp.boundary()
+    v1 = sp.v1()
+    vp, vm = np.maximum(v1, 0.0), np.minimum(v1, 0.0)
+    from oracle import collision as C
+    for p in (0, 1, 480, 500, 520, 998, 999):
+        left = fL if p == 0 else f0[p - 1]
+        right = fR if p == sp.n_x - 1 else f0[p + 1]
+        Q, Qp, Qm = C.collide_fields(sp.vel, f0[p].reshape(1, 32, 32), [(0, 0)], return_parts=True)
+        want = f0[p] - 0.004 * (vp * (f0[p] - left) + vm * (right - f0[p])) / sp.dx + 0.004 * Q[0].reshape(-1)
+        # FP32 collision term: its rounding scales with max(|Q|, |Q+|, |Q-|) of the cell,
+        # which near the boundaries (close to equilibrium) dwarfs the change of f
+        gate = 1e-5 * (np.max(np.abs(want - f0[p])) + 0.004 * float(C.scale(Q, Qp, Qm)[0]))
+        assert np.max(np.abs(got[p] - want)) <= gate, p
+
+
+def test_full_size_lowrank_step_properties():
+    """One low-rank step at the benchmark size from the rank-2 bimodal state:
+    orthonormal bases, rank within r + 2, and the Sec. 5.1 measure equal to
+    the norm of the change of the rebuilt solution (no drop)."""
+    import torch
+    B = require_gpu()
+    sp, g, sh = _paper_size(B)
+    try:
+        fL, fR = sp.boundary()
+        s = (np.tanh(0.5 * sp.x) + 1.0) / 2.0
+        dev = "cuda"
+        Yx, Rx, _ = B.boltz_qr_f64(torch.tensor(np.stack([1.0 - s, s]), device=dev), sp.dx)
+        Yv, Rv, _ = B.boltz_qr_f64(torch.tensor(np.stack([fL, fR]), device=dev), sp.wv)
+        Xd = torch.zeros((64, sp.n_x), dtype=torch.float64, device=dev)
+        Vd = torch.zeros((64, 1024), dtype=torch.float64, device=dev)
+        Sd = torch.zeros(64 * 64, dtype=torch.float64, device=dev)
+        Xd[:2], Vd[:2] = Yx, Yv
+        Sd[:4] = (Rx @ Rv.T).reshape(-1)
+        f_before = torch.empty((sp.n_x, 1024), dtype=torch.float64, device=dev)
+        B.boltz_shock_reconstruct(sh, Xd, Sd, Vd, 2, f_before)
+        r, err = B.boltz_shock_lowrank_step(sh, Xd, Sd, Vd, 2, 0.004, 0.0)
+        f_after = torch.empty_like(f_before)
+        B.boltz_shock_reconstruct(sh, Xd, Sd, Vd, r, f_after)
+        torch.cuda.synchronize()
+        X, V = Xd[:r].cpu().numpy(), Vd[:r].cpu().numpy()
+        direct = float(np.sqrt(sp.dx * sp.wv * ((f_after - f_before) ** 2).sum().item()))
+    finally:
+        sh.close()
+        g.close()
+    assert 1 <= r <= 4
+    assert np.allclose(sp.dx * X @ X.T, np.eye(r), atol=1e-10)
+    assert np.allclose(sp.wv * V @ V.T, np.eye(r), atol=1e-10)
+    assert abs(err - direct) <= 1e-8 * direct
+
+
 def test_uniform_state_stays_uniform():
     """Mach 1 (f_L = f_R, uniform initial Maxwellian): the boundary vector lies
     in span(V) and is not added; the state changes only by dt Q(M, M)."""
