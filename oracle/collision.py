@@ -275,13 +275,23 @@ def project(prob: Problem, V: np.ndarray, Q: np.ndarray) -> np.ndarray:
     return prob.dv ** prob.d * V.reshape(r, -1) @ Q.reshape(Q.shape[0], -1).T
 
 
+def velocity_axis(prob: Problem) -> np.ndarray:
+    """Grid points of one velocity axis, v_j = -L + j dv (Sec. 2.1 uniform grid)."""
+    return -prob.L + np.arange(prob.N) * prob.dv
+
+
+def cell_volume(prob: Problem) -> float:
+    """Weight of one grid point in the midpoint rule for int dv (Sec. 2.4): dv^d."""
+    return prob.dv ** prob.d
+
+
 def moments(prob: Problem, Q: np.ndarray) -> np.ndarray:
     """dv^d sum_v Q(v) {1, v_0..v_{d-1}, |v|^2} for each result (Sec. 1)."""
-    ax = -prob.L + np.arange(prob.N) * prob.dv
+    ax = velocity_axis(prob)
     V = np.meshgrid(*([ax] * prob.d), indexing="ij")
     phis = [np.ones(prob.shape)] + list(V) + [sum(x * x for x in V)]
     Qf = Q.reshape(-1, *prob.shape)
-    return np.stack([[prob.dv ** prob.d * np.sum(qq * ph) for ph in phis] for qq in Qf])
+    return np.stack([[cell_volume(prob) * np.sum(qq * ph) for ph in phis] for qq in Qf])
 
 
 # --------------------------------------------------------------------------

@@ -154,6 +154,37 @@ def test_maxwellian_is_an_equilibrium():
     assert np.abs(Q).max() / np.abs(Qp).max() < 1e-6
 
 
+@pytest.mark.parametrize("d,N,rho,u,T", [(2, 64, 1.3, [0.7, -0.4], 0.8), (3, 48, 0.6, [-0.5, 0.3, 0.9], 1.2)])
+def test_moments_of_a_maxwellian_match_the_closed_form(d, N, rho, u, T):
+    """The moment sums of Sec. 1 against the closed-form moments of a
+    Maxwellian rho (2 pi T)^(-d/2) exp(-|v-u|^2/(2T)) resolved on the grid
+    (the periodic midpoint rule is spectrally accurate; what is left is the
+    tail beyond the box, ~1e-9 here): mass rho, momentum rho u, energy
+    rho (|u|^2 + d T).  A wrong cell volume or a grid origin off by half a
+    cell fails it (see the planted mistakes below)."""
+    prob = C.Problem(N=N, d=d, L=8.0, R=8.0, gamma=1.0, n_rho=2, M=8 if d == 2 else 6)
+    m = W.maxwellian(N, d, 8.0, rho, u, T)
+    mom = C.moments(prob, m[None])[0]
+    u = np.asarray(u)
+    exact = np.concatenate([[rho], rho * u, [rho * (u @ u + d * T)]])
+    assert np.max(np.abs(mom - exact)) < 1e-7 * max(1.0, np.max(np.abs(exact)))
+
+
+MOMENT_MUTATIONS = {
+    "cell volume dv^(d-1)": ("cell_volume", lambda orig: (lambda prob: prob.dv ** (prob.d - 1))),
+    "grid origin at the cell centre": ("velocity_axis",
+        lambda orig: (lambda prob: orig(prob) + 0.5 * prob.dv)),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MOMENT_MUTATIONS))
+def test_planted_moment_mistake_is_caught(name, monkeypatch):
+    attr, make = MOMENT_MUTATIONS[name]
+    monkeypatch.setattr(C, attr, make(getattr(C, attr)))
+    with pytest.raises(AssertionError):
+        test_moments_of_a_maxwellian_match_the_closed_form(3, 48, 0.6, [-0.5, 0.3, 0.9], 1.2)
+
+
 def test_conservation_of_mass_momentum_energy():
     """int Q {1, v, |v|^2} dv = 0 (Sec. 1 moments, collision invariants) for
     Q(f,f) and the symmetrised Q(g,f) + Q(f,g); a single Q(g,f), g != f, keeps
