@@ -46,7 +46,16 @@
  * Errors: every entry point returns a boltz_status and never throws.  Argument
  * checks are synchronous and leave device memory untouched.  BOLTZ_ECUDA
  * reports a failed CUDA call (launch or allocation); a context error is
- * sticky in CUDA, so the grid should then be destroyed.
+ * sticky in CUDA, so the grid should then be destroyed.  Conditions found by
+ * the kernels (a bounded wait that gave up, a non-finite output value) are
+ * recorded in a device error word and reported by boltz_sync_status.
+ *
+ * Fault injection (for testing callers' error handling; host side only): the
+ * environment variable BOLTZ_FAULT, read at every call, set to "alloc" makes
+ * every workspace allocation fail (BOLTZ_ENOMEM), "badplan" makes batch
+ * planning reject every batch (BOLTZ_EINVAL), "nan" marks every collision
+ * batch queued by boltz_collide_batched as having produced a non-finite value
+ * (boltz_sync_status reports BOLTZ_ENONFINITE).  Unset, nothing is injected.
  *
  * Threading: a grid handle is not thread safe; distinct handles are
  * independent.  Calls on one handle must not overlap on different streams
@@ -122,7 +131,31 @@ typedef struct {
     size_t workspace_max;  /* cap on device workspace in bytes; 0 = library default */
     int field_budget_mb;   /* shifted-field memory per radial block, MB; 0 = 96 MB
                               (the schedule boltz_autotune chooses between)        */
+    int schedule;          /* schedule of the batched FP32 form:
+                              BOLTZ_SCHEDULE_AUTO (0): the pipelined schedule where
+                              it is built (d_v = 3, N = 32, at most 16 distinct
+                              inputs), the node-block schedule elsewhere;
+                              BOLTZ_SCHEDULE_NODE_BLOCKS (1): always the node-block
+                              schedule (the comparison baseline)                   */
 } boltz_options;
+
+/*
+ * Schedules of the batched FP32 form (same result up to FP32 rounding order):
+ *   NODE_BLOCKS  separate launches per block of radial nodes: every shifted
+ *                field is synthesised in full (three inverse passes per
+ *                direction), written to device memory, read back by the
+ *                sigma-contraction, whose per-node gain fields are written and
+ *                read back by the radial step.
+ *   PIPELINED    one persistent kernel: the axis-0 and axis-1 inverse passes
+ *                are computed once per distinct sigma_0 and per distinct
+ *                (sigma_0, sigma_1) of the direction rule (9 and 25 of the 38
+ *                directions) and kept in L2-sized node buffers, and the last
+ *                inverse pass of every direction is fused with the
+ *                sigma-contraction and the first forward pass, so the shifted
+ *                fields never leave the chip.
+ */
+#define BOLTZ_SCHEDULE_AUTO 0
+#define BOLTZ_SCHEDULE_NODE_BLOCKS 1
 
 /* Library ABI version (BOLTZ_ABI_VERSION of the build). */
 int boltz_abi_version(void);
@@ -145,7 +178,7 @@ const char* boltz_status_string(boltz_status s);
  *   opt    may be NULL (defaults)
  * Allocates the handle and its device tables on the current device.
  * Errors: BOLTZ_EINVAL (out may be NULL or a value is out of range; *out is
- * left untouched), BOLTZ_EUNSUPPORTED (valid but not built, e.g. N = 128),
+ * left untouched), BOLTZ_EUNSUPPORTED (valid but not built, e.g. d_v = 3 with N = 128),
  * BOLTZ_ENOMEM, BOLTZ_ECUDA.
  */
 boltz_status boltz_grid_init(boltz_grid* out, int N, int d_v, double L, double R, double gamma,
@@ -378,9 +411,12 @@ boltz_status boltz_workspace_size(boltz_grid g, int n_inputs, const int32_t* pai
 /*
  * Waits for the work queued on `stream` and reports device-detected errors
  * since the last check, then clears them: BOLTZ_ETIMEOUT if a bounded device
- * wait (an asynchronous-copy barrier) gave up, which leaves the affected
- * results invalid; BOLTZ_ECUDA if a CUDA call failed.  Kernels never trap or
- * spin without a limit; this call is how their failures surface.
+ * wait (an asynchronous-copy barrier or a dependency counter) gave up, which
+ * leaves the affected results invalid; BOLTZ_ENONFINITE if a collision
+ * output value written since the last check was NaN or infinite (a
+ * non-finite input propagates to the outputs of every pair that uses it);
+ * BOLTZ_ECUDA if a CUDA call failed.  Kernels never trap or spin without a
+ * limit; this call is how their failures surface.
  */
 boltz_status boltz_sync_status(boltz_grid g, void* stream);
 
@@ -403,7 +439,9 @@ typedef enum {
     BOLTZ_KCLASS_RADIAL = 4,    /* forward transform x radial multiplier, accumulated over q  */
     BOLTZ_KCLASS_OUTPUT = 5,    /* gain synthesis minus loss, written per ordered pair        */
     BOLTZ_KCLASS_PROJECT = 6,   /* projection tensor (two kernels)                            */
-    BOLTZ_KCLASS_COUNT = 7
+    BOLTZ_KCLASS_PIPELINE = 7,  /* pipelined schedule: shifted fields, sigma-contraction and
+                                   radial step of all nodes in one persistent kernel          */
+    BOLTZ_KCLASS_COUNT = 8
 } boltz_kernel_class;
 
 /*
