@@ -463,6 +463,9 @@ def main():
                     help="form of the headline measurement (the other arms run only with the default)")
     ap.add_argument("--field-budget-mb", type=int, default=0,
                     help="fix the schedule instead of autotuning it (e.g. for profiling runs)")
+    ap.add_argument("--schedule", default="auto", choices=["auto", "node-blocks"],
+                    help="batched-form schedule: the library's choice (pipelined on 3D 32^3), "
+                         "or the node-block launches for comparison")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -524,7 +527,9 @@ def main():
     n_in = fields.shape[0]
     pj = [p[0] for p in pairs]
     pl = [p[1] for p in pairs]
-    g = B.boltz_grid_init(N, d, L, R, gamma, n_rho, M, field_budget_mb=args.field_budget_mb)
+    g = B.boltz_grid_init(N, d, L, R, gamma, n_rho, M, field_budget_mb=args.field_budget_mb,
+                          schedule=B.BOLTZ_SCHEDULE_NODE_BLOCKS if args.schedule == "node-blocks"
+                          else B.BOLTZ_SCHEDULE_AUTO)
     dev = torch.device("cuda", local_rank)
     f_dev = torch.tensor(fields, device=dev)
     spec = torch.empty((n_in,) + g.half_shape, dtype=torch.complex64, device=dev)
@@ -730,22 +735,33 @@ def main():
         fl["shift"] = M * n_in * (ft + 2 * N ** d)
         fl["radial"] = 0
         fl["contract"] = (M // 2) * 2 * len(set(pairs)) * N ** d
-    launches_s, ms_s = prof["shift"]
-    shift_launches_per_step = launches_s / args.steps
+    pipelined = prof.get("pipeline", (0, 0.0))[0] > 0
+    if pipelined:
+        # one persistent kernel per step does the shifted fields, the sigma-contraction
+        # and the radial step of every node: its algorithmic work is the sum of the three
+        launches_s, ms_s = prof["pipeline"]
+        kernel_flops = fl["shift"] + fl["contract"] + fl["radial"]
+    else:
+        launches_s, ms_s = prof["shift"]
+        kernel_flops = fl["shift"]
+    kernel_launches_per_step = launches_s / args.steps
     avg_launch_ms = ms_s / max(launches_s, 1)
-    flops_per_launch = fl["shift"] / shift_launches_per_step
+    flops_per_launch = kernel_flops / max(kernel_launches_per_step, 1e-9)
     achieved = flops_per_launch / (avg_launch_ms * 1e-3) / 1e12
     traffic = None
     try:
         with open(TRAFFIC_FILE) as fh:
             entries = json.load(fh)
         ksrc = open(os.path.join(ROOT, "paper_2112_02695_gb300", "csrc", "kernels.cuh"), "rb").read()
+        if pipelined:
+            ksrc += open(os.path.join(ROOT, "paper_2112_02695_gb300", "csrc", "pencil.cuh"), "rb").read()
         fsrc = open(os.path.join(ROOT, "paper_2112_02695_gb300", "csrc", "fft.cuh"), "rb").read()
         lsrc = open(os.path.join(ROOT, "paper_2112_02695_gb300", "csrc", "boltz.cu"), "rb").read()
         digest = hashlib.sha256(ksrc + fsrc + lsrc).hexdigest()
         for tr in entries:
             if (tr.get("source_sha256") == digest and tr.get("config") == args.config
-                    and tr.get("form", "batched") == args.form and tr.get("field_budget_mb") == tuned_mb):
+                    and tr.get("form", "batched") == args.form
+                    and (tr.get("field_budget_mb") == tuned_mb or (pipelined and tr.get("schedule") == "pipelined"))):
                 traffic = tr["bytes_per_launch"]
     except (OSError, ValueError, KeyError):
         traffic = None
@@ -782,11 +798,15 @@ def main():
             "vs_baseline": None, "dtype": "bf16x3+f32" if args.form == "split" else "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD_NAMES[args.config], "evals_per_step": len(pairs),
                        "autotuned_field_budget_mb": tuned_mb, "form": args.form,
+                       "schedule": "pipelined" if pipelined else "node blocks",
                        "l2": "flushed between timed steps (512 MB write outside the timed events)",
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                          "frac": achieved / alu_peak, "traffic": traffic,
-                         "kernel": {"batched": "k_synth (phase-weighted inverse 3D transforms of the shifted fields)",
+                         "kernel": {"batched": ("k_pencil (pipelined schedule: shifted fields, sigma-contraction and "
+                                                "radial step of every node; algorithmic flops of the three)")
+                                    if pipelined else
+                                    "k_synth (phase-weighted inverse 3D transforms of the shifted fields)",
                                     "carleman": "k_synth SYN_MULT (multiplier-weighted inverse 3D transforms)",
                                     "split": "k_shift_split (tensor cores; algorithmic FFT flops over its time)"}[args.form],
                          "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz",

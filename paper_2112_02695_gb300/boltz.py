@@ -41,7 +41,10 @@ EXPORTED = (
     "boltz_shock_reconstruct",
 )
 
-KERNEL_CLASSES = ("spectrum", "prep", "shift", "contract", "radial", "output", "project")
+KERNEL_CLASSES = ("spectrum", "prep", "shift", "contract", "radial", "output", "project", "pipeline")
+
+BOLTZ_SCHEDULE_AUTO = 0
+BOLTZ_SCHEDULE_NODE_BLOCKS = 1
 
 
 class BoltzError(RuntimeError):
@@ -51,7 +54,8 @@ class BoltzError(RuntimeError):
 
 
 class _Options(ctypes.Structure):
-    _fields_ = [("b", ctypes.c_double), ("workspace_max", ctypes.c_size_t), ("field_budget_mb", ctypes.c_int)]
+    _fields_ = [("b", ctypes.c_double), ("workspace_max", ctypes.c_size_t), ("field_budget_mb", ctypes.c_int),
+                ("schedule", ctypes.c_int)]
 
 
 class _Work(ctypes.Structure):
@@ -192,9 +196,10 @@ class Grid:
 
 
 def boltz_grid_init(N: int, d_v: int, L: float, R: float, gamma: float, N_rho: int, M: int,
-                    b: float | None = None, workspace_max: int = 0, field_budget_mb: int = 0) -> Grid:
+                    b: float | None = None, workspace_max: int = 0, field_budget_mb: int = 0,
+                    schedule: int = BOLTZ_SCHEDULE_AUTO) -> Grid:
     h = ctypes.c_void_p()
-    opt = _Options(b if b is not None else 0.0, workspace_max, field_budget_mb)
+    opt = _Options(b if b is not None else 0.0, workspace_max, field_budget_mb, schedule)
     _check(_lib.boltz_grid_init(ctypes.byref(h), N, d_v, L, R, gamma, N_rho, M, ctypes.byref(opt)),
            "boltz_grid_init")
     area = 2 * np.pi if d_v == 2 else 4 * np.pi

@@ -16,6 +16,7 @@ namespace boltz_dev {
 constexpr uint32_t kSpinLimit = 1u << 26;     // mbarrier polls before giving up (backstop)
 constexpr uint64_t kWaitNs = 1000000000ull;    // device-time limit of one wait
 constexpr int kErrTimeout = 1;                 // bit in the device error word
+constexpr int kErrNonFinite = 2;               // bit: an output value was NaN or infinite
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));

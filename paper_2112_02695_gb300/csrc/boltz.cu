@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -21,6 +22,7 @@
 #include "boltz.h"
 #include "kernels.cuh"
 #include "lowrank.cuh"
+#include "pencil.cuh"
 #include "quadrature.hpp"
 #include "shock.cuh"
 #include "split.cuh"
@@ -61,6 +63,27 @@ struct Plan {
     size_t plan_bytes = 0;
     // workspace layout (byte offsets)
     size_t off_plan = 0, off_A = 0, off_P = 0, off_qhat = 0, off_fN = 0, off_lam = 0, off_img = 0, total = 0;
+    // pipelined schedule (pencil.cuh): one chunk, gain slots in TRI16 numbering,
+    // Qhat+ and the output lists over the used slots only
+    bool pencil = false;
+    int pen_n_used = 0;
+    std::vector<int> pen_slots;           // used TRI16 slots, ascending
+    std::vector<char> pen_blob;           // direction tree + slot list (device image)
+    size_t off_pen_blob = 0, off_X = 0, off_Pt = 0, off_ctr = 0;
+    size_t pen_off[9] = {};               // offsets inside the blob: grp, s0_dir, s0_child,
+                                          // s01_dir, step_blk, step_dir, step_sel, step_w, slots
+};
+
+// Direction structure of a 3D rule for the pipelined schedule: the distinct
+// sigma_0 values (grouped into tree items), the distinct (sigma_0, sigma_1)
+// values below each (one X block each), and the steps of the fused items
+// (two antipodal pairs each), see pencil.cuh.
+struct PencilTree {
+    bool ok = false;
+    int n_s0 = 0, n_s01 = 0, n_grp = 0;
+    std::vector<int> grp, s0_dir, s0_child, s01_dir;
+    std::vector<int4> step_blk, step_dir, step_sel;
+    std::vector<float2> step_w;
 };
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -94,6 +117,9 @@ struct boltz_grid_s {
     float* d_cm_w = nullptr;          // [M/2]
     int2* d_cm_dpair = nullptr;       // [M/2]
     int split_clusters = 1;           // resident clusters of the split kernel
+    int schedule = BOLTZ_SCHEDULE_AUTO;
+    PencilTree pen_tree;              // 3D N = 32 only
+    int pen_ctas = 0;                 // resident CTAs of the pipelined kernel
     int* d_err = nullptr;        // device error word (bit kErrTimeout: a bounded wait gave up)
     // workspace
     char* d_ws = nullptr;
@@ -171,9 +197,220 @@ int voxel_chunk(int N, int D) {
 boltz_status build_plan_carleman(const boltz_grid_s* g, const int32_t* pj, const int32_t* pl, int n_pairs,
                                  Plan& plan);
 
+// Direction tree of a 3D rule for the pipelined schedule.  Components are
+// compared exactly: the rules are built by permutations and sign changes of
+// their generators, so equal components are equal bit for bit.
+PencilTree build_pencil_tree(const boltz_grid_s* g) {
+    namespace pc = boltz_dev::pencil;
+    PencilTree T;
+    const int M = g->M;
+    const std::vector<double>& sg = g->dir.sigma;
+    std::vector<double> v0;                           // distinct sigma_0
+    std::vector<std::vector<double>> v1;              // distinct sigma_1 below each sigma_0
+    std::vector<int> p0(M), p1(M);
+    for (int p = 0; p < M; ++p) {
+        const double a = sg[3 * p], b = sg[3 * p + 1];
+        int i = (int)(std::find(v0.begin(), v0.end(), a) - v0.begin());
+        if (i == (int)v0.size()) {
+            v0.push_back(a);
+            v1.emplace_back();
+        }
+        int k = (int)(std::find(v1[i].begin(), v1[i].end(), b) - v1[i].begin());
+        if (k == (int)v1[i].size()) v1[i].push_back(b);
+        p0[p] = i;
+        p1[p] = k;
+    }
+    const int n0 = (int)v0.size();
+    std::vector<int> rep0(n0, -1);
+    std::vector<std::vector<int>> rep(n0);
+    for (int i = 0; i < n0; ++i) rep[i].assign(v1[i].size(), -1);
+    for (int p = 0; p < M; ++p) {
+        if (rep0[p0[p]] < 0) rep0[p0[p]] = p;
+        if (rep[p0[p]][p1[p]] < 0) rep[p0[p]][p1[p]] = p;
+    }
+    // tree items: sigma_0 values grouped by longest-first assignment of their
+    // (1 + children) transform passes, about 11 passes per group
+    int total = 0, max_rows = 0;
+    for (int i = 0; i < n0; ++i) {
+        total += 1 + (int)v1[i].size();
+        max_rows = std::max(max_rows, 1 + (int)v1[i].size());
+    }
+    if (max_rows > pc::MAX_ROWS) return T;
+    const int ng = std::max(1, std::min(n0, (total + 10) / 11));
+    std::vector<int> order(n0);
+    for (int i = 0; i < n0; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return v1[a].size() > v1[b].size(); });
+    std::vector<int> load(ng, 0);
+    std::vector<std::vector<int>> bins(ng);
+    for (int i : order) {
+        const int b = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        bins[b].push_back(i);
+        load[b] += 1 + (int)v1[i].size();
+    }
+    std::map<std::pair<int, int>, int> s01_index;
+    T.grp.push_back(0);
+    for (int b = 0; b < ng; ++b) {
+        for (int i : bins[b]) {
+            T.s0_dir.push_back(rep0[i]);
+            T.s0_child.push_back((int)T.s01_dir.size());
+            for (int k = 0; k < (int)v1[i].size(); ++k) {
+                s01_index[{i, k}] = (int)T.s01_dir.size();
+                T.s01_dir.push_back(rep[i][k]);
+            }
+        }
+        T.grp.push_back((int)T.s0_dir.size());
+    }
+    T.s0_child.push_back((int)T.s01_dir.size());
+    T.n_s0 = n0;
+    T.n_s01 = (int)T.s01_dir.size();
+    T.n_grp = ng;
+    std::vector<int> blk_of(M);
+    for (int p = 0; p < M; ++p) blk_of[p] = s01_index[{p0[p], p1[p]}];
+    // steps: two antipodal pairs each, pairs that read the same two X blocks together
+    std::map<std::pair<int, int>, std::vector<int>> buckets;
+    for (int p = 0; p < M; ++p) {
+        const int pb = g->dir.antipode[p];
+        if (p < pb) buckets[{std::min(blk_of[p], blk_of[pb]), std::max(blk_of[p], blk_of[pb])}].push_back(p);
+    }
+    std::vector<std::vector<int>> steps;
+    std::vector<int> singles;
+    for (auto& kv : buckets) {
+        const std::vector<int>& v = kv.second;
+        size_t i = 0;
+        for (; i + 1 < v.size(); i += 2) steps.push_back({v[i], v[i + 1]});
+        if (i < v.size()) singles.push_back(v[i]);
+    }
+    for (size_t i = 0; i < singles.size(); i += 2) {
+        if (i + 1 < singles.size()) steps.push_back({singles[i], singles[i + 1]});
+        else steps.push_back({singles[i]});
+    }
+    for (const auto& stp : steps) {
+        int dirs[4] = {-1, -1, -1, -1}, blk[4] = {-1, -1, -1, -1}, sel[4] = {0, 0, 0, 0};
+        float w[2] = {0.f, 0.f};
+        for (size_t k = 0; k < stp.size(); ++k) {
+            dirs[2 * k] = stp[k];
+            dirs[2 * k + 1] = g->dir.antipode[stp[k]];
+            w[k] = (float)g->dir.w[stp[k]];
+        }
+        int nb = 0;
+        for (int d = 0; d < 4; ++d) {
+            if (dirs[d] < 0) continue;
+            const int x = blk_of[dirs[d]];
+            int k = 0;
+            while (k < nb && blk[k] != x) ++k;
+            if (k == nb) blk[nb++] = x;
+            sel[d] = k;
+        }
+        T.step_blk.push_back(make_int4(blk[0], blk[1], blk[2], blk[3]));
+        T.step_dir.push_back(make_int4(dirs[0], dirs[1], dirs[2], dirs[3]));
+        T.step_sel.push_back(make_int4(sel[0], sel[1], sel[2], sel[3]));
+        T.step_w.push_back(make_float2(w[0], w[1]));
+    }
+    // the kernel keeps these tables in fixed-size shared arrays
+    T.ok = !T.step_dir.empty() && T.n_s0 <= pc::MAX_S && T.n_s01 <= pc::MAX_S &&
+           (int)T.step_dir.size() <= pc::MAX_STEP;
+    return T;
+}
+
+// Whether a batch runs on the pipelined schedule: batched FP32 form on a 3D
+// 32^3 grid whose tree was built, at most 16 distinct inputs.
+bool pencil_applies(const boltz_grid_s* g, const int32_t* pj, const int32_t* pl, int n_pairs, int form,
+                    size_t elem) {
+    if (form != BOLTZ_FORM_BATCHED || elem != 4 || g->D != 3 || g->N != 32 || !g->pen_tree.ok ||
+        g->schedule != BOLTZ_SCHEDULE_AUTO || g->pen_ctas <= 0)
+        return false;
+    std::set<int> ins(pj, pj + n_pairs);
+    ins.insert(pl, pl + n_pairs);
+    return (int)ins.size() <= boltz_dev::pencil::NJ;
+}
+
+// Plan of the pipelined schedule: the distinct inputs as one chunk, gain
+// slot u = TRI16 index of the chunk-local pair, outputs listed per used slot
+// (Qhat+ and the output kernel run over the used slots only).  Workspace:
+// descriptors | f_N, Lambda | X node buffers | Pt node buffers | Qhat+ | counters.
+boltz_status build_plan_pencil(const boltz_grid_s* g, const int32_t* pj, const int32_t* pl, int n_pairs,
+                               Plan& plan) {
+    namespace pc = boltz_dev::pencil;
+    plan = Plan();
+    plan.pencil = true;
+    ChunkPlan c;
+    std::set<int> ins(pj, pj + n_pairs);
+    ins.insert(pl, pl + n_pairs);
+    c.inputs.assign(ins.begin(), ins.end());
+    std::map<int, int> loc;
+    for (int i = 0; i < (int)c.inputs.size(); ++i) loc[c.inputs[i]] = i;
+    std::vector<std::vector<int>> outs_of(pc::NSLOT);
+    for (int e = 0; e < n_pairs; ++e) {
+        const int a = loc[pj[e]], b = loc[pl[e]];
+        outs_of[pc::tri_slot(std::min(a, b), std::max(a, b))].push_back(e);
+    }
+    for (int u = 0; u < pc::NSLOT; ++u) {
+        if (outs_of[u].empty()) continue;
+        plan.pen_slots.push_back(u);
+        c.out_start.push_back((int)c.outs.size());
+        for (int e : outs_of[u]) c.outs.push_back(make_int4(e, loc[pj[e]], loc[pl[e]], 0));
+    }
+    c.out_start.push_back((int)c.outs.size());
+    c.U = (int)plan.pen_slots.size();
+    plan.pen_n_used = c.U;
+    const int nc = (int)c.inputs.size();
+    plan.max_nc = nc;
+    plan.max_U = c.U;
+    plan.nq = g->n_rho;
+    // direction tree and slot list as one blob (16-byte aligned tables)
+    const PencilTree& T = g->pen_tree;
+    std::vector<char>& blob = plan.pen_blob;
+    auto put = [&](int which, const void* src, size_t bytes) {
+        plan.pen_off[which] = align_up(blob.size(), 16);
+        blob.resize(plan.pen_off[which] + bytes);
+        if (bytes) std::memcpy(blob.data() + plan.pen_off[which], src, bytes);
+    };
+    put(0, T.grp.data(), T.grp.size() * sizeof(int));
+    put(1, T.s0_dir.data(), T.s0_dir.size() * sizeof(int));
+    put(2, T.s0_child.data(), T.s0_child.size() * sizeof(int));
+    put(3, T.s01_dir.data(), T.s01_dir.size() * sizeof(int));
+    put(4, T.step_blk.data(), T.step_blk.size() * sizeof(int4));
+    put(5, T.step_dir.data(), T.step_dir.size() * sizeof(int4));
+    put(6, T.step_sel.data(), T.step_sel.size() * sizeof(int4));
+    put(7, T.step_w.data(), T.step_w.size() * sizeof(float2));
+    put(8, plan.pen_slots.data(), plan.pen_slots.size() * sizeof(int));
+    blob.resize(align_up(blob.size(), 16));
+    size_t off = 0;
+    c.off_inputs = off;
+    off = align_up(off + c.inputs.size() * sizeof(int), 256);
+    for (int k = 0; k < 3; ++k) c.off_tiles[k] = off;
+    c.off_start = off;
+    off = align_up(off + c.out_start.size() * sizeof(int), 256);
+    c.off_outs = off;
+    off = align_up(off + c.outs.size() * sizeof(int4), 256);
+    plan.off_pen_blob = off;
+    off = align_up(off + blob.size(), 256);
+    plan.plan_bytes = off;
+    plan.chunks.push_back(std::move(c));
+    const size_t field_bytes = size_t(g->n) * 4;
+    size_t w = align_up(off, 256);
+    plan.off_plan = 0;
+    plan.off_fN = w;                       // f_N [nc][n] then Lambda [nc][n]
+    w = align_up(w + size_t(nc) * field_bytes, 256);
+    plan.off_lam = w;
+    w = align_up(w + size_t(nc) * field_bytes, 256);
+    plan.off_X = w;
+    w = align_up(w + size_t(pc::NXB) * T.n_s01 * pc::NLB * pc::XBLK * sizeof(float2), 256);
+    plan.off_Pt = w;
+    w = align_up(w + size_t(pc::NPB) * pc::NSLOT * pc::NKB * pc::PLANE * sizeof(float2), 256);
+    plan.off_qhat = w;
+    w = align_up(w + size_t(plan.pen_n_used) * pc::HALF * sizeof(float2), 256);
+    plan.off_ctr = w;
+    w = align_up(w + size_t(pc::ctr_count(g->n_rho, plan.pen_n_used)) * sizeof(int), 256);
+    plan.off_A = plan.off_P = plan.off_img = w;
+    plan.total = w;
+    return BOLTZ_OK;
+}
+
 boltz_status build_plan(const boltz_grid_s* g, int n_inputs, const int32_t* pj, const int32_t* pl, int n_pairs,
                         int form, Plan& plan, size_t elem = 4) {
     if (form == BOLTZ_FORM_CARLEMAN) return build_plan_carleman(g, pj, pl, n_pairs, plan);
+    if (pencil_applies(g, pj, pl, n_pairs, form, elem)) return build_plan_pencil(g, pj, pl, n_pairs, plan);
     plan = Plan();
     const size_t field_bytes = size_t(g->n) * elem;
     // inputs per chunk: enough for one radial node's shifted fields to fit the L2-sized
@@ -509,9 +746,20 @@ boltz_status build_plan_carleman(const boltz_grid_s* g, const int32_t* pj, const
     return BOLTZ_OK;
 }
 
+// Host-side fault injection for the error paths (environment variable
+// BOLTZ_FAULT, read at every call): "alloc" fails every workspace allocation
+// with BOLTZ_ENOMEM, "badplan" makes batch planning reject every batch with
+// BOLTZ_EINVAL, "nan" marks every queued collision batch as having written a
+// non-finite value (boltz_sync_status then reports BOLTZ_ENONFINITE).
+// Nothing is injected on the device.
+bool fault_injected(const char* what) {
+    const char* v = std::getenv("BOLTZ_FAULT");
+    return v && std::strcmp(v, what) == 0;
+}
+
 boltz_status ensure_workspace(boltz_grid_s* g, size_t bytes, cudaStream_t stream) {
     if (bytes <= g->ws_cap) return BOLTZ_OK;
-    if (bytes > g->ws_max) return BOLTZ_ENOMEM;
+    if (bytes > g->ws_max || fault_injected("alloc")) return BOLTZ_ENOMEM;
     if (g->d_ws) {
         BZ_CUDA(cudaStreamSynchronize(stream));
         BZ_CUDA(cudaFree(g->d_ws));
@@ -540,6 +788,8 @@ boltz_status upload_plan(boltz_grid_s* g, const Plan& plan, cudaStream_t stream)
         std::memcpy(host.data() + c.off_start, c.out_start.data(), c.out_start.size() * sizeof(int));
         if (!c.outs.empty()) std::memcpy(host.data() + c.off_outs, c.outs.data(), c.outs.size() * sizeof(int4));
     }
+    if (plan.pencil && !plan.pen_blob.empty())
+        std::memcpy(host.data() + plan.off_pen_blob, plan.pen_blob.data(), plan.pen_blob.size());
     if (plan.plan_bytes) {
         BZ_CUDA(cudaMemcpyAsync(g->d_ws + plan.off_plan, host.data(), plan.plan_bytes, cudaMemcpyHostToDevice, stream));
         BZ_CUDA(cudaStreamSynchronize(stream));   // host staging buffer goes out of scope
@@ -954,6 +1204,7 @@ boltz_status check_pairs(int n_inputs, const int32_t* pj, const int32_t* pl, int
 // pair list changed).  Synchronous; never called during stream capture.
 boltz_status prepare_plan(boltz_grid_s* g, int n_inputs, const int32_t* pj, const int32_t* pl, int n_pairs, int form,
                           size_t min_ws, cudaStream_t st, size_t elem = 4) {
+    if (fault_injected("badplan")) return BOLTZ_EINVAL;
     const bool same = g->plan_uploaded && form == g->last_form && n_inputs == g->last_n_inputs &&
                       elem == g->last_elem &&
                       (int)g->last_j.size() == n_pairs &&
@@ -1281,7 +1532,88 @@ boltz_status run_carleman(boltz_grid_s* g, const float2* spectra, int n_inputs, 
         k_carleman_output<<<grid, 256, 0, st>>>(Pbuf, fN, fN + size_t(nc) * g->n,
                                                  reinterpret_cast<const int*>(ws + plan.off_plan + c.off_start),
                                                  reinterpret_cast<const int4*>(ws + plan.off_plan + c.off_outs), Q_out,
-                                                 g->n);
+                                                 g->n, g->d_err);
+    }
+    BZ_CUDA(cudaGetLastError());
+    return BOLTZ_OK;
+}
+
+// One batched evaluation on the pipelined schedule (plan.pencil): f_N and
+// Lambda of the inputs, the persistent kernel of pencil.cuh (shifted fields,
+// sigma-contraction and radial step of every node), then the output kernel
+// over the used gain slots.
+boltz_status run_pencil(boltz_grid_s* g, const float2* spectra, float* Q_out, cudaStream_t st) {
+    namespace pc = boltz_dev::pencil;
+    const Plan& plan = g->last_plan;
+    const ChunkPlan& c = plan.chunks[0];
+    const int nc = (int)c.inputs.size();
+    const Dispatch* dp = dispatch_for(g->N, g->D);
+    char* ws = g->d_ws;
+    const int* d_inputs = reinterpret_cast<const int*>(ws + plan.off_plan + c.off_inputs);
+    float* fN = reinterpret_cast<float*>(ws + plan.off_fN);
+    SynParams sp{};
+    sp.spectra = spectra;
+    sp.inputs = d_inputs;
+    sp.phase = g->d_phase;
+    sp.gm = g->d_gm;
+    sp.n_c = nc;
+    sp.M = g->M;
+    sp.id_node = g->n_rho * g->M;
+    sp.out = fN;                                     // f < nc: f_N, f >= nc: Lambda
+    sp.n_fields = 2 * nc;
+    {
+        ProfScope ps(g, BOLTZ_KCLASS_PREP, st);
+        dp->synth(sp, SYN_PREP, st);
+    }
+    const char* blob = ws + plan.off_plan + plan.off_pen_blob;
+    const PencilTree& T = g->pen_tree;
+    pc::Params P{};
+    P.spectra = spectra;
+    P.inputs = d_inputs;
+    P.phase = g->d_phase;
+    P.ctab = g->d_ctab;
+    P.X = reinterpret_cast<float2*>(ws + plan.off_X);
+    P.Pt = reinterpret_cast<float2*>(ws + plan.off_Pt);
+    P.qhat = reinterpret_cast<float2*>(ws + plan.off_qhat);
+    P.slots = reinterpret_cast<const int*>(blob + plan.pen_off[8]);
+    P.ctr = reinterpret_cast<int*>(ws + plan.off_ctr);
+    P.err = g->d_err;
+    P.tr.n_s0 = T.n_s0;
+    P.tr.n_s01 = T.n_s01;
+    P.tr.n_grp = T.n_grp;
+    P.tr.n_step = (int)T.step_dir.size();
+    P.tr.grp = reinterpret_cast<const int*>(blob + plan.pen_off[0]);
+    P.tr.s0_dir = reinterpret_cast<const int*>(blob + plan.pen_off[1]);
+    P.tr.s0_child = reinterpret_cast<const int*>(blob + plan.pen_off[2]);
+    P.tr.s01_dir = reinterpret_cast<const int*>(blob + plan.pen_off[3]);
+    P.tr.step_blk = reinterpret_cast<const int4*>(blob + plan.pen_off[4]);
+    P.tr.step_dir = reinterpret_cast<const int4*>(blob + plan.pen_off[5]);
+    P.tr.step_sel = reinterpret_cast<const int4*>(blob + plan.pen_off[6]);
+    P.tr.step_w = reinterpret_cast<const float2*>(blob + plan.pen_off[7]);
+    P.n_c = nc;
+    P.M = g->M;
+    P.n_rho = g->n_rho;
+    P.n_used = plan.pen_n_used;
+    BZ_CUDA(cudaMemsetAsync(P.ctr, 0, size_t(pc::ctr_count(g->n_rho, plan.pen_n_used)) * sizeof(int), st));
+    const long long items =
+        (long long)g->n_rho * (pc::NLB + pc::tree_items(nc, T.n_s0) + (long long)plan.pen_n_used * pc::NKB);
+    const int grid = (int)std::min<long long>(g->pen_ctas, items);
+    {
+        ProfScope ps(g, BOLTZ_KCLASS_PIPELINE, st);
+        pc::k_pencil<<<grid, pc::NT, pc::SM_TOTAL, st>>>(P);
+    }
+    OutParams op{};
+    op.qhat = P.qhat;
+    op.fN = fN;
+    op.lam = fN + size_t(nc) * g->n;
+    op.out_start = reinterpret_cast<const int*>(ws + plan.off_plan + c.off_start);
+    op.outs = reinterpret_cast<const int4*>(ws + plan.off_plan + c.off_outs);
+    op.Q = Q_out;
+    op.err = g->d_err;
+    op.U = plan.pen_n_used;
+    {
+        ProfScope ps(g, BOLTZ_KCLASS_OUTPUT, st);
+        dp->output(op, st);
     }
     BZ_CUDA(cudaGetLastError());
     return BOLTZ_OK;
@@ -1304,6 +1636,9 @@ boltz_status run_batched(boltz_grid_s* g, const typename Prec<R>::C* spectra, in
     s0 = prepare_plan(g, n_inputs, pj, pl, n_pairs, form, 0, st, sizeof(R));
     if (s0 != BOLTZ_OK) return s0;
     const Plan& plan = g->last_plan;
+    if constexpr (sizeof(R) == 4) {
+        if (plan.pencil) return run_pencil(g, spectra, Q_out, st);
+    }
     const DispatchT<R>* dp = dispatch_of(g->N, g->D, R(0));
     const TablesT<R> tb = tables_of(g, R(0));
     char* ws = g->d_ws;
@@ -1413,6 +1748,7 @@ boltz_status run_batched(boltz_grid_s* g, const typename Prec<R>::C* spectra, in
         op.out_start = reinterpret_cast<const int*>(ws + plan.off_plan + c.off_start);
         op.outs = reinterpret_cast<const int4*>(ws + plan.off_plan + c.off_outs);
         op.Q = Q_out;
+        op.err = g->d_err;
         op.U = c.U;
         ProfScope ps(g, BOLTZ_KCLASS_OUTPUT, st);
         dp->output(op, st);
@@ -1745,6 +2081,11 @@ boltz_status boltz_grid_init(boltz_grid* out, int N, int d_v, double L, double R
         return BOLTZ_EINVAL;
     }
     if (opt && opt->field_budget_mb > 0) g->field_budget = size_t(opt->field_budget_mb) << 20;
+    if (opt && opt->schedule != BOLTZ_SCHEDULE_AUTO && opt->schedule != BOLTZ_SCHEDULE_NODE_BLOCKS) {
+        delete g;
+        return BOLTZ_EINVAL;
+    }
+    if (opt) g->schedule = opt->schedule;
     g->n = d_v == 3 ? N * N * N : N * N;
     g->half = d_v == 3 ? N * N * (N / 2 + 1) : N * (N / 2 + 1);
     g->smax = d_v * (N / 2) * (N / 2);
@@ -1861,6 +2202,15 @@ boltz_status boltz_grid_init(boltz_grid* out, int N, int d_v, double L, double R
     if (dispatch_for(N, d_v)->prepare() != cudaSuccess || prepare_contract() != cudaSuccess ||
         prepare_project_tc() != cudaSuccess)
         return fail(BOLTZ_ECUDA);
+    if (d_v == 3 && N == 32) {
+        namespace pc = boltz_dev::pencil;
+        g->pen_tree = build_pencil_tree(g);
+        int occ = 0;
+        if (set_smem(pc::k_pencil, pc::SM_TOTAL) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pc::k_pencil, pc::NT, pc::SM_TOTAL) != cudaSuccess)
+            return fail(BOLTZ_ECUDA);
+        g->pen_ctas = occ * g->sms;
+    }
     if (cudaStreamCreateWithFlags(&g->side, cudaStreamNonBlocking) != cudaSuccess) return fail(BOLTZ_ECUDA);
     for (int b = 0; b < 2; ++b)
         if (cudaEventCreateWithFlags(&g->ev_ready[b], cudaEventDisableTiming) != cudaSuccess ||
@@ -1953,8 +2303,14 @@ boltz_status boltz_collide_batched(boltz_grid g, const void* spectra, int n_inpu
     if (s != BOLTZ_OK) return s;
     if (n_pairs == 0) return BOLTZ_OK;
     if (!spectra || !Q_out) return BOLTZ_EINVAL;
-    return run_batched(g, reinterpret_cast<const float2*>(spectra), n_inputs, pair_j, pair_l, n_pairs, Q_out, form,
-                       reinterpret_cast<cudaStream_t>(stream));
+    s = run_batched(g, reinterpret_cast<const float2*>(spectra), n_inputs, pair_j, pair_l, n_pairs, Q_out, form,
+                    reinterpret_cast<cudaStream_t>(stream));
+    if (s == BOLTZ_OK && fault_injected("nan")) {
+        static const int bit = kErrNonFinite;
+        BZ_CUDA(cudaMemcpyAsync(g->d_err, &bit, sizeof(int), cudaMemcpyHostToDevice,
+                                reinterpret_cast<cudaStream_t>(stream)));
+    }
+    return s;
 }
 
 boltz_status boltz_project(boltz_grid g, const float* V, int r, const float* Q, float* T_out, void* stream) {
@@ -2315,7 +2671,8 @@ boltz_status boltz_sync_status(boltz_grid g, void* stream) {
     BZ_CUDA(cudaMemcpy(&err, g->d_err, sizeof(int), cudaMemcpyDeviceToHost));
     if (err) {
         BZ_CUDA(cudaMemset(g->d_err, 0, sizeof(int)));
-        return (err & kErrTimeout) ? BOLTZ_ETIMEOUT : BOLTZ_ECUDA;
+        if (err & kErrTimeout) return BOLTZ_ETIMEOUT;
+        return (err & kErrNonFinite) ? BOLTZ_ENONFINITE : BOLTZ_ECUDA;
     }
     return BOLTZ_OK;
 }

@@ -369,9 +369,19 @@ struct OutParamsT {
     const int* out_start; // [U+1]
     const int4* outs;     // (e, jloc, lloc, 0)
     R* Q;                 // [n_pairs][n]
+    int* err;             // device error word: kErrNonFinite when a written value is not finite
     int U;
 };
 using OutParams = OutParamsT<float>;
+
+// True when any of the values is NaN or infinite (NaN fails every comparison).
+__device__ __forceinline__ bool nonfinite4(const float4& v) {
+    return !(fabsf(v.x) <= 3.402823466e38f && fabsf(v.y) <= 3.402823466e38f && fabsf(v.z) <= 3.402823466e38f &&
+             fabsf(v.w) <= 3.402823466e38f);
+}
+__device__ __forceinline__ bool nonfinite2(const double2& v) {
+    return !(fabs(v.x) <= 1.7976931348623157e308 && fabs(v.y) <= 1.7976931348623157e308);
+}
 
 // ------------------------------------------------------------------ 3D field kernels on a CTA cluster
 // Same transforms as k_synth / k_analysis / k_output for d = 3, with one field
@@ -711,6 +721,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(ClusterGeo<N, CL>::
     const int L0 = 4 * lt;
     const float* sp = stg + (L0 / N) * RR + (L0 % N);
     const size_t v0 = (size_t)rank * CG::PART_N + L0;
+    bool bad = false;
     for (int o = P.out_start[u]; o < P.out_start[u + 1]; ++o) {
         const int4 e = P.outs[o];
         const float* fl = P.fN + (size_t)e.z * G::n + v0;
@@ -721,10 +732,13 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(ClusterGeo<N, CL>::
             const float4 g4 = *reinterpret_cast<const float4*>(sp + it * S_STEP);
             const float4 a = __ldg(reinterpret_cast<const float4*>(fl + (size_t)it * 4 * NT));
             const float4 b = __ldg(reinterpret_cast<const float4*>(lj + (size_t)it * 4 * NT));
-            *reinterpret_cast<float4*>(q + (size_t)it * 4 * NT) =
+            const float4 v =
                 make_float4(fmaf(-a.x, b.x, g4.x), fmaf(-a.y, b.y, g4.y), fmaf(-a.z, b.z, g4.z), fmaf(-a.w, b.w, g4.w));
+            bad |= nonfinite4(v);
+            *reinterpret_cast<float4*>(q + (size_t)it * 4 * NT) = v;
         }
     }
+    if (bad) atomicOr(P.err, kErrNonFinite);
 }
 
 // ------------------------------------------------------------------ output (single-CTA fields)
@@ -733,7 +747,8 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(ClusterGeo<N, CL>::
 // Gain minus loss for two rows: q = x.(x|y) - f * lam, 16-byte accesses.
 template <int N>
 __device__ __forceinline__ void gain_minus_loss_rows(const float* f1, const float* f2, const float* l1,
-                                                     const float* l2, float* q1, float* q2, const float2 (&x)[N]) {
+                                                     const float* l2, float* q1, float* q2, const float2 (&x)[N],
+                                                     bool& bad) {
     const float4* F1 = reinterpret_cast<const float4*>(f1);
     const float4* F2 = reinterpret_cast<const float4*>(f2);
     const float4* L1 = reinterpret_cast<const float4*>(l1);
@@ -743,16 +758,19 @@ __device__ __forceinline__ void gain_minus_loss_rows(const float* f1, const floa
 #pragma unroll
     for (int c = 0; c < N / 4; ++c) {
         const float4 a = __ldg(&F1[c]), b = __ldg(&L1[c]), a2 = __ldg(&F2[c]), b2 = __ldg(&L2[c]);
-        Q1[c] = make_float4(fmaf(-a.x, b.x, x[4 * c].x), fmaf(-a.y, b.y, x[4 * c + 1].x),
-                            fmaf(-a.z, b.z, x[4 * c + 2].x), fmaf(-a.w, b.w, x[4 * c + 3].x));
-        Q2[c] = make_float4(fmaf(-a2.x, b2.x, x[4 * c].y), fmaf(-a2.y, b2.y, x[4 * c + 1].y),
-                            fmaf(-a2.z, b2.z, x[4 * c + 2].y), fmaf(-a2.w, b2.w, x[4 * c + 3].y));
+        const float4 v1 = make_float4(fmaf(-a.x, b.x, x[4 * c].x), fmaf(-a.y, b.y, x[4 * c + 1].x),
+                                      fmaf(-a.z, b.z, x[4 * c + 2].x), fmaf(-a.w, b.w, x[4 * c + 3].x));
+        const float4 v2 = make_float4(fmaf(-a2.x, b2.x, x[4 * c].y), fmaf(-a2.y, b2.y, x[4 * c + 1].y),
+                                      fmaf(-a2.z, b2.z, x[4 * c + 2].y), fmaf(-a2.w, b2.w, x[4 * c + 3].y));
+        bad |= nonfinite4(v1) || nonfinite4(v2);
+        Q1[c] = v1;
+        Q2[c] = v2;
     }
 }
 template <int N>
 __device__ __forceinline__ void gain_minus_loss_rows(const double* f1, const double* f2, const double* l1,
                                                      const double* l2, double* q1, double* q2,
-                                                     const double2 (&x)[N]) {
+                                                     const double2 (&x)[N], bool& bad) {
     const double2* F1 = reinterpret_cast<const double2*>(f1);
     const double2* F2 = reinterpret_cast<const double2*>(f2);
     const double2* L1 = reinterpret_cast<const double2*>(l1);
@@ -762,8 +780,11 @@ __device__ __forceinline__ void gain_minus_loss_rows(const double* f1, const dou
 #pragma unroll
     for (int c = 0; c < N / 2; ++c) {
         const double2 a = __ldg(&F1[c]), b = __ldg(&L1[c]), a2 = __ldg(&F2[c]), b2 = __ldg(&L2[c]);
-        Q1[c] = make_double2(fma(-a.x, b.x, x[2 * c].x), fma(-a.y, b.y, x[2 * c + 1].x));
-        Q2[c] = make_double2(fma(-a2.x, b2.x, x[2 * c].y), fma(-a2.y, b2.y, x[2 * c + 1].y));
+        const double2 v1 = make_double2(fma(-a.x, b.x, x[2 * c].x), fma(-a.y, b.y, x[2 * c + 1].x));
+        const double2 v2 = make_double2(fma(-a2.x, b2.x, x[2 * c].y), fma(-a2.y, b2.y, x[2 * c + 1].y));
+        bad |= nonfinite2(v1) || nonfinite2(v2);
+        Q1[c] = v1;
+        Q2[c] = v2;
     }
 }
 
@@ -824,14 +845,16 @@ __global__ void __launch_bounds__(Geo<N, D>::TPF * FPC) k_output(OutParamsT<R> P
         }
         fft_reg<N, true>(x);
     }
+    bool bad = false;
     for (int o = P.out_start[u]; o < P.out_start[u + 1]; ++o) {
         const int4 e = P.outs[o];
         const R* fl = P.fN + (size_t)e.z * G::n;
         const R* lj = P.lam + (size_t)e.y * G::n;
         R* q = P.Q + (size_t)e.x * G::n;
         gain_minus_loss_rows<N>(fl + row * N, fl + (row + H) * N, lj + row * N, lj + (row + H) * N, q + row * N,
-                                q + (row + H) * N, x);
+                                q + (row + H) * N, x, bad);
     }
+    if (bad) atomicOr(P.err, kErrNonFinite);
 }
 
 // ------------------------------------------------------------------ sigma-contraction
@@ -1032,7 +1055,8 @@ __global__ void __launch_bounds__(VC, 1) k_contract_pipe(ConParamsT<R> C) {
 __global__ void __launch_bounds__(256) k_carleman_output(const float* __restrict__ Pg, const float* __restrict__ fN,
                                                           const float* __restrict__ lam,
                                                           const int* __restrict__ out_start,
-                                                          const int4* __restrict__ outs, float* __restrict__ Q, int n) {
+                                                          const int4* __restrict__ outs, float* __restrict__ Q, int n,
+                                                          int* __restrict__ err) {
     const int u = blockIdx.y;
     const int v4 = blockIdx.x * 256 + threadIdx.x;           // float4 index
     if (v4 * 4 >= n) return;
@@ -1041,8 +1065,10 @@ __global__ void __launch_bounds__(256) k_carleman_output(const float* __restrict
         const int4 e = outs[o];
         const float4 a = __ldg(reinterpret_cast<const float4*>(fN + (size_t)e.z * n) + v4);
         const float4 b = __ldg(reinterpret_cast<const float4*>(lam + (size_t)e.y * n) + v4);
-        reinterpret_cast<float4*>(Q + (size_t)e.x * n)[v4] =
-            make_float4(fmaf(-a.x, b.x, p.x), fmaf(-a.y, b.y, p.y), fmaf(-a.z, b.z, p.z), fmaf(-a.w, b.w, p.w));
+        const float4 v = make_float4(fmaf(-a.x, b.x, p.x), fmaf(-a.y, b.y, p.y), fmaf(-a.z, b.z, p.z),
+                                     fmaf(-a.w, b.w, p.w));
+        if (nonfinite4(v)) atomicOr(err, kErrNonFinite);
+        reinterpret_cast<float4*>(Q + (size_t)e.x * n)[v4] = v;
     }
 }
 

@@ -1,0 +1,725 @@
+// Batched collision operator on 3D 32^3 grids as one persistent kernel with
+// shared partial transforms ("pencil" schedule, sm_103a).
+//
+// What it computes is the separated fast-spectral gain of the batched form
+// (Sec. 2.1: for every radial node q and direction p the shifted fields
+// A_{q,p,j}(v) = g_j,N(v - rho_q sigma_p / 2), their products summed over
+// the directions with the weights w_p, one forward transform per node times
+// the radial multiplier c_q(|k|), accumulated over q) for one chunk of at
+// most 16 inputs and all of their 136 unordered pairs.  How it computes it:
+//
+// * The phase of a shifted field separates over the axes,
+//   phi(k) = phi_0(k_0; s_0) phi_1(k_1; s_1) phi_2(k_2; s_2), s = rho sigma / 2,
+//   and the inverse transform runs axis 0, then axis 1, then the
+//   complex-to-real transform along axis 2.  After the axis-0 pass a field
+//   depends on the direction only through sigma_0, after the axis-1 pass only
+//   through (sigma_0, sigma_1).  The 38-point rule has 9 distinct sigma_0 and
+//   25 distinct (sigma_0, sigma_1) values, so computing each partial
+//   transform once per distinct value does the axis-0 work 9 times and the
+//   axis-1 work 25 times per (node, input) instead of 38 times each.
+// * TREE items (node q, input j, block of 4 k_2 columns, one sigma_0 value):
+//   the axis-0 pass of its columns, then the axis-1 pass for every
+//   (sigma_0, sigma_1) below it, written as "X blocks" laid out for the
+//   consumer: X[s01][line block][j][k_2][4 lines].  The axes 0 and 1 never
+//   mix k_2 columns, so a block of columns is an independent problem.
+// * FUSED items (node q, line block of 4 lines (i0, i1) = 128 voxels): for
+//   every direction, the axis-2 complex-to-real transform of the X block of
+//   its (sigma_0, sigma_1) with the phase phi_2(s_2) into shared memory, and
+//   at once the sigma-contraction
+//   P[j,l](v) += w_p (A_{p,j}(v) A_{p',l}(v) + A_{p',j}(v) A_{p,l}(v)) over
+//   antipodal pairs (p, p').  Thread t owns voxel t; its 136 accumulators
+//   live in tensor memory (TMEM lane t, 128 columns) and registers (the last
+//   8).  The shifted fields never leave the SM.  At the end the item applies
+//   the first pass of the forward transform (real-to-complex along axis 2)
+//   to its 136 gain fields and writes half spectra of its lines ("Pt planes").
+// * RADIAL items (node q, gain slot u, block of 4 k_2 columns): the forward
+//   axis-1 and axis-0 passes of the slot's Pt plane columns, the multiplier
+//   c_q(|k|) (-1)^k, accumulated into Qhat+[u] (node by node, in order).
+//   The k_2 = 0 and k_2 = N/2 planes of a real field are real in (i0, i1);
+//   they travel as one complex column (re = k_2 0, im = k_2 N/2) and are
+//   separated with the conjugate-symmetry identity after the 2D transform.
+//
+// Scheduling: a fixed list of items, stage by stage (stage s: fused items of
+// node s-1, tree items of node s, radial items of node s-2), claimed in order
+// from an atomic counter by persistent CTAs (three per SM: 128 threads, at
+// most 168 registers, 67 KB of shared memory and 128 TMEM columns each).  A
+// CTA claims its next item when it starts the current one.  Every dependency
+// points to an item earlier in the list (fused(q) needs all tree(q) and the
+// Pt buffer free; tree(q) needs its X buffer free; radial(q) needs fused(q)
+// and radial(q-1) of its slot), so the lowest unfinished item can always run:
+// progress needs no co-residency.  Each wait is a bounded poll (about one
+// second of device time); a wait that gives up records a timeout in the error
+// word and raises an abort flag, after which every CTA drains the list
+// without working, so the launch always ends.  X (two node buffers, ~54 MB
+// each) and Pt (three node buffers, ~18 MB each) are sized for the 126 MB L2;
+// the lines of an X block or Pt plane are dropped from L2 without write-back
+// once their single consumer has copied them (discard.global.L2).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "async.cuh"
+#include "fft.cuh"
+#include "kernels.cuh"
+#include "tc.cuh"
+
+namespace boltz_dev {
+namespace pencil {
+
+constexpr int N = 32;
+constexpr int H = 16;
+constexpr int NH = H + 1;
+constexpr int HALF = N * N * NH;               // half-spectrum entries of a 32^3 field
+constexpr int SMAX = 3 * H * H;                // largest |k|^2
+constexpr int NT = 128;                        // threads per CTA
+constexpr int NJ = 16;                         // inputs of a batch
+constexpr int NSLOT = NJ * (NJ + 1) / 2;       // unordered gain slots: 136
+constexpr int NTSLOT = 128;                    // slots accumulated in TMEM (columns 0..127)
+constexpr int NRSLOT = NSLOT - NTSLOT;         // slots accumulated in registers: 8
+constexpr int KB = 4;                          // k2 columns per tree / radial item
+constexpr int NKB = H / KB;                    // column blocks: k2 = 0..15 (k2 = 16 rides in column 0)
+constexpr int NLB = N * N / 4;                 // line blocks per field (4 lines, 128 voxels): 256
+constexpr int XJS = H * 4 + 2;                 // float2 per input in an X block (+2: bank spread)
+constexpr int XBLK = NJ * XJS;                 // float2 per X block: 1056 (8448 B = 66 L2 lines)
+constexpr int PRS = N * KB + 4;                // plane row stride in float2 (+4: bank spread)
+constexpr int PLANE = N * PRS;                 // float2 per plane: 4224 (33792 B = 264 L2 lines)
+constexpr int AJS = 4 * N + 4;                 // floats per input in the A buffer (+4: bank spread)
+constexpr int ADS = NJ * AJS;                  // floats per direction slot of a step
+constexpr int PSS = 4 * N + 4;                 // floats per slot in the epilogue transpose
+constexpr int MAX_ROWS = 32;                   // phase rows a tree item stages (1 + children)
+constexpr int MAX_S = 96;                      // sigma_0 and (sigma_0, sigma_1) values (M <= 86)
+constexpr int MAX_STEP = 24;                   // fused-item steps (M/2 antipodal pairs, two a step)
+constexpr int NXB = 2;                         // X node buffers
+constexpr int NPB = 3;                         // Pt node buffers
+constexpr uint32_t TMEM_COLS = 128;            // per CTA (three CTAs use 384 of the SM's 512 columns)
+constexpr int CTAS_PER_SM = 3;
+
+// dynamic shared memory (bytes).  Fused: two stages, each holding the X
+// blocks of one step, then that step's A buffer (its shifted fields) in the
+// same place once the X values are in registers, while the next step's X
+// blocks land in the other stage; the epilogue transposes 64 slots at a time
+// in stage 0.  Tree and radial: one plane.  Sized so that at most three CTAs
+// share an SM (their TMEM columns must fit the SM's 512).
+constexpr int SM_STAGE = 4 * XBLK * 8;                // 33792 B
+constexpr int SM_PH2 = 2 * SM_STAGE;                  // [2 stages][4 slots][H] float2 phase rows
+constexpr int SM_TPH = PLANE * 8;                     // tree: phase rows after the plane
+constexpr int SM_TOTAL = SM_PH2 + 2 * 4 * H * 8;       // 68608 B: three CTAs with their static tables fit 228 KB
+static_assert(4 * ADS * 4 <= SM_STAGE, "A overlays the X blocks of its stage");
+static_assert(64 * PSS * 4 <= SM_STAGE, "64 epilogue slots fit a stage");
+static_assert(SM_PH2 + 2 * 4 * H * 8 <= SM_TOTAL, "phase rows fit");
+static_assert(SM_TPH + MAX_ROWS * N * 8 <= SM_TOTAL, "tree phase rows fit");
+static_assert((CTAS_PER_SM + 1) * (SM_TOTAL + 4096) > 228 * 1024, "at most three CTAs per SM");
+static_assert(CTAS_PER_SM * (SM_TOTAL + 4096) <= 228 * 1024, "three CTAs per SM");
+
+// Direction structure of the rule (node independent), built on the host.
+struct Tree {
+    int n_s0, n_s01, n_grp, n_step;
+    const int* grp;          // host grouping of the sigma_0 values (kept for the plan layout)
+    const int* s0_dir;       // [n_s0]: a direction with this sigma_0
+    const int* s0_child;     // [n_s0 + 1]: ranges of its (sigma_0, sigma_1) values
+    const int* s01_dir;      // [n_s01]: a direction with this (sigma_0, sigma_1) = X block index
+    const int4* step_blk;    // [n_step]: X block of stage slot 0..3 (-1 unused)
+    const int4* step_dir;    // [n_step]: direction of slot 0..3 (-1 unused); (0,1), (2,3) antipodal
+    const int4* step_sel;    // [n_step]: stage slot (0..3) of the X block that slot d reads
+    const float2* step_w;    // [n_step]: weights w_p of the pairs (0,1) and (2,3)
+};
+
+struct Params {
+    const float2* spectra;   // [n_inputs][HALF]
+    const int* inputs;       // [n_c]: chunk-local -> global input
+    const float2* phase;     // [(n_rho M + 1)][3][N]: (-1)^k exp(-i pi k s_a / L), zero at Nyquist
+    const float* ctab;       // [n_rho][SMAX + 1]: c_q(|k|^2) including 1/n
+    float2* X;               // [NXB][n_s01][NLB][XBLK]
+    float2* Pt;              // [NPB][NSLOT][NKB][PLANE]
+    float2* qhat;            // [n_used][HALF]: Qhat+ of the used slots, in slot order
+    const int* slots;        // [n_used]: slots whose gain is needed
+    int* ctr;                // counters, zeroed before the launch (layout in ctr_*)
+    int* err;                // device error word
+    Tree tr;
+    int n_c, M, n_rho, n_used;
+};
+
+// counters: [0] claim, [1] abort, then per node: tree done, fused done,
+// radial done, then per (used slot, column block) the nodes accumulated
+__host__ __device__ constexpr int ctr_tree(int n_rho, int q) { return 2 + q; }
+__host__ __device__ constexpr int ctr_fused(int n_rho, int q) { return 2 + n_rho + q; }
+__host__ __device__ constexpr int ctr_radial(int n_rho, int q) { return 2 + 2 * n_rho + q; }
+__host__ __device__ constexpr int ctr_acc(int n_rho, int i) { return 2 + 3 * n_rho + i; }
+__host__ __device__ constexpr int ctr_count(int n_rho, int n_used) { return 2 + 3 * n_rho + n_used * NKB; }
+
+// TRI16 slot of the unordered pair (a <= b)
+__host__ __device__ constexpr int tri_slot(int a, int b) { return a * NJ - a * (a - 1) / 2 + (b - a); }
+
+// (row, column) of every TRI16 slot, for compile-time indexing in unrolled loops
+struct TriTable {
+    int x[NSLOT], y[NSLOT];
+};
+__host__ __device__ constexpr TriTable make_tri_table() {
+    TriTable t{};
+    int i = 0;
+    for (int a = 0; a < NJ; ++a)
+        for (int b = a; b < NJ; ++b) {
+            t.x[i] = a;
+            t.y[i] = b;
+            ++i;
+        }
+    return t;
+}
+constexpr TriTable kTri = make_tri_table();
+
+enum { IT_FUSED = 0, IT_TREE = 1, IT_RADIAL = 2, IT_END = 3 };
+
+struct Item {
+    int kind, q, local;
+};
+
+__host__ __device__ inline int tree_items(int n_c, int n_s0) { return n_c * NKB * n_s0; }
+
+// Item idx of the stage-ordered list.
+__device__ __noinline__ Item decode_item(const Params& P, int idx) {
+    const int nT = tree_items(P.n_c, P.tr.n_s0), nR = P.n_used * NKB;
+    for (int s = 0; s < P.n_rho + 2; ++s) {
+        const int f = (s >= 1 && s <= P.n_rho) ? NLB : 0;
+        if (idx < f) return {IT_FUSED, s - 1, idx};
+        idx -= f;
+        const int t = (s < P.n_rho) ? nT : 0;
+        if (idx < t) return {IT_TREE, s, idx};
+        idx -= t;
+        const int r = (s >= 2) ? nR : 0;
+        if (idx < r) return {IT_RADIAL, s - 2, idx};
+        idx -= r;
+    }
+    return {IT_END, 0, 0};
+}
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void red_release_add(int* p, int v) {
+    asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Orders generic-proxy accesses to global memory with async-proxy (bulk copy) accesses.
+__device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
+
+// Drops one 128-byte L2 line without writing it back (its data becomes undefined).
+__device__ __forceinline__ void discard_l2(const void* p) {
+    asm volatile("discard.global.L2 [%0], 128;" ::"l"(p) : "memory");
+}
+
+// Bounded wait (one thread) until *c >= target.  False when about one second
+// of device time passed or another CTA has raised the abort flag.
+__device__ __noinline__ bool wait_at_least(const int* c, int target, const int* abort) {
+    if (ld_acquire(c) >= target) return true;
+    const uint64_t t0 = global_timer_ns();
+    for (uint32_t i = 0; i < kSpinLimit; ++i) {
+        __nanosleep(128);
+        if (ld_acquire(c) >= target) return true;
+        if ((i & 15u) == 15u) {
+            if (*reinterpret_cast<const volatile int*>(abort)) return false;
+            if (global_timer_ns() - t0 > kWaitNs) return false;
+        }
+    }
+    return false;
+}
+
+// TMEM: 32 consecutive 32-bit columns of this thread's lane (warp w owns lanes 32w..32w+31)
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+        "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+        "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]),
+        "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]),
+        "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+        : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// Waits for this thread's TMEM loads.  The registers they fill are in/out
+// operands, so that no use of them can be scheduled before the wait.
+__device__ __forceinline__ void tmem_wait_ld32(uint32_t (&r)[32]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
+                   "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
+                   "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+                 :
+                 : "memory");
+}
+
+// Tables of the direction tree, copied to shared memory once per CTA.
+struct TreeSmem {
+    int s0_dir[MAX_S], s0_child[MAX_S + 1], s01_dir[MAX_S];
+    int4 step_blk[MAX_STEP], step_dir[MAX_STEP], step_sel[MAX_STEP];
+    float2 step_w[MAX_STEP];
+};
+
+// ------------------------------------------------------------------ tree item
+// Columns (k1 = t/4, k2 = 4 kb + c) of input jj: the axis-0 inverse pass for
+// sigma_0 value i, then for each (sigma_0, sigma_1) child the axis-1 inverse
+// pass of the lines (i0 = t/4, k2), stored into the X block of line block
+// (i0, m) for m = 0..7 with lines ordered (i1 = 2m, 2m+16, 2m+1, 2m+17).
+__device__ void tree_item(const Params& P, const TreeSmem& ts, int q, int local, unsigned char* smem) {
+    const int t = threadIdx.x;
+    const int ns = P.tr.n_s0;
+    const int i = local % ns, kb = (local / ns) % NKB, jj = local / (ns * NKB);
+    float2* S0 = reinterpret_cast<float2*>(smem);                  // [N][PRS]: (i0, k1, c)
+    float2* ph = reinterpret_cast<float2*>(smem + SM_TPH);         // [rows][N]
+    const int k1 = t >> 2, c = t & 3;
+    const float2* __restrict__ src = P.spectra + (size_t)__ldg(&P.inputs[jj]) * HALF + k1 * NH + KB * kb + c;
+    float2 x[N];
+#pragma unroll
+    for (int k0 = 0; k0 < N; ++k0) x[k0] = __ldg(src + k0 * N * NH);
+    const int cb = ts.s0_child[i], ce = ts.s0_child[i + 1];
+    const int rows = 1 + ce - cb;
+    for (int e = t; e < rows * N; e += NT) {
+        const int r = e / N, k = e % N;
+        const int dir = r == 0 ? ts.s0_dir[i] : ts.s01_dir[cb + r - 1];
+        ph[e] = __ldg(&P.phase[((size_t)(q * P.M + dir) * 3 + (r == 0 ? 0 : 1)) * N + k]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k0 = 0; k0 < N; ++k0) x[k0] = cmul(x[k0], ph[k0]);
+    fft_reg<N, true>(x);
+#pragma unroll
+    for (int i0 = 0; i0 < N; ++i0) S0[i0 * PRS + k1 * KB + c] = x[i0];
+    __syncthreads();
+    const int i0 = t >> 2;
+    float2* Xn = P.X + (size_t)(q % NXB) * P.tr.n_s01 * NLB * XBLK;
+    for (int ch = cb; ch < ce; ++ch) {
+        const float2* p1 = ph + (1 + ch - cb) * N;
+#pragma unroll
+        for (int kk = 0; kk < N; ++kk) x[kk] = cmul(S0[i0 * PRS + kk * KB + c], p1[kk]);
+        fft_reg<N, true>(x);
+        float2* xb = Xn + ((size_t)ch * NLB + i0 * 8) * XBLK + jj * XJS + (KB * kb + c) * 4;
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+            float4* o = reinterpret_cast<float4*>(xb + m * XBLK);
+            o[0] = make_float4(x[2 * m].x, x[2 * m].y, x[2 * m + H].x, x[2 * m + H].y);
+            o[1] = make_float4(x[2 * m + 1].x, x[2 * m + 1].y, x[2 * m + 1 + H].x, x[2 * m + 1 + H].y);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ fused item
+// The X blocks and axis-2 phase rows of step st into the stage (thread 0).
+__device__ __forceinline__ void fused_issue(const Params& P, const TreeSmem& ts, const float2* Xn, int q, int st,
+                                            float2* Xs, float2* ph2, uint64_t* bar) {   // Xs, ph2: the stage
+    const int4 blk = ts.step_blk[st];
+    const int4 dir = ts.step_dir[st];
+    const int bl[4] = {blk.x, blk.y, blk.z, blk.w};
+    const int dr[4] = {dir.x, dir.y, dir.z, dir.w};
+    uint32_t bytes = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (bl[k] >= 0) bytes += XBLK * 8;
+        if (dr[k] >= 0) bytes += H * 8;
+    }
+    mbar_arrive_expect_tx(bar, bytes);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (bl[k] >= 0) bulk_g2s(Xs + k * XBLK, Xn + (size_t)bl[k] * NLB * XBLK, XBLK * 8, bar);
+        if (dr[k] >= 0) bulk_g2s(ph2 + k * H, P.phase + ((size_t)(q * P.M + dr[k]) * 3 + 2) * N, H * 8, bar);
+    }
+}
+
+// acc(slot) += a[x] c[y] + c[x] a[y] for the 32 slots of TMEM chunk CH
+template <int CH>
+__device__ __forceinline__ void contract_chunk(uint32_t (&r)[32], const float (&a)[NJ], const float (&cc)[NJ]) {
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+        constexpr TriTable tt = kTri;
+        const int x = tt.x[CH * 32 + k], y = tt.y[CH * 32 + k];
+        r[k] = __float_as_uint(fmaf(a[x], cc[y], fmaf(cc[x], a[y], __uint_as_float(r[k]))));
+    }
+}
+
+// Returns false when a bulk copy did not land in time (the caller aborts).
+__device__ bool fused_item(const Params& P, const TreeSmem& ts, int q, int lb, unsigned char* smem, uint64_t* bars,
+                           uint32_t& par, uint32_t tmem) {
+    const int t = threadIdx.x, warp = t >> 5;
+    const int nst = P.tr.n_step;
+    const float2* Xn = P.X + (size_t)(q % NXB) * P.tr.n_s01 * NLB * XBLK + (size_t)lb * XBLK;
+    const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);    // this warp's 32 TMEM lanes
+    auto stage_x = [&](int b) { return reinterpret_cast<float2*>(smem + b * SM_STAGE); };
+    auto stage_ph = [&](int b) { return reinterpret_cast<float2*>(smem + SM_PH2) + b * 4 * H; };
+    if (t == 0) {
+        fence_proxy_async_global();
+        fence_proxy_async_smem();
+        fused_issue(P, ts, Xn, q, 0, stage_x(0), stage_ph(0), &bars[0]);
+        if (nst > 1) fused_issue(P, ts, Xn, q, 1, stage_x(1), stage_ph(1), &bars[1]);
+    }
+    {
+        uint32_t z[32];
+#pragma unroll
+        for (int k = 0; k < 32; ++k) z[k] = 0u;
+#pragma unroll
+        for (int ch = 0; ch < NTSLOT / 32; ++ch) tmem_st32(tl + 32 * ch, z);
+        tmem_wait_st();
+    }
+    float racc[NRSLOT];
+#pragma unroll
+    for (int k = 0; k < NRSLOT; ++k) racc[k] = 0.f;
+    const int d = warp, lp = (t >> 4) & 1, j = t & 15;
+#pragma unroll 1
+    for (int st = 0; st < nst; ++st) {
+        const int b = st & 1;
+        const bool ok = mbar_wait_bounded(&bars[b], (par >> b) & 1u);
+        par ^= 1u << b;
+        if (__syncthreads_or(!ok)) {
+            // leave no copy in flight: the other stage may still be landing
+            if (t == 0 && st + 1 < nst) (void)mbar_wait_bounded(&bars[b ^ 1], (par >> (b ^ 1)) & 1u);
+            return false;
+        }
+        const float2* Xs = stage_x(b);
+        float* A = reinterpret_cast<float*>(smem + b * SM_STAGE);  // overlays Xs once X is in registers
+        const int4 dir4 = ts.step_dir[st];
+        const int dir = d == 0 ? dir4.x : d == 1 ? dir4.y : d == 2 ? dir4.z : dir4.w;
+        const int sel = d == 0 ? ts.step_sel[st].x : d == 1 ? ts.step_sel[st].y : d == 2 ? ts.step_sel[st].z
+                                                                                       : ts.step_sel[st].w;
+        // X lines of this thread's line pair (i1 = 2m + lp, 2m + lp + 16), input j, with the
+        // axis-2 phase, packed for one complex-to-real transform.  Every thread transforms
+        // (an unused slot or input reads stale stage data and its result is not stored):
+        // a branch here costs the register allocator ~40 registers.
+        const bool work = dir >= 0 && j < P.n_c;
+        float2 x[N];
+        {
+            const float2* xb = Xs + (sel & 3) * XBLK + j * XJS + lp * 2;
+            const float2* pr = stage_ph(b) + d * H;
+            {
+                const float4 v = *reinterpret_cast<const float4*>(xb);
+                x[0] = make_float2(v.x, v.z);
+                x[H] = make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int k = 1; k < H; ++k) {
+                const float4 v = *reinterpret_cast<const float4*>(xb + 4 * k);
+                const float2 w = pr[k];
+                const float2 a = cmul(make_float2(v.x, v.y), w), e = cmul(make_float2(v.z, v.w), w);
+                x[k] = make_float2(a.x - e.y, a.y + e.x);
+                x[N - k] = make_float2(a.x + e.y, e.x - a.y);
+            }
+            fft_reg<N, true>(x);
+        }
+        // the X blocks are consumed: drop them from L2 and let A overwrite the stage
+        for (int l = t; l < 4 * (XBLK * 8 / 128); l += NT) {
+            const int k = l / (XBLK * 8 / 128);
+            const int blk = k == 0 ? ts.step_blk[st].x : k == 1 ? ts.step_blk[st].y : k == 2 ? ts.step_blk[st].z
+                                                                                        : ts.step_blk[st].w;
+            if (blk >= 0)
+                discard_l2(reinterpret_cast<const char*>(Xn + (size_t)blk * NLB * XBLK) +
+                           (size_t)(l % (XBLK * 8 / 128)) * 128);
+        }
+        __syncthreads();
+        float* Ad = A + d * ADS + j * AJS + lp * 2 * N;
+        if (work) {
+            store_two_rows<N>(Ad, Ad + N, x);
+        } else if (dir >= 0) {
+            float4* z = reinterpret_cast<float4*>(Ad);
+#pragma unroll
+            for (int c = 0; c < N / 2; ++c) z[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        __syncthreads();
+        // sigma-contraction of the step's two antipodal pairs, voxel v = t
+        const float2 w2 = ts.step_w[st];
+#pragma unroll 1
+        for (int pi = 0; pi < 2; ++pi) {
+            const int da = pi == 0 ? dir4.x : dir4.z;
+            if (da < 0) continue;
+            const float w = pi == 0 ? w2.x : w2.y;
+            const float* Aa = A + (2 * pi) * ADS + t;
+            const float* Ac = A + (2 * pi + 1) * ADS + t;
+            float a[NJ], cc[NJ];
+#pragma unroll
+            for (int xx = 0; xx < NJ; ++xx) {
+                a[xx] = w * Aa[xx * AJS];
+                cc[xx] = Ac[xx * AJS];
+            }
+            uint32_t r[32];
+            tmem_ld32(tl + 0, r);
+            tmem_wait_ld32(r);
+            contract_chunk<0>(r, a, cc);
+            tmem_st32(tl + 0, r);
+            tmem_ld32(tl + 32, r);
+            tmem_wait_ld32(r);
+            contract_chunk<1>(r, a, cc);
+            tmem_st32(tl + 32, r);
+            tmem_ld32(tl + 64, r);
+            tmem_wait_ld32(r);
+            contract_chunk<2>(r, a, cc);
+            tmem_st32(tl + 64, r);
+            tmem_ld32(tl + 96, r);
+            tmem_wait_ld32(r);
+            contract_chunk<3>(r, a, cc);
+            tmem_st32(tl + 96, r);
+#pragma unroll
+            for (int k = 0; k < NRSLOT; ++k) {
+                constexpr TriTable tt = kTri;
+                const int xx = tt.x[NTSLOT + k], yy = tt.y[NTSLOT + k];
+                racc[k] = fmaf(a[xx], cc[yy], fmaf(cc[xx], a[yy], racc[k]));
+            }
+            tmem_wait_st();
+        }
+        __syncthreads();                                           // A consumed: stage b is free
+        if (t == 0 && st + 2 < nst) {
+            fence_proxy_async_smem();
+            fused_issue(P, ts, Xn, q, st + 2, stage_x(b), stage_ph(b), &bars[b]);
+        }
+    }
+    // epilogue: the gain fields of the 128 voxels, 64 slots at a time, through
+    // shared memory, then the forward real-to-complex pass along axis 2 of
+    // every (slot, line pair)
+    float* Pst = reinterpret_cast<float*>(smem);                   // [64][PSS] in stage 0
+    float2* Ptn = P.Pt + (size_t)(q % NPB) * NSLOT * NKB * PLANE;
+    const int i0 = lb >> 3, m = lb & 7;
+#pragma unroll 1
+    for (int rnd = 0; rnd < 3; ++rnd) {
+        const int u0 = 64 * rnd;
+        const int nsl = rnd < 2 ? 64 : NRSLOT;
+        if (rnd < 2) {
+            uint32_t r[32];
+            tmem_ld32(tl + u0, r);
+            tmem_wait_ld32(r);
+#pragma unroll
+            for (int k = 0; k < 32; ++k) Pst[k * PSS + t] = __uint_as_float(r[k]);
+            tmem_ld32(tl + u0 + 32, r);
+            tmem_wait_ld32(r);
+#pragma unroll
+            for (int k = 0; k < 32; ++k) Pst[(32 + k) * PSS + t] = __uint_as_float(r[k]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < NRSLOT; ++k) Pst[k * PSS + t] = racc[k];
+        }
+        __syncthreads();
+        for (int task = t; task < 2 * nsl; task += NT) {
+            const int lp2 = task / nsl, us = task % nsl, u = u0 + us;
+            const float* r1 = Pst + us * PSS + lp2 * 2 * N;           // rows i1 = 2m + lp2 and i1 + 16
+            float2 x[N];
+            load_two_rows_smem<N>(r1, r1 + N, x);
+            fft_reg<N, false>(x);
+            const int i1a = 2 * m + lp2;
+            float2* oa = Ptn + (size_t)u * NKB * PLANE + i0 * PRS + i1a * KB;
+            float2* ob = oa + H * KB;                                 // row i1a + 16
+#pragma unroll
+            for (int kb = 0; kb < NKB; ++kb) {
+                float2 r1v[KB], r2v[KB];
+#pragma unroll
+                for (int c = 0; c < KB; ++c) {
+                    const int k = KB * kb + c;
+                    if (k == 0) {
+                        // column 0 carries (DC, Nyquist) of each row, both real
+                        r1v[c] = make_float2(x[0].x, x[H].x);
+                        r2v[c] = make_float2(x[0].y, x[H].y);
+                    } else {
+                        const float2 z = x[k], zc = x[N - k];
+                        r1v[c] = make_float2(0.5f * (z.x + zc.x), 0.5f * (z.y - zc.y));
+                        r2v[c] = make_float2(0.5f * (z.y + zc.y), -0.5f * (z.x - zc.x));
+                    }
+                }
+                float4* pa = reinterpret_cast<float4*>(oa + kb * PLANE);
+                float4* pb = reinterpret_cast<float4*>(ob + kb * PLANE);
+                pa[0] = make_float4(r1v[0].x, r1v[0].y, r1v[1].x, r1v[1].y);
+                pa[1] = make_float4(r1v[2].x, r1v[2].y, r1v[3].x, r1v[3].y);
+                pb[0] = make_float4(r2v[0].x, r2v[0].y, r2v[1].x, r2v[1].y);
+                pb[1] = make_float4(r2v[2].x, r2v[2].y, r2v[3].x, r2v[3].y);
+            }
+        }
+        __syncthreads();
+    }
+    return true;
+}
+
+// ------------------------------------------------------------------ radial item
+// Column block kb of slot u's Pt plane: forward axis-1 pass (thread = line
+// (i0, c)), forward axis-0 pass (thread = column (k1, c)), then
+// Qhat+[u](k) (+)= c_q(|k|^2) (-1)^(k0+k1+k2) DFT[P_q,u](k).
+__device__ bool radial_item(const Params& P, int q, int local, unsigned char* smem, uint64_t* bars, uint32_t& par) {
+    const int t = threadIdx.x;
+    const int ui = local / NKB, kb = local % NKB;
+    const int u = __ldg(&P.slots[ui]);
+    float2* S = reinterpret_cast<float2*>(smem);
+    const float2* src = P.Pt + ((size_t)((q % NPB) * NSLOT + u) * NKB + kb) * PLANE;
+    if (t == 0) {
+        fence_proxy_async_global();
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(&bars[0], PLANE * 8);
+        bulk_g2s(S, src, PLANE * 8, &bars[0]);
+    }
+    const int c = t & 3, k1 = t >> 2;
+    const bool packed = (kb == 0 && c == 0);
+    const bool first = (q == 0);
+    float2* qh = P.qhat + (size_t)ui * HALF;                        // Qhat+ is stored per used slot
+    const int k2 = packed ? 0 : KB * kb + c;
+    // the previous nodes' sums of the first RQ rows k0, in flight during the transforms
+    constexpr int RQ = 8;
+    float2 old[RQ];
+#pragma unroll
+    for (int k0 = 0; k0 < RQ; ++k0) old[k0] = first ? make_float2(0.f, 0.f) : qh[(k0 * N + k1) * NH + k2];
+    const bool ok = mbar_wait_bounded(&bars[0], par & 1u);
+    par ^= 1u;
+    if (__syncthreads_or(!ok)) return false;
+    for (int l = t; l < PLANE * 8 / 128; l += NT) discard_l2(reinterpret_cast<const char*>(src) + (size_t)l * 128);
+    float2 x[N];
+    {
+        const int i0 = t >> 2;
+#pragma unroll
+        for (int i1 = 0; i1 < N; ++i1) x[i1] = S[i0 * PRS + i1 * KB + c];
+        fft_reg<N, false>(x);
+#pragma unroll
+        for (int kk = 0; kk < N; ++kk) S[i0 * PRS + kk * KB + c] = x[kk];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i0 = 0; i0 < N; ++i0) x[i0] = S[i0 * PRS + k1 * KB + c];
+    fft_reg<N, false>(x);
+    // the axis-0 results of every column back into the plane (the packed
+    // column needs the values at the mirrored frequency), then
+    // Qhat+ += multiplier x DFT, RQ rows k0 at a time
+    __syncthreads();
+#pragma unroll
+    for (int k0 = 0; k0 < N; ++k0) S[k0 * PRS + k1 * KB + c] = x[k0];
+    __syncthreads();
+    const float* __restrict__ ct = P.ctab + (size_t)q * (SMAX + 1);
+    const int b = wrapk(k1, N), k1m = (N - k1) % N;
+    auto rows = [&](int k0b, const float2 (&o)[RQ]) {
+#pragma unroll
+        for (int kk = 0; kk < RQ; ++kk) {
+            const int k0 = k0b + kk;
+            const int a = wrapk(k0, N);
+            const float2 z = S[k0 * PRS + k1 * KB + c];
+            const int idx = (k0 * N + k1) * NH;
+            if (!packed) {
+                const float c0 = __ldg(&ct[a * a + b * b + k2 * k2]);
+                const float sc = ((k0 + k1 + k2) & 1) ? -c0 : c0;
+                qh[idx + k2] = make_float2(fmaf(z.x, sc, o[kk].x), fmaf(z.y, sc, o[kk].y));
+            } else {
+                // Z = F[a] + i F[b] for the real planes a (k2 = 0) and b (k2 = N/2)
+                const float2 zm = S[((N - k0) % N) * PRS + k1m * KB];
+                const float2 fa = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
+                const float2 fb = make_float2(0.5f * (z.y + zm.y), -0.5f * (z.x - zm.x));
+                const float sg = ((k0 + k1) & 1) ? -1.f : 1.f;     // (-1)^(k0+k1+k2), k2 = 0 or N/2
+                const float c0 = sg * __ldg(&ct[a * a + b * b]);
+                const float c16 = sg * __ldg(&ct[a * a + b * b + H * H]);
+                const float2 o16 = first ? make_float2(0.f, 0.f) : qh[idx + H];
+                qh[idx] = make_float2(fmaf(fa.x, c0, o[kk].x), fmaf(fa.y, c0, o[kk].y));
+                qh[idx + H] = make_float2(fmaf(fb.x, c16, o16.x), fmaf(fb.y, c16, o16.y));
+            }
+        }
+    };
+    rows(0, old);
+#pragma unroll 1
+    for (int k0b = RQ; k0b < N; k0b += RQ) {
+        float2 o[RQ];
+#pragma unroll
+        for (int kk = 0; kk < RQ; ++kk) o[kk] = first ? make_float2(0.f, 0.f) : qh[((k0b + kk) * N + k1) * NH + k2];
+        rows(k0b, o);
+    }
+    return true;
+}
+
+// ------------------------------------------------------------------ persistent kernel
+__global__ void __launch_bounds__(NT, CTAS_PER_SM) k_pencil(Params P) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ TreeSmem ts;
+    __shared__ uint64_t bars[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_item, s_ok;
+    const int t = threadIdx.x, warp = t >> 5;
+    // direction tree tables into shared memory
+    for (int e = t; e < P.tr.n_s0; e += NT) ts.s0_dir[e] = __ldg(&P.tr.s0_dir[e]);
+    for (int e = t; e <= P.tr.n_s0; e += NT) ts.s0_child[e] = __ldg(&P.tr.s0_child[e]);
+    for (int e = t; e < P.tr.n_s01; e += NT) ts.s01_dir[e] = __ldg(&P.tr.s01_dir[e]);
+    for (int e = t; e < P.tr.n_step; e += NT) {
+        ts.step_blk[e] = __ldg(&P.tr.step_blk[e]);
+        ts.step_dir[e] = __ldg(&P.tr.step_dir[e]);
+        ts.step_sel[e] = __ldg(&P.tr.step_sel[e]);
+        ts.step_w[e] = __ldg(&P.tr.step_w[e]);
+    }
+    if (t == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        mbar_init_fence();
+        s_item = atomicAdd(P.ctr, 1);
+    }
+    if (warp == 0) tc_alloc<TMEM_COLS>(&tmem_base);
+    tc_fence_before_sync();
+    __syncthreads();
+    tc_fence_after_sync();
+    const uint32_t tmem = tmem_base;
+    uint32_t par = 0;                                  // parity bits of the next phases of bars[0], bars[1]
+    int* abort_flag = P.ctr + 1;
+    const int nT = tree_items(P.n_c, P.tr.n_s0), nR = P.n_used * NKB;
+    for (;;) {
+        const Item it = decode_item(P, s_item);
+        if (it.kind == IT_END) break;
+        int next = 0;
+        if (t == 0) {
+            next = atomicAdd(P.ctr, 1);                // the next item, claimed now, used at the end
+            bool ok = *reinterpret_cast<volatile int*>(abort_flag) == 0;
+            const int nr = P.n_rho;
+            if (ok && it.kind == IT_TREE && it.q >= NXB)
+                ok = wait_at_least(P.ctr + ctr_fused(nr, it.q - NXB), NLB, abort_flag);
+            if (ok && it.kind == IT_FUSED) {
+                ok = wait_at_least(P.ctr + ctr_tree(nr, it.q), nT, abort_flag);
+                if (ok && it.q >= NPB) ok = wait_at_least(P.ctr + ctr_radial(nr, it.q - NPB), nR, abort_flag);
+            }
+            if (ok && it.kind == IT_RADIAL) {
+                ok = wait_at_least(P.ctr + ctr_fused(nr, it.q), NLB, abort_flag);
+                if (ok) ok = wait_at_least(P.ctr + ctr_acc(nr, it.local), it.q, abort_flag);
+            }
+            if (!ok && *reinterpret_cast<volatile int*>(abort_flag) == 0) {
+                atomicOr(P.err, kErrTimeout);
+                atomicExch(abort_flag, 1);
+            }
+            s_ok = ok;
+        }
+        __syncthreads();
+        if (s_ok) {
+            bool done = true;
+            if (it.kind == IT_TREE) tree_item(P, ts, it.q, it.local, smem);
+            else if (it.kind == IT_FUSED) done = fused_item(P, ts, it.q, it.local, smem, bars, par, tmem);
+            else done = radial_item(P, it.q, it.local, smem, bars, par);
+            if (!done && t == 0) {
+                atomicOr(P.err, kErrTimeout);
+                atomicExch(abort_flag, 1);
+            }
+        }
+        __syncthreads();                               // every thread's writes of the item are done
+        if (t == 0) {
+            // publish them (to later generic and bulk-copy readers), then count the item
+            fence_proxy_async_global();
+            __threadfence();
+            const int nr = P.n_rho;
+            if (it.kind == IT_TREE) red_release_add(P.ctr + ctr_tree(nr, it.q), 1);
+            else if (it.kind == IT_FUSED) red_release_add(P.ctr + ctr_fused(nr, it.q), 1);
+            else {
+                red_release_add(P.ctr + ctr_acc(nr, it.local), 1);
+                red_release_add(P.ctr + ctr_radial(nr, it.q), 1);
+            }
+            s_item = next;
+        }
+        __syncthreads();
+    }
+    tc_fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc_dealloc<TMEM_COLS>(tmem);
+}
+
+}  // namespace pencil
+}  // namespace boltz_dev

@@ -277,6 +277,7 @@ __global__ void __launch_bounds__(kWTPF * kWFPC) k_output_w128(OutParams P) {
     }
     fft128_coop<true>(y, l, gbase, tw);
     if (!active) return;
+    bool bad = false;
     for (int o = P.out_start[u]; o < P.out_start[u + 1]; ++o) {
         const int4 e = P.outs[o];
         const size_t off1 = (size_t)line * kW + 32 * l, off2 = (size_t)(line + kWH) * kW + 32 * l;
@@ -289,12 +290,16 @@ __global__ void __launch_bounds__(kWTPF * kWFPC) k_output_w128(OutParams P) {
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
             const float4 a = __ldg(&f1[c]), b = __ldg(&l1[c]), a2 = __ldg(&f2[c]), b2 = __ldg(&l2[c]);
-            q1[c] = make_float4(fmaf(-a.x, b.x, y[4 * c].x), fmaf(-a.y, b.y, y[4 * c + 1].x),
-                                fmaf(-a.z, b.z, y[4 * c + 2].x), fmaf(-a.w, b.w, y[4 * c + 3].x));
-            q2[c] = make_float4(fmaf(-a2.x, b2.x, y[4 * c].y), fmaf(-a2.y, b2.y, y[4 * c + 1].y),
-                                fmaf(-a2.z, b2.z, y[4 * c + 2].y), fmaf(-a2.w, b2.w, y[4 * c + 3].y));
+            const float4 v1 = make_float4(fmaf(-a.x, b.x, y[4 * c].x), fmaf(-a.y, b.y, y[4 * c + 1].x),
+                                          fmaf(-a.z, b.z, y[4 * c + 2].x), fmaf(-a.w, b.w, y[4 * c + 3].x));
+            const float4 v2 = make_float4(fmaf(-a2.x, b2.x, y[4 * c].y), fmaf(-a2.y, b2.y, y[4 * c + 1].y),
+                                          fmaf(-a2.z, b2.z, y[4 * c + 2].y), fmaf(-a2.w, b2.w, y[4 * c + 3].y));
+            bad |= nonfinite4(v1) || nonfinite4(v2);
+            q1[c] = v1;
+            q2[c] = v2;
         }
     }
+    if (bad) atomicOr(P.err, kErrNonFinite);
 }
 
 }  // namespace boltz_dev

@@ -19,10 +19,12 @@ def as_fp32(x):
     return np.asarray(x, dtype=np.float32).astype(np.float64)
 
 
-def gpu_collide(B, cfg, fields, pairs, form=0, return_T=False):
+def gpu_collide(B, cfg, fields, pairs, form=0, return_T=False, schedule=0, launches=None):
+    """Q (and T) from the library.  `launches`, when a dict, receives the
+    per-class launch counts of the call (to check which schedule ran)."""
     import torch
     N, d, L, R, gamma, n_rho, M = cfg
-    g = B.boltz_grid_init(N, d, L, R, gamma, n_rho, M)
+    g = B.boltz_grid_init(N, d, L, R, gamma, n_rho, M, schedule=schedule)
     try:
         f = torch.tensor(np.asarray(fields, dtype=np.float32), device="cuda")
         spec = B.boltz_spectrum(g, f)
@@ -31,6 +33,8 @@ def gpu_collide(B, cfg, fields, pairs, form=0, return_T=False):
         Q = B.boltz_collide_batched(g, spec, pj, pl, form=form)
         T = B.boltz_project(g, f, Q) if return_T else None
         B.boltz_sync_status(g)
+        if launches is not None:
+            launches.update({k: c for k, (c, _) in B.boltz_profile_read(g, reset=True).items()})
         torch.cuda.synchronize()
         out = Q.cpu().numpy().astype(np.float64)
         return (out, T.cpu().numpy().astype(np.float64)) if return_T else out
