@@ -366,9 +366,12 @@ boltz_status boltz_mott_smith(boltz_grid g, const void* spectra, double rho_L, d
  * embedded budget) may have no room for a new allocation.
  *   r       1..64 (the partial sums need r^3 x slices floats <= 2^19; the
  *           slice count is reduced to fit).  Larger r: BOLTZ_EINVAL.
- * The first call on a device resolves the array's device address with
- * cudaGetSymbolAddress (device current, once per device); make that first
- * call before any stream capture.  Every call shares the one array: calls
+ * Each call made outside stream capture resolves the array's device address
+ * on the current device with cudaGetSymbolAddress (so a device reset, which
+ * reloads the library's device image, is handled); a call made while
+ * `stream` is capturing reuses the address the last uncaptured call on that
+ * device resolved, so the first call on a device must come before any stream
+ * capture (otherwise BOLTZ_ECUDA).  Every call shares the one array: calls
  * that can overlap on the GPU (different streams, or different grids on the
  * same device) race on it and must be serialised by the caller.  Each call
  * writes every partial sum it reads, so no clearing is needed.

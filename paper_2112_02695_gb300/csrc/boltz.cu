@@ -306,9 +306,12 @@ PencilTree build_pencil_tree(const boltz_grid_s* g) {
         T.step_sel.push_back(make_int4(sel[0], sel[1], sel[2], sel[3]));
         T.step_w.push_back(make_float2(w[0], w[1]));
     }
-    // the kernel keeps these tables in fixed-size shared arrays
+    // the kernel keeps these tables in fixed-size shared arrays, and a tree
+    // item stages the phase rows of its whole group
+    bool rows_fit = true;
+    for (int b = 0; b < ng; ++b) rows_fit = rows_fit && load[b] <= pc::MAX_ROWS;
     T.ok = !T.step_dir.empty() && T.n_s0 <= pc::MAX_S && T.n_s01 <= pc::MAX_S &&
-           (int)T.step_dir.size() <= pc::MAX_STEP;
+           (int)T.step_dir.size() <= pc::MAX_STEP && rows_fit && g->n_rho + pc::RLAG <= pc::MAX_STAGE;
     return T;
 }
 
@@ -399,7 +402,7 @@ boltz_status build_plan_pencil(const boltz_grid_s* g, const int32_t* pj, const i
     plan.off_Pt = w;
     w = align_up(w + size_t(pc::NPB) * pc::NSLOT * pc::NKB * pc::PLANE * sizeof(float2), 256);
     plan.off_qhat = w;
-    w = align_up(w + size_t(plan.pen_n_used) * pc::HALF * sizeof(float2), 256);
+    w = align_up(w + size_t(plan.pen_n_used) * pc::NKB * pc::QBLK * sizeof(float2), 256);
     plan.off_ctr = w;
     w = align_up(w + size_t(pc::ctr_count(g->n_rho, plan.pen_n_used)) * sizeof(int), 256);
     plan.off_A = plan.off_P = plan.off_img = w;
@@ -1596,7 +1599,7 @@ boltz_status run_pencil(boltz_grid_s* g, const float2* spectra, float* Q_out, cu
     P.n_used = plan.pen_n_used;
     BZ_CUDA(cudaMemsetAsync(P.ctr, 0, size_t(pc::ctr_count(g->n_rho, plan.pen_n_used)) * sizeof(int), st));
     const long long items =
-        (long long)g->n_rho * (pc::NLB + pc::tree_items(nc, T.n_s0) + (long long)plan.pen_n_used * pc::NKB);
+        (long long)g->n_rho * (pc::NLB + pc::tree_items(nc, T.n_grp) + (long long)plan.pen_n_used);
     const int grid = (int)std::min<long long>(g->pen_ctas, items);
     {
         ProfScope ps(g, BOLTZ_KCLASS_PIPELINE, st);
@@ -1612,8 +1615,10 @@ boltz_status run_pencil(boltz_grid_s* g, const float2* spectra, float* Q_out, cu
     op.err = g->d_err;
     op.U = plan.pen_n_used;
     {
+        // gain synthesis from the packed Qhat+ layout of the pipelined kernel
+        using CG = ClusterGeo<32, 2>;
         ProfScope ps(g, BOLTZ_KCLASS_OUTPUT, st);
-        dp->output(op, st);
+        k_output_cl<32, 2, true><<<2 * op.U, CG::NT, CG::SMEM, st>>>(op);
     }
     BZ_CUDA(cudaGetLastError());
     return BOLTZ_OK;
@@ -1775,6 +1780,35 @@ cudaError_t prepare_project_tc() {
     return set_smem(k_project_tc<64>, ProjTcShape<64>::SMEM);
 }
 
+// Room for the projection's partial sums: at most 64 voxel slices of r^3.
+long long project_partial_floats(int r) { return 64LL * r * r * r; }
+
+// CUDA-core projection (tiny grids, and the allocation-free entry point):
+// partial sums of voxel slices, then their reduction in a fixed order with the
+// midpoint-rule weight dv^d.  The slice count is bounded by the room in
+// `partial` (max_partial floats, at least r^3).  Every partial entry the
+// reduction reads is written by k_project of the same call first, so nothing
+// an earlier call left in `partial` is ever read.
+boltz_status run_project_cuda_cores(boltz_grid_s* g, const float* V, int r, const float* Q, float* T, float* partial,
+                                    long long max_partial, cudaStream_t st) {
+    constexpr int PB = 8, RT = 16;
+    const int r2 = r * r;
+    const long long r3 = (long long)r * r2;
+    const int bx = (r2 + PB - 1) / PB, bz = (r + RT - 1) / RT;
+    int slices = std::max(1, std::min(64, (2 * 152) / std::max(1, bx * bz)));
+    slices = std::min(slices, std::max(1, g->n / 256));
+    slices = (int)std::max<long long>(1, std::min<long long>(slices, max_partial / r3));
+    {
+        ProfScope ps(g, BOLTZ_KCLASS_PROJECT, st);
+        k_project<PB, RT><<<dim3(bx, slices, bz), 256, 0, st>>>(V, Q, partial, r, g->n, slices);
+    }
+    const float scale = (float)std::pow(2.0 * g->L / g->N, g->D);
+    ProfScope ps(g, BOLTZ_KCLASS_PROJECT, st);
+    k_project_reduce<<<(int)((r3 + 255) / 256), 256, 0, st>>>(partial, T, (int)r3, slices, scale);
+    BZ_CUDA(cudaGetLastError());
+    return BOLTZ_OK;
+}
+
 boltz_status run_project(boltz_grid_s* g, const float* V, int r, const float* Q, float* T, float* partial,
                          cudaStream_t st) {
     const int r2 = r * r;
@@ -1790,12 +1824,7 @@ boltz_status run_project(boltz_grid_s* g, const float* V, int r, const float* Q,
         else if (r <= 48) launch_project_tc<48>(V, Q, partial, r, g->n, kpc, g->d_err, st);
         else launch_project_tc<64>(V, Q, partial, r, g->n, kpc, g->d_err, st);
     } else {
-        constexpr int PB = 8, RT = 16;
-        const int bx = (r2 + PB - 1) / PB, bz = (r + RT - 1) / RT;
-        slices = std::max(1, std::min(64, (2 * 152) / std::max(1, bx * bz)));
-        slices = std::min(slices, std::max(1, g->n / 256));
-        ProfScope ps(g, BOLTZ_KCLASS_PROJECT, st);
-        k_project<PB, RT><<<dim3(bx, slices, bz), 256, 0, st>>>(V, Q, partial, r, g->n, slices);
+        return run_project_cuda_cores(g, V, r, Q, T, partial, project_partial_floats(r), st);
     }
     ProfScope ps(g, BOLTZ_KCLASS_PROJECT, st);
     k_project_reduce<<<(count + 255) / 256, 256, 0, st>>>(partial, T, count, slices, scale);
@@ -1803,7 +1832,7 @@ boltz_status run_project(boltz_grid_s* g, const float* V, int r, const float* Q,
     return BOLTZ_OK;
 }
 
-size_t project_partial_bytes(int r) { return size_t(64) * r * r * r * sizeof(float); }
+size_t project_partial_bytes(int r) { return size_t(project_partial_floats(r)) * sizeof(float); }
 
 // FP64 projection of the check build: CUDA-core partial sums over voxel
 // slices, reduced in a fixed order (the same kernels as the FP32 fallback for
@@ -1837,26 +1866,32 @@ size_t project64_partial_bytes(int r) { return size_t(32) * r * r * r * sizeof(d
 constexpr int kNoAllocProjectFloats = 1 << 19;
 static __device__ __align__(256) float g_noalloc_project_partial[kNoAllocProjectFloats];
 
-// Resolves the array's device address once per device (the device must be
-// current); later calls on that device reuse the cached address.
-boltz_status noalloc_project_partial(float** out) {
+// The array's device address on the current device.  It is resolved with
+// cudaGetSymbolAddress on every call made outside stream capture (so that a
+// device reset, which reloads the module, cannot leave a stale address), and
+// cached per device for calls made while `st` is capturing, which must not
+// make that runtime call; the first call on a device must therefore come
+// before any capture.
+boltz_status noalloc_project_partial(float** out, cudaStream_t st) {
     static std::mutex mu;
     static std::map<int, float*> addr;
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
         (void)cudaGetLastError();
         return BOLTZ_ECUDA;
     }
     std::lock_guard<std::mutex> lock(mu);
-    auto it = addr.find(dev);
-    if (it == addr.end()) {
+    if (cap == cudaStreamCaptureStatusNone) {
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_project_partial) != cudaSuccess || p == nullptr) {
             (void)cudaGetLastError();
             return BOLTZ_ECUDA;
         }
-        it = addr.emplace(dev, static_cast<float*>(p)).first;
+        addr[dev] = static_cast<float*>(p);
     }
+    auto it = addr.find(dev);
+    if (it == addr.end()) return BOLTZ_ECUDA;       // first call on this device made during capture
     *out = it->second;
     return BOLTZ_OK;
 }
@@ -2205,11 +2240,24 @@ boltz_status boltz_grid_init(boltz_grid* out, int N, int d_v, double L, double R
     if (d_v == 3 && N == 32) {
         namespace pc = boltz_dev::pencil;
         g->pen_tree = build_pencil_tree(g);
-        int occ = 0;
+        // Resident CTAs per SM of the pipelined kernel, from its registers,
+        // shared memory and tensor-memory columns.  (The runtime's occupancy
+        // query reports one CTA per SM for any kernel that allocates tensor
+        // memory; three of these CTAs hold 384 of the SM's 512 columns.)
+        cudaFuncAttributes fa;
+        int regs_sm = 0, smem_sm = 0, resv = 0;
         if (set_smem(pc::k_pencil, pc::SM_TOTAL) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pc::k_pencil, pc::NT, pc::SM_TOTAL) != cudaSuccess)
+            set_smem(k_output_cl<32, 2, true>, ClusterGeo<32, 2>::SMEM) != cudaSuccess ||
+            cudaFuncGetAttributes(&fa, pc::k_pencil) != cudaSuccess ||
+            cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, g->device) != cudaSuccess ||
+            cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, g->device) != cudaSuccess ||
+            cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, g->device) != cudaSuccess)
             return fail(BOLTZ_ECUDA);
-        g->pen_ctas = occ * g->sms;
+        const int regs_cta = ((fa.numRegs + 7) / 8 * 8) * pc::NT;
+        const int smem_cta = (int)fa.sharedSizeBytes + pc::SM_TOTAL + resv;
+        int per_sm = std::min(regs_sm / std::max(regs_cta, 1), smem_sm / std::max(smem_cta, 1));
+        per_sm = std::min(per_sm, std::min(pc::CTAS_PER_SM, 512 / (int)pc::TMEM_COLS));
+        g->pen_ctas = std::max(per_sm, 0) * g->sms;
     }
     if (cudaStreamCreateWithFlags(&g->side, cudaStreamNonBlocking) != cudaSuccess) return fail(BOLTZ_ECUDA);
     for (int b = 0; b < 2; ++b)
@@ -2330,28 +2378,11 @@ boltz_status boltz_project_noalloc(boltz_grid g, const float* V, int r, const fl
     if (!g || !V || !Q || !T_out || r < 1 || r > 64) return BOLTZ_EINVAL;
     const long long r3 = (long long)r * r * r;
     if (r3 > kNoAllocProjectFloats) return BOLTZ_EINVAL;
-    float* partial = nullptr;
-    boltz_status s = noalloc_project_partial(&partial);
-    if (s != BOLTZ_OK) return s;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    constexpr int PB = 8, RT = 16;
-    const int r2 = r * r;
-    const int bx = (r2 + PB - 1) / PB, bz = (r + RT - 1) / RT;
-    int slices = std::max(1, std::min(64, (2 * 152) / std::max(1, bx * bz)));
-    slices = std::min(slices, std::max(1, g->n / 256));
-    slices = std::max(1, std::min<int>(slices, (int)(kNoAllocProjectFloats / r3)));
-    // every partial entry the reduction reads is written by k_project first,
-    // so nothing left in the array by an earlier call is ever read
-    {
-        ProfScope ps(g, BOLTZ_KCLASS_PROJECT, st);
-        k_project<PB, RT><<<dim3(bx, slices, bz), 256, 0, st>>>(V, Q, partial, r, g->n, slices);
-    }
-    const int count = r * r2;
-    const float scale = (float)std::pow(2.0 * g->L / g->N, g->D);
-    ProfScope ps(g, BOLTZ_KCLASS_PROJECT, st);
-    k_project_reduce<<<(count + 255) / 256, 256, 0, st>>>(partial, T_out, count, slices, scale);
-    BZ_CUDA(cudaGetLastError());
-    return BOLTZ_OK;
+    float* partial = nullptr;
+    boltz_status s = noalloc_project_partial(&partial, st);
+    if (s != BOLTZ_OK) return s;
+    return run_project_cuda_cores(g, V, r, Q, T_out, partial, kNoAllocProjectFloats, st);
 }
 
 boltz_status boltz_spectrum_f64(boltz_grid g, const double* f, int n_inputs, void* spectra_out, void* stream) {

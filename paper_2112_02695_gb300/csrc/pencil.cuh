@@ -39,19 +39,22 @@
 //   they travel as one complex column (re = k_2 0, im = k_2 N/2) and are
 //   separated with the conjugate-symmetry identity after the 2D transform.
 //
-// Scheduling: a fixed list of items, stage by stage (stage s: fused items of
-// node s-1, tree items of node s, radial items of node s-2), claimed in order
+// Scheduling: a fixed list of items, stage by stage (stage s: tree items of
+// node s, fused items of node s-1, radial items of node s-3), claimed in order
 // from an atomic counter by persistent CTAs (three per SM: 128 threads, at
 // most 168 registers, 67 KB of shared memory and 128 TMEM columns each).  A
-// CTA claims its next item when it starts the current one.  Every dependency
+// CTA claims its next item when it starts the current one (the claim's round
+// trip is hidden behind the work; claiming further ahead delays claimed items
+// behind long ones and stalls the items that depend on them).  Every dependency
 // points to an item earlier in the list (fused(q) needs all tree(q) and the
 // Pt buffer free; tree(q) needs its X buffer free; radial(q) needs fused(q)
 // and radial(q-1) of its slot), so the lowest unfinished item can always run:
 // progress needs no co-residency.  Each wait is a bounded poll (about one
 // second of device time); a wait that gives up records a timeout in the error
 // word and raises an abort flag, after which every CTA drains the list
-// without working, so the launch always ends.  X (two node buffers, ~54 MB
-// each) and Pt (three node buffers, ~18 MB each) are sized for the 126 MB L2;
+// without working, so the launch always ends.  X (three node buffers, ~54 MB
+// each, so that a tree item never waits on the fused items of the previous
+// node) and Pt (four node buffers, ~18 MB each) stay mostly in the 126 MB L2;
 // the lines of an X block or Pt plane are dropped from L2 without write-back
 // once their single consumer has copied them (discard.global.L2).
 #pragma once
@@ -90,8 +93,9 @@ constexpr int PSS = 4 * N + 4;                 // floats per slot in the epilogu
 constexpr int MAX_ROWS = 32;                   // phase rows a tree item stages (1 + children)
 constexpr int MAX_S = 96;                      // sigma_0 and (sigma_0, sigma_1) values (M <= 86)
 constexpr int MAX_STEP = 24;                   // fused-item steps (M/2 antipodal pairs, two a step)
-constexpr int NXB = 2;                         // X node buffers
-constexpr int NPB = 3;                         // Pt node buffers
+constexpr int NXB = 3;                         // X node buffers
+constexpr int NPB = 4;                         // Pt node buffers
+constexpr int RLAG = 3;                        // radial items of node s - RLAG run in stage s
 constexpr uint32_t TMEM_COLS = 128;            // per CTA (three CTAs use 384 of the SM's 512 columns)
 constexpr int CTAS_PER_SM = 3;
 
@@ -104,11 +108,14 @@ constexpr int CTAS_PER_SM = 3;
 constexpr int SM_STAGE = 4 * XBLK * 8;                // 33792 B
 constexpr int SM_PH2 = 2 * SM_STAGE;                  // [2 stages][4 slots][H] float2 phase rows
 constexpr int SM_TPH = PLANE * 8;                     // tree: phase rows after the plane
+constexpr int QBLK = N * N * KB;                      // float2 of one (slot, column block) of Qhat+
+constexpr int SM_QS = PLANE * 8;                      // radial: that Qhat+ block after the plane
 constexpr int SM_TOTAL = SM_PH2 + 2 * 4 * H * 8;       // 68608 B: three CTAs with their static tables fit 228 KB
 static_assert(4 * ADS * 4 <= SM_STAGE, "A overlays the X blocks of its stage");
 static_assert(64 * PSS * 4 <= SM_STAGE, "64 epilogue slots fit a stage");
 static_assert(SM_PH2 + 2 * 4 * H * 8 <= SM_TOTAL, "phase rows fit");
 static_assert(SM_TPH + MAX_ROWS * N * 8 <= SM_TOTAL, "tree phase rows fit");
+static_assert(SM_QS + QBLK * 8 <= SM_TOTAL, "radial Qhat+ block fits");
 static_assert((CTAS_PER_SM + 1) * (SM_TOTAL + 4096) > 228 * 1024, "at most three CTAs per SM");
 static_assert(CTAS_PER_SM * (SM_TOTAL + 4096) <= 228 * 1024, "three CTAs per SM");
 
@@ -132,7 +139,9 @@ struct Params {
     const float* ctab;       // [n_rho][SMAX + 1]: c_q(|k|^2) including 1/n
     float2* X;               // [NXB][n_s01][NLB][XBLK]
     float2* Pt;              // [NPB][NSLOT][NKB][PLANE]
-    float2* qhat;            // [n_used][HALF]: Qhat+ of the used slots, in slot order
+    float2* qhat;            // [n_used][NKB][QBLK]: Qhat+ of the used slots in the packed layout
+                             // the output kernel reads (k_output_cl with PK): [kb][k0][k1][c],
+                             // k2 = 4 kb + c, column 0 holding Y = A + i B of the planes k2 = 0, N/2
     const int* slots;        // [n_used]: slots whose gain is needed
     int* ctr;                // counters, zeroed before the launch (layout in ctr_*)
     int* err;                // device error word
@@ -141,12 +150,12 @@ struct Params {
 };
 
 // counters: [0] claim, [1] abort, then per node: tree done, fused done,
-// radial done, then per (used slot, column block) the nodes accumulated
+// radial done, then per used slot the nodes accumulated into its Qhat+
 __host__ __device__ constexpr int ctr_tree(int n_rho, int q) { return 2 + q; }
 __host__ __device__ constexpr int ctr_fused(int n_rho, int q) { return 2 + n_rho + q; }
 __host__ __device__ constexpr int ctr_radial(int n_rho, int q) { return 2 + 2 * n_rho + q; }
 __host__ __device__ constexpr int ctr_acc(int n_rho, int i) { return 2 + 3 * n_rho + i; }
-__host__ __device__ constexpr int ctr_count(int n_rho, int n_used) { return 2 + 3 * n_rho + n_used * NKB; }
+__host__ __device__ constexpr int ctr_count(int n_rho, int n_used) { return 2 + 3 * n_rho + n_used; }
 
 // TRI16 slot of the unordered pair (a <= b)
 __host__ __device__ constexpr int tri_slot(int a, int b) { return a * NJ - a * (a - 1) / 2 + (b - a); }
@@ -174,23 +183,31 @@ struct Item {
     int kind, q, local;
 };
 
-__host__ __device__ inline int tree_items(int n_c, int n_s0) { return n_c * NKB * n_s0; }
+__host__ __device__ inline int tree_items(int n_c, int n_grp) { return n_c * NKB * n_grp; }
+constexpr int MAX_STAGE = 128 + 3 + 1;         // stages: n_rho (<= 128) + RLAG, plus the end
 
-// Item idx of the stage-ordered list.
-__device__ __noinline__ Item decode_item(const Params& P, int idx) {
-    const int nT = tree_items(P.n_c, P.tr.n_s0), nR = P.n_used * NKB;
-    for (int s = 0; s < P.n_rho + 2; ++s) {
-        const int f = (s >= 1 && s <= P.n_rho) ? NLB : 0;
-        if (idx < f) return {IT_FUSED, s - 1, idx};
-        idx -= f;
-        const int t = (s < P.n_rho) ? nT : 0;
-        if (idx < t) return {IT_TREE, s, idx};
-        idx -= t;
-        const int r = (s >= 2) ? nR : 0;
-        if (idx < r) return {IT_RADIAL, s - 2, idx};
-        idx -= r;
-    }
-    return {IT_END, 0, 0};
+// Items of stage s in list order: tree items of node s, fused items of node
+// s-1, radial items of node s - RLAG.
+__host__ __device__ inline void stage_counts(int s, int n_rho, int nT, int nR, int& t, int& f, int& r) {
+    t = (s < n_rho) ? nT : 0;
+    f = (s >= 1 && s <= n_rho) ? NLB : 0;
+    r = (s >= RLAG && s < n_rho + RLAG) ? nR : 0;
+}
+
+// Item idx of the stage-ordered list, from the stage offsets (off[s] = first
+// item of stage s).  `stage` is the caller's cursor: its claims increase, so
+// the search resumes where the previous one ended.
+__device__ __noinline__ Item decode_item(const Params& P, const int* off, int& stage, int idx) {
+    const int ns = P.n_rho + RLAG;
+    if (idx >= off[ns]) return {IT_END, 0, 0};
+    while (idx >= off[stage + 1]) ++stage;
+    int t, f, r;
+    stage_counts(stage, P.n_rho, tree_items(P.n_c, P.tr.n_grp), P.n_used, t, f, r);
+    int k = idx - off[stage];
+    if (k < t) return {IT_TREE, stage, k};
+    k -= t;
+    if (k < f) return {IT_FUSED, stage - 1, k};
+    return {IT_RADIAL, stage - RLAG, k - f};
 }
 
 __device__ __forceinline__ int ld_acquire(const int* p) {
@@ -211,14 +228,20 @@ __device__ __forceinline__ void discard_l2(const void* p) {
     asm volatile("discard.global.L2 [%0], 128;" ::"l"(p) : "memory");
 }
 
-// Bounded wait (one thread) until *c >= target.  False when about one second
-// of device time passed or another CTA has raised the abort flag.
-__device__ __noinline__ bool wait_at_least(const int* c, int target, const int* abort) {
-    if (ld_acquire(c) >= target) return true;
+// Bounded wait (one thread) until *c1 >= t1 and *c2 >= t2 (c2 may be null).
+// Both counters are read at once, so a satisfied dependency costs one memory
+// round trip.  False when about one second of device time passed or another
+// CTA has raised the abort flag.
+__device__ __noinline__ bool wait_at_least(const int* c1, int t1, const int* c2, int t2, const int* abort) {
+    int v1 = ld_acquire(c1);
+    int v2 = c2 ? ld_acquire(c2) : t2;
+    if (v1 >= t1 && v2 >= t2) return true;
     const uint64_t t0 = global_timer_ns();
     for (uint32_t i = 0; i < kSpinLimit; ++i) {
         __nanosleep(128);
-        if (ld_acquire(c) >= target) return true;
+        if (v1 < t1) v1 = ld_acquire(c1);
+        if (v2 < t2) v2 = ld_acquire(c2);
+        if (v1 >= t1 && v2 >= t2) return true;
         if ((i & 15u) == 15u) {
             if (*reinterpret_cast<const volatile int*>(abort)) return false;
             if (global_timer_ns() - t0 > kWaitNs) return false;
@@ -265,55 +288,77 @@ __device__ __forceinline__ void tmem_wait_ld32(uint32_t (&r)[32]) {
 
 // Tables of the direction tree, copied to shared memory once per CTA.
 struct TreeSmem {
-    int s0_dir[MAX_S], s0_child[MAX_S + 1], s01_dir[MAX_S];
+    int grp[MAX_S + 1], s0_dir[MAX_S], s0_child[MAX_S + 1], s01_dir[MAX_S];
+    int stage_off[MAX_STAGE + 1];
     int4 step_blk[MAX_STEP], step_dir[MAX_STEP], step_sel[MAX_STEP];
     float2 step_w[MAX_STEP];
 };
 
 // ------------------------------------------------------------------ tree item
-// Columns (k1 = t/4, k2 = 4 kb + c) of input jj: the axis-0 inverse pass for
-// sigma_0 value i, then for each (sigma_0, sigma_1) child the axis-1 inverse
-// pass of the lines (i0 = t/4, k2), stored into the X block of line block
-// (i0, m) for m = 0..7 with lines ordered (i1 = 2m, 2m+16, 2m+1, 2m+17).
+// Columns (k1 = t/4, k2 = 4 kb + c) of input jj, for the sigma_0 values of
+// group g: the axis-0 inverse pass of each, then for each of its
+// (sigma_0, sigma_1) children the axis-1 inverse pass of the lines
+// (i0 = t/4, k2), stored into the X block of line block (i0, m) for m = 0..7
+// with lines ordered (i1 = 2m, 2m+16, 2m+1, 2m+17).  The column stays in
+// registers for the whole group; the group's phase rows are staged at once.
 __device__ void tree_item(const Params& P, const TreeSmem& ts, int q, int local, unsigned char* smem) {
     const int t = threadIdx.x;
-    const int ns = P.tr.n_s0;
-    const int i = local % ns, kb = (local / ns) % NKB, jj = local / (ns * NKB);
+    const int ng = P.tr.n_grp;
+    const int g = local % ng, kb = (local / ng) % NKB, jj = local / (ng * NKB);
     float2* S0 = reinterpret_cast<float2*>(smem);                  // [N][PRS]: (i0, k1, c)
     float2* ph = reinterpret_cast<float2*>(smem + SM_TPH);         // [rows][N]
     const int k1 = t >> 2, c = t & 3;
     const float2* __restrict__ src = P.spectra + (size_t)__ldg(&P.inputs[jj]) * HALF + k1 * NH + KB * kb + c;
-    float2 x[N];
+    float2 col[N];
 #pragma unroll
-    for (int k0 = 0; k0 < N; ++k0) x[k0] = __ldg(src + k0 * N * NH);
-    const int cb = ts.s0_child[i], ce = ts.s0_child[i + 1];
-    const int rows = 1 + ce - cb;
+    for (int k0 = 0; k0 < N; ++k0) col[k0] = __ldg(src + k0 * N * NH);
+    // phase rows of the group: for each sigma_0 its axis-0 row, then its children's axis-1 rows
+    const int i0b = ts.grp[g], i0e = ts.grp[g + 1];
+    const int cb0 = ts.s0_child[i0b], rows = (i0e - i0b) + (ts.s0_child[i0e] - cb0);
     for (int e = t; e < rows * N; e += NT) {
         const int r = e / N, k = e % N;
-        const int dir = r == 0 ? ts.s0_dir[i] : ts.s01_dir[cb + r - 1];
-        ph[e] = __ldg(&P.phase[((size_t)(q * P.M + dir) * 3 + (r == 0 ? 0 : 1)) * N + k]);
+        // row r: the sigma_0 values of the group occupy rows (i - i0b) + (s0_child[i] - cb0)
+        int i = i0b;
+        while (i + 1 < i0e && r >= (i + 1 - i0b) + (ts.s0_child[i + 1] - cb0)) ++i;
+        const int rr = r - ((i - i0b) + (ts.s0_child[i] - cb0));
+        const int dir = rr == 0 ? ts.s0_dir[i] : ts.s01_dir[ts.s0_child[i] + rr - 1];
+        ph[e] = __ldg(&P.phase[((size_t)(q * P.M + dir) * 3 + (rr == 0 ? 0 : 1)) * N + k]);
     }
     __syncthreads();
-#pragma unroll
-    for (int k0 = 0; k0 < N; ++k0) x[k0] = cmul(x[k0], ph[k0]);
-    fft_reg<N, true>(x);
-#pragma unroll
-    for (int i0 = 0; i0 < N; ++i0) S0[i0 * PRS + k1 * KB + c] = x[i0];
-    __syncthreads();
-    const int i0 = t >> 2;
     float2* Xn = P.X + (size_t)(q % NXB) * P.tr.n_s01 * NLB * XBLK;
-    for (int ch = cb; ch < ce; ++ch) {
-        const float2* p1 = ph + (1 + ch - cb) * N;
+    const int i0 = t >> 2;
+    for (int i = i0b; i < i0e; ++i) {
+        const int cb = ts.s0_child[i], ce = ts.s0_child[i + 1];
+        const float2* p0 = ph + ((i - i0b) + (cb - cb0)) * N;
+        float2 x[N];
 #pragma unroll
-        for (int kk = 0; kk < N; ++kk) x[kk] = cmul(S0[i0 * PRS + kk * KB + c], p1[kk]);
-        fft_reg<N, true>(x);
-        float2* xb = Xn + ((size_t)ch * NLB + i0 * 8) * XBLK + jj * XJS + (KB * kb + c) * 4;
-#pragma unroll
-        for (int m = 0; m < 8; ++m) {
-            float4* o = reinterpret_cast<float4*>(xb + m * XBLK);
-            o[0] = make_float4(x[2 * m].x, x[2 * m].y, x[2 * m + H].x, x[2 * m + H].y);
-            o[1] = make_float4(x[2 * m + 1].x, x[2 * m + 1].y, x[2 * m + 1 + H].x, x[2 * m + 1 + H].y);
+        for (int k0 = 0; k0 < N; ++k0) {
+            x[k0] = cmul(col[k0], p0[k0]);
+            if ((k0 & 7) == 7) asm volatile("" ::: "memory");
         }
+        fft_reg<N, true>(x);
+#pragma unroll
+        for (int r0 = 0; r0 < N; ++r0) S0[r0 * PRS + k1 * KB + c] = x[r0];
+        __syncthreads();
+        for (int ch = cb; ch < ce; ++ch) {
+            const float2* p1 = p0 + (1 + ch - cb) * N;
+            // loads in groups of eight: with the column held in registers, all
+            // sixty-four in flight at once would not fit the register budget
+#pragma unroll
+            for (int kk = 0; kk < N; ++kk) {
+                x[kk] = cmul(S0[i0 * PRS + kk * KB + c], p1[kk]);
+                if ((kk & 7) == 7) asm volatile("" ::: "memory");
+            }
+            fft_reg<N, true>(x);
+            float2* xb = Xn + ((size_t)ch * NLB + i0 * 8) * XBLK + jj * XJS + (KB * kb + c) * 4;
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                float4* o = reinterpret_cast<float4*>(xb + m * XBLK);
+                o[0] = make_float4(x[2 * m].x, x[2 * m].y, x[2 * m + H].x, x[2 * m + H].y);
+                o[1] = make_float4(x[2 * m + 1].x, x[2 * m + 1].y, x[2 * m + 1 + H].x, x[2 * m + 1 + H].y);
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -546,102 +591,132 @@ __device__ bool fused_item(const Params& P, const TreeSmem& ts, int q, int lb, u
 }
 
 // ------------------------------------------------------------------ radial item
-// Column block kb of slot u's Pt plane: forward axis-1 pass (thread = line
-// (i0, c)), forward axis-0 pass (thread = column (k1, c)), then
-// Qhat+[u](k) (+)= c_q(|k|^2) (-1)^(k0+k1+k2) DFT[P_q,u](k).
-__device__ bool radial_item(const Params& P, int q, int local, unsigned char* smem, uint64_t* bars, uint32_t& par) {
+// 1-D bulk copy of `bytes` from this CTA's shared memory to global memory, as
+// one bulk async-group of this thread.
+__device__ __forceinline__ void bulk_s2g(void* dst_gmem, const void* src_smem, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst_gmem),
+                 "r"(smem_u32(src_smem)), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// Waits until this thread's bulk stores have read their shared-memory sources.
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+
+// Slot u, column block by column block: the Pt plane's forward axis-1 pass
+// (thread = line (i0, c)), forward axis-0 pass (thread = column (k1, c)), then
+// Qhat+[u](k) (+)= c_q(|k|^2) (-1)^(k0+k1+k2) DFT[P_q,u](k), with the block of
+// Qhat+ copied into shared memory and back in one piece each way.
+__device__ bool radial_item(const Params& P, int q, int ui, unsigned char* smem, uint64_t* bars, uint32_t& par) {
     const int t = threadIdx.x;
-    const int ui = local / NKB, kb = local % NKB;
     const int u = __ldg(&P.slots[ui]);
     float2* S = reinterpret_cast<float2*>(smem);
-    const float2* src = P.Pt + ((size_t)((q % NPB) * NSLOT + u) * NKB + kb) * PLANE;
-    if (t == 0) {
-        fence_proxy_async_global();
-        fence_proxy_async_smem();
-        mbar_arrive_expect_tx(&bars[0], PLANE * 8);
-        bulk_g2s(S, src, PLANE * 8, &bars[0]);
-    }
-    const int c = t & 3, k1 = t >> 2;
-    const bool packed = (kb == 0 && c == 0);
+    float2* Qs = reinterpret_cast<float2*>(smem + SM_QS);          // [k0][k1][c]
     const bool first = (q == 0);
-    float2* qh = P.qhat + (size_t)ui * HALF;                        // Qhat+ is stored per used slot
-    const int k2 = packed ? 0 : KB * kb + c;
-    // the previous nodes' sums of the first RQ rows k0, in flight during the transforms
-    constexpr int RQ = 8;
-    float2 old[RQ];
-#pragma unroll
-    for (int k0 = 0; k0 < RQ; ++k0) old[k0] = first ? make_float2(0.f, 0.f) : qh[(k0 * N + k1) * NH + k2];
-    const bool ok = mbar_wait_bounded(&bars[0], par & 1u);
-    par ^= 1u;
-    if (__syncthreads_or(!ok)) return false;
-    for (int l = t; l < PLANE * 8 / 128; l += NT) discard_l2(reinterpret_cast<const char*>(src) + (size_t)l * 128);
-    float2 x[N];
-    {
-        const int i0 = t >> 2;
-#pragma unroll
-        for (int i1 = 0; i1 < N; ++i1) x[i1] = S[i0 * PRS + i1 * KB + c];
-        fft_reg<N, false>(x);
-#pragma unroll
-        for (int kk = 0; kk < N; ++kk) S[i0 * PRS + kk * KB + c] = x[kk];
-    }
-    __syncthreads();
-#pragma unroll
-    for (int i0 = 0; i0 < N; ++i0) x[i0] = S[i0 * PRS + k1 * KB + c];
-    fft_reg<N, false>(x);
-    // the axis-0 results of every column back into the plane (the packed
-    // column needs the values at the mirrored frequency), then
-    // Qhat+ += multiplier x DFT, RQ rows k0 at a time
-    __syncthreads();
-#pragma unroll
-    for (int k0 = 0; k0 < N; ++k0) S[k0 * PRS + k1 * KB + c] = x[k0];
-    __syncthreads();
     const float* __restrict__ ct = P.ctab + (size_t)q * (SMAX + 1);
+    const int c = t & 3, k1 = t >> 2;
     const int b = wrapk(k1, N), k1m = (N - k1) % N;
-    auto rows = [&](int k0b, const float2 (&o)[RQ]) {
+#pragma unroll 1
+    for (int kb = 0; kb < NKB; ++kb) {
+        const float2* src = P.Pt + ((size_t)((q % NPB) * NSLOT + u) * NKB + kb) * PLANE;
+        float2* qblk = P.qhat + ((size_t)ui * NKB + kb) * QBLK;
+        if (t == 0) {
+            bulk_wait_read();                                   // the previous block's store has read Qs
+            fence_proxy_async_global();
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(&bars[0], PLANE * 8 + (first ? 0 : QBLK * 8));
+            bulk_g2s(S, src, PLANE * 8, &bars[0]);
+            if (!first) bulk_g2s(Qs, qblk, QBLK * 8, &bars[0]);
+        }
+        const bool ok = mbar_wait_bounded(&bars[0], par & 1u);
+        par ^= 1u;
+        if (__syncthreads_or(!ok)) {
+            if (t == 0) bulk_wait_all();
+            return false;
+        }
+        for (int l = t; l < PLANE * 8 / 128; l += NT) discard_l2(reinterpret_cast<const char*>(src) + (size_t)l * 128);
+        float2 x[N];
+        {
+            const int i0 = t >> 2;
 #pragma unroll
-        for (int kk = 0; kk < RQ; ++kk) {
-            const int k0 = k0b + kk;
+            for (int i1 = 0; i1 < N; ++i1) x[i1] = S[i0 * PRS + i1 * KB + c];
+            fft_reg<N, false>(x);
+#pragma unroll
+            for (int kk = 0; kk < N; ++kk) S[i0 * PRS + kk * KB + c] = x[kk];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i0 = 0; i0 < N; ++i0) x[i0] = S[i0 * PRS + k1 * KB + c];
+        fft_reg<N, false>(x);
+        // the packed column (block 0, c = 0) needs its values at the mirrored frequency
+        const bool packed = (kb == 0 && c == 0);
+        __syncthreads();
+        if (packed) {
+#pragma unroll
+            for (int k0 = 0; k0 < N; ++k0) S[k0 * PRS + k1 * KB] = x[k0];
+        }
+        __syncthreads();
+        const int k2 = KB * kb + c;
+#pragma unroll
+        for (int k0 = 0; k0 < N; ++k0) {
             const int a = wrapk(k0, N);
-            const float2 z = S[k0 * PRS + k1 * KB + c];
-            const int idx = (k0 * N + k1) * NH;
+            float2 v;
             if (!packed) {
                 const float c0 = __ldg(&ct[a * a + b * b + k2 * k2]);
                 const float sc = ((k0 + k1 + k2) & 1) ? -c0 : c0;
-                qh[idx + k2] = make_float2(fmaf(z.x, sc, o[kk].x), fmaf(z.y, sc, o[kk].y));
+                v = make_float2(x[k0].x * sc, x[k0].y * sc);
             } else {
-                // Z = F[a] + i F[b] for the real planes a (k2 = 0) and b (k2 = N/2)
-                const float2 zm = S[((N - k0) % N) * PRS + k1m * KB];
-                const float2 fa = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
-                const float2 fb = make_float2(0.5f * (z.y + zm.y), -0.5f * (z.x - zm.x));
-                const float sg = ((k0 + k1) & 1) ? -1.f : 1.f;     // (-1)^(k0+k1+k2), k2 = 0 or N/2
-                const float c0 = sg * __ldg(&ct[a * a + b * b]);
-                const float c16 = sg * __ldg(&ct[a * a + b * b + H * H]);
-                const float2 o16 = first ? make_float2(0.f, 0.f) : qh[idx + H];
-                qh[idx] = make_float2(fmaf(fa.x, c0, o[kk].x), fmaf(fa.y, c0, o[kk].y));
-                qh[idx + H] = make_float2(fmaf(fb.x, c16, o16.x), fmaf(fb.y, c16, o16.y));
+                // Z = F[A] + i F[B] of the real planes A (k2 = 0) and B (k2 = N/2); the packed sum
+                // is Y = c0 F[A] + i c16 F[B] = ((c0 + c16) Z + (c0 - c16) conj Z(-k)) / 2
+                const float2 z = x[k0], zm = S[((N - k0) % N) * PRS + k1m * KB];
+                const float sg = ((k0 + k1) & 1) ? -0.5f : 0.5f;      // (-1)^(k0+k1+k2) / 2, k2 = 0 or N/2
+                const float c0 = __ldg(&ct[a * a + b * b]), c16 = __ldg(&ct[a * a + b * b + H * H]);
+                const float p = sg * (c0 + c16), m = sg * (c0 - c16);
+                v = make_float2(fmaf(p, z.x, m * zm.x), fmaf(p, z.y, -m * zm.y));
             }
+            float2* o = Qs + (k0 * N + k1) * KB + c;
+            if (!first) v = make_float2(v.x + o->x, v.y + o->y);
+            *o = v;
         }
-    };
-    rows(0, old);
-#pragma unroll 1
-    for (int k0b = RQ; k0b < N; k0b += RQ) {
-        float2 o[RQ];
-#pragma unroll
-        for (int kk = 0; kk < RQ; ++kk) o[kk] = first ? make_float2(0.f, 0.f) : qh[((k0b + kk) * N + k1) * NH + k2];
-        rows(k0b, o);
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (t == 0) bulk_s2g(qblk, Qs, QBLK * 8);
+    }
+    if (t == 0) {
+        bulk_wait_all();
+        fence_proxy_async_global();
     }
     return true;
 }
 
 // ------------------------------------------------------------------ persistent kernel
+// Publishes a finished item: its global writes (generic stores of every
+// thread, ordered by the CTA barrier that ended the item, and bulk stores that
+// thread 0 waited for) become visible with release semantics, then the item
+// is counted.
+__device__ __forceinline__ void publish(const Params& P, const Item& it) {
+    fence_proxy_async_global();
+    const int nr = P.n_rho;
+    if (it.kind == IT_TREE) red_release_add(P.ctr + ctr_tree(nr, it.q), 1);
+    else if (it.kind == IT_FUSED) red_release_add(P.ctr + ctr_fused(nr, it.q), 1);
+    else {
+        red_release_add(P.ctr + ctr_acc(nr, it.local), 1);
+        red_release_add(P.ctr + ctr_radial(nr, it.q), 1);
+    }
+}
+
 __global__ void __launch_bounds__(NT, CTAS_PER_SM) k_pencil(Params P) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ TreeSmem ts;
     __shared__ uint64_t bars[2];
     __shared__ uint32_t tmem_base;
-    __shared__ int s_item, s_ok;
+    __shared__ Item s_it[2];
+    __shared__ int s_ok;
     const int t = threadIdx.x, warp = t >> 5;
-    // direction tree tables into shared memory
+    const int nT = tree_items(P.n_c, P.tr.n_grp), nR = P.n_used;
+    const int nstage = P.n_rho + RLAG;
+    // direction tree tables and the list's stage offsets into shared memory
+    for (int e = t; e <= P.tr.n_grp; e += NT) ts.grp[e] = __ldg(&P.tr.grp[e]);
     for (int e = t; e < P.tr.n_s0; e += NT) ts.s0_dir[e] = __ldg(&P.tr.s0_dir[e]);
     for (int e = t; e <= P.tr.n_s0; e += NT) ts.s0_child[e] = __ldg(&P.tr.s0_child[e]);
     for (int e = t; e < P.tr.n_s01; e += NT) ts.s01_dir[e] = __ldg(&P.tr.s01_dir[e]);
@@ -651,11 +726,20 @@ __global__ void __launch_bounds__(NT, CTAS_PER_SM) k_pencil(Params P) {
         ts.step_sel[e] = __ldg(&P.tr.step_sel[e]);
         ts.step_w[e] = __ldg(&P.tr.step_w[e]);
     }
+    int stage = 0;                                     // thread 0: decoding cursor
     if (t == 0) {
+        int off = 0;
+        for (int st = 0; st < nstage; ++st) {
+            ts.stage_off[st] = off;
+            int nt, nf, nr;
+            stage_counts(st, P.n_rho, nT, nR, nt, nf, nr);
+            off += nt + nf + nr;
+        }
+        ts.stage_off[nstage] = off;
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
         mbar_init_fence();
-        s_item = atomicAdd(P.ctr, 1);
+        s_it[0] = decode_item(P, ts.stage_off, stage, atomicAdd(P.ctr, 1));
     }
     if (warp == 0) tc_alloc<TMEM_COLS>(&tmem_base);
     tc_fence_before_sync();
@@ -664,25 +748,26 @@ __global__ void __launch_bounds__(NT, CTAS_PER_SM) k_pencil(Params P) {
     const uint32_t tmem = tmem_base;
     uint32_t par = 0;                                  // parity bits of the next phases of bars[0], bars[1]
     int* abort_flag = P.ctr + 1;
-    const int nT = tree_items(P.n_c, P.tr.n_s0), nR = P.n_used * NKB;
-    for (;;) {
-        const Item it = decode_item(P, s_item);
+    Item prev{IT_END, 0, 0};
+    for (int i = 0;; ++i) {
+        const Item it = s_it[i & 1];
+        // lane 0 of warp 1 publishes the previous item while thread 0 claims the
+        // next one and waits for this one's dependencies
+        if (t == 32 && prev.kind != IT_END) publish(P, prev);
         if (it.kind == IT_END) break;
         int next = 0;
         if (t == 0) {
-            next = atomicAdd(P.ctr, 1);                // the next item, claimed now, used at the end
-            bool ok = *reinterpret_cast<volatile int*>(abort_flag) == 0;
+            // the next item is claimed now; it is decoded and stored once this item is done
+            next = atomicAdd(P.ctr, 1);
             const int nr = P.n_rho;
-            if (ok && it.kind == IT_TREE && it.q >= NXB)
-                ok = wait_at_least(P.ctr + ctr_fused(nr, it.q - NXB), NLB, abort_flag);
-            if (ok && it.kind == IT_FUSED) {
-                ok = wait_at_least(P.ctr + ctr_tree(nr, it.q), nT, abort_flag);
-                if (ok && it.q >= NPB) ok = wait_at_least(P.ctr + ctr_radial(nr, it.q - NPB), nR, abort_flag);
-            }
-            if (ok && it.kind == IT_RADIAL) {
-                ok = wait_at_least(P.ctr + ctr_fused(nr, it.q), NLB, abort_flag);
-                if (ok) ok = wait_at_least(P.ctr + ctr_acc(nr, it.local), it.q, abort_flag);
-            }
+            bool ok = true;
+            if (it.kind == IT_TREE && it.q >= NXB)
+                ok = wait_at_least(P.ctr + ctr_fused(nr, it.q - NXB), NLB, nullptr, 0, abort_flag);
+            else if (it.kind == IT_FUSED)
+                ok = wait_at_least(P.ctr + ctr_tree(nr, it.q), nT,
+                                   it.q >= NPB ? P.ctr + ctr_radial(nr, it.q - NPB) : nullptr, nR, abort_flag);
+            else if (it.kind == IT_RADIAL)
+                ok = wait_at_least(P.ctr + ctr_fused(nr, it.q), NLB, P.ctr + ctr_acc(nr, it.local), it.q, abort_flag);
             if (!ok && *reinterpret_cast<volatile int*>(abort_flag) == 0) {
                 atomicOr(P.err, kErrTimeout);
                 atomicExch(abort_flag, 1);
@@ -700,21 +785,9 @@ __global__ void __launch_bounds__(NT, CTAS_PER_SM) k_pencil(Params P) {
                 atomicExch(abort_flag, 1);
             }
         }
+        if (t == 0) s_it[(i + 1) & 1] = decode_item(P, ts.stage_off, stage, next);
         __syncthreads();                               // every thread's writes of the item are done
-        if (t == 0) {
-            // publish them (to later generic and bulk-copy readers), then count the item
-            fence_proxy_async_global();
-            __threadfence();
-            const int nr = P.n_rho;
-            if (it.kind == IT_TREE) red_release_add(P.ctr + ctr_tree(nr, it.q), 1);
-            else if (it.kind == IT_FUSED) red_release_add(P.ctr + ctr_fused(nr, it.q), 1);
-            else {
-                red_release_add(P.ctr + ctr_acc(nr, it.local), 1);
-                red_release_add(P.ctr + ctr_radial(nr, it.q), 1);
-            }
-            s_item = next;
-        }
-        __syncthreads();
+        prev = it;
     }
     tc_fence_before_sync();
     __syncthreads();

@@ -100,3 +100,57 @@ def test_autotune_picks_a_candidate_and_caches_it(tmp_path):
         assert (after - before).abs().max().item() <= 1e-6 * scale
     finally:
         g.close()
+
+
+# the six-grid uneven mixed batch: (N, d, gamma, M, r), R = L = 8, N_rho = N, bases seeded 2114 + i
+C5_GRIDS = [(24, 3, 0.0, 38, 32), (32, 3, 1.0, 38, 16), (48, 3, 0.0, 86, 8), (64, 3, 1.0, 86, 4),
+            (64, 2, 0.0, 16, 16), (128, 2, 1.0, 16, 8)]
+# sampled pair per grid checked against the oracle (None: the 64^3 grid at N_rho = 64 takes the
+# oracle several minutes; its kernels are the ones the 64^3 full-quadrature test checks)
+C5_SAMPLES = [(3, 17), (5, 2), (1, 1), None, (0, 15), (6, 3)]
+
+
+@pytest.mark.slow
+def test_c5_six_grid_batch_against_oracle():
+    """The whole C5 workload (six grids, 1680 pairs and six projections) as one
+    graph replay; each grid's replayed Q equals its individual call bit for
+    bit, and one sampled pair per grid matches the oracle (FP32 gate 1e-5)."""
+    import torch
+    B = require_gpu()
+    grids, items, fields = [], [], []
+    for i, (N, d, gamma, M, r) in enumerate(C5_GRIDS):
+        g = B.boltz_grid_init(N, d, 8.0, 8.0, gamma, N, M)
+        grids.append(g)
+        V = as_fp32(W.hermite_maxwellian_basis(N, d, 8.0, r, seed=2114 + i))
+        fields.append(V)
+        f = torch.tensor(V, dtype=torch.float32, device="cuda")
+        pj = [j for j in range(r) for _ in range(r)]
+        pl = [l for _ in range(r) for l in range(r)]
+        items.append(dict(grid=g, fields=f, spectra=torch.zeros((r,) + g.half_shape, dtype=torch.complex64,
+                                                                device="cuda"),
+                          pair_j=pj, pair_l=pl, Q_out=torch.full((r * r,) + g.shape, float("nan"), device="cuda"),
+                          V=f, T_out=torch.full((r, r, r), float("nan"), device="cuda")))
+    batch = B.boltz_batch_plan(items)
+    try:
+        B.boltz_batch_run(batch)
+        torch.cuda.synchronize()
+        for g in grids:
+            B.boltz_sync_status(g)
+        replayed = [it["Q_out"].clone() for it in items]
+    finally:
+        batch.close()
+    for i, ((N, d, gamma, M, r), g, it) in enumerate(zip(C5_GRIDS, grids, items)):
+        spec = B.boltz_spectrum(g, it["fields"])
+        Q1 = B.boltz_collide_batched(g, spec, it["pair_j"], it["pair_l"])
+        B.boltz_sync_status(g)
+        assert torch.equal(replayed[i], Q1), i
+        if C5_SAMPLES[i] is None:
+            continue
+        a, b = C5_SAMPLES[i]
+        sub = sorted({a, b})
+        loc = {k: n for n, k in enumerate(sub)}
+        _, Qo, s = oracle_collide((N, d, 8.0, 8.0, gamma, N, M), fields[i][sub], [(loc[a], loc[b])])
+        Qg = replayed[i][a * r + b].cpu().numpy().astype(np.float64)[None]
+        assert rel_err(Qg, Qo, s).max() < 1e-5, i
+    for g in grids:
+        g.close()

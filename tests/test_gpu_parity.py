@@ -286,3 +286,19 @@ def test_c4_full_size_gain_symmetry_and_bilinearity(B):
     pred_f = 0.3 * Qg[2 * 8 + 1] + 0.7 * Qg[2 * 8 + 5]
     assert np.max(np.abs(Qg[64] - pred_g)) / scale < TOL
     assert np.max(np.abs(Qg[65] - pred_f)) / scale < TOL
+
+
+@pytest.mark.slow
+def test_c4_full_quadrature_pair_against_oracle(B):
+    """C4 at its full quadrature (64^3 on [-10,10]^3, gamma = 1, R = 10,
+    N_rho = 32 x M = 86, rank-8 basis, seed 2113): the pair Q(V_3, V_3) of the
+    64-pair batch against the oracle, FP32 form at 1e-5 and split-precision
+    form at 1e-3 (the oracle of one input takes ~2 minutes on 8 cores)."""
+    cfg = (64, 3, 10.0, 10.0, 1.0, 32, 86)
+    V = as_fp32(W.hermite_maxwellian_basis(64, 3, 10.0, 8, seed=2113))
+    pairs = [(j, l) for j in range(8) for l in range(8)]
+    Qf = gpu_collide(B, cfg, V, pairs, form=0)[3 * 8 + 3][None]
+    Qs = gpu_collide(B, cfg, V, pairs, form=2)[3 * 8 + 3][None]
+    _, Qo, s = oracle_collide(cfg, V[3:4], [(0, 0)])
+    assert rel_err(Qf, Qo, s).max() < TOL
+    assert rel_err(Qs, Qo, s).max() < 1e-3

@@ -16,7 +16,7 @@ pytestmark = pytest.mark.gpu
 TOL = 1e-5
 
 
-@pytest.mark.parametrize("N,d,r", [(16, 3, 16), (32, 2, 32)])
+@pytest.mark.parametrize("N,d,r", [(16, 3, 16), (32, 2, 32), (32, 2, 64)])
 def test_noalloc_projection_matches_allocating_projection(N, d, r):
     import torch
     B = require_gpu()
