@@ -69,7 +69,7 @@ struct Plan {
     int pen_n_used = 0;
     std::vector<int> pen_slots;           // used TRI16 slots, ascending
     std::vector<char> pen_blob;           // direction tree + slot list (device image)
-    size_t off_pen_blob = 0, off_X = 0, off_Pt = 0, off_ctr = 0;
+    size_t off_pen_blob = 0, off_X = 0, off_Pt = 0, off_ctr = 0, off_qstd = 0;
     size_t pen_off[9] = {};               // offsets inside the blob: grp, s0_dir, s0_child,
                                           // s01_dir, step_blk, step_dir, step_sel, step_w, slots
 };
@@ -401,8 +401,10 @@ boltz_status build_plan_pencil(const boltz_grid_s* g, const int32_t* pj, const i
     w = align_up(w + size_t(pc::NXB) * T.n_s01 * pc::NLB * pc::XBLK * sizeof(float2), 256);
     plan.off_Pt = w;
     w = align_up(w + size_t(pc::NPB) * pc::NSLOT * pc::NKB * pc::PLANE * sizeof(float2), 256);
-    plan.off_qhat = w;
+    plan.off_qhat = w;                     // packed running sums, then the final sums (standard layout)
     w = align_up(w + size_t(plan.pen_n_used) * pc::NKB * pc::QBLK * sizeof(float2), 256);
+    plan.off_qstd = w;
+    w = align_up(w + size_t(plan.pen_n_used) * pc::HALF * sizeof(float2), 256);
     plan.off_ctr = w;
     w = align_up(w + size_t(pc::ctr_count(g->n_rho, plan.pen_n_used)) * sizeof(int), 256);
     plan.off_A = plan.off_P = plan.off_img = w;
@@ -1578,6 +1580,7 @@ boltz_status run_pencil(boltz_grid_s* g, const float2* spectra, float* Q_out, cu
     P.X = reinterpret_cast<float2*>(ws + plan.off_X);
     P.Pt = reinterpret_cast<float2*>(ws + plan.off_Pt);
     P.qhat = reinterpret_cast<float2*>(ws + plan.off_qhat);
+    P.qstd = reinterpret_cast<float2*>(ws + plan.off_qstd);
     P.slots = reinterpret_cast<const int*>(blob + plan.pen_off[8]);
     P.ctr = reinterpret_cast<int*>(ws + plan.off_ctr);
     P.err = g->d_err;
@@ -1606,7 +1609,7 @@ boltz_status run_pencil(boltz_grid_s* g, const float2* spectra, float* Q_out, cu
         pc::k_pencil<<<grid, pc::NT, pc::SM_TOTAL, st>>>(P);
     }
     OutParams op{};
-    op.qhat = P.qhat;
+    op.qhat = P.qstd;
     op.fN = fN;
     op.lam = fN + size_t(nc) * g->n;
     op.out_start = reinterpret_cast<const int*>(ws + plan.off_plan + c.off_start);
@@ -1615,10 +1618,8 @@ boltz_status run_pencil(boltz_grid_s* g, const float2* spectra, float* Q_out, cu
     op.err = g->d_err;
     op.U = plan.pen_n_used;
     {
-        // gain synthesis from the packed Qhat+ layout of the pipelined kernel
-        using CG = ClusterGeo<32, 2>;
         ProfScope ps(g, BOLTZ_KCLASS_OUTPUT, st);
-        k_output_cl<32, 2, true><<<2 * op.U, CG::NT, CG::SMEM, st>>>(op);
+        dp->output(op, st);
     }
     BZ_CUDA(cudaGetLastError());
     return BOLTZ_OK;
@@ -2247,7 +2248,7 @@ boltz_status boltz_grid_init(boltz_grid* out, int N, int d_v, double L, double R
         cudaFuncAttributes fa;
         int regs_sm = 0, smem_sm = 0, resv = 0;
         if (set_smem(pc::k_pencil, pc::SM_TOTAL) != cudaSuccess ||
-            set_smem(k_output_cl<32, 2, true>, ClusterGeo<32, 2>::SMEM) != cudaSuccess ||
+
             cudaFuncGetAttributes(&fa, pc::k_pencil) != cudaSuccess ||
             cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, g->device) != cudaSuccess ||
             cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, g->device) != cudaSuccess ||

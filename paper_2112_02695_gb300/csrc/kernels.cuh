@@ -663,25 +663,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(ClusterGeo<N, CL>::
     }
 }
 
-// Qhat+ value at (k0, k1, k2).  Standard layout: the half spectrum of every
-// slot.  PK (the pipelined schedule's layout, 32^3 only): per slot four blocks
-// of 4 columns, [k2 / 4][k0][k1][k2 % 4], where column 0 holds
-// Y = A + i B for the two real-field planes A (k2 = 0) and B (k2 = N/2), both
-// Hermitian in (k0, k1): A = (Y(k) + conj Y(-k)) / 2, B = (Y(k) - conj Y(-k)) / 2i.
-template <int N, bool PK>
-__device__ __forceinline__ float2 qhat_at(const float2* __restrict__ src, int k0, int k1, int k2) {
-    if constexpr (!PK) {
-        return src[(k0 * N + k1) * (N / 2 + 1) + k2];
-    } else {
-        if (k2 > 0 && k2 < N / 2) return src[(((k2 >> 2) * N + k0) * N + k1) * 4 + (k2 & 3)];
-        const float2 y = src[(k0 * N + k1) * 4];
-        const float2 ym = src[(((N - k0) % N) * N + (N - k1) % N) * 4];
-        return k2 == 0 ? make_float2(0.5f * (y.x + ym.x), 0.5f * (y.y - ym.y))
-                       : make_float2(0.5f * (y.y + ym.y), -0.5f * (y.x - ym.x));
-    }
-}
-
-template <int N, int CL, bool PK = false>
+template <int N, int CL>
 __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(ClusterGeo<N, CL>::NT, 1) k_output_cl(OutParams P) {
     using G = Geo<N, 3>;
     using CG = ClusterGeo<N, CL>;
@@ -695,7 +677,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(ClusterGeo<N, CL>::
     const int u = blockIdx.x / CL;
     const bool active = u < P.U;
     const int lt = threadIdx.x;
-    const float2* __restrict__ src = P.qhat + (size_t)u * (PK ? N * N * (N / 2) : G::half);
+    const float2* __restrict__ src = P.qhat + (size_t)u * G::half;
     float2 x[N];
     // axis 0 over every column (k1 in this CTA's range, k2 = 0..N/2), sign (-1)^k from the index parity
     if (active) {
@@ -703,7 +685,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(ClusterGeo<N, CL>::
             const int k1 = rank * PP + c / NH, k2 = c % NH;
 #pragma unroll
             for (int k0 = 0; k0 < N; ++k0) {
-                const float2 v = qhat_at<N, PK>(src, k0, k1, k2);
+                const float2 v = src[(k0 * N + k1) * NH + k2];
                 x[k0] = ((k0 + k1 + k2) & 1) ? make_float2(-v.x, -v.y) : v;
             }
             fft_reg<N, true>(x);

@@ -17,11 +17,12 @@
 //   25 distinct (sigma_0, sigma_1) values, so computing each partial
 //   transform once per distinct value does the axis-0 work 9 times and the
 //   axis-1 work 25 times per (node, input) instead of 38 times each.
-// * TREE items (node q, input j, block of 4 k_2 columns, one sigma_0 value):
-//   the axis-0 pass of its columns, then the axis-1 pass for every
-//   (sigma_0, sigma_1) below it, written as "X blocks" laid out for the
-//   consumer: X[s01][line block][j][k_2][4 lines].  The axes 0 and 1 never
-//   mix k_2 columns, so a block of columns is an independent problem.
+// * TREE items (node q, input j, block of 4 k_2 columns, group of sigma_0
+//   values): the axis-0 pass of its columns for each sigma_0, then the axis-1
+//   pass for every (sigma_0, sigma_1) below it, written as "X blocks" laid
+//   out for the consumer: X[s01][line block][j][k_2][4 lines].  The axes 0
+//   and 1 never mix k_2 columns, so a block of columns is an independent
+//   problem.
 // * FUSED items (node q, line block of 4 lines (i0, i1) = 128 voxels): for
 //   every direction, the axis-2 complex-to-real transform of the X block of
 //   its (sigma_0, sigma_1) with the phase phi_2(s_2) into shared memory, and
@@ -32,12 +33,15 @@
 //   8).  The shifted fields never leave the SM.  At the end the item applies
 //   the first pass of the forward transform (real-to-complex along axis 2)
 //   to its 136 gain fields and writes half spectra of its lines ("Pt planes").
-// * RADIAL items (node q, gain slot u, block of 4 k_2 columns): the forward
-//   axis-1 and axis-0 passes of the slot's Pt plane columns, the multiplier
-//   c_q(|k|) (-1)^k, accumulated into Qhat+[u] (node by node, in order).
-//   The k_2 = 0 and k_2 = N/2 planes of a real field are real in (i0, i1);
-//   they travel as one complex column (re = k_2 0, im = k_2 N/2) and are
-//   separated with the conjugate-symmetry identity after the 2D transform.
+// * RADIAL items (node q, gain slot u): for each block of 4 k_2 columns, the
+//   forward axis-1 and axis-0 passes of the slot's Pt plane columns and the
+//   multiplier c_q(|k|) (-1)^k, accumulated into Qhat+[u] (node by node, in
+//   order) in a packed layout copied in and out of shared memory in one piece;
+//   the last node writes the finished sums in the standard half-spectrum
+//   layout the output kernel reads.  The k_2 = 0 and k_2 = N/2 planes of a
+//   real field are real in (i0, i1): they travel as one complex column
+//   (re = k_2 0, im = k_2 N/2), and so do their running sums, separated with
+//   the conjugate-symmetry identity at the end.
 //
 // Scheduling: a fixed list of items, stage by stage (stage s: tree items of
 // node s, fused items of node s-1, radial items of node s-3), claimed in order
@@ -54,9 +58,9 @@
 // word and raises an abort flag, after which every CTA drains the list
 // without working, so the launch always ends.  X (three node buffers, ~54 MB
 // each, so that a tree item never waits on the fused items of the previous
-// node) and Pt (four node buffers, ~18 MB each) stay mostly in the 126 MB L2;
-// the lines of an X block or Pt plane are dropped from L2 without write-back
-// once their single consumer has copied them (discard.global.L2).
+// node) and Pt (four node buffers, ~18 MB each) stay mostly in the 126 MB L2.
+// (Dropping consumed lines from L2 with discard.global.L2 saves their
+// write-back but was measured 6% slower overall.)
 #pragma once
 
 #include <cuda_runtime.h>
@@ -139,9 +143,11 @@ struct Params {
     const float* ctab;       // [n_rho][SMAX + 1]: c_q(|k|^2) including 1/n
     float2* X;               // [NXB][n_s01][NLB][XBLK]
     float2* Pt;              // [NPB][NSLOT][NKB][PLANE]
-    float2* qhat;            // [n_used][NKB][QBLK]: Qhat+ of the used slots in the packed layout
-                             // the output kernel reads (k_output_cl with PK): [kb][k0][k1][c],
+    float2* qhat;            // [n_used][NKB][QBLK]: running Qhat+ sums of the used slots, packed:
+                             // [kb][k0][k1][c],
                              // k2 = 4 kb + c, column 0 holding Y = A + i B of the planes k2 = 0, N/2
+    float2* qstd;            // [n_used][HALF]: the final Qhat+ in the standard half-spectrum
+                             // layout, written by the last node's radial items
     const int* slots;        // [n_used]: slots whose gain is needed
     int* ctr;                // counters, zeroed before the launch (layout in ctr_*)
     int* err;                // device error word
@@ -222,11 +228,6 @@ __device__ __forceinline__ void red_release_add(int* p, int v) {
 
 // Orders generic-proxy accesses to global memory with async-proxy (bulk copy) accesses.
 __device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
-
-// Drops one 128-byte L2 line without writing it back (its data becomes undefined).
-__device__ __forceinline__ void discard_l2(const void* p) {
-    asm volatile("discard.global.L2 [%0], 128;" ::"l"(p) : "memory");
-}
 
 // Bounded wait (one thread) until *c1 >= t1 and *c2 >= t2 (c2 may be null).
 // Both counters are read at once, so a satisfied dependency costs one memory
@@ -462,15 +463,7 @@ __device__ bool fused_item(const Params& P, const TreeSmem& ts, int q, int lb, u
             }
             fft_reg<N, true>(x);
         }
-        // the X blocks are consumed: drop them from L2 and let A overwrite the stage
-        for (int l = t; l < 4 * (XBLK * 8 / 128); l += NT) {
-            const int k = l / (XBLK * 8 / 128);
-            const int blk = k == 0 ? ts.step_blk[st].x : k == 1 ? ts.step_blk[st].y : k == 2 ? ts.step_blk[st].z
-                                                                                        : ts.step_blk[st].w;
-            if (blk >= 0)
-                discard_l2(reinterpret_cast<const char*>(Xn + (size_t)blk * NLB * XBLK) +
-                           (size_t)(l % (XBLK * 8 / 128)) * 128);
-        }
+        // the X values are in registers: A may overwrite the stage
         __syncthreads();
         float* Ad = A + d * ADS + j * AJS + lp * 2 * N;
         if (work) {
@@ -634,7 +627,6 @@ __device__ bool radial_item(const Params& P, int q, int ui, unsigned char* smem,
             if (t == 0) bulk_wait_all();
             return false;
         }
-        for (int l = t; l < PLANE * 8 / 128; l += NT) discard_l2(reinterpret_cast<const char*>(src) + (size_t)l * 128);
         float2 x[N];
         {
             const int i0 = t >> 2;
@@ -678,9 +670,28 @@ __device__ bool radial_item(const Params& P, int q, int ui, unsigned char* smem,
             if (!first) v = make_float2(v.x + o->x, v.y + o->y);
             *o = v;
         }
-        fence_proxy_async_smem();
-        __syncthreads();
-        if (t == 0) bulk_s2g(qblk, Qs, QBLK * 8);
+        if (q < P.n_rho - 1) {
+            fence_proxy_async_smem();
+            __syncthreads();
+            if (t == 0) bulk_s2g(qblk, Qs, QBLK * 8);
+        } else {
+            // last node: the finished sums in the standard half-spectrum layout,
+            // the packed column split back into its k2 = 0 and k2 = N/2 planes
+            __syncthreads();
+            float2* qs = P.qstd + (size_t)ui * HALF;
+#pragma unroll 4
+            for (int k0 = 0; k0 < N; ++k0) {
+                const float2 y = Qs[(k0 * N + k1) * KB + c];
+                if (kb != 0 || c != 0) {
+                    qs[(k0 * N + k1) * NH + k2] = y;
+                } else {
+                    const float2 ym = Qs[(((N - k0) % N) * N + k1m) * KB];
+                    qs[(k0 * N + k1) * NH] = make_float2(0.5f * (y.x + ym.x), 0.5f * (y.y - ym.y));
+                    qs[(k0 * N + k1) * NH + H] = make_float2(0.5f * (y.y + ym.y), -0.5f * (y.x - ym.x));
+                }
+            }
+            __syncthreads();
+        }
     }
     if (t == 0) {
         bulk_wait_all();
