@@ -44,7 +44,7 @@
 //   the conjugate-symmetry identity at the end.
 //
 // Scheduling: a fixed list of items, stage by stage (stage s: tree items of
-// node s, fused items of node s-1, radial items of node s-3), claimed in order
+// node s, fused items of node s-2, radial items of node s-4), claimed in order
 // from an atomic counter by persistent CTAs (three per SM: 128 threads, at
 // most 168 registers, 67 KB of shared memory and 128 TMEM columns each).  A
 // CTA claims its next item when it starts the current one (the claim's round
@@ -53,12 +53,13 @@
 // points to an item earlier in the list (fused(q) needs all tree(q) and the
 // Pt buffer free; tree(q) needs its X buffer free; radial(q) needs fused(q)
 // and radial(q-1) of its slot), so the lowest unfinished item can always run:
-// progress needs no co-residency.  Each wait is a bounded poll (about one
-// second of device time); a wait that gives up records a timeout in the error
-// word and raises an abort flag, after which every CTA drains the list
-// without working, so the launch always ends.  X (three node buffers, ~54 MB
-// each, so that a tree item never waits on the fused items of the previous
-// node) and Pt (four node buffers, ~18 MB each) stay mostly in the 126 MB L2.
+// progress needs no co-residency.  The two-stage lags give every dependency a
+// stage of slack.  Each wait is a bounded poll (about one second of device
+// time); a wait that gives up records a timeout in the error word and raises
+// an abort flag, after which every CTA drains the list without working, so the
+// launch always ends.  X has four node buffers (~56 MB each) and Pt four
+// (~18 MB each); together they exceed the L2, so most of their lines make one
+// round trip to DRAM, which carries under half of its bandwidth.
 // (Dropping consumed lines from L2 with discard.global.L2 saves their
 // write-back but was measured 6% slower overall.)
 #pragma once
@@ -97,9 +98,10 @@ constexpr int PSS = 4 * N + 4;                 // floats per slot in the epilogu
 constexpr int MAX_ROWS = 32;                   // phase rows a tree item stages (1 + children)
 constexpr int MAX_S = 96;                      // sigma_0 and (sigma_0, sigma_1) values (M <= 86)
 constexpr int MAX_STEP = 24;                   // fused-item steps (M/2 antipodal pairs, two a step)
-constexpr int NXB = 3;                         // X node buffers
+constexpr int NXB = 4;                         // X node buffers
 constexpr int NPB = 4;                         // Pt node buffers
-constexpr int RLAG = 3;                        // radial items of node s - RLAG run in stage s
+constexpr int FLAG = 2;                        // fused items of node s - FLAG run in stage s
+constexpr int RLAG = 4;                        // radial items of node s - RLAG run in stage s
 constexpr uint32_t TMEM_COLS = 128;            // per CTA (three CTAs use 384 of the SM's 512 columns)
 constexpr int CTAS_PER_SM = 3;
 
@@ -166,22 +168,42 @@ __host__ __device__ constexpr int ctr_count(int n_rho, int n_used) { return 2 + 
 // TRI16 slot of the unordered pair (a <= b)
 __host__ __device__ constexpr int tri_slot(int a, int b) { return a * NJ - a * (a - 1) / 2 + (b - a); }
 
-// (row, column) of every TRI16 slot, for compile-time indexing in unrolled loops
-struct TriTable {
-    int x[NSLOT], y[NSLOT];
+// Accumulator columns of a fused item.  Column pair (2i, 2i + 1), i < 64, holds
+// the slots (x, y) and (x, y + 1) with y even, so that one packed two-lane FMA
+// updates both from the natural input pairs (2h, 2h + 1); row x runs over
+// y = x (x even) or x + 1 (x odd) .. 15.  The 8 diagonal slots (x, x) of odd x
+// left over are kept in registers (column 128 + (x - 1) / 2).
+struct PairTable {
+    int x[NTSLOT / 2], yh[NTSLOT / 2];   // pair i: row x, columns y = 2 yh, 2 yh + 1
 };
-__host__ __device__ constexpr TriTable make_tri_table() {
-    TriTable t{};
+__host__ __device__ constexpr PairTable make_pair_table() {
+    PairTable t{};
     int i = 0;
     for (int a = 0; a < NJ; ++a)
-        for (int b = a; b < NJ; ++b) {
+        for (int b = (a + 1) & ~1; b < NJ; b += 2) {
             t.x[i] = a;
-            t.y[i] = b;
+            t.yh[i] = b / 2;
             ++i;
         }
     return t;
 }
-constexpr TriTable kTri = make_tri_table();
+constexpr PairTable kPair = make_pair_table();
+
+// TRI16 slot of accumulator column c (for the epilogue's runtime index)
+struct ColSlots {
+    int u[NSLOT];
+};
+__host__ __device__ constexpr ColSlots make_col_slots() {
+    ColSlots cs{};
+    const PairTable pt = make_pair_table();
+    for (int i = 0; i < NTSLOT / 2; ++i) {
+        cs.u[2 * i] = tri_slot(pt.x[i], 2 * pt.yh[i]);
+        cs.u[2 * i + 1] = tri_slot(pt.x[i], 2 * pt.yh[i] + 1);
+    }
+    for (int k = 0; k < NRSLOT; ++k) cs.u[NTSLOT + k] = tri_slot(2 * k + 1, 2 * k + 1);
+    return cs;
+}
+__constant__ ColSlots kColSlots = make_col_slots();
 
 enum { IT_FUSED = 0, IT_TREE = 1, IT_RADIAL = 2, IT_END = 3 };
 
@@ -190,13 +212,13 @@ struct Item {
 };
 
 __host__ __device__ inline int tree_items(int n_c, int n_grp) { return n_c * NKB * n_grp; }
-constexpr int MAX_STAGE = 128 + 3 + 1;         // stages: n_rho (<= 128) + RLAG, plus the end
+constexpr int MAX_STAGE = 128 + RLAG + 1;      // stages: n_rho (<= 128) + RLAG, plus the end
 
 // Items of stage s in list order: tree items of node s, fused items of node
-// s-1, radial items of node s - RLAG.
+// s - FLAG, radial items of node s - RLAG.
 __host__ __device__ inline void stage_counts(int s, int n_rho, int nT, int nR, int& t, int& f, int& r) {
     t = (s < n_rho) ? nT : 0;
-    f = (s >= 1 && s <= n_rho) ? NLB : 0;
+    f = (s >= FLAG && s < n_rho + FLAG) ? NLB : 0;
     r = (s >= RLAG && s < n_rho + RLAG) ? nR : 0;
 }
 
@@ -212,7 +234,7 @@ __device__ __noinline__ Item decode_item(const Params& P, const int* off, int& s
     int k = idx - off[stage];
     if (k < t) return {IT_TREE, stage, k};
     k -= t;
-    if (k < f) return {IT_FUSED, stage - 1, k};
+    if (k < f) return {IT_FUSED, stage - FLAG, k};
     return {IT_RADIAL, stage - RLAG, k - f};
 }
 
@@ -364,35 +386,51 @@ __device__ void tree_item(const Params& P, const TreeSmem& ts, int q, int local,
 }
 
 // ------------------------------------------------------------------ fused item
-// The X blocks and axis-2 phase rows of step st into the stage (thread 0).
+// Stage slot k (0..3) of step st: its X block and axis-2 phase row into the
+// stage.  Issued by lane 0 of warp k, one of the four arrivals on the stage's
+// mbarrier, so that no single thread pays for all eight copies of a step.
 __device__ __forceinline__ void fused_issue(const Params& P, const TreeSmem& ts, const float2* Xn, int q, int st,
-                                            float2* Xs, float2* ph2, uint64_t* bar) {   // Xs, ph2: the stage
+                                            int k, float2* Xs, float2* ph2, uint64_t* bar) {   // Xs, ph2: the stage
     const int4 blk = ts.step_blk[st];
     const int4 dir = ts.step_dir[st];
-    const int bl[4] = {blk.x, blk.y, blk.z, blk.w};
-    const int dr[4] = {dir.x, dir.y, dir.z, dir.w};
-    uint32_t bytes = 0;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        if (bl[k] >= 0) bytes += XBLK * 8;
-        if (dr[k] >= 0) bytes += H * 8;
-    }
+    const int bl = k == 0 ? blk.x : k == 1 ? blk.y : k == 2 ? blk.z : blk.w;
+    const int dr = k == 0 ? dir.x : k == 1 ? dir.y : k == 2 ? dir.z : dir.w;
+    const uint32_t bytes = (bl >= 0 ? XBLK * 8 : 0) + (dr >= 0 ? H * 8 : 0);
     mbar_arrive_expect_tx(bar, bytes);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        if (bl[k] >= 0) bulk_g2s(Xs + k * XBLK, Xn + (size_t)bl[k] * NLB * XBLK, XBLK * 8, bar);
-        if (dr[k] >= 0) bulk_g2s(ph2 + k * H, P.phase + ((size_t)(q * P.M + dr[k]) * 3 + 2) * N, H * 8, bar);
-    }
+    if (bl >= 0) bulk_g2s(Xs + k * XBLK, Xn + (size_t)bl * NLB * XBLK, XBLK * 8, bar);
+    if (dr >= 0) bulk_g2s(ph2 + k * H, P.phase + ((size_t)(q * P.M + dr) * 3 + 2) * N, H * 8, bar);
 }
 
-// acc(slot) += a[x] c[y] + c[x] a[y] for the 32 slots of TMEM chunk CH
+// Two FP32 lanes in one 64-bit register, and the packed FMA of sm_100+.
+__device__ __forceinline__ uint64_t f2pack(float lo, float hi) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2unpack(uint64_t r, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(r));
+}
+__device__ __forceinline__ uint64_t ffma2(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+// acc(x, y) += a[x] c[y] + c[x] a[y] for the 16 column pairs of TMEM chunk CH
+// (two slots per packed FMA; a2, c2: the natural pairs (2h, 2h + 1) of a, c)
 template <int CH>
-__device__ __forceinline__ void contract_chunk(uint32_t (&r)[32], const float (&a)[NJ], const float (&cc)[NJ]) {
+__device__ __forceinline__ void contract_chunk(uint32_t (&r)[32], const float (&a)[NJ], const float (&cc)[NJ],
+                                               const uint64_t (&a2)[NJ / 2], const uint64_t (&c2)[NJ / 2]) {
 #pragma unroll
-    for (int k = 0; k < 32; ++k) {
-        constexpr TriTable tt = kTri;
-        const int x = tt.x[CH * 32 + k], y = tt.y[CH * 32 + k];
-        r[k] = __float_as_uint(fmaf(a[x], cc[y], fmaf(cc[x], a[y], __uint_as_float(r[k]))));
+    for (int k = 0; k < 16; ++k) {
+        constexpr PairTable pt = kPair;
+        const int x = pt.x[CH * 16 + k], yh = pt.yh[CH * 16 + k];
+        uint64_t v = f2pack(__uint_as_float(r[2 * k]), __uint_as_float(r[2 * k + 1]));
+        v = ffma2(f2pack(a[x], a[x]), c2[yh], ffma2(f2pack(cc[x], cc[x]), a2[yh], v));
+        float lo, hi;
+        f2unpack(v, lo, hi);
+        r[2 * k] = __float_as_uint(lo);
+        r[2 * k + 1] = __float_as_uint(hi);
     }
 }
 
@@ -405,11 +443,11 @@ __device__ bool fused_item(const Params& P, const TreeSmem& ts, int q, int lb, u
     const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);    // this warp's 32 TMEM lanes
     auto stage_x = [&](int b) { return reinterpret_cast<float2*>(smem + b * SM_STAGE); };
     auto stage_ph = [&](int b) { return reinterpret_cast<float2*>(smem + SM_PH2) + b * 4 * H; };
-    if (t == 0) {
+    if ((t & 31) == 0) {
         fence_proxy_async_global();
         fence_proxy_async_smem();
-        fused_issue(P, ts, Xn, q, 0, stage_x(0), stage_ph(0), &bars[0]);
-        if (nst > 1) fused_issue(P, ts, Xn, q, 1, stage_x(1), stage_ph(1), &bars[1]);
+        fused_issue(P, ts, Xn, q, 0, warp, stage_x(0), stage_ph(0), &bars[0]);
+        if (nst > 1) fused_issue(P, ts, Xn, q, 1, warp, stage_x(1), stage_ph(1), &bars[1]);
     }
     {
         uint32_t z[32];
@@ -430,7 +468,10 @@ __device__ bool fused_item(const Params& P, const TreeSmem& ts, int q, int lb, u
         par ^= 1u << b;
         if (__syncthreads_or(!ok)) {
             // leave no copy in flight: the other stage may still be landing
-            if (t == 0 && st + 1 < nst) (void)mbar_wait_bounded(&bars[b ^ 1], (par >> (b ^ 1)) & 1u);
+            if (t == 0) {
+                (void)mbar_wait_bounded(&bars[b], ((par >> b) & 1u) ^ 1u);
+                if (st + 1 < nst) (void)mbar_wait_bounded(&bars[b ^ 1], (par >> (b ^ 1)) & 1u);
+            }
             return false;
         }
         const float2* Xs = stage_x(b);
@@ -489,35 +530,40 @@ __device__ bool fused_item(const Params& P, const TreeSmem& ts, int q, int lb, u
                 a[xx] = w * Aa[xx * AJS];
                 cc[xx] = Ac[xx * AJS];
             }
+            uint64_t a2[NJ / 2], c2[NJ / 2];
+#pragma unroll
+            for (int h = 0; h < NJ / 2; ++h) {
+                a2[h] = f2pack(a[2 * h], a[2 * h + 1]);
+                c2[h] = f2pack(cc[2 * h], cc[2 * h + 1]);
+            }
             uint32_t r[32];
             tmem_ld32(tl + 0, r);
             tmem_wait_ld32(r);
-            contract_chunk<0>(r, a, cc);
+            contract_chunk<0>(r, a, cc, a2, c2);
             tmem_st32(tl + 0, r);
             tmem_ld32(tl + 32, r);
             tmem_wait_ld32(r);
-            contract_chunk<1>(r, a, cc);
+            contract_chunk<1>(r, a, cc, a2, c2);
             tmem_st32(tl + 32, r);
             tmem_ld32(tl + 64, r);
             tmem_wait_ld32(r);
-            contract_chunk<2>(r, a, cc);
+            contract_chunk<2>(r, a, cc, a2, c2);
             tmem_st32(tl + 64, r);
             tmem_ld32(tl + 96, r);
             tmem_wait_ld32(r);
-            contract_chunk<3>(r, a, cc);
+            contract_chunk<3>(r, a, cc, a2, c2);
             tmem_st32(tl + 96, r);
 #pragma unroll
             for (int k = 0; k < NRSLOT; ++k) {
-                constexpr TriTable tt = kTri;
-                const int xx = tt.x[NTSLOT + k], yy = tt.y[NTSLOT + k];
-                racc[k] = fmaf(a[xx], cc[yy], fmaf(cc[xx], a[yy], racc[k]));
+                const int xx = 2 * k + 1;                          // diagonal slot (x, x), x odd
+                racc[k] = fmaf(a[xx], cc[xx], fmaf(cc[xx], a[xx], racc[k]));
             }
             tmem_wait_st();
         }
         __syncthreads();                                           // A consumed: stage b is free
-        if (t == 0 && st + 2 < nst) {
+        if ((t & 31) == 0 && st + 2 < nst) {
             fence_proxy_async_smem();
-            fused_issue(P, ts, Xn, q, st + 2, stage_x(b), stage_ph(b), &bars[b]);
+            fused_issue(P, ts, Xn, q, st + 2, warp, stage_x(b), stage_ph(b), &bars[b]);
         }
     }
     // epilogue: the gain fields of the 128 voxels, 64 slots at a time, through
@@ -546,7 +592,7 @@ __device__ bool fused_item(const Params& P, const TreeSmem& ts, int q, int lb, u
         }
         __syncthreads();
         for (int task = t; task < 2 * nsl; task += NT) {
-            const int lp2 = task / nsl, us = task % nsl, u = u0 + us;
+            const int lp2 = task / nsl, us = task % nsl, u = kColSlots.u[u0 + us];
             const float* r1 = Pst + us * PSS + lp2 * 2 * N;           // rows i1 = 2m + lp2 and i1 + 16
             float2 x[N];
             load_two_rows_smem<N>(r1, r1 + N, x);
@@ -609,22 +655,32 @@ __device__ bool radial_item(const Params& P, int q, int ui, unsigned char* smem,
     const float* __restrict__ ct = P.ctab + (size_t)q * (SMAX + 1);
     const int c = t & 3, k1 = t >> 2;
     const int b = wrapk(k1, N), k1m = (N - k1) % N;
+    const float2* src0 = P.Pt + (size_t)((q % NPB) * NSLOT + u) * NKB * PLANE;
+    float2* qblk0 = P.qhat + (size_t)ui * NKB * QBLK;
+    // the plane (bars[2]) and the running-sum block (bars[3]) of a column block travel
+    // separately: each is copied in as soon as its buffer is free, the plane of the
+    // next block while this block accumulates, the sums while the next plane transforms
+    if (t == 0) {
+        fence_proxy_async_global();
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(&bars[2], PLANE * 8);
+        bulk_g2s(S, src0, PLANE * 8, &bars[2]);
+        if (!first) {
+            mbar_arrive_expect_tx(&bars[3], QBLK * 8);
+            bulk_g2s(Qs, qblk0, QBLK * 8, &bars[3]);
+        }
+    }
 #pragma unroll 1
     for (int kb = 0; kb < NKB; ++kb) {
-        const float2* src = P.Pt + ((size_t)((q % NPB) * NSLOT + u) * NKB + kb) * PLANE;
-        float2* qblk = P.qhat + ((size_t)ui * NKB + kb) * QBLK;
-        if (t == 0) {
-            bulk_wait_read();                                   // the previous block's store has read Qs
-            fence_proxy_async_global();
-            fence_proxy_async_smem();
-            mbar_arrive_expect_tx(&bars[0], PLANE * 8 + (first ? 0 : QBLK * 8));
-            bulk_g2s(S, src, PLANE * 8, &bars[0]);
-            if (!first) bulk_g2s(Qs, qblk, QBLK * 8, &bars[0]);
-        }
-        const bool ok = mbar_wait_bounded(&bars[0], par & 1u);
-        par ^= 1u;
+        float2* qblk = qblk0 + (size_t)kb * QBLK;
+        bool ok = mbar_wait_bounded(&bars[2], (par >> 2) & 1u);
+        par ^= 4u;
         if (__syncthreads_or(!ok)) {
-            if (t == 0) bulk_wait_all();
+            if (t == 0) {
+                (void)mbar_wait_bounded(&bars[2], ((par >> 2) & 1u) ^ 1u);   // the copy that was late
+                if (!first) (void)mbar_wait_bounded(&bars[3], (par >> 3) & 1u);
+                bulk_wait_all();
+            }
             return false;
         }
         float2 x[N];
@@ -647,7 +703,19 @@ __device__ bool radial_item(const Params& P, int q, int ui, unsigned char* smem,
 #pragma unroll
             for (int k0 = 0; k0 < N; ++k0) S[k0 * PRS + k1 * KB] = x[k0];
         }
-        __syncthreads();
+        if (!first) {
+            ok = mbar_wait_bounded(&bars[3], (par >> 3) & 1u);
+            par ^= 8u;
+        } else if (t == 0) {
+            bulk_wait_read();                                   // the previous block's store has read Qs
+        }
+        if (__syncthreads_or(!ok)) {
+            if (t == 0) {
+                (void)mbar_wait_bounded(&bars[3], ((par >> 3) & 1u) ^ 1u);
+                bulk_wait_all();
+            }
+            return false;
+        }
         const int k2 = KB * kb + c;
 #pragma unroll
         for (int k0 = 0; k0 < N; ++k0) {
@@ -672,12 +740,28 @@ __device__ bool radial_item(const Params& P, int q, int ui, unsigned char* smem,
         }
         if (q < P.n_rho - 1) {
             fence_proxy_async_smem();
-            __syncthreads();
-            if (t == 0) bulk_s2g(qblk, Qs, QBLK * 8);
+            __syncthreads();                                    // Qs complete, S read for the last time
+            if (t == 0) {
+                bulk_s2g(qblk, Qs, QBLK * 8);
+                if (kb + 1 < NKB) {
+                    mbar_arrive_expect_tx(&bars[2], PLANE * 8);
+                    bulk_g2s(S, src0 + (size_t)(kb + 1) * PLANE, PLANE * 8, &bars[2]);
+                    if (!first) {
+                        bulk_wait_read();                       // the store has read Qs
+                        mbar_arrive_expect_tx(&bars[3], QBLK * 8);
+                        bulk_g2s(Qs, qblk + QBLK, QBLK * 8, &bars[3]);
+                    }
+                }
+            }
         } else {
             // last node: the finished sums in the standard half-spectrum layout,
             // the packed column split back into its k2 = 0 and k2 = N/2 planes
             __syncthreads();
+            if (t == 0 && kb + 1 < NKB) {
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(&bars[2], PLANE * 8);
+                bulk_g2s(S, src0 + (size_t)(kb + 1) * PLANE, PLANE * 8, &bars[2]);
+            }
             float2* qs = P.qstd + (size_t)ui * HALF;
 #pragma unroll 4
             for (int k0 = 0; k0 < N; ++k0) {
@@ -690,7 +774,12 @@ __device__ bool radial_item(const Params& P, int q, int ui, unsigned char* smem,
                     qs[(k0 * N + k1) * NH + H] = make_float2(0.5f * (y.y + ym.y), -0.5f * (y.x - ym.x));
                 }
             }
-            __syncthreads();
+            fence_proxy_async_smem();
+            __syncthreads();                                    // Qs read
+            if (t == 0 && kb + 1 < NKB && !first) {
+                mbar_arrive_expect_tx(&bars[3], QBLK * 8);
+                bulk_g2s(Qs, qblk + QBLK, QBLK * 8, &bars[3]);
+            }
         }
     }
     if (t == 0) {
@@ -719,7 +808,7 @@ __device__ __forceinline__ void publish(const Params& P, const Item& it) {
 __global__ void __launch_bounds__(NT, CTAS_PER_SM) k_pencil(Params P) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ TreeSmem ts;
-    __shared__ uint64_t bars[2];
+    __shared__ uint64_t bars[4];
     __shared__ uint32_t tmem_base;
     __shared__ Item s_it[2];
     __shared__ int s_ok;
@@ -747,8 +836,10 @@ __global__ void __launch_bounds__(NT, CTAS_PER_SM) k_pencil(Params P) {
             off += nt + nf + nr;
         }
         ts.stage_off[nstage] = off;
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
+        mbar_init(&bars[0], 4);                        // fused stages: one arrival per warp
+        mbar_init(&bars[1], 4);
+        mbar_init(&bars[2], 1);                        // radial: Pt planes
+        mbar_init(&bars[3], 1);                        // radial: running-sum blocks
         mbar_init_fence();
         s_it[0] = decode_item(P, ts.stage_off, stage, atomicAdd(P.ctr, 1));
     }
@@ -757,7 +848,7 @@ __global__ void __launch_bounds__(NT, CTAS_PER_SM) k_pencil(Params P) {
     __syncthreads();
     tc_fence_after_sync();
     const uint32_t tmem = tmem_base;
-    uint32_t par = 0;                                  // parity bits of the next phases of bars[0], bars[1]
+    uint32_t par = 0;                                  // parity bits of the next phases of bars[0..3]
     int* abort_flag = P.ctr + 1;
     Item prev{IT_END, 0, 0};
     for (int i = 0;; ++i) {
@@ -783,7 +874,9 @@ __global__ void __launch_bounds__(NT, CTAS_PER_SM) k_pencil(Params P) {
                 atomicOr(P.err, kErrTimeout);
                 atomicExch(abort_flag, 1);
             }
-            s_ok = ok;
+            // after an abort no item works (the CTA whose item failed may hold
+            // stale copy-stage parities)
+            s_ok = ok && *reinterpret_cast<volatile int*>(abort_flag) == 0;
         }
         __syncthreads();
         if (s_ok) {
