@@ -27,7 +27,10 @@ F_2(s) = 2 pi J0(s).  Steps, in the order the method takes them:
   5. Qhat+_k = sum_q b w_q rho_q^{gamma+d-1} F_d(pi rho_q |k| / (2L)) DFT[P_q]_k
   6. loss: Lambda_g = sum_l G-(l) ghat_l e^{i pi l.v/L},
      G-(l) = b |S^{d-1}| sum_q w_q rho_q^{gamma+d-1} F_d(pi rho_q |l| / L);
-     Q- = f_N * Lambda_g
+     Q- = f_N * Lambda_g.  Option loss="mass_consistent": the sigma-average
+     taken with the gain's own direction rule instead of exactly,
+     G-(l) = b F_d(0) sum_q w_q rho_q^{gamma+d-1} sum_p w_p e^{-i pi rho_q l.sigma_p / L}
+           = G_sep(l, -l), so that Qhat_0 (the mass of Q) vanishes to rounding
   7. Q = Re IDFT(Qhat+) - Q-
   8. projection T_kjl = dv^d sum_v V_k(v) Q_jl(v) (midpoint rule, Sec. 2.4)
   9. direct sum (tiny grids): Qhat_k = sum_{l+m = k mod N} [G_sep(l,m) - G-(l)] ghat_l fhat_m
@@ -74,6 +77,7 @@ class Problem:
     n_rho: int = 0
     M: int = 0
     b: float | None = None
+    loss: str = "exact"
     rho: np.ndarray | None = None
     w_rho: np.ndarray | None = None
     sigma: np.ndarray | None = None
@@ -83,6 +87,8 @@ class Problem:
     def __post_init__(self):
         if self.N % 2:
             raise ValueError("N must be even")
+        if self.loss not in ("exact", "mass_consistent"):
+            raise ValueError("loss must be 'exact' or 'mass_consistent'")
         if self.b is None:
             self.b = 1.0 / sphere_area(self.d)
         if self.rho is None:
@@ -211,6 +217,34 @@ def loss_weight(prob: Problem, kmag: np.ndarray) -> np.ndarray:
     return prob.b * sphere_area(prob.d) * acc
 
 
+def loss_weight_mass_consistent(prob: Problem, lvec: np.ndarray) -> np.ndarray:
+    """G-(l) = G_sep(l, -l) = b F_d(0) sum_q w_q rho_q^{gamma+d-1} sum_p w_p
+    exp(-i pi rho_q l.sigma_p / L) for integer frequency vectors l [..., d]:
+    the gain's separated kernel at m = -l, where |l + m| = 0.  The direction
+    rules are centrally symmetric, so the sum is real (its cosine part)."""
+    lv = np.asarray(lvec, dtype=np.float64)
+    acc = np.zeros(lv.shape[:-1])
+    for q in range(prob.n_rho):
+        sig = np.zeros(lv.shape[:-1])
+        for p in range(prob.M):
+            sig += prob.w_sigma[p] * np.cos(math.pi * prob.rho[q] * (lv @ prob.sigma[p]) / prob.L)
+        acc += prob.w_rho[q] * prob.rho[q] ** kernel_power(prob) * sig
+    return prob.b * float(F_d(prob.d, 0.0)) * acc
+
+
+def freq_vectors(prob: Problem) -> np.ndarray:
+    """Integer frequency vector of every spectral index, shape [N]*d + [d]."""
+    fr = freq_of_index(prob.N)
+    return np.stack(np.meshgrid(*([fr] * prob.d), indexing="ij"), axis=-1)
+
+
+def loss_table(prob: Problem) -> np.ndarray:
+    """G-(l) at every spectral index, for the loss reading the problem names."""
+    if prob.loss == "mass_consistent":
+        return loss_weight_mass_consistent(prob, freq_vectors(prob))
+    return loss_weight(prob, kabs(prob))
+
+
 # --------------------------------------------------------------------------
 # the collision operator
 # --------------------------------------------------------------------------
@@ -246,7 +280,7 @@ def collide(prob: Problem, spec: np.ndarray, pairs, return_parts: bool = False):
             P += prob.w_sigma[p] * A[jj] * B[ll]
         Qhat_plus += cq[q][None] * dft(prob, P)
     Q_plus = synthesize(prob, Qhat_plus)
-    Gm = loss_weight(prob, kmag)
+    Gm = loss_table(prob)
     lam = synthesize(prob, Gm[None] * S)          # Lambda_g for every used input
     fN = synthesize(prob, S)                      # f_N on the grid
     Q_minus = loss_field(fN, lam, jj, ll)
@@ -320,8 +354,11 @@ def direct_sum(prob: Problem, ghat: np.ndarray, fhat: np.ndarray) -> np.ndarray:
                 -1j * math.pi * prob.rho[q] * (diff @ prob.sigma[p]) / (2.0 * prob.L))
         G += (prob.b * prob.w_rho[q] * prob.rho[q] ** kernel_power(prob)
               * F_d(d, math.pi * prob.rho[q] * kw_abs / (2.0 * prob.L))) * H
-    labs = np.sqrt(np.sum(lv.astype(np.float64) ** 2, axis=1))
-    G -= loss_weight(prob, labs)[:, None]
+    if prob.loss == "mass_consistent":
+        G -= loss_weight_mass_consistent(prob, lv)[:, None]
+    else:
+        labs = np.sqrt(np.sum(lv.astype(np.float64) ** 2, axis=1))
+        G -= loss_weight(prob, labs)[:, None]
     gl = ghat.reshape(-1)
     fm = fhat.reshape(-1)
     contrib = G * gl[:, None] * fm[None, :]
