@@ -137,7 +137,21 @@ typedef struct {
                               inputs), the node-block schedule elsewhere;
                               BOLTZ_SCHEDULE_NODE_BLOCKS (1): always the node-block
                               schedule (the comparison baseline)                   */
+    int loss;              /* loss weight G-(l) of the separated forms (batched,
+                              plain, split, FP64 check build):
+                              BOLTZ_LOSS_EXACT (0): b |S^{d-1}| sum_q w_q rho_q^{gamma+d-1}
+                              F_d(pi rho_q |l| / L), the exact sigma- and omega-average;
+                              BOLTZ_LOSS_MASS_CONSISTENT (1): G_sep(l, -l) =
+                              b F_d(0) sum_q w_q rho_q^{gamma+d-1} sum_p w_p
+                              cos(pi rho_q l.sigma_p / L), the sigma-average taken with
+                              the gain's own direction rule, so that the k = 0 mode of
+                              Q (its mass) cancels to rounding.  A per-mode table
+                              (half-spectrum entries, FP32 and FP64) is built at grid
+                              creation.  The Carleman form keeps its own loss.  Other
+                              values: BOLTZ_EINVAL                                  */
 } boltz_options;
+
+enum { BOLTZ_LOSS_EXACT = 0, BOLTZ_LOSS_MASS_CONSISTENT = 1 };
 
 /*
  * Schedules of the batched FP32 form (same result up to FP32 rounding order):

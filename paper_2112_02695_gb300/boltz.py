@@ -45,6 +45,8 @@ KERNEL_CLASSES = ("spectrum", "prep", "shift", "contract", "radial", "output", "
 
 BOLTZ_SCHEDULE_AUTO = 0
 BOLTZ_SCHEDULE_NODE_BLOCKS = 1
+BOLTZ_LOSS_EXACT = 0
+BOLTZ_LOSS_MASS_CONSISTENT = 1
 
 
 class BoltzError(RuntimeError):
@@ -55,7 +57,7 @@ class BoltzError(RuntimeError):
 
 class _Options(ctypes.Structure):
     _fields_ = [("b", ctypes.c_double), ("workspace_max", ctypes.c_size_t), ("field_budget_mb", ctypes.c_int),
-                ("schedule", ctypes.c_int)]
+                ("schedule", ctypes.c_int), ("loss", ctypes.c_int)]
 
 
 class _Work(ctypes.Structure):
@@ -197,9 +199,9 @@ class Grid:
 
 def boltz_grid_init(N: int, d_v: int, L: float, R: float, gamma: float, N_rho: int, M: int,
                     b: float | None = None, workspace_max: int = 0, field_budget_mb: int = 0,
-                    schedule: int = BOLTZ_SCHEDULE_AUTO) -> Grid:
+                    schedule: int = BOLTZ_SCHEDULE_AUTO, loss: int = BOLTZ_LOSS_EXACT) -> Grid:
     h = ctypes.c_void_p()
-    opt = _Options(b if b is not None else 0.0, workspace_max, field_budget_mb, schedule)
+    opt = _Options(b if b is not None else 0.0, workspace_max, field_budget_mb, schedule, loss)
     _check(_lib.boltz_grid_init(ctypes.byref(h), N, d_v, L, R, gamma, N_rho, M, ctypes.byref(opt)),
            "boltz_grid_init")
     area = 2 * np.pi if d_v == 2 else 4 * np.pi

@@ -100,12 +100,14 @@ struct boltz_grid_s {
     float2* d_phase = nullptr;   // [(n_rho*M + 1)][D][N]
     float* d_ctab = nullptr;     // [n_rho][smax+1]
     float* d_gm = nullptr;       // [smax+1]
+    float* d_gmf = nullptr;      // [half] per-mode loss weight (mass-consistent loss), else null
     float* d_w = nullptr;        // [M/2] weight of each antipodal direction pair
     int2* d_dpair = nullptr;     // [M/2] (p, antipode(p)), p < antipode(p)
     // the same tables unrounded, for the FP64 check build (small grids only)
     double2* d_phase64 = nullptr;
     double* d_ctab64 = nullptr;
     double* d_gm64 = nullptr;
+    double* d_gmf64 = nullptr;
     double* d_w64 = nullptr;
     // split-precision form: per-node BF16 shift matrices (built on first use)
     uint8_t* d_smat = nullptr;
@@ -118,6 +120,7 @@ struct boltz_grid_s {
     int2* d_cm_dpair = nullptr;       // [M/2]
     int split_clusters = 1;           // resident clusters of the split kernel
     int schedule = BOLTZ_SCHEDULE_AUTO;
+    int loss = BOLTZ_LOSS_EXACT;
     PencilTree pen_tree;              // 3D N = 32 only
     int pen_ctas = 0;                 // resident CTAs of the pipelined kernel
     int* d_err = nullptr;        // device error word (bit kErrTimeout: a bounded wait gave up)
@@ -1145,10 +1148,11 @@ struct TablesT {
     const R* ctab;
     const R* gm;
     const R* w;
+    const R* gmf;            // per-mode loss weight (mass-consistent loss) or null
 };
-TablesT<float> tables_of(const boltz_grid_s* g, float) { return {g->d_phase, g->d_ctab, g->d_gm, g->d_w}; }
+TablesT<float> tables_of(const boltz_grid_s* g, float) { return {g->d_phase, g->d_ctab, g->d_gm, g->d_w, g->d_gmf}; }
 TablesT<double> tables_of(const boltz_grid_s* g, double) {
-    return {g->d_phase64, g->d_ctab64, g->d_gm64, g->d_w64};
+    return {g->d_phase64, g->d_ctab64, g->d_gm64, g->d_w64, g->d_gmf64};
 }
 
 // Asymmetric contraction of the Carleman form (FULL 8 x T strips and LIST 16).
@@ -1561,6 +1565,7 @@ boltz_status run_pencil(boltz_grid_s* g, const float2* spectra, float* Q_out, cu
     sp.inputs = d_inputs;
     sp.phase = g->d_phase;
     sp.gm = g->d_gm;
+    sp.gm_full = g->d_gmf;
     sp.n_c = nc;
     sp.M = g->M;
     sp.id_node = g->n_rho * g->M;
@@ -1662,6 +1667,7 @@ boltz_status run_batched(boltz_grid_s* g, const typename Prec<R>::C* spectra, in
         sp.inputs = d_inputs;
         sp.phase = tb.phase;
         sp.gm = tb.gm;
+        sp.gm_full = tb.gmf;
         sp.n_c = nc;
         sp.M = g->M;
         sp.id_node = g->n_rho * g->M;
@@ -2122,6 +2128,11 @@ boltz_status boltz_grid_init(boltz_grid* out, int N, int d_v, double L, double R
         return BOLTZ_EINVAL;
     }
     if (opt) g->schedule = opt->schedule;
+    if (opt && opt->loss != BOLTZ_LOSS_EXACT && opt->loss != BOLTZ_LOSS_MASS_CONSISTENT) {
+        delete g;
+        return BOLTZ_EINVAL;
+    }
+    if (opt) g->loss = opt->loss;
     g->n = d_v == 3 ? N * N * N : N * N;
     g->half = d_v == 3 ? N * N * (N / 2 + 1) : N * (N / 2 + 1);
     g->smax = d_v * (N / 2) * (N / 2);
@@ -2168,6 +2179,42 @@ boltz_status boltz_grid_init(boltz_grid* out, int N, int d_v, double L, double R
             acc += base * boltz::omega_average(d_v, kPi * g->rho[q] * km / L);
         }
         gm64[sq] = g->b * area * acc;
+    }
+    // mass-consistent loss: G-(l) = G_sep(l, -l) = b F_d(0) sum_q w_q rho_q^kp
+    // sum_p w_p cos(pi rho_q l.sigma_p / L) per half-spectrum mode, the direction
+    // sum formed as the real part of a product of per-axis phases
+    std::vector<double> gmf64;
+    if (g->loss == BOLTZ_LOSS_MASS_CONSISTENT) {
+        const int NHh = N / 2 + 1;
+        gmf64.assign(g->half, 0.0);
+        std::vector<double> er(size_t(d_v) * N), ei(size_t(d_v) * N);
+        for (int q = 0; q < N_rho; ++q) {
+            const double cq = g->b * area * g->w_rho[q] * std::pow(g->rho[q], kp);   // F_d(0) = |S^{d-1}|
+            for (int p = 0; p < M; ++p) {
+                const double wq = cq * g->dir.w[p];
+                for (int a = 0; a < d_v; ++a)
+                    for (int i = 0; i < N; ++i) {
+                        const int k = i < H ? i : i - N;
+                        const double ang = -kPi * g->rho[q] * k * g->dir.sigma[p * d_v + a] / L;
+                        er[size_t(a) * N + i] = std::cos(ang);
+                        ei[size_t(a) * N + i] = std::sin(ang);
+                    }
+                if (d_v == 3) {
+                    for (int i0 = 0; i0 < N; ++i0)
+                        for (int i1 = 0; i1 < N; ++i1) {
+                            const double zr = er[i0] * er[N + i1] - ei[i0] * ei[N + i1];
+                            const double zi = er[i0] * ei[N + i1] + ei[i0] * er[N + i1];
+                            double* row = &gmf64[(size_t(i0) * N + i1) * NHh];
+                            for (int i2 = 0; i2 < NHh; ++i2)
+                                row[i2] += wq * (zr * er[2 * N + (i2 % N)] - zi * ei[2 * N + (i2 % N)]);
+                        }
+                } else {
+                    for (int i0 = 0; i0 < N; ++i0)
+                        for (int i1 = 0; i1 < NHh; ++i1)
+                            gmf64[size_t(i0) * NHh + i1] += wq * (er[i0] * er[N + (i1 % N)] - ei[i0] * ei[N + (i1 % N)]);
+                }
+            }
+        }
     }
     std::vector<float2> phase(phase64.size());
     for (size_t i = 0; i < phase.size(); ++i) phase[i] = make_float2((float)phase64[i].x, (float)phase64[i].y);
@@ -2217,6 +2264,24 @@ boltz_status boltz_grid_init(boltz_grid* out, int N, int d_v, double L, double R
         cudaMemcpy(g->d_dpair, dpair.data(), n_dp * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(g->d_err, 0, sizeof(int)) != cudaSuccess)
         return fail(BOLTZ_ECUDA);
+    if (!gmf64.empty()) {
+        std::vector<float> gmf(gmf64.begin(), gmf64.end());
+        if (cudaMalloc(&g->d_gmf, gmf.size() * sizeof(float)) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return fail(BOLTZ_ENOMEM);
+        }
+        if (cudaMemcpy(g->d_gmf, gmf.data(), gmf.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+            return fail(BOLTZ_ECUDA);
+        if (fp64_shape(N, d_v)) {
+            if (cudaMalloc(&g->d_gmf64, gmf64.size() * sizeof(double)) != cudaSuccess) {
+                (void)cudaGetLastError();
+                return fail(BOLTZ_ENOMEM);
+            }
+            if (cudaMemcpy(g->d_gmf64, gmf64.data(), gmf64.size() * sizeof(double), cudaMemcpyHostToDevice) !=
+                cudaSuccess)
+                return fail(BOLTZ_ECUDA);
+        }
+    }
     if (fp64_shape(N, d_v)) {
         if (cudaMalloc(&g->d_phase64, phase64.size() * sizeof(double2)) != cudaSuccess ||
             cudaMalloc(&g->d_ctab64, ctab64.size() * sizeof(double)) != cudaSuccess ||
@@ -2290,6 +2355,8 @@ boltz_status boltz_grid_destroy(boltz_grid g) {
     cudaFree(g->d_phase);
     cudaFree(g->d_ctab);
     cudaFree(g->d_gm);
+    cudaFree(g->d_gmf);
+    cudaFree(g->d_gmf64);
     cudaFree(g->d_w);
     cudaFree(g->d_dpair);
     cudaFree(g->d_err);

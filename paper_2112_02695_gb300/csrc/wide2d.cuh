@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(kWTPF * kWFPC) k_synth_w128(SynParams P) {
             float2 v = cmul(__ldg(&src[k0 * kWNH + k1]), cmul(w1, __ldg(&ph[k0])));
             if (MODE == SYN_PREP && use_gm) {
                 const int a = wrapk(k0, kW);
-                v = cscale(v, __ldg(&P.gm[a * a + k1 * k1]));
+                v = cscale(v, P.gm_full ? __ldg(&P.gm_full[k0 * kWNH + k1]) : __ldg(&P.gm[a * a + k1 * k1]));
             }
             y[m] = v;
         }

@@ -19,12 +19,12 @@ def as_fp32(x):
     return np.asarray(x, dtype=np.float32).astype(np.float64)
 
 
-def gpu_collide(B, cfg, fields, pairs, form=0, return_T=False, schedule=0, launches=None):
+def gpu_collide(B, cfg, fields, pairs, form=0, return_T=False, schedule=0, launches=None, loss=0):
     """Q (and T) from the library.  `launches`, when a dict, receives the
     per-class launch counts of the call (to check which schedule ran)."""
     import torch
     N, d, L, R, gamma, n_rho, M = cfg
-    g = B.boltz_grid_init(N, d, L, R, gamma, n_rho, M, schedule=schedule)
+    g = B.boltz_grid_init(N, d, L, R, gamma, n_rho, M, schedule=schedule, loss=loss)
     try:
         f = torch.tensor(np.asarray(fields, dtype=np.float32), device="cuda")
         spec = B.boltz_spectrum(g, f)
@@ -42,10 +42,10 @@ def gpu_collide(B, cfg, fields, pairs, form=0, return_T=False, schedule=0, launc
         g.close()
 
 
-def oracle_collide(cfg, fields, pairs):
+def oracle_collide(cfg, fields, pairs, loss="exact"):
     from oracle import collision as C
     N, d, L, R, gamma, n_rho, M = cfg
-    prob = C.Problem(N=N, d=d, L=L, R=R, gamma=gamma, n_rho=n_rho, M=M)
+    prob = C.Problem(N=N, d=d, L=L, R=R, gamma=gamma, n_rho=n_rho, M=M, loss=loss)
     Q, Qp, Qm = C.collide_fields(prob, fields, pairs, return_parts=True)
     return prob, Q, C.scale(Q, Qp, Qm)
 
