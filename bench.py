@@ -705,6 +705,34 @@ def main():
                     "kernel_shares": {k: round(ms / tot_c, 4) for k, (_, ms) in prof_c.items() if ms > 0}}
         carleman["speedup_vs_separated_fp32"] = carleman["value"] / (value / world)
 
+    # mass of every Q of the batch with the default (exact) loss and with the
+    # mass-consistent loss option: |dv^d sum Q| / dv^d sum |Q|, worst pair, and the
+    # option's step time
+    mass = None
+    if kind == "pairs" and args.form == "batched":
+        def rel_mass(gg, QQ):
+            mom = B.boltz_moments(gg, QQ)[:, 0]
+            l1 = QQ.abs().reshape(QQ.shape[0], -1).sum(dim=1).double() * (2.0 * L / N) ** d
+            return float((mom.abs() / l1).max().item())
+        step()
+        torch.cuda.synchronize()
+        mass = {"exact_loss": rel_mass(g, Q)}
+        gmc = B.boltz_grid_init(N, d, L, R, gamma, n_rho, M, loss=B.BOLTZ_LOSS_MASS_CONSISTENT)
+        Qmc = torch.empty_like(Q)
+
+        def step_mc():
+            B.boltz_spectrum(gmc, f_dev, out=spec)
+            B.boltz_collide_batched(gmc, spec, pj, pl, out=Qmc)
+            B.boltz_project(gmc, f_dev, Qmc, out=T)
+        for _ in range(args.warmup):
+            step_mc()
+        tm = timed(step_mc, max(3, args.steps // 4))
+        B.boltz_sync_status(gmc)
+        mass["mass_consistent_loss"] = rel_mass(gmc, Qmc)
+        mass["mass_consistent_ms_per_step"] = sum(tm) / len(tm)
+        mass["normalisation"] = "max over the batch of |int Q dv| / int |Q| dv (FP64 moment sums)"
+        gmc.close()
+
     # low-rank step consumers of this batch (Sec. 2.4 K- and L-step collision terms,
     # FP64 QR of K and L, Sec. 3.2 SVD truncation and basis rotation), L2 flushed before each call
     lowrank = None
@@ -818,6 +846,7 @@ def main():
             "plain_fp32": plain,
             "split_bf16": split,
             "carleman_form": carleman,
+            "mass_conservation": mass,
             "lowrank_step_consumers": lowrank,
             "mott_smith": mott,
             "error_vs_oracle": errors,
