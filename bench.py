@@ -281,6 +281,41 @@ def lowrank_consumers(B, T, Q, r, n_v, flush, dev, n_x=1000, reps=20):
     return out
 
 
+def other_workloads():
+    """Short runs of the other workloads (each in its own process, 10 timed
+    steps), reported beside the headline so that their numbers come from the
+    same run: value, time per step and each one's own roofline or rate."""
+    out = {}
+    runs = [("c3", []), ("c4", []), ("c5", []), ("shock", []), ("shock_carleman", ["--form", "carleman"])]
+    for name, extra in runs:
+        cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--config", name.split("_")[0], "--steps", "10",
+               "--warmup", "3", "--no-cpu-baseline", "--no-plain", "--no-split", "--no-carleman", "--no-others"] + extra
+        try:
+            r = subprocess.run(cmd, capture_output=True, text=True, timeout=600)
+            lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+            if r.returncode != 0 or not lines:
+                out[name] = {"error": (r.stderr.strip().splitlines() or ["no output"])[-1][:200]}
+                continue
+            d = json.loads(lines[-1])
+        except (subprocess.TimeoutExpired, ValueError) as exc:
+            out[name] = {"error": str(exc)[:200]}
+            continue
+        keep = {k: d[k] for k in ("value", "unit", "ms_per_step", "steps") if k in d}
+        keep["workload"] = d.get("config", {}).get("workload")
+        if d.get("roofline"):
+            keep["roofline_frac"] = d["roofline"].get("frac")
+            keep["step_alu_frac"] = d["roofline"].get("step_alu_frac")
+            keep["kernel"] = d["roofline"].get("kernel")
+        for k in ("full_tensor", "speedup_lowrank_vs_full", "rank", "lowrank_vs_full", "mass_conservation"):
+            if k in d:
+                keep[k] = d[k]
+        if "graph_kernels" in d.get("config", {}):
+            keep["graph_kernels"] = d["config"]["graph_kernels"]
+        keep["clocks"] = d.get("clocks")
+        out[name] = keep
+    return out
+
+
 def host_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -459,6 +494,8 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-split", action="store_true")
     ap.add_argument("--no-carleman", action="store_true")
+    ap.add_argument("--no-others", action="store_true",
+                    help="skip the short runs of the other workloads (c3, c4, c5, shock) reported beside c2")
     ap.add_argument("--form", default="batched", choices=["batched", "split", "carleman"],
                     help="form of the headline measurement (the other arms run only with the default)")
     ap.add_argument("--field-budget-mb", type=int, default=0,
@@ -819,6 +856,10 @@ def main():
                 errors["carleman_vs_its_oracle"] = sample_errors(
                     B, g, dict(res, Q=Qo, scale=COL.scale(Qo, Qop, Qom)), {"carleman": B.BOLTZ_FORM_CARLEMAN})["carleman"]
 
+    others = None
+    if rank == 0 and world == 1 and not args.no_others and args.config == "c2" and args.form == "batched":
+        others = other_workloads()
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
@@ -851,6 +892,7 @@ def main():
             "mott_smith": mott,
             "error_vs_oracle": errors,
             "cpu_baseline": cpu,
+            "other_workloads": others,
             "wall_s_timed_region": wall,
         }
         print(json.dumps(line))

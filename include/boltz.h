@@ -133,8 +133,9 @@ typedef struct {
                               (the schedule boltz_autotune chooses between)        */
     int schedule;          /* schedule of the batched FP32 form:
                               BOLTZ_SCHEDULE_AUTO (0): the pipelined schedule where
-                              it is built (d_v = 3, N = 32, at most 16 distinct
-                              inputs), the node-block schedule elsewhere;
+                              it is built (d_v = 3, N = 32, and no group of inputs
+                              joined by pairs larger than 16), the node-block
+                              schedule elsewhere;
                               BOLTZ_SCHEDULE_NODE_BLOCKS (1): always the node-block
                               schedule (the comparison baseline)                   */
     int loss;              /* loss weight G-(l) of the separated forms (batched,
@@ -166,7 +167,10 @@ enum { BOLTZ_LOSS_EXACT = 0, BOLTZ_LOSS_MASS_CONSISTENT = 1 };
  *                directions) and kept in L2-sized node buffers, and the last
  *                inverse pass of every direction is fused with the
  *                sigma-contraction and the first forward pass, so the shifted
- *                fields never leave the chip.
+ *                fields never leave the chip.  The inputs are split into
+ *                chunks of at most 16 (each pair's two inputs in one chunk,
+ *                e.g. the cells of a full tensor grid Q(f_x, f_x) in chunks of
+ *                16 cells), one launch per chunk.
  */
 #define BOLTZ_SCHEDULE_AUTO 0
 #define BOLTZ_SCHEDULE_NODE_BLOCKS 1

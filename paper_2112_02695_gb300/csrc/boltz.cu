@@ -7,10 +7,12 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <mutex>
 #include <new>
@@ -72,6 +74,9 @@ struct Plan {
     size_t off_pen_blob = 0, off_X = 0, off_Pt = 0, off_ctr = 0, off_qstd = 0;
     size_t pen_off[9] = {};               // offsets inside the blob: grp, s0_dir, s0_child,
                                           // s01_dir, step_blk, step_dir, step_sel, step_w, slots
+                                          // (the slot list of chunk 0; chunk k's at pen_slot_off[k])
+    std::vector<size_t> pen_slot_off;     // per chunk: its used-slot list inside the blob
+    std::vector<std::array<unsigned, 5>> pen_mask;   // per chunk: used TRI16 slots as a bit set
 };
 
 // Direction structure of a 3D rule for the pipelined schedule: the distinct
@@ -319,20 +324,59 @@ PencilTree build_pencil_tree(const boltz_grid_s* g) {
     return T;
 }
 
+// Chunks of the pipelined schedule: the inputs of every connected component
+// of the pair graph (inputs joined by a pair) stay together, and components
+// are packed largest first into chunks of at most 16 inputs (first fit), each
+// chunk's inputs in ascending order.  False when a component has more than
+// 16 inputs.
+bool pencil_chunks(const int32_t* pj, const int32_t* pl, int n_pairs, std::vector<std::vector<int>>& chunks) {
+    namespace pc = boltz_dev::pencil;
+    std::map<int, int> parent;
+    std::function<int(int)> find = [&](int a) {
+        while (parent[a] != a) a = parent[a] = parent[parent[a]];
+        return a;
+    };
+    for (int e = 0; e < n_pairs; ++e) {
+        for (int v : {pj[e], pl[e]})
+            if (!parent.count(v)) parent[v] = v;
+        const int a = find(pj[e]), b = find(pl[e]);
+        if (a != b) parent[std::max(a, b)] = std::min(a, b);
+    }
+    std::map<int, std::vector<int>> comp;
+    for (auto& kv : parent) comp[find(kv.first)].push_back(kv.first);
+    std::vector<std::vector<int>> cs;
+    for (auto& kv : comp) {
+        if ((int)kv.second.size() > pc::NJ) return false;
+        cs.push_back(kv.second);
+    }
+    std::stable_sort(cs.begin(), cs.end(), [](const std::vector<int>& a, const std::vector<int>& b) {
+        return a.size() > b.size();
+    });
+    chunks.clear();
+    for (const auto& c : cs) {
+        size_t k = 0;
+        while (k < chunks.size() && chunks[k].size() + c.size() > (size_t)pc::NJ) ++k;
+        if (k == chunks.size()) chunks.emplace_back();
+        chunks[k].insert(chunks[k].end(), c.begin(), c.end());
+    }
+    for (auto& c : chunks) std::sort(c.begin(), c.end());
+    return !chunks.empty();
+}
+
 // Whether a batch runs on the pipelined schedule: batched FP32 form on a 3D
-// 32^3 grid whose tree was built, at most 16 distinct inputs.
+// 32^3 grid whose tree was built, every connected group of inputs at most 16.
 bool pencil_applies(const boltz_grid_s* g, const int32_t* pj, const int32_t* pl, int n_pairs, int form,
                     size_t elem) {
     if (form != BOLTZ_FORM_BATCHED || elem != 4 || g->D != 3 || g->N != 32 || !g->pen_tree.ok ||
         g->schedule != BOLTZ_SCHEDULE_AUTO || g->pen_ctas <= 0)
         return false;
-    std::set<int> ins(pj, pj + n_pairs);
-    ins.insert(pl, pl + n_pairs);
-    return (int)ins.size() <= boltz_dev::pencil::NJ;
+    std::vector<std::vector<int>> chunks;
+    return pencil_chunks(pj, pl, n_pairs, chunks);
 }
 
-// Plan of the pipelined schedule: the distinct inputs as one chunk, gain
-// slot u = TRI16 index of the chunk-local pair, outputs listed per used slot
+// Plan of the pipelined schedule: the inputs in chunks of at most 16 (one
+// persistent launch each, in order, sharing the node buffers), gain slot
+// u = TRI16 index of the chunk-local pair, outputs listed per used slot
 // (Qhat+ and the output kernel run over the used slots only).  Workspace:
 // descriptors | f_N, Lambda | X node buffers | Pt node buffers | Qhat+ | counters.
 boltz_status build_plan_pencil(const boltz_grid_s* g, const int32_t* pj, const int32_t* pl, int n_pairs,
@@ -340,60 +384,77 @@ boltz_status build_plan_pencil(const boltz_grid_s* g, const int32_t* pj, const i
     namespace pc = boltz_dev::pencil;
     plan = Plan();
     plan.pencil = true;
-    ChunkPlan c;
-    std::set<int> ins(pj, pj + n_pairs);
-    ins.insert(pl, pl + n_pairs);
-    c.inputs.assign(ins.begin(), ins.end());
-    std::map<int, int> loc;
-    for (int i = 0; i < (int)c.inputs.size(); ++i) loc[c.inputs[i]] = i;
-    std::vector<std::vector<int>> outs_of(pc::NSLOT);
+    std::vector<std::vector<int>> groups;
+    if (!pencil_chunks(pj, pl, n_pairs, groups)) return BOLTZ_EINVAL;
+    std::map<int, int> chunk_of, loc;
+    for (int k = 0; k < (int)groups.size(); ++k)
+        for (int i = 0; i < (int)groups[k].size(); ++i) {
+            chunk_of[groups[k][i]] = k;
+            loc[groups[k][i]] = i;
+        }
+    std::vector<std::vector<std::vector<int>>> outs_of(groups.size(), std::vector<std::vector<int>>(pc::NSLOT));
     for (int e = 0; e < n_pairs; ++e) {
         const int a = loc[pj[e]], b = loc[pl[e]];
-        outs_of[pc::tri_slot(std::min(a, b), std::max(a, b))].push_back(e);
+        outs_of[chunk_of[pj[e]]][pc::tri_slot(std::min(a, b), std::max(a, b))].push_back(e);
     }
-    for (int u = 0; u < pc::NSLOT; ++u) {
-        if (outs_of[u].empty()) continue;
-        plan.pen_slots.push_back(u);
-        c.out_start.push_back((int)c.outs.size());
-        for (int e : outs_of[u]) c.outs.push_back(make_int4(e, loc[pj[e]], loc[pl[e]], 0));
-    }
-    c.out_start.push_back((int)c.outs.size());
-    c.U = (int)plan.pen_slots.size();
-    plan.pen_n_used = c.U;
-    const int nc = (int)c.inputs.size();
-    plan.max_nc = nc;
-    plan.max_U = c.U;
-    plan.nq = g->n_rho;
-    // direction tree and slot list as one blob (16-byte aligned tables)
+    // direction tree, then each chunk's slot list, as one blob (16-byte aligned tables)
     const PencilTree& T = g->pen_tree;
     std::vector<char>& blob = plan.pen_blob;
-    auto put = [&](int which, const void* src, size_t bytes) {
-        plan.pen_off[which] = align_up(blob.size(), 16);
-        blob.resize(plan.pen_off[which] + bytes);
-        if (bytes) std::memcpy(blob.data() + plan.pen_off[which], src, bytes);
+    auto put = [&](const void* src, size_t bytes) {
+        const size_t at = align_up(blob.size(), 16);
+        blob.resize(at + bytes);
+        if (bytes) std::memcpy(blob.data() + at, src, bytes);
+        return at;
     };
-    put(0, T.grp.data(), T.grp.size() * sizeof(int));
-    put(1, T.s0_dir.data(), T.s0_dir.size() * sizeof(int));
-    put(2, T.s0_child.data(), T.s0_child.size() * sizeof(int));
-    put(3, T.s01_dir.data(), T.s01_dir.size() * sizeof(int));
-    put(4, T.step_blk.data(), T.step_blk.size() * sizeof(int4));
-    put(5, T.step_dir.data(), T.step_dir.size() * sizeof(int4));
-    put(6, T.step_sel.data(), T.step_sel.size() * sizeof(int4));
-    put(7, T.step_w.data(), T.step_w.size() * sizeof(float2));
-    put(8, plan.pen_slots.data(), plan.pen_slots.size() * sizeof(int));
+    plan.pen_off[0] = put(T.grp.data(), T.grp.size() * sizeof(int));
+    plan.pen_off[1] = put(T.s0_dir.data(), T.s0_dir.size() * sizeof(int));
+    plan.pen_off[2] = put(T.s0_child.data(), T.s0_child.size() * sizeof(int));
+    plan.pen_off[3] = put(T.s01_dir.data(), T.s01_dir.size() * sizeof(int));
+    plan.pen_off[4] = put(T.step_blk.data(), T.step_blk.size() * sizeof(int4));
+    plan.pen_off[5] = put(T.step_dir.data(), T.step_dir.size() * sizeof(int4));
+    plan.pen_off[6] = put(T.step_sel.data(), T.step_sel.size() * sizeof(int4));
+    plan.pen_off[7] = put(T.step_w.data(), T.step_w.size() * sizeof(float2));
+    for (int k = 0; k < (int)groups.size(); ++k) {
+        ChunkPlan c;
+        c.inputs = groups[k];
+        std::vector<int> slots;
+        std::array<unsigned, 5> mask{};
+        for (int u = 0; u < pc::NSLOT; ++u) {
+            if (outs_of[k][u].empty()) continue;
+            slots.push_back(u);
+            mask[u >> 5] |= 1u << (u & 31);
+            c.out_start.push_back((int)c.outs.size());
+            for (int e : outs_of[k][u]) c.outs.push_back(make_int4(e, loc[pj[e]], loc[pl[e]], 0));
+        }
+        c.out_start.push_back((int)c.outs.size());
+        c.U = (int)slots.size();
+        plan.pen_slot_off.push_back(put(slots.data(), slots.size() * sizeof(int)));
+        plan.pen_mask.push_back(mask);
+        if (k == 0) {
+            plan.pen_slots = slots;
+            plan.pen_off[8] = plan.pen_slot_off[0];
+        }
+        plan.max_nc = std::max(plan.max_nc, (int)c.inputs.size());
+        plan.max_U = std::max(plan.max_U, c.U);
+        plan.chunks.push_back(std::move(c));
+    }
     blob.resize(align_up(blob.size(), 16));
+    plan.pen_n_used = plan.max_U;
+    plan.nq = g->n_rho;
     size_t off = 0;
-    c.off_inputs = off;
-    off = align_up(off + c.inputs.size() * sizeof(int), 256);
-    for (int k = 0; k < 3; ++k) c.off_tiles[k] = off;
-    c.off_start = off;
-    off = align_up(off + c.out_start.size() * sizeof(int), 256);
-    c.off_outs = off;
-    off = align_up(off + c.outs.size() * sizeof(int4), 256);
+    for (auto& c : plan.chunks) {
+        c.off_inputs = off;
+        off = align_up(off + c.inputs.size() * sizeof(int), 256);
+        for (int k = 0; k < 3; ++k) c.off_tiles[k] = off;
+        c.off_start = off;
+        off = align_up(off + c.out_start.size() * sizeof(int), 256);
+        c.off_outs = off;
+        off = align_up(off + c.outs.size() * sizeof(int4), 256);
+    }
     plan.off_pen_blob = off;
     off = align_up(off + blob.size(), 256);
     plan.plan_bytes = off;
-    plan.chunks.push_back(std::move(c));
+    const int nc = plan.max_nc;
     const size_t field_bytes = size_t(g->n) * 4;
     size_t w = align_up(off, 256);
     plan.off_plan = 0;
@@ -406,11 +467,11 @@ boltz_status build_plan_pencil(const boltz_grid_s* g, const int32_t* pj, const i
     plan.off_Pt = w;
     w = align_up(w + size_t(pc::NPB) * pc::NSLOT * pc::NKB * pc::PLANE * sizeof(float2), 256);
     plan.off_qhat = w;                     // packed running sums, then the final sums (standard layout)
-    w = align_up(w + size_t(plan.pen_n_used) * pc::NKB * pc::QBLK * sizeof(float2), 256);
+    w = align_up(w + size_t(plan.max_U) * pc::NKB * pc::QBLK * sizeof(float2), 256);
     plan.off_qstd = w;
-    w = align_up(w + size_t(plan.pen_n_used) * pc::HALF * sizeof(float2), 256);
+    w = align_up(w + size_t(plan.max_U) * pc::HALF * sizeof(float2), 256);
     plan.off_ctr = w;
-    w = align_up(w + size_t(pc::ctr_count(g->n_rho, plan.pen_n_used)) * sizeof(int), 256);
+    w = align_up(w + size_t(pc::ctr_count(g->n_rho, plan.max_U)) * sizeof(int), 256);
     plan.off_A = plan.off_P = plan.off_img = w;
     plan.total = w;
     return BOLTZ_OK;
@@ -1548,84 +1609,86 @@ boltz_status run_carleman(boltz_grid_s* g, const float2* spectra, int n_inputs, 
     return BOLTZ_OK;
 }
 
-// One batched evaluation on the pipelined schedule (plan.pencil): f_N and
-// Lambda of the inputs, the persistent kernel of pencil.cuh (shifted fields,
-// sigma-contraction and radial step of every node), then the output kernel
-// over the used gain slots.
+// One batched evaluation on the pipelined schedule (plan.pencil), chunk by
+// chunk: f_N and Lambda of the chunk's inputs, the persistent kernel of
+// pencil.cuh (shifted fields, sigma-contraction and radial step of every
+// node), then the output kernel over the chunk's used gain slots.
 boltz_status run_pencil(boltz_grid_s* g, const float2* spectra, float* Q_out, cudaStream_t st) {
     namespace pc = boltz_dev::pencil;
     const Plan& plan = g->last_plan;
-    const ChunkPlan& c = plan.chunks[0];
-    const int nc = (int)c.inputs.size();
     const Dispatch* dp = dispatch_for(g->N, g->D);
     char* ws = g->d_ws;
-    const int* d_inputs = reinterpret_cast<const int*>(ws + plan.off_plan + c.off_inputs);
-    float* fN = reinterpret_cast<float*>(ws + plan.off_fN);
-    SynParams sp{};
-    sp.spectra = spectra;
-    sp.inputs = d_inputs;
-    sp.phase = g->d_phase;
-    sp.gm = g->d_gm;
-    sp.gm_full = g->d_gmf;
-    sp.n_c = nc;
-    sp.M = g->M;
-    sp.id_node = g->n_rho * g->M;
-    sp.out = fN;                                     // f < nc: f_N, f >= nc: Lambda
-    sp.n_fields = 2 * nc;
-    {
-        ProfScope ps(g, BOLTZ_KCLASS_PREP, st);
-        dp->synth(sp, SYN_PREP, st);
-    }
     const char* blob = ws + plan.off_plan + plan.off_pen_blob;
     const PencilTree& T = g->pen_tree;
-    pc::Params P{};
-    P.spectra = spectra;
-    P.inputs = d_inputs;
-    P.phase = g->d_phase;
-    P.ctab = g->d_ctab;
-    P.X = reinterpret_cast<float2*>(ws + plan.off_X);
-    P.Pt = reinterpret_cast<float2*>(ws + plan.off_Pt);
-    P.qhat = reinterpret_cast<float2*>(ws + plan.off_qhat);
-    P.qstd = reinterpret_cast<float2*>(ws + plan.off_qstd);
-    P.slots = reinterpret_cast<const int*>(blob + plan.pen_off[8]);
-    P.ctr = reinterpret_cast<int*>(ws + plan.off_ctr);
-    P.err = g->d_err;
-    P.tr.n_s0 = T.n_s0;
-    P.tr.n_s01 = T.n_s01;
-    P.tr.n_grp = T.n_grp;
-    P.tr.n_step = (int)T.step_dir.size();
-    P.tr.grp = reinterpret_cast<const int*>(blob + plan.pen_off[0]);
-    P.tr.s0_dir = reinterpret_cast<const int*>(blob + plan.pen_off[1]);
-    P.tr.s0_child = reinterpret_cast<const int*>(blob + plan.pen_off[2]);
-    P.tr.s01_dir = reinterpret_cast<const int*>(blob + plan.pen_off[3]);
-    P.tr.step_blk = reinterpret_cast<const int4*>(blob + plan.pen_off[4]);
-    P.tr.step_dir = reinterpret_cast<const int4*>(blob + plan.pen_off[5]);
-    P.tr.step_sel = reinterpret_cast<const int4*>(blob + plan.pen_off[6]);
-    P.tr.step_w = reinterpret_cast<const float2*>(blob + plan.pen_off[7]);
-    P.n_c = nc;
-    P.M = g->M;
-    P.n_rho = g->n_rho;
-    P.n_used = plan.pen_n_used;
-    BZ_CUDA(cudaMemsetAsync(P.ctr, 0, size_t(pc::ctr_count(g->n_rho, plan.pen_n_used)) * sizeof(int), st));
-    const long long items =
-        (long long)g->n_rho * (pc::NLB + pc::tree_items(nc, T.n_grp) + (long long)plan.pen_n_used);
-    const int grid = (int)std::min<long long>(g->pen_ctas, items);
-    {
-        ProfScope ps(g, BOLTZ_KCLASS_PIPELINE, st);
-        pc::k_pencil<<<grid, pc::NT, pc::SM_TOTAL, st>>>(P);
-    }
-    OutParams op{};
-    op.qhat = P.qstd;
-    op.fN = fN;
-    op.lam = fN + size_t(nc) * g->n;
-    op.out_start = reinterpret_cast<const int*>(ws + plan.off_plan + c.off_start);
-    op.outs = reinterpret_cast<const int4*>(ws + plan.off_plan + c.off_outs);
-    op.Q = Q_out;
-    op.err = g->d_err;
-    op.U = plan.pen_n_used;
-    {
-        ProfScope ps(g, BOLTZ_KCLASS_OUTPUT, st);
-        dp->output(op, st);
+    float* fN = reinterpret_cast<float*>(ws + plan.off_fN);
+    for (size_t k = 0; k < plan.chunks.size(); ++k) {
+        const ChunkPlan& c = plan.chunks[k];
+        const int nc = (int)c.inputs.size();
+        const int* d_inputs = reinterpret_cast<const int*>(ws + plan.off_plan + c.off_inputs);
+        SynParams sp{};
+        sp.spectra = spectra;
+        sp.inputs = d_inputs;
+        sp.phase = g->d_phase;
+        sp.gm = g->d_gm;
+        sp.gm_full = g->d_gmf;
+        sp.n_c = nc;
+        sp.M = g->M;
+        sp.id_node = g->n_rho * g->M;
+        sp.out = fN;                                 // f < nc: f_N, f >= nc: Lambda
+        sp.n_fields = 2 * nc;
+        {
+            ProfScope ps(g, BOLTZ_KCLASS_PREP, st);
+            dp->synth(sp, SYN_PREP, st);
+        }
+        pc::Params P{};
+        P.spectra = spectra;
+        P.inputs = d_inputs;
+        P.phase = g->d_phase;
+        P.ctab = g->d_ctab;
+        P.X = reinterpret_cast<float2*>(ws + plan.off_X);
+        P.Pt = reinterpret_cast<float2*>(ws + plan.off_Pt);
+        P.qhat = reinterpret_cast<float2*>(ws + plan.off_qhat);
+        P.qstd = reinterpret_cast<float2*>(ws + plan.off_qstd);
+        P.slots = reinterpret_cast<const int*>(blob + plan.pen_slot_off[k]);
+        for (int w = 0; w < 5; ++w) P.used[w] = plan.pen_mask[k][w];
+        P.ctr = reinterpret_cast<int*>(ws + plan.off_ctr);
+        P.err = g->d_err;
+        P.tr.n_s0 = T.n_s0;
+        P.tr.n_s01 = T.n_s01;
+        P.tr.n_grp = T.n_grp;
+        P.tr.n_step = (int)T.step_dir.size();
+        P.tr.grp = reinterpret_cast<const int*>(blob + plan.pen_off[0]);
+        P.tr.s0_dir = reinterpret_cast<const int*>(blob + plan.pen_off[1]);
+        P.tr.s0_child = reinterpret_cast<const int*>(blob + plan.pen_off[2]);
+        P.tr.s01_dir = reinterpret_cast<const int*>(blob + plan.pen_off[3]);
+        P.tr.step_blk = reinterpret_cast<const int4*>(blob + plan.pen_off[4]);
+        P.tr.step_dir = reinterpret_cast<const int4*>(blob + plan.pen_off[5]);
+        P.tr.step_sel = reinterpret_cast<const int4*>(blob + plan.pen_off[6]);
+        P.tr.step_w = reinterpret_cast<const float2*>(blob + plan.pen_off[7]);
+        P.n_c = nc;
+        P.M = g->M;
+        P.n_rho = g->n_rho;
+        P.n_used = c.U;
+        BZ_CUDA(cudaMemsetAsync(P.ctr, 0, size_t(pc::ctr_count(g->n_rho, c.U)) * sizeof(int), st));
+        const long long items = (long long)g->n_rho * (pc::NLB + pc::tree_items(nc, T.n_grp) + (long long)c.U);
+        const int grid = (int)std::min<long long>(g->pen_ctas, items);
+        {
+            ProfScope ps(g, BOLTZ_KCLASS_PIPELINE, st);
+            pc::k_pencil<<<grid, pc::NT, pc::SM_TOTAL, st>>>(P);
+        }
+        OutParams op{};
+        op.qhat = P.qstd;
+        op.fN = fN;
+        op.lam = fN + size_t(nc) * g->n;
+        op.out_start = reinterpret_cast<const int*>(ws + plan.off_plan + c.off_start);
+        op.outs = reinterpret_cast<const int4*>(ws + plan.off_plan + c.off_outs);
+        op.Q = Q_out;
+        op.err = g->d_err;
+        op.U = c.U;
+        {
+            ProfScope ps(g, BOLTZ_KCLASS_OUTPUT, st);
+            dp->output(op, st);
+        }
     }
     BZ_CUDA(cudaGetLastError());
     return BOLTZ_OK;

@@ -151,6 +151,7 @@ struct Params {
     float2* qstd;            // [n_used][HALF]: the final Qhat+ in the standard half-spectrum
                              // layout, written by the last node's radial items
     const int* slots;        // [n_used]: slots whose gain is needed
+    unsigned used[5];        // the same slots as a bit set (slot u: bit u % 32 of word u / 32)
     int* ctr;                // counters, zeroed before the launch (layout in ctr_*)
     int* err;                // device error word
     Tree tr;
@@ -593,6 +594,7 @@ __device__ bool fused_item(const Params& P, const TreeSmem& ts, int q, int lb, u
         __syncthreads();
         for (int task = t; task < 2 * nsl; task += NT) {
             const int lp2 = task / nsl, us = task % nsl, u = kColSlots.u[u0 + us];
+            if (!((P.used[u >> 5] >> (u & 31)) & 1u)) continue;      // no radial item reads this slot
             const float* r1 = Pst + us * PSS + lp2 * 2 * N;           // rows i1 = 2m + lp2 and i1 + 16
             float2 x[N];
             load_two_rows_smem<N>(r1, r1 + N, x);

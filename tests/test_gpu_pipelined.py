@@ -95,3 +95,30 @@ def test_pipelined_is_bitwise_reproducible(B):
         assert torch.equal(Q1, Q2)
     finally:
         g.close()
+
+
+def test_pipelined_several_chunks_against_oracle(B):
+    """40 inputs whose pairs connect groups of at most 16 (diagonal cells, a few
+    pairs within groups): the pipelined schedule runs one persistent launch per
+    chunk of at most 16 inputs, each chunk's gain slots only."""
+    cfg = (32, 3, 8.0, 8.0, 1.0, 2, 14)
+    f = as_fp32(W.random_fields(32, 3, 8.0, 40, seed=801))
+    pairs = [(x, x) for x in range(40)] + [(0, 1), (1, 0), (5, 7), (30, 31), (39, 38), (12, 12)]
+    launches = {}
+    Qg = gpu_collide(B, cfg, f, pairs, launches=launches)
+    assert launches["pipeline"] == 3 and launches["shift"] == 0        # 40 inputs: chunks of 16, 16, 8
+    _, Qo, s = oracle_collide(cfg, f, pairs)
+    assert rel_err(Qg, Qo, s).max() < TOL
+
+
+def test_pipelined_falls_back_for_a_group_of_seventeen(B):
+    """A chain of pairs joining 17 inputs cannot be split into chunks of 16:
+    the node-block schedule runs it, with the same result."""
+    cfg = (32, 3, 8.0, 8.0, 1.0, 1, 6)
+    f = as_fp32(W.random_fields(32, 3, 8.0, 17, seed=802))
+    pairs = [(x, x + 1) for x in range(16)]
+    launches = {}
+    Qg = gpu_collide(B, cfg, f, pairs, launches=launches)
+    assert launches["pipeline"] == 0 and launches["shift"] > 0
+    _, Qo, s = oracle_collide(cfg, f, pairs)
+    assert rel_err(Qg, Qo, s).max() < TOL
