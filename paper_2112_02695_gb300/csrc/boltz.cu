@@ -77,6 +77,7 @@ struct Plan {
                                           // (the slot list of chunk 0; chunk k's at pen_slot_off[k])
     std::vector<size_t> pen_slot_off;     // per chunk: its used-slot list inside the blob
     std::vector<std::array<unsigned, 5>> pen_mask;   // per chunk: used TRI16 slots as a bit set
+    std::vector<char> pen_diag;           // per chunk: every used slot is a diagonal (j, j)
 };
 
 // Direction structure of a 3D rule for the pipelined schedule: the distinct
@@ -128,6 +129,7 @@ struct boltz_grid_s {
     int loss = BOLTZ_LOSS_EXACT;
     PencilTree pen_tree;              // 3D N = 32 only
     int pen_ctas = 0;                 // resident CTAs of the pipelined kernel
+    int pen_ctas_diag = 0;            // the same for its diagonal-slot variant
     int* d_err = nullptr;        // device error word (bit kErrTimeout: a bounded wait gave up)
     // workspace
     char* d_ws = nullptr;
@@ -428,6 +430,13 @@ boltz_status build_plan_pencil(const boltz_grid_s* g, const int32_t* pj, const i
         }
         c.out_start.push_back((int)c.outs.size());
         c.U = (int)slots.size();
+        bool diag = true;
+        for (int u : slots) {
+            bool on_diagonal = false;
+            for (int a = 0; a < pc::NJ; ++a) on_diagonal = on_diagonal || u == pc::tri_slot(a, a);
+            diag = diag && on_diagonal;
+        }
+        plan.pen_diag.push_back(diag);
         plan.pen_slot_off.push_back(put(slots.data(), slots.size() * sizeof(int)));
         plan.pen_mask.push_back(mask);
         if (k == 0) {
@@ -1671,10 +1680,12 @@ boltz_status run_pencil(boltz_grid_s* g, const float2* spectra, float* Q_out, cu
         P.n_used = c.U;
         BZ_CUDA(cudaMemsetAsync(P.ctr, 0, size_t(pc::ctr_count(g->n_rho, c.U)) * sizeof(int), st));
         const long long items = (long long)g->n_rho * (pc::NLB + pc::tree_items(nc, T.n_grp) + (long long)c.U);
-        const int grid = (int)std::min<long long>(g->pen_ctas, items);
+        const bool diag = plan.pen_diag[k];
+        const int grid = (int)std::min<long long>(diag ? g->pen_ctas_diag : g->pen_ctas, items);
         {
             ProfScope ps(g, BOLTZ_KCLASS_PIPELINE, st);
-            pc::k_pencil<<<grid, pc::NT, pc::SM_TOTAL, st>>>(P);
+            if (diag) pc::k_pencil<true><<<grid, pc::NT, pc::SM_TOTAL, st>>>(P);
+            else pc::k_pencil<false><<<grid, pc::NT, pc::SM_TOTAL, st>>>(P);
         }
         OutParams op{};
         op.qhat = P.qstd;
@@ -2374,20 +2385,26 @@ boltz_status boltz_grid_init(boltz_grid* out, int N, int d_v, double L, double R
         // shared memory and tensor-memory columns.  (The runtime's occupancy
         // query reports one CTA per SM for any kernel that allocates tensor
         // memory; three of these CTAs hold 384 of the SM's 512 columns.)
-        cudaFuncAttributes fa;
         int regs_sm = 0, smem_sm = 0, resv = 0;
-        if (set_smem(pc::k_pencil, pc::SM_TOTAL) != cudaSuccess ||
-
-            cudaFuncGetAttributes(&fa, pc::k_pencil) != cudaSuccess ||
-            cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, g->device) != cudaSuccess ||
+        if (cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, g->device) != cudaSuccess ||
             cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, g->device) != cudaSuccess ||
             cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, g->device) != cudaSuccess)
             return fail(BOLTZ_ECUDA);
-        const int regs_cta = ((fa.numRegs + 7) / 8 * 8) * pc::NT;
-        const int smem_cta = (int)fa.sharedSizeBytes + pc::SM_TOTAL + resv;
-        int per_sm = std::min(regs_sm / std::max(regs_cta, 1), smem_sm / std::max(smem_cta, 1));
-        per_sm = std::min(per_sm, std::min(pc::CTAS_PER_SM, 512 / (int)pc::TMEM_COLS));
-        g->pen_ctas = std::max(per_sm, 0) * g->sms;
+        auto resident = [&](auto kernel, bool uses_tmem, int& ctas) {
+            cudaFuncAttributes fa;
+            if (set_smem(kernel, pc::SM_TOTAL) != cudaSuccess || cudaFuncGetAttributes(&fa, kernel) != cudaSuccess)
+                return false;
+            const int regs_cta = ((fa.numRegs + 7) / 8 * 8) * pc::NT;
+            const int smem_cta = (int)fa.sharedSizeBytes + pc::SM_TOTAL + resv;
+            int per_sm = std::min(regs_sm / std::max(regs_cta, 1), smem_sm / std::max(smem_cta, 1));
+            per_sm = std::min(per_sm, pc::CTAS_PER_SM);
+            if (uses_tmem) per_sm = std::min(per_sm, 512 / (int)pc::TMEM_COLS);
+            ctas = std::max(per_sm, 0) * g->sms;
+            return true;
+        };
+        if (!resident(pc::k_pencil<false>, true, g->pen_ctas) ||
+            !resident(pc::k_pencil<true>, false, g->pen_ctas_diag))
+            return fail(BOLTZ_ECUDA);
     }
     if (cudaStreamCreateWithFlags(&g->side, cudaStreamNonBlocking) != cudaSuccess) return fail(BOLTZ_ECUDA);
     for (int b = 0; b < 2; ++b)

@@ -436,6 +436,10 @@ __device__ __forceinline__ void contract_chunk(uint32_t (&r)[32], const float (&
 }
 
 // Returns false when a bulk copy did not land in time (the caller aborts).
+// DIAG: every used gain slot is a diagonal (j, j) (the cells of a full tensor
+// grid, Q(f_x, f_x)): the 16 diagonal accumulators stay in registers, tensor
+// memory is not used, and the epilogue transforms those 16 slots only.
+template <bool DIAG>
 __device__ bool fused_item(const Params& P, const TreeSmem& ts, int q, int lb, unsigned char* smem, uint64_t* bars,
                            uint32_t& par, uint32_t tmem) {
     const int t = threadIdx.x, warp = t >> 5;
@@ -450,7 +454,7 @@ __device__ bool fused_item(const Params& P, const TreeSmem& ts, int q, int lb, u
         fused_issue(P, ts, Xn, q, 0, warp, stage_x(0), stage_ph(0), &bars[0]);
         if (nst > 1) fused_issue(P, ts, Xn, q, 1, warp, stage_x(1), stage_ph(1), &bars[1]);
     }
-    {
+    if constexpr (!DIAG) {
         uint32_t z[32];
 #pragma unroll
         for (int k = 0; k < 32; ++k) z[k] = 0u;
@@ -458,9 +462,10 @@ __device__ bool fused_item(const Params& P, const TreeSmem& ts, int q, int lb, u
         for (int ch = 0; ch < NTSLOT / 32; ++ch) tmem_st32(tl + 32 * ch, z);
         tmem_wait_st();
     }
-    float racc[NRSLOT];
+    constexpr int NREG = DIAG ? NJ : NRSLOT;
+    float racc[NREG];                          // DIAG: slot (x, x) in racc[x]; else the odd diagonals
 #pragma unroll
-    for (int k = 0; k < NRSLOT; ++k) racc[k] = 0.f;
+    for (int k = 0; k < NREG; ++k) racc[k] = 0.f;
     const int d = warp, lp = (t >> 4) & 1, j = t & 15;
 #pragma unroll 1
     for (int st = 0; st < nst; ++st) {
@@ -531,6 +536,11 @@ __device__ bool fused_item(const Params& P, const TreeSmem& ts, int q, int lb, u
                 a[xx] = w * Aa[xx * AJS];
                 cc[xx] = Ac[xx * AJS];
             }
+            if constexpr (DIAG) {
+#pragma unroll
+                for (int xx = 0; xx < NJ; ++xx) racc[xx] = fmaf(a[xx], cc[xx], fmaf(cc[xx], a[xx], racc[xx]));
+                continue;
+            }
             uint64_t a2[NJ / 2], c2[NJ / 2];
 #pragma unroll
             for (int h = 0; h < NJ / 2; ++h) {
@@ -574,10 +584,13 @@ __device__ bool fused_item(const Params& P, const TreeSmem& ts, int q, int lb, u
     float2* Ptn = P.Pt + (size_t)(q % NPB) * NSLOT * NKB * PLANE;
     const int i0 = lb >> 3, m = lb & 7;
 #pragma unroll 1
-    for (int rnd = 0; rnd < 3; ++rnd) {
+    for (int rnd = 0; rnd < (DIAG ? 1 : 3); ++rnd) {
         const int u0 = 64 * rnd;
-        const int nsl = rnd < 2 ? 64 : NRSLOT;
-        if (rnd < 2) {
+        const int nsl = DIAG ? NJ : rnd < 2 ? 64 : NRSLOT;
+        if (DIAG) {
+#pragma unroll
+            for (int k = 0; k < NREG; ++k) Pst[k * PSS + t] = racc[k];
+        } else if (rnd < 2) {
             uint32_t r[32];
             tmem_ld32(tl + u0, r);
             tmem_wait_ld32(r);
@@ -589,11 +602,12 @@ __device__ bool fused_item(const Params& P, const TreeSmem& ts, int q, int lb, u
             for (int k = 0; k < 32; ++k) Pst[(32 + k) * PSS + t] = __uint_as_float(r[k]);
         } else {
 #pragma unroll
-            for (int k = 0; k < NRSLOT; ++k) Pst[k * PSS + t] = racc[k];
+            for (int k = 0; k < NREG; ++k) Pst[k * PSS + t] = racc[k];
         }
         __syncthreads();
         for (int task = t; task < 2 * nsl; task += NT) {
-            const int lp2 = task / nsl, us = task % nsl, u = kColSlots.u[u0 + us];
+            const int lp2 = task / nsl, us = task % nsl;
+            const int u = DIAG ? tri_slot(us, us) : kColSlots.u[u0 + us];
             if (!((P.used[u >> 5] >> (u & 31)) & 1u)) continue;      // no radial item reads this slot
             const float* r1 = Pst + us * PSS + lp2 * 2 * N;           // rows i1 = 2m + lp2 and i1 + 16
             float2 x[N];
@@ -807,6 +821,7 @@ __device__ __forceinline__ void publish(const Params& P, const Item& it) {
     }
 }
 
+template <bool DIAG>
 __global__ void __launch_bounds__(NT, CTAS_PER_SM) k_pencil(Params P) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ TreeSmem ts;
@@ -845,11 +860,11 @@ __global__ void __launch_bounds__(NT, CTAS_PER_SM) k_pencil(Params P) {
         mbar_init_fence();
         s_it[0] = decode_item(P, ts.stage_off, stage, atomicAdd(P.ctr, 1));
     }
-    if (warp == 0) tc_alloc<TMEM_COLS>(&tmem_base);
+    if (!DIAG && warp == 0) tc_alloc<TMEM_COLS>(&tmem_base);
     tc_fence_before_sync();
     __syncthreads();
     tc_fence_after_sync();
-    const uint32_t tmem = tmem_base;
+    const uint32_t tmem = DIAG ? 0u : tmem_base;
     uint32_t par = 0;                                  // parity bits of the next phases of bars[0..3]
     int* abort_flag = P.ctr + 1;
     Item prev{IT_END, 0, 0};
@@ -884,7 +899,7 @@ __global__ void __launch_bounds__(NT, CTAS_PER_SM) k_pencil(Params P) {
         if (s_ok) {
             bool done = true;
             if (it.kind == IT_TREE) tree_item(P, ts, it.q, it.local, smem);
-            else if (it.kind == IT_FUSED) done = fused_item(P, ts, it.q, it.local, smem, bars, par, tmem);
+            else if (it.kind == IT_FUSED) done = fused_item<DIAG>(P, ts, it.q, it.local, smem, bars, par, tmem);
             else done = radial_item(P, it.q, it.local, smem, bars, par);
             if (!done && t == 0) {
                 atomicOr(P.err, kErrTimeout);
@@ -897,7 +912,7 @@ __global__ void __launch_bounds__(NT, CTAS_PER_SM) k_pencil(Params P) {
     }
     tc_fence_before_sync();
     __syncthreads();
-    if (warp == 0) tc_dealloc<TMEM_COLS>(tmem);
+    if (!DIAG && warp == 0) tc_dealloc<TMEM_COLS>(tmem);
 }
 
 }  // namespace pencil
