@@ -586,7 +586,19 @@ boltz_status boltz_basis_rotate_f64(const double* X, int r, int n, const double*
  *                        cross terms (Sec. 5.1, eqs. "err low rank1-2"): the
  *                        paper's convergence measure, and its drop_tol =
  *                        c err rule when passed back.  Synchronises `stream`
- *                        (the new rank is read back).
+ *                        (the new rank is read back).  A step called again
+ *                        with the same rank, X, S, V pointers and dt, with
+ *                        both boundary vectors kept, is captured once as a
+ *                        CUDA graph (on a stream of its own) and replayed:
+ *                        one host synchronisation per step instead of three
+ *                        and no per-kernel launch cost, the same kernels in
+ *                        the same order (the same results).  The graph is
+ *                        captured again when the grid's workspace moved; a
+ *                        replay that finds a boundary vector in span(V)
+ *                        writes nothing and the step runs directly, as do
+ *                        later steps on those buffers.  The environment
+ *                        variable BOLTZ_SHOCK_GRAPH=0 (read at every call)
+ *                        turns replays off; so do BOLTZ_FAULT and profiling.
  *   boltz_shock_reconstruct  f DEVICE float64 [n_x][N^d] = X^T S V.
  * Errors: BOLTZ_EINVAL (sizes, r + 2 > r_max or > n_x, non-finite dt),
  * BOLTZ_ENONFINITE (a QR met linearly dependent rows; the factors are then

@@ -18,6 +18,7 @@
 #include <new>
 #include <set>
 #include <string>
+#include <tuple>
 #include <utility>
 #include <vector>
 
@@ -3013,7 +3014,28 @@ struct boltz_shock_s {
           *S32 = nullptr, *D32 = nullptr, *Cs32 = nullptr, *G32 = nullptr;
     void* spec_v = nullptr;
     void* qr_ws = nullptr;
-    int* d_int = nullptr;                 // [0] QR info (K), [1] QR info (L), [2] r_keep, [3] SVD info
+    int* d_int = nullptr;                 // [0] QR info (K), [1] QR info (L), [2] r_keep, [3] SVD info,
+                                          // [4] skip bits of a replayed step (1: a boundary vector not
+                                          // kept, 2: a QR or the rank failed)
+    double* d_tol = nullptr;              // drop_tol of a replayed step
+    // replayed steps: one CUDA graph per (rank, X, S, V, dt) seen twice, both boundary
+    // vectors kept; h_pin: [0] drop_tol, [1..2] d_int[0..4] read back, [3] the step's err
+    double* h_pin = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    struct GraphKey {
+        int r;
+        const double *X, *S, *V;
+        double dt;
+        bool operator<(const GraphKey& o) const {
+            return std::tie(r, X, S, V, dt) < std::tie(o.r, o.X, o.S, o.V, o.dt);
+        }
+    };
+    struct StepGraph {
+        cudaGraphExec_t exec = nullptr;
+        char* ws = nullptr;               // the grid workspace the graph's kernels read
+    };
+    std::map<GraphKey, StepGraph> graphs;
+    std::set<GraphKey> seen, direct_only;    // keys seen once; keys whose replay found a vector not kept
 };
 
 namespace {
@@ -3066,7 +3088,7 @@ boltz_status boltz_shock_create(boltz_grid g, int n_x, double L_x, const double*
         {(void**)&s->K32, rm * nx * 4}, {(void**)&s->C32, rm * nx * 4}, {(void**)&s->E32, rm * rm * rm * 4},
         {(void**)&s->S32, rm * rm * 4}, {(void**)&s->D32, rm * rm * 4}, {(void**)&s->Cs32, rm * rm * rm * 4},
         {(void**)&s->G32, rm * nv * 4}, {(void**)&s->spec_v, rm * half * 8}, {&s->qr_ws, qr_bytes},
-        {(void**)&s->d_int, 64}};
+        {(void**)&s->d_int, 64}, {(void**)&s->d_tol, 8}};
     size_t total = 0;
     for (auto& pt : parts) total = align_up(total + pt.second, 256);
     if (cudaMalloc(&s->mem, total) != cudaSuccess) {
@@ -3105,6 +3127,12 @@ boltz_status boltz_shock_create(boltz_grid g, int n_x, double L_x, const double*
     s->rb = (std::sqrt(std::max(mid + rad, 0.0)) >= 1e-10) + (std::sqrt(std::max(mid - rad, 0.0)) >= 1e-10);
     s->pair_x.resize(n_x);
     for (int p = 0; p < n_x; ++p) s->pair_x[p] = p;
+    if (cudaMallocHost(&s->h_pin, 64) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        (void)cudaGetLastError();
+        boltz_shock_destroy(s);
+        return BOLTZ_ENOMEM;
+    }
     *out = s;
     return BOLTZ_OK;
 }
@@ -3112,6 +3140,9 @@ boltz_status boltz_shock_create(boltz_grid g, int n_x, double L_x, const double*
 boltz_status boltz_shock_destroy(boltz_shock s) {
     if (!s) return BOLTZ_OK;
     cudaDeviceSynchronize();
+    for (auto& kv : s->graphs) cudaGraphExecDestroy(kv.second.exec);
+    if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+    cudaFreeHost(s->h_pin);
     cudaFree(s->mem);
     delete s;
     return BOLTZ_OK;
@@ -3136,39 +3167,21 @@ boltz_status boltz_shock_full_step(boltz_shock s, double* f, int n_steps, double
     return BOLTZ_OK;
 }
 
-boltz_status boltz_shock_lowrank_step(boltz_shock s, double* X, double* S, double* V, int* r_io, double dt,
-                                      double drop_tol, double* err_out, void* stream) {
-    if (!s || !X || !S || !V || !r_io || !(dt > 0) || !std::isfinite(dt) || !(drop_tol >= 0) ||
-        !std::isfinite(drop_tol))
-        return BOLTZ_EINVAL;
-    const int r = *r_io, nx = s->n_x, nv = s->n_v;
-    if (r < 1 || r + s->rb > s->r_max || r + s->rb > nx) return BOLTZ_EINVAL;
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+}  // extern "C"
+
+namespace {
+
+// The collision batch and steps 1-4 of a low-rank step on the augmented basis
+// Vh of rh rows (filled by the caller): the collision batch of all ordered
+// pairs of Vh and its projection, the K-, S- and L-steps (Sec. 2.4), the
+// change of f over the step (Sec. 5.1) and the SVD of the new S with the drop
+// tolerance (Sec. 3.2).  drop_tol_dev, when not null, replaces drop_tol.
+boltz_status lr_core(boltz_shock s, const double* X, const double* S, int r, int rh, double dt, double drop_tol,
+                     const double* drop_tol_dev, cudaStream_t st) {
     using namespace boltz_dev;
-    const int T = kShT;
+    const int T = kShT, nx = s->n_x, nv = s->n_v;
+    void* stream = reinterpret_cast<void*>(st);
     boltz_status rs;
-    // 0. add basis (Sec. 3.1): V_hat = [V; f_L, f_R orthonormalised against V by Gram-Schmidt, twice].
-    // A boundary vector that keeps less than 1e-10 of its norm lies in span(V) already and is not
-    // appended (it would carry no weight and make the K-step QR singular).
-    BZ_CUDA(cudaMemcpyAsync(s->Vh, V, (size_t)r * nv * 8, cudaMemcpyDeviceToDevice, st));
-    int rh = r;
-    for (int k = 0; k < s->rb; ++k) {
-        double* b = s->Vh + (size_t)rh * nv;
-        const double* src = k == 0 ? s->fL : s->fR;
-        BZ_CUDA(cudaMemcpyAsync(b, src, (size_t)nv * 8, cudaMemcpyDeviceToDevice, st));
-        k_sh_rowdots<<<1, T, 0, st>>>(src, nv, src, 1.0, s->nrm);
-        for (int pass = 0; pass < 2; ++pass) {
-            k_sh_rowdots<<<rh, T, 0, st>>>(s->Vh, nv, b, s->wv, s->cvec);
-            k_sh_subtract<<<sh_grid(nv), T, 0, st>>>(b, s->Vh, s->cvec, rh, nv);
-        }
-        k_sh_rowdots<<<1, T, 0, st>>>(b, nv, b, 1.0, s->nrm + 1);
-        double hn[2];
-        BZ_CUDA(cudaMemcpyAsync(hn, s->nrm, sizeof(hn), cudaMemcpyDeviceToHost, st));
-        BZ_CUDA(cudaStreamSynchronize(st));
-        if (!(hn[1] > 1e-20 * hn[0])) continue;
-        k_sh_normalize<<<1, T, 0, st>>>(b, nv, s->wv);
-        ++rh;
-    }
     // K = X^T S on the old rows, zero on the added ones (the added directions carry no weight)
     k_sh_comb<false><<<sh_grid((size_t)r * nx), T, 0, st>>>(X, r, nx, S, r, r, s->K);
     if (rh > r) BZ_CUDA(cudaMemsetAsync(s->K + (size_t)r * nx, 0, (size_t)(rh - r) * nx * 8, st));
@@ -3218,10 +3231,78 @@ boltz_status boltz_shock_lowrank_step(boltz_shock s, double* X, double* S, doubl
     k_sh_dgram<false><<<dim3(rh, rh), T, 0, st>>>(s->X1, s->K1, s->K, rh, nx, s->dx, s->Pk);
     k_sh_dgram<false><<<dim3(rh, rh), T, 0, st>>>(s->Vh, s->L1, s->L, rh, nv, s->wv, s->Gv);
     k_sh_err<<<1, T, 0, st>>>(s->nk, s->nl, s->Pk, s->Gv, s->S1, s->S2, rh, s->errd);
-    // 4. drop (Sec. 3.2): SVD of S, keep sigma >= drop_tol, rotate the bases
-    if ((rs = boltz_svd_truncate_f64(s->Sn, rh, drop_tol, s->U, s->sig, s->Qm, s->d_int + 2, s->d_int + 3,
-                                     stream)) != BOLTZ_OK)
-        return rs;
+    // 4. drop (Sec. 3.2): SVD of S, keep sigma >= drop_tol
+    if ((rs = ensure_lowrank_attrs()) != BOLTZ_OK) return rs;
+    k_svd_jacobi_f64<<<1, 1024, kSvdSmem, st>>>(s->Sn, rh, drop_tol, s->U, s->sig, s->Qm, s->d_int + 2, s->d_int + 3,
+                                                drop_tol_dev);
+    BZ_CUDA(cudaGetLastError());
+    return BOLTZ_OK;
+}
+
+// Rotation of the bases by the kept singular vectors: X <- X1 U, V <- Vn Qm,
+// S <- diag(sigma); r_dev / skip as in k_rotate_f64 (null: the host's rk).
+void lr_rotate(boltz_shock s, double* X, double* S, double* V, int rh, int rk, const int* r_dev, const int* skip,
+               cudaStream_t st) {
+    using namespace boltz_dev;
+    const int gx = (s->n_x + kLrThreads - 1) / kLrThreads, gv = (s->n_v + kLrThreads - 1) / kLrThreads;
+    if (rh <= 16) {
+        k_rotate_f64<16><<<gx, kLrThreads, 0, st>>>(s->X1, s->U, rh, rk, s->n_x, X, r_dev, skip);
+        k_rotate_f64<16><<<gv, kLrThreads, 0, st>>>(s->Vn, s->Qm, rh, rk, s->n_v, V, r_dev, skip);
+    } else if (rh <= 32) {
+        k_rotate_f64<32><<<gx, kLrThreads, 0, st>>>(s->X1, s->U, rh, rk, s->n_x, X, r_dev, skip);
+        k_rotate_f64<32><<<gv, kLrThreads, 0, st>>>(s->Vn, s->Qm, rh, rk, s->n_v, V, r_dev, skip);
+    } else {
+        k_rotate_f64<64><<<gx, kLrThreads, 0, st>>>(s->X1, s->U, rh, rk, s->n_x, X, r_dev, skip);
+        k_rotate_f64<64><<<gv, kLrThreads, 0, st>>>(s->Vn, s->Qm, rh, rk, s->n_v, V, r_dev, skip);
+    }
+    k_sh_diag<<<1, kShT, 0, st>>>(s->sig, rk, S, r_dev, skip);
+}
+
+// Step 0, adding the boundary basis (Sec. 3.1): V_hat = [V; f_L, f_R
+// orthonormalised against V by Gram-Schmidt, twice].  KEEP_ALL (a replayed
+// step): both are appended and k_sh_keep_check records on the device whether
+// that was right; otherwise a vector keeping less than 1e-10 of its norm lies
+// in span(V) already and is not appended (it would carry no weight and make
+// the K-step QR singular), a decision read back on the host.  Returns rh.
+template <bool KEEP_ALL>
+boltz_status lr_append(boltz_shock s, const double* V, int r, int* rh_out, cudaStream_t st) {
+    using namespace boltz_dev;
+    const int T = kShT, nv = s->n_v;
+    BZ_CUDA(cudaMemcpyAsync(s->Vh, V, (size_t)r * nv * 8, cudaMemcpyDeviceToDevice, st));
+    int rh = r;
+    for (int k = 0; k < s->rb; ++k) {
+        double* b = s->Vh + (size_t)rh * nv;
+        const double* src = k == 0 ? s->fL : s->fR;
+        BZ_CUDA(cudaMemcpyAsync(b, src, (size_t)nv * 8, cudaMemcpyDeviceToDevice, st));
+        k_sh_rowdots<<<1, T, 0, st>>>(src, nv, src, 1.0, s->nrm);
+        for (int pass = 0; pass < 2; ++pass) {
+            k_sh_rowdots<<<rh, T, 0, st>>>(s->Vh, nv, b, s->wv, s->cvec);
+            k_sh_subtract<<<sh_grid(nv), T, 0, st>>>(b, s->Vh, s->cvec, rh, nv);
+        }
+        k_sh_rowdots<<<1, T, 0, st>>>(b, nv, b, 1.0, s->nrm + 1);
+        if constexpr (KEEP_ALL) {
+            k_sh_keep_check<<<1, 32, 0, st>>>(s->nrm, s->d_int + 4);
+        } else {
+            double hn[2];
+            BZ_CUDA(cudaMemcpyAsync(hn, s->nrm, sizeof(hn), cudaMemcpyDeviceToHost, st));
+            BZ_CUDA(cudaStreamSynchronize(st));
+            if (!(hn[1] > 1e-20 * hn[0])) continue;
+        }
+        k_sh_normalize<<<1, T, 0, st>>>(b, nv, s->wv);
+        ++rh;
+    }
+    *rh_out = rh;
+    return BOLTZ_OK;
+}
+
+// One low-rank step with every decision made on the host (the reference path).
+boltz_status lr_step_direct(boltz_shock s, double* X, double* S, double* V, int* r_io, double dt, double drop_tol,
+                            double* err_out, cudaStream_t st) {
+    const int r = *r_io;
+    int rh = r;
+    boltz_status rs;
+    if ((rs = lr_append<false>(s, V, r, &rh, st)) != BOLTZ_OK) return rs;
+    if ((rs = lr_core(s, X, S, r, rh, dt, drop_tol, nullptr, st)) != BOLTZ_OK) return rs;
     int hinfo[4] = {0, 0, 0, 0};
     double herr = 0.0;
     BZ_CUDA(cudaMemcpyAsync(hinfo, s->d_int, sizeof(hinfo), cudaMemcpyDeviceToHost, st));
@@ -3231,12 +3312,107 @@ boltz_status boltz_shock_lowrank_step(boltz_shock s, double* X, double* S, doubl
     if (hinfo[0] != 0 || hinfo[1] != 0) return BOLTZ_ENONFINITE;       // a QR met linearly dependent rows
     const int rk = hinfo[2];
     if (rk < 1) return BOLTZ_ENONFINITE;
-    if ((rs = boltz_basis_rotate_f64(s->X1, rh, nx, s->U, rk, X, stream)) != BOLTZ_OK) return rs;
-    if ((rs = boltz_basis_rotate_f64(s->Vn, rh, nv, s->Qm, rk, V, stream)) != BOLTZ_OK) return rs;
-    k_sh_diag<<<1, T, 0, st>>>(s->sig, rk, S);
+    lr_rotate(s, X, S, V, rh, rk, nullptr, nullptr, st);
     BZ_CUDA(cudaGetLastError());
     *r_io = rk;
     return BOLTZ_OK;
+}
+
+// The launches of a replayed step (captured once): both boundary vectors
+// appended, drop_tol from s->d_tol (copied from the pinned h_pin[0] by the
+// graph's first node), the rank-dependent tail driven by the device's r_keep
+// and skip bits, and the values the host needs copied back to h_pin.
+boltz_status lr_step_graph_body(boltz_shock s, double* X, double* S, double* V, int r, double dt, cudaStream_t st) {
+    using namespace boltz_dev;
+    boltz_status rs;
+    BZ_CUDA(cudaMemcpyAsync(s->d_tol, s->h_pin, sizeof(double), cudaMemcpyHostToDevice, st));
+    BZ_CUDA(cudaMemsetAsync(s->d_int + 4, 0, sizeof(int), st));
+    int rh = r;
+    if ((rs = lr_append<true>(s, V, r, &rh, st)) != BOLTZ_OK) return rs;
+    if ((rs = lr_core(s, X, S, r, rh, dt, 0.0, s->d_tol, st)) != BOLTZ_OK) return rs;
+    k_sh_step_check<<<1, 32, 0, st>>>(s->d_int, s->d_int + 4);
+    lr_rotate(s, X, S, V, rh, rh, s->d_int + 2, s->d_int + 4, st);
+    BZ_CUDA(cudaMemcpyAsync(s->h_pin + 1, s->d_int, 5 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    BZ_CUDA(cudaMemcpyAsync(s->h_pin + 4, s->errd, sizeof(double), cudaMemcpyDeviceToHost, st));
+    BZ_CUDA(cudaGetLastError());
+    return BOLTZ_OK;
+}
+
+// Whether the grid's cached plan is the all-pairs batch of n inputs in `form`.
+bool plan_is_all_pairs(const boltz_grid_s* g, int n, int form) {
+    if (!g->plan_uploaded || g->last_form != form || g->last_n_inputs != n || g->last_elem != 4 ||
+        (int)g->last_j.size() != n * n)
+        return false;
+    for (int k = 0; k < n * n; ++k)
+        if (g->last_j[k] != k / n || g->last_l[k] != k % n) return false;
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+boltz_status boltz_shock_lowrank_step(boltz_shock s, double* X, double* S, double* V, int* r_io, double dt,
+                                      double drop_tol, double* err_out, void* stream) {
+    if (!s || !X || !S || !V || !r_io || !(dt > 0) || !std::isfinite(dt) || !(drop_tol >= 0) ||
+        !std::isfinite(drop_tol))
+        return BOLTZ_EINVAL;
+    const int r = *r_io, nx = s->n_x;
+    if (r < 1 || r + s->rb > s->r_max || r + s->rb > nx) return BOLTZ_EINVAL;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    boltz_grid_s* g = s->g;
+    // Replayed steps: a step with the same (rank, X, S, V, dt) as an earlier one, both
+    // boundary vectors kept, runs as one CUDA graph, with one host synchronisation
+    // instead of three and no per-kernel launch cost.  The first such step runs
+    // directly (it also leaves the grid's all-pairs plan cached for the graph); the
+    // graph is captured at the second and replayed while the grid's workspace and
+    // cached plan stay those it was captured with.  A replay that finds a boundary
+    // vector in span(V) writes nothing, and the step runs directly.
+    const boltz_shock_s::GraphKey key{r, X, S, V, dt};
+    const int rh = r + s->rb;
+    const char* env = std::getenv("BOLTZ_SHOCK_GRAPH");
+    const bool eligible = s->rb == 2 && !g->prof_on && !fault_injected("badplan") && !fault_injected("alloc") &&
+                          !(env && std::strcmp(env, "0") == 0) && !s->direct_only.count(key);
+    if (eligible && s->seen.count(key) && plan_is_all_pairs(g, rh, s->form)) {
+        auto it = s->graphs.find(key);
+        if (it != s->graphs.end() && it->second.ws != g->d_ws) {
+            cudaGraphExecDestroy(it->second.exec);
+            s->graphs.erase(it);
+            it = s->graphs.end();
+        }
+        if (it == s->graphs.end()) {
+            cudaGraph_t graph = nullptr;
+            cudaGraphExec_t exec = nullptr;
+            bool ok = cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+            if (ok) {
+                const boltz_status rs = lr_step_graph_body(s, X, S, V, r, dt, s->cap_stream);
+                ok = cudaStreamEndCapture(s->cap_stream, &graph) == cudaSuccess && rs == BOLTZ_OK;
+                ok = ok && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+                if (graph) cudaGraphDestroy(graph);
+            }
+            (void)cudaGetLastError();
+            if (ok) it = s->graphs.emplace(key, boltz_shock_s::StepGraph{exec, g->d_ws}).first;
+            else if (exec) cudaGraphExecDestroy(exec);
+        }
+        if (it != s->graphs.end()) {
+            s->h_pin[0] = drop_tol;
+            BZ_CUDA(cudaGraphLaunch(it->second.exec, st));
+            BZ_CUDA(cudaStreamSynchronize(st));
+            int hinfo[5];
+            std::memcpy(hinfo, s->h_pin + 1, sizeof(hinfo));
+            if (!(hinfo[4] & 1)) {
+                if (err_out) *err_out = s->h_pin[4];
+                if (hinfo[0] != 0 || hinfo[1] != 0 || hinfo[2] < 1) return BOLTZ_ENONFINITE;
+                *r_io = hinfo[2];
+                return BOLTZ_OK;
+            }
+            s->direct_only.insert(key);            // this basis keeps dropping a boundary vector
+            cudaGraphExecDestroy(it->second.exec);
+            s->graphs.erase(it);
+        }
+    }
+    if (eligible) s->seen.insert(key);
+    return lr_step_direct(s, X, S, V, r_io, dt, drop_tol, err_out, st);
 }
 
 boltz_status boltz_shock_reconstruct(boltz_shock s, const double* X, const double* S, const double* V, int r,

@@ -412,10 +412,13 @@ __device__ bool jacobi_sweeps(T* A, T* V, int r, T tol, int max_sweeps) {
     return false;
 }
 
+// drop_tol_dev, when not null, replaces drop_tol (a value written to device
+// memory before the launch, as in a replayed graph).
 __global__ void __launch_bounds__(1024) k_svd_jacobi_f64(const double* __restrict__ S, int r, double drop_tol,
                                                         double* __restrict__ U, double* __restrict__ sigma,
                                                         double* __restrict__ Qm, int* __restrict__ r_keep,
-                                                        int* __restrict__ info) {
+                                                        int* __restrict__ info,
+                                                        const double* __restrict__ drop_tol_dev = nullptr) {
     extern __shared__ double svd_smem[];
     double* A = svd_smem;                          // column-major: column c at c*64
     double* V = svd_smem + 64 * 64;
@@ -487,8 +490,9 @@ __global__ void __launch_bounds__(1024) k_svd_jacobi_f64(const double* __restric
             order[i] = order[best];
             order[best] = tmp;
         }
+        const double tol = drop_tol_dev ? *drop_tol_dev : drop_tol;
         int keep = 0;
-        for (int i = 0; i < r; ++i) keep += sv[order[i]] >= drop_tol ? 1 : 0;
+        for (int i = 0; i < r; ++i) keep += sv[order[i]] >= tol ? 1 : 0;
         *r_keep = keep;
         *info = converged ? 0 : 1;
     }
@@ -503,10 +507,17 @@ __global__ void __launch_bounds__(1024) k_svd_jacobi_f64(const double* __restric
     }
 }
 
-// X_bar_k(x) = sum_i X_i(x) U_ik, k < r_new (U row-major r x r, ld r)
+// X_bar_k(x) = sum_i X_i(x) U_ik, k < r_new (U row-major r x r, ld r).
+// r_new_dev, when not null, replaces r_new; skip, when not null and set,
+// makes the kernel write nothing (both read from device memory, as in a
+// replayed graph whose earlier kernels decide them).
 template <int RMAX>
 __global__ void __launch_bounds__(kLrThreads) k_rotate_f64(const double* __restrict__ X, const double* __restrict__ U,
-                                                          int r, int r_new, int n, double* __restrict__ out) {
+                                                          int r, int r_new, int n, double* __restrict__ out,
+                                                          const int* __restrict__ r_new_dev = nullptr,
+                                                          const int* __restrict__ skip = nullptr) {
+    if (skip && *skip) return;
+    if (r_new_dev) r_new = min(max(*r_new_dev, 0), r);
     __shared__ double Us[64 * 64];
     for (int e = threadIdx.x; e < r * r; e += kLrThreads) Us[e] = U[e];
     __syncthreads();

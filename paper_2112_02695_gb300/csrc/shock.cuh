@@ -310,9 +310,29 @@ __global__ void __launch_bounds__(kShT) k_sh_err(const double* __restrict__ nk, 
     if (threadIdx.x == 0) *err = sqrt(fmax(s, 0.0));
 }
 
-// S = diag(sigma[:r]) (packed [r][r])
-__global__ void k_sh_diag(const double* __restrict__ sigma, int r, double* __restrict__ S) {
+// S = diag(sigma[:r]) (packed [r][r]); r_dev and skip as in k_rotate_f64
+__global__ void k_sh_diag(const double* __restrict__ sigma, int r, double* __restrict__ S,
+                          const int* __restrict__ r_dev = nullptr, const int* __restrict__ skip = nullptr) {
+    if (skip && *skip) return;
+    if (r_dev) r = *r_dev;
     for (int t = threadIdx.x; t < r * r; t += blockDim.x) S[t] = (t / r == t % r) ? sigma[t / r] : 0.0;
+}
+
+// Keep/drop decision of an appended boundary vector made on the device: it
+// is kept when its squared norm after Gram-Schmidt, nrm[1], is more than
+// 1e-20 of its squared norm before, nrm[0].  A replayed graph assumes that
+// both boundary vectors are kept; skip[0] records that one was not, and the
+// kernels that write the step's outputs then do nothing (the host reruns the
+// step without the graph).
+__global__ void k_sh_keep_check(const double* __restrict__ nrm, int* __restrict__ skip) {
+    if (threadIdx.x == 0 && !(nrm[1] > 1e-20 * nrm[0])) *skip |= 1;
+}
+
+// After the drop: a QR that met linearly dependent rows (info[0], info[1]) or
+// no singular value kept (info[2] < 1) sets skip bit 2, so that the outputs
+// stay as they were, as the host-driven step leaves them on that error.
+__global__ void k_sh_step_check(const int* __restrict__ info, int* __restrict__ skip) {
+    if (threadIdx.x == 0 && (info[0] != 0 || info[1] != 0 || info[2] < 1)) *skip |= 2;
 }
 
 // f[x][v] = sum_i X_i(x) L_i(v)

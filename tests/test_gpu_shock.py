@@ -297,3 +297,51 @@ def test_rejections():
     finally:
         sh.close()
         g.close()
+
+
+@pytest.mark.parametrize("form,start", [(0, "factor"), (3, "factor"), (0, "bimodal")])
+def test_replayed_steps_equal_direct_steps(monkeypatch, form, start):
+    """Eight low-rank steps on the same buffers: from the third on they replay
+    a captured graph; with BOLTZ_SHOCK_GRAPH=0 every step runs directly.  The
+    factors, ranks and convergence measures agree bit for bit.  The bimodal
+    start (1 - s) f_L + s f_R has f_L, f_R in span(V): replays find a boundary
+    vector not kept, write nothing, and the step runs directly."""
+    import torch
+    from oracle import shock as SH
+    B = require_gpu()
+
+    def run():
+        sp, g, sh = make(B, form=form)
+        n_x, n_v = sp.n_x, N ** 2
+        try:
+            rm = sh.r_max
+            Xd = torch.zeros((rm, n_x), dtype=torch.float64, device="cuda")
+            Vd = torch.zeros((rm, n_v), dtype=torch.float64, device="cuda")
+            Sd = torch.zeros(rm * rm, dtype=torch.float64, device="cuda")
+            if start == "factor":
+                X, S, V = SH.factor(sp, sp.initial(), 4)
+                r = 4
+            else:
+                fL, fR = sp.boundary()
+                x = -L_X + (np.arange(n_x) + 0.5) * (2 * L_X / n_x)
+                s = (np.tanh(0.5 * x) + 1.0) / 2.0
+                X, S, V = SH.factor(sp, np.outer(1.0 - s, fL) + np.outer(s, fR), 2)
+                r = 2
+            Xd[:r] = torch.tensor(X)
+            Vd[:r] = torch.tensor(V)
+            Sd[: r * r] = torch.tensor(S.ravel())
+            hist = []
+            for _ in range(8):
+                r, err = B.boltz_shock_lowrank_step(sh, Xd, Sd, Vd, r, DT, 1e-7)
+                hist.append((r, err))
+            torch.cuda.synchronize()
+            return hist, Xd.cpu().numpy(), Sd.cpu().numpy(), Vd.cpu().numpy()
+        finally:
+            sh.close()
+            g.close()
+
+    h1, X1, S1, V1 = run()
+    monkeypatch.setenv("BOLTZ_SHOCK_GRAPH", "0")
+    h2, X2, S2, V2 = run()
+    assert h1 == h2
+    assert np.array_equal(X1, X2) and np.array_equal(S1, S2) and np.array_equal(V1, V2)
