@@ -2102,6 +2102,7 @@ boltz_status ensure_lowrank_attrs() {
     std::lock_guard<std::mutex> lock(mu);
     if (done.count(dev)) return BOLTZ_OK;
     if (set_smem(k_chol_f64, kCholSmem) != cudaSuccess || set_smem(k_svd_jacobi_f64, kSvdSmem) != cudaSuccess ||
+        set_smem(k_qr_small_f64, kQrSmallSmem) != cudaSuccess ||
         set_smem(k_lstep_collision<64>, lstep_smem<64>()) != cudaSuccess ||
         set_smem(k_lr_coupling, kCouplingSmem) != cudaSuccess) {
         (void)cudaGetLastError();
@@ -2955,7 +2956,9 @@ boltz_status boltz_qr_f64(const double* W, int r, int n, double w, double* Y, do
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     BZ_CUDA(cudaMemsetAsync(info, 0, sizeof(int), st));
     char* ws = static_cast<char*>(workspace);
-    if (r <= 16) launch_qr<16>(W, r, n, w, Y, R, ws, info, st);
+    if (r <= kQrSmallR && n <= kQrSmallN)            // one CTA holds the whole block
+        k_qr_small_f64<<<1, kQrSmallThreads, size_t(r) * n * sizeof(double), st>>>(W, r, n, w, Y, R, info);
+    else if (r <= 16) launch_qr<16>(W, r, n, w, Y, R, ws, info, st);
     else if (r <= 32) launch_qr<32>(W, r, n, w, Y, R, ws, info, st);
     else launch_qr<64>(W, r, n, w, Y, R, ws, info, st);
     BZ_CUDA(cudaGetLastError());

@@ -324,6 +324,108 @@ __global__ void __launch_bounds__(kLrThreads) k_apply_rinv_f64(const double* W, 
     }
 }
 
+// ---------------------------------------------------------------- Cholesky-QR2, one CTA (FP64)
+// The same factorisation for small blocks (r <= kQrSmallR rows of n <=
+// kQrSmallN entries, e.g. the K and L factors of a low-rank step): W staged
+// in shared memory once, both passes (Gram, Cholesky, R^-1, apply) in one
+// CTA, one warp per Gram entry with lanes over the entries in a fixed order.
+// Same outputs and failure convention as the multi-kernel path.
+constexpr int kQrSmallR = 8, kQrSmallN = 2048, kQrSmallThreads = 1024;
+constexpr size_t kQrSmallSmem = size_t(kQrSmallR) * kQrSmallN * sizeof(double);
+
+__global__ void __launch_bounds__(kQrSmallThreads) k_qr_small_f64(const double* __restrict__ W, int r, int n, double w,
+                                                                double* __restrict__ Y, double* __restrict__ R,
+                                                                int* __restrict__ info) {
+    extern __shared__ double qs_smem[];
+    double* Ws = qs_smem;                                  // [r][n]
+    __shared__ double G[kQrSmallR * kQrSmallR], Rs[kQrSmallR * kQrSmallR], Xs[kQrSmallR * kQrSmallR],
+        R1[kQrSmallR * kQrSmallR];
+    __shared__ int bad;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    constexpr int NW = kQrSmallThreads / 32;
+    for (int e = t; e < r * n; e += kQrSmallThreads) Ws[e] = W[e];
+    if (t == 0) bad = 0;
+    __syncthreads();
+    for (int pass = 0; pass < 2; ++pass) {
+        // G = w W W^T, entry (a, b) by warp e: lanes over v, shuffle tree
+        for (int e = warp; e < r * r; e += NW) {
+            const int a = e / r, b = e % r;
+            double g = 0.0;
+            if (a <= b) {
+                for (int v = lane; v < n; v += 32) g = fma(Ws[a * n + v], Ws[b * n + v], g);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) g += __shfl_down_sync(0xffffffffu, g, o);
+            }
+            if (lane == 0 && a <= b) {
+                G[a * r + b] = w * g;
+                G[b * r + a] = w * g;
+            }
+            if (lane == 0) Rs[e] = 0.0;
+        }
+        __syncthreads();
+        if (t == 0) {                                          // G = R^T R, R upper
+            for (int k = 0; k < r && !bad; ++k) {
+                double d = G[k * r + k];
+                for (int i = 0; i < k; ++i) d -= Rs[i * r + k] * Rs[i * r + k];
+                if (!(d > 0.0)) {
+                    bad = k + 1;
+                    break;
+                }
+                Rs[k * r + k] = sqrt(d);
+                for (int j = k + 1; j < r; ++j) {
+                    double a = G[k * r + j];
+                    for (int i = 0; i < k; ++i) a -= Rs[i * r + k] * Rs[i * r + j];
+                    Rs[k * r + j] = a / Rs[k * r + k];
+                }
+            }
+        }
+        __syncthreads();
+        if (bad) {
+            if (t == 0 && *info == 0) *info = bad;
+            const double nan = __longlong_as_double(0x7ff8000000000000ll);
+            for (int e = t; e < r * r; e += kQrSmallThreads) R[e] = nan;
+            for (int e = t; e < r * n; e += kQrSmallThreads) Y[e] = nan;
+            return;
+        }
+        for (int j = t; j < r; j += kQrSmallThreads) {         // R X = I, one column per thread
+            for (int i = r - 1; i >= 0; --i) {
+                double a = (i == j) ? 1.0 : 0.0;
+                for (int k = i + 1; k <= j; ++k) a -= Rs[i * r + k] * Xs[k * r + j];
+                Xs[i * r + j] = (i <= j) ? a / Rs[i * r + i] : 0.0;
+            }
+        }
+        __syncthreads();
+        // W <- W R^-1 in place: each thread reads its entries' r values first
+        for (int v = t; v < n; v += kQrSmallThreads) {
+            double x[kQrSmallR];
+#pragma unroll
+            for (int i = 0; i < kQrSmallR; ++i) x[i] = i < r ? Ws[i * n + v] : 0.0;
+#pragma unroll
+            for (int k = 0; k < kQrSmallR; ++k) {
+                if (k >= r) break;
+                double y = 0.0;
+#pragma unroll
+                for (int i = 0; i < kQrSmallR; ++i)
+                    if (i <= k) y = fma(x[i], Xs[i * r + k], y);
+                Ws[k * n + v] = y;
+            }
+        }
+        // R of the two passes: R = R2 R1
+        for (int e = t; e < r * r; e += kQrSmallThreads) {
+            if (pass == 0) {
+                R1[e] = Rs[e];
+            } else {
+                const int i = e / r, j = e % r;
+                double o = 0.0;
+                for (int k = i; k <= j; ++k) o += Rs[i * r + k] * R1[k * r + j];
+                R[e] = o;
+            }
+        }
+        __syncthreads();
+    }
+    for (int e = t; e < r * n; e += kQrSmallThreads) Y[e] = Ws[e];
+}
+
 // ---------------------------------------------------------------- one-sided Jacobi SVD (FP64)
 // One CTA of 32 warps: in every round of a sweep the columns are paired by
 // the round-robin schedule and warp p rotates pair p (lanes split the r
