@@ -710,6 +710,12 @@ def main():
                                   "tensor_tflops_executed": tc_achieved, "peak": bf16_peak,
                                   "frac": tc_achieved / bf16_peak, "peak_source": peak_src,
                                   "share_of_step": mss / max(sum(ms for _, ms in prof_s.values()), 1e-9)}}
+        # the same kernel against the algorithmic (FFT) flops of the fields it makes,
+        # at the pipe it runs on: how much of the BF16 peak the method's own work uses
+        alg_field = flops_per_transform(N ** d) + 3 * N ** d
+        alg_tflops = alg_field * fields_per_launch / (mss / ls * 1e-3) / 1e12
+        split["shift_kernel"]["alg_tflops"] = alg_tflops
+        split["shift_kernel"]["alg_frac_of_bf16_peak"] = alg_tflops / bf16_peak
         split["speedup_vs_fp32_batched"] = split["value"] / (value / world)
 
     # Carleman form (the paper's own fast method, gamma = d - 2 only) on the same batch
