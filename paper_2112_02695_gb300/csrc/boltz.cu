@@ -66,8 +66,9 @@ struct Plan {
     size_t plan_bytes = 0;
     // workspace layout (byte offsets)
     size_t off_plan = 0, off_A = 0, off_P = 0, off_qhat = 0, off_fN = 0, off_lam = 0, off_img = 0, total = 0;
-    // pipelined schedule (pencil.cuh): one chunk, gain slots in TRI16 numbering,
-    // Qhat+ and the output lists over the used slots only
+    // pipelined schedule (pencil.cuh): chunks of at most 16 inputs (one launch
+    // each), gain slots in TRI16 numbering, Qhat+ and the output lists over
+    // each chunk's used slots only
     bool pencil = false;
     int pen_n_used = 0;
     std::vector<int> pen_slots;           // used TRI16 slots, ascending

@@ -6,7 +6,9 @@
 // A_{q,p,j}(v) = g_j,N(v - rho_q sigma_p / 2), their products summed over
 // the directions with the weights w_p, one forward transform per node times
 // the radial multiplier c_q(|k|), accumulated over q) for one chunk of at
-// most 16 inputs and all of their 136 unordered pairs.  How it computes it:
+// most 16 inputs and the used ones of their 136 unordered pairs (one launch
+// per chunk; a batch of more inputs is split into chunks on the host).  How
+// it computes it:
 //
 // * The phase of a shifted field separates over the axes,
 //   phi(k) = phi_0(k_0; s_0) phi_1(k_1; s_1) phi_2(k_2; s_2), s = rho sigma / 2,
