@@ -170,7 +170,8 @@ enum { BOLTZ_LOSS_EXACT = 0, BOLTZ_LOSS_MASS_CONSISTENT = 1 };
  *                fields never leave the chip.  The inputs are split into
  *                chunks of at most 16 (each pair's two inputs in one chunk,
  *                e.g. the cells of a full tensor grid Q(f_x, f_x) in chunks of
- *                16 cells), one launch per chunk.
+ *                16 cells); chunks of one shape (input count and used
+ *                pairs) run in one launch, at most 64 chunks each.
  */
 #define BOLTZ_SCHEDULE_AUTO 0
 #define BOLTZ_SCHEDULE_NODE_BLOCKS 1

@@ -66,20 +66,20 @@ struct Plan {
     size_t plan_bytes = 0;
     // workspace layout (byte offsets)
     size_t off_plan = 0, off_A = 0, off_P = 0, off_qhat = 0, off_fN = 0, off_lam = 0, off_img = 0, total = 0;
-    // pipelined schedule (pencil.cuh): chunks of at most 16 inputs (one launch
-    // each), gain slots in TRI16 numbering, Qhat+ and the output lists over
-    // each chunk's used slots only
+    // pipelined schedule (pencil.cuh): chunks of at most 16 inputs, gain
+    // slots in TRI16 numbering, Qhat+ and the output lists over each chunk's
+    // used slots only.  Chunks of one shape share a launch: an entry of
+    // `chunks` is then one launch, its inputs and output slots chunk after
+    // chunk (U = chunks x used slots per chunk).
     bool pencil = false;
-    int pen_n_used = 0;
-    std::vector<int> pen_slots;           // used TRI16 slots, ascending
-    std::vector<char> pen_blob;           // direction tree + slot list (device image)
+    std::vector<char> pen_blob;           // direction tree + slot lists (device image)
     size_t off_pen_blob = 0, off_X = 0, off_Pt = 0, off_ctr = 0, off_qstd = 0;
-    size_t pen_off[9] = {};               // offsets inside the blob: grp, s0_dir, s0_child,
-                                          // s01_dir, step_blk, step_dir, step_sel, step_w, slots
-                                          // (the slot list of chunk 0; chunk k's at pen_slot_off[k])
-    std::vector<size_t> pen_slot_off;     // per chunk: its used-slot list inside the blob
-    std::vector<std::array<unsigned, 5>> pen_mask;   // per chunk: used TRI16 slots as a bit set
-    std::vector<char> pen_diag;           // per chunk: every used slot is a diagonal (j, j)
+    size_t pen_off[8] = {};               // offsets inside the blob: grp, s0_dir, s0_child,
+                                          // s01_dir, step_blk, step_dir, step_sel, step_w
+    std::vector<int> pen_nchunk;          // per launch: its chunks
+    std::vector<size_t> pen_slot_off;     // per launch: its chunks' used-slot list inside the blob
+    std::vector<std::array<unsigned, 5>> pen_mask;   // per launch: used TRI16 slots as a bit set
+    std::vector<char> pen_diag;           // per launch: every used slot is a diagonal (j, j)
 };
 
 // Direction structure of a 3D rule for the pipelined schedule: the distinct
@@ -324,7 +324,7 @@ PencilTree build_pencil_tree(const boltz_grid_s* g) {
     bool rows_fit = true;
     for (int b = 0; b < ng; ++b) rows_fit = rows_fit && load[b] <= pc::MAX_ROWS;
     T.ok = !T.step_dir.empty() && T.n_s0 <= pc::MAX_S && T.n_s01 <= pc::MAX_S &&
-           (int)T.step_dir.size() <= pc::MAX_STEP && rows_fit && g->n_rho + pc::RLAG <= pc::MAX_STAGE;
+           (int)T.step_dir.size() <= pc::MAX_STEP && rows_fit;
     return T;
 }
 
@@ -378,10 +378,16 @@ bool pencil_applies(const boltz_grid_s* g, const int32_t* pj, const int32_t* pl,
     return pencil_chunks(pj, pl, n_pairs, chunks);
 }
 
-// Plan of the pipelined schedule: the inputs in chunks of at most 16 (one
-// persistent launch each, in order, sharing the node buffers), gain slot
-// u = TRI16 index of the chunk-local pair, outputs listed per used slot
-// (Qhat+ and the output kernel run over the used slots only).  Workspace:
+// Chunks of one shape that share a persistent launch, at most this many: the
+// launch's f_N, Lambda and Qhat+ grow with its chunks (about 9 MB each).
+constexpr int kPenChunksPerLaunch = 64;
+
+// Plan of the pipelined schedule: the inputs in chunks of at most 16, gain
+// slot u = TRI16 index of the chunk-local pair, outputs listed per used slot
+// (Qhat+ and the output kernel run over the used slots only).  Chunks with
+// the same input count and used slots run in one persistent launch (its node
+// list runs through the chunks one after another); the launches run in order
+// and share the node buffers.  Workspace:
 // descriptors | f_N, Lambda | X node buffers | Pt node buffers | Qhat+ | counters.
 boltz_status build_plan_pencil(const boltz_grid_s* g, const int32_t* pj, const int32_t* pl, int n_pairs,
                                Plan& plan) {
@@ -418,39 +424,60 @@ boltz_status build_plan_pencil(const boltz_grid_s* g, const int32_t* pj, const i
     plan.pen_off[5] = put(T.step_dir.data(), T.step_dir.size() * sizeof(int4));
     plan.pen_off[6] = put(T.step_sel.data(), T.step_sel.size() * sizeof(int4));
     plan.pen_off[7] = put(T.step_w.data(), T.step_w.size() * sizeof(float2));
-    for (int k = 0; k < (int)groups.size(); ++k) {
-        ChunkPlan c;
-        c.inputs = groups[k];
-        std::vector<int> slots;
-        std::array<unsigned, 5> mask{};
+    std::vector<std::vector<int>> slots_of(groups.size());
+    std::vector<std::array<unsigned, 5>> mask_of(groups.size());
+    for (size_t k = 0; k < groups.size(); ++k) {
+        mask_of[k].fill(0u);
         for (int u = 0; u < pc::NSLOT; ++u) {
             if (outs_of[k][u].empty()) continue;
-            slots.push_back(u);
-            mask[u >> 5] |= 1u << (u & 31);
-            c.out_start.push_back((int)c.outs.size());
-            for (int e : outs_of[k][u]) c.outs.push_back(make_int4(e, loc[pj[e]], loc[pl[e]], 0));
+            slots_of[k].push_back(u);
+            mask_of[k][u >> 5] |= 1u << (u & 31);
         }
+    }
+    // launches: chunks of one shape, in the order of their first chunk
+    std::vector<std::vector<int>> launches;
+    for (int k = 0; k < (int)groups.size(); ++k) {
+        int at = -1;
+        for (int j = 0; j < (int)launches.size() && at < 0; ++j) {
+            const int k0 = launches[j][0];
+            if ((int)launches[j].size() < kPenChunksPerLaunch && groups[k0].size() == groups[k].size() &&
+                mask_of[k0] == mask_of[k])
+                at = j;
+        }
+        if (at < 0) {
+            at = (int)launches.size();
+            launches.emplace_back();
+        }
+        launches[at].push_back(k);
+    }
+    for (const auto& ln : launches) {
+        ChunkPlan c;
+        const int nc = (int)groups[ln[0]].size();
+        const std::vector<int>& slots = slots_of[ln[0]];
+        for (int k : ln) c.inputs.insert(c.inputs.end(), groups[k].begin(), groups[k].end());
+        for (int ci = 0; ci < (int)ln.size(); ++ci)
+            for (int u : slots) {
+                c.out_start.push_back((int)c.outs.size());
+                for (int e : outs_of[ln[ci]][u])
+                    c.outs.push_back(make_int4(e, ci * nc + loc[pj[e]], ci * nc + loc[pl[e]], 0));
+            }
         c.out_start.push_back((int)c.outs.size());
-        c.U = (int)slots.size();
+        c.U = (int)(ln.size() * slots.size());
         bool diag = true;
         for (int u : slots) {
             bool on_diagonal = false;
             for (int a = 0; a < pc::NJ; ++a) on_diagonal = on_diagonal || u == pc::tri_slot(a, a);
             diag = diag && on_diagonal;
         }
+        plan.pen_nchunk.push_back((int)ln.size());
         plan.pen_diag.push_back(diag);
         plan.pen_slot_off.push_back(put(slots.data(), slots.size() * sizeof(int)));
-        plan.pen_mask.push_back(mask);
-        if (k == 0) {
-            plan.pen_slots = slots;
-            plan.pen_off[8] = plan.pen_slot_off[0];
-        }
+        plan.pen_mask.push_back(mask_of[ln[0]]);
         plan.max_nc = std::max(plan.max_nc, (int)c.inputs.size());
         plan.max_U = std::max(plan.max_U, c.U);
         plan.chunks.push_back(std::move(c));
     }
     blob.resize(align_up(blob.size(), 16));
-    plan.pen_n_used = plan.max_U;
     plan.nq = g->n_rho;
     size_t off = 0;
     for (auto& c : plan.chunks) {
@@ -482,7 +509,9 @@ boltz_status build_plan_pencil(const boltz_grid_s* g, const int32_t* pj, const i
     plan.off_qstd = w;
     w = align_up(w + size_t(plan.max_U) * pc::HALF * sizeof(float2), 256);
     plan.off_ctr = w;
-    w = align_up(w + size_t(pc::ctr_count(g->n_rho, plan.max_U)) * sizeof(int), 256);
+    int max_nodes = 0;
+    for (int n : plan.pen_nchunk) max_nodes = std::max(max_nodes, n * g->n_rho);
+    w = align_up(w + size_t(pc::ctr_count(max_nodes, plan.max_U)) * sizeof(int), 256);
     plan.off_A = plan.off_P = plan.off_img = w;
     plan.total = w;
     return BOLTZ_OK;
@@ -1620,10 +1649,11 @@ boltz_status run_carleman(boltz_grid_s* g, const float2* spectra, int n_inputs, 
     return BOLTZ_OK;
 }
 
-// One batched evaluation on the pipelined schedule (plan.pencil), chunk by
-// chunk: f_N and Lambda of the chunk's inputs, the persistent kernel of
-// pencil.cuh (shifted fields, sigma-contraction and radial step of every
-// node), then the output kernel over the chunk's used gain slots.
+// One batched evaluation on the pipelined schedule (plan.pencil), launch by
+// launch (one chunk, or several of one shape): f_N and Lambda of the
+// launch's inputs, the persistent kernel of pencil.cuh (shifted fields,
+// sigma-contraction and radial step of every node of every chunk), then the
+// output kernel over the launch's used gain slots.
 boltz_status run_pencil(boltz_grid_s* g, const float2* spectra, float* Q_out, cudaStream_t st) {
     namespace pc = boltz_dev::pencil;
     const Plan& plan = g->last_plan;
@@ -1634,7 +1664,8 @@ boltz_status run_pencil(boltz_grid_s* g, const float2* spectra, float* Q_out, cu
     float* fN = reinterpret_cast<float*>(ws + plan.off_fN);
     for (size_t k = 0; k < plan.chunks.size(); ++k) {
         const ChunkPlan& c = plan.chunks[k];
-        const int nc = (int)c.inputs.size();
+        const int nc = (int)c.inputs.size();          // inputs of the launch (all its chunks)
+        const int n_chunk = plan.pen_nchunk[k];
         const int* d_inputs = reinterpret_cast<const int*>(ws + plan.off_plan + c.off_inputs);
         SynParams sp{};
         sp.spectra = spectra;
@@ -1676,12 +1707,14 @@ boltz_status run_pencil(boltz_grid_s* g, const float2* spectra, float* Q_out, cu
         P.tr.step_dir = reinterpret_cast<const int4*>(blob + plan.pen_off[5]);
         P.tr.step_sel = reinterpret_cast<const int4*>(blob + plan.pen_off[6]);
         P.tr.step_w = reinterpret_cast<const float2*>(blob + plan.pen_off[7]);
-        P.n_c = nc;
+        P.n_c = nc / n_chunk;
         P.M = g->M;
         P.n_rho = g->n_rho;
-        P.n_used = c.U;
-        BZ_CUDA(cudaMemsetAsync(P.ctr, 0, size_t(pc::ctr_count(g->n_rho, c.U)) * sizeof(int), st));
-        const long long items = (long long)g->n_rho * (pc::NLB + pc::tree_items(nc, T.n_grp) + (long long)c.U);
+        P.n_used = c.U / n_chunk;
+        P.n_node = n_chunk * g->n_rho;
+        BZ_CUDA(cudaMemsetAsync(P.ctr, 0, size_t(pc::ctr_count(P.n_node, c.U)) * sizeof(int), st));
+        const long long items =
+            (long long)P.n_node * (pc::NLB + pc::tree_items(P.n_c, T.n_grp) + (long long)P.n_used);
         const bool diag = plan.pen_diag[k];
         const int grid = (int)std::min<long long>(diag ? g->pen_ctas_diag : g->pen_ctas, items);
         {

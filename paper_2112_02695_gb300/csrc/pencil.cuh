@@ -5,10 +5,12 @@
 // (Sec. 2.1: for every radial node q and direction p the shifted fields
 // A_{q,p,j}(v) = g_j,N(v - rho_q sigma_p / 2), their products summed over
 // the directions with the weights w_p, one forward transform per node times
-// the radial multiplier c_q(|k|), accumulated over q) for one chunk of at
-// most 16 inputs and the used ones of their 136 unordered pairs (one launch
-// per chunk; a batch of more inputs is split into chunks on the host).  How
-// it computes it:
+// the radial multiplier c_q(|k|), accumulated over q) for chunks of at most
+// 16 inputs and the used ones of their 136 unordered pairs each.  A batch of
+// more inputs is split into chunks on the host; chunks of one shape (the same
+// input count and used slots) run in one launch, as one list of radial nodes
+// (node q of the launch is node q % n_rho of chunk q / n_rho).  How it
+// computes it:
 //
 // * The phase of a shifted field separates over the axes,
 //   phi(k) = phi_0(k_0; s_0) phi_1(k_1; s_1) phi_2(k_2; s_2), s = rho sigma / 2,
@@ -54,7 +56,7 @@
 // behind long ones and stalls the items that depend on them).  Every dependency
 // points to an item earlier in the list (fused(q) needs all tree(q) and the
 // Pt buffer free; tree(q) needs its X buffer free; radial(q) needs fused(q)
-// and radial(q-1) of its slot), so the lowest unfinished item can always run:
+// and radial(q-1) of its chunk's slot), so the lowest unfinished item can always run:
 // progress needs no co-residency.  The two-stage lags give every dependency a
 // stage of slack.  Each wait is a bounded poll (about one second of device
 // time); a wait that gives up records a timeout in the error word and raises
@@ -142,31 +144,35 @@ struct Tree {
 
 struct Params {
     const float2* spectra;   // [n_inputs][HALF]
-    const int* inputs;       // [n_c]: chunk-local -> global input
+    const int* inputs;       // [n_chunk][n_c]: chunk-local -> global input
     const float2* phase;     // [(n_rho M + 1)][3][N]: (-1)^k exp(-i pi k s_a / L), zero at Nyquist
     const float* ctab;       // [n_rho][SMAX + 1]: c_q(|k|^2) including 1/n
     float2* X;               // [NXB][n_s01][NLB][XBLK]
     float2* Pt;              // [NPB][NSLOT][NKB][PLANE]
-    float2* qhat;            // [n_used][NKB][QBLK]: running Qhat+ sums of the used slots, packed:
+    float2* qhat;            // [n_chunk][n_used][NKB][QBLK]: running Qhat+ sums of the used slots, packed:
                              // [kb][k0][k1][c],
                              // k2 = 4 kb + c, column 0 holding Y = A + i B of the planes k2 = 0, N/2
-    float2* qstd;            // [n_used][HALF]: the final Qhat+ in the standard half-spectrum
+    float2* qstd;            // [n_chunk][n_used][HALF]: the final Qhat+ in the standard half-spectrum
                              // layout, written by the last node's radial items
-    const int* slots;        // [n_used]: slots whose gain is needed
-    unsigned used[5];        // the same slots as a bit set (slot u: bit u % 32 of word u / 32)
+    const int* slots;        // [n_used]: slots whose gain is needed (the same in every chunk)
+    unsigned used[5];        // the same slots as a bit set (slot u: bit u % 32 of word u / 32),
+                             // one set for every chunk of the launch
     int* ctr;                // counters, zeroed before the launch (layout in ctr_*)
     int* err;                // device error word
     Tree tr;
-    int n_c, M, n_rho, n_used;
+    int n_c, M, n_rho, n_used;   // per chunk: inputs, directions, radial nodes, used slots
+    int n_node;                  // radial nodes of the launch: chunks x n_rho (node q of the
+                                 // launch is node q % n_rho of chunk q / n_rho)
 };
 
-// counters: [0] claim, [1] abort, then per node: tree done, fused done,
-// radial done, then per used slot the nodes accumulated into its Qhat+
-__host__ __device__ constexpr int ctr_tree(int n_rho, int q) { return 2 + q; }
-__host__ __device__ constexpr int ctr_fused(int n_rho, int q) { return 2 + n_rho + q; }
-__host__ __device__ constexpr int ctr_radial(int n_rho, int q) { return 2 + 2 * n_rho + q; }
-__host__ __device__ constexpr int ctr_acc(int n_rho, int i) { return 2 + 3 * n_rho + i; }
-__host__ __device__ constexpr int ctr_count(int n_rho, int n_used) { return 2 + 3 * n_rho + n_used; }
+// counters: [0] claim, [1] abort, then per node of the launch: tree done,
+// fused done, radial done, then per used slot of every chunk the nodes
+// accumulated into its Qhat+
+__host__ __device__ constexpr int ctr_tree(int n_node, int q) { return 2 + q; }
+__host__ __device__ constexpr int ctr_fused(int n_node, int q) { return 2 + n_node + q; }
+__host__ __device__ constexpr int ctr_radial(int n_node, int q) { return 2 + 2 * n_node + q; }
+__host__ __device__ constexpr int ctr_acc(int n_node, int i) { return 2 + 3 * n_node + i; }
+__host__ __device__ constexpr int ctr_count(int n_node, int n_slots) { return 2 + 3 * n_node + n_slots; }
 
 // TRI16 slot of the unordered pair (a <= b)
 __host__ __device__ constexpr int tri_slot(int a, int b) { return a * NJ - a * (a - 1) / 2 + (b - a); }
@@ -215,26 +221,32 @@ struct Item {
 };
 
 __host__ __device__ inline int tree_items(int n_c, int n_grp) { return n_c * NKB * n_grp; }
-constexpr int MAX_STAGE = 128 + RLAG + 1;      // stages: n_rho (<= 128) + RLAG, plus the end
 
 // Items of stage s in list order: tree items of node s, fused items of node
 // s - FLAG, radial items of node s - RLAG.
-__host__ __device__ inline void stage_counts(int s, int n_rho, int nT, int nR, int& t, int& f, int& r) {
-    t = (s < n_rho) ? nT : 0;
-    f = (s >= FLAG && s < n_rho + FLAG) ? NLB : 0;
-    r = (s >= RLAG && s < n_rho + RLAG) ? nR : 0;
+__host__ __device__ inline void stage_counts(int s, int n_node, int nT, int nR, int& t, int& f, int& r) {
+    t = (s < n_node) ? nT : 0;
+    f = (s >= FLAG && s < n_node + FLAG) ? NLB : 0;
+    r = (s >= RLAG && s < n_node + RLAG) ? nR : 0;
 }
 
-// Item idx of the stage-ordered list, from the stage offsets (off[s] = first
-// item of stage s).  `stage` is the caller's cursor: its claims increase, so
-// the search resumes where the previous one ended.
-__device__ __noinline__ Item decode_item(const Params& P, const int* off, int& stage, int idx) {
-    const int ns = P.n_rho + RLAG;
-    if (idx >= off[ns]) return {IT_END, 0, 0};
-    while (idx >= off[stage + 1]) ++stage;
+// First item of stage s: every stage has nT tree, NLB fused and nR radial
+// items while its node index is in range, so the offset is a closed form.
+__device__ __forceinline__ int stage_offset(int s, int nn, int nT, int nR) {
+    auto cl = [nn](int v) { return v < 0 ? 0 : (v > nn ? nn : v); };
+    return nT * cl(s) + NLB * cl(s - FLAG) + nR * cl(s - RLAG);
+}
+
+// Item idx of the stage-ordered list.  `stage` is the caller's cursor: its
+// claims increase, so the search resumes where the previous one ended.
+__device__ __noinline__ Item decode_item(const Params& P, int& stage, int idx) {
+    const int nn = P.n_node, nT = tree_items(P.n_c, P.tr.n_grp), nR = P.n_used;
+    const int ns = nn + RLAG;
+    if (idx >= stage_offset(ns, nn, nT, nR)) return {IT_END, 0, 0};
+    while (idx >= stage_offset(stage + 1, nn, nT, nR)) ++stage;
     int t, f, r;
-    stage_counts(stage, P.n_rho, tree_items(P.n_c, P.tr.n_grp), P.n_used, t, f, r);
-    int k = idx - off[stage];
+    stage_counts(stage, nn, nT, nR, t, f, r);
+    int k = idx - stage_offset(stage, nn, nT, nR);
     if (k < t) return {IT_TREE, stage, k};
     k -= t;
     if (k < f) return {IT_FUSED, stage - FLAG, k};
@@ -315,7 +327,6 @@ __device__ __forceinline__ void tmem_wait_ld32(uint32_t (&r)[32]) {
 // Tables of the direction tree, copied to shared memory once per CTA.
 struct TreeSmem {
     int grp[MAX_S + 1], s0_dir[MAX_S], s0_child[MAX_S + 1], s01_dir[MAX_S];
-    int stage_off[MAX_STAGE + 1];
     int4 step_blk[MAX_STEP], step_dir[MAX_STEP], step_sel[MAX_STEP];
     float2 step_w[MAX_STEP];
 };
@@ -334,7 +345,9 @@ __device__ void tree_item(const Params& P, const TreeSmem& ts, int q, int local,
     float2* S0 = reinterpret_cast<float2*>(smem);                  // [N][PRS]: (i0, k1, c)
     float2* ph = reinterpret_cast<float2*>(smem + SM_TPH);         // [rows][N]
     const int k1 = t >> 2, c = t & 3;
-    const float2* __restrict__ src = P.spectra + (size_t)__ldg(&P.inputs[jj]) * HALF + k1 * NH + KB * kb + c;
+    const int ql = q % P.n_rho, ch = q / P.n_rho;                  // node of chunk ch
+    const float2* __restrict__ src =
+        P.spectra + (size_t)__ldg(&P.inputs[ch * P.n_c + jj]) * HALF + k1 * NH + KB * kb + c;
     float2 col[N];
 #pragma unroll
     for (int k0 = 0; k0 < N; ++k0) col[k0] = __ldg(src + k0 * N * NH);
@@ -348,7 +361,7 @@ __device__ void tree_item(const Params& P, const TreeSmem& ts, int q, int local,
         while (i + 1 < i0e && r >= (i + 1 - i0b) + (ts.s0_child[i + 1] - cb0)) ++i;
         const int rr = r - ((i - i0b) + (ts.s0_child[i] - cb0));
         const int dir = rr == 0 ? ts.s0_dir[i] : ts.s01_dir[ts.s0_child[i] + rr - 1];
-        ph[e] = __ldg(&P.phase[((size_t)(q * P.M + dir) * 3 + (rr == 0 ? 0 : 1)) * N + k]);
+        ph[e] = __ldg(&P.phase[((size_t)(ql * P.M + dir) * 3 + (rr == 0 ? 0 : 1)) * N + k]);
     }
     __syncthreads();
     float2* Xn = P.X + (size_t)(q % NXB) * P.tr.n_s01 * NLB * XBLK;
@@ -401,7 +414,7 @@ __device__ __forceinline__ void fused_issue(const Params& P, const TreeSmem& ts,
     const uint32_t bytes = (bl >= 0 ? XBLK * 8 : 0) + (dr >= 0 ? H * 8 : 0);
     mbar_arrive_expect_tx(bar, bytes);
     if (bl >= 0) bulk_g2s(Xs + k * XBLK, Xn + (size_t)bl * NLB * XBLK, XBLK * 8, bar);
-    if (dr >= 0) bulk_g2s(ph2 + k * H, P.phase + ((size_t)(q * P.M + dr) * 3 + 2) * N, H * 8, bar);
+    if (dr >= 0) bulk_g2s(ph2 + k * H, P.phase + ((size_t)((q % P.n_rho) * P.M + dr) * 3 + 2) * N, H * 8, bar);
 }
 
 // Two FP32 lanes in one 64-bit register, and the packed FMA of sm_100+.
@@ -666,15 +679,16 @@ __device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.w
 // Qhat+ copied into shared memory and back in one piece each way.
 __device__ bool radial_item(const Params& P, int q, int ui, unsigned char* smem, uint64_t* bars, uint32_t& par) {
     const int t = threadIdx.x;
+    const int ql = q % P.n_rho, gi = (q / P.n_rho) * P.n_used + ui;   // node of the chunk, slot of the launch
     const int u = __ldg(&P.slots[ui]);
     float2* S = reinterpret_cast<float2*>(smem);
     float2* Qs = reinterpret_cast<float2*>(smem + SM_QS);          // [k0][k1][c]
-    const bool first = (q == 0);
-    const float* __restrict__ ct = P.ctab + (size_t)q * (SMAX + 1);
+    const bool first = (ql == 0);
+    const float* __restrict__ ct = P.ctab + (size_t)ql * (SMAX + 1);
     const int c = t & 3, k1 = t >> 2;
     const int b = wrapk(k1, N), k1m = (N - k1) % N;
     const float2* src0 = P.Pt + (size_t)((q % NPB) * NSLOT + u) * NKB * PLANE;
-    float2* qblk0 = P.qhat + (size_t)ui * NKB * QBLK;
+    float2* qblk0 = P.qhat + (size_t)gi * NKB * QBLK;
     // the plane (bars[2]) and the running-sum block (bars[3]) of a column block travel
     // separately: each is copied in as soon as its buffer is free, the plane of the
     // next block while this block accumulates, the sums while the next plane transforms
@@ -756,7 +770,7 @@ __device__ bool radial_item(const Params& P, int q, int ui, unsigned char* smem,
             if (!first) v = make_float2(v.x + o->x, v.y + o->y);
             *o = v;
         }
-        if (q < P.n_rho - 1) {
+        if (ql < P.n_rho - 1) {
             fence_proxy_async_smem();
             __syncthreads();                                    // Qs complete, S read for the last time
             if (t == 0) {
@@ -780,7 +794,7 @@ __device__ bool radial_item(const Params& P, int q, int ui, unsigned char* smem,
                 mbar_arrive_expect_tx(&bars[2], PLANE * 8);
                 bulk_g2s(S, src0 + (size_t)(kb + 1) * PLANE, PLANE * 8, &bars[2]);
             }
-            float2* qs = P.qstd + (size_t)ui * HALF;
+            float2* qs = P.qstd + (size_t)gi * HALF;
 #pragma unroll 4
             for (int k0 = 0; k0 < N; ++k0) {
                 const float2 y = Qs[(k0 * N + k1) * KB + c];
@@ -814,12 +828,12 @@ __device__ bool radial_item(const Params& P, int q, int ui, unsigned char* smem,
 // is counted.
 __device__ __forceinline__ void publish(const Params& P, const Item& it) {
     fence_proxy_async_global();
-    const int nr = P.n_rho;
-    if (it.kind == IT_TREE) red_release_add(P.ctr + ctr_tree(nr, it.q), 1);
-    else if (it.kind == IT_FUSED) red_release_add(P.ctr + ctr_fused(nr, it.q), 1);
+    const int nn = P.n_node;
+    if (it.kind == IT_TREE) red_release_add(P.ctr + ctr_tree(nn, it.q), 1);
+    else if (it.kind == IT_FUSED) red_release_add(P.ctr + ctr_fused(nn, it.q), 1);
     else {
-        red_release_add(P.ctr + ctr_acc(nr, it.local), 1);
-        red_release_add(P.ctr + ctr_radial(nr, it.q), 1);
+        red_release_add(P.ctr + ctr_acc(nn, (it.q / P.n_rho) * P.n_used + it.local), 1);
+        red_release_add(P.ctr + ctr_radial(nn, it.q), 1);
     }
 }
 
@@ -833,7 +847,6 @@ __global__ void __launch_bounds__(NT, CTAS_PER_SM) k_pencil(Params P) {
     __shared__ int s_ok;
     const int t = threadIdx.x, warp = t >> 5;
     const int nT = tree_items(P.n_c, P.tr.n_grp), nR = P.n_used;
-    const int nstage = P.n_rho + RLAG;
     // direction tree tables and the list's stage offsets into shared memory
     for (int e = t; e <= P.tr.n_grp; e += NT) ts.grp[e] = __ldg(&P.tr.grp[e]);
     for (int e = t; e < P.tr.n_s0; e += NT) ts.s0_dir[e] = __ldg(&P.tr.s0_dir[e]);
@@ -847,20 +860,12 @@ __global__ void __launch_bounds__(NT, CTAS_PER_SM) k_pencil(Params P) {
     }
     int stage = 0;                                     // thread 0: decoding cursor
     if (t == 0) {
-        int off = 0;
-        for (int st = 0; st < nstage; ++st) {
-            ts.stage_off[st] = off;
-            int nt, nf, nr;
-            stage_counts(st, P.n_rho, nT, nR, nt, nf, nr);
-            off += nt + nf + nr;
-        }
-        ts.stage_off[nstage] = off;
         mbar_init(&bars[0], 4);                        // fused stages: one arrival per warp
         mbar_init(&bars[1], 4);
         mbar_init(&bars[2], 1);                        // radial: Pt planes
         mbar_init(&bars[3], 1);                        // radial: running-sum blocks
         mbar_init_fence();
-        s_it[0] = decode_item(P, ts.stage_off, stage, atomicAdd(P.ctr, 1));
+        s_it[0] = decode_item(P, stage, atomicAdd(P.ctr, 1));
     }
     if (!DIAG && warp == 0) tc_alloc<TMEM_COLS>(&tmem_base);
     tc_fence_before_sync();
@@ -880,15 +885,17 @@ __global__ void __launch_bounds__(NT, CTAS_PER_SM) k_pencil(Params P) {
         if (t == 0) {
             // the next item is claimed now; it is decoded and stored once this item is done
             next = atomicAdd(P.ctr, 1);
-            const int nr = P.n_rho;
+            const int nn = P.n_node;
             bool ok = true;
             if (it.kind == IT_TREE && it.q >= NXB)
-                ok = wait_at_least(P.ctr + ctr_fused(nr, it.q - NXB), NLB, nullptr, 0, abort_flag);
+                ok = wait_at_least(P.ctr + ctr_fused(nn, it.q - NXB), NLB, nullptr, 0, abort_flag);
             else if (it.kind == IT_FUSED)
-                ok = wait_at_least(P.ctr + ctr_tree(nr, it.q), nT,
-                                   it.q >= NPB ? P.ctr + ctr_radial(nr, it.q - NPB) : nullptr, nR, abort_flag);
-            else if (it.kind == IT_RADIAL)
-                ok = wait_at_least(P.ctr + ctr_fused(nr, it.q), NLB, P.ctr + ctr_acc(nr, it.local), it.q, abort_flag);
+                ok = wait_at_least(P.ctr + ctr_tree(nn, it.q), nT,
+                                   it.q >= NPB ? P.ctr + ctr_radial(nn, it.q - NPB) : nullptr, nR, abort_flag);
+            else if (it.kind == IT_RADIAL)   // the slot's sums hold the chunk's earlier nodes
+                ok = wait_at_least(P.ctr + ctr_fused(nn, it.q), NLB,
+                                   P.ctr + ctr_acc(nn, (it.q / P.n_rho) * P.n_used + it.local), it.q % P.n_rho,
+                                   abort_flag);
             if (!ok && *reinterpret_cast<volatile int*>(abort_flag) == 0) {
                 atomicOr(P.err, kErrTimeout);
                 atomicExch(abort_flag, 1);
@@ -908,7 +915,7 @@ __global__ void __launch_bounds__(NT, CTAS_PER_SM) k_pencil(Params P) {
                 atomicExch(abort_flag, 1);
             }
         }
-        if (t == 0) s_it[(i + 1) & 1] = decode_item(P, ts.stage_off, stage, next);
+        if (t == 0) s_it[(i + 1) & 1] = decode_item(P, stage, next);
         __syncthreads();                               // every thread's writes of the item are done
         prev = it;
     }

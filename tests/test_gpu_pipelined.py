@@ -99,8 +99,8 @@ def test_pipelined_is_bitwise_reproducible(B):
 
 def test_pipelined_several_chunks_against_oracle(B):
     """40 inputs whose pairs connect groups of at most 16 (diagonal cells, a few
-    pairs within groups): the pipelined schedule runs one persistent launch per
-    chunk of at most 16 inputs, each chunk's gain slots only."""
+    pairs within groups): chunks of at most 16 inputs, each with its own gain
+    slots; here the three chunks differ in shape, so each has a launch."""
     cfg = (32, 3, 8.0, 8.0, 1.0, 2, 14)
     f = as_fp32(W.random_fields(32, 3, 8.0, 40, seed=801))
     pairs = [(x, x) for x in range(40)] + [(0, 1), (1, 0), (5, 7), (30, 31), (39, 38), (12, 12)]
@@ -122,3 +122,36 @@ def test_pipelined_falls_back_for_a_group_of_seventeen(B):
     assert launches["pipeline"] == 0 and launches["shift"] > 0
     _, Qo, s = oracle_collide(cfg, f, pairs)
     assert rel_err(Qg, Qo, s).max() < TOL
+
+
+@pytest.mark.parametrize("n_rho,diag", [(1, True), (3, True), (3, False)])
+def test_pipelined_chunks_of_one_shape_share_a_launch(B, n_rho, diag):
+    """48 inputs in three chunks of one shape (diagonal pairs only, or pairs
+    (2i, 2i+1) both ways plus the diagonal): one persistent launch runs the
+    node lists of all three chunks one after another, so with N_rho = 3 the
+    node buffers are reused across chunk boundaries."""
+    cfg = (32, 3, 8.0, 8.0, 1.0, n_rho, 14)
+    f = as_fp32(W.random_fields(32, 3, 8.0, 48, seed=803 + n_rho))
+    if diag:
+        pairs = [(x, x) for x in range(48)]
+    else:
+        pairs = [p for i in range(24) for p in ((2 * i, 2 * i + 1), (2 * i + 1, 2 * i), (2 * i, 2 * i))]
+    launches = {}
+    Qg = gpu_collide(B, cfg, f, pairs, launches=launches)
+    assert launches["pipeline"] == 1 and launches["shift"] == 0
+    _, Qo, s = oracle_collide(cfg, f, pairs)
+    assert rel_err(Qg, Qo, s).max() < TOL
+
+
+def test_pipelined_caps_the_chunks_of_a_launch(B):
+    """1056 diagonal pairs: 66 chunks of one shape, at most 64 in a launch, so
+    two launches; the result equals the node-block schedule's."""
+    cfg = (32, 3, 8.0, 8.0, 1.0, 1, 6)
+    f = as_fp32(W.random_fields(32, 3, 8.0, 1056, seed=804))
+    pairs = [(x, x) for x in range(1056)]
+    lp, ln = {}, {}
+    Qp = gpu_collide(B, cfg, f, pairs, launches=lp)
+    Qn = gpu_collide(B, cfg, f, pairs, schedule=1, launches=ln)
+    assert lp["pipeline"] == 2 and ln["pipeline"] == 0
+    scale = np.max(np.abs(Qn), axis=(1, 2, 3))
+    assert (np.max(np.abs(Qp - Qn), axis=(1, 2, 3)) / scale).max() < TOL
