@@ -2136,7 +2136,6 @@ boltz_status ensure_lowrank_attrs() {
     std::lock_guard<std::mutex> lock(mu);
     if (done.count(dev)) return BOLTZ_OK;
     if (set_smem(k_chol_f64, kCholSmem) != cudaSuccess || set_smem(k_svd_jacobi_f64, kSvdSmem) != cudaSuccess ||
-        set_smem(k_qr_small_f64, kQrSmallSmem) != cudaSuccess ||
         set_smem(k_lstep_collision<64>, lstep_smem<64>()) != cudaSuccess ||
         set_smem(k_lr_coupling, kCouplingSmem) != cudaSuccess) {
         (void)cudaGetLastError();
@@ -2149,7 +2148,8 @@ boltz_status ensure_lowrank_attrs() {
 int qr_slices(int n) { return std::max(1, std::min(512, n / 128)); }
 
 size_t qr_workspace_bytes(int r, int n) {
-    return align_up(size_t(qr_slices(n) + 2) * r * r * sizeof(double), 256);
+    return std::max(align_up(size_t(qr_slices(n) + 2) * r * r * sizeof(double), 256),
+                    align_up(qr_spread_bytes(), 256));
 }
 
 template <int RMAX>
@@ -2165,6 +2165,33 @@ void launch_qr(const double* W, int r, int n, double w, double* Y, double* R, ch
     k_gram_f64<<<ns, kLrThreads, 0, st>>>(Y, r, n, ns, part);
     k_chol_f64<<<1, kCholThreads, kCholSmem, st>>>(part, ns, r, w, R1, R, Rinv, info);
     k_apply_rinv_f64<RMAX><<<grid, kLrThreads, 0, st>>>(Y, Rinv, r, n, Y);
+}
+
+// Cholesky-QR2 of boltz_qr_f64.  The spread kernels' tickets are left at zero
+// by every call; zero_tickets clears them first (a workspace of unknown
+// contents).
+boltz_status qr_f64_launch(const double* W, int r, int n, double w, double* Y, double* R, char* ws, int* info,
+                           cudaStream_t st, bool zero_tickets) {
+    boltz_status s = ensure_lowrank_attrs();
+    if (s != BOLTZ_OK) return s;
+    BZ_CUDA(cudaMemsetAsync(info, 0, sizeof(int), st));
+    if (r <= kQrSpreadR && n <= kQrSpreadMaxN) {      // Gram sums and applications over up to 152 CTAs
+        const int rows = qr_spread_rows(n), grid = (n + rows - 1) / rows;
+        double* wsd = reinterpret_cast<double*>(ws);
+        if (zero_tickets)
+            BZ_CUDA(cudaMemsetAsync(ws + qr_spread_ticket_offset(), 0, 2 * sizeof(unsigned), st));
+        k_qr_spread_f64<0><<<grid, kQrSpreadThreads, 0, st>>>(W, r, n, w, rows, Y, R, wsd, info);
+        k_qr_spread_f64<1><<<grid, kQrSpreadThreads, 0, st>>>(W, r, n, w, rows, Y, R, wsd, info);
+        k_qr_spread_apply<<<(n + kQrSpreadThreads - 1) / kQrSpreadThreads, kQrSpreadThreads, 0, st>>>(Y, r, n, wsd);
+    } else if (r <= 16) {
+        launch_qr<16>(W, r, n, w, Y, R, ws, info, st);
+    } else if (r <= 32) {
+        launch_qr<32>(W, r, n, w, Y, R, ws, info, st);
+    } else {
+        launch_qr<64>(W, r, n, w, Y, R, ws, info, st);
+    }
+    BZ_CUDA(cudaGetLastError());
+    return BOLTZ_OK;
 }
 
 }  // namespace
@@ -2985,18 +3012,8 @@ boltz_status boltz_qr_f64(const double* W, int r, int n, double w, double* Y, do
                           int* info, void* stream) {
     if (r < 1 || r > 64 || n < r || !(w > 0) || !std::isfinite(w) || !W || !Y || !R || !workspace || !info)
         return BOLTZ_EINVAL;
-    boltz_status s = ensure_lowrank_attrs();
-    if (s != BOLTZ_OK) return s;
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    BZ_CUDA(cudaMemsetAsync(info, 0, sizeof(int), st));
-    char* ws = static_cast<char*>(workspace);
-    if (r <= kQrSmallR && n <= kQrSmallN)            // one CTA holds the whole block
-        k_qr_small_f64<<<1, kQrSmallThreads, size_t(r) * n * sizeof(double), st>>>(W, r, n, w, Y, R, info);
-    else if (r <= 16) launch_qr<16>(W, r, n, w, Y, R, ws, info, st);
-    else if (r <= 32) launch_qr<32>(W, r, n, w, Y, R, ws, info, st);
-    else launch_qr<64>(W, r, n, w, Y, R, ws, info, st);
-    BZ_CUDA(cudaGetLastError());
-    return BOLTZ_OK;
+    return qr_f64_launch(W, r, n, w, Y, R, static_cast<char*>(workspace), info,
+                         reinterpret_cast<cudaStream_t>(stream), true);
 }
 
 boltz_status boltz_svd_truncate_f64(const double* S, int r, double drop_tol, double* U, double* sigma, double* Q,
@@ -3007,7 +3024,8 @@ boltz_status boltz_svd_truncate_f64(const double* S, int r, double drop_tol, dou
     boltz_status s = ensure_lowrank_attrs();
     if (s != BOLTZ_OK) return s;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    k_svd_jacobi_f64<<<1, 1024, kSvdSmem, st>>>(S, r, drop_tol, U, sigma, Q, r_keep, info);
+    if (r <= kSvdSmallR) k_svd_small_f64<<<1, 32, 0, st>>>(S, r, drop_tol, U, sigma, Q, r_keep, info);
+    else k_svd_jacobi_f64<<<1, 1024, kSvdSmem, st>>>(S, r, drop_tol, U, sigma, Q, r_keep, info);
     BZ_CUDA(cudaGetLastError());
     return BOLTZ_OK;
 }
@@ -3053,7 +3071,7 @@ struct boltz_shock_s {
     void* qr_ws = nullptr;
     int* d_int = nullptr;                 // [0] QR info (K), [1] QR info (L), [2] r_keep, [3] SVD info,
                                           // [4] skip bits of a replayed step (1: a boundary vector not
-                                          // kept, 2: a QR or the rank failed)
+                                          // kept, 2: a QR or the rank failed), [8] k_sh_change's ticket
     double* d_tol = nullptr;              // drop_tol of a replayed step
     // replayed steps: one CUDA graph per (rank, X, S, V, dt) seen twice, both boundary
     // vectors kept; h_pin: [0] drop_tol, [1..2] d_int[0..4] read back, [3] the step's err
@@ -3137,6 +3155,11 @@ boltz_status boltz_shock_create(boltz_grid g, int n_x, double L_x, const double*
     for (auto& pt : parts) {
         *pt.first = s->mem + off;
         off = align_up(off + pt.second, 256);
+    }
+    // the tickets of the spread QR and of k_sh_change start at zero (each launch leaves them so)
+    if (cudaMemset(s->d_int, 0, 64) != cudaSuccess || cudaMemset(s->qr_ws, 0, qr_bytes) != cudaSuccess) {
+        boltz_shock_destroy(s);
+        return BOLTZ_ECUDA;
     }
     // inflow Maxwellians and the v_1 coordinate of every grid point (axis 0 is v_1)
     std::vector<double> v1(nv);
@@ -3243,7 +3266,9 @@ boltz_status lr_core(boltz_shock s, const double* X, const double* S, int r, int
     if ((rs = boltz_kstep_collision(s->T32, rh, s->K32, nx, s->C32, stream)) != BOLTZ_OK) return rs;
     k_sh_kupdate<<<sh_grid((size_t)rh * nx), T, 0, st>>>(s->K, s->C32, s->Ap, s->Am, s->gL, s->gR, rh, nx, dt, s->dx,
                                                          s->K1);
-    if ((rs = boltz_qr_f64(s->K1, rh, nx, s->dx, s->X1, s->S1, s->qr_ws, s->d_int, stream)) != BOLTZ_OK) return rs;
+    if ((rs = qr_f64_launch(s->K1, rh, nx, s->dx, s->X1, s->S1, static_cast<char*>(s->qr_ws), s->d_int, st,
+                            false)) != BOLTZ_OK)
+        return rs;
     // 2. S-step (Sec. 2.4 S-step): transport through the updated K, collision term with S1
     sh_ghosts(s, s->K1, rh, st);
     k_sh_xgram<<<dim3(rh, rh), T, 0, st>>>(s->X1, s->K1, s->gL, s->gR, rh, nx, s->dx, s->Bp, s->Bm);
@@ -3260,17 +3285,21 @@ boltz_status lr_core(boltz_shock s, const double* X, const double* S, int r, int
     if ((rs = boltz_lowrank_coupling(s->E32, s->S32, rh, nullptr, s->Cs32, nullptr, stream)) != BOLTZ_OK) return rs;
     if ((rs = boltz_lstep_collision(s->Q32, rh, s->Cs32, nv, s->G32, stream)) != BOLTZ_OK) return rs;
     k_sh_lupdate<<<sh_grid((size_t)rh * nv), T, 0, st>>>(s->L, s->Vh, s->v1, s->Bp, s->Bm, s->G32, rh, nv, dt, s->L1);
-    if ((rs = boltz_qr_f64(s->L1, rh, nv, s->wv, s->Vn, s->R, s->qr_ws, s->d_int + 1, stream)) != BOLTZ_OK) return rs;
+    if ((rs = qr_f64_launch(s->L1, rh, nv, s->wv, s->Vn, s->R, static_cast<char*>(s->qr_ws), s->d_int + 1, st,
+                            false)) != BOLTZ_OK)
+        return rs;
     k_sh_transpose<<<1, T, 0, st>>>(s->R, rh, rh, s->Sn);          // L_i = sum_j R_ji V'_j
     // change of f over the step from the increments (Sec. 5.1), before the drop
-    k_sh_dgram<true><<<rh, T, 0, st>>>(nullptr, s->K1, s->K, rh, nx, s->dx, s->nk);
-    k_sh_dgram<true><<<rh, T, 0, st>>>(nullptr, s->L1, s->L, rh, nv, s->wv, s->nl);
-    k_sh_dgram<false><<<dim3(rh, rh), T, 0, st>>>(s->X1, s->K1, s->K, rh, nx, s->dx, s->Pk);
-    k_sh_dgram<false><<<dim3(rh, rh), T, 0, st>>>(s->Vh, s->L1, s->L, rh, nv, s->wv, s->Gv);
-    k_sh_err<<<1, T, 0, st>>>(s->nk, s->nl, s->Pk, s->Gv, s->S1, s->S2, rh, s->errd);
+    k_sh_change<<<2 * rh + 2 * rh * rh, T, 0, st>>>(s->K1, s->K, s->X1, s->L1, s->L, s->Vh, rh, nx, nv, s->dx, s->wv,
+                                                   s->S1, s->S2, s->nk, s->nl, s->Pk, s->Gv,
+                                                   reinterpret_cast<unsigned*>(s->d_int + 8), s->errd);
     // 4. drop (Sec. 3.2): SVD of S, keep sigma >= drop_tol
     if ((rs = ensure_lowrank_attrs()) != BOLTZ_OK) return rs;
-    k_svd_jacobi_f64<<<1, 1024, kSvdSmem, st>>>(s->Sn, rh, drop_tol, s->U, s->sig, s->Qm, s->d_int + 2, s->d_int + 3,
+    if (rh <= kSvdSmallR)
+        k_svd_small_f64<<<1, 32, 0, st>>>(s->Sn, rh, drop_tol, s->U, s->sig, s->Qm, s->d_int + 2, s->d_int + 3,
+                                          drop_tol_dev);
+    else
+        k_svd_jacobi_f64<<<1, 1024, kSvdSmem, st>>>(s->Sn, rh, drop_tol, s->U, s->sig, s->Qm, s->d_int + 2, s->d_int + 3,
                                                 drop_tol_dev);
     BZ_CUDA(cudaGetLastError());
     return BOLTZ_OK;
@@ -3297,16 +3326,36 @@ void lr_rotate(boltz_shock s, double* X, double* S, double* V, int rh, int rk, c
 
 // Step 0, adding the boundary basis (Sec. 3.1): V_hat = [V; f_L, f_R
 // orthonormalised against V by Gram-Schmidt, twice].  KEEP_ALL (a replayed
-// step): both are appended and k_sh_keep_check records on the device whether
-// that was right; otherwise a vector keeping less than 1e-10 of its norm lies
-// in span(V) already and is not appended (it would carry no weight and make
-// the K-step QR singular), a decision read back on the host.  Returns rh.
+// step): both are appended and the device records whether that was right;
+// otherwise a vector keeping less than 1e-10 of its norm lies in span(V)
+// already and is not appended (it would carry no weight and make the K-step
+// QR singular), a decision read back on the host.  Velocity grids of at most
+// 4096 points run the whole augmentation in one CTA (k_sh_augment), larger
+// ones as a chain of dot, subtract and normalise kernels.  Returns rh.
 template <bool KEEP_ALL>
 boltz_status lr_append(boltz_shock s, const double* V, int r, int* rh_out, cudaStream_t st) {
     using namespace boltz_dev;
     const int T = kShT, nv = s->n_v;
     BZ_CUDA(cudaMemcpyAsync(s->Vh, V, (size_t)r * nv * 8, cudaMemcpyDeviceToDevice, st));
     int rh = r;
+    if (nv <= kAugThreads * kAugEPT && r + s->rb <= kAugR && s->rb <= 2) {
+        // one CTA per call: both vectors at once when the step assumes both kept
+        if constexpr (KEEP_ALL) {
+            k_sh_augment<<<1, kAugThreads, 0, st>>>(s->Vh, r, nv, s->wv, s->fL, s->fR, s->rb, s->nrm, s->d_int + 4);
+            *rh_out = r + s->rb;
+            return BOLTZ_OK;
+        }
+        for (int k = 0; k < s->rb; ++k) {
+            k_sh_augment<<<1, kAugThreads, 0, st>>>(s->Vh, rh, nv, s->wv, k == 0 ? s->fL : s->fR, nullptr, 1,
+                                                    s->nrm, nullptr);
+            double hn[2];
+            BZ_CUDA(cudaMemcpyAsync(hn, s->nrm, sizeof(hn), cudaMemcpyDeviceToHost, st));
+            BZ_CUDA(cudaStreamSynchronize(st));
+            if (hn[1] > 1e-20 * hn[0]) ++rh;
+        }
+        *rh_out = rh;
+        return BOLTZ_OK;
+    }
     for (int k = 0; k < s->rb; ++k) {
         double* b = s->Vh + (size_t)rh * nv;
         const double* src = k == 0 ? s->fL : s->fR;

@@ -10,7 +10,8 @@
 //                       Cholesky factor, triangular solve, done twice)
 //   k_svd_jacobi_f64    S = U Sigma Q^T by one-sided (Hestenes) Jacobi rotations
 //                       in round-robin pair order, singular values sorted
-//                       descending; r' = #{sigma >= drop_tol}               (FP64)
+//                       descending; r' = #{sigma >= drop_tol}               (FP64;
+//                       k_svd_small_f64: the same in one warp for r <= 16)
 //   k_rotate_f64        X_bar_k = sum_i X_i U_ik, k < r'                    (FP64)
 #pragma once
 
@@ -324,106 +325,189 @@ __global__ void __launch_bounds__(kLrThreads) k_apply_rinv_f64(const double* W, 
     }
 }
 
-// ---------------------------------------------------------------- Cholesky-QR2, one CTA (FP64)
-// The same factorisation for small blocks (r <= kQrSmallR rows of n <=
-// kQrSmallN entries, e.g. the K and L factors of a low-rank step): W staged
-// in shared memory once, both passes (Gram, Cholesky, R^-1, apply) in one
-// CTA, one warp per Gram entry with lanes over the entries in a fixed order.
-// Same outputs and failure convention as the multi-kernel path.
-constexpr int kQrSmallR = 8, kQrSmallN = 2048, kQrSmallThreads = 1024;
-constexpr size_t kQrSmallSmem = size_t(kQrSmallR) * kQrSmallN * sizeof(double);
+// ---------------------------------------------------------------- Cholesky-QR2 over many CTAs (FP64)
+// The same factorisation for r <= kQrSpreadR rows of n <= kQrSpreadMaxN
+// entries (e.g. the K and L factors of a low-rank step).  FP64 issues at a
+// small fraction of the FP32 rate on this GPU, so the Gram sums and the R^-1
+// applications are spread over up to 152 CTAs (a block of at most 256
+// entries each), and the small factorisations run in whichever CTA finishes
+// its block last (a ticket counter: nothing waits):
+//   pass 0: partial Gram of W; last CTA: G = w sum of the partials in CTA
+//           order, G = R1^T R1, X1 = R1^-1;
+//   pass 1: W X1 written to Y, its partial Gram; last CTA: R2, X2 = R2^-1,
+//           R = R2 R1;
+//   then Y <- Y X2 (k_qr_spread_apply).
+// A Cholesky factorisation that meets a pivot d <= 0 records k + 1 in info
+// (the first failure) and writes NaN to R and to the inverse, so that Y
+// comes out NaN, as on the multi-kernel path.
+constexpr int kQrSpreadR = 16, kQrSpreadThreads = 256, kQrSpreadRows = 256, kQrSpreadCtas = 152;
+constexpr int kQrSpreadMaxN = kQrSpreadCtas * kQrSpreadRows;
+constexpr int kQrSpreadPairs = kQrSpreadR * (kQrSpreadR + 1) / 2;
 
-__global__ void __launch_bounds__(kQrSmallThreads) k_qr_small_f64(const double* __restrict__ W, int r, int n, double w,
-                                                                double* __restrict__ Y, double* __restrict__ R,
-                                                                int* __restrict__ info) {
-    extern __shared__ double qs_smem[];
-    double* Ws = qs_smem;                                  // [r][n]
-    __shared__ double G[kQrSmallR * kQrSmallR], Rs[kQrSmallR * kQrSmallR], Xs[kQrSmallR * kQrSmallR],
-        R1[kQrSmallR * kQrSmallR];
-    __shared__ int bad;
-    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    constexpr int NW = kQrSmallThreads / 32;
-    for (int e = t; e < r * n; e += kQrSmallThreads) Ws[e] = W[e];
-    if (t == 0) bad = 0;
-    __syncthreads();
-    for (int pass = 0; pass < 2; ++pass) {
-        // G = w W W^T, entry (a, b) by warp e: lanes over v, shuffle tree
-        for (int e = warp; e < r * r; e += NW) {
-            const int a = e / r, b = e % r;
-            double g = 0.0;
-            if (a <= b) {
-                for (int v = lane; v < n; v += 32) g = fma(Ws[a * n + v], Ws[b * n + v], g);
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) g += __shfl_down_sync(0xffffffffu, g, o);
-            }
-            if (lane == 0 && a <= b) {
-                G[a * r + b] = w * g;
-                G[b * r + a] = w * g;
-            }
-            if (lane == 0) Rs[e] = 0.0;
+// entries per CTA: at least 16, so that small blocks use few CTAs
+__host__ __device__ inline int qr_spread_rows(int n) {
+    const int rows = (n + kQrSpreadCtas - 1) / kQrSpreadCtas;
+    return rows < 16 ? 16 : rows;
+}
+
+// workspace: partial Grams [ctas][kQrSpreadPairs], X1, X2, R1 [16 * 16] each, two tickets
+__host__ __device__ constexpr size_t qr_spread_ticket_offset() {
+    return (size_t(kQrSpreadCtas) * kQrSpreadPairs + 3 * kQrSpreadR * kQrSpreadR) * sizeof(double);
+}
+__host__ __device__ constexpr size_t qr_spread_bytes() { return qr_spread_ticket_offset() + 64; }
+
+// G = R^T R (R upper, r <= 32) and X = R^-1 by one warp, lane j owning column
+// j; returns 0 or the 1-based index of the first pivot that is not positive.
+__device__ inline int chol_inv_warp(const double* G, int r, double* Rs, double* Xs, double* Dinv) {
+    const int lane = threadIdx.x & 31;
+    for (int e = lane; e < r * r; e += 32) {
+        Rs[e] = 0.0;
+        Xs[e] = 0.0;
+    }
+    __syncwarp();
+    for (int k = 0; k < r; ++k) {
+        double a = 0.0;
+        if (lane >= k && lane < r) {
+            a = G[k * r + lane];
+            for (int i = 0; i < k; ++i) a = fma(-Rs[i * r + k], Rs[i * r + lane], a);
         }
-        __syncthreads();
-        if (t == 0) {                                          // G = R^T R, R upper
-            for (int k = 0; k < r && !bad; ++k) {
-                double d = G[k * r + k];
-                for (int i = 0; i < k; ++i) d -= Rs[i * r + k] * Rs[i * r + k];
-                if (!(d > 0.0)) {
-                    bad = k + 1;
-                    break;
-                }
-                Rs[k * r + k] = sqrt(d);
-                for (int j = k + 1; j < r; ++j) {
-                    double a = G[k * r + j];
-                    for (int i = 0; i < k; ++i) a -= Rs[i * r + k] * Rs[i * r + j];
-                    Rs[k * r + j] = a / Rs[k * r + k];
-                }
-            }
+        const double d = __shfl_sync(0xffffffffu, a, k);
+        if (!(d > 0.0)) return k + 1;                      // the same value in every lane
+        const double inv = rsqrt(d);
+        if (lane >= k && lane < r) Rs[k * r + lane] = lane == k ? d * inv : a * inv;
+        if (lane == 0) Dinv[k] = inv;
+        __syncwarp();
+    }
+    if (lane < r) {                                        // column j of R^-1, bottom up
+        const int j = lane;
+        for (int i = j; i >= 0; --i) {
+            double a = i == j ? 1.0 : 0.0;
+            for (int k = i + 1; k <= j; ++k) a = fma(-Rs[i * r + k], Xs[k * r + j], a);
+            Xs[i * r + j] = a * Dinv[i];
         }
-        __syncthreads();
-        if (bad) {
-            if (t == 0 && *info == 0) *info = bad;
-            const double nan = __longlong_as_double(0x7ff8000000000000ll);
-            for (int e = t; e < r * r; e += kQrSmallThreads) R[e] = nan;
-            for (int e = t; e < r * n; e += kQrSmallThreads) Y[e] = nan;
-            return;
-        }
-        for (int j = t; j < r; j += kQrSmallThreads) {         // R X = I, one column per thread
-            for (int i = r - 1; i >= 0; --i) {
-                double a = (i == j) ? 1.0 : 0.0;
-                for (int k = i + 1; k <= j; ++k) a -= Rs[i * r + k] * Xs[k * r + j];
-                Xs[i * r + j] = (i <= j) ? a / Rs[i * r + i] : 0.0;
-            }
-        }
-        __syncthreads();
-        // W <- W R^-1 in place: each thread reads its entries' r values first
-        for (int v = t; v < n; v += kQrSmallThreads) {
-            double x[kQrSmallR];
-#pragma unroll
-            for (int i = 0; i < kQrSmallR; ++i) x[i] = i < r ? Ws[i * n + v] : 0.0;
-#pragma unroll
-            for (int k = 0; k < kQrSmallR; ++k) {
-                if (k >= r) break;
-                double y = 0.0;
-#pragma unroll
-                for (int i = 0; i < kQrSmallR; ++i)
-                    if (i <= k) y = fma(x[i], Xs[i * r + k], y);
-                Ws[k * n + v] = y;
-            }
-        }
-        // R of the two passes: R = R2 R1
-        for (int e = t; e < r * r; e += kQrSmallThreads) {
-            if (pass == 0) {
-                R1[e] = Rs[e];
-            } else {
-                const int i = e / r, j = e % r;
-                double o = 0.0;
-                for (int k = i; k <= j; ++k) o += Rs[i * r + k] * R1[k * r + j];
-                R[e] = o;
-            }
-        }
+    }
+    __syncwarp();
+    return 0;
+}
+
+template <int PASS>
+__global__ void __launch_bounds__(kQrSpreadThreads) k_qr_spread_f64(const double* W, int r, int n, double w, int rows,
+                                                                   double* Y, double* __restrict__ R,
+                                                                   double* __restrict__ ws, int* __restrict__ info) {
+    __shared__ double Ws[kQrSpreadR * kQrSpreadRows];     // this CTA's entries, [row i][entry]
+    __shared__ double Xin[kQrSpreadR * kQrSpreadR];
+    __shared__ double G[kQrSpreadR * kQrSpreadR], Rs[kQrSpreadR * kQrSpreadR], Xs[kQrSpreadR * kQrSpreadR];
+    __shared__ double Dinv[kQrSpreadR];
+    __shared__ int last;
+    double* part = ws;
+    double* X1 = ws + size_t(kQrSpreadCtas) * kQrSpreadPairs;
+    double* X2 = X1 + kQrSpreadR * kQrSpreadR;
+    double* R1 = X2 + kQrSpreadR * kQrSpreadR;
+    unsigned* ticket = reinterpret_cast<unsigned*>(reinterpret_cast<char*>(ws) + qr_spread_ticket_offset());
+    const int t = threadIdx.x, v0 = blockIdx.x * rows, nr = min(rows, n - v0);
+    const int npairs = r * (r + 1) / 2;
+    if (PASS == 1) {
+        for (int e = t; e < r * r; e += kQrSpreadThreads) Xin[e] = X1[e];
         __syncthreads();
     }
-    for (int e = t; e < r * n; e += kQrSmallThreads) Y[e] = Ws[e];
+    if (t < nr) {
+        double x[kQrSpreadR];
+#pragma unroll
+        for (int i = 0; i < kQrSpreadR; ++i) x[i] = i < r ? W[(size_t)i * n + v0 + t] : 0.0;
+        if (PASS == 1) {                                   // row of W X1 (upper-triangular X1)
+#pragma unroll
+            for (int k = kQrSpreadR - 1; k >= 0; --k) {
+                if (k >= r) continue;
+                double y = 0.0;
+#pragma unroll
+                for (int i = 0; i <= k; ++i) y = fma(x[i], Xin[i * r + k], y);
+                x[k] = y;
+            }
+#pragma unroll
+            for (int i = 0; i < kQrSpreadR; ++i)
+                if (i < r) Y[(size_t)i * n + v0 + t] = x[i];
+        }
+#pragma unroll
+        for (int i = 0; i < kQrSpreadR; ++i)
+            if (i < r) Ws[i * kQrSpreadRows + t] = x[i];
+    }
+    __syncthreads();
+    if (t < npairs) {                                      // entry t = (a, b), a <= b, row-major upper triangle
+        int e = t, a = 0;
+        while (e >= r - a) {
+            e -= r - a;
+            ++a;
+        }
+        const int b = a + e;
+        double g = 0.0;
+        for (int c = 0; c < nr; ++c) g = fma(Ws[a * kQrSpreadRows + c], Ws[b * kQrSpreadRows + c], g);
+        part[(size_t)blockIdx.x * kQrSpreadPairs + t] = g;
+    }
+    __threadfence();
+    __syncthreads();
+    if (t == 0) last = atomicAdd(&ticket[PASS], 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (t < npairs) {
+        int e = t, a = 0;
+        while (e >= r - a) {
+            e -= r - a;
+            ++a;
+        }
+        const int b = a + e;
+        double g = 0.0;
+        for (int c = 0; c < (int)gridDim.x; ++c) g += __ldcg(&part[(size_t)c * kQrSpreadPairs + t]);
+        G[a * r + b] = w * g;
+        G[b * r + a] = w * g;
+    }
+    __syncthreads();
+    __shared__ int bad;
+    if (t < 32) {
+        const int bk = chol_inv_warp(G, r, Rs, Xs, Dinv);
+        if (t == 0) bad = bk;
+    }
+    __syncthreads();
+    const double nan = __longlong_as_double(0x7ff8000000000000ll);
+    if (bad && t == 0 && *info == 0) *info = bad;
+    double* Xout = PASS == 0 ? X1 : X2;
+    for (int e = t; e < r * r; e += kQrSpreadThreads) {
+        Xout[e] = bad ? nan : Xs[e];
+        if (PASS == 0) {
+            R1[e] = bad ? nan : Rs[e];
+        } else {
+            const int i = e / r, j = e % r;
+            double o = 0.0;
+            for (int k = i; k <= j; ++k) o = fma(Rs[i * r + k], __ldcg(&R1[k * r + j]), o);
+            R[e] = bad ? nan : o;
+        }
+    }
+    if (t == 0) ticket[PASS] = 0u;
+}
+
+// Y <- Y X2 in place, one entry per thread (the last step of the spread QR)
+__global__ void __launch_bounds__(kQrSpreadThreads) k_qr_spread_apply(double* Y, int r, int n,
+                                                                     const double* __restrict__ ws) {
+    __shared__ double Xs[kQrSpreadR * kQrSpreadR];
+    const double* X2 = ws + size_t(kQrSpreadCtas) * kQrSpreadPairs + kQrSpreadR * kQrSpreadR;
+    for (int e = threadIdx.x; e < r * r; e += kQrSpreadThreads) Xs[e] = X2[e];
+    __syncthreads();
+    const int v = blockIdx.x * kQrSpreadThreads + threadIdx.x;
+    if (v >= n) return;
+    double x[kQrSpreadR];
+#pragma unroll
+    for (int i = 0; i < kQrSpreadR; ++i) x[i] = i < r ? Y[(size_t)i * n + v] : 0.0;
+#pragma unroll
+    for (int k = kQrSpreadR - 1; k >= 0; --k) {
+        if (k >= r) continue;
+        double y = 0.0;
+#pragma unroll
+        for (int i = 0; i <= k; ++i) y = fma(x[i], Xs[i * r + k], y);
+        x[k] = y;
+    }
+#pragma unroll
+    for (int i = 0; i < kQrSpreadR; ++i)
+        if (i < r) Y[(size_t)i * n + v] = x[i];
 }
 
 // ---------------------------------------------------------------- one-sided Jacobi SVD (FP64)
@@ -606,6 +690,155 @@ __global__ void __launch_bounds__(1024) k_svd_jacobi_f64(const double* __restric
         U[e] = s > 0.0 ? A[c * 64 + i] / s : 0.0;
         Qm[e] = V[c * 64 + i];
         if (i == 0) sigma[k] = s;
+    }
+}
+
+// The same SVD for r <= 16 in one warp: eight lane groups of four, group g
+// rotating pair g of each round (its lanes split the r entries, sums by two
+// xor shuffles, every lane of the group computing the same rotation), and
+// __syncwarp between rounds instead of a CTA barrier.  The steps are those of
+// k_svd_jacobi_f64: FP32 sweeps, FP64 re-orthonormalisation of the rotations,
+// FP64 sweeps from A = S V, then the sorted column norms.
+constexpr int kSvdSmallR = 16;
+
+template <typename T>
+__device__ bool small_sweeps(T* A, T* V, int r, T tol, int max_sweeps) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, u = lane & 3;
+    const int m = (r + 1) & ~1;
+    const T tol2 = tol * tol;
+    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+        int rotated = 0;
+        for (int round = 0; round < m - 1; ++round) {
+            int p = 0, q = r;                                // groups past m / 2 stay idle (q >= r)
+            if (g < m / 2) {
+                auto slot = [&](int pos) { return pos == 0 ? 0 : 1 + (pos - 1 + round) % (m - 1); };
+                p = slot(g);
+                q = slot(m - 1 - g);
+                if (p > q) {
+                    const int tmp = p;
+                    p = q;
+                    q = tmp;
+                }
+            }
+            T al = T(0), be = T(0), ga = T(0);
+            if (q < r) {
+                for (int i = u; i < r; i += 4) {
+                    const T x = A[p * kSvdSmallR + i], y = A[q * kSvdSmallR + i];
+                    al = fma(x, x, al);
+                    be = fma(y, y, be);
+                    ga = fma(x, y, ga);
+                }
+            }
+#pragma unroll
+            for (int o = 1; o < 4; o <<= 1) {                // every lane takes part
+                al += __shfl_xor_sync(0xffffffffu, al, o);
+                be += __shfl_xor_sync(0xffffffffu, be, o);
+                ga += __shfl_xor_sync(0xffffffffu, ga, o);
+            }
+            if (q < r && ga != T(0) && ga * ga > tol2 * (al * be)) {
+                const T zeta = (be - al) / (T(2) * ga);
+                const T tt = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(fma(zeta, zeta, T(1))));
+                const T c = jac_rsqrt(fma(tt, tt, T(1)));
+                const T sn = c * tt;
+                for (int i = u; i < r; i += 4) {
+                    const T x = A[p * kSvdSmallR + i], y = A[q * kSvdSmallR + i];
+                    A[p * kSvdSmallR + i] = c * x - sn * y;
+                    A[q * kSvdSmallR + i] = sn * x + c * y;
+                    const T vx = V[p * kSvdSmallR + i], vy = V[q * kSvdSmallR + i];
+                    V[p * kSvdSmallR + i] = c * vx - sn * vy;
+                    V[q * kSvdSmallR + i] = sn * vx + c * vy;
+                }
+                rotated = 1;
+            }
+            __syncwarp();
+        }
+        if (!__any_sync(0xffffffffu, rotated)) return true;
+    }
+    return false;
+}
+
+__global__ void __launch_bounds__(32) k_svd_small_f64(const double* __restrict__ S, int r, double drop_tol,
+                                                     double* __restrict__ U, double* __restrict__ sigma,
+                                                     double* __restrict__ Qm, int* __restrict__ r_keep,
+                                                     int* __restrict__ info,
+                                                     const double* __restrict__ drop_tol_dev = nullptr) {
+    constexpr int R = kSvdSmallR;
+    __shared__ double A[R * R], V[R * R], E[R * R], Sm[R * R];   // column-major: column c at c*R
+    __shared__ float Af[R * R], Vf[R * R];
+    __shared__ double sv[R];
+    __shared__ int order[R];
+    const int t = threadIdx.x;
+    for (int e = t; e < R * R; e += 32) {
+        const int c = e / R, i = e % R;
+        const double x = (c < r && i < r) ? S[i * r + c] : 0.0;
+        Sm[e] = x;                                   // Sm[c * R + i] = S[i][c]
+        Af[e] = (float)x;
+        Vf[e] = (c == i && c < r) ? 1.f : 0.f;
+    }
+    __syncwarp();
+    (void)small_sweeps<float>(Af, Vf, r, 1e-6f, kSvdMaxSweeps);
+    for (int e = t; e < R * R; e += 32) V[e] = (double)Vf[e];
+    __syncwarp();
+    for (int it = 0; it < 2; ++it) {                 // V <- V (I - E/2), E = V^T V - I
+        for (int e = t; e < r * r; e += 32) {
+            const int a = e / r, b = e % r;
+            double g = 0.0;
+            for (int i = 0; i < r; ++i) g = fma(V[a * R + i], V[b * R + i], g);
+            E[a * R + b] = g - (a == b ? 1.0 : 0.0);
+        }
+        __syncwarp();
+        for (int e = t; e < r * r; e += 32) {
+            const int c = e / r, i = e % r;
+            double v = V[c * R + i];
+            for (int k = 0; k < r; ++k) v = fma(-0.5 * V[k * R + i], E[k * R + c], v);
+            A[c * R + i] = v;
+        }
+        __syncwarp();
+        for (int e = t; e < r * r; e += 32) {
+            const int c = e / r, i = e % r;
+            V[c * R + i] = A[c * R + i];
+        }
+        __syncwarp();
+    }
+    for (int e = t; e < R * R; e += 32) {            // A = S V
+        const int c = e / R, i = e % R;
+        double a = 0.0;
+        if (c < r && i < r)
+            for (int k = 0; k < r; ++k) a = fma(Sm[k * R + i], V[c * R + k], a);
+        A[e] = a;
+    }
+    __syncwarp();
+    const bool converged = small_sweeps<double>(A, V, r, 1e-15, kSvdMaxSweeps);
+    if (t < r) {
+        double nn = 0.0;
+        for (int i = 0; i < r; ++i) nn = fma(A[t * R + i], A[t * R + i], nn);
+        sv[t] = sqrt(nn);
+    }
+    __syncwarp();
+    if (t == 0) {
+        for (int i = 0; i < r; ++i) order[i] = i;
+        for (int i = 0; i < r; ++i) {
+            int best = i;
+            for (int j = i + 1; j < r; ++j)
+                if (sv[order[j]] > sv[order[best]]) best = j;
+            const int tmp = order[i];
+            order[i] = order[best];
+            order[best] = tmp;
+        }
+        const double tol = drop_tol_dev ? *drop_tol_dev : drop_tol;
+        int keep = 0;
+        for (int i = 0; i < r; ++i) keep += sv[order[i]] >= tol ? 1 : 0;
+        *r_keep = keep;
+        *info = converged ? 0 : 1;
+    }
+    __syncwarp();
+    for (int e = t; e < r * r; e += 32) {
+        const int i = e / r, k = e % r;
+        const int c = order[k];
+        const double sc = sv[c];
+        U[e] = sc > 0.0 ? A[c * R + i] / sc : 0.0;
+        Qm[e] = V[c * R + i];
+        if (i == 0) sigma[k] = sc;
     }
 }
 

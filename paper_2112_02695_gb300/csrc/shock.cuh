@@ -269,45 +269,159 @@ __global__ void __launch_bounds__(kShT) k_sh_normalize(double* __restrict__ b, i
     for (int v = threadIdx.x; v < n; v += kShT) b[v] *= scale;
 }
 
-// Gram matrix of increments: G[i][j] = w sum_n A_i(n) (B1_j(n) - B0_j(n)),
-// block (i, j); DIAG: j = i only, G[i] = w sum_n (B1_i - B0_i)^2 (A unused).
-template <bool DIAG>
-__global__ void __launch_bounds__(kShT) k_sh_dgram(const double* __restrict__ A, const double* __restrict__ B1,
-                                                  const double* __restrict__ B0, int rB, int n, double w,
-                                                  double* __restrict__ G) {
-    __shared__ double red[kShT / 32];
-    const int i = blockIdx.x, j = DIAG ? blockIdx.x : blockIdx.y;
-    const double* b1 = B1 + (size_t)j * n;
-    const double* b0 = B0 + (size_t)j * n;
-    const double* a = DIAG ? nullptr : A + (size_t)i * n;
-    double s = 0.0;
-    for (int k = threadIdx.x; k < n; k += kShT) {
-        const double d = b1[k] - b0[k];
-        s = fma(DIAG ? d : a[k], d, s);
+// The whole basis augmentation (Sec. 3.1) of `count` boundary vectors in one
+// CTA, for n <= kAugThreads * kAugEPT entries and at most kAugR basis
+// columns: vector k (src[k]) goes to column rh0 + k of Vh, is orthogonalised
+// twice against the columns before it (c_j = w <V_j, b>, b -= sum c_j V_j),
+// and is kept when its squared norm after is more than 1e-20 of its squared
+// norm before (nrm[2k], nrm[2k + 1]); a kept vector is scaled to unit w-norm.
+// skip, when not null, gets bit 1 for a vector that was not kept (a replayed
+// step assumes both are).  Each thread owns the entries v = t + kAugThreads e,
+// every sum has a fixed order.
+constexpr int kAugThreads = 1024, kAugEPT = 4, kAugR = 32;
+
+__global__ void __launch_bounds__(kAugThreads) k_sh_augment(double* __restrict__ Vh, int rh0, int n, double w,
+                                                            const double* __restrict__ src0,
+                                                            const double* __restrict__ src1, int count,
+                                                            double* __restrict__ nrm, int* __restrict__ skip) {
+    __shared__ double red[kAugThreads / 32][kAugR];
+    __shared__ double cs[kAugR];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    // warp partial j of a fixed-order block sum; finish_sums(nj) leaves the sums in cs[0..nj)
+    auto warp_part = [&](double x, int j) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) red[warp][j] = x;
+    };
+    auto finish_sums = [&](int nj) {
+        __syncthreads();
+        if (t < nj) {
+            double x = 0.0;
+            for (int k = 0; k < kAugThreads / 32; ++k) x += red[k][t];
+            cs[t] = x;
+        }
+        __syncthreads();
+    };
+    auto sq_sum = [&](const double (&bv)[kAugEPT]) {
+        double x = 0.0;
+#pragma unroll
+        for (int e = 0; e < kAugEPT; ++e) x = fma(bv[e], bv[e], x);
+        warp_part(x, 0);
+        finish_sums(1);
+        const double r = cs[0];
+        __syncthreads();
+        return r;
+    };
+    for (int k = 0; k < count; ++k) {
+        const int rh = rh0 + k;
+        const double* src = k == 0 ? src0 : src1;
+        double* b = Vh + (size_t)rh * n;
+        double bv[kAugEPT];
+#pragma unroll
+        for (int e = 0; e < kAugEPT; ++e) {
+            const int v = t + e * kAugThreads;
+            bv[e] = v < n ? src[v] : 0.0;
+        }
+        const double n0 = sq_sum(bv);
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int j = 0; j < rh; ++j) {
+                double x = 0.0;
+#pragma unroll
+                for (int e = 0; e < kAugEPT; ++e) {
+                    const int v = t + e * kAugThreads;
+                    if (v < n) x = fma(Vh[(size_t)j * n + v], bv[e], x);
+                }
+                warp_part(x, j);
+            }
+            finish_sums(rh);
+#pragma unroll
+            for (int e = 0; e < kAugEPT; ++e) {
+                const int v = t + e * kAugThreads;
+                if (v < n) {
+                    double x = bv[e];
+                    for (int j = 0; j < rh; ++j) x = fma(-(w * cs[j]), Vh[(size_t)j * n + v], x);
+                    bv[e] = x;
+                }
+            }
+            __syncthreads();
+        }
+        const double n1 = sq_sum(bv);
+        const bool kept = n1 > 1e-20 * n0;
+        const double scale = kept && n1 > 0.0 ? 1.0 / sqrt(w * n1) : 1.0;
+#pragma unroll
+        for (int e = 0; e < kAugEPT; ++e) {
+            const int v = t + e * kAugThreads;
+            if (v < n) b[v] = bv[e] * scale;
+        }
+        if (t == 0) {
+            nrm[2 * k] = n0;
+            nrm[2 * k + 1] = n1;
+            if (skip && !kept) *skip |= 1;
+        }
+        __syncthreads();                      // column rh written before the next vector reads it
     }
-    s = sh_block_sum(s, red);
-    if (threadIdx.x == 0) G[DIAG ? i : i * rB + j] = w * s;
 }
 
 // Change of f over a low-rank step (Sec. 5.1, eqs. "err low rank1" and "err low rank2"):
 //   err^2 = sum_j |dK_j|^2 + sum_ij dS_ij^2 + sum_i |dL_i|^2
 //           + 2 sum_ij P_ij dS_ij + 2 sum_ij dS_ij Qd_ij + 2 sum_ij P_ij Qd_ij,
-// P_ij = <dK_j, X'_i>_x (P[i][j]), Qd_ij = <dL_i, V_j>_v (stored as Gv[j][i]),
-// dS = S2 - S1, |dK_j|^2 = nk[j], |dL_i|^2 = nl[i].  One block; err >= 0.
-__global__ void __launch_bounds__(kShT) k_sh_err(const double* __restrict__ nk, const double* __restrict__ nl,
-                                                const double* __restrict__ P, const double* __restrict__ Gv,
-                                                const double* __restrict__ S1, const double* __restrict__ S2, int r,
-                                                double* __restrict__ err) {
+// P_ij = <dK_j, X'_i>_x (Pk[i][j]), Qd_ij = <dL_i, V_j>_v (stored as Gv[j][i]),
+// dS = S2 - S1, err >= 0.  One launch of 2 r + 2 r^2 blocks, one inner product
+// each: block b < r: nk[b] = dx |K1_b - K0_b|^2; b < 2 r: nl = wv |L1 - L0|^2;
+// then Pk[i][j] = dx <X1_i, K1_j - K0_j>, then Gv[i][j] = wv <Vh_i, L1_j - L0_j>.
+// The block that finishes last (a ticket counter, reset to zero afterwards;
+// nothing waits) forms err from them.
+__global__ void __launch_bounds__(kShT) k_sh_change(const double* __restrict__ K1, const double* __restrict__ K0,
+                                                   const double* __restrict__ X1, const double* __restrict__ L1,
+                                                   const double* __restrict__ L0, const double* __restrict__ Vh,
+                                                   int r, int n_x, int n_v, double dx, double wv,
+                                                   const double* __restrict__ S1, const double* __restrict__ S2,
+                                                   double* nk, double* nl, double* Pk, double* Gv,
+                                                   unsigned* __restrict__ ticket, double* __restrict__ err) {
     __shared__ double red[kShT / 32];
-    double s = 0.0;
+    __shared__ int last;
+    int b = blockIdx.x;
+    const double *A = nullptr, *B1, *B0;
+    double w;
+    int n;
+    double* out;
+    if (b < r) {
+        B1 = K1 + (size_t)b * n_x, B0 = K0 + (size_t)b * n_x, n = n_x, w = dx, out = nk + b;
+    } else if ((b -= r) < r) {
+        B1 = L1 + (size_t)b * n_v, B0 = L0 + (size_t)b * n_v, n = n_v, w = wv, out = nl + b;
+    } else if ((b -= r) < r * r) {
+        const int i = b / r, j = b % r;
+        A = X1 + (size_t)i * n_x, B1 = K1 + (size_t)j * n_x, B0 = K0 + (size_t)j * n_x, n = n_x, w = dx, out = Pk + b;
+    } else {
+        b -= r * r;
+        const int i = b / r, j = b % r;
+        A = Vh + (size_t)i * n_v, B1 = L1 + (size_t)j * n_v, B0 = L0 + (size_t)j * n_v, n = n_v, w = wv, out = Gv + b;
+    }
+    double acc = 0.0;
+    for (int k = threadIdx.x; k < n; k += kShT) {
+        const double d = B1[k] - B0[k];
+        acc = fma(A ? A[k] : d, d, acc);
+    }
+    acc = sh_block_sum(acc, red);
+    if (threadIdx.x == 0) *out = w * acc;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double e = 0.0;
     for (int t = threadIdx.x; t < r * r; t += kShT) {
         const int i = t / r, j = t % r;
-        const double ds = S2[t] - S1[t], q = Gv[j * r + i];
-        s += ds * ds + 2.0 * P[t] * ds + 2.0 * ds * q + 2.0 * P[t] * q;
-        if (i == j) s += nk[i] + nl[i];
+        const double ds = S2[t] - S1[t], q = __ldcg(&Gv[j * r + i]), pk = __ldcg(&Pk[t]);
+        e += ds * ds + 2.0 * pk * ds + 2.0 * ds * q + 2.0 * pk * q;
+        if (i == j) e += __ldcg(&nk[i]) + __ldcg(&nl[i]);
     }
-    s = sh_block_sum(s, red);
-    if (threadIdx.x == 0) *err = sqrt(fmax(s, 0.0));
+    e = sh_block_sum(e, red);
+    if (threadIdx.x == 0) {
+        *err = sqrt(fmax(e, 0.0));
+        *ticket = 0u;
+    }
 }
 
 // S = diag(sigma[:r]) (packed [r][r]); r_dev and skip as in k_rotate_f64
