@@ -3073,6 +3073,7 @@ struct boltz_shock_s {
                                           // [4] skip bits of a replayed step (1: a boundary vector not
                                           // kept, 2: a QR or the rank failed), [8] k_sh_change's ticket
     double* d_tol = nullptr;              // drop_tol of a replayed step
+    boltz_dev::AugState* aug = nullptr;   // scratch of the basis augmentation
     // replayed steps: one CUDA graph per (rank, X, S, V, dt) seen twice, both boundary
     // vectors kept; h_pin: [0] drop_tol, [1..2] d_int[0..4] read back, [3] the step's err
     double* h_pin = nullptr;
@@ -3143,7 +3144,7 @@ boltz_status boltz_shock_create(boltz_grid g, int n_x, double L_x, const double*
         {(void**)&s->K32, rm * nx * 4}, {(void**)&s->C32, rm * nx * 4}, {(void**)&s->E32, rm * rm * rm * 4},
         {(void**)&s->S32, rm * rm * 4}, {(void**)&s->D32, rm * rm * 4}, {(void**)&s->Cs32, rm * rm * rm * 4},
         {(void**)&s->G32, rm * nv * 4}, {(void**)&s->spec_v, rm * half * 8}, {&s->qr_ws, qr_bytes},
-        {(void**)&s->d_int, 64}, {(void**)&s->d_tol, 8}};
+        {(void**)&s->d_int, 64}, {(void**)&s->d_tol, 8}, {(void**)&s->aug, sizeof(boltz_dev::AugState)}};
     size_t total = 0;
     for (auto& pt : parts) total = align_up(total + pt.second, 256);
     if (cudaMalloc(&s->mem, total) != cudaSuccess) {
@@ -3157,7 +3158,8 @@ boltz_status boltz_shock_create(boltz_grid g, int n_x, double L_x, const double*
         off = align_up(off + pt.second, 256);
     }
     // the tickets of the spread QR and of k_sh_change start at zero (each launch leaves them so)
-    if (cudaMemset(s->d_int, 0, 64) != cudaSuccess || cudaMemset(s->qr_ws, 0, qr_bytes) != cudaSuccess) {
+    if (cudaMemset(s->d_int, 0, 64) != cudaSuccess || cudaMemset(s->qr_ws, 0, qr_bytes) != cudaSuccess ||
+        cudaMemset(s->aug, 0, sizeof(boltz_dev::AugState)) != cudaSuccess) {
         boltz_shock_destroy(s);
         return BOLTZ_ECUDA;
     }
@@ -3271,7 +3273,7 @@ boltz_status lr_core(boltz_shock s, const double* X, const double* S, int r, int
         return rs;
     // 2. S-step (Sec. 2.4 S-step): transport through the updated K, collision term with S1
     sh_ghosts(s, s->K1, rh, st);
-    k_sh_xgram<<<dim3(rh, rh), T, 0, st>>>(s->X1, s->K1, s->gL, s->gR, rh, nx, s->dx, s->Bp, s->Bm);
+    k_sh_xgram<<<dim3(rh, rh), T, 0, st>>>(s->X1, s->K1, s->gL, s->gR, rh, nx, s->Bp, s->Bm);
     k_sh_triple<<<dim3(rh, rh), T, 0, st>>>(s->X1, rh, nx, s->dx, s->E32);
     k_sh_to_f32<<<1, T, 0, st>>>(s->S1, s->S32, (size_t)rh * rh);
     if ((rs = boltz_lowrank_coupling(s->E32, s->S32, rh, s->T32, s->Cs32, s->D32, stream)) != BOLTZ_OK) return rs;
@@ -3280,7 +3282,7 @@ boltz_status lr_core(boltz_shock s, const double* X, const double* S, int r, int
     k_sh_comb<true><<<sh_grid((size_t)rh * nv), T, 0, st>>>(s->Vh, rh, nv, s->S2, rh, rh, s->L);
     k_sh_comb<false><<<sh_grid((size_t)rh * nx), T, 0, st>>>(s->X1, rh, nx, s->S2, rh, rh, s->Kt);
     sh_ghosts(s, s->Kt, rh, st);
-    k_sh_xgram<<<dim3(rh, rh), T, 0, st>>>(s->X1, s->Kt, s->gL, s->gR, rh, nx, s->dx, s->Bp, s->Bm);
+    k_sh_xgram<<<dim3(rh, rh), T, 0, st>>>(s->X1, s->Kt, s->gL, s->gR, rh, nx, s->Bp, s->Bm);
     k_sh_to_f32<<<1, T, 0, st>>>(s->S2, s->S32, (size_t)rh * rh);
     if ((rs = boltz_lowrank_coupling(s->E32, s->S32, rh, nullptr, s->Cs32, nullptr, stream)) != BOLTZ_OK) return rs;
     if ((rs = boltz_lstep_collision(s->Q32, rh, s->Cs32, nv, s->G32, stream)) != BOLTZ_OK) return rs;
@@ -3329,29 +3331,55 @@ void lr_rotate(boltz_shock s, double* X, double* S, double* V, int rh, int rk, c
 // step): both are appended and the device records whether that was right;
 // otherwise a vector keeping less than 1e-10 of its norm lies in span(V)
 // already and is not appended (it would carry no weight and make the K-step
-// QR singular), a decision read back on the host.  Velocity grids of at most
-// 4096 points run the whole augmentation in one CTA (k_sh_augment), larger
-// ones as a chain of dot, subtract and normalise kernels.  Returns rh.
+// QR singular), a decision read back on the host.  Up to 31 basis columns
+// the augmentation runs on the k_aug_* kernels (inner products spread over
+// up to 128 CTAs, 3 launches per vector), beyond that as a chain of dot,
+// subtract and normalise kernels.  Returns rh.
 template <bool KEEP_ALL>
 boltz_status lr_append(boltz_shock s, const double* V, int r, int* rh_out, cudaStream_t st) {
     using namespace boltz_dev;
     const int T = kShT, nv = s->n_v;
     BZ_CUDA(cudaMemcpyAsync(s->Vh, V, (size_t)r * nv * 8, cudaMemcpyDeviceToDevice, st));
     int rh = r;
-    if (nv <= kAugThreads * kAugEPT && r + s->rb <= kAugR && s->rb <= 2) {
-        // one CTA per call: both vectors at once when the step assumes both kept
+    if (r + s->rb <= kAugR && s->rb <= 2) {
+        const int G = (int)std::min<size_t>(std::max<size_t>((nv + kAugT - 1) / kAugT, 1), kAugCtas);
+        auto start = [&](int rc, const double* src, int scale_prev, int k) {
+            if (rc <= 8) k_aug_start<8><<<G, kAugT, 0, st>>>(s->Vh, rc, nv, s->wv, src, scale_prev, s->nrm, k, s->aug);
+            else if (rc <= 16) k_aug_start<16><<<G, kAugT, 0, st>>>(s->Vh, rc, nv, s->wv, src, scale_prev, s->nrm, k, s->aug);
+            else k_aug_start<32><<<G, kAugT, 0, st>>>(s->Vh, rc, nv, s->wv, src, scale_prev, s->nrm, k, s->aug);
+        };
+        auto update = [&](int rc, int k, int* skip) {
+            if (rc <= 8) {
+                k_aug_update<8, 0><<<G, kAugT, 0, st>>>(s->Vh, rc, nv, s->wv, s->nrm, k, skip, s->aug);
+                k_aug_update<8, 1><<<G, kAugT, 0, st>>>(s->Vh, rc, nv, s->wv, s->nrm, k, skip, s->aug);
+            } else if (rc <= 16) {
+                k_aug_update<16, 0><<<G, kAugT, 0, st>>>(s->Vh, rc, nv, s->wv, s->nrm, k, skip, s->aug);
+                k_aug_update<16, 1><<<G, kAugT, 0, st>>>(s->Vh, rc, nv, s->wv, s->nrm, k, skip, s->aug);
+            } else {
+                k_aug_update<32, 0><<<G, kAugT, 0, st>>>(s->Vh, rc, nv, s->wv, s->nrm, k, skip, s->aug);
+                k_aug_update<32, 1><<<G, kAugT, 0, st>>>(s->Vh, rc, nv, s->wv, s->nrm, k, skip, s->aug);
+            }
+        };
         if constexpr (KEEP_ALL) {
-            k_sh_augment<<<1, kAugThreads, 0, st>>>(s->Vh, r, nv, s->wv, s->fL, s->fR, s->rb, s->nrm, s->d_int + 4);
+            // both vectors, the first scaled at the start of the second
+            for (int k = 0; k < s->rb; ++k) {
+                start(r + k, k == 0 ? s->fL : s->fR, k > 0, k);
+                update(r + k, k, s->d_int + 4);
+            }
+            k_aug_scale<<<G, kAugT, 0, st>>>(s->Vh, r + s->rb - 1, nv, s->aug);
             *rh_out = r + s->rb;
             return BOLTZ_OK;
         }
         for (int k = 0; k < s->rb; ++k) {
-            k_sh_augment<<<1, kAugThreads, 0, st>>>(s->Vh, rh, nv, s->wv, k == 0 ? s->fL : s->fR, nullptr, 1,
-                                                    s->nrm, nullptr);
+            start(rh, k == 0 ? s->fL : s->fR, 0, 0);
+            update(rh, 0, nullptr);
             double hn[2];
             BZ_CUDA(cudaMemcpyAsync(hn, s->nrm, sizeof(hn), cudaMemcpyDeviceToHost, st));
             BZ_CUDA(cudaStreamSynchronize(st));
-            if (hn[1] > 1e-20 * hn[0]) ++rh;
+            if (hn[1] > 1e-20 * hn[0]) {
+                k_aug_scale<<<G, kAugT, 0, st>>>(s->Vh, rh, nv, s->aug);
+                ++rh;
+            }
         }
         *rh_out = rh;
         return BOLTZ_OK;

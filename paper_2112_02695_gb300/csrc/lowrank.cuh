@@ -449,17 +449,38 @@ __global__ void __launch_bounds__(kQrSpreadThreads) k_qr_spread_f64(const double
     __syncthreads();
     if (!last) return;
     __threadfence();
-    if (t < npairs) {
-        int e = t, a = 0;
-        while (e >= r - a) {
-            e -= r - a;
-            ++a;
+    {   // G = w sum of the partials: warp wp takes entries wp, wp + 8, ...; lanes over CTAs, then a shuffle tree
+        constexpr int NWP = kQrSpreadThreads / 32, EPW = (kQrSpreadPairs + NWP - 1) / NWP;
+        const int wp = t >> 5, lane = t & 31;
+        double acc[EPW];
+#pragma unroll
+        for (int k = 0; k < EPW; ++k) acc[k] = 0.0;
+        for (int c = lane; c < (int)gridDim.x; c += 32) {
+#pragma unroll
+            for (int k = 0; k < EPW; ++k) {
+                const int e = wp + NWP * k;
+                if (e < npairs) acc[k] += __ldcg(&part[(size_t)c * kQrSpreadPairs + e]);
+            }
         }
-        const int b = a + e;
-        double g = 0.0;
-        for (int c = 0; c < (int)gridDim.x; ++c) g += __ldcg(&part[(size_t)c * kQrSpreadPairs + t]);
-        G[a * r + b] = w * g;
-        G[b * r + a] = w * g;
+#pragma unroll
+        for (int k = 0; k < EPW; ++k) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], o);
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int k = 0; k < EPW; ++k) {
+                int e = wp + NWP * k, a = 0;
+                if (e >= npairs) continue;
+                while (e >= r - a) {
+                    e -= r - a;
+                    ++a;
+                }
+                const int b = a + e;
+                G[a * r + b] = w * acc[k];
+                G[b * r + a] = w * acc[k];
+            }
+        }
     }
     __syncthreads();
     __shared__ int bad;
@@ -701,6 +722,38 @@ __global__ void __launch_bounds__(1024) k_svd_jacobi_f64(const double* __restric
 // FP64 sweeps from A = S V, then the sorted column norms.
 constexpr int kSvdSmallR = 16;
 
+// Jacobi rotation (c, s) that zeroes <a_p, a_q> = ga given |a_p|^2 = al and
+// |a_q|^2 = be: tan = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), zeta =
+// (be - al) / (2 ga), written as tan = +-|h| / (|d| + sqrt(d^2 + h^2)) with
+// d = be - al, h = 2 ga.
+__device__ __forceinline__ void jac_rotation(float al, float be, float ga, float& c, float& s) {
+    const float zeta = (be - al) / (2.f * ga);
+    const float tt = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
+    c = rsqrtf(fmaf(tt, tt, 1.f));
+    s = c * tt;
+}
+// FP64: FP64 divisions and square roots are slow on this GPU, so the angle
+// comes from FP32 arithmetic on d and h scaled by a power of two (exact), and
+// (c, s) is then normalised in FP64 by two terms of the series of
+// (c^2 + s^2)^(-1/2) around 1 (error ~ (c^2 + s^2 - 1)^3).  An angle good to
+// FP32 accuracy leaves ~1e-7 of the pair's inner product, which the next
+// sweep removes; every rotation is orthogonal to FP64 rounding.
+__device__ __forceinline__ void jac_rotation(double al, double be, double ga, double& c, double& s) {
+    const double d = be - al, h = 2.0 * ga;
+    int ex;
+    (void)frexp(fmax(fabs(d), fabs(h)), &ex);
+    const double sc = ldexp(1.0, -ex);
+    const float df = (float)(d * sc), hf = (float)(h * sc);
+    const float sg = (d == 0.0 || (d > 0.0) == (h > 0.0)) ? 1.f : -1.f;
+    const float tf = sg * fabsf(hf) / (fabsf(df) + sqrtf(fmaf(df, df, hf * hf)));
+    const float cf = rsqrtf(fmaf(tf, tf, 1.f));
+    double cd = (double)cf, sd = (double)(cf * tf);
+    const double e = fma(cd, cd, fma(sd, sd, -1.0));
+    const double corr = fma(e, fma(e, 0.375, -0.5), 1.0);
+    c = cd * corr;
+    s = sd * corr;
+}
+
 template <typename T>
 __device__ bool small_sweeps(T* A, T* V, int r, T tol, int max_sweeps) {
     const int lane = threadIdx.x & 31, g = lane >> 2, u = lane & 3;
@@ -736,10 +789,8 @@ __device__ bool small_sweeps(T* A, T* V, int r, T tol, int max_sweeps) {
                 ga += __shfl_xor_sync(0xffffffffu, ga, o);
             }
             if (q < r && ga != T(0) && ga * ga > tol2 * (al * be)) {
-                const T zeta = (be - al) / (T(2) * ga);
-                const T tt = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(fma(zeta, zeta, T(1))));
-                const T c = jac_rsqrt(fma(tt, tt, T(1)));
-                const T sn = c * tt;
+                T c, sn;
+                jac_rotation(al, be, ga, c, sn);
                 for (int i = u; i < r; i += 4) {
                     const T x = A[p * kSvdSmallR + i], y = A[q * kSvdSmallR + i];
                     A[p * kSvdSmallR + i] = c * x - sn * y;

@@ -45,13 +45,14 @@ __global__ void k_sh_full(const double* __restrict__ f, const float* __restrict_
                           const double* __restrict__ fR, const double* __restrict__ v1, int n_x, int n_v, double dt,
                           double dx, double* __restrict__ g) {
     const size_t total = (size_t)n_x * n_v;
+    const double cfl = dt / dx;
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
         const int p = (int)(t / n_v), v = (int)(t % n_v);
         const double c = f[t];
         const double l = p > 0 ? f[t - n_v] : fL[v];
         const double r = p < n_x - 1 ? f[t + n_v] : fR[v];
         const double a = v1[v], ap = fmax(a, 0.0), am = fmin(a, 0.0);
-        g[t] = c - dt / dx * (ap * (c - l) + am * (r - c)) + dt * (double)Q[t];
+        g[t] = c - cfl * (ap * (c - l) + am * (r - c)) + dt * (double)Q[t];
     }
 }
 
@@ -131,13 +132,15 @@ __global__ void k_sh_ghosts(const double* __restrict__ K, int r, int n_x, const 
     }
 }
 
-__device__ __forceinline__ double sh_dplus(const double* K, int n_x, const double* gL, int l, int x, double dx) {
+// dx D+ K_l(x) and dx D- K_l(x): the differences only (FP64 division is slow;
+// callers apply 1/dx once, or not at all where a factor dx cancels it)
+__device__ __forceinline__ double sh_diff_plus(const double* K, int n_x, const double* gL, int l, int x) {
     const double* Kl = K + (size_t)l * n_x;
-    return (Kl[x] - (x > 0 ? Kl[x - 1] : gL[l])) / dx;
+    return Kl[x] - (x > 0 ? Kl[x - 1] : gL[l]);
 }
-__device__ __forceinline__ double sh_dminus(const double* K, int n_x, const double* gR, int l, int x, double dx) {
+__device__ __forceinline__ double sh_diff_minus(const double* K, int n_x, const double* gR, int l, int x) {
     const double* Kl = K + (size_t)l * n_x;
-    return ((x < n_x - 1 ? Kl[x + 1] : gR[l]) - Kl[x]) / dx;
+    return (x < n_x - 1 ? Kl[x + 1] : gR[l]) - Kl[x];
 }
 
 // K-step Euler update (Sec. 2.4, K-step (b), upwind form of Sec. 2.3):
@@ -147,33 +150,36 @@ __global__ void k_sh_kupdate(const double* __restrict__ K, const float* __restri
                              const double* __restrict__ gR, int r, int n_x, double dt, double dx,
                              double* __restrict__ K1) {
     const size_t total = (size_t)r * n_x;
+    const double cfl = dt / dx;
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
         const int j = (int)(t / n_x), x = (int)(t % n_x);
         double tr = 0.0;
         for (int l = 0; l < r; ++l)
-            tr = fma(Ap[j * r + l], sh_dplus(K, n_x, gL, l, x, dx), fma(Am[j * r + l], sh_dminus(K, n_x, gR, l, x, dx), tr));
-        K1[t] = K[t] - dt * tr + dt * (double)C[t];
+            tr = fma(Ap[j * r + l], sh_diff_plus(K, n_x, gL, l, x),
+                     fma(Am[j * r + l], sh_diff_minus(K, n_x, gR, l, x), tr));
+        K1[t] = K[t] - cfl * tr + dt * (double)C[t];
     }
 }
 
 // Space Gram matrices of the transport, block (i, l):
 //   Bp[i][l] = dx sum_x X_i(x) D+ K_l(x),  Bm[i][l] = dx sum_x X_i(x) D- K_l(x)
+// (the factor dx cancels the 1/dx of the differences)
 __global__ void __launch_bounds__(kShT) k_sh_xgram(const double* __restrict__ X, const double* __restrict__ K,
                                                   const double* __restrict__ gL, const double* __restrict__ gR,
-                                                  int r, int n_x, double dx, double* Bp, double* Bm) {
+                                                  int r, int n_x, double* Bp, double* Bm) {
     __shared__ double red[kShT / 32];
     const int i = blockIdx.x, l = blockIdx.y;
     const double* Xi = X + (size_t)i * n_x;
     double sp = 0.0, sm = 0.0;
     for (int x = threadIdx.x; x < n_x; x += kShT) {
-        sp = fma(Xi[x], sh_dplus(K, n_x, gL, l, x, dx), sp);
-        sm = fma(Xi[x], sh_dminus(K, n_x, gR, l, x, dx), sm);
+        sp = fma(Xi[x], sh_diff_plus(K, n_x, gL, l, x), sp);
+        sm = fma(Xi[x], sh_diff_minus(K, n_x, gR, l, x), sm);
     }
     sp = sh_block_sum(sp, red);
     sm = sh_block_sum(sm, red);
     if (threadIdx.x == 0) {
-        Bp[i * r + l] = dx * sp;
-        Bm[i * r + l] = dx * sm;
+        Bp[i * r + l] = sp;
+        Bm[i * r + l] = sm;
     }
 }
 
@@ -269,97 +275,165 @@ __global__ void __launch_bounds__(kShT) k_sh_normalize(double* __restrict__ b, i
     for (int v = threadIdx.x; v < n; v += kShT) b[v] *= scale;
 }
 
-// The whole basis augmentation (Sec. 3.1) of `count` boundary vectors in one
-// CTA, for n <= kAugThreads * kAugEPT entries and at most kAugR basis
-// columns: vector k (src[k]) goes to column rh0 + k of Vh, is orthogonalised
-// twice against the columns before it (c_j = w <V_j, b>, b -= sum c_j V_j),
-// and is kept when its squared norm after is more than 1e-20 of its squared
-// norm before (nrm[2k], nrm[2k + 1]); a kept vector is scaled to unit w-norm.
-// skip, when not null, gets bit 1 for a vector that was not kept (a replayed
-// step assumes both are).  Each thread owns the entries v = t + kAugThreads e,
-// every sum has a fixed order.
-constexpr int kAugThreads = 1024, kAugEPT = 4, kAugR = 32;
+// The basis augmentation (Sec. 3.1) spread over up to kAugCtas CTAs (FP64
+// issues slowly on this GPU, so the inner products use many SMs).  Boundary
+// vector k goes to column rh = rh0 + k of Vh: b = src, two Gram-Schmidt passes
+// against the columns before it (c_j = w <V_j, b>, b -= sum_j c_j V_j), kept
+// when |b|^2 after > 1e-20 |b|^2 before, then scaled to unit w-norm.  Each
+// launch ends with the CTA that finishes last (a ticket counter, left at zero;
+// nothing waits) summing the per-CTA partial sums in CTA order:
+//   k_aug_start   b = src (after scaling column rh - 1, the previous vector);
+//                 partials of |src|^2 and <V_j, b>; last: c, nrm[2k]
+//   k_aug_update  b -= sum c_j V_j; PASS 0: partials of <V_j, b>, last: c;
+//                 PASS 1: partial |b|^2, last: nrm[2k + 1], the keep decision,
+//                 the scale, skip bit 1 if not kept (when skip is not null)
+//   k_aug_scale   b *= scale (the last vector)
+// Thread t of CTA c owns the entries v = c kAugT + t + e kAugT G (G CTAs), the
+// same in every launch, so b needs no other synchronisation.
+constexpr int kAugT = 128, kAugCtas = 128, kAugR = 32, kAugSlots = kAugR + 1;
 
-__global__ void __launch_bounds__(kAugThreads) k_sh_augment(double* __restrict__ Vh, int rh0, int n, double w,
-                                                            const double* __restrict__ src0,
-                                                            const double* __restrict__ src1, int count,
-                                                            double* __restrict__ nrm, int* __restrict__ skip) {
-    __shared__ double red[kAugThreads / 32][kAugR];
-    __shared__ double cs[kAugR];
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    // warp partial j of a fixed-order block sum; finish_sums(nj) leaves the sums in cs[0..nj)
-    auto warp_part = [&](double x, int j) {
+struct AugState {                  // device scratch of the augmentation
+    double part[kAugCtas][kAugSlots];
+    double coef[kAugR];            // w <V_j, b> of the last pass
+    double scale;                  // scale of the vector finished last (1 if not kept)
+    unsigned ticket;
+};
+
+// block sums of acc[0..nj) (and of x when with_x) into part[blockIdx.x][.]
+template <int RM>
+__device__ __forceinline__ void aug_partials(const double (&acc)[RM], int nj, double x, bool with_x, AugState* S) {
+    __shared__ double red[kAugT / 32][kAugSlots];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < RM; ++j) {
+        double y = acc[j];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) y += __shfl_down_sync(0xffffffffu, y, o);
+        if (lane == 0 && j < nj) red[warp][j] = y;
+    }
+    if (with_x) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-        if (lane == 0) red[warp][j] = x;
-    };
-    auto finish_sums = [&](int nj) {
-        __syncthreads();
-        if (t < nj) {
-            double x = 0.0;
-            for (int k = 0; k < kAugThreads / 32; ++k) x += red[k][t];
-            cs[t] = x;
-        }
-        __syncthreads();
-    };
-    auto sq_sum = [&](const double (&bv)[kAugEPT]) {
-        double x = 0.0;
+        if (lane == 0) red[warp][kAugR] = x;
+    }
+    __syncthreads();
+    const int t = threadIdx.x;
+    const int slot = t < nj ? t : (t == kAugT - 1 && with_x ? kAugR : -1);
+    if (slot >= 0) {
+        double y = 0.0;
 #pragma unroll
-        for (int e = 0; e < kAugEPT; ++e) x = fma(bv[e], bv[e], x);
-        warp_part(x, 0);
-        finish_sums(1);
-        const double r = cs[0];
-        __syncthreads();
-        return r;
-    };
-    for (int k = 0; k < count; ++k) {
-        const int rh = rh0 + k;
-        const double* src = k == 0 ? src0 : src1;
-        double* b = Vh + (size_t)rh * n;
-        double bv[kAugEPT];
+        for (int w = 0; w < kAugT / 32; ++w) y += red[w][slot];
+        S->part[blockIdx.x][slot] = y;
+    }
+}
+
+// true in the CTA that finished last (every CTA has written its partials)
+__device__ __forceinline__ bool aug_last(AugState* S) {
+    __shared__ int last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(&S->ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (last) __threadfence();
+    return last;
+}
+
+// sum over the CTAs of slot j, by warp j % 4 with lanes over CTAs (fixed order)
+__device__ __forceinline__ double aug_total(AugState* S, int j) {
+    const int lane = threadIdx.x & 31;
+    double y = 0.0;
+    for (int c = lane; c < (int)gridDim.x; c += 32) y += __ldcg(&S->part[c][j]);
 #pragma unroll
-        for (int e = 0; e < kAugEPT; ++e) {
-            const int v = t + e * kAugThreads;
-            bv[e] = v < n ? src[v] : 0.0;
-        }
-        const double n0 = sq_sum(bv);
-        for (int pass = 0; pass < 2; ++pass) {
-            for (int j = 0; j < rh; ++j) {
-                double x = 0.0;
+    for (int o = 16; o > 0; o >>= 1) y += __shfl_down_sync(0xffffffffu, y, o);
+    return __shfl_sync(0xffffffffu, y, 0);
+}
+
+template <int RM>
+__global__ void __launch_bounds__(kAugT) k_aug_start(double* Vh, int rh, int n, double w,
+                                                      const double* __restrict__ src, int scale_prev,
+                                                      double* __restrict__ nrm, int k, AugState* S) {
+    const int G = gridDim.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const double sp = scale_prev ? __ldcg(&S->scale) : 1.0;
+    double* b = Vh + (size_t)rh * n;
+    double acc[RM];
 #pragma unroll
-                for (int e = 0; e < kAugEPT; ++e) {
-                    const int v = t + e * kAugThreads;
-                    if (v < n) x = fma(Vh[(size_t)j * n + v], bv[e], x);
-                }
-                warp_part(x, j);
+    for (int j = 0; j < RM; ++j) acc[j] = 0.0;
+    double x2 = 0.0;
+    for (int v = blockIdx.x * kAugT + threadIdx.x; v < n; v += G * kAugT) {
+        if (scale_prev) Vh[(size_t)(rh - 1) * n + v] *= sp;
+        const double bv = src[v];
+        b[v] = bv;
+        x2 = fma(bv, bv, x2);
+#pragma unroll
+        for (int j = 0; j < RM; ++j)
+            if (j < rh) acc[j] = fma(Vh[(size_t)j * n + v], bv, acc[j]);
+    }
+    aug_partials<RM>(acc, rh, x2, true, S);
+    if (!aug_last(S)) return;
+    for (int j = warp; j <= kAugR; j += kAugT / 32) {
+        if (j < rh || j == kAugR) {
+            const double y = aug_total(S, j);
+            if (lane == 0) {
+                if (j < rh) S->coef[j] = w * y;
+                else nrm[2 * k] = y;
             }
-            finish_sums(rh);
-#pragma unroll
-            for (int e = 0; e < kAugEPT; ++e) {
-                const int v = t + e * kAugThreads;
-                if (v < n) {
-                    double x = bv[e];
-                    for (int j = 0; j < rh; ++j) x = fma(-(w * cs[j]), Vh[(size_t)j * n + v], x);
-                    bv[e] = x;
-                }
-            }
-            __syncthreads();
         }
-        const double n1 = sq_sum(bv);
-        const bool kept = n1 > 1e-20 * n0;
-        const double scale = kept && n1 > 0.0 ? 1.0 / sqrt(w * n1) : 1.0;
+    }
+    if (threadIdx.x == 0) S->ticket = 0u;
+}
+
+template <int RM, int PASS>
+__global__ void __launch_bounds__(kAugT) k_aug_update(double* Vh, int rh, int n, double w, double* __restrict__ nrm,
+                                                       int k, int* __restrict__ skip, AugState* S) {
+    __shared__ double c[kAugR];
+    const int G = gridDim.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x < rh) c[threadIdx.x] = __ldcg(&S->coef[threadIdx.x]);
+    __syncthreads();
+    double* b = Vh + (size_t)rh * n;
+    double acc[RM];
 #pragma unroll
-        for (int e = 0; e < kAugEPT; ++e) {
-            const int v = t + e * kAugThreads;
-            if (v < n) b[v] = bv[e] * scale;
+    for (int j = 0; j < RM; ++j) acc[j] = 0.0;
+    double x2 = 0.0;
+    for (int v = blockIdx.x * kAugT + threadIdx.x; v < n; v += G * kAugT) {
+        double Vv[RM];
+#pragma unroll
+        for (int j = 0; j < RM; ++j) Vv[j] = j < rh ? Vh[(size_t)j * n + v] : 0.0;
+        double bv = b[v];
+#pragma unroll
+        for (int j = 0; j < RM; ++j)
+            if (j < rh) bv = fma(-c[j], Vv[j], bv);
+        b[v] = bv;
+        if (PASS == 0) {
+#pragma unroll
+            for (int j = 0; j < RM; ++j)
+                if (j < rh) acc[j] = fma(Vv[j], bv, acc[j]);
+        } else {
+            x2 = fma(bv, bv, x2);
         }
-        if (t == 0) {
-            nrm[2 * k] = n0;
+    }
+    aug_partials<RM>(acc, PASS == 0 ? rh : 0, x2, PASS == 1, S);
+    if (!aug_last(S)) return;
+    if (PASS == 0) {
+        for (int j = warp; j < rh; j += kAugT / 32) {
+            const double y = aug_total(S, j);
+            if (lane == 0) S->coef[j] = w * y;
+        }
+    } else if (warp == 0) {
+        const double n1 = aug_total(S, kAugR);
+        if (lane == 0) {
+            const double n0 = nrm[2 * k];
+            const bool kept = n1 > 1e-20 * n0;
             nrm[2 * k + 1] = n1;
+            S->scale = kept && n1 > 0.0 ? 1.0 / sqrt(w * n1) : 1.0;
             if (skip && !kept) *skip |= 1;
         }
-        __syncthreads();                      // column rh written before the next vector reads it
     }
+    if (threadIdx.x == 0) S->ticket = 0u;
+}
+
+__global__ void __launch_bounds__(kAugT) k_aug_scale(double* Vh, int rh, int n, const AugState* S) {
+    const double sc = __ldcg(&S->scale);
+    for (int v = blockIdx.x * kAugT + threadIdx.x; v < n; v += gridDim.x * kAugT) Vh[(size_t)rh * n + v] *= sc;
 }
 
 // Change of f over a low-rank step (Sec. 5.1, eqs. "err low rank1" and "err low rank2"):
