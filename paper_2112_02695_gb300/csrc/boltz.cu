@@ -982,6 +982,10 @@ struct Launch {
     static constexpr int FPC_A = (D == 2) ? (64 / G::TPF > 1 ? 64 / G::TPF : 1) : FPC;
     static constexpr int BLOCK_A = G::TPF * FPC_A;
     static constexpr size_t SMEM_A = size_t(G::SMEM_F) * FPC_A * sizeof(float2);
+    // 2D synthesis launches of fewer than two CTAs per SM at FPC fields a CTA
+    // (small batches, e.g. the bases of a low-rank step) run FPC_A a CTA
+    static constexpr bool SMALL_SYN = (D == 2 && FPC_A < FPC);
+    static constexpr int kSmallSynCtas = 2 * 152;
 
     // 2D N = 128: lines split over 4-lane groups
     static constexpr bool WIDE = (D == 2 && N == 128);
@@ -1017,6 +1021,11 @@ struct Launch {
             if ((e = set_smem(k_synth<N, D, FPC, SYN_SHIFT>, SMEM)) != cudaSuccess) return e;
             if ((e = set_smem(k_synth<N, D, FPC, SYN_PREP>, SMEM)) != cudaSuccess) return e;
             if ((e = set_smem(k_synth<N, D, FPC, SYN_MULT>, SMEM)) != cudaSuccess) return e;
+            if constexpr (SMALL_SYN) {
+                if ((e = set_smem(k_synth<N, D, FPC_A, SYN_SHIFT>, SMEM_A)) != cudaSuccess) return e;
+                if ((e = set_smem(k_synth<N, D, FPC_A, SYN_PREP>, SMEM_A)) != cudaSuccess) return e;
+                if ((e = set_smem(k_synth<N, D, FPC_A, SYN_MULT>, SMEM_A)) != cudaSuccess) return e;
+            }
             if ((e = set_smem(k_analysis<N, D, FPC_A, ANA_SPECTRUM>, SMEM_A)) != cudaSuccess) return e;
             if ((e = set_smem(k_analysis<N, D, FPC_A, ANA_ACCUM>, SMEM_A)) != cudaSuccess) return e;
             return set_smem(k_output<N, D, FPC_A>, SMEM_A);
@@ -1037,6 +1046,18 @@ struct Launch {
                 k_synth_cl<N, CLS, SYN_PREP><<<CLS * p.n_fields, CG::NT, CG::SMEM, st>>>(p);
         } else {
             const int grid = (p.n_fields + FPC - 1) / FPC;
+            if constexpr (SMALL_SYN) {
+                if (grid < kSmallSynCtas) {
+                    const int ga = (p.n_fields + FPC_A - 1) / FPC_A;
+                    if (mode == SYN_SHIFT)
+                        k_synth<N, D, FPC_A, SYN_SHIFT><<<ga, BLOCK_A, SMEM_A, st>>>(p);
+                    else if (mode == SYN_MULT)
+                        k_synth<N, D, FPC_A, SYN_MULT><<<ga, BLOCK_A, SMEM_A, st>>>(p);
+                    else
+                        k_synth<N, D, FPC_A, SYN_PREP><<<ga, BLOCK_A, SMEM_A, st>>>(p);
+                    return;
+                }
+            }
             if (mode == SYN_SHIFT)
                 k_synth<N, D, FPC, SYN_SHIFT><<<grid, BLOCK, SMEM, st>>>(p);
             else if (mode == SYN_MULT)
@@ -1932,7 +1953,7 @@ boltz_status run_project(boltz_grid_s* g, const float* V, int r, const float* Q,
     const int count = r * r2;
     const float scale = (float)std::pow(2.0 * g->L / g->N, g->D);
     int slices;
-    if (g->n >= 512) {
+    if (g->n >= 512 && r > 8) {                             // small r: the CUDA-core kernels fill more SMs
         const int kpc = std::max(512, g->n / 64);           // n is a power of two: kpc divides it
         slices = g->n / kpc;
         ProfScope ps(g, BOLTZ_KCLASS_PROJECT, st);

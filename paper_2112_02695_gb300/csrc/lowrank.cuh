@@ -449,37 +449,30 @@ __global__ void __launch_bounds__(kQrSpreadThreads) k_qr_spread_f64(const double
     __syncthreads();
     if (!last) return;
     __threadfence();
-    {   // G = w sum of the partials: warp wp takes entries wp, wp + 8, ...; lanes over CTAs, then a shuffle tree
-        constexpr int NWP = kQrSpreadThreads / 32, EPW = (kQrSpreadPairs + NWP - 1) / NWP;
-        const int wp = t >> 5, lane = t & 31;
-        double acc[EPW];
-#pragma unroll
-        for (int k = 0; k < EPW; ++k) acc[k] = 0.0;
-        for (int c = lane; c < (int)gridDim.x; c += 32) {
-#pragma unroll
-            for (int k = 0; k < EPW; ++k) {
-                const int e = wp + NWP * k;
-                if (e < npairs) acc[k] += __ldcg(&part[(size_t)c * kQrSpreadPairs + e]);
-            }
+    {   // G = w sum of the partials.  An FP64 instruction costs a warp the same for one lane as for 32, so
+        // thread (slice, entry) sums the CTAs c = slice, slice + S, ... of one entry (whole warps busy),
+        // then one thread per entry adds the S slice sums in order.
+        __shared__ double sl[kQrSpreadThreads];
+        const int pad = (npairs + 31) & ~31, S = kQrSpreadThreads / pad;     // slices (>= 1: pad <= 160)
+        const int slice = t / pad, e = t % pad;
+        if (slice < S) {
+            double g = 0.0;
+            if (e < npairs)
+                for (int c = slice; c < (int)gridDim.x; c += S) g += __ldcg(&part[(size_t)c * kQrSpreadPairs + e]);
+            sl[slice * pad + e] = g;
         }
-#pragma unroll
-        for (int k = 0; k < EPW; ++k) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], o);
-        }
-        if (lane == 0) {
-#pragma unroll
-            for (int k = 0; k < EPW; ++k) {
-                int e = wp + NWP * k, a = 0;
-                if (e >= npairs) continue;
-                while (e >= r - a) {
-                    e -= r - a;
-                    ++a;
-                }
-                const int b = a + e;
-                G[a * r + b] = w * acc[k];
-                G[b * r + a] = w * acc[k];
+        __syncthreads();
+        if (t < npairs) {
+            double g = 0.0;
+            for (int k = 0; k < S; ++k) g += sl[k * pad + t];
+            int ee = t, a = 0;
+            while (ee >= r - a) {
+                ee -= r - a;
+                ++a;
             }
+            const int b = a + ee;
+            G[a * r + b] = w * g;
+            G[b * r + a] = w * g;
         }
     }
     __syncthreads();
@@ -754,17 +747,26 @@ __device__ __forceinline__ void jac_rotation(double al, double be, double ga, do
     s = sd * corr;
 }
 
-template <typename T>
+// Lane groups of LG lanes (8 for r <= 8, 4 for r <= 16), group g rotating
+// pair g of a round.  FP64: a sweep in which no pair had |<a_p, a_q>| above
+// 1e-8 |a_p| |a_q| ends the iteration (its rotations leave every inner product
+// near 1e-15 of the norms: the FP32 angle is good to ~1e-7 and the cross terms
+// are products of two such inner products), which saves the checking sweep.
+template <typename T, int LG>
 __device__ bool small_sweeps(T* A, T* V, int r, T tol, int max_sweeps) {
-    const int lane = threadIdx.x & 31, g = lane >> 2, u = lane & 3;
+    const int lane = threadIdx.x & 31, g = lane / LG, u = lane % LG;
     const int m = (r + 1) & ~1;
     const T tol2 = tol * tol;
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-        int rotated = 0;
+        int rotated = 0, big = 0;
         for (int round = 0; round < m - 1; ++round) {
             int p = 0, q = r;                                // groups past m / 2 stay idle (q >= r)
             if (g < m / 2) {
-                auto slot = [&](int pos) { return pos == 0 ? 0 : 1 + (pos - 1 + round) % (m - 1); };
+                auto slot = [&](int pos) {
+                    int x = pos - 1 + round;
+                    if (x >= m - 1) x -= m - 1;
+                    return pos == 0 ? 0 : 1 + x;
+                };
                 p = slot(g);
                 q = slot(m - 1 - g);
                 if (p > q) {
@@ -775,7 +777,7 @@ __device__ bool small_sweeps(T* A, T* V, int r, T tol, int max_sweeps) {
             }
             T al = T(0), be = T(0), ga = T(0);
             if (q < r) {
-                for (int i = u; i < r; i += 4) {
+                for (int i = u; i < r; i += LG) {
                     const T x = A[p * kSvdSmallR + i], y = A[q * kSvdSmallR + i];
                     al = fma(x, x, al);
                     be = fma(y, y, be);
@@ -783,15 +785,17 @@ __device__ bool small_sweeps(T* A, T* V, int r, T tol, int max_sweeps) {
                 }
             }
 #pragma unroll
-            for (int o = 1; o < 4; o <<= 1) {                // every lane takes part
+            for (int o = 1; o < LG; o <<= 1) {               // every lane takes part
                 al += __shfl_xor_sync(0xffffffffu, al, o);
                 be += __shfl_xor_sync(0xffffffffu, be, o);
                 ga += __shfl_xor_sync(0xffffffffu, ga, o);
             }
-            if (q < r && ga != T(0) && ga * ga > tol2 * (al * be)) {
+            const T g2 = ga * ga, ab = al * be;
+            if (q < r && ga != T(0) && g2 > tol2 * ab) {
+                if (sizeof(T) == 8 && g2 > T(1e-16) * ab) big = 1;
                 T c, sn;
                 jac_rotation(al, be, ga, c, sn);
-                for (int i = u; i < r; i += 4) {
+                for (int i = u; i < r; i += LG) {
                     const T x = A[p * kSvdSmallR + i], y = A[q * kSvdSmallR + i];
                     A[p * kSvdSmallR + i] = c * x - sn * y;
                     A[q * kSvdSmallR + i] = sn * x + c * y;
@@ -804,6 +808,7 @@ __device__ bool small_sweeps(T* A, T* V, int r, T tol, int max_sweeps) {
             __syncwarp();
         }
         if (!__any_sync(0xffffffffu, rotated)) return true;
+        if (sizeof(T) == 8 && !__any_sync(0xffffffffu, big)) return true;
     }
     return false;
 }
@@ -827,7 +832,8 @@ __global__ void __launch_bounds__(32) k_svd_small_f64(const double* __restrict__
         Vf[e] = (c == i && c < r) ? 1.f : 0.f;
     }
     __syncwarp();
-    (void)small_sweeps<float>(Af, Vf, r, 1e-6f, kSvdMaxSweeps);
+    if (r <= 8) (void)small_sweeps<float, 8>(Af, Vf, r, 1e-6f, kSvdMaxSweeps);
+    else (void)small_sweeps<float, 4>(Af, Vf, r, 1e-6f, kSvdMaxSweeps);
     for (int e = t; e < R * R; e += 32) V[e] = (double)Vf[e];
     __syncwarp();
     for (int it = 0; it < 2; ++it) {                 // V <- V (I - E/2), E = V^T V - I
@@ -851,19 +857,21 @@ __global__ void __launch_bounds__(32) k_svd_small_f64(const double* __restrict__
         }
         __syncwarp();
     }
-    for (int e = t; e < R * R; e += 32) {            // A = S V
-        const int c = e / R, i = e % R;
+    for (int e = t; e < r * r; e += 32) {            // A = S V (only the leading r x r block is used)
+        const int c = e / r, i = e % r;
         double a = 0.0;
-        if (c < r && i < r)
-            for (int k = 0; k < r; ++k) a = fma(Sm[k * R + i], V[c * R + k], a);
-        A[e] = a;
+        for (int k = 0; k < r; ++k) a = fma(Sm[k * R + i], V[c * R + k], a);
+        A[c * R + i] = a;
     }
     __syncwarp();
-    const bool converged = small_sweeps<double>(A, V, r, 1e-15, kSvdMaxSweeps);
+    const bool converged = r <= 8 ? small_sweeps<double, 8>(A, V, r, 1e-15, kSvdMaxSweeps)
+                                  : small_sweeps<double, 4>(A, V, r, 1e-15, kSvdMaxSweeps);
+    __shared__ double inv_sv[R];
     if (t < r) {
         double nn = 0.0;
         for (int i = 0; i < r; ++i) nn = fma(A[t * R + i], A[t * R + i], nn);
         sv[t] = sqrt(nn);
+        inv_sv[t] = sv[t] > 0.0 ? 1.0 / sv[t] : 0.0;
     }
     __syncwarp();
     if (t == 0) {
@@ -886,10 +894,9 @@ __global__ void __launch_bounds__(32) k_svd_small_f64(const double* __restrict__
     for (int e = t; e < r * r; e += 32) {
         const int i = e / r, k = e % r;
         const int c = order[k];
-        const double sc = sv[c];
-        U[e] = sc > 0.0 ? A[c * R + i] / sc : 0.0;
+        U[e] = A[c * R + i] * inv_sv[c];
         Qm[e] = V[c * R + i];
-        if (i == 0) sigma[k] = sc;
+        if (i == 0) sigma[k] = sv[c];
     }
 }
 
