@@ -19,6 +19,7 @@
 #include <set>
 #include <string>
 #include <tuple>
+#include <type_traits>
 #include <utility>
 #include <vector>
 
@@ -55,6 +56,7 @@ struct ChunkPlan {
     std::vector<int> out_start;                   // [U+1]
     std::vector<int4> outs;                       // (e, jloc, lloc, 0)
     int U = 0;
+    int split = 1;                                // Carleman form: direction splits of the contraction
     // offsets of this chunk's descriptors inside the device plan buffer (bytes)
     size_t off_inputs = 0, off_tiles[3] = {0, 0, 0}, off_start = 0, off_outs = 0;
 };
@@ -821,9 +823,17 @@ boltz_status build_plan_carleman(const boltz_grid_s* g, const int32_t* pj, const
         c.out_start[c.U] = (int)c.outs.size();
         plan.chunks.push_back(std::move(c));
     }
+    // a chunk of few voxel-chunk x tile blocks splits the direction pairs over
+    // up to 8 blocks (at least two pairs each) to fill more SMs; the partial
+    // sums are added by the output kernel
+    size_t max_pu = 0;
     for (auto& c : plan.chunks) {
         plan.max_nc = std::max(plan.max_nc, (int)c.inputs.size());
         plan.max_U = std::max(plan.max_U, c.U);
+        const long long blocks =
+            (long long)(g->n / voxel_chunk(g->N, g->D)) * (long long)(c.tiles[TILE_FULL].size() + c.tiles[TILE_LIST].size());
+        c.split = (int)std::max<long long>(1, std::min<long long>({8, (long long)(g->M / 2) / 2, 152 / std::max(1LL, blocks)}));
+        max_pu = std::max(max_pu, (size_t)c.split * c.U);
     }
     plan.nq = 1;
     size_t off = 0;
@@ -845,7 +855,7 @@ boltz_status build_plan_carleman(const boltz_grid_s* g, const int32_t* pj, const
     plan.off_A = w;
     w = align_up(w + size_t(g->M) * plan.max_nc * field_bytes, 256);
     plan.off_P = w;
-    w = align_up(w + size_t(plan.max_U) * field_bytes, 256);
+    w = align_up(w + max_pu * field_bytes, 256);
     plan.off_qhat = w;
     plan.off_fN = w;
     w = align_up(w + size_t(plan.max_nc) * field_bytes, 256);
@@ -1286,7 +1296,7 @@ struct ContractLaunchA {
     static constexpr size_t SMEM = size_t(STAGES) * ROWS * VC * sizeof(float);
     static cudaError_t prepare() { return set_smem(k_contract_pipe<KIND, TJ, TL, VC, STAGES, float, true>, SMEM); }
     static void launch(const ConParams& cp, int n_tiles, cudaStream_t st) {
-        dim3 grid(cp.n / VC, n_tiles, 1);
+        dim3 grid(cp.n / VC, n_tiles, cp.n_split > 1 ? cp.n_split : 1);
         k_contract_pipe<KIND, TJ, TL, VC, STAGES, float, true><<<grid, VC, SMEM, st>>>(cp);
     }
 };
@@ -1652,6 +1662,7 @@ boltz_status run_carleman(boltz_grid_s* g, const float2* spectra, int n_inputs, 
         cp.n_c = nc;
         cp.U = c.U;
         cp.n = g->n;
+        cp.n_split = c.split;
         for (int k : {TILE_FULL, TILE_LIST}) {
             if (c.tiles[k].empty()) continue;
             cp.tiles = reinterpret_cast<const Tile*>(ws + plan.off_plan + c.off_tiles[k]);
@@ -1664,7 +1675,7 @@ boltz_status run_carleman(boltz_grid_s* g, const float2* spectra, int n_inputs, 
         k_carleman_output<<<grid, 256, 0, st>>>(Pbuf, fN, fN + size_t(nc) * g->n,
                                                  reinterpret_cast<const int*>(ws + plan.off_plan + c.off_start),
                                                  reinterpret_cast<const int4*>(ws + plan.off_plan + c.off_outs), Q_out,
-                                                 g->n, g->d_err);
+                                                 g->n, g->d_err, c.split, c.U);
     }
     BZ_CUDA(cudaGetLastError());
     return BOLTZ_OK;
@@ -3364,22 +3375,27 @@ boltz_status lr_append(boltz_shock s, const double* V, int r, int* rh_out, cudaS
     int rh = r;
     if (r + s->rb <= kAugR && s->rb <= 2) {
         const int G = (int)std::min<size_t>(std::max<size_t>((nv + kAugT - 1) / kAugT, 1), kAugCtas);
+        // RM: the smallest instantiated bound >= the columns (unused slots still cost FP64 issue)
+        auto with_rm = [](int rc, auto&& f) {
+            if (rc <= 2) f(std::integral_constant<int, 2>{});
+            else if (rc <= 4) f(std::integral_constant<int, 4>{});
+            else if (rc <= 6) f(std::integral_constant<int, 6>{});
+            else if (rc <= 8) f(std::integral_constant<int, 8>{});
+            else if (rc <= 16) f(std::integral_constant<int, 16>{});
+            else f(std::integral_constant<int, 32>{});
+        };
         auto start = [&](int rc, const double* src, int scale_prev, int k) {
-            if (rc <= 8) k_aug_start<8><<<G, kAugT, 0, st>>>(s->Vh, rc, nv, s->wv, src, scale_prev, s->nrm, k, s->aug);
-            else if (rc <= 16) k_aug_start<16><<<G, kAugT, 0, st>>>(s->Vh, rc, nv, s->wv, src, scale_prev, s->nrm, k, s->aug);
-            else k_aug_start<32><<<G, kAugT, 0, st>>>(s->Vh, rc, nv, s->wv, src, scale_prev, s->nrm, k, s->aug);
+            with_rm(rc, [&](auto RMc) {
+                k_aug_start<decltype(RMc)::value>
+                    <<<G, kAugT, 0, st>>>(s->Vh, rc, nv, s->wv, src, scale_prev, s->nrm, k, s->aug);
+            });
         };
         auto update = [&](int rc, int k, int* skip) {
-            if (rc <= 8) {
-                k_aug_update<8, 0><<<G, kAugT, 0, st>>>(s->Vh, rc, nv, s->wv, s->nrm, k, skip, s->aug);
-                k_aug_update<8, 1><<<G, kAugT, 0, st>>>(s->Vh, rc, nv, s->wv, s->nrm, k, skip, s->aug);
-            } else if (rc <= 16) {
-                k_aug_update<16, 0><<<G, kAugT, 0, st>>>(s->Vh, rc, nv, s->wv, s->nrm, k, skip, s->aug);
-                k_aug_update<16, 1><<<G, kAugT, 0, st>>>(s->Vh, rc, nv, s->wv, s->nrm, k, skip, s->aug);
-            } else {
-                k_aug_update<32, 0><<<G, kAugT, 0, st>>>(s->Vh, rc, nv, s->wv, s->nrm, k, skip, s->aug);
-                k_aug_update<32, 1><<<G, kAugT, 0, st>>>(s->Vh, rc, nv, s->wv, s->nrm, k, skip, s->aug);
-            }
+            with_rm(rc, [&](auto RMc) {
+                constexpr int RM = decltype(RMc)::value;
+                k_aug_update<RM, 0><<<G, kAugT, 0, st>>>(s->Vh, rc, nv, s->wv, s->nrm, k, skip, s->aug);
+                k_aug_update<RM, 1><<<G, kAugT, 0, st>>>(s->Vh, rc, nv, s->wv, s->nrm, k, skip, s->aug);
+            });
         };
         if constexpr (KEEP_ALL) {
             // both vectors, the first scaled at the start of the second

@@ -878,12 +878,13 @@ struct Tile {
 template <typename R>
 struct ConParamsT {
     const R* A;            // [nq][M][n_c][n]
-    R* P;                  // [nq][U][n]
+    R* P;                  // [nq][U][n]; the asymmetric sum: [n_split][U][n] partial sums
     const Tile* tiles;
     const R* w;            // [M/2] weight of each antipodal direction pair
     const int2* dpair;     // [M/2] (p, antipode(p)) with p < antipode(p)
     int* err;              // device error word
     int n_dpair, M, n_c, U, n;
+    int n_split;           // asymmetric sum: direction pairs split over gridDim.z = n_split blocks (>= 1)
 };
 using ConParams = ConParamsT<float>;
 
@@ -926,13 +927,16 @@ __global__ void __launch_bounds__(VC, 1) k_contract_pipe(ConParamsT<R> C) {
     const int nch = C.n / VC;                                     // VC is the layout's voxel chunk
     const size_t blk = (size_t)C.n_c * VC;                        // one (slot, chunk) block
     // radial node of the block: the last node first, since its fields were the
-    // last ones written and are the likeliest to still be in L2
-    const int qz = (int)(gridDim.z - 1 - blockIdx.z);
+    // last ones written and are the likeliest to still be in L2.  The
+    // asymmetric sum has no radial nodes: blockIdx.z selects its share
+    // [k0, k1) of the direction pairs instead, summed into partial P block z.
+    const int qz = ASYM ? 0 : (int)(gridDim.z - 1 - blockIdx.z);
     // block of (slot = qz*M + p, chunk = blockIdx.x)
     auto block_of = [&](int p) -> const R* {
         return C.A + (((size_t)qz * C.M + p) * nch + blockIdx.x) * blk;
     };
-    const int npairs = C.n_dpair;
+    const int k0 = ASYM ? (int)(((long long)C.n_dpair * blockIdx.z) / gridDim.z) : 0;
+    const int npairs = ASYM ? (int)(((long long)C.n_dpair * (blockIdx.z + 1)) / gridDim.z) : C.n_dpair;
     if (t == 0) {
         for (int s = 0; s < STAGES; ++s) mbar_init(&bars[s], 1);
         mbar_init_fence();
@@ -940,7 +944,7 @@ __global__ void __launch_bounds__(VC, 1) k_contract_pipe(ConParamsT<R> C) {
     __syncthreads();
     // rows of one direction: TRI j0..j0+TJ; FULL j0..j0+TJ then l0..l0+TL; LIST ja[], lb[]
     auto issue = [&](int k) {                                     // warp 0 only
-        const int s = k % STAGES;
+        const int s = (k - k0) % STAGES;
         const int2 d = C.dpair[k];
         R* dstp = sbuf + (size_t)s * ROWS * VC;
         if (lane == 0) mbar_arrive_expect_tx(&bars[s], STAGE_BYTES);
@@ -972,19 +976,19 @@ __global__ void __launch_bounds__(VC, 1) k_contract_pipe(ConParamsT<R> C) {
         }
     };
     if (warp == 0)
-        for (int k = 0; k < STAGES && k < npairs; ++k) issue(k);
+        for (int k = k0; k < k0 + STAGES && k < npairs; ++k) issue(k);
     R acc[NACC];
 #pragma unroll
     for (int i = 0; i < NACC; ++i) acc[i] = R(0);
-    for (int k = 0; k < npairs; ++k) {
-        const int s = k % STAGES;
-        const bool ok = mbar_wait_bounded(&bars[s], (uint32_t)(k / STAGES) & 1u);
+    for (int k = k0; k < npairs; ++k) {
+        const int s = (k - k0) % STAGES;
+        const bool ok = mbar_wait_bounded(&bars[s], (uint32_t)((k - k0) / STAGES) & 1u);
         if (__syncthreads_or(!ok)) {
             // a copy did not land: record it, wait (bounded) for the copies still in flight, leave
             if (t == 0) {
                 atomicOr(C.err, kErrTimeout);
                 for (int k2 = k; k2 < npairs && k2 < k + STAGES; ++k2)
-                    (void)mbar_wait_bounded(&bars[k2 % STAGES], (uint32_t)(k2 / STAGES) & 1u);
+                    (void)mbar_wait_bounded(&bars[(k2 - k0) % STAGES], (uint32_t)((k2 - k0) / STAGES) & 1u);
             }
             __syncthreads();
             return;
@@ -1041,7 +1045,7 @@ __global__ void __launch_bounds__(VC, 1) k_contract_pipe(ConParamsT<R> C) {
         }
     }
     const size_t n = (size_t)C.n;
-    R* __restrict__ Pq = C.P + (size_t)qz * C.U * n + (size_t)blockIdx.x * VC + t;
+    R* __restrict__ Pq = C.P + (size_t)(ASYM ? blockIdx.z : qz) * C.U * n + (size_t)blockIdx.x * VC + t;
     const int cnt = (KIND == TILE_LIST) ? tl.count : NACC;
 #pragma unroll
     for (int i = 0; i < NACC; ++i)
@@ -1051,16 +1055,21 @@ __global__ void __launch_bounds__(VC, 1) k_contract_pipe(ConParamsT<R> C) {
 // ------------------------------------------------------------------ Carleman-form output
 // Q[e](v) = P[u](v) - f_N[l](v) Lambda[j](v) for every ordered pair e = (j, l)
 // of slot u (no forward transform: the gain's grid values are the weighted sum
-// of products itself).  Blocks (voxel quarter-chunk, slot).
+// of products itself), P the sum of the n_split partial blocks [z][U][n] of
+// the contraction.  Blocks (voxel quarter-chunk, slot).
 __global__ void __launch_bounds__(256) k_carleman_output(const float* __restrict__ Pg, const float* __restrict__ fN,
                                                           const float* __restrict__ lam,
                                                           const int* __restrict__ out_start,
                                                           const int4* __restrict__ outs, float* __restrict__ Q, int n,
-                                                          int* __restrict__ err) {
+                                                          int* __restrict__ err, int n_split = 1, int U = 0) {
     const int u = blockIdx.y;
     const int v4 = blockIdx.x * 256 + threadIdx.x;           // float4 index
     if (v4 * 4 >= n) return;
-    const float4 p = __ldg(reinterpret_cast<const float4*>(Pg + (size_t)u * n) + v4);
+    float4 p = __ldg(reinterpret_cast<const float4*>(Pg + (size_t)u * n) + v4);
+    for (int z = 1; z < n_split; ++z) {                      // partial sums of the direction splits, in order
+        const float4 q = __ldg(reinterpret_cast<const float4*>(Pg + ((size_t)z * U + u) * n) + v4);
+        p = make_float4(p.x + q.x, p.y + q.y, p.z + q.z, p.w + q.w);
+    }
     for (int o = out_start[u]; o < out_start[u + 1]; ++o) {
         const int4 e = outs[o];
         const float4 a = __ldg(reinterpret_cast<const float4*>(fN + (size_t)e.z * n) + v4);
