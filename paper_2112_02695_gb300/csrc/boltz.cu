@@ -2199,21 +2199,24 @@ void launch_qr(const double* W, int r, int n, double w, double* Y, double* R, ch
     k_apply_rinv_f64<RMAX><<<grid, kLrThreads, 0, st>>>(Y, Rinv, r, n, Y);
 }
 
-// Cholesky-QR2 of boltz_qr_f64.  The spread kernels' tickets are left at zero
-// by every call; zero_tickets clears them first (a workspace of unknown
-// contents).
+// Cholesky-QR2 of boltz_qr_f64.  tickets: two counters of the spread kernels
+// that are zero and that nothing else writes (every call leaves them at zero);
+// null puts them at the end of the spread layout in ws and clears them first
+// (a workspace of unknown contents, which the multi-kernel path also writes).
 boltz_status qr_f64_launch(const double* W, int r, int n, double w, double* Y, double* R, char* ws, int* info,
-                           cudaStream_t st, bool zero_tickets) {
+                           cudaStream_t st, unsigned* tickets) {
     boltz_status s = ensure_lowrank_attrs();
     if (s != BOLTZ_OK) return s;
     BZ_CUDA(cudaMemsetAsync(info, 0, sizeof(int), st));
     if (r <= kQrSpreadR && n <= kQrSpreadMaxN) {      // Gram sums and applications over up to 152 CTAs
         const int rows = qr_spread_rows(n), grid = (n + rows - 1) / rows;
         double* wsd = reinterpret_cast<double*>(ws);
-        if (zero_tickets)
-            BZ_CUDA(cudaMemsetAsync(ws + qr_spread_ticket_offset(), 0, 2 * sizeof(unsigned), st));
-        k_qr_spread_f64<0><<<grid, kQrSpreadThreads, 0, st>>>(W, r, n, w, rows, Y, R, wsd, info);
-        k_qr_spread_f64<1><<<grid, kQrSpreadThreads, 0, st>>>(W, r, n, w, rows, Y, R, wsd, info);
+        if (!tickets) {
+            tickets = reinterpret_cast<unsigned*>(ws + qr_spread_ticket_offset());
+            BZ_CUDA(cudaMemsetAsync(tickets, 0, 2 * sizeof(unsigned), st));
+        }
+        k_qr_spread_f64<0><<<grid, kQrSpreadThreads, 0, st>>>(W, r, n, w, rows, Y, R, wsd, tickets, info);
+        k_qr_spread_f64<1><<<grid, kQrSpreadThreads, 0, st>>>(W, r, n, w, rows, Y, R, wsd, tickets, info);
         k_qr_spread_apply<<<(n + kQrSpreadThreads - 1) / kQrSpreadThreads, kQrSpreadThreads, 0, st>>>(Y, r, n, wsd);
     } else if (r <= 16) {
         launch_qr<16>(W, r, n, w, Y, R, ws, info, st);
@@ -3045,7 +3048,7 @@ boltz_status boltz_qr_f64(const double* W, int r, int n, double w, double* Y, do
     if (r < 1 || r > 64 || n < r || !(w > 0) || !std::isfinite(w) || !W || !Y || !R || !workspace || !info)
         return BOLTZ_EINVAL;
     return qr_f64_launch(W, r, n, w, Y, R, static_cast<char*>(workspace), info,
-                         reinterpret_cast<cudaStream_t>(stream), true);
+                         reinterpret_cast<cudaStream_t>(stream), nullptr);
 }
 
 boltz_status boltz_svd_truncate_f64(const double* S, int r, double drop_tol, double* U, double* sigma, double* Q,
@@ -3103,7 +3106,8 @@ struct boltz_shock_s {
     void* qr_ws = nullptr;
     int* d_int = nullptr;                 // [0] QR info (K), [1] QR info (L), [2] r_keep, [3] SVD info,
                                           // [4] skip bits of a replayed step (1: a boundary vector not
-                                          // kept, 2: a QR or the rank failed), [8] k_sh_change's ticket
+                                          // kept, 2: a QR or the rank failed), [8] k_sh_change's ticket,
+                                          // [10..11] the spread QR's tickets
     double* d_tol = nullptr;              // drop_tol of a replayed step
     boltz_dev::AugState* aug = nullptr;   // scratch of the basis augmentation
     // replayed steps: one CUDA graph per (rank, X, S, V, dt) seen twice, both boundary
@@ -3189,8 +3193,9 @@ boltz_status boltz_shock_create(boltz_grid g, int n_x, double L_x, const double*
         *pt.first = s->mem + off;
         off = align_up(off + pt.second, 256);
     }
-    // the tickets of the spread QR and of k_sh_change start at zero (each launch leaves them so)
-    if (cudaMemset(s->d_int, 0, 64) != cudaSuccess || cudaMemset(s->qr_ws, 0, qr_bytes) != cudaSuccess ||
+    // the tickets of the spread QR, k_sh_change and the augmentation start at zero (each launch
+    // leaves them so)
+    if (cudaMemset(s->d_int, 0, 64) != cudaSuccess ||
         cudaMemset(s->aug, 0, sizeof(boltz_dev::AugState)) != cudaSuccess) {
         boltz_shock_destroy(s);
         return BOLTZ_ECUDA;
@@ -3301,7 +3306,7 @@ boltz_status lr_core(boltz_shock s, const double* X, const double* S, int r, int
     k_sh_kupdate<<<sh_grid((size_t)rh * nx), T, 0, st>>>(s->K, s->C32, s->Ap, s->Am, s->gL, s->gR, rh, nx, dt, s->dx,
                                                          s->K1);
     if ((rs = qr_f64_launch(s->K1, rh, nx, s->dx, s->X1, s->S1, static_cast<char*>(s->qr_ws), s->d_int, st,
-                            false)) != BOLTZ_OK)
+                            reinterpret_cast<unsigned*>(s->d_int + 10))) != BOLTZ_OK)
         return rs;
     // 2. S-step (Sec. 2.4 S-step): transport through the updated K, collision term with S1
     sh_ghosts(s, s->K1, rh, st);
@@ -3320,7 +3325,7 @@ boltz_status lr_core(boltz_shock s, const double* X, const double* S, int r, int
     if ((rs = boltz_lstep_collision(s->Q32, rh, s->Cs32, nv, s->G32, stream)) != BOLTZ_OK) return rs;
     k_sh_lupdate<<<sh_grid((size_t)rh * nv), T, 0, st>>>(s->L, s->Vh, s->v1, s->Bp, s->Bm, s->G32, rh, nv, dt, s->L1);
     if ((rs = qr_f64_launch(s->L1, rh, nv, s->wv, s->Vn, s->R, static_cast<char*>(s->qr_ws), s->d_int + 1, st,
-                            false)) != BOLTZ_OK)
+                            reinterpret_cast<unsigned*>(s->d_int + 10))) != BOLTZ_OK)
         return rs;
     k_sh_transpose<<<1, T, 0, st>>>(s->R, rh, rh, s->Sn);          // L_i = sum_j R_ji V'_j
     // change of f over the step from the increments (Sec. 5.1), before the drop

@@ -350,7 +350,8 @@ __host__ __device__ inline int qr_spread_rows(int n) {
     return rows < 16 ? 16 : rows;
 }
 
-// workspace: partial Grams [ctas][kQrSpreadPairs], X1, X2, R1 [16 * 16] each, two tickets
+// workspace: partial Grams [ctas][kQrSpreadPairs], X1, X2, R1 [16 * 16] each, then room for two
+// tickets (used when the caller passes none of its own)
 __host__ __device__ constexpr size_t qr_spread_ticket_offset() {
     return (size_t(kQrSpreadCtas) * kQrSpreadPairs + 3 * kQrSpreadR * kQrSpreadR) * sizeof(double);
 }
@@ -390,10 +391,12 @@ __device__ inline int chol_inv_warp(const double* G, int r, double* Rs, double* 
     return 0;
 }
 
+// ticket: two counters, zero before the first launch and left at zero.
 template <int PASS>
 __global__ void __launch_bounds__(kQrSpreadThreads) k_qr_spread_f64(const double* W, int r, int n, double w, int rows,
                                                                    double* Y, double* __restrict__ R,
-                                                                   double* __restrict__ ws, int* __restrict__ info) {
+                                                                   double* __restrict__ ws, unsigned* __restrict__ ticket,
+                                                                   int* __restrict__ info) {
     __shared__ double Ws[kQrSpreadR * kQrSpreadRows];     // this CTA's entries, [row i][entry]
     __shared__ double Xin[kQrSpreadR * kQrSpreadR];
     __shared__ double G[kQrSpreadR * kQrSpreadR], Rs[kQrSpreadR * kQrSpreadR], Xs[kQrSpreadR * kQrSpreadR];
@@ -403,7 +406,6 @@ __global__ void __launch_bounds__(kQrSpreadThreads) k_qr_spread_f64(const double
     double* X1 = ws + size_t(kQrSpreadCtas) * kQrSpreadPairs;
     double* X2 = X1 + kQrSpreadR * kQrSpreadR;
     double* R1 = X2 + kQrSpreadR * kQrSpreadR;
-    unsigned* ticket = reinterpret_cast<unsigned*>(reinterpret_cast<char*>(ws) + qr_spread_ticket_offset());
     const int t = threadIdx.x, v0 = blockIdx.x * rows, nr = min(rows, n - v0);
     const int npairs = r * (r + 1) / 2;
     if (PASS == 1) {
@@ -749,9 +751,12 @@ __device__ __forceinline__ void jac_rotation(double al, double be, double ga, do
 
 // Lane groups of LG lanes (8 for r <= 8, 4 for r <= 16), group g rotating
 // pair g of a round.  FP64: a sweep in which no pair had |<a_p, a_q>| above
-// 1e-8 |a_p| |a_q| ends the iteration (its rotations leave every inner product
-// near 1e-15 of the norms: the FP32 angle is good to ~1e-7 and the cross terms
-// are products of two such inner products), which saves the checking sweep.
+// 1e-8 |a_p| |a_q| and every rotation was small (|sin| <= 1e-7) ends the
+// iteration: each rotation leaves its own pair near 1e-15 of the norms (the
+// FP32 angle is good to ~1e-7) and moves the other pairs' inner products by
+// at most |sin| times theirs, which saves the checking sweep.  (Columns of
+// nearly equal norm rotate by ~45 degrees however small their inner product,
+// so such sweeps run to the check.)
 template <typename T, int LG>
 __device__ bool small_sweeps(T* A, T* V, int r, T tol, int max_sweeps) {
     const int lane = threadIdx.x & 31, g = lane / LG, u = lane % LG;
@@ -792,9 +797,9 @@ __device__ bool small_sweeps(T* A, T* V, int r, T tol, int max_sweeps) {
             }
             const T g2 = ga * ga, ab = al * be;
             if (q < r && ga != T(0) && g2 > tol2 * ab) {
-                if (sizeof(T) == 8 && g2 > T(1e-16) * ab) big = 1;
                 T c, sn;
                 jac_rotation(al, be, ga, c, sn);
+                if (sizeof(T) == 8 && (g2 > T(1e-16) * ab || fabs(sn) > T(1e-7))) big = 1;
                 for (int i = u; i < r; i += LG) {
                     const T x = A[p * kSvdSmallR + i], y = A[q * kSvdSmallR + i];
                     A[p * kSvdSmallR + i] = c * x - sn * y;

@@ -131,6 +131,55 @@ def test_svd_truncate_f64(B, r):
     assert np.max(np.abs(U[:, big].T @ U[:, big] - np.eye(int(big.sum())))) < 1e-10
 
 
+@pytest.mark.parametrize("r,n", [(16, 38912), (16, 38913), (5, 17), (3, 3000), (9, 1000), (2, 2)])
+def test_qr_f64_sizes_at_the_path_limits(B, r, n):
+    """Cholesky-QR2 at the edges of the spread path (r <= 16, n <= 152 x 256 =
+    38912: entries per CTA = max(16, ceil(n / 152)), a ragged last CTA) and
+    just past it (the multi-kernel path), against the oracle."""
+    import torch
+    from oracle import lowrank as LR
+    rng = np.random.default_rng(500 + r + n)
+    W = rng.standard_normal((r, n)) * np.exp(0.5 * rng.standard_normal((r, 1)))
+    w = 0.03
+    Y, R, info = B.boltz_qr_f64(torch.tensor(W, device="cuda"), w)
+    Y, R = Y.cpu().numpy(), R.cpu().numpy()
+    assert int(info.item()) == 0
+    Yo, Ro = LR.qr_weighted(W, w)
+    assert np.max(np.abs(R - Ro)) / np.max(np.abs(Ro)) < 1e-11
+    assert np.max(np.abs(Y - Yo)) / np.max(np.abs(Yo)) < 1e-11
+    assert np.max(np.abs(w * Y @ Y.T - np.eye(r))) < 1e-12
+
+
+@pytest.mark.parametrize("r,spectrum", [(8, "repeated"), (16, "repeated"), (5, "clustered"), (12, "clustered"),
+                                        (2, "repeated"), (3, "rank1")])
+def test_svd_truncate_f64_repeated_and_clustered_values(B, r, spectrum):
+    """Equal and nearly equal singular values (Jacobi pairs of equal norms,
+    rotations of about 45 degrees), and a rank-one matrix: the one-warp SVD's
+    FP32-derived angles and its early end of the FP64 sweeps still give
+    orthonormal factors, sigma to 1e-12 and U Sigma Q^T = S to 1e-12."""
+    import torch
+    rng = np.random.default_rng(600 + r)
+    U0, _ = np.linalg.qr(rng.standard_normal((r, r)))
+    Q0, _ = np.linalg.qr(rng.standard_normal((r, r)))
+    if spectrum == "repeated":
+        s0 = np.array([3.0] * (r // 2) + [1.0] * (r - r // 2))
+    elif spectrum == "clustered":
+        s0 = 2.0 + 1e-9 * np.arange(r)[::-1]
+    else:
+        s0 = np.array([5.0] + [0.0] * (r - 1))
+    S = U0 @ np.diag(s0) @ Q0.T
+    U, sig, Qm, rk, info = B.boltz_svd_truncate_f64(torch.tensor(S, device="cuda"), 0.5)
+    U, sig, Qm = U.cpu().numpy(), sig.cpu().numpy(), Qm.cpu().numpy()
+    assert int(info.item()) == 0
+    so = np.sort(s0)[::-1]
+    assert np.max(np.abs(sig - so)) <= 1e-12 * so[0]
+    assert int(rk.item()) == int(np.sum(so >= 0.5))
+    assert np.max(np.abs(U @ np.diag(sig) @ Qm.T - S)) <= 1e-12 * so[0]
+    assert np.max(np.abs(Qm.T @ Qm - np.eye(r))) < 1e-12
+    big = sig > 1e-9 * sig[0]
+    assert np.max(np.abs(U[:, big].T @ U[:, big] - np.eye(int(big.sum())))) < 1e-11
+
+
 def test_drop_step_end_to_end(B):
     """Sec. 3.2 on the GPU: SVD of S, keep sigma >= drop_tol, rotate X and V;
     the truncated factorisation X_bar S_bar V_bar^T differs from X S V^T by at
