@@ -3072,7 +3072,8 @@ boltz_status boltz_basis_rotate_f64(const double* X, int r, int n, const double*
     if (!X || !U || !X_out || X_out == X) return BOLTZ_EINVAL;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const int grid = (n + kLrThreads - 1) / kLrThreads;
-    if (r <= 16) k_rotate_f64<16><<<grid, kLrThreads, 0, st>>>(X, U, r, r_new, n, X_out);
+    if (r <= 8) k_rotate_f64<8><<<grid, kLrThreads, 0, st>>>(X, U, r, r_new, n, X_out);
+    else if (r <= 16) k_rotate_f64<16><<<grid, kLrThreads, 0, st>>>(X, U, r, r_new, n, X_out);
     else if (r <= 32) k_rotate_f64<32><<<grid, kLrThreads, 0, st>>>(X, U, r, r_new, n, X_out);
     else k_rotate_f64<64><<<grid, kLrThreads, 0, st>>>(X, U, r, r_new, n, X_out);
     BZ_CUDA(cudaGetLastError());
@@ -3098,7 +3099,7 @@ struct boltz_shock_s {
     double *Vh = nullptr, *K = nullptr, *K1 = nullptr, *X1 = nullptr, *S1 = nullptr, *S2 = nullptr, *L = nullptr,
            *L1 = nullptr, *Kt = nullptr, *Vn = nullptr, *R = nullptr, *Sn = nullptr, *U = nullptr, *Qm = nullptr,
            *sig = nullptr, *Ap = nullptr, *Am = nullptr, *Pl = nullptr, *Pr = nullptr, *bl = nullptr,
-           *br = nullptr, *gL = nullptr, *gR = nullptr, *Bp = nullptr, *Bm = nullptr, *cvec = nullptr,
+           *br = nullptr, *Bp = nullptr, *Bm = nullptr, *cvec = nullptr,
            *nrm = nullptr, *Pk = nullptr, *Gv = nullptr, *nk = nullptr, *nl = nullptr, *errd = nullptr;
     float *V32 = nullptr, *Q32 = nullptr, *T32 = nullptr, *K32 = nullptr, *C32 = nullptr, *E32 = nullptr,
           *S32 = nullptr, *D32 = nullptr, *Cs32 = nullptr, *G32 = nullptr;
@@ -3134,11 +3135,6 @@ namespace {
 
 int sh_grid(size_t n) { return (int)std::min<size_t>((n + boltz_dev::kShT - 1) / boltz_dev::kShT, 4096); }
 
-// Upwind boundary values of K (Sec. 2.3): needs the velocity Grams of the current basis.
-void sh_ghosts(boltz_shock s, const double* Kx, int r, cudaStream_t st) {
-    boltz_dev::k_sh_ghosts<<<1, 64, 0, st>>>(Kx, r, s->n_x, s->Pl, s->Pr, s->bl, s->br, s->gL, s->gR);
-}
-
 }  // namespace
 
 extern "C" {
@@ -3172,7 +3168,7 @@ boltz_status boltz_shock_create(boltz_grid g, int n_x, double L_x, const double*
         {(void**)&s->U, rm * rm * 8}, {(void**)&s->Qm, rm * rm * 8}, {(void**)&s->sig, rm * 8},
         {(void**)&s->Ap, rm * rm * 8}, {(void**)&s->Am, rm * rm * 8},
         {(void**)&s->Pl, rm * rm * 8}, {(void**)&s->Pr, rm * rm * 8}, {(void**)&s->bl, rm * 8},
-        {(void**)&s->br, rm * 8}, {(void**)&s->gL, rm * 8}, {(void**)&s->gR, rm * 8},
+        {(void**)&s->br, rm * 8},
         {(void**)&s->Bp, rm * rm * 8}, {(void**)&s->Bm, rm * rm * 8}, {(void**)&s->cvec, rm * 8},
         {(void**)&s->nrm, 4 * 8}, {(void**)&s->Pk, rm * rm * 8}, {(void**)&s->Gv, rm * rm * 8},
         {(void**)&s->nk, rm * 8}, {(void**)&s->nl, rm * 8}, {(void**)&s->errd, 8},
@@ -3300,17 +3296,16 @@ boltz_status lr_core(boltz_shock s, const double* X, const double* S, int r, int
         return rs;
     if ((rs = boltz_project(s->g, s->V32, rh, s->Q32, s->T32, stream)) != BOLTZ_OK) return rs;
     // 1. K-step (Sec. 2.4 K-step): Euler with the upwind transport and the collision term, then QR
-    sh_ghosts(s, s->K, rh, st);
     k_sh_to_f32<<<sh_grid((size_t)rh * nx), T, 0, st>>>(s->K, s->K32, (size_t)rh * nx);
     if ((rs = boltz_kstep_collision(s->T32, rh, s->K32, nx, s->C32, stream)) != BOLTZ_OK) return rs;
-    k_sh_kupdate<<<sh_grid((size_t)rh * nx), T, 0, st>>>(s->K, s->C32, s->Ap, s->Am, s->gL, s->gR, rh, nx, dt, s->dx,
+    k_sh_kupdate<<<sh_grid((size_t)rh * nx), T, 0, st>>>(s->K, s->C32, s->Ap, s->Am, s->Pl, s->Pr, s->bl, s->br, rh, nx,
+                                                         dt, s->dx,
                                                          s->K1);
     if ((rs = qr_f64_launch(s->K1, rh, nx, s->dx, s->X1, s->S1, static_cast<char*>(s->qr_ws), s->d_int, st,
                             reinterpret_cast<unsigned*>(s->d_int + 10))) != BOLTZ_OK)
         return rs;
     // 2. S-step (Sec. 2.4 S-step): transport through the updated K, collision term with S1
-    sh_ghosts(s, s->K1, rh, st);
-    k_sh_xgram<<<dim3(rh, rh), T, 0, st>>>(s->X1, s->K1, s->gL, s->gR, rh, nx, s->Bp, s->Bm);
+    k_sh_xgram<<<dim3(rh, rh), T, 0, st>>>(s->X1, s->K1, s->Pl, s->Pr, s->bl, s->br, rh, nx, s->Bp, s->Bm);
     k_sh_triple<<<dim3(rh, rh), T, 0, st>>>(s->X1, rh, nx, s->dx, s->E32);
     k_sh_to_f32<<<1, T, 0, st>>>(s->S1, s->S32, (size_t)rh * rh);
     if ((rs = boltz_lowrank_coupling(s->E32, s->S32, rh, s->T32, s->Cs32, s->D32, stream)) != BOLTZ_OK) return rs;
@@ -3318,8 +3313,7 @@ boltz_status lr_core(boltz_shock s, const double* X, const double* S, int r, int
     // 3. L-step (Sec. 2.4 L-step): L = S2 V, transport through K~ = X'^T S2, collision term, then QR
     k_sh_comb<true><<<sh_grid((size_t)rh * nv), T, 0, st>>>(s->Vh, rh, nv, s->S2, rh, rh, s->L);
     k_sh_comb<false><<<sh_grid((size_t)rh * nx), T, 0, st>>>(s->X1, rh, nx, s->S2, rh, rh, s->Kt);
-    sh_ghosts(s, s->Kt, rh, st);
-    k_sh_xgram<<<dim3(rh, rh), T, 0, st>>>(s->X1, s->Kt, s->gL, s->gR, rh, nx, s->Bp, s->Bm);
+    k_sh_xgram<<<dim3(rh, rh), T, 0, st>>>(s->X1, s->Kt, s->Pl, s->Pr, s->bl, s->br, rh, nx, s->Bp, s->Bm);
     k_sh_to_f32<<<1, T, 0, st>>>(s->S2, s->S32, (size_t)rh * rh);
     if ((rs = boltz_lowrank_coupling(s->E32, s->S32, rh, nullptr, s->Cs32, nullptr, stream)) != BOLTZ_OK) return rs;
     if ((rs = boltz_lstep_collision(s->Q32, rh, s->Cs32, nv, s->G32, stream)) != BOLTZ_OK) return rs;
@@ -3350,7 +3344,11 @@ void lr_rotate(boltz_shock s, double* X, double* S, double* V, int rh, int rk, c
                cudaStream_t st) {
     using namespace boltz_dev;
     const int gx = (s->n_x + kLrThreads - 1) / kLrThreads, gv = (s->n_v + kLrThreads - 1) / kLrThreads;
-    if (rh <= 16) {
+    // the smallest bound >= rh: unused slots of the unrolled sums still cost FP64 issue
+    if (rh <= 8) {
+        k_rotate_f64<8><<<gx, kLrThreads, 0, st>>>(s->X1, s->U, rh, rk, s->n_x, X, r_dev, skip);
+        k_rotate_f64<8><<<gv, kLrThreads, 0, st>>>(s->Vn, s->Qm, rh, rk, s->n_v, V, r_dev, skip);
+    } else if (rh <= 16) {
         k_rotate_f64<16><<<gx, kLrThreads, 0, st>>>(s->X1, s->U, rh, rk, s->n_x, X, r_dev, skip);
         k_rotate_f64<16><<<gv, kLrThreads, 0, st>>>(s->Vn, s->Qm, rh, rk, s->n_v, V, r_dev, skip);
     } else if (rh <= 32) {

@@ -117,10 +117,12 @@ __global__ void __launch_bounds__(kShT) k_sh_vgram(const double* __restrict__ V,
 
 // Boundary values of K (Sec. 2.3, eq. "boundary general"; outflow part from
 // the first interior cell): g_L[j] = bl[j] + sum_l K_l(x_1) Pl[l][j],
-// g_R[j] = br[j] + sum_l K_l(x_N) Pr[l][j].  One block, thread j.
-__global__ void k_sh_ghosts(const double* __restrict__ K, int r, int n_x, const double* __restrict__ Pl,
-                            const double* __restrict__ Pr, const double* __restrict__ bl,
-                            const double* __restrict__ br, double* gL, double* gR) {
+// g_R[j] = br[j] + sum_l K_l(x_N) Pr[l][j].  Computed by the kernels that use
+// them, thread j of the block (r <= 64), into shared memory.
+__device__ __forceinline__ void sh_ghost_values(const double* __restrict__ K, int r, int n_x,
+                                                const double* __restrict__ Pl, const double* __restrict__ Pr,
+                                                const double* __restrict__ bl, const double* __restrict__ br,
+                                                double* gL, double* gR) {
     for (int j = threadIdx.x; j < r; j += blockDim.x) {
         double a = bl[j], b = br[j];
         for (int l = 0; l < r; ++l) {
@@ -130,6 +132,7 @@ __global__ void k_sh_ghosts(const double* __restrict__ K, int r, int n_x, const 
         gL[j] = a;
         gR[j] = b;
     }
+    __syncthreads();
 }
 
 // dx D+ K_l(x) and dx D- K_l(x): the differences only (FP64 division is slow;
@@ -146,9 +149,12 @@ __device__ __forceinline__ double sh_diff_minus(const double* K, int n_x, const 
 // K-step Euler update (Sec. 2.4, K-step (b), upwind form of Sec. 2.3):
 //   K1_j(x) = K_j(x) - dt sum_l (Ap[j][l] D+ K_l(x) + Am[j][l] D- K_l(x)) + dt C_j(x)
 __global__ void k_sh_kupdate(const double* __restrict__ K, const float* __restrict__ C, const double* __restrict__ Ap,
-                             const double* __restrict__ Am, const double* __restrict__ gL,
-                             const double* __restrict__ gR, int r, int n_x, double dt, double dx,
+                             const double* __restrict__ Am, const double* __restrict__ Pl,
+                             const double* __restrict__ Pr, const double* __restrict__ bl,
+                             const double* __restrict__ br, int r, int n_x, double dt, double dx,
                              double* __restrict__ K1) {
+    __shared__ double gL[64], gR[64];
+    sh_ghost_values(K, r, n_x, Pl, Pr, bl, br, gL, gR);
     const size_t total = (size_t)r * n_x;
     const double cfl = dt / dx;
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
@@ -165,9 +171,12 @@ __global__ void k_sh_kupdate(const double* __restrict__ K, const float* __restri
 //   Bp[i][l] = dx sum_x X_i(x) D+ K_l(x),  Bm[i][l] = dx sum_x X_i(x) D- K_l(x)
 // (the factor dx cancels the 1/dx of the differences)
 __global__ void __launch_bounds__(kShT) k_sh_xgram(const double* __restrict__ X, const double* __restrict__ K,
-                                                  const double* __restrict__ gL, const double* __restrict__ gR,
+                                                  const double* __restrict__ Pl, const double* __restrict__ Pr,
+                                                  const double* __restrict__ bl, const double* __restrict__ br,
                                                   int r, int n_x, double* Bp, double* Bm) {
     __shared__ double red[kShT / 32];
+    __shared__ double gL[64], gR[64];
+    sh_ghost_values(K, r, n_x, Pl, Pr, bl, br, gL, gR);
     const int i = blockIdx.x, l = blockIdx.y;
     const double* Xi = X + (size_t)i * n_x;
     double sp = 0.0, sm = 0.0;
