@@ -252,6 +252,57 @@ def test_full_size_lowrank_step_properties():
     assert abs(err - direct) <= 1e-8 * direct
 
 
+def test_large_velocity_grid_lowrank_steps_properties():
+    """3D 48^3 velocity grid (110592 points: the L-factor QR takes the
+    multi-kernel Cholesky-QR2 path, the K-factor QR of 8 cells the spread
+    one, both on the same workspace), three low-rank steps from the rank-2
+    bimodal state: orthonormal bases after every step; with no drop (first
+    step) the Sec. 5.1 measure equals the norm of the rebuilt change, then
+    drop_tol = 0.2 x the previous measure, as in the benchmark."""
+    import torch
+    from oracle import collision as C
+    from oracle import shock as SH
+    B = require_gpu()
+    vel = C.Problem(N=48, d=3, L=10.0, R=10.0, gamma=1.0, n_rho=2, M=6)
+    sp = SH.ShockProblem(vel=vel, n_x=8, L_x=6.0, mach=1.4)
+    g = B.boltz_grid_init(48, 3, 10.0, 10.0, 1.0, 2, 6)
+    fL, fR = sp.boundary()
+    sh = B.boltz_shock_create(g, 8, 6.0, fL, fR, 10, 0)
+    nv = 48 ** 3
+    try:
+        s = (np.tanh(0.5 * sp.x) + 1.0) / 2.0
+        dev = "cuda"
+        Yx, Rx, _ = B.boltz_qr_f64(torch.tensor(np.stack([1.0 - s, s]), device=dev), sp.dx)
+        Yv, Rv, _ = B.boltz_qr_f64(torch.tensor(np.stack([fL, fR]), device=dev), sp.wv)
+        Xd = torch.zeros((10, sp.n_x), dtype=torch.float64, device=dev)
+        Vd = torch.zeros((10, nv), dtype=torch.float64, device=dev)
+        Sd = torch.zeros(100, dtype=torch.float64, device=dev)
+        Xd[:2], Vd[:2] = Yx, Yv
+        Sd[:4] = (Rx @ Rv.T).reshape(-1)
+        r, tol = 2, 0.0
+        f_before = torch.empty((sp.n_x, nv), dtype=torch.float64, device=dev)
+        f_after = torch.empty_like(f_before)
+        for step in range(3):
+            B.boltz_shock_reconstruct(sh, Xd, Sd, Vd, r, f_before)
+            r_prev = r
+            r, err = B.boltz_shock_lowrank_step(sh, Xd, Sd, Vd, r, 0.004, tol)
+            torch.cuda.synchronize()
+            X, V = Xd[:r].cpu().numpy(), Vd[:r].cpu().numpy()
+            assert 1 <= r <= r_prev + 2
+            assert np.allclose(sp.dx * X @ X.T, np.eye(r), atol=1e-10)
+            assert np.allclose(sp.wv * V @ V.T, np.eye(r), atol=1e-10)
+            assert err > 0.0
+            if step == 0:
+                B.boltz_shock_reconstruct(sh, Xd, Sd, Vd, r, f_after)
+                torch.cuda.synchronize()
+                direct = float(np.sqrt(sp.dx * sp.wv * ((f_after - f_before) ** 2).sum().item()))
+                assert abs(err - direct) <= 1e-8 * direct
+            tol = 0.2 * err
+    finally:
+        sh.close()
+        g.close()
+
+
 def test_uniform_state_stays_uniform():
     """Mach 1 (f_L = f_R, uniform initial Maxwellian): the boundary vector lies
     in span(V) and is not added; the state changes only by dt Q(M, M)."""
