@@ -283,12 +283,15 @@ def lowrank_consumers(B, T, Q, r, n_v, flush, dev, n_x=1000, reps=20):
 
 def other_workloads():
     """Short runs of the other workloads (each in its own process, 10 timed
-    steps), reported beside the headline so that their numbers come from the
-    same run: value, time per step and each one's own roofline or rate."""
+    steps; the shock 100, since a rank change inside the timed steps costs a
+    direct step and a graph capture), reported beside the headline so that
+    their numbers come from the same run: value, time per step and each one's
+    own roofline or rate."""
     out = {}
     runs = [("c3", []), ("c4", []), ("c5", []), ("shock", []), ("shock_carleman", ["--form", "carleman"])]
     for name, extra in runs:
-        cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--config", name.split("_")[0], "--steps", "10",
+        steps = "100" if name.startswith("shock") else "10"
+        cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--config", name.split("_")[0], "--steps", steps,
                "--warmup", "3", "--no-cpu-baseline", "--no-plain", "--no-split", "--no-carleman", "--no-others"] + extra
         try:
             r = subprocess.run(cmd, capture_output=True, text=True, timeout=600)
